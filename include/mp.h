@@ -1,0 +1,202 @@
+/*
+ * mp.h -- C ABI of the B300 metapath-query engine.
+ *
+ * The engine evaluates metapath queries over a heterogeneous information network (HIN)
+ * as chains of typed sparse adjacency products in CSR form with exact uint64 path
+ * counts. Every call below follows the paper's statement of the problem:
+ *
+ *   - a HIN is a set of typed nodes and typed edges; each edge type r between node types
+ *     o' and o'' is a |o'| x |o''| 0/1 adjacency matrix A_r (Sec. 2, Def. 1);
+ *   - a metapath <o_1 ... o_n> has length n (number of node types, Def. 2) and a
+ *     constrained metapath adds per-node property constraints (Def. 3);
+ *   - a query returns every pair <v_o, v_d> joined by at least one instance, with the
+ *     number of instances (Problem 1): the non-zeros of
+ *         A_m = M_1 A_{o1 o2} M_2 A_{o2 o3} ... A_{o(n-1) o(n)} M_n,
+ *     M_i being the 0/1 diagonal of the nodes of type o_i that meet the constraints at
+ *     position i (the constrained adjacency M_c * A of Sec. 2);
+ *   - a workload is a sequence of such queries (Problem 2), served with the chain-order
+ *     planner of Sec. 3.1-3.2 (Eq. 1, Eq. 2) and the Overlap-Tree cache of Sec. 3.3-3.4.
+ *
+ * Conventions
+ *   - Every call returns an int: MP_OK (0) or a negative MP_ERR_* code; no call throws
+ *     or aborts across the ABI. mp_strerror() names a code.
+ *   - Ownership: the library copies every input array before the call returns. Result
+ *     buffers are allocated by the CALLER, sized from mp_result_info(). Tickets stay
+ *     valid until mp_release().
+ *   - Results are canonical CSR: int64 row pointers (rows+1 entries, empty rows kept),
+ *     int32 column ids strictly ascending within a row, uint64 counts >= 1, no stored
+ *     zeros. A count that does not fit in 64 bits is reported as MP_ERR_OVERFLOW on the
+ *     query's ticket, never wrapped.
+ *   - Threads: calls on one context are serialised by an internal lock.
+ *   - Device: one GPU per context (mp_config.device). Device pointers passed in or out
+ *     belong to that device.
+ */
+#ifndef MP_H_
+#define MP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MP_OK 0
+#define MP_ERR_ARG (-1)       /* malformed argument */
+#define MP_ERR_STATE (-2)     /* call not valid in the context's current state */
+#define MP_ERR_BUDGET (-3)    /* the HBM byte budget cannot hold the work */
+#define MP_ERR_TOO_LARGE (-4) /* result or intermediate beyond the size guard */
+#define MP_ERR_OVERFLOW (-5)  /* a path count exceeds 2^64 - 1 */
+#define MP_ERR_TIMEOUT (-6)   /* mp_wait timed out, or a bounded device wait gave up */
+#define MP_ERR_CUDA (-7)      /* a CUDA runtime call failed */
+#define MP_ERR_NOMEM (-8)     /* host or device allocation failed */
+#define MP_ERR_NOTFOUND (-9)  /* unknown ticket, type, property or relation */
+#define MP_ERR_INTERNAL (-10) /* a device-side consistency check failed */
+
+/* cache replacement policies (Sec. 3.4.2) */
+#define MP_POLICY_ATRAPOS 0 /* Alg. 1: PGDS utility + Overlap-Tree cost dependencies */
+#define MP_POLICY_PGDS 1    /* popularity-aware greedy dual-size */
+#define MP_POLICY_LRU 2     /* least recently used */
+#define MP_POLICY_NONE 3    /* no caching */
+
+/* chain-order planners */
+#define MP_PLAN_DP 0            /* Eq. 1 DP with the Eq. 2 cost and E_ac densities */
+#define MP_PLAN_LEFT_TO_RIGHT 1 /* ((A1 A2) A3) ... */
+#define MP_PLAN_DP_SAMPLED 2    /* Eq. 1 DP, densities from per-row nnz sampling */
+
+/* row-bin classes, for mp_config.force_bin_class (tests and the autotuner) */
+#define MP_BIN_AUTO (-1)
+#define MP_BIN_WARP_HASH 0  /* one warp per row, shared-memory hash table */
+#define MP_BIN_BLOCK_HASH 1 /* one block per row, shared-memory hash table */
+#define MP_BIN_DENSE 2      /* one block per row, dense shared-memory accumulator */
+#define MP_BIN_GLOBAL 3     /* one block per row, dense accumulator in global scratch */
+
+typedef struct mp_ctx mp_ctx;
+typedef uint64_t mp_ticket;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    uint64_t hbm_budget_bytes; /* bytes the cache may hold (Sec. 3.4 cache size) */
+    uint32_t max_slots;        /* queries admitted at once by the serving loop */
+    int32_t policy;            /* MP_POLICY_* */
+    int32_t planner;           /* MP_PLAN_* */
+    void *cuda_stream;         /* cudaStream_t to launch on; NULL = the library's own */
+    double alpha, beta, gamma; /* Eq. 2 coefficients */
+    int32_t force_bin_class;   /* MP_BIN_AUTO, or force every non-empty row into a class
+                                  (rows that cannot fit it go to the next larger one) */
+    uint64_t max_result_bytes; /* size guard per product (0 = no guard) */
+    uint64_t scratch_bytes;    /* cap on the global-accumulator scratch (0 = default) */
+    uint32_t sample_rows;      /* rows sampled per product by MP_PLAN_DP_SAMPLED */
+    uint64_t seed;             /* seed of the sampled-row choice */
+} mp_config;
+
+/* Fill *cfg with defaults: device 0, 8 GiB budget, 64 slots, ATRAPOS policy, DP
+ * planner, alpha = beta = gamma = 1, automatic bins, no size guard. */
+void mp_config_default(mp_config *cfg);
+
+/* Create a context on cfg->device. Errors: MP_ERR_ARG, MP_ERR_CUDA. */
+int mp_create(const mp_config *cfg, mp_ctx **out);
+void mp_destroy(mp_ctx *ctx);
+
+/* ---- HIN ingestion (Sec. 2, Def. 1); ingestion time is not query time (Sec. 4.1.4) */
+
+/* Declare a node type with `count` nodes (ids 0..count-1). */
+int mp_add_node_type(mp_ctx *ctx, const char *name, uint32_t count, int32_t *type_id);
+
+/* Attach an int32 property to every node of a type; `values` has `count` entries of
+ * that type, host memory, copied. */
+int mp_add_property_i32(mp_ctx *ctx, int32_t type_id, const char *prop, const int32_t *values);
+
+/* Add the edge type src_type -> dst_type from n_edges host (src, dst) pairs, copied.
+ * Repeated pairs collapse (0/1 adjacency). The reverse relation dst -> src is created
+ * too and gets id (*rel_id ^ 1). Errors: MP_ERR_ARG for out-of-range ids. */
+int mp_add_relation(mp_ctx *ctx, int32_t src_type, int32_t dst_type, uint64_t n_edges,
+                    const uint32_t *src, const uint32_t *dst, int32_t *rel_id);
+
+/* Build the device CSR of every relation and upload properties. No adds after this. */
+int mp_finalize_hin(mp_ctx *ctx);
+
+/* Look-ups by name. */
+int mp_type_id(mp_ctx *ctx, const char *name, int32_t *type_id);
+int mp_property_id(mp_ctx *ctx, int32_t type_id, const char *prop, int32_t *prop_id);
+/* Relation from src_type to dst_type (the first one added, for queries with rels=NULL). */
+int mp_relation_id(mp_ctx *ctx, int32_t src_type, int32_t dst_type, int32_t *rel_id);
+
+/* ---- queries (Sec. 2, Def. 2-3, Problem 1-2) */
+
+#define MP_OP_RANGE 0 /* lo <= v <= hi */
+#define MP_OP_EQ 1    /* v == lo */
+#define MP_OP_IN 2    /* v in set[0..set_len) */
+
+typedef struct {
+    int32_t pos;          /* 0-based position in the metapath */
+    int32_t prop;         /* property id from mp_property_id, or -1 for the node id */
+    int32_t op;           /* MP_OP_* */
+    int64_t lo, hi;
+    const uint32_t *set;  /* host array for MP_OP_IN, copied */
+    uint32_t set_len;
+} mp_constraint;
+
+typedef struct {
+    uint32_t n_types;      /* metapath length n >= 2 */
+    const int32_t *types;  /* n type ids */
+    const int32_t *rels;   /* n-1 relation ids, or NULL: the relation of each type pair */
+    uint32_t n_constraints;
+    const mp_constraint *c;
+} mp_query;
+
+/* Evaluate one query. The query is copied; the result is held under *ticket until
+ * mp_release. Query errors (MP_ERR_OVERFLOW, MP_ERR_TOO_LARGE, MP_ERR_BUDGET) are
+ * returned here and by mp_wait for the ticket. */
+int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket);
+
+/* Evaluate n queries as one workload: products shared by several queries run once;
+ * all products that are ready at the same time run in one launch per pass. tickets[i]
+ * receives the ticket of q[i]; the return value is MP_OK when every query succeeded,
+ * else the first failing query's error (each ticket keeps its own status). */
+int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ticket *tickets);
+
+/* Wait for a ticket's result: MP_OK, the query's own error, or MP_ERR_TIMEOUT. */
+int mp_wait(mp_ctx *ctx, mp_ticket ticket, uint32_t timeout_ms);
+
+/* Shape of a finished result. Any output pointer may be NULL. */
+int mp_result_info(mp_ctx *ctx, mp_ticket ticket, uint32_t *rows, uint32_t *cols, uint64_t *nnz);
+
+/* Copy a result into caller-owned buffers: row_ptr (rows+1), col (nnz), val (nnz).
+ * on_device = 0: host pointers (pageable or pinned); 1: device pointers on the
+ * context's device. Any of the three may be NULL to skip it. */
+int mp_result_copy(mp_ctx *ctx, mp_ticket ticket, int64_t *row_ptr, int32_t *col, uint64_t *val,
+                   int on_device);
+
+/* Drop a ticket and its result. */
+int mp_release(mp_ctx *ctx, mp_ticket ticket);
+
+/* Device time in milliseconds spent on the ticket's query (products it ran itself). */
+int mp_result_time(mp_ctx *ctx, mp_ticket ticket, double *ms);
+
+const char *mp_strerror(int code);
+
+/* ---- diagnostics */
+
+/* Work counters of a ticket's query: Gustavson scalar products summed over its sparse
+ * products, rows per bin class in the symbolic and numeric passes (11 entries each:
+ * warp-hash tables of 32..1024 slots, block-hash tables of 2048..8192 slots, dense
+ * shared-memory, global scratch) and the number of sparse products it ran. Any output
+ * pointer may be NULL. */
+int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t *sym_bins,
+                    uint32_t *num_bins, uint32_t *n_products);
+
+/* The chain planner alone (host only; Sec. 3.1 Eq. 1 with the Eq. 2 cost and E_ac
+ * densities of Sec. 3.2). p factors; factor t is dims[t] x dims[t+1] with nnz[t]
+ * non-zeros. known_cost / known_rho (p*p, row-major, NaN = unknown, both NULL = none)
+ * give sub-chains (i, j) whose cost and density are known. split (p*p) receives the
+ * chosen split k of every sub-chain (-1 for single factors and known sub-chains);
+ * cost (p*p, may be NULL) the optimal costs. Ties keep the smallest k. */
+int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, double alpha, double beta,
+                  double gamma, const double *known_cost, const double *known_rho, int32_t *split,
+                  double *cost);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MP_H_ */

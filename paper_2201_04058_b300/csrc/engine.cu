@@ -1,0 +1,503 @@
+// Host runtime of the metapath engine and the C ABI of include/mp.h.
+//
+// A context owns one CUDA stream, a stream-ordered device pool, the device HIN store
+// (CSR of every relation in both directions, Sec. 2 Def. 1; int32 properties) and the
+// results of submitted queries. A query (Def. 2-3, Problem 1) is evaluated as
+//   1. masks: one bitmap per constrained position, the diagonal M_i of Def. 3;
+//   2. plan:  Eq. 1 DP over the masked factors' sizes and nnz (planner.cpp);
+//   3. run:   the plan tree in post-order, one sparse product per internal node
+//             (spgemm.cu), masks applied where a base relation enters a product.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mp.h"
+#include "engine.h"
+#include "internal.h"
+
+using namespace mp;
+using Query = mp_ctx::Query;
+using Result = mp_ctx::Result;
+
+// ------------------------------------------------------------------ allocator
+
+namespace mp {
+
+struct PoolAlloc final : Alloc {
+    size_t live = 0;
+    void *alloc(size_t bytes, cudaStream_t s) override {
+        void *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void free(void *p, cudaStream_t s) override {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+}  // namespace mp
+
+// ------------------------------------------------------------------ context
+
+void mp_ctx::free_mat(Mat &m) {
+    if (m.rp) alloc->free(m.rp, stream);
+    if (m.ci) alloc->free(m.ci, stream);
+    if (m.val) alloc->free(m.val, stream);
+    m = Mat{};
+}
+
+static int check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mp: %s: %s\n", what, cudaGetErrorString(e));
+        return MP_ERR_CUDA;
+    }
+    return MP_OK;
+}
+
+extern "C" void mp_config_default(mp_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->device = 0;
+    c->hbm_budget_bytes = 8ull << 30;
+    c->max_slots = 64;
+    c->policy = MP_POLICY_ATRAPOS;
+    c->planner = MP_PLAN_DP;
+    c->cuda_stream = nullptr;
+    c->alpha = 1.0;
+    c->beta = 1.0;
+    c->gamma = 1.0;
+    c->force_bin_class = MP_BIN_AUTO;
+    c->max_result_bytes = 0;
+    c->scratch_bytes = 0;
+    c->sample_rows = 1024;
+    c->seed = 1;
+}
+
+extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
+    if (!out) return MP_ERR_ARG;
+    *out = nullptr;
+    mp_config c;
+    if (cfg) c = *cfg; else mp_config_default(&c);
+    if (c.policy < 0 || c.policy > MP_POLICY_NONE || c.planner < 0 || c.planner > MP_PLAN_DP_SAMPLED ||
+        c.force_bin_class < MP_BIN_AUTO || c.force_bin_class > MP_BIN_GLOBAL)
+        return MP_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? MP_ERR_CUDA : MP_ERR_ARG;
+    }
+    if (check_cuda(cudaSetDevice(c.device), "cudaSetDevice")) return MP_ERR_CUDA;
+    std::unique_ptr<mp_ctx> ctx(new mp_ctx());
+    ctx->cfg = c;
+    if (c.cuda_stream) {
+        ctx->stream = (cudaStream_t)c.cuda_stream;
+        ctx->own_stream = false;
+    } else {
+        if (check_cuda(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "stream")) return MP_ERR_CUDA;
+        ctx->own_stream = true;
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+    ctx->tun.sm_count = sms;
+    ctx->tun.force_class = c.force_bin_class;
+    if (c.scratch_bytes) ctx->tun.scratch_cap = c.scratch_bytes;
+    ctx->alloc.reset(new PoolAlloc());
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx.release();
+    return MP_OK;
+}
+
+extern "C" void mp_destroy(mp_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->cfg.device);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->cache_clear();
+        for (auto &kv : ctx->results) ctx->free_mat(kv.second.m);
+        ctx->results.clear();
+        for (auto &r : ctx->rels) ctx->free_mat(r.dev);
+        for (auto &p : ctx->props)
+            if (p.dev) ctx->alloc->free(p.dev, ctx->stream);
+        if (ctx->scratch.base) ctx->alloc->free(ctx->scratch.base, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        cudaEventDestroy(ctx->ev0);
+        cudaEventDestroy(ctx->ev1);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+// ------------------------------------------------------------------ HIN ingestion
+
+extern "C" int mp_add_node_type(mp_ctx *ctx, const char *name, uint32_t count, int32_t *type_id) {
+    if (!ctx || !name || !*name) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->finalized) return MP_ERR_STATE;
+    for (auto &t : ctx->types)
+        if (t.name == name) return MP_ERR_ARG;
+    ctx->types.push_back({name, count});
+    if (type_id) *type_id = (int32_t)ctx->types.size() - 1;
+    return MP_OK;
+}
+
+extern "C" int mp_add_property_i32(mp_ctx *ctx, int32_t type_id, const char *prop, const int32_t *values) {
+    if (!ctx || !prop || !*prop) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->finalized) return MP_ERR_STATE;
+    if (type_id < 0 || type_id >= (int)ctx->types.size()) return MP_ERR_NOTFOUND;
+    const uint32_t n = ctx->types[type_id].count;
+    if (n && !values) return MP_ERR_ARG;
+    for (auto &p : ctx->props)
+        if (p.type == type_id && p.name == prop) return MP_ERR_ARG;
+    mp_ctx::Prop p;
+    p.type = type_id;
+    p.name = prop;
+    p.host.assign(values, values + n);
+    ctx->props.push_back(std::move(p));
+    return MP_OK;
+}
+
+extern "C" int mp_add_relation(mp_ctx *ctx, int32_t src_type, int32_t dst_type, uint64_t n_edges,
+                               const uint32_t *src, const uint32_t *dst, int32_t *rel_id) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->finalized) return MP_ERR_STATE;
+    const int nt = (int)ctx->types.size();
+    if (src_type < 0 || src_type >= nt || dst_type < 0 || dst_type >= nt) return MP_ERR_NOTFOUND;
+    if (n_edges && (!src || !dst)) return MP_ERR_ARG;
+    const uint32_t ns = ctx->types[src_type].count, nd = ctx->types[dst_type].count;
+    for (uint64_t e = 0; e < n_edges; e++)
+        if (src[e] >= ns || dst[e] >= nd) return MP_ERR_ARG;
+    mp_ctx::Rel fwd, rev;
+    fwd.src = src_type;
+    fwd.dst = dst_type;
+    fwd.s.assign(src, src + n_edges);
+    fwd.d.assign(dst, dst + n_edges);
+    rev.src = dst_type;
+    rev.dst = src_type;
+    ctx->rels.push_back(std::move(fwd));
+    ctx->rels.push_back(std::move(rev));
+    if (rel_id) *rel_id = (int32_t)ctx->rels.size() - 2;
+    return MP_OK;
+}
+
+// Host CSR of the 0/1 adjacency of (s, d) pairs: counting sort by row, then sort and
+// de-duplicate each row.
+static void build_csr(const std::vector<uint32_t> &s, const std::vector<uint32_t> &d, uint32_t nrows,
+                      std::vector<int64_t> &rp, std::vector<int32_t> &ci) {
+    std::vector<int64_t> cnt((size_t)nrows + 1, 0);
+    for (uint32_t x : s) cnt[x + 1]++;
+    for (size_t i = 0; i < nrows; i++) cnt[i + 1] += cnt[i];
+    std::vector<int32_t> tmp(s.size());
+    std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+    for (size_t e = 0; e < s.size(); e++) tmp[cur[s[e]]++] = (int32_t)d[e];
+    rp.assign((size_t)nrows + 1, 0);
+    ci.clear();
+    ci.reserve(s.size());
+    for (uint32_t i = 0; i < nrows; i++) {
+        auto b = tmp.begin() + cnt[i], e = tmp.begin() + cnt[i + 1];
+        std::sort(b, e);
+        auto last = std::unique(b, e);
+        ci.insert(ci.end(), b, last);
+        rp[i + 1] = (int64_t)ci.size();
+    }
+}
+
+extern "C" int mp_finalize_hin(mp_ctx *ctx) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->finalized) return MP_ERR_STATE;
+    cudaSetDevice(ctx->cfg.device);
+    cudaStream_t s = ctx->stream;
+    for (size_t r = 0; r < ctx->rels.size(); r += 2) {
+        auto &f = ctx->rels[r];
+        auto &b = ctx->rels[r + 1];
+        for (int dir = 0; dir < 2; dir++) {
+            auto &R = dir == 0 ? f : b;
+            const uint32_t nr = ctx->types[R.src].count, nc = ctx->types[R.dst].count;
+            std::vector<int64_t> rp;
+            std::vector<int32_t> ci;
+            if (dir == 0) build_csr(f.s, f.d, nr, rp, ci);
+            else build_csr(f.d, f.s, nr, rp, ci);
+            Mat &m = R.dev;
+            m.nrows = nr;
+            m.ncols = nc;
+            m.nnz = (int64_t)ci.size();
+            m.rp = (int64_t *)ctx->alloc->alloc(rp.size() * 8, s);
+            m.ci = (int32_t *)ctx->alloc->alloc(std::max<size_t>(ci.size(), 1) * 4, s);
+            if (!m.rp || !m.ci) return MP_ERR_NOMEM;
+            if (check_cuda(cudaMemcpyAsync(m.rp, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, s), "upload"))
+                return MP_ERR_CUDA;
+            if (!ci.empty() &&
+                check_cuda(cudaMemcpyAsync(m.ci, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, s), "upload"))
+                return MP_ERR_CUDA;
+            if (check_cuda(cudaStreamSynchronize(s), "upload")) return MP_ERR_CUDA;
+        }
+        f.s.clear();
+        f.s.shrink_to_fit();
+        f.d.clear();
+        f.d.shrink_to_fit();
+    }
+    for (auto &p : ctx->props) {
+        size_t n = p.host.size();
+        p.dev = (int32_t *)ctx->alloc->alloc(std::max<size_t>(n, 1) * 4, s);
+        if (!p.dev) return MP_ERR_NOMEM;
+        if (n && check_cuda(cudaMemcpyAsync(p.dev, p.host.data(), n * 4, cudaMemcpyHostToDevice, s), "upload"))
+            return MP_ERR_CUDA;
+    }
+    if (check_cuda(cudaStreamSynchronize(s), "upload")) return MP_ERR_CUDA;
+    ctx->finalized = true;
+    return MP_OK;
+}
+
+extern "C" int mp_type_id(mp_ctx *ctx, const char *name, int32_t *type_id) {
+    if (!ctx || !name || !type_id) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (size_t t = 0; t < ctx->types.size(); t++)
+        if (ctx->types[t].name == name) {
+            *type_id = (int32_t)t;
+            return MP_OK;
+        }
+    return MP_ERR_NOTFOUND;
+}
+
+extern "C" int mp_property_id(mp_ctx *ctx, int32_t type_id, const char *prop, int32_t *prop_id) {
+    if (!ctx || !prop || !prop_id) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (size_t p = 0; p < ctx->props.size(); p++)
+        if (ctx->props[p].type == type_id && ctx->props[p].name == prop) {
+            *prop_id = (int32_t)p;
+            return MP_OK;
+        }
+    return MP_ERR_NOTFOUND;
+}
+
+extern "C" int mp_relation_id(mp_ctx *ctx, int32_t src_type, int32_t dst_type, int32_t *rel_id) {
+    if (!ctx || !rel_id) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (size_t r = 0; r < ctx->rels.size(); r++)
+        if (ctx->rels[r].src == src_type && ctx->rels[r].dst == dst_type) {
+            *rel_id = (int32_t)r;
+            return MP_OK;
+        }
+    return MP_ERR_NOTFOUND;
+}
+
+// ------------------------------------------------------------------ queries
+
+int mp_ctx::parse(const mp_query *q, Query &out) {
+    if (!q || q->n_types < 2 || !q->types) return MP_ERR_ARG;
+    if (q->n_constraints && !q->c) return MP_ERR_ARG;
+    const int n = (int)q->n_types;
+    out.types.assign(q->types, q->types + n);
+    for (int t : out.types)
+        if (t < 0 || t >= (int)types.size()) return MP_ERR_NOTFOUND;
+    out.rels.resize(n - 1);
+    for (int t = 0; t + 1 < n; t++) {
+        int r = -1;
+        if (q->rels) {
+            r = q->rels[t];
+            if (r < 0 || r >= (int)rels.size()) return MP_ERR_NOTFOUND;
+            if (rels[r].src != out.types[t] || rels[r].dst != out.types[t + 1]) return MP_ERR_ARG;
+        } else {
+            for (size_t x = 0; x < rels.size(); x++)
+                if (rels[x].src == out.types[t] && rels[x].dst == out.types[t + 1]) {
+                    r = (int)x;
+                    break;
+                }
+            if (r < 0) return MP_ERR_NOTFOUND;
+        }
+        out.rels[t] = r;
+    }
+    out.cons.assign(n, {});
+    for (uint32_t c = 0; c < q->n_constraints; c++) {
+        const mp_constraint &k = q->c[c];
+        if (k.pos < 0 || k.pos >= n) return MP_ERR_ARG;
+        if (k.op < MP_OP_RANGE || k.op > MP_OP_IN) return MP_ERR_ARG;
+        if (k.prop >= 0) {
+            if (k.prop >= (int)props.size() || props[k.prop].type != out.types[k.pos]) return MP_ERR_ARG;
+        } else if (k.prop != -1) {
+            return MP_ERR_ARG;
+        }
+        if (k.op == MP_OP_IN && k.set_len && !k.set) return MP_ERR_ARG;
+        Constraint cc;
+        cc.prop = k.prop;
+        cc.op = k.op;
+        cc.lo = k.lo;
+        cc.hi = k.op == MP_OP_EQ ? k.lo : k.hi;
+        if (k.op == MP_OP_IN) {
+            cc.set.assign(k.set, k.set + k.set_len);
+            std::sort(cc.set.begin(), cc.set.end());
+            cc.set.erase(std::unique(cc.set.begin(), cc.set.end()), cc.set.end());
+        }
+        out.cons[k.pos].push_back(std::move(cc));
+    }
+    return MP_OK;
+}
+
+extern "C" int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket) {
+    if (!ctx || !ticket) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->finalized) return MP_ERR_STATE;
+    cudaSetDevice(ctx->cfg.device);
+    Query qq;
+    int rc = ctx->parse(q, qq);
+    if (rc) return rc;
+    Result res;
+    rc = ctx->run_query(qq, res);
+    res.status = rc;
+    *ticket = ctx->next_ticket++;
+    ctx->results.emplace(*ticket, std::move(res));
+    return rc;
+}
+
+extern "C" int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ticket *tickets) {
+    if (!ctx || (n && (!q || !tickets))) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->finalized) return MP_ERR_STATE;
+    cudaSetDevice(ctx->cfg.device);
+    std::vector<Query> qs(n);
+    for (uint32_t i = 0; i < n; i++) {
+        int rc = ctx->parse(&q[i], qs[i]);
+        if (rc) return rc;
+    }
+    std::vector<Result> res(n);
+    int first = ctx->run_batch(qs, res);
+    for (uint32_t i = 0; i < n; i++) {
+        tickets[i] = ctx->next_ticket++;
+        ctx->results.emplace(tickets[i], std::move(res[i]));
+    }
+    return first;
+}
+
+extern "C" int mp_wait(mp_ctx *ctx, mp_ticket t, uint32_t timeout_ms) {
+    (void)timeout_ms;
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    return it->second.status;
+}
+
+extern "C" int mp_result_info(mp_ctx *ctx, mp_ticket t, uint32_t *rows, uint32_t *cols, uint64_t *nnz) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (it->second.status) return it->second.status;
+    const Mat &m = it->second.m;
+    if (rows) *rows = (uint32_t)m.nrows;
+    if (cols) *cols = (uint32_t)m.ncols;
+    if (nnz) *nnz = (uint64_t)m.nnz;
+    return MP_OK;
+}
+
+extern "C" int mp_result_copy(mp_ctx *ctx, mp_ticket t, int64_t *row_ptr, int32_t *col, uint64_t *val,
+                              int on_device) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (it->second.status) return it->second.status;
+    cudaSetDevice(ctx->cfg.device);
+    const Mat &m = it->second.m;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t s = ctx->stream;
+    if (row_ptr && check_cuda(cudaMemcpyAsync(row_ptr, m.rp, (size_t)(m.nrows + 1) * 8, k, s), "copy"))
+        return MP_ERR_CUDA;
+    if (m.nnz && col && check_cuda(cudaMemcpyAsync(col, m.ci, (size_t)m.nnz * 4, k, s), "copy"))
+        return MP_ERR_CUDA;
+    if (m.nnz && val && check_cuda(cudaMemcpyAsync(val, m.val, (size_t)m.nnz * 8, k, s), "copy"))
+        return MP_ERR_CUDA;
+    return check_cuda(cudaStreamSynchronize(s), "copy");
+}
+
+extern "C" int mp_release(mp_ctx *ctx, mp_ticket t) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    ctx->release_result(it->second);
+    ctx->results.erase(it);
+    return MP_OK;
+}
+
+extern "C" int mp_result_time(mp_ctx *ctx, mp_ticket t, double *ms) {
+    if (!ctx || !ms) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    *ms = it->second.ms;
+    return MP_OK;
+}
+
+extern "C" int mp_result_stats(mp_ctx *ctx, mp_ticket t, uint64_t *products, uint32_t *sym_bins,
+                               uint32_t *num_bins, uint32_t *n_products) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    const Result &r = it->second;
+    if (products) *products = r.st.products;
+    for (int b = 0; b < NBINS; b++) {
+        if (sym_bins) sym_bins[b] = r.st.sym_bins[b];
+        if (num_bins) num_bins[b] = r.st.num_bins[b];
+    }
+    if (n_products) *n_products = r.n_products;
+    return MP_OK;
+}
+
+extern "C" int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, double alpha, double beta,
+                             double gamma, const double *known_cost, const double *known_rho, int32_t *split,
+                             double *cost) {
+    if (p < 1 || !dims || !nnz || !split) return MP_ERR_ARG;
+    if ((known_cost == nullptr) != (known_rho == nullptr)) return MP_ERR_ARG;
+    for (uint32_t t = 0; t <= p; t++)
+        if (!(dims[t] > 0)) return MP_ERR_ARG;
+    std::vector<int> sp((size_t)p * p);
+    std::vector<double> c((size_t)p * p), r((size_t)p * p);
+    plan_chain((int)p, dims, nnz, alpha, beta, gamma, known_cost, known_rho, sp.data(), c.data(), r.data());
+    for (size_t t = 0; t < sp.size(); t++) split[t] = sp[t];
+    if (cost)
+        for (size_t t = 0; t < c.size(); t++) cost[t] = c[t];
+    return MP_OK;
+}
+
+extern "C" const char *mp_strerror(int code) {
+    switch (code) {
+        case MP_OK: return "ok";
+        case MP_ERR_ARG: return "invalid argument";
+        case MP_ERR_STATE: return "call not valid in this state";
+        case MP_ERR_BUDGET: return "HBM budget exceeded";
+        case MP_ERR_TOO_LARGE: return "result exceeds the size guard";
+        case MP_ERR_OVERFLOW: return "path count exceeds 2^64-1";
+        case MP_ERR_TIMEOUT: return "timed out";
+        case MP_ERR_CUDA: return "CUDA error";
+        case MP_ERR_NOMEM: return "out of memory";
+        case MP_ERR_NOTFOUND: return "not found";
+        case MP_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown error";
+    }
+}

@@ -1,0 +1,352 @@
+"""ctypes binding of include/mp.h (argument marshalling only).
+
+Every function below calls the C entry point of the same name in ``_lib/libmp.so``;
+all work happens in that library's CUDA kernels. ``Engine`` is a convenience wrapper
+that loads a generated HIN and turns query dicts into ``mp_query`` structs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmp.so")
+
+MP_OK = 0
+MP_ERR_ARG, MP_ERR_STATE, MP_ERR_BUDGET, MP_ERR_TOO_LARGE, MP_ERR_OVERFLOW = -1, -2, -3, -4, -5
+MP_ERR_TIMEOUT, MP_ERR_CUDA, MP_ERR_NOMEM, MP_ERR_NOTFOUND, MP_ERR_INTERNAL = -6, -7, -8, -9, -10
+MP_POLICY_ATRAPOS, MP_POLICY_PGDS, MP_POLICY_LRU, MP_POLICY_NONE = 0, 1, 2, 3
+MP_PLAN_DP, MP_PLAN_LEFT_TO_RIGHT, MP_PLAN_DP_SAMPLED = 0, 1, 2
+MP_BIN_AUTO, MP_BIN_WARP_HASH, MP_BIN_BLOCK_HASH, MP_BIN_DENSE, MP_BIN_GLOBAL = -1, 0, 1, 2, 3
+MP_OP_RANGE, MP_OP_EQ, MP_OP_IN = 0, 1, 2
+NBINS = 11
+
+EXPORTS = [
+    "mp_config_default", "mp_create", "mp_destroy", "mp_add_node_type", "mp_add_property_i32",
+    "mp_add_relation", "mp_finalize_hin", "mp_type_id", "mp_property_id", "mp_relation_id",
+    "mp_submit", "mp_submit_batch", "mp_wait", "mp_result_info", "mp_result_copy", "mp_release",
+    "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain",
+]
+
+
+class mp_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64), ("max_slots", C.c_uint32),
+                ("policy", C.c_int32), ("planner", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("force_bin_class", C.c_int32), ("max_result_bytes", C.c_uint64),
+                ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class mp_constraint(C.Structure):
+    _fields_ = [("pos", C.c_int32), ("prop", C.c_int32), ("op", C.c_int32), ("lo", C.c_int64),
+                ("hi", C.c_int64), ("set", C.c_void_p), ("set_len", C.c_uint32)]
+
+
+class mp_query(C.Structure):
+    _fields_ = [("n_types", C.c_uint32), ("types", C.c_void_p), ("rels", C.c_void_p),
+                ("n_constraints", C.c_uint32), ("c", C.c_void_p)]
+
+
+class MPError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded engine library. Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"engine library missing: {LIB_PATH} (run paper_2201_04058_b300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        P, I32, U32, U64 = C.POINTER, C.c_int32, C.c_uint32, C.c_uint64
+        sig = {
+            "mp_config_default": (None, [P(mp_config)]),
+            "mp_create": (C.c_int, [P(mp_config), P(C.c_void_p)]),
+            "mp_destroy": (None, [C.c_void_p]),
+            "mp_add_node_type": (C.c_int, [C.c_void_p, C.c_char_p, U32, P(I32)]),
+            "mp_add_property_i32": (C.c_int, [C.c_void_p, I32, C.c_char_p, C.c_void_p]),
+            "mp_add_relation": (C.c_int, [C.c_void_p, I32, I32, U64, C.c_void_p, C.c_void_p, P(I32)]),
+            "mp_finalize_hin": (C.c_int, [C.c_void_p]),
+            "mp_type_id": (C.c_int, [C.c_void_p, C.c_char_p, P(I32)]),
+            "mp_property_id": (C.c_int, [C.c_void_p, I32, C.c_char_p, P(I32)]),
+            "mp_relation_id": (C.c_int, [C.c_void_p, I32, I32, P(I32)]),
+            "mp_submit": (C.c_int, [C.c_void_p, P(mp_query), P(U64)]),
+            "mp_submit_batch": (C.c_int, [C.c_void_p, U32, P(mp_query), P(U64)]),
+            "mp_wait": (C.c_int, [C.c_void_p, U64, U32]),
+            "mp_result_info": (C.c_int, [C.c_void_p, U64, P(U32), P(U32), P(U64)]),
+            "mp_result_copy": (C.c_int, [C.c_void_p, U64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+            "mp_release": (C.c_int, [C.c_void_p, U64]),
+            "mp_result_time": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
+            "mp_strerror": (C.c_char_p, [C.c_int]),
+            "mp_result_stats": (C.c_int, [C.c_void_p, U64, P(U64), C.c_void_p, C.c_void_p, P(U32)]),
+            "mp_plan_chain": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().mp_strerror(code).decode()
+
+
+def _ck(rc, what):
+    if rc != MP_OK:
+        raise MPError(rc, what)
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+# ---- same-name wrappers of the C entry points --------------------------------------
+
+def mp_config_default() -> mp_config:
+    c = mp_config()
+    lib().mp_config_default(C.byref(c))
+    return c
+
+
+def mp_create(cfg: mp_config | None = None):
+    h = C.c_void_p()
+    _ck(lib().mp_create(C.byref(cfg) if cfg is not None else None, C.byref(h)), "mp_create")
+    return h
+
+
+def mp_destroy(ctx):
+    lib().mp_destroy(ctx)
+
+
+def mp_add_node_type(ctx, name: str, count: int) -> int:
+    t = C.c_int32()
+    _ck(lib().mp_add_node_type(ctx, name.encode(), int(count), C.byref(t)), "mp_add_node_type")
+    return t.value
+
+
+def mp_add_property_i32(ctx, type_id: int, prop: str, values):
+    v = np.ascontiguousarray(values, np.int32)
+    _ck(lib().mp_add_property_i32(ctx, type_id, prop.encode(), _ptr(v)), "mp_add_property_i32")
+
+
+def mp_add_relation(ctx, src_type: int, dst_type: int, src, dst) -> int:
+    s = np.ascontiguousarray(src, np.uint32)
+    d = np.ascontiguousarray(dst, np.uint32)
+    if s.shape != d.shape:
+        raise ValueError("src and dst differ in length")
+    r = C.c_int32()
+    _ck(lib().mp_add_relation(ctx, src_type, dst_type, s.size, _ptr(s), _ptr(d), C.byref(r)), "mp_add_relation")
+    return r.value
+
+
+def mp_finalize_hin(ctx):
+    _ck(lib().mp_finalize_hin(ctx), "mp_finalize_hin")
+
+
+def mp_type_id(ctx, name: str) -> int:
+    t = C.c_int32()
+    _ck(lib().mp_type_id(ctx, name.encode(), C.byref(t)), "mp_type_id")
+    return t.value
+
+
+def mp_property_id(ctx, type_id: int, prop: str) -> int:
+    p = C.c_int32()
+    _ck(lib().mp_property_id(ctx, type_id, prop.encode(), C.byref(p)), "mp_property_id")
+    return p.value
+
+
+def mp_relation_id(ctx, src_type: int, dst_type: int) -> int:
+    r = C.c_int32()
+    _ck(lib().mp_relation_id(ctx, src_type, dst_type, C.byref(r)), "mp_relation_id")
+    return r.value
+
+
+class _QueryBuf:
+    """Keeps the ctypes arrays of one mp_query alive."""
+
+    def __init__(self, types, rels, cons):
+        self.types = np.ascontiguousarray(types, np.int32)
+        self.rels = None if rels is None else np.ascontiguousarray(rels, np.int32)
+        self.sets = []
+        arr = (mp_constraint * max(1, len(cons)))()
+        for i, (pos, prop, op, lo, hi, st) in enumerate(cons):
+            sv = None
+            if st is not None:
+                sv = np.ascontiguousarray(st, np.uint32)
+                self.sets.append(sv)
+            arr[i] = mp_constraint(pos, prop, op, lo, hi, None if sv is None else sv.ctypes.data,
+                                   0 if sv is None else sv.size)
+        self.cons = arr
+        self.q = mp_query(self.types.size, self.types.ctypes.data,
+                          None if self.rels is None else self.rels.ctypes.data, len(cons), C.addressof(arr))
+
+
+def make_query(types, rels=None, constraints=()):
+    """constraints: iterable of (pos, prop_id or -1, op, lo, hi, set or None)."""
+    return _QueryBuf(types, rels, list(constraints))
+
+
+def mp_submit(ctx, query: _QueryBuf) -> tuple[int, int]:
+    """Returns (status, ticket); the ticket is valid even when the status is an error."""
+    t = C.c_uint64()
+    rc = lib().mp_submit(ctx, C.byref(query.q), C.byref(t))
+    if rc in (MP_ERR_ARG, MP_ERR_STATE, MP_ERR_NOTFOUND) and t.value == 0:
+        raise MPError(rc, "mp_submit")
+    return rc, t.value
+
+
+def mp_submit_batch(ctx, queries) -> tuple[int, list[int]]:
+    n = len(queries)
+    arr = (mp_query * max(1, n))(*[q.q for q in queries])
+    tk = (C.c_uint64 * max(1, n))()
+    rc = lib().mp_submit_batch(ctx, n, arr, tk)
+    if rc in (MP_ERR_ARG, MP_ERR_STATE, MP_ERR_NOTFOUND) and n and tk[0] == 0:
+        raise MPError(rc, "mp_submit_batch")
+    return rc, [int(tk[i]) for i in range(n)]
+
+
+def mp_wait(ctx, ticket: int, timeout_ms: int = 0) -> int:
+    return lib().mp_wait(ctx, ticket, timeout_ms)
+
+
+def mp_result_info(ctx, ticket: int):
+    r, c, z = C.c_uint32(), C.c_uint32(), C.c_uint64()
+    _ck(lib().mp_result_info(ctx, ticket, C.byref(r), C.byref(c), C.byref(z)), "mp_result_info")
+    return r.value, c.value, z.value
+
+
+def mp_result_copy(ctx, ticket: int, row_ptr=None, col=None, val=None, on_device: bool = False):
+    """Copy into caller buffers: numpy arrays (host) or integer device addresses."""
+    def addr(a):
+        if a is None:
+            return None
+        if isinstance(a, int):
+            return C.c_void_p(a)
+        return C.c_void_p(a.ctypes.data)
+    _ck(lib().mp_result_copy(ctx, ticket, addr(row_ptr), addr(col), addr(val), 1 if on_device else 0),
+        "mp_result_copy")
+
+
+def mp_release(ctx, ticket: int):
+    _ck(lib().mp_release(ctx, ticket), "mp_release")
+
+
+def mp_result_time(ctx, ticket: int) -> float:
+    ms = C.c_double()
+    _ck(lib().mp_result_time(ctx, ticket, C.byref(ms)), "mp_result_time")
+    return ms.value
+
+
+def mp_result_stats(ctx, ticket: int):
+    prod, npr = C.c_uint64(), C.c_uint32()
+    sb = np.zeros(NBINS, np.uint32)
+    nb = np.zeros(NBINS, np.uint32)
+    _ck(lib().mp_result_stats(ctx, ticket, C.byref(prod), _ptr(sb), _ptr(nb), C.byref(npr)), "mp_result_stats")
+    return {"products": prod.value, "sym_bins": sb, "num_bins": nb, "n_products": npr.value}
+
+
+def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None):
+    """Splits (p x p int32) and costs (p x p float64) of the C++ planner. known maps
+    (i, j) -> (cost, density)."""
+    dims = np.ascontiguousarray(dims, np.float64)
+    nnz = np.ascontiguousarray(nnz, np.float64)
+    p = nnz.size
+    kc = kr = None
+    if known:
+        kc = np.full((p, p), np.nan)
+        kr = np.full((p, p), np.nan)
+        for (i, j), (c, r) in known.items():
+            kc[i, j], kr[i, j] = c, r
+    split = np.zeros((p, p), np.int32)
+    cost = np.zeros((p, p), np.float64)
+    _ck(lib().mp_plan_chain(p, _ptr(dims), _ptr(nnz), alpha, beta, gamma, _ptr(kc), _ptr(kr), _ptr(split),
+                            _ptr(cost)), "mp_plan_chain")
+    return split, cost
+
+
+# ---- convenience wrapper -------------------------------------------------------------
+
+_OPS = {"range": MP_OP_RANGE, "eq": MP_OP_EQ, "in": MP_OP_IN}
+
+
+class Engine:
+    """One context with a HIN loaded from a generator dict (see the ``gen`` module)."""
+
+    def __init__(self, hin, **cfg_fields):
+        self.cfg = mp_config_default()
+        for k, v in cfg_fields.items():
+            setattr(self.cfg, k, v)
+        self.ctx = mp_create(self.cfg)
+        self.type_id = {}
+        for name, n in hin["types"].items():
+            self.type_id[name] = mp_add_node_type(self.ctx, name, n)
+        self.prop_id = {}
+        for (t, p), vals in hin["props"].items():
+            mp_add_property_i32(self.ctx, self.type_id[t], p, vals)
+        for a, b, s, d in hin["relations"]:
+            mp_add_relation(self.ctx, self.type_id[a], self.type_id[b], s, d)
+        mp_finalize_hin(self.ctx)
+        for (t, p) in hin["props"]:
+            self.prop_id[(t, p)] = mp_property_id(self.ctx, self.type_id[t], p)
+
+    def query(self, q):
+        cons = []
+        for c in q.get("constraints", []):
+            t = q["types"][c["pos"]]
+            prop = -1 if c.get("prop") is None else self.prop_id[(t, c["prop"])]
+            op = _OPS[c["op"]]
+            lo = int(c.get("lo", 0))
+            hi = int(c.get("hi", lo))
+            st = c.get("set") if op == MP_OP_IN else None
+            if op == MP_OP_IN and st is None:
+                st = np.zeros(0, np.uint32)
+            cons.append((int(c["pos"]), prop, op, lo, hi, st))
+        return make_query([self.type_id[t] for t in q["types"]], None, cons)
+
+    def submit(self, q):
+        return mp_submit(self.ctx, self.query(q))
+
+    def submit_batch(self, qs):
+        return mp_submit_batch(self.ctx, [self.query(q) for q in qs])
+
+    def fetch(self, ticket):
+        rows, cols, nnz = mp_result_info(self.ctx, ticket)
+        rp = np.empty(rows + 1, np.int64)
+        ci = np.empty(nnz, np.int32)
+        val = np.empty(nnz, np.uint64)
+        mp_result_copy(self.ctx, ticket, rp, ci, val)
+        return rp, ci, val
+
+    def run(self, q):
+        """Submit, fetch and release one query; raises MPError on a query error."""
+        rc, t = self.submit(q)
+        try:
+            _ck(rc, "query")
+            return self.fetch(t)
+        finally:
+            mp_release(self.ctx, t)
+
+    def release(self, ticket):
+        mp_release(self.ctx, ticket)
+
+    def close(self):
+        if self.ctx:
+            mp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

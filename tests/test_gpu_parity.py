@@ -1,0 +1,191 @@
+"""GPU parity: the engine's results, through the C ABI, equal the CPU oracle's bit for bit
+(canonical CSR with exact uint64 counts) on seeded synthetic HINs, for every row-bin
+class forced in turn, both planners, constraints of every kind, and the degenerate
+cases (length-2 metapaths, masks that empty everything, overflow)."""
+import numpy as np
+import pytest
+
+import gen
+from oracle import chain as OC
+from oracle.hin import OracleHIN
+
+pytestmark = pytest.mark.gpu
+
+BIN_CLASSES = [-1, 0, 1, 2, 3]  # auto, warp hash, block hash, dense smem, global scratch
+
+
+def _mp():
+    from paper_2201_04058_b300 import mp
+    return mp
+
+
+def assert_same(got, want, what=""):
+    for name, g, w in zip(("row_ptr", "col", "val"), got, want):
+        assert g.dtype == w.dtype, (what, name)
+        assert g.shape == w.shape, (what, name, g.shape, w.shape)
+        if not np.array_equal(g, w):
+            bad = np.nonzero(g != w)[0][:5]
+            raise AssertionError(f"{what}: {name} differs at {bad}: {g[bad]} vs {w[bad]}")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    h = gen.config1_hin()
+    return h, OracleHIN(h)
+
+
+@pytest.fixture(scope="module")
+def c1_engines(c1, cuda_ok):
+    mp = _mp()
+    engines = {b: mp.Engine(c1[0], force_bin_class=b) for b in BIN_CLASSES}
+    yield engines
+    for e in engines.values():
+        e.close()
+
+
+@pytest.mark.parametrize("force", BIN_CLASSES)
+def test_aptpa_2000_papers(c1, c1_engines, force):
+    want = OC.evaluate(c1[1], gen.config1_query())
+    assert_same(c1_engines[force].run(gen.config1_query()), want, f"APTPA bin {force}")
+
+
+@pytest.mark.parametrize("force", BIN_CLASSES)
+def test_random_constrained_queries(c1, c1_engines, force):
+    qs = gen.random_queries(c1[0], 100 + max(force, 0), 25, lengths=(2, 7), p_cons=0.4)
+    for q in qs:
+        assert_same(c1_engines[force].run(q), OC.evaluate(c1[1], q), q["types"])
+
+
+def test_forced_bins_are_used(c1, c1_engines):
+    mp = _mp()
+    q = gen.config1_query()
+    want_class = {0: range(0, 6), 1: range(6, 9), 2: [9], 3: [10]}
+    for force, bins in want_class.items():
+        e = c1_engines[force]
+        rc, t = e.submit(q)
+        assert rc == 0
+        st = mp.mp_result_stats(e.ctx, t)
+        e.release(t)
+        used = set(np.nonzero(st["num_bins"])[0].tolist()) | set(np.nonzero(st["sym_bins"])[0].tolist())
+        assert used and used <= set(bins) | {9, 10}, (force, used)
+        assert st["n_products"] >= 1 and st["products"] > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tiny_hins_every_bin(seed, cuda_ok):
+    mp = _mp()
+    h = gen.tiny_hin(seed, max_nodes=10)
+    o = OracleHIN(h)
+    qs = gen.random_queries(h, seed, 20, lengths=(2, 7), p_cons=0.5)
+    for force in BIN_CLASSES:
+        e = mp.Engine(h, force_bin_class=force)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (force, q["types"]))
+        finally:
+            e.close()
+
+
+def test_planners_agree(c1, cuda_ok):
+    mp = _mp()
+    qs = gen.random_queries(c1[0], 7, 15, lengths=(4, 7), p_cons=0.3)
+    e_dp = mp.Engine(c1[0], planner=mp.MP_PLAN_DP)
+    e_lr = mp.Engine(c1[0], planner=mp.MP_PLAN_LEFT_TO_RIGHT)
+    try:
+        for q in qs:
+            want = OC.evaluate(c1[1], q)
+            assert_same(e_dp.run(q), want, "dp")
+            assert_same(e_lr.run(q), want, "left-to-right")
+    finally:
+        e_dp.close()
+        e_lr.close()
+
+
+def test_long_metapaths_through_hubs(c1, c1_engines):
+    for q in gen.long_queries(5, 6):
+        assert_same(c1_engines[-1].run(q), OC.evaluate(c1[1], q), "".join(q["types"]))
+
+
+def test_empty_results_and_length_two(c1, c1_engines):
+    e = c1_engines[-1]
+    qs = [
+        {"types": list("APTPA"), "constraints": [{"pos": 2, "prop": None, "op": "in", "set": np.zeros(0, np.uint32)}]},
+        {"types": list("APA"), "constraints": [{"pos": 1, "prop": "year", "op": "range", "lo": 3000, "hi": 4000}]},
+        {"types": ["P", "A"], "constraints": [{"pos": 0, "prop": "year", "op": "range", "lo": 2000, "hi": 2010}]},
+        {"types": ["A", "P"], "constraints": []},
+        {"types": ["T", "P"], "constraints": [{"pos": 1, "prop": "year", "op": "in", "set": np.array([1990, 2001, 2020], np.uint32)}]},
+    ]
+    for q in qs:
+        assert_same(e.run(q), OC.evaluate(c1[1], q), q["types"])
+
+
+def test_unknown_relation_rejected(c1, c1_engines):
+    mp = _mp()
+    e = c1_engines[-1]
+    with pytest.raises(mp.MPError) as ex:
+        e.submit({"types": ["A", "V"], "constraints": []})
+    assert ex.value.code == mp.MP_ERR_NOTFOUND
+
+
+def test_overflow_is_an_error_not_a_wrap(cuda_ok):
+    """A complete bipartite 100 x 100 relation: an (ABAB...A) metapath of length 11 has
+    100^10 > 2^64 instances between every pair, so the count cannot be represented."""
+    mp = _mp()
+    n = 100
+    s = np.repeat(np.arange(n, dtype=np.uint32), n)
+    d = np.tile(np.arange(n, dtype=np.uint32), n)
+    h = {"types": {"A": n, "B": n}, "relations": [("A", "B", s, d)], "props": {}}
+    q = {"types": list("ABABABABABA"), "constraints": []}
+    with pytest.raises(OC.OracleOverflow):
+        OC.evaluate(OracleHIN(h), q)
+    for force in (-1, 0, 1, 3):
+        e = mp.Engine(h, force_bin_class=force)
+        try:
+            rc, t = e.submit(q)
+            assert rc == mp.MP_ERR_OVERFLOW, force
+            e.release(t)
+            # one step shorter fits: 100^9 < 2^64
+            q9 = {"types": list("ABABABABAB"), "constraints": []}
+            rp, ci, val = e.run(q9)
+            assert np.all(val == np.uint64(100 ** 8)) and rp[-1] == n * n
+        finally:
+            e.close()
+
+
+@pytest.fixture(scope="module")
+def c2_small(cuda_ok):
+    h = gen.config2_hin(scale=0.01)
+    return h, OracleHIN(h)
+
+
+@pytest.mark.parametrize("force", BIN_CLASSES)
+def test_scaled_scholarly_workload(c2_small, force):
+    """The twenty constrained queries of the scholarly workload on a 1 % HIN (50 k papers,
+    40 k authors): output widths beyond the dense shared-memory limit, hub rows in the
+    block-hash and global bins."""
+    mp = _mp()
+    h, o = c2_small
+    e = mp.Engine(h, force_bin_class=force)
+    try:
+        for q in gen.config2_queries(h, seed=2, n_anchor_a=32, n_anchor_t=4):
+            assert_same(e.run(q), OC.evaluate(o, q), (force, "".join(q["types"])))
+    finally:
+        e.close()
+
+
+def test_copy_to_device_buffers(c1, c1_engines):
+    import torch
+    mp = _mp()
+    e = c1_engines[-1]
+    rc, t = e.submit(gen.config1_query())
+    assert rc == 0
+    rows, cols, nnz = mp.mp_result_info(e.ctx, t)
+    rp = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
+    ci = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    val = torch.empty(nnz, dtype=torch.int64, device="cuda")
+    mp.mp_result_copy(e.ctx, t, rp.data_ptr(), ci.data_ptr(), val.data_ptr(), on_device=True)
+    e.release(t)
+    want = OC.evaluate(c1[1], gen.config1_query())
+    np.testing.assert_array_equal(rp.cpu().numpy(), want[0])
+    np.testing.assert_array_equal(ci.cpu().numpy(), want[1])
+    np.testing.assert_array_equal(val.cpu().numpy().view(np.uint64), want[2])
