@@ -1,0 +1,369 @@
+"""Benchmark of the metapath-query engine on one B300 (or N independent replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+                    [--workload scholarly] [--scale S] [--no-cpu-baseline]
+
+Workload "scholarly": a seeded scholarly-shaped HIN with 5 M papers, 4 M authors, 5 k
+venues and 50 k topics (Zipf author/topic degrees, one venue per paper, a uniform year
+per paper) and twenty constrained queries, four each of APA, APVPA, APTPA, TPAPT and
+VPTPV with year in [2010, 2020] on every paper position; all but APA are anchored on a
+seeded set of first-node entities. One step evaluates all twenty queries, each planned
+by the Eq. 1 / Eq. 2 DP, through the engine's C ABI. The HIN stays resident in HBM
+(ingestion is not query time, as in Sec. 4.1.4); L2 is flushed between steps.
+
+Prints one JSON line: queries/s (value), per-query latency p50/p99, the end-to-end rate
+with results copied to pinned host memory, the dominant kernel's achieved bandwidth
+against the measured HBM peak, clocks sampled during the timed region, the CPU oracle's
+rate on a bounded sample, and the number of kernel launches.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "metapath queries/sec, p50/p99 latency; SpGEMM GB/s vs ~8 TB/s HBM"
+UNIT = "queries/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="scholarly", choices=["scholarly"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-queries", type=int, default=5)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist
+
+
+def reduce_max(x: float, ws: int, device=None) -> float:
+    """Max of a float over ranks (identity at world size 1)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(name, scale):
+    import gen
+    if name == "scholarly":
+        hin = gen.config2_hin(seed=2, scale=scale)
+        qs = gen.config2_queries(hin, seed=2)
+        cfg = {"workload": "scholarly HIN, 20 constrained metapath queries (APA, APVPA, APTPA, TPAPT, VPTPV)",
+               "papers": hin["types"]["P"], "authors": hin["types"]["A"], "venues": hin["types"]["V"],
+               "topics": hin["types"]["T"], "queries_per_step": len(qs),
+               "constraints": "year in [2010,2020] on every P; first-node id sets of 256 A / 16 T / 16 V",
+               "planner": "Eq.1 DP, Eq.2 cost, E_ac", "cache": "off (plain one-query-at-a-time chain)",
+               "l2": "flushed between steps (512 MB write)"}
+        return hin, qs, cfg
+    raise ValueError(name)
+
+
+def query_bytes(q):
+    """Host->device payload of one query: type ids, constraint records and id sets."""
+    n = 4 * len(q["types"]) + 40 * len(q["constraints"])
+    for c in q["constraints"]:
+        if c.get("set") is not None:
+            n += 4 * len(c["set"])
+    return n
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks / traffic
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("spgemm.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2201_04058_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or None when
+    the summary is absent or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel_name)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def cpu_oracle_rate(hin, qs, n_sample):
+    """The CPU oracle as it stands (single-threaded C) on the first n_sample queries."""
+    from oracle import chain as OC
+    from oracle.hin import OracleHIN
+    o = OracleHIN(hin)
+    sample = qs[:n_sample]
+    t0 = time.perf_counter()
+    for q in sample:
+        OC.evaluate(o, q)
+    dt = time.perf_counter() - t0
+    return {"value": len(sample) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {len(sample)} of the {len(qs)} queries (one per template), single thread, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the oracle on the host cores, one query per step, cycling
+    through the workload's queries."""
+    if rank != 0:
+        return
+    hin, qs, cfg = workload(args.workload, args.scale)
+    from oracle import chain as OC
+    from oracle.hin import OracleHIN
+    o = OracleHIN(hin)
+    for i in range(args.warmup):
+        OC.evaluate(o, qs[i % len(qs)])
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        t = time.perf_counter()
+        OC.evaluate(o, qs[(args.warmup + i) % len(qs)])
+        lat.append(time.perf_counter() - t)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic", "config": dict(cfg, queries_per_step=1), "impl": "reference",
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "one query per step, cycling through the workload, single thread"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- engine leg
+
+def run_engine(args, ws, rank, local):
+    import torch
+    from paper_2201_04058_b300 import mp
+
+    torch.cuda.set_device(local)
+    dist_init(ws, "nccl")
+    dev = torch.device("cuda", local)
+    hin, qs, cfg = workload(args.workload, args.scale)
+    stream = torch.cuda.Stream(device=dev)
+    eng = mp.Engine(hin, device=local, cuda_stream=stream.cuda_stream, policy=mp.MP_POLICY_NONE)
+    bufs = [eng.query(q) for q in qs]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step(copy_out=None):
+        lat = []
+        for b in bufs:
+            rc, t = mp.mp_submit(eng.ctx, b)
+            if rc != mp.MP_OK:
+                raise mp.MPError(rc, "query")
+            lat.append(mp.mp_result_time(eng.ctx, t))
+            if copy_out is not None:
+                copy_out(t)
+            mp.mp_release(eng.ctx, t)
+        return lat
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+
+        # device-timed steps, L2 flushed between them
+        mp.mp_kernel_stats_reset(eng.ctx)
+        _, l0 = mp.mp_kernel_stats(eng.ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        lat = []
+        barrier(ws)
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                lat += step()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        barrier(ws)
+        kstats, l1 = mp.mp_kernel_stats(eng.ctx)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_s = reduce_max(sum(step_ms) / 1e3, ws, dev)
+
+        # end to end: pinned host buffers, results copied back every query
+        pinned = {}
+        d2h = [0]
+
+        def copy_out(t):
+            rows, cols, nnz = mp.mp_result_info(eng.ctx, t)
+            need = (rows + 1) * 8 + nnz * 12
+            if pinned.get("cap", 0) < need:
+                pinned["buf"] = torch.empty(need, dtype=torch.uint8, pin_memory=True)
+                pinned["cap"] = need
+            base = pinned["buf"].data_ptr()
+            mp.mp_result_copy(eng.ctx, t, base, base + (rows + 1) * 8, base + (rows + 1) * 8 + nnz * 4)
+            d2h[0] += need
+
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            flush.zero_()
+            step(copy_out)
+        torch.cuda.synchronize()
+        e2e_s = reduce_max(time.perf_counter() - t0, ws, dev)
+
+    n_q = len(qs)
+    value = ws * n_q * args.steps / total_s
+    peak, peak_kind = measured_peak()
+    dom = max(kstats.items(), key=lambda kv: kv[1]["ms"]) if kstats else None
+    roofline = None
+    if dom:
+        name, k = dom
+        ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
+        traffic = ncu_traffic(name)
+        roofline = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "traffic": traffic, "launches": k["launches"], "ms_per_launch": k["ms"] / k["launches"],
+                    "algorithmic_bytes_per_launch": k["bytes"] / k["launches"],
+                    "share_of_step": k["ms"] / sum(step_ms)}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
+           "config": dict(cfg, parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "e2e": {"value": ws * n_q * e2e_steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": sum(query_bytes(q) for q in qs),
+                   "d2h_bytes_per_step": d2h[0] // e2e_steps},
+           "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
+           "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                           "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in kstats.items()}}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(hin, qs, args.cpu_sample_queries)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    eng.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_engine(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,22 +200,28 @@ def _year_on_every(types, t, lo, hi, prop="year"):
             for i, x in enumerate(types) if x == t]
 
 
-def config2_queries(hin, seed: int = 2, n_anchor_a: int = 64, n_anchor_t: int = 4):
+def config2_queries(hin, seed: int = 2, n_anchor_a: int = 256, n_anchor_t: int = 16,
+                    n_anchor_v: int = 16):
     """Twenty constrained queries: four each of APA, APVPA, APTPA, TPAPT and VPTPV,
     with year in [2010, 2020] on every P position. APVPA and APTPA are anchored on a
-    seeded set of n_anchor_a authors and TPAPT on n_anchor_t topics (a first-node
-    id-set constraint: the 'entity of interest' of the session workloads, Sec. 4.1.2),
-    drawn uniformly among nodes with at least one edge."""
+    seeded set of n_anchor_a authors, TPAPT on n_anchor_t topics and VPTPV on
+    n_anchor_v venues (a first-node id-set constraint: the 'entity of interest' of the
+    session workloads, Sec. 4.1.2), drawn uniformly among nodes with at least one edge.
+    APA runs unanchored."""
     g = stream(seed, 500)
     deg_a = np.zeros(hin["types"]["A"], np.int64)
     deg_t = np.zeros(hin["types"]["T"], np.int64)
+    deg_v = np.zeros(hin["types"]["V"], np.int64)
     for a, b, s, d in hin["relations"]:
+        if (a, b) == ("P", "V"):
+            deg_v += np.bincount(d, minlength=deg_v.size)
         if (a, b) == ("P", "A"):
             deg_a += np.bincount(d, minlength=deg_a.size)
         if (a, b) == ("P", "T"):
             deg_t += np.bincount(d, minlength=deg_t.size)
     live_a = np.nonzero(deg_a)[0]
     live_t = np.nonzero(deg_t)[0]
+    live_v = np.nonzero(deg_v)[0]
     out = []
     for rep in range(4):
         for name in ("APA", "APVPA", "APTPA", "TPAPT", "VPTPV"):
@@ -226,6 +232,9 @@ def config2_queries(hin, seed: int = 2, n_anchor_a: int = 64, n_anchor_t: int = 
                 cons.append({"pos": 0, "prop": None, "op": "in", "set": ids.astype(np.uint32)})
             elif name == "TPAPT":
                 ids = np.sort(g.choice(live_t, size=min(n_anchor_t, live_t.size), replace=False))
+                cons.append({"pos": 0, "prop": None, "op": "in", "set": ids.astype(np.uint32)})
+            elif name == "VPTPV":
+                ids = np.sort(g.choice(live_v, size=min(n_anchor_v, live_v.size), replace=False))
                 cons.append({"pos": 0, "prop": None, "op": "in", "set": ids.astype(np.uint32)})
             out.append({"types": types, "constraints": cons})
     return out

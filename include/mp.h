@@ -186,6 +186,24 @@ const char *mp_strerror(int code);
 int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t *sym_bins,
                     uint32_t *num_bins, uint32_t *n_products);
 
+/* Per-kernel counters of the SpGEMM passes since the last reset: one entry per (pass,
+ * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
+ * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),
+ * dense, global. ms sums the device time between CUDA events recorded on the launch
+ * stream around each launch; bytes sums the algorithmic bytes of the launches (X row
+ * pointers, X entries with the two Y row pointers each looks up, one Y column id (and
+ * value, numeric pass) per Gustavson product, 12 bytes per output entry). Up to cap
+ * entries are written; *n receives the number written. *launches receives every kernel
+ * launch this library made in the process (all kernels, not only the passes). */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double ms;
+    double bytes;
+} mp_kernel_stat;
+int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, uint32_t *n, uint64_t *launches);
+int mp_kernel_stats_reset(mp_ctx *ctx);
+
 /* The chain planner alone (host only; Sec. 3.1 Eq. 1 with the Eq. 2 cost and E_ac
  * densities of Sec. 3.2). p factors; factor t is dims[t] x dims[t+1] with nnz[t]
  * non-zeros. known_cost / known_rho (p*p, row-major, NaN = unknown, both NULL = none)

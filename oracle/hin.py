@@ -16,7 +16,9 @@ import numpy as np
 def csr_from_pairs(src, dst, n_rows, n_cols):
     """0/1 CSR (int64 row pointers, int32 columns ascending per row) of the edge list."""
     key = np.asarray(src, np.int64) * int(n_cols) + np.asarray(dst, np.int64)
-    key = np.unique(key)
+    key = np.sort(key)
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     r = key // int(n_cols)
     c = (key % int(n_cols)).astype(np.int32)
     rp = np.zeros(int(n_rows) + 1, np.int64)

@@ -125,6 +125,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     ctx->alloc.reset(new PoolAlloc());
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
+    if (!ctx->prof.init()) return MP_ERR_CUDA;
     *out = ctx.release();
     return MP_OK;
 }
@@ -144,6 +145,7 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         cudaStreamSynchronize(ctx->stream);
         cudaEventDestroy(ctx->ev0);
         cudaEventDestroy(ctx->ev1);
+        ctx->prof.destroy();
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
@@ -482,6 +484,37 @@ extern "C" int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, 
     for (size_t t = 0; t < sp.size(); t++) split[t] = sp[t];
     if (cost)
         for (size_t t = 0; t < c.size(); t++) cost[t] = c[t];
+    return MP_OK;
+}
+
+extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, uint32_t *n, uint64_t *launches) {
+    if (!ctx) return MP_ERR_ARG;
+    static const char *bins[NBINS] = {"w32", "w64", "w128", "w256", "w512", "w1024",
+                                      "k2048", "k4096", "k8192", "dense", "global"};
+    std::lock_guard<std::mutex> g(ctx->mu);
+    uint32_t w = 0;
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++) {
+            const KStat &k = ctx->prof.k[p][b];
+            if (!k.launches) continue;
+            if (out && w < cap) {
+                snprintf(out[w].name, sizeof(out[w].name), "%s_%s", p ? "num" : "sym", bins[b]);
+                out[w].launches = k.launches;
+                out[w].ms = k.ms;
+                out[w].bytes = k.bytes;
+                w++;
+            }
+        }
+    if (n) *n = w;
+    if (launches) *launches = g_launches.load();
+    return MP_OK;
+}
+
+extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++) ctx->prof.k[p][b] = KStat{};
     return MP_OK;
 }
 

@@ -61,6 +61,7 @@ struct mp_ctx {
     std::unique_ptr<mp::Alloc> alloc;
     mp::Scratch scratch;
     mp::Tuning tun;
+    mp::Prof prof;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
     int parse(const mp_query *q, Query &out);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -49,6 +50,24 @@ struct Stats {
     float ms = 0.f;
 };
 
+// Per-kernel counters of the two SpGEMM passes (index [pass][bin], pass 0 = symbolic,
+// 1 = numeric): launches, device time from CUDA events around each launch, and the
+// algorithmic bytes of the work the launch did (see spgemm.cu for the byte model).
+struct KStat {
+    uint64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+struct Prof {
+    bool on = true;
+    cudaEvent_t ev[2][NBINS][2] = {};
+    KStat k[2][NBINS];
+    bool init();
+    void destroy();
+};
+
+// Kernel launches made by this library in this process.
+extern std::atomic<uint64_t> g_launches;
+
 // An owned device CSR result.
 struct Mat {
     int64_t nrows = 0, ncols = 0, nnz = 0;
@@ -87,7 +106,7 @@ void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned 
 // C = diag(rm) X diag(km) Y diag(cm). Masks may be nullptr. Returns MP_* code.
 int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
            const uint32_t *cm, Alloc &al, Scratch &scr, const Tuning &tun, cudaStream_t s,
-           uint64_t max_result_bytes, Mat *out, Stats *st);
+           uint64_t max_result_bytes, Mat *out, Stats *st, Prof *prof);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,

@@ -116,7 +116,7 @@ int mp_ctx::exec(const Query &q, const std::vector<uint32_t *> &masks, const std
     const uint32_t *cm = (k + 1 == j) ? masks[j + 1] : nullptr;
     Mat C;
     rc = spgemm(L.m.view(), R.m.view(), rm, km, cm, *alloc, scratch, tun, stream, cfg.max_result_bytes, &C,
-                &r.st);
+                &r.st, &prof);
     r.n_products++;
     if (L.owned) free_mat(L.m);
     if (R.owned) free_mat(R.m);

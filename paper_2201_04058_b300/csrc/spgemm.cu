@@ -25,11 +25,36 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <utility>
 
 #include "../../include/mp.h"
 #include "internal.h"
 
 namespace mp {
+
+std::atomic<uint64_t> g_launches{0};
+
+bool Prof::init() {
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++)
+            for (int e = 0; e < 2; e++)
+                if (cudaEventCreate(&ev[p][b][e]) != cudaSuccess) return false;
+    return true;
+}
+
+void Prof::destroy() {
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++)
+            for (int e = 0; e < 2; e++)
+                if (ev[p][b][e]) cudaEventDestroy(ev[p][b][e]);
+}
+
+// Every kernel launch of the library goes through kl(), which counts it.
+template <class... KArgs, class... Args>
+static inline void kl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args &&...args) {
+    k<<<g, b, smem, s>>>(std::forward<Args>(args)...);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 static constexpr uint32_t EMPTY = 0xffffffffu;
 static constexpr unsigned FULL = 0xffffffffu;
@@ -116,21 +141,21 @@ static inline unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1
 
 void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s) {
     int64_t nw = (n + 31) / 32;
-    if (nw) k_mask_fill<<<grid_for(nw, 256), 256, 0, s>>>(m, nw, ones ? FULL : 0u, n);
+    if (nw) kl(k_mask_fill, grid_for(nw, 256), 256, 0, s, m, nw, ones ? FULL : 0u, n);
 }
 
 void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
                     cudaStream_t s) {
-    if (n) k_mask_and_range<<<grid_for(n, 256), 256, 0, s>>>(m, prop, n, lo, hi);
+    if (n) kl(k_mask_and_range, grid_for(n, 256), 256, 0, s, m, prop, n, lo, hi);
 }
 
 void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t len, int64_t n,
                   cudaStream_t s) {
     int64_t nw = (n + 31) / 32;
     if (!nw) return;
-    k_mask_fill<<<grid_for(nw, 256), 256, 0, s>>>(tmp, nw, 0u, n);
-    if (len) k_set_bits<<<grid_for(len, 256), 256, 0, s>>>(tmp, set, len, n);
-    k_and_words<<<grid_for(nw, 256), 256, 0, s>>>(m, tmp, nw);
+    kl(k_mask_fill, grid_for(nw, 256), 256, 0, s, tmp, nw, 0u, n);
+    if (len) kl(k_set_bits, grid_for(len, 256), 256, 0, s, tmp, set, len, n);
+    kl(k_and_words, grid_for(nw, 256), 256, 0, s, m, tmp, nw);
 }
 
 // nnz of diag(rm) A diag(cm): one warp per row.
@@ -157,7 +182,7 @@ void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned 
                 cudaStream_t s) {
     if (!A.nrows) return;
     unsigned g = (unsigned)std::min<int64_t>(grid_for(A.nrows * 32, 256), 148 * 16);
-    k_masked_nnz<<<g, 256, 0, s>>>(A, rm, cm, out);
+    kl(k_masked_nnz, g, 256, 0, s, A, rm, cm, out);
 }
 
 // ------------------------------------------------------------------ scan
@@ -246,9 +271,9 @@ void scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *part = (int64_t *)al.alloc((size_t)(nb + 1) * sizeof(int64_t), s);
-    k_scan_tiles<<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, part);
-    k_scan_parts<<<1, 1024, 0, s>>>(part, nb);
-    k_scan_apply<<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, n, part, nb);
+    kl(k_scan_tiles, (unsigned)nb, SCAN_T, 0, s, in, n, part);
+    kl(k_scan_parts, 1, 1024, 0, s, part, nb);
+    kl(k_scan_apply, (unsigned)nb, SCAN_T, 0, s, in, out, n, part, nb);
     al.free(part, s);
 }
 
@@ -259,13 +284,36 @@ struct BinArgs {
     int dense_max_cols, dense_min_u, force;
 };
 
+// Per-bin tallies of one pass: rows, X entries, Gustavson products and output entries
+// (the inputs of the algorithmic byte count of each bin's kernel).
+struct BinTally {
+    uint32_t counts[NBINS];
+    unsigned long long xent[NBINS], prods[NBINS], outn[NBINS];
+};
+
+__device__ __forceinline__ void tally_flush(BinTally *g, uint32_t *hc, unsigned long long *hx,
+                                            unsigned long long *hp, unsigned long long *ho) {
+    const int t = threadIdx.x;
+    if (t < NBINS && hc[t]) {
+        atomicAdd(g->counts + t, hc[t]);
+        atomicAdd(g->xent + t, hx[t]);
+        atomicAdd(g->prods + t, hp[t]);
+        if (ho) atomicAdd(g->outn + t, ho[t]);
+    }
+}
+
 // prod_i and the symbolic bin of every row; rows with prod_i = 0 get nnz_i = 0 and no bin.
 __global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km, BinArgs ba,
-                          uint64_t *prod, int8_t *bin, int64_t *nnz, uint32_t *counts,
+                          uint64_t *prod, int8_t *bin, int64_t *nnz, BinTally *tally,
                           unsigned long long *total_prod) {
-    __shared__ uint32_t hist[NBINS];
+    __shared__ uint32_t hc[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS];
     __shared__ unsigned long long bsum;
-    if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
+    if (threadIdx.x < NBINS) {
+        hc[threadIdx.x] = 0;
+        hx[threadIdx.x] = 0;
+        hp[threadIdx.x] = 0;
+    }
     if (threadIdx.x == 0) bsum = 0;
     __syncthreads();
     int lane = threadIdx.x & 31;
@@ -274,8 +322,10 @@ __global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km
     unsigned long long mysum = 0;
     for (int64_t i = w; i < X.nrows; i += nwarps) {
         uint64_t s = 0;
+        int64_t b = 0, e = 0;
         if (bit_of(rm, (uint32_t)i)) {
-            int64_t b = X.rp[i], e = X.rp[i + 1];
+            b = X.rp[i];
+            e = X.rp[i + 1];
             for (int64_t p = b + lane; p < e; p += 32) {
                 int32_t k = __ldg(X.ci + p);
                 if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
@@ -284,27 +334,36 @@ __global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km
         }
         if (lane == 0) {
             prod[i] = s;
-            int b = -1;
+            int bb = -1;
             if (s) {
-                b = bin_for(s, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.force);
-                atomicAdd(&hist[b], 1u);
+                bb = bin_for(s, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.force);
+                atomicAdd(&hc[bb], 1u);
+                atomicAdd(&hx[bb], (unsigned long long)(e - b));
+                atomicAdd(&hp[bb], (unsigned long long)s);
             } else {
                 nnz[i] = 0;
             }
-            bin[i] = (int8_t)b;
+            bin[i] = (int8_t)bb;
             mysum += s;
         }
     }
     if (lane == 0 && mysum) atomicAdd(&bsum, mysum);
     __syncthreads();
-    if (threadIdx.x < NBINS && hist[threadIdx.x]) atomicAdd(counts + threadIdx.x, hist[threadIdx.x]);
+    tally_flush(tally, hc, hx, hp, nullptr);
     if (threadIdx.x == 0 && bsum) atomicAdd(total_prod, bsum);
 }
 
 // Numeric bins from exact row sizes (nnz = rp[i+1] - rp[i]).
-__global__ void k_numbin(const int64_t *rp, int64_t n, BinArgs ba, int8_t *bin, uint32_t *counts) {
-    __shared__ uint32_t hist[NBINS];
-    if (threadIdx.x < NBINS) hist[threadIdx.x] = 0;
+__global__ void k_numbin(const int64_t *rp, const int64_t *xrp, const uint64_t *prod, int64_t n, BinArgs ba,
+                         int8_t *bin, BinTally *tally) {
+    __shared__ uint32_t hc[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS];
+    if (threadIdx.x < NBINS) {
+        hc[threadIdx.x] = 0;
+        hx[threadIdx.x] = 0;
+        hp[threadIdx.x] = 0;
+        ho[threadIdx.x] = 0;
+    }
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -312,12 +371,15 @@ __global__ void k_numbin(const int64_t *rp, int64_t n, BinArgs ba, int8_t *bin, 
         int b = -1;
         if (z) {
             b = bin_for((uint64_t)z, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.force);
-            atomicAdd(&hist[b], 1u);
+            atomicAdd(&hc[b], 1u);
+            atomicAdd(&hx[b], (unsigned long long)(xrp[i + 1] - xrp[i]));
+            atomicAdd(&hp[b], (unsigned long long)prod[i]);
+            atomicAdd(&ho[b], (unsigned long long)z);
         }
         bin[i] = (int8_t)b;
     }
     __syncthreads();
-    if (threadIdx.x < NBINS && hist[threadIdx.x]) atomicAdd(counts + threadIdx.x, hist[threadIdx.x]);
+    tally_flush(tally, hc, hx, hp, ho);
 }
 
 // counts[0..NBINS) -> offsets[0..NBINS]; cursors reset.
@@ -845,7 +907,7 @@ __global__ void __launch_bounds__(NT) k_num_global(PassArgs a, int bin) {
 template <class K>
 static void launch(K kern, unsigned grid, int nt, size_t smem, cudaStream_t s, const PassArgs &a, int bin) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, nt, smem, s>>>(a, bin);
+    kl(kern, grid, nt, smem, s, a, bin);
 }
 
 static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_blocks) {
@@ -853,55 +915,94 @@ static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_bloc
     return std::max(1u, std::min(g, (unsigned)max_blocks));
 }
 
-// Launch every bin's kernel of one pass. Counts live on the device; each grid loops
-// over its bin's rows, so an empty bin costs one short launch. host_counts (if not
-// null) limits launches to the non-empty bins and sizes the grids.
-static void run_pass(bool numeric, const PassArgs &a, const uint32_t *host_counts, int64_t ncols,
-                     int nscr_ctas, const Tuning &tun, cudaStream_t s) {
+// Launch every non-empty bin's kernel of one pass, each grid sized to its bin's rows
+// (capped at a few blocks per SM; the kernels loop over their bin). With prof, CUDA
+// events bracket each launch.
+static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t ncols, int nscr_ctas,
+                     const Tuning &tun, cudaStream_t s, Prof *prof) {
+    const bool numeric = pass == 1;
     const int sms = tun.sm_count;
-    auto has = [&](int b) { return host_counts == nullptr || host_counts[b] > 0; };
-    auto up = [&](int b) { return host_counts ? host_counts[b] : 0xffffffffu; };
     const size_t stage = sizeof(Stage);
-#define WARP_BIN(BIN, T, W)                                                                     \
-    if (has(BIN)) {                                                                             \
-        unsigned g = blocks_for(up(BIN), W, sms * 8);                                           \
-        if (numeric)                                                                            \
-            launch(k_num_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 12, s, a, BIN); \
-        else                                                                                    \
-            launch(k_sym_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 4, s, a, BIN);  \
+    for (int b = 0; b < NBINS; b++) {
+        const uint32_t rows = host_counts[b];
+        if (!rows) continue;
+        if (b == B_DENSE && ncols > tun.dense_max_cols) continue;
+        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][0], s);
+        switch (b) {
+#define WARP_BIN(BIN, T, W)                                                                              \
+    case BIN: {                                                                                          \
+        unsigned g = blocks_for(rows, W, sms * 8);                                                       \
+        if (numeric)                                                                                     \
+            launch(k_num_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 12, s, a, BIN);        \
+        else                                                                                             \
+            launch(k_sym_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 4, s, a, BIN);         \
+        break;                                                                                           \
     }
-    WARP_BIN(B_W32, 32, 8)
-    WARP_BIN(B_W64, 64, 8)
-    WARP_BIN(B_W128, 128, 8)
-    WARP_BIN(B_W256, 256, 8)
-    WARP_BIN(B_W512, 512, 4)
-    WARP_BIN(B_W1024, 1024, 4)
+            WARP_BIN(B_W32, 32, 8)
+            WARP_BIN(B_W64, 64, 8)
+            WARP_BIN(B_W128, 128, 8)
+            WARP_BIN(B_W256, 256, 8)
+            WARP_BIN(B_W512, 512, 4)
+            WARP_BIN(B_W1024, 1024, 4)
 #undef WARP_BIN
 #define BLOCK_BIN(BIN, T, NT)                                                              \
-    if (has(BIN)) {                                                                        \
-        unsigned g = blocks_for(up(BIN), 1, sms * 4);                                      \
+    case BIN: {                                                                            \
+        unsigned g = blocks_for(rows, 1, sms * 4);                                         \
         if (numeric)                                                                       \
             launch(k_num_block<T, NT>, g, NT, NT * stage + (size_t)T * 12, s, a, BIN);     \
         else                                                                               \
             launch(k_sym_block<T, NT>, g, NT, NT * stage + (size_t)T * 4, s, a, BIN);      \
+        break;                                                                             \
     }
-    BLOCK_BIN(B_K2048, 2048, 256)
-    BLOCK_BIN(B_K4096, 4096, 512)
-    BLOCK_BIN(B_K8192, 8192, 1024)
+            BLOCK_BIN(B_K2048, 2048, 256)
+            BLOCK_BIN(B_K4096, 4096, 512)
+            BLOCK_BIN(B_K8192, 8192, 1024)
 #undef BLOCK_BIN
-    if (has(B_DENSE) && ncols <= tun.dense_max_cols) {
-        unsigned g = blocks_for(up(B_DENSE), 1, sms * 4);
-        if (numeric)
-            launch(k_num_dense<256>, g, 256, 256 * stage + (size_t)ncols * 8, s, a, B_DENSE);
-        else
-            launch(k_sym_dense<256>, g, 256, 256 * stage + (size_t)((ncols + 31) / 32) * 4, s, a, B_DENSE);
+            case B_DENSE: {
+                unsigned g = blocks_for(rows, 1, sms * 4);
+                if (numeric)
+                    launch(k_num_dense<256>, g, 256, 256 * stage + (size_t)ncols * 8, s, a, B_DENSE);
+                else
+                    launch(k_sym_dense<256>, g, 256, 256 * stage + (size_t)((ncols + 31) / 32) * 4, s, a, B_DENSE);
+                break;
+            }
+            case B_GLOBAL: {
+                unsigned g = blocks_for(rows, 1, nscr_ctas);
+                if (numeric)
+                    launch(k_num_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
+                else
+                    launch(k_sym_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
+                break;
+            }
+        }
+        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][1], s);
     }
-    if (has(B_GLOBAL)) {
-        unsigned g = blocks_for(up(B_GLOBAL), 1, nscr_ctas);
-        if (numeric)
-            launch(k_num_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
-        else
-            launch(k_sym_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
+}
+
+// Algorithmic bytes of one bin's kernel in one pass (every X entry: column id, value if
+// any, and the two Y row pointers it looks up; every Gustavson product: the Y column id
+// and, in the numeric pass, the Y value; every output entry: column id + uint64 value;
+// every row: its X row pointers, and its nnz (symbolic) or C row pointers (numeric)).
+static double bin_bytes(int pass, const BinTally &t, int b, bool x_val, bool y_val) {
+    const double rows = t.counts[b], xe = (double)t.xent[b], pr = (double)t.prods[b], on = (double)t.outn[b];
+    if (pass == 0) return rows * 16 + xe * (4 + 16) + pr * 4 + rows * 8;
+    return rows * 32 + xe * (4 + (x_val ? 8 : 0) + 16) + pr * (4 + (y_val ? 8 : 0)) + on * 12;
+}
+
+static void prof_collect(Prof *prof, int pass, const BinTally &t, bool x_val, bool y_val, int64_t ncols,
+                         const Tuning &tun) {
+    if (!prof || !prof->on) return;
+    for (int b = 0; b < NBINS; b++) {
+        if (!t.counts[b] || (b == B_DENSE && ncols > tun.dense_max_cols)) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof->ev[pass][b][0], prof->ev[pass][b][1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        KStat &k = prof->k[pass][b];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += bin_bytes(pass, t, b, x_val, y_val);
     }
 }
 
@@ -912,16 +1013,17 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
         cudaError_t e_ = (x);                                                     \
         if (e_ != cudaSuccess) {                                                  \
             fprintf(stderr, "mp: %s failed: %s\n", #x, cudaGetErrorString(e_));   \
-            return MP_ERR_CUDA;                                                   \
+            rc = MP_ERR_CUDA;                                                     \
+            goto fail;                                                            \
         }                                                                         \
     } while (0)
 
-// Make the scratch hold n slices of `stride` bytes, zeroed. Returns slices available.
+// Make the scratch hold up to one slice of `stride` bytes per SM, zeroed, within the
+// scratch cap. Returns the number of slices available (0 on allocation failure).
 static int ensure_scratch(Scratch &scr, size_t stride, const Tuning &tun, Alloc &al, cudaStream_t s) {
-    int want = tun.sm_count;
     size_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
     int fit = (int)std::max<size_t>(1, cap / stride);
-    int n = std::min(want, fit);
+    int n = std::min(tun.sm_count, fit);
     size_t need = stride * (size_t)n;
     if (scr.bytes < need) {
         if (scr.base) al.free(scr.base, s);
@@ -938,137 +1040,151 @@ static int ensure_scratch(Scratch &scr, size_t stride, const Tuning &tun, Alloc 
 
 int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km, const uint32_t *cm,
            Alloc &al, Scratch &scr, const Tuning &tun, cudaStream_t s, uint64_t max_result_bytes,
-           Mat *out, Stats *st) {
+           Mat *out, Stats *st, Prof *prof) {
     const int64_t m = X.nrows;
     out->nrows = m;
     out->ncols = Y.ncols;
     out->nnz = 0;
-    // workspace: prod u64[m], bins i8[m], list u32[m], counts/offsets/cursors, err, totals
     struct Small {
-        uint32_t counts[NBINS];
+        BinTally tally;
         uint32_t offsets[NBINS + 1];
         uint32_t cursors[NBINS];
         uint32_t err;
         unsigned long long total_prod;
     };
+    // workspace: prod u64[m], bins i8[m], row list u32[m], two Small blocks
     const size_t off_prod = 0;
     const size_t off_bin = align256(off_prod + (size_t)m * 8);
     const size_t off_list = align256(off_bin + (size_t)m);
     const size_t off_small = align256(off_list + (size_t)m * 4);
     const size_t ws_bytes = align256(off_small + sizeof(Small) * 2);
+    const size_t stride = align256((size_t)Y.ncols * 8 + (size_t)((Y.ncols + 31) / 32) * 4);
+    const BinArgs ba{Y.ncols, tun.dense_max_cols, tun.dense_min_u, tun.force_class};
+    int rc = MP_OK;
+    int nscr = 0;
+    int64_t nnz = 0;
+    uint32_t err = 0;
+    Small h_sym, h_num;
+    PassArgs pa{};
+    uint64_t *prod;
+    int8_t *bin;
+    uint32_t *list;
+    Small *sm_sym, *sm_num;
     char *ws = (char *)al.alloc(ws_bytes, s);
     out->rp = (int64_t *)al.alloc((size_t)(m + 1) * 8, s);
     if (!ws || !out->rp) {
-        if (ws) al.free(ws, s);
-        if (out->rp) al.free(out->rp, s);
-        out->rp = nullptr;
-        return MP_ERR_NOMEM;
+        rc = MP_ERR_NOMEM;
+        goto fail;
     }
-    uint64_t *prod = (uint64_t *)(ws + off_prod);
-    int8_t *bin = (int8_t *)(ws + off_bin);
-    uint32_t *list = (uint32_t *)(ws + off_list);
-    Small *sm_sym = (Small *)(ws + off_small);
-    Small *sm_num = sm_sym + 1;
+    prod = (uint64_t *)(ws + off_prod);
+    bin = (int8_t *)(ws + off_bin);
+    list = (uint32_t *)(ws + off_list);
+    sm_sym = (Small *)(ws + off_small);
+    sm_num = sm_sym + 1;
     CK(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s));
 
-    BinArgs ba{Y.ncols, tun.dense_max_cols, tun.dense_min_u, tun.force_class};
-    // scratch for the GLOBAL bin
-    const size_t stride = align256((size_t)Y.ncols * 8 + (size_t)((Y.ncols + 31) / 32) * 4);
-
+    // 1-2. per-row work, symbolic bins, rows grouped by bin
     if (m > 0) {
         unsigned g = (unsigned)std::min<int64_t>(grid_for(m * 32, 256), (int64_t)tun.sm_count * 32);
-        k_rowwork<<<g, 256, 0, s>>>(X, Y, rm, km, ba, prod, bin, out->rp, sm_sym->counts,
-                                    &sm_sym->total_prod);
-        k_bin_offsets<<<1, 32, 0, s>>>(sm_sym->counts, sm_sym->offsets, sm_sym->cursors);
+        kl(k_rowwork, g, 256, 0, s, X, Y, rm, km, ba, prod, bin, out->rp, &sm_sym->tally, &sm_sym->total_prod);
+        kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
         unsigned gf = (unsigned)std::min<int64_t>(grid_for(m, 256), (int64_t)tun.sm_count * 16);
-        k_bin_fill<<<gf, 256, 0, s>>>(bin, m, sm_sym->offsets, sm_sym->cursors, list);
+        kl(k_bin_fill, gf, 256, 0, s, bin, m, sm_sym->offsets, sm_sym->cursors, list);
     }
-    // bin counts to the host: grids sized to the work, empty bins skipped
-    Small h_sym;
     CK(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    int nscr = 0;
-    if (h_sym.counts[B_GLOBAL]) {
+    if (h_sym.tally.counts[B_GLOBAL]) {
         nscr = ensure_scratch(scr, stride, tun, al, s);
         if (!nscr) {
-            al.free(ws, s);
-            al.free(out->rp, s);
-            out->rp = nullptr;
-            return MP_ERR_NOMEM;
+            rc = MP_ERR_NOMEM;
+            goto fail;
         }
     }
-    PassArgs pa{};
+    // 3-4. symbolic pass, row pointers
     pa.X = X;
     pa.Y = Y;
     pa.km = km;
     pa.cm = cm;
     pa.list = list;
-    pa.counts = sm_sym->counts;
+    pa.counts = sm_sym->tally.counts;
     pa.offsets = sm_sym->offsets;
     pa.nnz = out->rp;
     pa.err = &sm_sym->err;
     pa.scratch = (char *)scr.base;
     pa.scratch_stride = stride;
-    if (m > 0) run_pass(false, pa, h_sym.counts, Y.ncols, nscr, tun, s);
+    if (m > 0) run_pass(0, pa, h_sym.tally.counts, Y.ncols, nscr, tun, s, prof);
     scan_i64(out->rp, out->rp, m, al, s);
-    int64_t nnz = 0;
-    uint32_t err = 0;
     CK(cudaMemcpyAsync(&nnz, out->rp + m, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&err, &sm_sym->err, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    prof_collect(prof, 0, h_sym.tally, X.val != nullptr, Y.val != nullptr, Y.ncols, tun);
     if (st) {
         st->products += h_sym.total_prod;
-        for (int b = 0; b < NBINS; b++) st->sym_bins[b] += h_sym.counts[b];
+        for (int b = 0; b < NBINS; b++) st->sym_bins[b] += h_sym.tally.counts[b];
     }
     if (err) {
-        al.free(ws, s);
-        return (err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+        rc = (err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+        goto fail;
     }
     out->nnz = nnz;
     if (max_result_bytes && out->bytes() > max_result_bytes) {
-        al.free(ws, s);
-        return MP_ERR_TOO_LARGE;
+        rc = MP_ERR_TOO_LARGE;
+        goto fail;
     }
     out->ci = (int32_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s);
     out->val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
     if (!out->ci || !out->val) {
-        al.free(ws, s);
-        return MP_ERR_NOMEM;
+        rc = MP_ERR_NOMEM;
+        goto fail;
     }
+    // 5. numeric pass on bins of the exact row sizes
     if (nnz > 0) {
         unsigned g = (unsigned)std::min<int64_t>(grid_for(m, 256), (int64_t)tun.sm_count * 16);
-        k_numbin<<<g, 256, 0, s>>>(out->rp, m, ba, bin, sm_num->counts);
-        k_bin_offsets<<<1, 32, 0, s>>>(sm_num->counts, sm_num->offsets, sm_num->cursors);
-        k_bin_fill<<<g, 256, 0, s>>>(bin, m, sm_num->offsets, sm_num->cursors, list);
-        Small h_num;
+        kl(k_numbin, g, 256, 0, s, out->rp, X.rp, prod, m, ba, bin, &sm_num->tally);
+        kl(k_bin_offsets, 1, 32, 0, s, sm_num->tally.counts, sm_num->offsets, sm_num->cursors);
+        kl(k_bin_fill, g, 256, 0, s, bin, m, sm_num->offsets, sm_num->cursors, list);
         CK(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (h_num.counts[B_GLOBAL]) {
+        if (h_num.tally.counts[B_GLOBAL]) {
             nscr = ensure_scratch(scr, stride, tun, al, s);
             if (!nscr) {
-                al.free(ws, s);
-                return MP_ERR_NOMEM;
+                rc = MP_ERR_NOMEM;
+                goto fail;
             }
         }
-        pa.counts = sm_num->counts;
+        pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
         pa.rp = out->rp;
         pa.out_ci = out->ci;
         pa.out_val = out->val;
         pa.err = &sm_num->err;
         pa.scratch = (char *)scr.base;
-        run_pass(true, pa, h_num.counts, Y.ncols, nscr, tun, s);
+        run_pass(1, pa, h_num.tally.counts, Y.ncols, nscr, tun, s, prof);
         CK(cudaMemcpyAsync(&err, &sm_num->err, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        prof_collect(prof, 1, h_num.tally, X.val != nullptr, Y.val != nullptr, Y.ncols, tun);
         if (st)
-            for (int b = 0; b < NBINS; b++) st->num_bins[b] += h_num.counts[b];
+            for (int b = 0; b < NBINS; b++) st->num_bins[b] += h_num.tally.counts[b];
+        if (err) {
+            rc = (err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+            goto fail;
+        }
     }
+    CK(cudaGetLastError());
     al.free(ws, s);
     if (st) st->nnz += (uint64_t)nnz;
-    CK(cudaGetLastError());
-    if (err) return (err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
     return MP_OK;
+fail:
+    if (ws) al.free(ws, s);
+    if (out->rp) al.free(out->rp, s);
+    if (out->ci) al.free(out->ci, s);
+    if (out->val) al.free(out->val, s);
+    out->rp = nullptr;
+    out->ci = nullptr;
+    out->val = nullptr;
+    return rc;
 }
+#undef CK
 
 // ------------------------------------------------------------------ length-2 metapaths
 
@@ -1108,6 +1224,15 @@ __global__ void k_filter_fill(DCsr A, const uint32_t *rm, const uint32_t *cm, co
     }
 }
 
+#define CK(x)                                                                     \
+    do {                                                                          \
+        cudaError_t e_ = (x);                                                     \
+        if (e_ != cudaSuccess) {                                                  \
+            fprintf(stderr, "mp: %s failed: %s\n", #x, cudaGetErrorString(e_));   \
+            return MP_ERR_CUDA;                                                   \
+        }                                                                         \
+    } while (0)
+
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, const Tuning &tun,
            cudaStream_t s, Mat *out) {
     const int64_t m = A.nrows;
@@ -1116,7 +1241,7 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
     out->rp = (int64_t *)al.alloc((size_t)(m + 1) * 8, s);
     if (!out->rp) return MP_ERR_NOMEM;
     unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(m * 32, 256), (int64_t)tun.sm_count * 32));
-    if (m) k_filter_count<<<g, 256, 0, s>>>(A, rm, cm, out->rp);
+    if (m) kl(k_filter_count, g, 256, 0, s, A, rm, cm, out->rp);
     scan_i64(out->rp, out->rp, m, al, s);
     int64_t nnz = 0;
     CK(cudaMemcpyAsync(&nnz, out->rp + m, 8, cudaMemcpyDeviceToHost, s));
@@ -1125,7 +1250,7 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
     out->ci = (int32_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s);
     out->val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
     if (!out->ci || !out->val) return MP_ERR_NOMEM;
-    if (nnz) k_filter_fill<<<g, 256, 0, s>>>(A, rm, cm, out->rp, out->ci, out->val);
+    if (nnz) kl(k_filter_fill, g, 256, 0, s, A, rm, cm, out->rp, out->ci, out->val);
     CK(cudaGetLastError());
     return MP_OK;
 }
@@ -1153,7 +1278,7 @@ __global__ void k_mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n
 
 void mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64_t *set, int64_t len,
                         cudaStream_t s) {
-    if (n) k_mask_and_in_values<<<grid_for(n, 256), 256, 0, s>>>(m, prop, n, set, len);
+    if (n) kl(k_mask_and_in_values, grid_for(n, 256), 256, 0, s, m, prop, n, set, len);
 }
 
 }  // namespace mp

@@ -27,7 +27,8 @@ EXPORTS = [
     "mp_config_default", "mp_create", "mp_destroy", "mp_add_node_type", "mp_add_property_i32",
     "mp_add_relation", "mp_finalize_hin", "mp_type_id", "mp_property_id", "mp_relation_id",
     "mp_submit", "mp_submit_batch", "mp_wait", "mp_result_info", "mp_result_copy", "mp_release",
-    "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain",
+    "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain", "mp_kernel_stats",
+    "mp_kernel_stats_reset",
 ]
 
 
@@ -47,6 +48,10 @@ class mp_constraint(C.Structure):
 class mp_query(C.Structure):
     _fields_ = [("n_types", C.c_uint32), ("types", C.c_void_p), ("rels", C.c_void_p),
                 ("n_constraints", C.c_uint32), ("c", C.c_void_p)]
+
+
+class mp_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
 class MPError(RuntimeError):
@@ -86,6 +91,8 @@ def lib():
             "mp_result_time": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
             "mp_strerror": (C.c_char_p, [C.c_int]),
             "mp_result_stats": (C.c_int, [C.c_void_p, U64, P(U64), C.c_void_p, C.c_void_p, P(U32)]),
+            "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
+            "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_plan_chain": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         }
@@ -273,6 +280,19 @@ def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None):
     _ck(lib().mp_plan_chain(p, _ptr(dims), _ptr(nnz), alpha, beta, gamma, _ptr(kc), _ptr(kr), _ptr(split),
                             _ptr(cost)), "mp_plan_chain")
     return split, cost
+
+
+def mp_kernel_stats(ctx):
+    """({name: {"launches", "ms", "bytes"}}, total kernel launches of the library)."""
+    arr = (mp_kernel_stat * 64)()
+    n, launches = C.c_uint32(), C.c_uint64()
+    _ck(lib().mp_kernel_stats(ctx, arr, 64, C.byref(n), C.byref(launches)), "mp_kernel_stats")
+    return ({arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+             for i in range(n.value)}, launches.value)
+
+
+def mp_kernel_stats_reset(ctx):
+    _ck(lib().mp_kernel_stats_reset(ctx), "mp_kernel_stats_reset")
 
 
 # ---- convenience wrapper -------------------------------------------------------------
