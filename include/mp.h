@@ -204,6 +204,39 @@ typedef struct {
 int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, uint32_t *n, uint64_t *launches);
 int mp_kernel_stats_reset(mp_ctx *ctx);
 
+/* ---- host-only replay of the Overlap Tree and the cache policies (no GPU needed)
+ *
+ * The same tree and policy code the engine runs, driven by a caller-given trace. Symbols
+ * are node type ids (>= 0). pos_keys gives one constraint description per position of an
+ * inserted metapath (NULL or "" = unconstrained); keys of sub-metapaths are the
+ * descriptions of their positions, renumbered from 0, as "i:<desc>" joined by '|'. */
+typedef struct mp_otree mp_otree;
+int mp_otree_create(mp_otree **out);
+void mp_otree_destroy(mp_otree *t);
+/* Insert a metapath and all its suffixes (Sec. 3.3.2). */
+int mp_otree_insert(mp_otree *t, uint32_t n, const int32_t *types, const char *const *pos_keys);
+/* Occurrences of the sub-metapath s (Sec. 3.3.1 f); key NULL = any constraints. */
+int mp_otree_frequency(mp_otree *t, uint32_t n, const int32_t *s, const char *key, uint64_t *f);
+/* Node count (without the root), leaf count and the Sec. 3.3.3 invariant check. */
+int mp_otree_info(mp_otree *t, uint64_t *nodes, uint64_t *leaves, int32_t *invariants_ok);
+
+typedef struct mp_cachesim mp_cachesim;
+/* A cache of `capacity` bytes under MP_POLICY_ATRAPOS (Alg. 1), _PGDS or _LRU. */
+int mp_cachesim_create(double capacity, int32_t policy, mp_cachesim **out);
+void mp_cachesim_destroy(mp_cachesim *c);
+/* One request (Alg. 1) of the item (types, key) with tree frequency f, cost and size;
+ * *outcome = 0 hit, 1 inserted, 2 rejected (above 80 % of the capacity). */
+int mp_cachesim_request(mp_cachesim *c, uint32_t n, const int32_t *types, const char *key, double f,
+                        double cost, double size, int32_t *outcome);
+/* Current cost and utility h of an item; *present = 0 when it is not cached. */
+int mp_cachesim_entry(mp_cachesim *c, uint32_t n, const int32_t *types, const char *key, double *cost,
+                      double *utility, int32_t *present);
+/* The i-th evicted item id ("t0,t1,...,#key"); *n_total = evictions so far. buf may be
+ * NULL to read only the count. */
+int mp_cachesim_evicted(mp_cachesim *c, uint32_t i, char *buf, uint32_t cap, uint32_t *n_total);
+/* Inflation value L, bytes used and items held. */
+int mp_cachesim_state(mp_cachesim *c, double *L, double *used, uint32_t *items);
+
 /* The chain planner alone (host only; Sec. 3.1 Eq. 1 with the Eq. 2 cost and E_ac
  * densities of Sec. 3.2). p factors; factor t is dims[t] x dims[t+1] with nnz[t]
  * non-zeros. known_cost / known_rho (p*p, row-major, NaN = unknown, both NULL = none)

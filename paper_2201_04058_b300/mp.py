@@ -28,7 +28,9 @@ EXPORTS = [
     "mp_add_relation", "mp_finalize_hin", "mp_type_id", "mp_property_id", "mp_relation_id",
     "mp_submit", "mp_submit_batch", "mp_wait", "mp_result_info", "mp_result_copy", "mp_release",
     "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain", "mp_kernel_stats",
-    "mp_kernel_stats_reset",
+    "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
+    "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
+    "mp_cachesim_evicted", "mp_cachesim_state",
 ]
 
 
@@ -93,6 +95,19 @@ def lib():
             "mp_result_stats": (C.c_int, [C.c_void_p, U64, P(U64), C.c_void_p, C.c_void_p, P(U32)]),
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
+            "mp_otree_create": (C.c_int, [P(C.c_void_p)]),
+            "mp_otree_destroy": (None, [C.c_void_p]),
+            "mp_otree_insert": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_void_p]),
+            "mp_otree_frequency": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_char_p, P(U64)]),
+            "mp_otree_info": (C.c_int, [C.c_void_p, P(U64), P(U64), P(I32)]),
+            "mp_cachesim_create": (C.c_int, [C.c_double, I32, P(C.c_void_p)]),
+            "mp_cachesim_destroy": (None, [C.c_void_p]),
+            "mp_cachesim_request": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_char_p, C.c_double, C.c_double,
+                                              C.c_double, P(I32)]),
+            "mp_cachesim_entry": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_char_p, P(C.c_double),
+                                            P(C.c_double), P(I32)]),
+            "mp_cachesim_evicted": (C.c_int, [C.c_void_p, U32, C.c_char_p, U32, P(U32)]),
+            "mp_cachesim_state": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_double), P(U32)]),
             "mp_plan_chain": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         }
@@ -293,6 +308,87 @@ def mp_kernel_stats(ctx):
 
 def mp_kernel_stats_reset(ctx):
     _ck(lib().mp_kernel_stats_reset(ctx), "mp_kernel_stats_reset")
+
+
+class OTree:
+    """Host-only Overlap Tree replay (mp_otree_*)."""
+
+    def __init__(self):
+        self.h = C.c_void_p()
+        _ck(lib().mp_otree_create(C.byref(self.h)), "mp_otree_create")
+
+    def insert(self, types, pos_keys=None):
+        t = np.ascontiguousarray(types, np.int32)
+        keys = None
+        if pos_keys is not None:
+            keys = (C.c_char_p * t.size)(*[(k or "").encode() for k in pos_keys])
+        _ck(lib().mp_otree_insert(self.h, t.size, _ptr(t), keys), "mp_otree_insert")
+
+    def frequency(self, s, key=None):
+        t = np.ascontiguousarray(s, np.int32)
+        f = C.c_uint64()
+        _ck(lib().mp_otree_frequency(self.h, t.size, _ptr(t), None if key is None else key.encode(), C.byref(f)),
+            "mp_otree_frequency")
+        return f.value
+
+    def info(self):
+        n, l, ok = C.c_uint64(), C.c_uint64(), C.c_int32()
+        _ck(lib().mp_otree_info(self.h, C.byref(n), C.byref(l), C.byref(ok)), "mp_otree_info")
+        return n.value, l.value, bool(ok.value)
+
+    def __del__(self):
+        try:
+            lib().mp_otree_destroy(self.h)
+        except Exception:
+            pass
+
+
+class CacheSim:
+    """Host-only cache-policy replay (mp_cachesim_*)."""
+
+    def __init__(self, capacity, policy):
+        self.h = C.c_void_p()
+        _ck(lib().mp_cachesim_create(float(capacity), int(policy), C.byref(self.h)), "mp_cachesim_create")
+
+    def request(self, types, key, f, cost, size):
+        t = np.ascontiguousarray(types, np.int32)
+        out = C.c_int32()
+        _ck(lib().mp_cachesim_request(self.h, t.size, _ptr(t), key.encode(), float(f), float(cost), float(size),
+                                      C.byref(out)), "mp_cachesim_request")
+        return ("hit", "inserted", "rejected")[out.value]
+
+    def entry(self, types, key):
+        t = np.ascontiguousarray(types, np.int32)
+        c, h, pr = C.c_double(), C.c_double(), C.c_int32()
+        _ck(lib().mp_cachesim_entry(self.h, t.size, _ptr(t), key.encode(), C.byref(c), C.byref(h), C.byref(pr)),
+            "mp_cachesim_entry")
+        return (c.value, h.value) if pr.value else None
+
+    def evicted(self):
+        n = C.c_uint32()
+        _ck(lib().mp_cachesim_evicted(self.h, 0, None, 0, C.byref(n)), "mp_cachesim_evicted")
+        out = []
+        buf = C.create_string_buffer(1 << 16)
+        for i in range(n.value):
+            _ck(lib().mp_cachesim_evicted(self.h, i, buf, len(buf), None), "mp_cachesim_evicted")
+            out.append(buf.value.decode())
+        return out
+
+    def state(self):
+        L, used, items = C.c_double(), C.c_double(), C.c_uint32()
+        _ck(lib().mp_cachesim_state(self.h, C.byref(L), C.byref(used), C.byref(items)), "mp_cachesim_state")
+        return L.value, used.value, items.value
+
+    def __del__(self):
+        try:
+            lib().mp_cachesim_destroy(self.h)
+        except Exception:
+            pass
+
+
+def cache_item_id(types, key):
+    """The engine's id string of a cached item (types + constraint key)."""
+    return "".join(f"{int(t)}," for t in types) + "#" + key
 
 
 # ---- convenience wrapper -------------------------------------------------------------
