@@ -38,7 +38,8 @@ struct Tuning {
     int dense_max_cols = 8192;   // DENSE needs ncols * 8 bytes of shared memory
     int dense_min_u = 256;       // ... and a row bound of at least this many entries
     int force_class = -1;        // -1 auto, else MP_BIN_* class
-    uint64_t scratch_cap = 4ull << 30;
+    uint64_t heavy = 65536;      // rows with more Gustavson products go to GLOBAL
+    uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     int sm_count = 148;
 };
 
@@ -99,9 +100,10 @@ void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int
 void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t set_len, int64_t n,
                   cudaStream_t s);
 
-// nnz of diag(rm) A diag(cm), added into *out (device).
+// nnz of diag(rm) A diag(cm), added into *out (device). long_rows (A.nrows entries) and
+// *n_long (zeroed) are device scratch for rows longer than 8192 entries.
 void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
-                cudaStream_t s);
+                uint32_t *long_rows, uint32_t *n_long, cudaStream_t s);
 
 // C = diag(rm) X diag(km) Y diag(cm). Masks may be nullptr. Returns MP_* code.
 int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,

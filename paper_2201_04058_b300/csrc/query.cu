@@ -73,7 +73,14 @@ int mp_ctx::leaf_nnz(const Query &q, const std::vector<uint32_t *> &masks, std::
     for (int t = 0; t < p; t++) {
         const Mat &A = rels[q.rels[t]].dev;
         if (masks[t] || masks[t + 1]) {
-            masked_nnz(A.view(), masks[t], masks[t + 1], d + t, stream);
+            uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
+            if (!lr) {
+                alloc->free(d, stream);
+                return MP_ERR_NOMEM;
+            }
+            cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
+            masked_nnz(A.view(), masks[t], masks[t + 1], d + t, lr, lr + A.nrows, stream);
+            alloc->free(lr, stream);
             any = true;
         } else {
             nnz[t] = (double)A.nnz;

@@ -72,10 +72,12 @@ __host__ __device__ __forceinline__ int next_pow2_log(uint64_t x) {
     return e;
 }
 
-// Bin of a row whose output has at most u entries (u >= 1), for an output of ncols
-// columns. Hash tables are sized T >= 2u (load factor <= 1/2).
-__host__ __device__ __forceinline__ int bin_for(uint64_t u, int64_t ncols, int dense_max_cols,
-                                                int dense_min_u, int force) {
+// Bin of a row with prod Gustavson products and at most u output entries (u >= 1), for
+// an output of ncols columns. Hash tables are sized T >= 2u (load factor <= 1/2). Rows
+// with more than `heavy` products, or whose output is too wide for a shared-memory
+// table, go to GLOBAL, where the row is split over many blocks.
+__host__ __device__ __forceinline__ int bin_for(uint64_t prod, uint64_t u, int64_t ncols, int dense_max_cols,
+                                                int dense_min_u, uint64_t heavy, int force) {
     if ((uint64_t)ncols < u) u = (uint64_t)ncols;
     const bool dense_ok = ncols <= dense_max_cols;
     int e = next_pow2_log(2 * u);
@@ -95,6 +97,7 @@ __host__ __device__ __forceinline__ int bin_for(uint64_t u, int64_t ncols, int d
         default:
             break;
     }
+    if (prod > heavy) return B_GLOBAL;
     if (dense_ok && u >= (uint64_t)dense_min_u) return B_DENSE;
     if (e <= 10) return B_W32 + (e - 5);
     if (e <= 13) return B_K2048 + (e - 11);
@@ -158,9 +161,10 @@ void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t len, 
     kl(k_and_words, grid_for(nw, 256), 256, 0, s, m, tmp, nw);
 }
 
-// nnz of diag(rm) A diag(cm): one warp per row.
-__global__ void k_masked_nnz(DCsr A, const uint32_t *rm, const uint32_t *cm,
-                             unsigned long long *out) {
+// nnz of diag(rm) A diag(cm): one warp per row; rows longer than 8192 entries are queued
+// and summed by every block (k_masked_nnz_long).
+__global__ void k_masked_nnz(DCsr A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
+                             uint32_t *long_rows, uint32_t *n_long) {
     int lane = threadIdx.x & 31;
     int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -172,17 +176,36 @@ __global__ void k_masked_nnz(DCsr A, const uint32_t *rm, const uint32_t *cm,
             if (lane == 0) c += (unsigned long long)(e - b);
             continue;
         }
+        if (e - b > 8192) {
+            if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+            continue;
+        }
         for (int64_t p = b + lane; p < e; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
     }
     for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
     if (lane == 0 && c) atomicAdd(out, c);
 }
 
-void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
-                cudaStream_t s) {
+__global__ void k_masked_nnz_long(DCsr A, const uint32_t *cm, unsigned long long *out, const uint32_t *long_rows,
+                                  const uint32_t *n_long) {
+    const uint32_t n = *n_long;
+    unsigned long long c = 0;
+    for (uint32_t r = 0; r < n; r++) {
+        const uint32_t i = long_rows[r];
+        for (int64_t p = A.rp[i] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.rp[i + 1];
+             p += (int64_t)gridDim.x * blockDim.x)
+            c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+    }
+    for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out, uint32_t *long_rows,
+                uint32_t *n_long, cudaStream_t s) {
     if (!A.nrows) return;
     unsigned g = (unsigned)std::min<int64_t>(grid_for(A.nrows * 32, 256), 148 * 16);
-    kl(k_masked_nnz, g, 256, 0, s, A, rm, cm, out);
+    kl(k_masked_nnz, g, 256, 0, s, A, rm, cm, out, long_rows, n_long);
+    if (cm) kl(k_masked_nnz_long, 148 * 4, 256, 0, s, A, cm, out, long_rows, n_long);
 }
 
 // ------------------------------------------------------------------ scan
@@ -282,104 +305,165 @@ void scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_
 struct BinArgs {
     int64_t ncols;
     int dense_max_cols, dense_min_u, force;
+    uint64_t heavy;
 };
 
-// Per-bin tallies of one pass: rows, X entries, Gustavson products and output entries
-// (the inputs of the algorithmic byte count of each bin's kernel).
+// Per-bin tallies of one pass: rows, X entries, Gustavson products, output entries and the
+// algorithmic bytes of the bin's kernel.
 struct BinTally {
     uint32_t counts[NBINS];
-    unsigned long long xent[NBINS], prods[NBINS], outn[NBINS];
+    unsigned long long xent[NBINS], prods[NBINS], outn[NBINS], bytes[NBINS];
 };
 
-__device__ __forceinline__ void tally_flush(BinTally *g, uint32_t *hc, unsigned long long *hx,
-                                            unsigned long long *hp, unsigned long long *ho) {
-    const int t = threadIdx.x;
-    if (t < NBINS && hc[t]) {
-        atomicAdd(g->counts + t, hc[t]);
-        atomicAdd(g->xent + t, hx[t]);
-        atomicAdd(g->prods + t, hp[t]);
-        if (ho) atomicAdd(g->outn + t, ho[t]);
+static constexpr int64_t LONGX = 8192;  // X rows longer than this are summed by all blocks
+
+// prod_i = sum over the masked X_i entries of the Y row lengths: one warp per row; rows
+// with more than LONGX entries are queued for k_rowwork_long.
+__global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km, uint64_t *prod,
+                          uint32_t *long_rows, uint32_t *n_long) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < X.nrows; i += nwarps) {
+        uint64_t s = 0;
+        if (bit_of(rm, (uint32_t)i)) {
+            const int64_t b = X.rp[i], e = X.rp[i + 1];
+            if (e - b > LONGX) {
+                if (lane == 0) {
+                    prod[i] = 0;
+                    long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+                }
+                continue;
+            }
+            for (int64_t p = b + lane; p < e; p += 32) {
+                const int32_t k = __ldg(X.ci + p);
+                if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
+            }
+            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+        }
+        if (lane == 0) prod[i] = s;
     }
 }
 
-// prod_i and the symbolic bin of every row; rows with prod_i = 0 get nnz_i = 0 and no bin.
-__global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km, BinArgs ba,
-                          uint64_t *prod, int8_t *bin, int64_t *nnz, BinTally *tally,
-                          unsigned long long *total_prod) {
+// The queued long rows: every block takes a strided share of every long row's entries.
+__global__ void k_rowwork_long(DCsr X, DCsr Y, const uint32_t *km, uint64_t *prod, const uint32_t *long_rows,
+                               const uint32_t *n_long) {
+    __shared__ unsigned long long red[32];
+    const uint32_t n = *n_long;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t r = 0; r < n; r++) {
+        const uint32_t i = long_rows[r];
+        const int64_t b = X.rp[i], e = X.rp[i + 1];
+        unsigned long long s = 0;
+        for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const int32_t k = __ldg(X.ci + p);
+            if (bit_of(km, (uint32_t)k)) s += (unsigned long long)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
+        }
+        for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+        if (lane == 0) red[wid] = s;
+        __syncthreads();
+        if (wid == 0) {
+            s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
+            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+            if (lane == 0 && s) atomicAdd((unsigned long long *)(prod + i), s);
+        }
+        __syncthreads();
+    }
+}
+
+// Symbolic bin of every row from prod_i; rows without products get nnz_i = 0, no bin.
+__global__ void k_binassign(const int64_t *xrp, const uint64_t *prod, int64_t m, BinArgs ba, int8_t *bin,
+                            int64_t *nnz, BinTally *tally, unsigned long long *total_prod) {
     __shared__ uint32_t hc[NBINS];
-    __shared__ unsigned long long hx[NBINS], hp[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS], hb[NBINS];
     __shared__ unsigned long long bsum;
     if (threadIdx.x < NBINS) {
         hc[threadIdx.x] = 0;
         hx[threadIdx.x] = 0;
         hp[threadIdx.x] = 0;
+        hb[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) bsum = 0;
     __syncthreads();
-    int lane = threadIdx.x & 31;
-    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long mysum = 0;
-    for (int64_t i = w; i < X.nrows; i += nwarps) {
-        uint64_t s = 0;
-        int64_t b = 0, e = 0;
-        if (bit_of(rm, (uint32_t)i)) {
-            b = X.rp[i];
-            e = X.rp[i + 1];
-            for (int64_t p = b + lane; p < e; p += 32) {
-                int32_t k = __ldg(X.ci + p);
-                if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
-            }
-            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
-        }
-        if (lane == 0) {
-            prod[i] = s;
-            int bb = -1;
-            if (s) {
-                bb = bin_for(s, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.force);
-                atomicAdd(&hc[bb], 1u);
-                atomicAdd(&hx[bb], (unsigned long long)(e - b));
-                atomicAdd(&hp[bb], (unsigned long long)s);
-            } else {
-                nnz[i] = 0;
-            }
-            bin[i] = (int8_t)bb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = prod[i];
+        int b = -1;
+        if (s) {
+            b = bin_for(s, s, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.force);
+            const unsigned long long xe = (unsigned long long)(xrp[i + 1] - xrp[i]);
+            atomicAdd(&hc[b], 1u);
+            atomicAdd(&hx[b], xe);
+            atomicAdd(&hp[b], (unsigned long long)s);
+            // symbolic bytes: X row pointers + nnz write, per X entry its column id and the
+            // two Y row pointers, per product one Y column id
+            atomicAdd(&hb[b], 24ull + xe * 20ull + (unsigned long long)s * 4ull);
             mysum += s;
+        } else {
+            nnz[i] = 0;
         }
+        bin[i] = (int8_t)b;
     }
-    if (lane == 0 && mysum) atomicAdd(&bsum, mysum);
+    if (mysum) atomicAdd(&bsum, mysum);
     __syncthreads();
-    tally_flush(tally, hc, hx, hp, nullptr);
-    if (threadIdx.x == 0 && bsum) atomicAdd(total_prod, bsum);
+    const int t = threadIdx.x;
+    if (t < NBINS && hc[t]) {
+        atomicAdd(tally->counts + t, hc[t]);
+        atomicAdd(tally->xent + t, hx[t]);
+        atomicAdd(tally->prods + t, hp[t]);
+        atomicAdd(tally->bytes + t, hb[t]);
+    }
+    if (t == 0 && bsum) atomicAdd(total_prod, bsum);
 }
 
-// Numeric bins from exact row sizes (nnz = rp[i+1] - rp[i]).
+// Numeric bins from the exact row sizes (nnz = rp[i+1] - rp[i]); rows the symbolic pass
+// put in GLOBAL stay there (their bitmaps give the output positions).
 __global__ void k_numbin(const int64_t *rp, const int64_t *xrp, const uint64_t *prod, int64_t n, BinArgs ba,
-                         int8_t *bin, BinTally *tally) {
+                         bool x_val, bool y_val, int8_t *bin, BinTally *tally, uint32_t *err) {
     __shared__ uint32_t hc[NBINS];
-    __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS], hb[NBINS];
     if (threadIdx.x < NBINS) {
         hc[threadIdx.x] = 0;
         hx[threadIdx.x] = 0;
         hp[threadIdx.x] = 0;
         ho[threadIdx.x] = 0;
+        hb[threadIdx.x] = 0;
     }
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t z = rp[i + 1] - rp[i];
+        const int64_t z = rp[i + 1] - rp[i];
         int b = -1;
         if (z) {
-            b = bin_for((uint64_t)z, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ba.force);
+            if (bin[i] == B_GLOBAL) {
+                b = B_GLOBAL;
+            } else {
+                b = bin_for(prod[i], (uint64_t)z, ba.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.force);
+                if (b == B_GLOBAL) atomicOr(err, ERR_PROBE);  // cannot happen: nnz <= the symbolic bound
+            }
+            const unsigned long long xe = (unsigned long long)(xrp[i + 1] - xrp[i]);
+            const unsigned long long pr = prod[i];
             atomicAdd(&hc[b], 1u);
-            atomicAdd(&hx[b], (unsigned long long)(xrp[i + 1] - xrp[i]));
-            atomicAdd(&hp[b], (unsigned long long)prod[i]);
+            atomicAdd(&hx[b], xe);
+            atomicAdd(&hp[b], pr);
             atomicAdd(&ho[b], (unsigned long long)z);
+            // numeric bytes: X and C row pointers, per X entry its column id (+ value) and
+            // two Y row pointers, per product a Y column id (+ value), per output 12 bytes
+            atomicAdd(&hb[b], 32ull + xe * (20ull + (x_val ? 8ull : 0ull)) + pr * (4ull + (y_val ? 8ull : 0ull)) +
+                                  (unsigned long long)z * 12ull);
         }
         bin[i] = (int8_t)b;
     }
     __syncthreads();
-    tally_flush(tally, hc, hx, hp, ho);
+    const int t = threadIdx.x;
+    if (t < NBINS && hc[t]) {
+        atomicAdd(tally->counts + t, hc[t]);
+        atomicAdd(tally->xent + t, hx[t]);
+        atomicAdd(tally->prods + t, hp[t]);
+        atomicAdd(tally->outn + t, ho[t]);
+        atomicAdd(tally->bytes + t, hb[t]);
+    }
 }
 
 // counts[0..NBINS) -> offsets[0..NBINS]; cursors reset.
@@ -423,15 +507,15 @@ struct Stage {
     uint64_t a;
 };
 
-// Enumerate every scalar product of row i with a group of G threads (G = 32: one warp;
+// Enumerate the scalar products of X entries [b, e) (all of row i, or a chunk of it) with a
+// group of G threads (G = 32: one warp;
 // G = blockDim: one block). f(j, v) is called once per product that passes cm, where v
 // = X_ik * Y_kj (1 when both are pattern-only; values only read when VAL).
 template <int G, bool VAL, class F>
 __device__ __forceinline__ void for_each_product(const DCsr &X, const DCsr &Y, const uint32_t *km,
-                                                 const uint32_t *cm, int64_t i, Stage *sg,
+                                                 const uint32_t *cm, int64_t b, int64_t e, Stage *sg,
                                                  int64_t *gtot, int64_t *warp_sums, int t,
                                                  uint32_t *err, F &&f) {
-    const int64_t b = X.rp[i], e = X.rp[i + 1];
     const int lane = t & 31;
     for (int64_t c0 = b; c0 < e; c0 += G) {
         const int64_t p = c0 + t;
@@ -556,8 +640,6 @@ struct PassArgs {
     int32_t *out_ci;
     uint64_t *out_val;
     uint32_t *err;
-    char *scratch;         // GLOBAL bin
-    size_t scratch_stride;
 };
 
 // ------------------------------------------------------------------ warp-hash bins
@@ -574,7 +656,7 @@ __global__ void __launch_bounds__(W * 32) k_sym_warp(PassArgs a, int bin) {
         for (int s = lane; s < T; s += 32) keys[s] = EMPTY;
         __syncwarp();
         int c = 0;
-        for_each_product<32, false>(a.X, a.Y, a.km, a.cm, i, sg, nullptr, nullptr, lane, a.err,
+        for_each_product<32, false>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, nullptr, nullptr, lane, a.err,
                                     [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, a.err); });
         for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
         if (lane == 0) a.nnz[i] = c;
@@ -597,7 +679,7 @@ __global__ void __launch_bounds__(W * 32) k_num_warp(PassArgs a, int bin) {
             vals[s] = 0;
         }
         __syncwarp();
-        for_each_product<32, true>(a.X, a.Y, a.km, a.cm, i, sg, nullptr, nullptr, lane, a.err,
+        for_each_product<32, true>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, nullptr, nullptr, lane, a.err,
                                    [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, a.err); });
         __syncwarp();
         // compact occupied slots to the front (in place: writes never pass the read point)
@@ -648,7 +730,7 @@ __global__ void __launch_bounds__(NT) k_sym_block(PassArgs a, int bin) {
         if (threadIdx.x == 0) cnt_s = 0;
         __syncthreads();
         int c = 0;
-        for_each_product<NT, false>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
+        for_each_product<NT, false>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, &gtot, warp_sums, threadIdx.x, a.err,
                                     [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, a.err); });
         for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt_s, c);
@@ -675,7 +757,7 @@ __global__ void __launch_bounds__(NT) k_num_block(PassArgs a, int bin) {
             vals[s] = 0;
         }
         __syncthreads();
-        for_each_product<NT, true>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
+        for_each_product<NT, true>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, &gtot, warp_sums, threadIdx.x, a.err,
                                    [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, a.err); });
         __syncthreads();
         uint32_t k[PER];
@@ -731,7 +813,7 @@ __global__ void __launch_bounds__(NT) k_sym_dense(PassArgs a, int bin) {
         if (threadIdx.x == 0) cnt_s = 0;
         __syncthreads();
         int c = 0;
-        for_each_product<NT, false>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
+        for_each_product<NT, false>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, &gtot, warp_sums, threadIdx.x, a.err,
                                     [&](uint32_t j, uint64_t) {
                                         uint32_t m = 1u << (j & 31);
                                         c += (atomicOr(bm + (j >> 5), m) & m) == 0;
@@ -758,7 +840,7 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
         const int64_t i = a.list[base + r];
         for (int s = threadIdx.x; s < ncols; s += NT) acc[s] = 0;
         __syncthreads();
-        for_each_product<NT, true>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
+        for_each_product<NT, true>(a.X, a.Y, a.km, a.cm, a.X.rp[i], a.X.rp[i + 1], sg, &gtot, warp_sums, threadIdx.x, a.err,
                                    [&](uint32_t j, uint64_t v) {
                                        unsigned long long old = atomicAdd(acc + j, (unsigned long long)v);
                                        if (old + v < old) atomicOr(a.err, ERR_OVERFLOW);
@@ -787,118 +869,120 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
     }
 }
 
-// ------------------------------------------------------------------ global-scratch bin
+// ------------------------------------------------------------------ GLOBAL bin: split rows
 
-// Each block owns one scratch slice: ncols uint64 accumulators, then ceil(ncols/32) bitmap
-// words. Both are all-zero on entry and are restored to zero before the block moves on.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_sym_global(PassArgs a, int bin) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int64_t warp_sums[32];
-    __shared__ int64_t gtot;
-    __shared__ int cnt_s;
-    __shared__ uint32_t wlo, whi;
-    Stage *sg = (Stage *)smem;
-    char *slice = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
-    uint32_t *bm = (uint32_t *)(slice + (size_t)a.Y.ncols * 8);
-    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
-        const int64_t i = a.list[base + r];
-        if (threadIdx.x == 0) {
-            cnt_s = 0;
-            wlo = 0xffffffffu;
-            whi = 0;
-        }
-        __syncthreads();
-        int c = 0;
-        uint32_t lo = 0xffffffffu, hi = 0;
-        for_each_product<NT, false>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
-                                    [&](uint32_t j, uint64_t) {
-                                        uint32_t m = 1u << (j & 31);
-                                        c += (atomicOr(bm + (j >> 5), m) & m) == 0;
-                                        lo = min(lo, j >> 5);
-                                        hi = max(hi, j >> 5);
-                                    });
-        for (int d = 16; d; d >>= 1) {
-            c += __shfl_xor_sync(FULL, c, d);
-            lo = min(lo, __shfl_xor_sync(FULL, lo, d));
-            hi = max(hi, __shfl_xor_sync(FULL, hi, d));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            if (c) atomicAdd(&cnt_s, c);
-            atomicMin(&wlo, lo);
-            atomicMax(&whi, hi);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) a.nnz[i] = cnt_s;
-        if (wlo <= whi)
-            for (uint32_t s = wlo + threadIdx.x; s <= whi; s += NT) bm[s] = 0;
-        __syncthreads();
+// Heavy rows and rows too wide for a shared-memory table. Each row is cut into work items
+// of XCH X entries, spread over all blocks, so a few huge rows still fill the GPU.
+//   symbolic: every product sets bit j of the row's bitmap (1 bit per output column);
+//             a rank pass turns the bitmap into rank[w] = set bits before word w, and the
+//             row's nnz is the total;
+//   numeric:  a fill pass writes each set bit's column id at its rank (so the row comes
+//             out in ascending column order) and zeroes the value; then every product
+//             adds its count straight into the output slot rank[w] + popc(bits below j).
+// Bitmaps and ranks are 8 bytes per 32 output columns per row; rows are processed in
+// rounds that fit the scratch cap (one round keeps the symbolic bitmaps for the numeric
+// pass, several rounds rebuild them).
+static constexpr int XCH = 256;  // X entries per work item
+static constexpr int GNT = 256;  // threads per GLOBAL block
+static constexpr int RW = 8;     // bitmap words per thread in the rank pass
+
+struct GlobArgs {
+    const uint32_t *list;     // rows of the GLOBAL bin, in symbolic order
+    const int64_t *item_off;  // R+1 work-item offsets
+    int64_t r0, r1;           // rows of this round
+    uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
+    int64_t nw;
+};
+
+__global__ void k_glob_items(const uint32_t *list, int64_t R, const int64_t *xrp, int64_t *cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = list[r];
+        const int64_t len = xrp[i + 1] - xrp[i];
+        cnt[r] = len > 0 ? (len + XCH - 1) / XCH : 1;
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_num_global(PassArgs a, int bin) {
-    extern __shared__ __align__(16) unsigned char smem[];
+template <bool NUM>
+__global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
+    __shared__ Stage sg[GNT];
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t gtot;
-    __shared__ uint32_t wlo, whi;
-    Stage *sg = (Stage *)smem;
-    char *slice = a.scratch + (size_t)blockIdx.x * a.scratch_stride;
-    unsigned long long *acc = (unsigned long long *)slice;
-    uint32_t *bm = (uint32_t *)(slice + (size_t)a.Y.ncols * 8);
-    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
-        const int64_t i = a.list[base + r];
-        if (threadIdx.x == 0) {
-            wlo = 0xffffffffu;
-            whi = 0;
+    const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
+    for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+        int64_t lo = g.r0, hi = g.r1 - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (g.item_off[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        __syncthreads();
-        uint32_t lo = 0xffffffffu, hi = 0;
-        for_each_product<NT, true>(a.X, a.Y, a.km, a.cm, i, sg, &gtot, warp_sums, threadIdx.x, a.err,
-                                   [&](uint32_t j, uint64_t v) {
-                                       unsigned long long old = atomicAdd(acc + j, (unsigned long long)v);
-                                       if (old + v < old) atomicOr(a.err, ERR_OVERFLOW);
-                                       if (old == 0) atomicOr(bm + (j >> 5), 1u << (j & 31));
-                                       lo = min(lo, j >> 5);
-                                       hi = max(hi, j >> 5);
-                                   });
-        for (int d = 16; d; d >>= 1) {
-            lo = min(lo, __shfl_xor_sync(FULL, lo, d));
-            hi = max(hi, __shfl_xor_sync(FULL, hi, d));
+        const uint32_t i = g.list[lo];
+        const int64_t xb = a.X.rp[i] + (t - g.item_off[lo]) * XCH;
+        const int64_t xe = min(a.X.rp[i + 1], xb + XCH);
+        uint32_t *bm = g.bm + (lo - g.r0) * g.nw;
+        if (!NUM) {
+            for_each_product<GNT, false>(a.X, a.Y, a.km, a.cm, xb, xe, sg, &gtot, warp_sums, threadIdx.x, a.err,
+                                         [&](uint32_t j, uint64_t) { atomicOr(bm + (j >> 5), 1u << (j & 31)); });
+        } else {
+            const uint32_t *rk = g.rank + (lo - g.r0) * g.nw;
+            unsigned long long *val = (unsigned long long *)a.out_val + a.rp[i];
+            for_each_product<GNT, true>(a.X, a.Y, a.km, a.cm, xb, xe, sg, &gtot, warp_sums, threadIdx.x, a.err,
+                                        [&](uint32_t j, uint64_t v) {
+                                            const uint32_t w = j >> 5;
+                                            const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
+                                            const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
+                                            if (old + v < old) atomicOr(a.err, ERR_OVERFLOW);
+                                        });
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&wlo, lo);
-            atomicMax(&whi, hi);
-        }
-        __syncthreads();
-        const int64_t o = a.rp[i];
-        const int64_t rowlen = a.rp[i + 1] - o;
-        int64_t done = 0;
-        const uint32_t w0 = wlo, w1 = whi;
-        if (w0 <= w1) {
-            for (uint32_t t0 = w0; t0 <= w1; t0 += NT) {
-                const uint32_t w = t0 + threadIdx.x;
-                uint32_t word = (w <= w1) ? bm[w] : 0u;
-                int64_t pos = done + block_excl_scan<NT>(__popc(word), warp_sums, &gtot);
-                while (word) {
-                    const int b = __ffs(word) - 1;
-                    word &= word - 1;
-                    const uint32_t j = w * 32 + b;
-                    if (pos < rowlen) {
-                        a.out_ci[o + pos] = (int32_t)j;
-                        a.out_val[o + pos] = acc[j];
-                    }
-                    acc[j] = 0;
-                    pos++;
-                }
-                if (w <= w1) bm[w] = 0;
-                done += gtot;
+    }
+}
+
+__global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int numeric) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    for (int64_t r = g.r0 + blockIdx.x; r < g.r1; r += gridDim.x) {
+        const uint32_t i = g.list[r];
+        const uint32_t *bm = g.bm + (r - g.r0) * g.nw;
+        uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        int64_t carry = 0;
+        for (int64_t w0 = 0; w0 < g.nw; w0 += (int64_t)GNT * RW) {
+            const int64_t wb = w0 + (int64_t)threadIdx.x * RW;
+            int cnt[RW];
+            int c = 0;
+#pragma unroll
+            for (int u = 0; u < RW; u++) {
+                cnt[u] = wb + u < g.nw ? __popc(bm[wb + u]) : 0;
+                c += cnt[u];
             }
+            int64_t ex = carry + block_excl_scan<GNT>(c, warp_sums, &gtot);
+#pragma unroll
+            for (int u = 0; u < RW; u++) {
+                if (wb + u < g.nw) rk[wb + u] = (uint32_t)ex;
+                ex += cnt[u];
+            }
+            carry += gtot;
         }
-        if (threadIdx.x == 0 && done != rowlen) atomicOr(a.err, ERR_COUNT);
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (!numeric) a.nnz[i] = carry;
+            else if (a.rp[i + 1] - a.rp[i] != carry) atomicOr(a.err, ERR_COUNT);
+        }
+    }
+}
+
+// One thread per bitmap word: the word's set bits become consecutive output entries.
+__global__ void k_glob_fill(PassArgs a, GlobArgs g) {
+    const int64_t total = (g.r1 - g.r0) * g.nw;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = x / g.nw, w = x - slot * g.nw;
+        uint32_t word = g.bm[x];
+        if (!word) continue;
+        const uint32_t i = g.list[g.r0 + slot];
+        int64_t pos = a.rp[i] + g.rank[x];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            a.out_ci[pos] = (int32_t)(w * 32 + b);
+            a.out_val[pos] = 0;
+            pos++;
+        }
     }
 }
 
@@ -915,15 +999,15 @@ static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_bloc
     return std::max(1u, std::min(g, (unsigned)max_blocks));
 }
 
-// Launch every non-empty bin's kernel of one pass, each grid sized to its bin's rows
-// (capped at a few blocks per SM; the kernels loop over their bin). With prof, CUDA
-// events bracket each launch.
-static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t ncols, int nscr_ctas,
-                     const Tuning &tun, cudaStream_t s, Prof *prof) {
+// Launch every non-empty shared-memory bin's kernel of one pass, each grid sized to its
+// bin's rows (capped at a few blocks per SM; the kernels loop over their bin). With
+// prof, CUDA events bracket each launch. GLOBAL is run separately (glob_pass).
+static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t ncols, const Tuning &tun,
+                     cudaStream_t s, Prof *prof) {
     const bool numeric = pass == 1;
     const int sms = tun.sm_count;
     const size_t stage = sizeof(Stage);
-    for (int b = 0; b < NBINS; b++) {
+    for (int b = 0; b < B_GLOBAL; b++) {
         const uint32_t rows = host_counts[b];
         if (!rows) continue;
         if (b == B_DENSE && ncols > tun.dense_max_cols) continue;
@@ -966,31 +1050,12 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
                     launch(k_sym_dense<256>, g, 256, 256 * stage + (size_t)((ncols + 31) / 32) * 4, s, a, B_DENSE);
                 break;
             }
-            case B_GLOBAL: {
-                unsigned g = blocks_for(rows, 1, nscr_ctas);
-                if (numeric)
-                    launch(k_num_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
-                else
-                    launch(k_sym_global<512>, g, 512, 512 * stage, s, a, B_GLOBAL);
-                break;
-            }
         }
         if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][1], s);
     }
 }
 
-// Algorithmic bytes of one bin's kernel in one pass (every X entry: column id, value if
-// any, and the two Y row pointers it looks up; every Gustavson product: the Y column id
-// and, in the numeric pass, the Y value; every output entry: column id + uint64 value;
-// every row: its X row pointers, and its nnz (symbolic) or C row pointers (numeric)).
-static double bin_bytes(int pass, const BinTally &t, int b, bool x_val, bool y_val) {
-    const double rows = t.counts[b], xe = (double)t.xent[b], pr = (double)t.prods[b], on = (double)t.outn[b];
-    if (pass == 0) return rows * 16 + xe * (4 + 16) + pr * 4 + rows * 8;
-    return rows * 32 + xe * (4 + (x_val ? 8 : 0) + 16) + pr * (4 + (y_val ? 8 : 0)) + on * 12;
-}
-
-static void prof_collect(Prof *prof, int pass, const BinTally &t, bool x_val, bool y_val, int64_t ncols,
-                         const Tuning &tun) {
+static void prof_collect(Prof *prof, int pass, const BinTally &t, int64_t ncols, const Tuning &tun) {
     if (!prof || !prof->on) return;
     for (int b = 0; b < NBINS; b++) {
         if (!t.counts[b] || (b == B_DENSE && ncols > tun.dense_max_cols)) continue;
@@ -1002,7 +1067,7 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t, bool x_val, bo
         KStat &k = prof->k[pass][b];
         k.launches++;
         k.ms += ms;
-        k.bytes += bin_bytes(pass, t, b, x_val, y_val);
+        k.bytes += (double)t.bytes[b];
     }
 }
 
@@ -1018,29 +1083,49 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
         }                                                                         \
     } while (0)
 
-// Make the scratch hold up to one slice of `stride` bytes per SM, zeroed, within the
-// scratch cap. Returns the number of slices available (0 on allocation failure).
-static int ensure_scratch(Scratch &scr, size_t stride, const Tuning &tun, Alloc &al, cudaStream_t s) {
-    size_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
-    int fit = (int)std::max<size_t>(1, cap / stride);
-    int n = std::min(tun.sm_count, fit);
-    size_t need = stride * (size_t)n;
-    if (scr.bytes < need) {
-        if (scr.base) al.free(scr.base, s);
-        scr.base = al.alloc(need, s);
-        if (!scr.base) {
-            scr.bytes = 0;
-            return 0;
+// State of the GLOBAL bin of one product across its two passes.
+struct Glob {
+    int64_t R = 0, nw = 0, per_round = 0, rounds = 0;
+    uint32_t *list = nullptr;   // copy of the bin's rows in symbolic order
+    int64_t *item_off = nullptr;
+    uint32_t *bm = nullptr, *rank = nullptr;
+    bool kept = false;          // bitmaps of a single round survive into the numeric pass
+};
+
+static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
+    if (g.list) al.free(g.list, s);
+    if (g.item_off) al.free(g.item_off, s);
+    if (g.bm) al.free(g.bm, s);
+    if (g.rank) al.free(g.rank, s);
+    g = Glob{};
+}
+
+// One pass of the GLOBAL bin (all rounds). pass 0 counts, pass 1 writes the rows.
+static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, cudaStream_t s, Prof *prof) {
+    const unsigned grid = (unsigned)tun.sm_count * 8;
+    if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
+    for (int64_t r0 = 0; r0 < g.R; r0 += g.per_round) {
+        GlobArgs ga{g.list, g.item_off, r0, std::min(g.R, r0 + g.per_round), g.bm, g.rank, g.nw};
+        const int64_t rows = ga.r1 - ga.r0;
+        if (pass == 0 || !g.kept) {
+            cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
+            kl(k_glob_set<false>, grid, GNT, 0, s, a, ga);
+            kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
         }
-        scr.bytes = need;
-        cudaMemsetAsync(scr.base, 0, need, s);
+        if (pass == 1) {
+            const int64_t words = rows * g.nw;
+            kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0, s,
+               a, ga);
+            kl(k_glob_set<true>, grid, GNT, 0, s, a, ga);
+        }
     }
-    return (int)std::min<size_t>(n, scr.bytes / stride);
+    if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
 }
 
 int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km, const uint32_t *cm,
            Alloc &al, Scratch &scr, const Tuning &tun, cudaStream_t s, uint64_t max_result_bytes,
            Mat *out, Stats *st, Prof *prof) {
+    (void)scr;
     const int64_t m = X.nrows;
     out->nrows = m;
     out->ncols = Y.ncols;
@@ -1050,25 +1135,27 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
         uint32_t offsets[NBINS + 1];
         uint32_t cursors[NBINS];
         uint32_t err;
+        uint32_t n_long;
         unsigned long long total_prod;
     };
-    // workspace: prod u64[m], bins i8[m], row list u32[m], two Small blocks
+    // workspace: prod u64[m], bins i8[m], row list u32[m], long-row list, two Small blocks
+    const int64_t max_long = m;
     const size_t off_prod = 0;
     const size_t off_bin = align256(off_prod + (size_t)m * 8);
     const size_t off_list = align256(off_bin + (size_t)m);
-    const size_t off_small = align256(off_list + (size_t)m * 4);
+    const size_t off_long = align256(off_list + (size_t)m * 4);
+    const size_t off_small = align256(off_long + (size_t)max_long * 4);
     const size_t ws_bytes = align256(off_small + sizeof(Small) * 2);
-    const size_t stride = align256((size_t)Y.ncols * 8 + (size_t)((Y.ncols + 31) / 32) * 4);
-    const BinArgs ba{Y.ncols, tun.dense_max_cols, tun.dense_min_u, tun.force_class};
+    const BinArgs ba{Y.ncols, tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy};
     int rc = MP_OK;
-    int nscr = 0;
     int64_t nnz = 0;
     uint32_t err = 0;
     Small h_sym, h_num;
     PassArgs pa{};
+    Glob gl;
     uint64_t *prod;
     int8_t *bin;
-    uint32_t *list;
+    uint32_t *list, *long_rows;
     Small *sm_sym, *sm_num;
     char *ws = (char *)al.alloc(ws_bytes, s);
     out->rp = (int64_t *)al.alloc((size_t)(m + 1) * 8, s);
@@ -1079,6 +1166,7 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
     prod = (uint64_t *)(ws + off_prod);
     bin = (int8_t *)(ws + off_bin);
     list = (uint32_t *)(ws + off_list);
+    long_rows = (uint32_t *)(ws + off_long);
     sm_sym = (Small *)(ws + off_small);
     sm_num = sm_sym + 1;
     CK(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s));
@@ -1086,21 +1174,16 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
     // 1-2. per-row work, symbolic bins, rows grouped by bin
     if (m > 0) {
         unsigned g = (unsigned)std::min<int64_t>(grid_for(m * 32, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, X, Y, rm, km, ba, prod, bin, out->rp, &sm_sym->tally, &sm_sym->total_prod);
-        kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
+        kl(k_rowwork, g, 256, 0, s, X, Y, rm, km, prod, long_rows, &sm_sym->n_long);
+        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, X, Y, km, prod, long_rows, &sm_sym->n_long);
         unsigned gf = (unsigned)std::min<int64_t>(grid_for(m, 256), (int64_t)tun.sm_count * 16);
+        kl(k_binassign, gf, 256, 0, s, X.rp, prod, m, ba, bin, out->rp, &sm_sym->tally, &sm_sym->total_prod);
+        kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
         kl(k_bin_fill, gf, 256, 0, s, bin, m, sm_sym->offsets, sm_sym->cursors, list);
     }
     CK(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h_sym.tally.counts[B_GLOBAL]) {
-        nscr = ensure_scratch(scr, stride, tun, al, s);
-        if (!nscr) {
-            rc = MP_ERR_NOMEM;
-            goto fail;
-        }
-    }
-    // 3-4. symbolic pass, row pointers
+
     pa.X = X;
     pa.Y = Y;
     pa.km = km;
@@ -1110,14 +1193,35 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
     pa.offsets = sm_sym->offsets;
     pa.nnz = out->rp;
     pa.err = &sm_sym->err;
-    pa.scratch = (char *)scr.base;
-    pa.scratch_stride = stride;
-    if (m > 0) run_pass(0, pa, h_sym.tally.counts, Y.ncols, nscr, tun, s, prof);
+    // GLOBAL bin set-up: its rows, work items, bitmap rounds
+    gl.R = h_sym.tally.counts[B_GLOBAL];
+    if (gl.R) {
+        gl.nw = (Y.ncols + 31) / 32;
+        const uint64_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
+        gl.per_round = std::max<int64_t>(1, std::min<int64_t>(gl.R, (int64_t)(cap / ((uint64_t)gl.nw * 8))));
+        gl.rounds = (gl.R + gl.per_round - 1) / gl.per_round;
+        gl.kept = gl.rounds == 1;
+        gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
+        gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
+        gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
+        gl.rank = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
+        if (!gl.list || !gl.item_off || !gl.bm || !gl.rank) {
+            rc = MP_ERR_NOMEM;
+            goto fail;
+        }
+        CK(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4, cudaMemcpyDeviceToDevice, s));
+        kl(k_glob_items, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, gl.list, gl.R, X.rp,
+           gl.item_off);
+        scan_i64(gl.item_off, gl.item_off, gl.R, al, s);
+    }
+    // 3-4. symbolic pass, row pointers
+    if (m > 0) run_pass(0, pa, h_sym.tally.counts, Y.ncols, tun, s, prof);
+    if (gl.R) glob_pass(0, gl, pa, tun, s, prof);
     scan_i64(out->rp, out->rp, m, al, s);
     CK(cudaMemcpyAsync(&nnz, out->rp + m, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&err, &sm_sym->err, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    prof_collect(prof, 0, h_sym.tally, X.val != nullptr, Y.val != nullptr, Y.ncols, tun);
+    prof_collect(prof, 0, h_sym.tally, Y.ncols, tun);
     if (st) {
         st->products += h_sym.total_prod;
         for (int b = 0; b < NBINS; b++) st->sym_bins[b] += h_sym.tally.counts[b];
@@ -1137,32 +1241,26 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
         rc = MP_ERR_NOMEM;
         goto fail;
     }
-    // 5. numeric pass on bins of the exact row sizes
+    // 5. numeric pass on bins of the exact row sizes (GLOBAL rows keep their bin)
     if (nnz > 0) {
         unsigned g = (unsigned)std::min<int64_t>(grid_for(m, 256), (int64_t)tun.sm_count * 16);
-        kl(k_numbin, g, 256, 0, s, out->rp, X.rp, prod, m, ba, bin, &sm_num->tally);
+        kl(k_numbin, g, 256, 0, s, out->rp, X.rp, prod, m, ba, X.val != nullptr, Y.val != nullptr, bin,
+           &sm_num->tally, &sm_num->err);
         kl(k_bin_offsets, 1, 32, 0, s, sm_num->tally.counts, sm_num->offsets, sm_num->cursors);
         kl(k_bin_fill, g, 256, 0, s, bin, m, sm_num->offsets, sm_num->cursors, list);
         CK(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (h_num.tally.counts[B_GLOBAL]) {
-            nscr = ensure_scratch(scr, stride, tun, al, s);
-            if (!nscr) {
-                rc = MP_ERR_NOMEM;
-                goto fail;
-            }
-        }
         pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
         pa.rp = out->rp;
         pa.out_ci = out->ci;
         pa.out_val = out->val;
         pa.err = &sm_num->err;
-        pa.scratch = (char *)scr.base;
-        run_pass(1, pa, h_num.tally.counts, Y.ncols, nscr, tun, s, prof);
+        run_pass(1, pa, h_num.tally.counts, Y.ncols, tun, s, prof);
+        if (gl.R) glob_pass(1, gl, pa, tun, s, prof);
         CK(cudaMemcpyAsync(&err, &sm_num->err, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        prof_collect(prof, 1, h_num.tally, X.val != nullptr, Y.val != nullptr, Y.ncols, tun);
+        prof_collect(prof, 1, h_num.tally, Y.ncols, tun);
         if (st)
             for (int b = 0; b < NBINS; b++) st->num_bins[b] += h_num.tally.counts[b];
         if (err) {
@@ -1171,10 +1269,12 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
         }
     }
     CK(cudaGetLastError());
+    glob_release(gl, al, s);
     al.free(ws, s);
     if (st) st->nnz += (uint64_t)nnz;
     return MP_OK;
 fail:
+    glob_release(gl, al, s);
     if (ws) al.free(ws, s);
     if (out->rp) al.free(out->rp, s);
     if (out->ci) al.free(out->ci, s);

@@ -132,14 +132,15 @@ def test_unknown_relation_rejected(c1, c1_engines):
 
 
 def test_overflow_is_an_error_not_a_wrap(cuda_ok):
-    """A complete bipartite 100 x 100 relation: an (ABAB...A) metapath of length 11 has
-    100^10 > 2^64 instances between every pair, so the count cannot be represented."""
+    """A complete bipartite 100 x 100 relation: a metapath ABAB... of length n has
+    100^(n-2) instances between every pair of end nodes; at n = 12 that is 10^20 > 2^64,
+    so the count cannot be represented, while n = 11 (10^18) fits."""
     mp = _mp()
     n = 100
     s = np.repeat(np.arange(n, dtype=np.uint32), n)
     d = np.tile(np.arange(n, dtype=np.uint32), n)
     h = {"types": {"A": n, "B": n}, "relations": [("A", "B", s, d)], "props": {}}
-    q = {"types": list("ABABABABABA"), "constraints": []}
+    q = {"types": list("ABABABABABAB"), "constraints": []}
     with pytest.raises(OC.OracleOverflow):
         OC.evaluate(OracleHIN(h), q)
     for force in (-1, 0, 1, 3):
@@ -149,9 +150,9 @@ def test_overflow_is_an_error_not_a_wrap(cuda_ok):
             assert rc == mp.MP_ERR_OVERFLOW, force
             e.release(t)
             # one step shorter fits: 100^9 < 2^64
-            q9 = {"types": list("ABABABABAB"), "constraints": []}
-            rp, ci, val = e.run(q9)
-            assert np.all(val == np.uint64(100 ** 8)) and rp[-1] == n * n
+            q11 = {"types": list("ABABABABABA"), "constraints": []}
+            rp, ci, val = e.run(q11)
+            assert np.all(val == np.uint64(100 ** 9)) and rp[-1] == n * n
         finally:
             e.close()
 
