@@ -186,6 +186,12 @@ const char *mp_strerror(int code);
 int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t *sym_bins,
                     uint32_t *num_bins, uint32_t *n_products);
 
+/* Cache counters since mp_create (Sec. 3.4): requests (look-ups that found an entry plus
+ * insertion attempts), hits, inserts, rejections (80 % rule), evictions, bytes held and
+ * entries held. Any pointer may be NULL. MP_ERR_STATE when the policy is MP_POLICY_NONE. */
+int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *inserts, uint64_t *rejected,
+                   uint64_t *evictions, uint64_t *bytes, uint64_t *entries);
+
 /* Per-kernel counters of the SpGEMM passes since the last reset: one entry per (pass,
  * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
  * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),

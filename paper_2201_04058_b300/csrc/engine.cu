@@ -54,13 +54,6 @@ struct PoolAlloc final : Alloc {
 
 // ------------------------------------------------------------------ context
 
-void mp_ctx::free_mat(Mat &m) {
-    if (m.rp) alloc->free(m.rp, stream);
-    if (m.ci) alloc->free(m.ci, stream);
-    if (m.val) alloc->free(m.val, stream);
-    m = Mat{};
-}
-
 static int check_cuda(cudaError_t e, const char *what) {
     if (e != cudaSuccess) {
         fprintf(stderr, "mp: %s: %s\n", what, cudaGetErrorString(e));
@@ -123,6 +116,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     ctx->tun.force_class = c.force_bin_class;
     if (c.scratch_bytes) ctx->tun.scratch_cap = c.scratch_bytes;
     ctx->alloc.reset(new PoolAlloc());
+    if (c.policy != MP_POLICY_NONE) ctx->cache.reset(new CachePolicy((double)c.hbm_budget_bytes, c.policy));
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
     if (!ctx->prof.init()) return MP_ERR_CUDA;
@@ -136,7 +130,6 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
     {
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->cache_clear();
-        for (auto &kv : ctx->results) ctx->free_mat(kv.second.m);
         ctx->results.clear();
         for (auto &r : ctx->rels) ctx->free_mat(r.dev);
         for (auto &p : ctx->props)
@@ -356,6 +349,43 @@ int mp_ctx::parse(const mp_query *q, Query &out) {
         }
         out.cons[k.pos].push_back(std::move(cc));
     }
+    // canonical per-position constraint text (sorted), used by the Overlap Tree and the
+    // cache keys; a query with any non-default relation also tags each position > 0 with
+    // the relation that enters it, so sub-chains over different relations never share keys
+    bool custom_rel = false;
+    for (int t = 0; t + 1 < n; t++) {
+        for (size_t x = 0; x < rels.size(); x++)
+            if (rels[x].src == out.types[t] && rels[x].dst == out.types[t + 1]) {
+                if ((int)x != out.rels[t]) custom_rel = true;
+                break;
+            }
+    }
+    out.pos_keys.assign(n, std::string());
+    for (int i = 0; i < n; i++) {
+        std::vector<std::string> parts;
+        for (const Constraint &c : out.cons[i]) {
+            std::string d = "p" + std::to_string(c.prop) + "o" + std::to_string(c.op);
+            if (c.op == MP_OP_IN) {
+                d += "{";
+                for (size_t e = 0; e < c.set.size(); e++) {
+                    if (e) d += ",";
+                    d += std::to_string(c.set[e]);
+                }
+                d += "}";
+            } else {
+                d += "[" + std::to_string(c.lo) + "," + std::to_string(c.hi) + "]";
+            }
+            parts.push_back(d);
+        }
+        std::sort(parts.begin(), parts.end());
+        std::string key;
+        for (auto &x : parts) {
+            if (!key.empty()) key += "&";
+            key += x;
+        }
+        if (custom_rel && i > 0) key += "@r" + std::to_string(out.rels[i - 1]);
+        out.pos_keys[i] = key;
+    }
     return MP_OK;
 }
 
@@ -367,11 +397,12 @@ extern "C" int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket) {
     Query qq;
     int rc = ctx->parse(q, qq);
     if (rc) return rc;
-    Result res;
-    rc = ctx->run_query(qq, res);
-    res.status = rc;
+    std::vector<Query> qs(1);
+    qs[0] = std::move(qq);
+    std::vector<Result> res(1);
+    rc = ctx->run_batch(qs, res);
     *ticket = ctx->next_ticket++;
-    ctx->results.emplace(*ticket, std::move(res));
+    ctx->results.emplace(*ticket, std::move(res[0]));
     return rc;
 }
 
@@ -409,7 +440,7 @@ extern "C" int mp_result_info(mp_ctx *ctx, mp_ticket t, uint32_t *rows, uint32_t
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
     if (it->second.status) return it->second.status;
-    const Mat &m = it->second.m;
+    const Mat &m = it->second.m->m;
     if (rows) *rows = (uint32_t)m.nrows;
     if (cols) *cols = (uint32_t)m.ncols;
     if (nnz) *nnz = (uint64_t)m.nnz;
@@ -424,7 +455,7 @@ extern "C" int mp_result_copy(mp_ctx *ctx, mp_ticket t, int64_t *row_ptr, int32_
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
     if (it->second.status) return it->second.status;
     cudaSetDevice(ctx->cfg.device);
-    const Mat &m = it->second.m;
+    const Mat &m = it->second.m->m;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaStream_t s = ctx->stream;
     if (row_ptr && check_cuda(cudaMemcpyAsync(row_ptr, m.rp, (size_t)(m.nrows + 1) * 8, k, s), "copy"))
@@ -441,7 +472,6 @@ extern "C" int mp_release(mp_ctx *ctx, mp_ticket t) {
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
-    ctx->release_result(it->second);
     ctx->results.erase(it);
     return MP_OK;
 }
@@ -507,6 +537,22 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
         }
     if (n) *n = w;
     if (launches) *launches = g_launches.load();
+    return MP_OK;
+}
+
+extern "C" int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *inserts,
+                              uint64_t *rejected, uint64_t *evictions, uint64_t *bytes, uint64_t *entries) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->cache) return MP_ERR_STATE;
+    const auto &c = ctx->cstats;
+    if (requests) *requests = c.requests;
+    if (hits) *hits = c.hits;
+    if (inserts) *inserts = c.inserts;
+    if (rejected) *rejected = c.rejected;
+    if (evictions) *evictions = c.evictions;
+    if (bytes) *bytes = (uint64_t)ctx->cache->used();
+    if (entries) *entries = (uint64_t)ctx->cache->size();
     return MP_OK;
 }
 

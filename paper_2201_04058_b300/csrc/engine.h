@@ -10,6 +10,22 @@
 
 #include "../../include/mp.h"
 #include "internal.h"
+#include "otree.h"
+
+// A device CSR shared by results, cache entries and in-flight products; freed (stream
+// ordered) when the last holder lets go. Base relations are never owned.
+struct DevMat {
+    mp::Mat m;
+    mp::Alloc *al = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevMat() {
+        if (!al) return;
+        if (m.rp) al->free(m.rp, s);
+        if (m.ci) al->free(m.ci, s);
+        if (m.val) al->free(m.val, s);
+    }
+};
+using MatPtr = std::shared_ptr<DevMat>;
 
 struct mp_ctx {
     struct NodeType {
@@ -35,17 +51,18 @@ struct mp_ctx {
     struct Query {
         std::vector<int32_t> types, rels;
         std::vector<std::vector<Constraint>> cons;  // per position
+        std::vector<std::string> pos_keys;          // canonical constraint text per position
     };
     struct Result {
         int status = 0;
-        mp::Mat m;
+        MatPtr m;
         double ms = 0.0;
         mp::Stats st;
         uint32_t n_products = 0;
+        uint32_t cache_hits = 0;
     };
-    struct Operand {
-        mp::Mat m;
-        bool owned = false;
+    struct CacheCounters {
+        uint64_t requests = 0, hits = 0, inserts = 0, rejected = 0, evictions = 0;
     };
 
     mp_config cfg{};
@@ -64,14 +81,15 @@ struct mp_ctx {
     mp::Prof prof;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
+    mp::OverlapTree otree;
+    std::unique_ptr<mp::CachePolicy> cache;  // null when cfg.policy == MP_POLICY_NONE
+    CacheCounters cstats;
+
     int parse(const mp_query *q, Query &out);
     int build_masks(const Query &q, std::vector<uint32_t *> &masks);
     void free_masks(std::vector<uint32_t *> &masks);
-    int leaf_nnz(const Query &q, const std::vector<uint32_t *> &masks, std::vector<double> &nnz);
-    int exec(const Query &q, const std::vector<uint32_t *> &masks, const std::vector<int> &split, int p,
-             int i, int j, Operand &out, Result &r);
-    int run_query(const Query &q, Result &r);
     int run_batch(std::vector<Query> &qs, std::vector<Result> &rs);
+    MatPtr wrap(const mp::Mat &m);
     void free_mat(mp::Mat &m);
     void release_result(Result &r);
     void cache_clear();

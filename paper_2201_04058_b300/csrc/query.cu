@@ -1,18 +1,55 @@
-// Query evaluation: constraint masks (Def. 3), the chain plan (Eq. 1, Eq. 2) and the
-// post-order run of the plan's sparse products.
+// Query and workload evaluation: constraint masks (Def. 3), chain plans (Eq. 1, Eq. 2),
+// the product DAG of a batch of queries, and the Overlap-Tree cache (Sec. 3.3, 3.4).
+//
+// A batch of queries becomes one DAG of sparse products. Every internal node of a
+// query's plan is a sub-chain, identified by its node types, relations and the
+// constraints on its positions; identical sub-chains of different queries become one
+// node, and a sub-chain whose result is cached becomes a finished node. Planning sees
+// both as known sub-chains with retrieval cost 0 (end of Sec. 3.2). Nodes run level by
+// level (a node's level is one more than its deepest child). After the batch, each
+// query's whole result and the longest sub-metapath it computed that has occurred at
+// least twice are offered to the cache (Sec. 3.4.1), whose replacement policy decides
+// (Alg. 1).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstdio>
+#include <functional>
+#include <unordered_map>
 #include <vector>
 
 #include "engine.h"
 
 using namespace mp;
+using Query = mp_ctx::Query;
+using Result = mp_ctx::Result;
 
 namespace mp {
 void mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64_t *sorted_set,
                         int64_t len, cudaStream_t s);
+}
+
+MatPtr mp_ctx::wrap(const Mat &m) {
+    auto p = std::make_shared<DevMat>();
+    p->m = m;
+    p->al = alloc.get();
+    p->s = stream;
+    return p;
+}
+
+void mp_ctx::free_mat(Mat &m) {
+    if (m.rp) alloc->free(m.rp, stream);
+    if (m.ci) alloc->free(m.ci, stream);
+    if (m.val) alloc->free(m.val, stream);
+    m = Mat{};
+}
+
+void mp_ctx::release_result(Result &r) { r.m.reset(); }
+
+void mp_ctx::cache_clear() {
+    if (cache) cache->clear();
 }
 
 int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
@@ -32,7 +69,6 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
                 mask_and_range(m, prop, cnt, c.lo, c.hi, stream);
                 continue;
             }
-            // MP_OP_IN
             const int64_t len = (int64_t)c.set.size();
             if (!prop) {
                 uint32_t *tmp = (uint32_t *)alloc->alloc(std::max<size_t>(nw, 1) * 4, stream);
@@ -62,126 +98,346 @@ void mp_ctx::free_masks(std::vector<uint32_t *> &masks) {
     masks.clear();
 }
 
-// nnz of every masked factor diag(M_t) A_t diag(M_{t+1}), for the planner.
-int mp_ctx::leaf_nnz(const Query &q, const std::vector<uint32_t *> &masks, std::vector<double> &nnz) {
-    const int p = (int)q.rels.size();
-    nnz.assign(p, 0.0);
-    unsigned long long *d = (unsigned long long *)alloc->alloc((size_t)p * 8, stream);
-    if (!d) return MP_ERR_NOMEM;
-    cudaMemsetAsync(d, 0, (size_t)p * 8, stream);
-    bool any = false;
-    for (int t = 0; t < p; t++) {
-        const Mat &A = rels[q.rels[t]].dev;
-        if (masks[t] || masks[t + 1]) {
-            uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
-            if (!lr) {
-                alloc->free(d, stream);
-                return MP_ERR_NOMEM;
-            }
-            cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
-            masked_nnz(A.view(), masks[t], masks[t + 1], d + t, lr, lr + A.nrows, stream);
-            alloc->free(lr, stream);
-            any = true;
-        } else {
-            nnz[t] = (double)A.nnz;
-        }
-    }
-    if (any) {
-        std::vector<unsigned long long> h(p);
-        cudaMemcpyAsync(h.data(), d, (size_t)p * 8, cudaMemcpyDeviceToHost, stream);
-        if (cudaStreamSynchronize(stream) != cudaSuccess) {
-            alloc->free(d, stream);
-            return MP_ERR_CUDA;
-        }
-        for (int t = 0; t < p; t++)
-            if (masks[t] || masks[t + 1]) nnz[t] = (double)h[t];
-    }
-    alloc->free(d, stream);
-    return MP_OK;
+namespace {
+
+// One sub-chain of some query's plan: factors i..j of query q (positions i..j+1).
+struct PNode {
+    std::string id;
+    std::vector<int32_t> types;
+    std::string key;
+    int q = -1, i = 0, j = 0, k = 0;  // registering query, its factor range and split
+    int left = -1, right = -1;  // child node indices; -1 = the base factor itself
+    int level = 0;
+    MatPtr res;
+    bool from_cache = false;
+    bool filter = false;        // length-2 query: diag(M_1) A diag(M_2)
+    int consumers = 0;
+    bool keep = false;          // a query's result or a cache candidate
+    int status = MP_OK;
+    double ms = 0.0;            // device time of this node's own product
+    double subtree_ms = 0.0;    // of every product this node's computation needed
+    double c_ops = 0.0;         // Eq. 2 with the product's actual counts
+    double rho_est = 0.0;       // planner density estimate (for batch-mates)
+    mp::Stats st;
+};
+
+std::string subchain_key(const Query &q, int i, int j) {
+    return window_key(q.pos_keys, (size_t)i, (size_t)(j - i + 2));
 }
 
-int mp_ctx::exec(const Query &q, const std::vector<uint32_t *> &masks, const std::vector<int> &split, int p,
-                 int i, int j, Operand &out, Result &r) {
-    if (i == j) {
-        out.m = rels[q.rels[i]].dev;
-        out.owned = false;
-        return MP_OK;
-    }
-    const int k = split[(size_t)i * p + j];
-    Operand L, R;
-    int rc = exec(q, masks, split, p, i, k, L, r);
-    if (rc) return rc;
-    rc = exec(q, masks, split, p, k + 1, j, R, r);
-    if (rc) {
-        if (L.owned) free_mat(L.m);
-        return rc;
-    }
-    // A base relation enters with the masks of its two end positions; an intermediate
-    // already carries them (0/1 diagonals are idempotent, so re-applying is harmless).
-    const uint32_t *rm = (i == k) ? masks[i] : nullptr;
-    const uint32_t *km = (i == k || k + 1 == j) ? masks[k + 1] : nullptr;
-    const uint32_t *cm = (k + 1 == j) ? masks[j + 1] : nullptr;
-    Mat C;
-    rc = spgemm(L.m.view(), R.m.view(), rm, km, cm, *alloc, scratch, tun, stream, cfg.max_result_bytes, &C,
-                &r.st, &prof);
-    r.n_products++;
-    if (L.owned) free_mat(L.m);
-    if (R.owned) free_mat(R.m);
-    if (rc) {
-        free_mat(C);
-        return rc;
-    }
-    out.m = C;
-    out.owned = true;
-    return MP_OK;
+std::vector<int32_t> subchain_types(const Query &q, int i, int j) {
+    return std::vector<int32_t>(q.types.begin() + i, q.types.begin() + j + 2);
 }
 
-int mp_ctx::run_query(const Query &q, Result &r) {
-    const int n = (int)q.types.size(), p = n - 1;
-    cudaEventRecord(ev0, stream);
-    std::vector<uint32_t *> masks;
-    int rc = build_masks(q, masks);
-    if (!rc && p == 1) {
-        rc = filter(rels[q.rels[0]].dev.view(), masks[0], masks[1], *alloc, tun, stream, &r.m);
-        if (rc) free_mat(r.m);
-    } else if (!rc) {
-        std::vector<int> split((size_t)p * p, -1);
-        if (cfg.planner == MP_PLAN_LEFT_TO_RIGHT) {
-            for (int i = 0; i < p; i++)
-                for (int j = i + 1; j < p; j++) split[(size_t)i * p + j] = j - 1;
-        } else {
-            std::vector<double> dims(n), nnz;
-            for (int t = 0; t < n; t++) dims[t] = (double)types[q.types[t]].count;
-            rc = leaf_nnz(q, masks, nnz);
-            if (!rc) plan_chain(p, dims.data(), nnz.data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr,
-                                split.data(), nullptr, nullptr);
-        }
-        if (!rc) {
-            Operand out;
-            rc = exec(q, masks, split, p, 0, p - 1, out, r);
-            if (!rc) r.m = out.m;
-        }
-    }
-    free_masks(masks);
-    cudaEventRecord(ev1, stream);
-    cudaError_t e = cudaEventSynchronize(ev1);
-    if (e != cudaSuccess && !rc) rc = MP_ERR_CUDA;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    r.ms = ms;
-    r.status = rc;
-    return rc;
-}
+}  // namespace
 
 int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
-    int first = MP_OK;
-    for (size_t i = 0; i < qs.size(); i++) {
-        int rc = run_query(qs[i], rs[i]);
-        if (rc && first == MP_OK) first = rc;
+    const size_t nq = qs.size();
+    cudaEventRecord(ev0, stream);
+    std::vector<std::vector<uint32_t *>> masks(nq);
+    std::vector<int> qstatus(nq, MP_OK);
+    for (size_t q = 0; q < nq; q++) qstatus[q] = build_masks(qs[q], masks[q]);
+
+    // exact nnz of every masked base factor, for the planner: one device array, one sync
+    std::vector<std::vector<double>> leaf(nq);
+    {
+        size_t total = 0;
+        for (auto &q : qs) total += q.rels.size();
+        unsigned long long *d = (unsigned long long *)alloc->alloc(std::max<size_t>(total, 1) * 8, stream);
+        if (!d) return MP_ERR_NOMEM;
+        cudaMemsetAsync(d, 0, std::max<size_t>(total, 1) * 8, stream);
+        std::vector<void *> tmp;
+        size_t off = 0;
+        for (size_t q = 0; q < nq; q++) {
+            const int p = (int)qs[q].rels.size();
+            leaf[q].assign(p, 0.0);
+            for (int t = 0; t < p; t++) {
+                const Mat &A = rels[qs[q].rels[t]].dev;
+                if (!qstatus[q] && (masks[q][t] || masks[q][t + 1])) {
+                    uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
+                    if (!lr) return MP_ERR_NOMEM;
+                    cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
+                    masked_nnz(A.view(), masks[q][t], masks[q][t + 1], d + off + t, lr, lr + A.nrows, stream);
+                    tmp.push_back(lr);
+                } else {
+                    leaf[q][t] = -1.0;  // unmasked: the relation's nnz
+                }
+            }
+            off += p;
+        }
+        std::vector<unsigned long long> h(std::max<size_t>(total, 1));
+        cudaMemcpyAsync(h.data(), d, std::max<size_t>(total, 1) * 8, cudaMemcpyDeviceToHost, stream);
+        if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+        for (void *x : tmp) alloc->free(x, stream);
+        alloc->free(d, stream);
+        off = 0;
+        for (size_t q = 0; q < nq; q++) {
+            for (size_t t = 0; t < qs[q].rels.size(); t++)
+                leaf[q][t] = leaf[q][t] < 0 ? (double)rels[qs[q].rels[t]].dev.nnz : (double)h[off + t];
+            off += qs[q].rels.size();
+        }
     }
+
+    // Overlap Tree: every query's metapath and suffixes (Sec. 3.3.2)
+    if (cache)
+        for (size_t q = 0; q < nq; q++)
+            if (!qstatus[q]) otree.insert(qs[q].types, qs[q].pos_keys);
+
+    // plans and the product DAG
+    std::vector<PNode> nodes;
+    std::unordered_map<std::string, int> by_id;
+    std::vector<int> root(nq, -1);
+    for (size_t q = 0; q < nq; q++) {
+        if (qstatus[q]) continue;
+        const Query &Q = qs[q];
+        const int n = (int)Q.types.size(), p = n - 1;
+        std::vector<double> dims(n);
+        for (int t = 0; t < n; t++) dims[t] = (double)types[Q.types[t]].count;
+        if (p == 1) {
+            PNode nd;
+            nd.id = "filter#" + std::to_string(q);
+            nd.q = (int)q;
+            nd.filter = true;
+            nd.level = 1;
+            nd.keep = true;
+            root[q] = (int)nodes.size();
+            nodes.push_back(std::move(nd));
+            continue;
+        }
+        // sub-chains already known: in the cache, computed earlier in this batch, or
+        // evicted with a recorded cost
+        std::vector<double> kc((size_t)p * p, NAN), kr((size_t)p * p, NAN);
+        for (int i = 0; i < p; i++)
+            for (int j = i + 1; j < p; j++) {
+                const std::vector<int32_t> ty = subchain_types(Q, i, j);
+                const std::string key = subchain_key(Q, i, j);
+                const std::string id = CachePolicy::make_id(ty, key);
+                const double cells = dims[i] * dims[j + 1];
+                auto it = by_id.find(id);
+                if (it != by_id.end()) {
+                    kc[(size_t)i * p + j] = 0.0;
+                    kr[(size_t)i * p + j] = nodes[it->second].rho_est;
+                    continue;
+                }
+                if (cache) {
+                    CacheItem *ci = cache->find(id);
+                    if (ci) {
+                        kc[(size_t)i * p + j] = 0.0;
+                        kr[(size_t)i * p + j] = (double)std::static_pointer_cast<DevMat>(ci->payload)->m.nnz / cells;
+                        continue;
+                    }
+                    OTEntry *e = otree.entry(ty.data(), ty.size(), key);
+                    if (e && e->c_ops >= 0.0) {
+                        kc[(size_t)i * p + j] = e->c_ops;
+                        kr[(size_t)i * p + j] = e->nnz / cells;
+                    }
+                }
+            }
+        std::vector<int> split((size_t)p * p, -1), split_pure((size_t)p * p, -1);
+        std::vector<double> D((size_t)p * p, 0.0);
+        if (cfg.planner == MP_PLAN_LEFT_TO_RIGHT) {
+            for (int i = 0; i < p; i++)
+                for (int j = i + 1; j < p; j++) split[(size_t)i * p + j] = split_pure[(size_t)i * p + j] = j - 1;
+        } else {
+            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, kc.data(), kr.data(),
+                       split.data(), nullptr, D.data());
+            // plan of every sub-chain on its own, for known sub-chains that still need computing
+            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr,
+                       split_pure.data(), nullptr, nullptr);
+        }
+        // register nodes bottom-up
+        std::function<int(int, int)> reg = [&](int i, int j) -> int {
+            if (i == j) return -1;
+            const std::vector<int32_t> ty = subchain_types(Q, i, j);
+            const std::string key = subchain_key(Q, i, j);
+            const std::string id = CachePolicy::make_id(ty, key);
+            auto it = by_id.find(id);
+            if (it != by_id.end()) {
+                nodes[it->second].consumers++;
+                return it->second;
+            }
+            PNode nd;
+            nd.id = id;
+            nd.types = ty;
+            nd.key = key;
+            nd.q = (int)q;
+            nd.i = i;
+            nd.j = j;
+            nd.consumers = 1;
+            nd.rho_est = D[(size_t)i * p + j];
+            if (cache) {
+                CacheItem *ci = cache->find(id);
+                if (ci) {
+                    nd.res = std::static_pointer_cast<DevMat>(ci->payload);
+                    nd.from_cache = true;
+                    nd.level = 0;
+                    cstats.requests++;
+                    cstats.hits++;
+                    cache->request(ty, key, (double)otree.frequency(ty.data(), ty.size(), &key), ci->c, ci->s,
+                                   nullptr, nullptr);
+                    const int idx = (int)nodes.size();
+                    nodes.push_back(std::move(nd));
+                    by_id.emplace(id, idx);
+                    return idx;
+                }
+            }
+            int k = split[(size_t)i * p + j];
+            if (k < 0) k = split_pure[(size_t)i * p + j];  // known (evicted) but not at hand: compute it
+            nd.k = k;
+            const int l = reg(i, k);
+            const int r = reg(k + 1, j);
+            nd.left = l;
+            nd.right = r;
+            nd.level = 1 + std::max(l >= 0 ? nodes[l].level : 0, r >= 0 ? nodes[r].level : 0);
+            const int idx = (int)nodes.size();
+            nodes.push_back(std::move(nd));
+            by_id.emplace(id, idx);
+            return idx;
+        };
+        root[q] = reg(0, p - 1);
+        nodes[root[q]].keep = true;
+    }
+
+    // cache candidates: the longest computed sub-metapath of each query seen at least twice
+    std::vector<int> candidate(nq, -1);
+    if (cache) {
+        for (size_t q = 0; q < nq; q++) {
+            if (root[q] < 0) continue;
+            int best = -1;
+            std::function<void(int)> walk = [&](int x) {
+                if (x < 0) return;
+                const PNode &nd = nodes[x];
+                if (x != root[q] && !nd.from_cache && !nd.filter) {
+                    const uint64_t f = otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
+                    if (f >= 2 && (best < 0 || nd.types.size() > nodes[best].types.size())) best = x;
+                }
+                walk(nd.left);
+                walk(nd.right);
+            };
+            walk(root[q]);
+            candidate[q] = best;
+            if (best >= 0) nodes[best].keep = true;
+        }
+    }
+
+    // run the DAG level by level
+    int max_level = 0;
+    for (auto &nd : nodes) max_level = std::max(max_level, nd.level);
+    for (int lvl = 1; lvl <= max_level; lvl++) {
+        for (size_t x = 0; x < nodes.size(); x++) {
+            PNode &nd = nodes[x];
+            if (nd.level != lvl || nd.res) continue;
+            const Query &Q = qs[nd.q];
+            const auto &M = masks[nd.q];
+            auto t0 = std::chrono::steady_clock::now();
+            Mat C;
+            int rc;
+            if (nd.filter) {
+                rc = filter(rels[Q.rels[0]].dev.view(), M[0], M[1], *alloc, tun, stream, &C);
+            } else {
+                const int k = nd.k;
+                if (nd.left >= 0 && nodes[nd.left].status) rc = nodes[nd.left].status;
+                else if (nd.right >= 0 && nodes[nd.right].status) rc = nodes[nd.right].status;
+                else {
+                    const int i = nd.i, j = nd.j;
+                    DCsr Xv = nd.left >= 0 ? nodes[nd.left].res->m.view() : rels[Q.rels[i]].dev.view();
+                    DCsr Yv = nd.right >= 0 ? nodes[nd.right].res->m.view() : rels[Q.rels[j]].dev.view();
+                    // a base factor enters with the masks of its end positions; a node's
+                    // result already carries them (0/1 diagonals are idempotent)
+                    const uint32_t *rm = nd.left < 0 ? M[i] : nullptr;
+                    const uint32_t *km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
+                    const uint32_t *cm = nd.right < 0 ? M[j + 1] : nullptr;
+                    rc = spgemm(Xv, Yv, rm, km, cm, *alloc, scratch, tun, stream, cfg.max_result_bytes, &C, &nd.st,
+                                &prof);
+                    if (!rc) {
+                        // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
+                        const double nnz_x = nd.left >= 0 ? (double)nodes[nd.left].res->m.nnz
+                                                          : (double)rels[Q.rels[i]].dev.nnz;
+                        nd.c_ops = cfg.alpha * nnz_x + cfg.beta * (double)nd.st.products + cfg.gamma * (double)C.nnz;
+                    }
+                }
+            }
+            nd.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            nd.subtree_ms = nd.ms + (nd.left >= 0 && !nodes[nd.left].from_cache ? nodes[nd.left].subtree_ms : 0.0) +
+                            (nd.right >= 0 && !nodes[nd.right].from_cache ? nodes[nd.right].subtree_ms : 0.0);
+            nd.status = rc;
+            if (!rc) nd.res = wrap(C);
+            else free_mat(C);
+            // operands no longer needed by anyone
+            for (int c : {nd.left, nd.right}) {
+                if (c < 0) continue;
+                if (--nodes[c].consumers <= 0 && !nodes[c].keep) nodes[c].res.reset();
+            }
+        }
+    }
+
+    // results, statistics, cache insertion (Sec. 3.4.1) under the replacement policy
+    int first = MP_OK;
+    for (size_t q = 0; q < nq; q++) {
+        Result &r = rs[q];
+        if (qstatus[q]) {
+            r.status = qstatus[q];
+        } else {
+            PNode &rt = nodes[root[q]];
+            r.status = rt.status;
+            if (!rt.status) r.m = rt.res;
+            std::function<void(int)> acc = [&](int x) {
+                if (x < 0) return;
+                const PNode &nd = nodes[x];
+                if (nd.q == (int)q && !nd.from_cache) {
+                    r.st.products += nd.st.products;
+                    r.st.nnz += nd.st.nnz;
+                    for (int b = 0; b < NBINS; b++) {
+                        r.st.sym_bins[b] += nd.st.sym_bins[b];
+                        r.st.num_bins[b] += nd.st.num_bins[b];
+                    }
+                    r.n_products += nd.filter ? 0 : 1;
+                }
+                if (nd.from_cache) r.cache_hits++;
+                acc(nd.left);
+                acc(nd.right);
+            };
+            acc(root[q]);
+        }
+        if (r.status && first == MP_OK) first = r.status;
+    }
+    if (cache) {
+        auto offer = [&](PNode &nd) {
+            if (nd.from_cache || nd.filter || nd.status || !nd.res) return;
+            const double f = (double)otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
+            std::vector<CacheItem> ev;
+            cstats.requests++;
+            auto out = cache->request(nd.types, nd.key, f, nd.subtree_ms, (double)nd.res->m.bytes(),
+                                      std::static_pointer_cast<void>(nd.res), &ev);
+            if (out == CachePolicy::INSERTED) cstats.inserts++;
+            if (out == CachePolicy::REJECTED) cstats.rejected++;
+            if (out == CachePolicy::HIT) cstats.hits++;
+            cstats.evictions += ev.size();
+            OTEntry *e = otree.entry(nd.types.data(), nd.types.size(), nd.key);
+            if (e) {
+                e->cached = out != CachePolicy::REJECTED;
+                e->c_ms = nd.subtree_ms;
+                e->c_ops = nd.c_ops;
+                e->nnz = (double)nd.res->m.nnz;
+            }
+            for (auto &it : ev) {
+                OTEntry *ee = otree.entry(it.types.data(), it.types.size(), it.key);
+                if (ee) ee->cached = false;
+            }
+        };
+        for (size_t q = 0; q < nq; q++) {
+            if (root[q] < 0) continue;
+            offer(nodes[root[q]]);
+            if (candidate[q] >= 0) offer(nodes[candidate[q]]);
+        }
+    }
+    for (auto &m : masks) free_masks(m);
+    nodes.clear();
+    cudaEventRecord(ev1, stream);
+    cudaError_t e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    for (size_t q = 0; q < nq; q++) rs[q].ms = ms;
+    if (e != cudaSuccess && first == MP_OK) first = MP_ERR_CUDA;
     return first;
 }
-
-void mp_ctx::release_result(Result &r) { free_mat(r.m); }
-
-void mp_ctx::cache_clear() {}

@@ -871,8 +871,10 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
 
 // ------------------------------------------------------------------ GLOBAL bin: split rows
 
-// Heavy rows and rows too wide for a shared-memory table. Each row is cut into work items
-// of XCH X entries, spread over all blocks, so a few huge rows still fill the GPU.
+// Heavy rows and rows too wide for a shared-memory table. Each row's Gustavson products,
+// in the order of its X entries, are cut into work items of PCH products, and the items
+// of all rows are spread over all blocks, so a few huge rows (or one hub Y row) still
+// fill the GPU:
 //   symbolic: every product sets bit j of the row's bitmap (1 bit per output column);
 //             a rank pass turns the bitmap into rank[w] = set bits before word w, and the
 //             row's nnz is the total;
@@ -882,31 +884,63 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
 // Bitmaps and ranks are 8 bytes per 32 output columns per row; rows are processed in
 // rounds that fit the scratch cap (one round keeps the symbolic bitmaps for the numeric
 // pass, several rounds rebuild them).
-static constexpr int XCH = 256;  // X entries per work item
-static constexpr int GNT = 256;  // threads per GLOBAL block
-static constexpr int RW = 8;     // bitmap words per thread in the rank pass
+static constexpr int64_t PCH = 16384;  // Gustavson products per work item
+static constexpr int GNT = 256;        // threads per GLOBAL block
+static constexpr int RW = 8;           // bitmap words per thread in the rank pass
 
 struct GlobArgs {
     const uint32_t *list;     // rows of the GLOBAL bin, in symbolic order
     const int64_t *item_off;  // R+1 work-item offsets
+    const int64_t *xbase;     // R+1 offsets of each row's X entries in xoff
+    const int64_t *xoff;      // per X entry of a GLOBAL row: masked products before it
+    const uint64_t *prod;     // prod_i per row
     int64_t r0, r1;           // rows of this round
     uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
     int64_t nw;
 };
 
-__global__ void k_glob_items(const uint32_t *list, int64_t R, const int64_t *xrp, int64_t *cnt) {
+// Per GLOBAL row: its X entry count and its number of work items.
+__global__ void k_glob_prep(const uint32_t *list, int64_t R, const int64_t *xrp, const uint64_t *prod, int64_t *xlen,
+                            int64_t *items) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = list[r];
-        const int64_t len = xrp[i + 1] - xrp[i];
-        cnt[r] = len > 0 ? (len + XCH - 1) / XCH : 1;
+        xlen[r] = xrp[i + 1] - xrp[i];
+        items[r] = ((int64_t)prod[i] + PCH - 1) / PCH;
     }
 }
 
-template <bool NUM>
-__global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
-    __shared__ Stage sg[GNT];
+// xoff: exclusive prefix of the masked Y-row lengths over each GLOBAL row's X entries.
+__global__ void __launch_bounds__(GNT) k_glob_xoff(DCsr X, DCsr Y, const uint32_t *km, const uint32_t *list, int64_t R,
+                                                   const int64_t *xbase, int64_t *xoff) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t gtot;
+    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+        const uint32_t i = list[r];
+        const int64_t b = X.rp[i], e = X.rp[i + 1];
+        int64_t *out = xoff + xbase[r];
+        int64_t carry = 0;
+        for (int64_t c0 = b; c0 < e; c0 += GNT) {
+            const int64_t p = c0 + threadIdx.x;
+            int64_t len = 0;
+            if (p < e) {
+                const int32_t k = __ldg(X.ci + p);
+                if (bit_of(km, (uint32_t)k)) len = __ldg(Y.rp + k + 1) - __ldg(Y.rp + k);
+            }
+            const int64_t ex = block_excl_scan<GNT>(len, warp_sums, &gtot);
+            if (p < e) out[p - b] = carry + ex;
+            carry += gtot;
+        }
+    }
+}
+
+// One work item per block iteration: products [s0, s1) of one row. The X entries that
+// hold them are staged GNT at a time with their product offsets (from xoff); consecutive
+// threads take consecutive products, so a long Y row is read coalesced.
+template <bool NUM>
+__global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
+    __shared__ int64_t s_off[GNT + 1];
+    __shared__ int64_t s_st[GNT];
+    __shared__ uint64_t s_a[GNT];
     const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
     for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         int64_t lo = g.r0, hi = g.r1 - 1;
@@ -914,23 +948,59 @@ __global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
             const int64_t mid = (lo + hi + 1) >> 1;
             if (g.item_off[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        const uint32_t i = g.list[lo];
-        const int64_t xb = a.X.rp[i] + (t - g.item_off[lo]) * XCH;
-        const int64_t xe = min(a.X.rp[i + 1], xb + XCH);
-        uint32_t *bm = g.bm + (lo - g.r0) * g.nw;
-        if (!NUM) {
-            for_each_product<GNT, false>(a.X, a.Y, a.km, a.cm, xb, xe, sg, &gtot, warp_sums, threadIdx.x, a.err,
-                                         [&](uint32_t j, uint64_t) { atomicOr(bm + (j >> 5), 1u << (j & 31)); });
-        } else {
-            const uint32_t *rk = g.rank + (lo - g.r0) * g.nw;
-            unsigned long long *val = (unsigned long long *)a.out_val + a.rp[i];
-            for_each_product<GNT, true>(a.X, a.Y, a.km, a.cm, xb, xe, sg, &gtot, warp_sums, threadIdx.x, a.err,
-                                        [&](uint32_t j, uint64_t v) {
-                                            const uint32_t w = j >> 5;
-                                            const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
-                                            const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
-                                            if (old + v < old) atomicOr(a.err, ERR_OVERFLOW);
-                                        });
+        const int64_t r = lo;
+        const uint32_t i = g.list[r];
+        const int64_t xb = a.X.rp[i], xe = a.X.rp[i + 1];
+        const int64_t *xo = g.xoff + g.xbase[r];
+        const int64_t total = (int64_t)g.prod[i];
+        const int64_t s0 = (t - g.item_off[r]) * PCH;
+        const int64_t s1 = min(total, s0 + PCH);
+        // first X entry whose products reach s0: the last p with xo[p] <= s0
+        int64_t plo = 0, phi = xe - xb - 1;
+        while (plo < phi) {
+            const int64_t mid = (plo + phi + 1) >> 1;
+            if (__ldg(xo + mid) <= s0) plo = mid; else phi = mid - 1;
+        }
+        uint32_t *bm = g.bm + (r - g.r0) * g.nw;
+        const uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        unsigned long long *val = NUM ? (unsigned long long *)a.out_val + a.rp[i] : nullptr;
+        for (int64_t c0 = xb + plo; c0 < xe; c0 += GNT) {
+            const int64_t base = __ldg(xo + (c0 - xb));
+            if (base >= s1) break;  // uniform: every thread reads the same base
+            const int64_t p = c0 + threadIdx.x;
+            const int nent = (int)min((int64_t)GNT, xe - c0);
+            if (threadIdx.x < nent) {
+                const int32_t k = __ldg(a.X.ci + p);
+                s_off[threadIdx.x] = __ldg(xo + (p - xb)) - base;
+                s_st[threadIdx.x] = __ldg(a.Y.rp + k);
+                s_a[threadIdx.x] = (NUM && a.X.val) ? __ldg(a.X.val + p) : 1ull;
+            }
+            if (threadIdx.x == 0) s_off[nent] = (c0 + nent < xe ? __ldg(xo + (c0 + nent - xb)) : total) - base;
+            __syncthreads();
+            const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
+            for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
+                int l = 0, h = nent - 1;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (s_off[mid] <= f) l = mid; else h = mid - 1;
+                }
+                const int64_t q = s_st[l] + (f - s_off[l]);
+                const uint32_t j = (uint32_t)__ldg(a.Y.ci + q);
+                if (!bit_of(a.cm, j)) continue;
+                if (!NUM) {
+                    atomicOr(bm + (j >> 5), 1u << (j & 31));
+                } else {
+                    const uint64_t av = s_a[l];
+                    const uint64_t bv = a.Y.val ? __ldg(a.Y.val + q) : 1ull;
+                    const uint64_t v = av * bv;
+                    if (__umul64hi(av, bv)) atomicOr(a.err, ERR_OVERFLOW);
+                    const uint32_t w = j >> 5;
+                    const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
+                    const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
+                    if (old + v < old) atomicOr(a.err, ERR_OVERFLOW);
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -1087,7 +1157,8 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Glob {
     int64_t R = 0, nw = 0, per_round = 0, rounds = 0;
     uint32_t *list = nullptr;   // copy of the bin's rows in symbolic order
-    int64_t *item_off = nullptr;
+    int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr;
+    const uint64_t *prod = nullptr;
     uint32_t *bm = nullptr, *rank = nullptr;
     bool kept = false;          // bitmaps of a single round survive into the numeric pass
 };
@@ -1095,6 +1166,8 @@ struct Glob {
 static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.list) al.free(g.list, s);
     if (g.item_off) al.free(g.item_off, s);
+    if (g.xbase) al.free(g.xbase, s);
+    if (g.xoff) al.free(g.xoff, s);
     if (g.bm) al.free(g.bm, s);
     if (g.rank) al.free(g.rank, s);
     g = Glob{};
@@ -1105,7 +1178,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     for (int64_t r0 = 0; r0 < g.R; r0 += g.per_round) {
-        GlobArgs ga{g.list, g.item_off, r0, std::min(g.R, r0 + g.per_round), g.bm, g.rank, g.nw};
+        GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bm, g.rank, g.nw};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
@@ -1201,18 +1274,25 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
         gl.per_round = std::max<int64_t>(1, std::min<int64_t>(gl.R, (int64_t)(cap / ((uint64_t)gl.nw * 8))));
         gl.rounds = (gl.R + gl.per_round - 1) / gl.per_round;
         gl.kept = gl.rounds == 1;
+        const int64_t xtot = (int64_t)h_sym.tally.xent[B_GLOBAL];
+        gl.prod = prod;
         gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
+        gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
+        gl.xoff = (int64_t *)al.alloc((size_t)std::max<int64_t>(xtot, 1) * 8, s);
         gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
         gl.rank = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
-        if (!gl.list || !gl.item_off || !gl.bm || !gl.rank) {
+        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff || !gl.bm || !gl.rank) {
             rc = MP_ERR_NOMEM;
             goto fail;
         }
         CK(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4, cudaMemcpyDeviceToDevice, s));
-        kl(k_glob_items, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, gl.list, gl.R, X.rp,
-           gl.item_off);
+        kl(k_glob_prep, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, gl.list, gl.R, X.rp, prod,
+           gl.xbase, gl.item_off);
         scan_i64(gl.item_off, gl.item_off, gl.R, al, s);
+        scan_i64(gl.xbase, gl.xbase, gl.R, al, s);
+        kl(k_glob_xoff, (unsigned)std::min<int64_t>(gl.R, (int64_t)tun.sm_count * 8), GNT, 0, s, X, Y, km, gl.list,
+           gl.R, gl.xbase, gl.xoff);
     }
     // 3-4. symbolic pass, row pointers
     if (m > 0) run_pass(0, pa, h_sym.tally.counts, Y.ncols, tun, s, prof);

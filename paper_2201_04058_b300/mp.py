@@ -30,7 +30,7 @@ EXPORTS = [
     "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain", "mp_kernel_stats",
     "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
-    "mp_cachesim_evicted", "mp_cachesim_state",
+    "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats",
 ]
 
 
@@ -95,6 +95,7 @@ def lib():
             "mp_result_stats": (C.c_int, [C.c_void_p, U64, P(U64), C.c_void_p, C.c_void_p, P(U32)]),
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
+            "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
             "mp_otree_create": (C.c_int, [P(C.c_void_p)]),
             "mp_otree_destroy": (None, [C.c_void_p]),
             "mp_otree_insert": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_void_p]),
@@ -306,6 +307,13 @@ def mp_kernel_stats(ctx):
              for i in range(n.value)}, launches.value)
 
 
+def mp_cache_stats(ctx):
+    v = [C.c_uint64() for _ in range(7)]
+    _ck(lib().mp_cache_stats(ctx, *[C.byref(x) for x in v]), "mp_cache_stats")
+    return dict(zip(("requests", "hits", "inserts", "rejected", "evictions", "bytes", "entries"),
+                    (x.value for x in v)))
+
+
 def mp_kernel_stats_reset(ctx):
     _ck(lib().mp_kernel_stats_reset(ctx), "mp_kernel_stats_reset")
 
@@ -443,6 +451,16 @@ class Engine:
         val = np.empty(nnz, np.uint64)
         mp_result_copy(self.ctx, ticket, rp, ci, val)
         return rp, ci, val
+
+    def run_batch(self, qs):
+        """Submit a batch, fetch every result (or the error code) and release the tickets."""
+        rc, tickets = self.submit_batch(qs)
+        out = []
+        for t in tickets:
+            st = mp_wait(self.ctx, t)
+            out.append(self.fetch(t) if st == MP_OK else st)
+            mp_release(self.ctx, t)
+        return rc, out
 
     def run(self, q):
         """Submit, fetch and release one query; raises MPError on a query error."""

@@ -37,7 +37,7 @@ def c1():
 @pytest.fixture(scope="module")
 def c1_engines(c1, cuda_ok):
     mp = _mp()
-    engines = {b: mp.Engine(c1[0], force_bin_class=b) for b in BIN_CLASSES}
+    engines = {b: mp.Engine(c1[0], force_bin_class=b, policy=mp.MP_POLICY_NONE) for b in BIN_CLASSES}
     yield engines
     for e in engines.values():
         e.close()
@@ -82,7 +82,7 @@ def test_tiny_hins_every_bin(seed, cuda_ok):
     o = OracleHIN(h)
     qs = gen.random_queries(h, seed, 20, lengths=(2, 7), p_cons=0.5)
     for force in BIN_CLASSES:
-        e = mp.Engine(h, force_bin_class=force)
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
         try:
             for q in qs:
                 assert_same(e.run(q), OC.evaluate(o, q), (force, q["types"]))
@@ -93,8 +93,8 @@ def test_tiny_hins_every_bin(seed, cuda_ok):
 def test_planners_agree(c1, cuda_ok):
     mp = _mp()
     qs = gen.random_queries(c1[0], 7, 15, lengths=(4, 7), p_cons=0.3)
-    e_dp = mp.Engine(c1[0], planner=mp.MP_PLAN_DP)
-    e_lr = mp.Engine(c1[0], planner=mp.MP_PLAN_LEFT_TO_RIGHT)
+    e_dp = mp.Engine(c1[0], planner=mp.MP_PLAN_DP, policy=mp.MP_POLICY_NONE)
+    e_lr = mp.Engine(c1[0], planner=mp.MP_PLAN_LEFT_TO_RIGHT, policy=mp.MP_POLICY_NONE)
     try:
         for q in qs:
             want = OC.evaluate(c1[1], q)
@@ -144,7 +144,7 @@ def test_overflow_is_an_error_not_a_wrap(cuda_ok):
     with pytest.raises(OC.OracleOverflow):
         OC.evaluate(OracleHIN(h), q)
     for force in (-1, 0, 1, 3):
-        e = mp.Engine(h, force_bin_class=force)
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
         try:
             rc, t = e.submit(q)
             assert rc == mp.MP_ERR_OVERFLOW, force
@@ -170,7 +170,7 @@ def test_scaled_scholarly_workload(c2_small, force):
     block-hash and global bins."""
     mp = _mp()
     h, o = c2_small
-    e = mp.Engine(h, force_bin_class=force)
+    e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
     try:
         for q in gen.config2_queries(h, seed=2, n_anchor_a=32, n_anchor_t=4):
             assert_same(e.run(q), OC.evaluate(o, q), (force, "".join(q["types"])))
