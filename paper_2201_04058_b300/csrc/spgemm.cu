@@ -161,26 +161,37 @@ void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t len, 
     kl(k_and_words, grid_for(nw, 256), 256, 0, s, m, tmp, nw);
 }
 
-// nnz of diag(rm) A diag(cm): one warp per row; rows longer than 8192 entries are queued
-// and summed by every block (k_masked_nnz_long).
+// nnz of diag(rm) A diag(cm). Each lane takes one of 32 consecutive rows; rows longer
+// than 16 entries are counted by the whole warp, and rows longer than 8192 entries are
+// queued and counted by every block (k_masked_nnz_long).
 __global__ void k_masked_nnz(DCsr A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
                              uint32_t *long_rows, uint32_t *n_long) {
-    int lane = threadIdx.x & 31;
-    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long c = 0;
-    for (int64_t i = w; i < A.nrows; i += nwarps) {
-        if (!bit_of(rm, (uint32_t)i)) continue;
-        int64_t b = A.rp[i], e = A.rp[i + 1];
+    for (int64_t i0 = w * 32; i0 < A.nrows; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        int64_t b = 0, e = 0;
+        if (i < A.nrows && bit_of(rm, (uint32_t)i)) {
+            b = A.rp[i];
+            e = A.rp[i + 1];
+        }
         if (!cm) {
-            if (lane == 0) c += (unsigned long long)(e - b);
+            c += (unsigned long long)(e - b);
             continue;
         }
-        if (e - b > 8192) {
-            if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
-            continue;
+        const bool mine = e - b <= 16;
+        if (mine)
+            for (int64_t p = b; p < e; p++) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+        if (e - b > 8192) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+        unsigned coop = __ballot_sync(FULL, !mine && e - b <= 8192);
+        while (coop) {
+            const int src = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+            for (int64_t p = bb + lane; p < ee; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
         }
-        for (int64_t p = b + lane; p < e; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
     }
     for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
     if (lane == 0 && c) atomicAdd(out, c);
@@ -317,31 +328,43 @@ struct BinTally {
 
 static constexpr int64_t LONGX = 8192;  // X rows longer than this are summed by all blocks
 
-// prod_i = sum over the masked X_i entries of the Y row lengths: one warp per row; rows
-// with more than LONGX entries are queued for k_rowwork_long.
+// prod_i = sum over the masked X_i entries of the Y row lengths. Each lane takes one of 32
+// consecutive rows; rows longer than 16 entries are summed by the whole warp, one after
+// the other, and rows longer than LONGX are queued for k_rowwork_long.
 __global__ void k_rowwork(DCsr X, DCsr Y, const uint32_t *rm, const uint32_t *km, uint64_t *prod,
                           uint32_t *long_rows, uint32_t *n_long) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = w; i < X.nrows; i += nwarps) {
+    for (int64_t i0 = w * 32; i0 < X.nrows; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        int64_t b = 0, e = 0;
+        if (i < X.nrows && bit_of(rm, (uint32_t)i)) {
+            b = X.rp[i];
+            e = X.rp[i + 1];
+        }
         uint64_t s = 0;
-        if (bit_of(rm, (uint32_t)i)) {
-            const int64_t b = X.rp[i], e = X.rp[i + 1];
-            if (e - b > LONGX) {
-                if (lane == 0) {
-                    prod[i] = 0;
-                    long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
-                }
-                continue;
-            }
-            for (int64_t p = b + lane; p < e; p += 32) {
+        const bool mine = e - b <= 16;
+        if (mine)
+            for (int64_t p = b; p < e; p++) {
                 const int32_t k = __ldg(X.ci + p);
                 if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
             }
-            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+        if (e - b > LONGX) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+        unsigned coop = __ballot_sync(FULL, !mine && e - b <= LONGX);
+        while (coop) {
+            const int src = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+            uint64_t c = 0;
+            for (int64_t p = bb + lane; p < ee; p += 32) {
+                const int32_t k = __ldg(X.ci + p);
+                if (bit_of(km, (uint32_t)k)) c += (uint64_t)(__ldg(Y.rp + k + 1) - __ldg(Y.rp + k));
+            }
+            for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+            if (lane == src) s = c;
         }
-        if (lane == 0) prod[i] = s;
+        if (i < X.nrows) prod[i] = (e - b > LONGX) ? 0 : s;
     }
 }
 
@@ -909,27 +932,22 @@ __global__ void k_glob_prep(const uint32_t *list, int64_t R, const int64_t *xrp,
     }
 }
 
-// xoff: exclusive prefix of the masked Y-row lengths over each GLOBAL row's X entries.
-__global__ void __launch_bounds__(GNT) k_glob_xoff(DCsr X, DCsr Y, const uint32_t *km, const uint32_t *list, int64_t R,
-                                                   const int64_t *xbase, int64_t *xoff) {
-    __shared__ int64_t warp_sums[32];
-    __shared__ int64_t gtot;
-    for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
-        const uint32_t i = list[r];
-        const int64_t b = X.rp[i], e = X.rp[i + 1];
-        int64_t *out = xoff + xbase[r];
-        int64_t carry = 0;
-        for (int64_t c0 = b; c0 < e; c0 += GNT) {
-            const int64_t p = c0 + threadIdx.x;
-            int64_t len = 0;
-            if (p < e) {
-                const int32_t k = __ldg(X.ci + p);
-                if (bit_of(km, (uint32_t)k)) len = __ldg(Y.rp + k + 1) - __ldg(Y.rp + k);
-            }
-            const int64_t ex = block_excl_scan<GNT>(len, warp_sums, &gtot);
-            if (p < e) out[p - b] = carry + ex;
-            carry += gtot;
+// xoff, step 1: the masked Y-row length of every X entry of every GLOBAL row, as one flat
+// array (row r's entries start at xbase[r]); a device-wide exclusive scan (scan_i64) then
+// turns it into each entry's global product offset.
+__global__ void k_glob_xlen(DCsr X, DCsr Y, const uint32_t *km, const uint32_t *list, int64_t R,
+                            const int64_t *xbase, int64_t *xoff) {
+    const int64_t xtot = xbase[R];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < xtot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
         }
+        const uint32_t i = list[lo];
+        const int64_t p = X.rp[i] + (e - xbase[lo]);
+        const int32_t k = __ldg(X.ci + p);
+        xoff[e] = bit_of(km, (uint32_t)k) ? __ldg(Y.rp + k + 1) - __ldg(Y.rp + k) : 0;
     }
 }
 
@@ -952,8 +970,9 @@ __global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
         const uint32_t i = g.list[r];
         const int64_t xb = a.X.rp[i], xe = a.X.rp[i + 1];
         const int64_t *xo = g.xoff + g.xbase[r];
-        const int64_t total = (int64_t)g.prod[i];
-        const int64_t s0 = (t - g.item_off[r]) * PCH;
+        // product offsets are global across the GLOBAL rows: this row's start at xo[0]
+        const int64_t total = __ldg(xo) + (int64_t)g.prod[i];
+        const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
         const int64_t s1 = min(total, s0 + PCH);
         // first X entry whose products reach s0: the last p with xo[p] <= s0
         int64_t plo = 0, phi = xe - xb - 1;
@@ -1279,7 +1298,7 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
         gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
-        gl.xoff = (int64_t *)al.alloc((size_t)std::max<int64_t>(xtot, 1) * 8, s);
+        gl.xoff = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
         gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
         gl.rank = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
         if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff || !gl.bm || !gl.rank) {
@@ -1291,8 +1310,9 @@ int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
            gl.xbase, gl.item_off);
         scan_i64(gl.item_off, gl.item_off, gl.R, al, s);
         scan_i64(gl.xbase, gl.xbase, gl.R, al, s);
-        kl(k_glob_xoff, (unsigned)std::min<int64_t>(gl.R, (int64_t)tun.sm_count * 8), GNT, 0, s, X, Y, km, gl.list,
-           gl.R, gl.xbase, gl.xoff);
+        kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(xtot, 256), (int64_t)tun.sm_count * 16)),
+           256, 0, s, X, Y, km, gl.list, gl.R, gl.xbase, gl.xoff);
+        scan_i64(gl.xoff, gl.xoff, xtot, al, s);
     }
     // 3-4. symbolic pass, row pointers
     if (m > 0) run_pass(0, pa, h_sym.tally.counts, Y.ncols, tun, s, prof);
