@@ -134,7 +134,6 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         for (auto &r : ctx->rels) ctx->free_mat(r.dev);
         for (auto &p : ctx->props)
             if (p.dev) ctx->alloc->free(p.dev, ctx->stream);
-        if (ctx->scratch.base) ctx->alloc->free(ctx->scratch.base, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         cudaEventDestroy(ctx->ev0);
         cudaEventDestroy(ctx->ev1);

@@ -76,7 +76,6 @@ struct mp_ctx {
     std::unordered_map<uint64_t, Result> results;
     uint64_t next_ticket = 1;
     std::unique_ptr<mp::Alloc> alloc;
-    mp::Scratch scratch;
     mp::Tuning tun;
     mp::Prof prof;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

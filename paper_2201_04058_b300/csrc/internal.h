@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace mp {
 
@@ -86,13 +87,6 @@ struct Alloc {
     virtual ~Alloc() = default;
 };
 
-// Per-context scratch for the GLOBAL bin: n_ctas slices of (ncols u64 + words u32),
-// kept all-zero between launches.
-struct Scratch {
-    void *base = nullptr;
-    size_t bytes = 0;
-};
-
 // ---- masks: bit j of word j >> 5 set = node j passes
 void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s);
 void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
@@ -105,10 +99,23 @@ void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t set_l
 void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
                 uint32_t *long_rows, uint32_t *n_long, cudaStream_t s);
 
-// C = diag(rm) X diag(km) Y diag(cm). Masks may be nullptr. Returns MP_* code.
-int spgemm(const DCsr &X, const DCsr &Y, const uint32_t *rm, const uint32_t *km,
-           const uint32_t *cm, Alloc &al, Scratch &scr, const Tuning &tun, cudaStream_t s,
-           uint64_t max_result_bytes, Mat *out, Stats *st, Prof *prof);
+// One product of a wave: C = diag(rm) X diag(km) Y diag(cm) (masks may be nullptr).
+struct WaveIn {
+    DCsr X, Y;
+    const uint32_t *rm = nullptr, *km = nullptr, *cm = nullptr;
+};
+struct WaveOut {
+    int status = 0;  // MP_OK, MP_ERR_OVERFLOW, MP_ERR_TOO_LARGE, ...
+    Mat m;           // owned by the caller on success
+    uint64_t products = 0;
+    uint32_t sym_bins[NBINS] = {};
+    uint32_t num_bins[NBINS] = {};
+};
+// Run independent products together: one launch per bin and pass for the whole wave.
+// Returns MP_OK or a wave-wide error (CUDA, out of memory); per-product errors are in
+// out[p].status.
+int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,

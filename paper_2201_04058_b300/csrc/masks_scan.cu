@@ -1,0 +1,283 @@
+// Constraint masks (Def. 3), masked nnz of base relations, the row-pointer scan and the
+// length-2 metapath filter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace mp {
+
+// ------------------------------------------------------------------ masks
+
+__global__ void k_mask_fill(uint32_t *m, int64_t nw, uint32_t v, int64_t n) {
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    uint32_t x = v;
+    if (v && w == nw - 1 && (n & 31)) x = (1u << (n & 31)) - 1u;  // no bits past n
+    m[w] = x;
+}
+
+// One thread per node; a warp ballot forms one 32-node word.
+__global__ void k_mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo,
+                                 int64_t hi) {
+    int64_t base = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool ok = false;
+    if (i < n) {
+        int64_t v = prop ? (int64_t)__ldg(prop + i) : i;
+        ok = v >= lo && v <= hi;
+    }
+    uint32_t word = __ballot_sync(FULL, ok);
+    if ((threadIdx.x & 31) == 0 && i < n) m[(base + (threadIdx.x & ~31)) >> 5] &= word;
+}
+
+__global__ void k_set_bits(uint32_t *m, const uint32_t *set, int64_t len, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    uint32_t j = set[t];
+    if ((int64_t)j < n) atomicOr(m + (j >> 5), 1u << (j & 31));
+}
+
+__global__ void k_and_words(uint32_t *m, const uint32_t *t, int64_t nw) {
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w < nw) m[w] &= t[w];
+}
+
+
+void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s) {
+    int64_t nw = (n + 31) / 32;
+    if (nw) kl(k_mask_fill, grid_for(nw, 256), 256, 0, s, m, nw, ones ? FULL : 0u, n);
+}
+
+void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
+                    cudaStream_t s) {
+    if (n) kl(k_mask_and_range, grid_for(n, 256), 256, 0, s, m, prop, n, lo, hi);
+}
+
+void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t len, int64_t n,
+                  cudaStream_t s) {
+    int64_t nw = (n + 31) / 32;
+    if (!nw) return;
+    kl(k_mask_fill, grid_for(nw, 256), 256, 0, s, tmp, nw, 0u, n);
+    if (len) kl(k_set_bits, grid_for(len, 256), 256, 0, s, tmp, set, len, n);
+    kl(k_and_words, grid_for(nw, 256), 256, 0, s, m, tmp, nw);
+}
+
+// nnz of diag(rm) A diag(cm). Each lane takes one of 32 consecutive rows; rows longer
+// than 16 entries are counted by the whole warp, and rows longer than 8192 entries are
+// queued and counted by every block (k_masked_nnz_long).
+__global__ void k_masked_nnz(DCsr A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
+                             uint32_t *long_rows, uint32_t *n_long) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long c = 0;
+    for (int64_t i0 = w * 32; i0 < A.nrows; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        int64_t b = 0, e = 0;
+        if (i < A.nrows && bit_of(rm, (uint32_t)i)) {
+            b = A.rp[i];
+            e = A.rp[i + 1];
+        }
+        if (!cm) {
+            c += (unsigned long long)(e - b);
+            continue;
+        }
+        const bool mine = e - b <= 16;
+        if (mine)
+            for (int64_t p = b; p < e; p++) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+        if (e - b > 8192) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+        unsigned coop = __ballot_sync(FULL, !mine && e - b <= 8192);
+        while (coop) {
+            const int src = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+            for (int64_t p = bb + lane; p < ee; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+        }
+    }
+    for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
+    if (lane == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void k_masked_nnz_long(DCsr A, const uint32_t *cm, unsigned long long *out, const uint32_t *long_rows,
+                                  const uint32_t *n_long) {
+    const uint32_t n = *n_long;
+    unsigned long long c = 0;
+    for (uint32_t r = 0; r < n; r++) {
+        const uint32_t i = long_rows[r];
+        for (int64_t p = A.rp[i] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.rp[i + 1];
+             p += (int64_t)gridDim.x * blockDim.x)
+            c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+    }
+    for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out, uint32_t *long_rows,
+                uint32_t *n_long, cudaStream_t s) {
+    if (!A.nrows) return;
+    unsigned g = (unsigned)std::min<int64_t>(grid_for(A.nrows * 32, 256), 148 * 16);
+    kl(k_masked_nnz, g, 256, 0, s, A, rm, cm, out, long_rows, n_long);
+    if (cm) kl(k_masked_nnz_long, 148 * 4, 256, 0, s, A, cm, out, long_rows, n_long);
+}
+
+// ------------------------------------------------------------------ scan
+
+static constexpr int SCAN_T = 512, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int64_t *in, int64_t n, int64_t *part) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+    int64_t s = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_I; t++)
+        if (base + t < n) s += in[base + t];
+    block_excl_scan<SCAN_T>(s, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_parts(int64_t *part, int64_t nb) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = i < nb ? part[i] : 0;
+        int64_t e = block_excl_scan<1024>(v, ws, &tot);
+        if (i < nb) part[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int64_t *in, int64_t *out, int64_t n,
+                                                       const int64_t *part, int64_t nb) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
+    int64_t v[SCAN_I];
+    int64_t s = 0;
+#pragma unroll
+    for (int t = 0; t < SCAN_I; t++) {
+        v[t] = base + t < n ? in[base + t] : 0;
+        s += v[t];
+    }
+    int64_t e = block_excl_scan<SCAN_T>(s, ws, &tot) + part[blockIdx.x];
+    // all reads of this tile are done (the scan synchronised), so out may alias in
+#pragma unroll
+    for (int t = 0; t < SCAN_I; t++) {
+        if (base + t < n) out[base + t] = e;
+        e += v[t];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = part[nb];
+}
+
+void scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s) {
+    if (n == 0) {
+        cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+        return;
+    }
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t *part = (int64_t *)al.alloc((size_t)(nb + 1) * sizeof(int64_t), s);
+    kl(k_scan_tiles, (unsigned)nb, SCAN_T, 0, s, in, n, part);
+    kl(k_scan_parts, 1, 1024, 0, s, part, nb);
+    kl(k_scan_apply, (unsigned)nb, SCAN_T, 0, s, in, out, n, part, nb);
+    al.free(part, s);
+}
+
+// ------------------------------------------------------------------ length-2 metapaths
+
+__global__ void k_filter_count(DCsr A, const uint32_t *rm, const uint32_t *cm, int64_t *cnt) {
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < A.nrows; i += nwarps) {
+        int64_t c = 0;
+        if (bit_of(rm, (uint32_t)i))
+            for (int64_t p = A.rp[i] + lane; p < A.rp[i + 1]; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        if (lane == 0) cnt[i] = c;
+    }
+}
+
+__global__ void k_filter_fill(DCsr A, const uint32_t *rm, const uint32_t *cm, const int64_t *rp,
+                              int32_t *ci, uint64_t *val) {
+    int lane = threadIdx.x & 31;
+    int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < A.nrows; i += nwarps) {
+        if (!bit_of(rm, (uint32_t)i)) continue;
+        int64_t o = rp[i];
+        for (int64_t p0 = A.rp[i]; p0 < A.rp[i + 1]; p0 += 32) {
+            int64_t p = p0 + lane;
+            int32_t j = p < A.rp[i + 1] ? __ldg(A.ci + p) : 0;
+            bool keep = p < A.rp[i + 1] && bit_of(cm, (uint32_t)j);
+            unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                int64_t q = o + __popc(bal & ((1u << lane) - 1u));
+                ci[q] = j;
+                val[q] = A.val ? A.val[p] : 1ull;
+            }
+            o += __popc(bal);
+        }
+    }
+}
+
+#define CK(x)                                                                     \
+    do {                                                                          \
+        cudaError_t e_ = (x);                                                     \
+        if (e_ != cudaSuccess) {                                                  \
+            fprintf(stderr, "mp: %s failed: %s\n", #x, cudaGetErrorString(e_));   \
+            return MP_ERR_CUDA;                                                   \
+        }                                                                         \
+    } while (0)
+
+int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, const Tuning &tun,
+           cudaStream_t s, Mat *out) {
+    const int64_t m = A.nrows;
+    out->nrows = m;
+    out->ncols = A.ncols;
+    out->rp = (int64_t *)al.alloc((size_t)(m + 1) * 8, s);
+    if (!out->rp) return MP_ERR_NOMEM;
+    unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(m * 32, 256), (int64_t)tun.sm_count * 32));
+    if (m) kl(k_filter_count, g, 256, 0, s, A, rm, cm, out->rp);
+    scan_i64(out->rp, out->rp, m, al, s);
+    int64_t nnz = 0;
+    CK(cudaMemcpyAsync(&nnz, out->rp + m, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->nnz = nnz;
+    out->ci = (int32_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s);
+    out->val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
+    if (!out->ci || !out->val) return MP_ERR_NOMEM;
+    if (nnz) kl(k_filter_fill, g, 256, 0, s, A, rm, cm, out->rp, out->ci, out->val);
+    CK(cudaGetLastError());
+    return MP_OK;
+}
+
+__global__ void k_mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64_t *set,
+                                     int64_t len) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool ok = false;
+    if (i < n) {
+        const int64_t v = prop[i];
+        int64_t lo = 0, hi = len;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (set[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        ok = lo < len && set[lo] == v;
+    }
+    uint32_t word = __ballot_sync(FULL, ok);
+    if ((threadIdx.x & 31) == 0 && i < n) m[i >> 5] &= word;
+}
+
+void mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64_t *set, int64_t len,
+                        cudaStream_t s) {
+    if (n) kl(k_mask_and_in_values, grid_for(n, 256), 256, 0, s, m, prop, n, set, len);
+}
+
+}  // namespace mp

@@ -320,54 +320,89 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         }
     }
 
-    // run the DAG level by level
+    // run the DAG level by level; every product of a level runs in one wave
     int max_level = 0;
     for (auto &nd : nodes) max_level = std::max(max_level, nd.level);
-    for (int lvl = 1; lvl <= max_level; lvl++) {
+    auto release_operands = [&](PNode &nd) {
+        for (int c : {nd.left, nd.right}) {
+            if (c < 0) continue;
+            if (--nodes[c].consumers <= 0 && !nodes[c].keep) nodes[c].res.reset();
+        }
+    };
+    int wave_rc = MP_OK;
+    for (int lvl = 1; lvl <= max_level && wave_rc == MP_OK; lvl++) {
+        std::vector<int> members;
+        std::vector<WaveIn> win;
         for (size_t x = 0; x < nodes.size(); x++) {
             PNode &nd = nodes[x];
             if (nd.level != lvl || nd.res) continue;
             const Query &Q = qs[nd.q];
             const auto &M = masks[nd.q];
-            auto t0 = std::chrono::steady_clock::now();
-            Mat C;
-            int rc;
             if (nd.filter) {
-                rc = filter(rels[Q.rels[0]].dev.view(), M[0], M[1], *alloc, tun, stream, &C);
-            } else {
-                const int k = nd.k;
-                if (nd.left >= 0 && nodes[nd.left].status) rc = nodes[nd.left].status;
-                else if (nd.right >= 0 && nodes[nd.right].status) rc = nodes[nd.right].status;
-                else {
-                    const int i = nd.i, j = nd.j;
-                    DCsr Xv = nd.left >= 0 ? nodes[nd.left].res->m.view() : rels[Q.rels[i]].dev.view();
-                    DCsr Yv = nd.right >= 0 ? nodes[nd.right].res->m.view() : rels[Q.rels[j]].dev.view();
-                    // a base factor enters with the masks of its end positions; a node's
-                    // result already carries them (0/1 diagonals are idempotent)
-                    const uint32_t *rm = nd.left < 0 ? M[i] : nullptr;
-                    const uint32_t *km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
-                    const uint32_t *cm = nd.right < 0 ? M[j + 1] : nullptr;
-                    rc = spgemm(Xv, Yv, rm, km, cm, *alloc, scratch, tun, stream, cfg.max_result_bytes, &C, &nd.st,
-                                &prof);
-                    if (!rc) {
-                        // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
-                        const double nnz_x = nd.left >= 0 ? (double)nodes[nd.left].res->m.nnz
-                                                          : (double)rels[Q.rels[i]].dev.nnz;
-                        nd.c_ops = cfg.alpha * nnz_x + cfg.beta * (double)nd.st.products + cfg.gamma * (double)C.nnz;
-                    }
-                }
+                auto t0 = std::chrono::steady_clock::now();
+                Mat C;
+                nd.status = filter(rels[Q.rels[0]].dev.view(), M[0], M[1], *alloc, tun, stream, &C);
+                nd.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                nd.subtree_ms = nd.ms;
+                if (!nd.status) nd.res = wrap(C);
+                else free_mat(C);
+                continue;
             }
-            nd.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (nd.left >= 0 && nodes[nd.left].status) {
+                nd.status = nodes[nd.left].status;
+                release_operands(nd);
+                continue;
+            }
+            if (nd.right >= 0 && nodes[nd.right].status) {
+                nd.status = nodes[nd.right].status;
+                release_operands(nd);
+                continue;
+            }
+            const int i = nd.i, j = nd.j, k = nd.k;
+            WaveIn in;
+            in.X = nd.left >= 0 ? nodes[nd.left].res->m.view() : rels[Q.rels[i]].dev.view();
+            in.Y = nd.right >= 0 ? nodes[nd.right].res->m.view() : rels[Q.rels[j]].dev.view();
+            // a base factor enters with the masks of its end positions; a node's result
+            // already carries them (0/1 diagonals are idempotent)
+            in.rm = nd.left < 0 ? M[i] : nullptr;
+            in.km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
+            in.cm = nd.right < 0 ? M[j + 1] : nullptr;
+            members.push_back((int)x);
+            win.push_back(in);
+        }
+        if (members.empty()) continue;
+        std::vector<WaveOut> wout;
+        auto t0 = std::chrono::steady_clock::now();
+        wave_rc = spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof);
+        const double wave_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        double wave_prod = 0.0;
+        for (auto &o : wout) wave_prod += (double)o.products;
+        for (size_t t = 0; t < members.size(); t++) {
+            PNode &nd = nodes[members[t]];
+            if (wave_rc) {
+                nd.status = wave_rc;
+                release_operands(nd);
+                continue;
+            }
+            WaveOut &o = wout[t];
+            nd.status = o.status;
+            nd.st.products = o.products;
+            nd.st.nnz = (uint64_t)o.m.nnz;
+            for (int b = 0; b < NBINS; b++) {
+                nd.st.sym_bins[b] = o.sym_bins[b];
+                nd.st.num_bins[b] = o.num_bins[b];
+            }
+            // the wave's time, shared in proportion to the products each member ran
+            nd.ms = wave_prod > 0 ? wave_ms * (double)o.products / wave_prod : wave_ms / (double)members.size();
             nd.subtree_ms = nd.ms + (nd.left >= 0 && !nodes[nd.left].from_cache ? nodes[nd.left].subtree_ms : 0.0) +
                             (nd.right >= 0 && !nodes[nd.right].from_cache ? nodes[nd.right].subtree_ms : 0.0);
-            nd.status = rc;
-            if (!rc) nd.res = wrap(C);
-            else free_mat(C);
-            // operands no longer needed by anyone
-            for (int c : {nd.left, nd.right}) {
-                if (c < 0) continue;
-                if (--nodes[c].consumers <= 0 && !nodes[c].keep) nodes[c].res.reset();
+            if (!o.status) {
+                // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
+                nd.c_ops = cfg.alpha * (double)(nd.left >= 0 ? nodes[nd.left].res->m.nnz : rels[qs[nd.q].rels[nd.i]].dev.nnz) +
+                           cfg.beta * (double)o.products + cfg.gamma * (double)o.m.nnz;
+                nd.res = wrap(o.m);
             }
+            release_operands(nd);
         }
     }
 

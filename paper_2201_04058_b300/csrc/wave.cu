@@ -1,0 +1,1143 @@
+// Sparse x sparse products of the metapath chain on sm_103a, many products per launch.
+//
+// One product C = diag(rm) X diag(km) Y diag(cm) is the constrained-adjacency product of
+// Sec. 2 (Problem 1 and the M_c * A that follows it) for one split of a chain: X and Y are
+// base 0/1 adjacency matrices (Def. 1) or earlier uint64 results, and the masks are the 0/1
+// diagonals M of Def. 3 stored as bitmaps. Counts are exact uint64; a count beyond 2^64 - 1
+// raises ERR_OVERFLOW instead of wrapping.
+//
+// A wave is a set of independent products (every ready product of a batch of queries).
+// Their rows are concatenated into one row space, so each step below is one launch per
+// bin for the whole wave, however many products it holds:
+//   1. row work:  prod_i = sum_{k in X_i, km[k]} nnz(Y_k), the Gustavson scalar products of
+//                 row i (an upper bound of nnz(C_i)); rows are binned by it;
+//   2. symbolic:  exact nnz(C_i) per bin: warp-per-row or block-per-row hash sets in shared
+//                 memory, a dense shared-memory bitmap for narrow outputs, or, for heavy
+//                 and wide rows, a per-row bitmap in global memory with the row's products
+//                 cut into equal work items spread over all SMs;
+//   3. scan:      row pointers of the whole wave (warp-shuffle block scans), rebased per
+//                 product;
+//   4. numeric:   rows re-binned by their exact nnz; accumulate (col -> count) with 64-bit
+//                 shared-memory atomics (hash or dense), or straight into the output slots
+//                 given by the bitmap ranks; rows leave in ascending column order (bitonic
+//                 sort for hash bins, in-order sweeps otherwise).
+// Every row's products are enumerated by a group of threads that scans the lengths of the
+// Y rows it needs and walks the flattened product list with a stride of the group size,
+// so consecutive threads read consecutive entries of a Y row.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mp {
+
+std::atomic<uint64_t> g_launches{0};
+
+bool Prof::init() {
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++)
+            for (int e = 0; e < 2; e++)
+                if (cudaEventCreate(&ev[p][b][e]) != cudaSuccess) return false;
+    return true;
+}
+
+void Prof::destroy() {
+    for (int p = 0; p < 2; p++)
+        for (int b = 0; b < NBINS; b++)
+            for (int e = 0; e < 2; e++)
+                if (ev[p][b][e]) cudaEventDestroy(ev[p][b][e]);
+}
+
+// One product of a wave, as the kernels see it.
+struct Prod {
+    DCsr X, Y;
+    const uint32_t *rm, *km, *cm;
+    int64_t row0;   // first wave row of this product
+    int64_t *rp;    // output row pointers (X.nrows + 1)
+    int32_t *ci;    // output column ids (after the symbolic pass)
+    uint64_t *val;  // output counts
+};
+
+// Per-product counters kept on the device.
+struct PStat {
+    unsigned long long prods;
+    long long nnz;
+    uint32_t err;
+    uint32_t sym_bins[NBINS];
+    uint32_t num_bins[NBINS];
+};
+
+struct BinArgs {
+    int dense_max_cols, dense_min_u, force;
+    uint64_t heavy;
+};
+
+// Per-bin tallies of one pass over the wave: rows, X entries, Gustavson products, output
+// entries and the algorithmic bytes of the bin's kernel.
+struct BinTally {
+    uint32_t counts[NBINS];
+    unsigned long long xent[NBINS], prods[NBINS], outn[NBINS], bytes[NBINS];
+};
+
+static constexpr int64_t LONGX = 8192;  // X rows longer than this are summed by all blocks
+
+// ------------------------------------------------------------------ row work + bins
+
+// Product of every wave row (binary search over the products' first rows).
+__global__ void k_rowprod(const int64_t *row0s, int w, int64_t M, int32_t *rowprod) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < M; g += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = w - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(row0s + mid) <= g) lo = mid; else hi = mid - 1;
+        }
+        rowprod[g] = lo;
+    }
+}
+
+// prod_i of every wave row. Each lane takes one of 32 consecutive rows; rows longer than
+// 16 entries are summed by the whole warp, one after the other, and rows longer than
+// LONGX are queued for k_rowwork_long.
+__global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, uint32_t *long_rows,
+                          uint32_t *n_long) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g0 = w * 32; g0 < M; g0 += nwarps * 32) {
+        const int64_t g = g0 + lane;
+        int64_t b = 0, e = 0;
+        const Prod *P = nullptr;
+        if (g < M) {
+            P = prods + rowprod[g];
+            const int64_t i = g - P->row0;
+            if (bit_of(P->rm, (uint32_t)i)) {
+                b = P->X.rp[i];
+                e = P->X.rp[i + 1];
+            }
+        }
+        uint64_t s = 0;
+        const bool mine = e - b <= 16;
+        if (mine)
+            for (int64_t p = b; p < e; p++) {
+                const int32_t k = __ldg(P->X.ci + p);
+                if (bit_of(P->km, (uint32_t)k)) s += (uint64_t)(__ldg(P->Y.rp + k + 1) - __ldg(P->Y.rp + k));
+            }
+        if (e - b > LONGX) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)g;
+        unsigned coop = __ballot_sync(FULL, !mine && e - b <= LONGX);
+        while (coop) {
+            const int src = __ffs(coop) - 1;
+            coop &= coop - 1;
+            const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+            const int32_t pi = __shfl_sync(FULL, g < M ? rowprod[g] : 0, src);
+            const Prod &Q = prods[pi];
+            uint64_t c = 0;
+            for (int64_t p = bb + lane; p < ee; p += 32) {
+                const int32_t k = __ldg(Q.X.ci + p);
+                if (bit_of(Q.km, (uint32_t)k)) c += (uint64_t)(__ldg(Q.Y.rp + k + 1) - __ldg(Q.Y.rp + k));
+            }
+            for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+            if (lane == src) s = c;
+        }
+        if (g < M) prod[g] = (e - b > LONGX) ? 0 : s;
+    }
+}
+
+// The queued long rows: every block takes a strided share of every long row's entries.
+__global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, const uint32_t *long_rows,
+                               const uint32_t *n_long) {
+    __shared__ unsigned long long red[32];
+    const uint32_t n = *n_long;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t r = 0; r < n; r++) {
+        const uint32_t g = long_rows[r];
+        const Prod &P = prods[rowprod[g]];
+        const int64_t i = g - P.row0;
+        const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
+        unsigned long long s = 0;
+        for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const int32_t k = __ldg(P.X.ci + p);
+            if (bit_of(P.km, (uint32_t)k)) s += (unsigned long long)(__ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k));
+        }
+        for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+        if (lane == 0) red[wid] = s;
+        __syncthreads();
+        if (wid == 0) {
+            s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
+            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+            if (lane == 0 && s) atomicAdd((unsigned long long *)(prod + g), s);
+        }
+        __syncthreads();
+    }
+}
+
+// Adds v into counter[key] once per group of lanes holding the same key (warp-aggregated).
+__device__ __forceinline__ void agg_add_u32(uint32_t *counter_base, int key, bool active, uint32_t v) {
+    const unsigned peers = __match_any_sync(FULL, active ? key : -1);
+    if (!active) return;
+    const int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(counter_base + key, v * (uint32_t)__popc(peers));
+}
+
+// Symbolic bin of every wave row from prod_i; rows without products get nnz_i = 0 and no
+// bin. Tallies per bin (for the byte model) and per product (products, rows per bin).
+__global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uint64_t *prod, int64_t M, BinArgs ba,
+                            int8_t *bin, int64_t *nnz, BinTally *tally, PStat *ps) {
+    __shared__ uint32_t hc[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS], hb[NBINS];
+    constexpr int NP = 8;  // products aggregated in shared memory per chunk of rows
+    __shared__ unsigned long long sp[NP];
+    if (threadIdx.x < NBINS) {
+        hc[threadIdx.x] = 0;
+        hx[threadIdx.x] = 0;
+        hp[threadIdx.x] = 0;
+        hb[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < M; g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + threadIdx.x;
+        const int pfirst = rowprod[g0];
+        if (threadIdx.x < NP) sp[threadIdx.x] = 0;
+        __syncthreads();
+        int b = -1, pi = 0;
+        uint64_t s = 0;
+        if (g < M) {
+            pi = rowprod[g];
+            const Prod &P = prods[pi];
+            s = prod[g];
+            if (s) {
+                const int64_t i = g - P.row0;
+                b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.force);
+                const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
+                atomicAdd(&hc[b], 1u);
+                atomicAdd(&hx[b], xe);
+                atomicAdd(&hp[b], (unsigned long long)s);
+                // symbolic bytes: X row pointers + nnz write, per X entry its column id and the
+                // two Y row pointers, per product one Y column id
+                atomicAdd(&hb[b], 24ull + xe * 20ull + (unsigned long long)s * 4ull);
+                if (pi - pfirst < NP) atomicAdd(&sp[pi - pfirst], (unsigned long long)s);
+                else atomicAdd(&ps[pi].prods, (unsigned long long)s);
+            } else {
+                nnz[g] = 0;
+            }
+            bin[g] = (int8_t)b;
+        }
+        // rows per (product, bin), aggregated over lanes with the same pair
+        agg_add_u32(&ps[0].sym_bins[0], pi * (int)(sizeof(PStat) / 4) + b, b >= 0, 1u);
+        __syncthreads();
+        if (threadIdx.x < NP && sp[threadIdx.x]) atomicAdd(&ps[pfirst + threadIdx.x].prods, sp[threadIdx.x]);
+        __syncthreads();
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < NBINS && hc[t]) {
+        atomicAdd(tally->counts + t, hc[t]);
+        atomicAdd(tally->xent + t, hx[t]);
+        atomicAdd(tally->prods + t, hp[t]);
+        atomicAdd(tally->bytes + t, hb[t]);
+    }
+}
+
+// Numeric bins from the exact row sizes (grp = wave row pointers); rows the symbolic pass
+// put in GLOBAL stay there (their bitmaps give the output positions).
+__global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_t *grp, const uint64_t *prod,
+                         int64_t M, BinArgs ba, int8_t *bin, BinTally *tally, PStat *ps) {
+    __shared__ uint32_t hc[NBINS];
+    __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS], hb[NBINS];
+    if (threadIdx.x < NBINS) {
+        hc[threadIdx.x] = 0;
+        hx[threadIdx.x] = 0;
+        hp[threadIdx.x] = 0;
+        ho[threadIdx.x] = 0;
+        hb[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < M; g0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = g0 + threadIdx.x;
+        int b = -1, pi = 0;
+        if (g < M) {
+            pi = rowprod[g];
+            const Prod &P = prods[pi];
+            const int64_t z = P.ci ? grp[g + 1] - grp[g] : 0;  // no outputs: product failed
+            if (z) {
+                if (bin[g] == B_GLOBAL) {
+                    b = B_GLOBAL;
+                } else {
+                    b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.force);
+                    if (b == B_GLOBAL) atomicOr(&ps[pi].err, ERR_PROBE);  // cannot happen: nnz <= the bound
+                }
+                const int64_t i = g - P.row0;
+                const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
+                const unsigned long long pr = prod[g];
+                atomicAdd(&hc[b], 1u);
+                atomicAdd(&hx[b], xe);
+                atomicAdd(&hp[b], pr);
+                atomicAdd(&ho[b], (unsigned long long)z);
+                // numeric bytes: X and C row pointers, per X entry its column id (+ value) and
+                // two Y row pointers, per product a Y column id (+ value), per output 12 bytes
+                atomicAdd(&hb[b], 32ull + xe * (20ull + (P.X.val ? 8ull : 0ull)) +
+                                      pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 12ull);
+            }
+            bin[g] = (int8_t)b;
+        }
+        agg_add_u32(&ps[0].num_bins[0], pi * (int)(sizeof(PStat) / 4) + b, b >= 0, 1u);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < NBINS && hc[t]) {
+        atomicAdd(tally->counts + t, hc[t]);
+        atomicAdd(tally->xent + t, hx[t]);
+        atomicAdd(tally->prods + t, hp[t]);
+        atomicAdd(tally->outn + t, ho[t]);
+        atomicAdd(tally->bytes + t, hb[t]);
+    }
+}
+
+// counts[0..NBINS) -> offsets[0..NBINS]; cursors reset.
+__global__ void k_bin_offsets(const uint32_t *counts, uint32_t *offsets, uint32_t *cursors) {
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int b = 0; b < NBINS; b++) {
+            offsets[b] = s;
+            s += counts[b];
+            cursors[b] = 0;
+        }
+        offsets[NBINS] = s;
+    }
+}
+
+__global__ void k_bin_fill(const int8_t *bin, int64_t n, const uint32_t *offsets, uint32_t *cursors, uint32_t *list) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int b = i < n ? bin[i] : -1;
+        const unsigned peers = __match_any_sync(FULL, b);
+        if (b >= 0) {
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(cursors + b, (uint32_t)__popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+            list[offsets[b] + base + rank] = (uint32_t)i;
+        }
+    }
+}
+
+// Per-product row pointers from the wave's: rp_p[i] = grp[row0 + i] - grp[row0], and each
+// product's nnz.
+__global__ void k_rebase(const Prod *prods, const int32_t *rowprod, const int64_t *grp, int64_t M, PStat *ps) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < M; g += (int64_t)gridDim.x * blockDim.x) {
+        const int pi = rowprod[g];
+        const Prod &P = prods[pi];
+        const int64_t i = g - P.row0;
+        const int64_t base = grp[P.row0];
+        P.rp[i] = grp[g] - base;
+        if (i == P.X.nrows - 1) {
+            P.rp[i + 1] = grp[g + 1] - base;
+            ps[pi].nnz = grp[g + 1] - base;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ shared-memory bins
+
+struct PassArgs {
+    const Prod *prods;
+    const int32_t *rowprod;
+    const uint32_t *list;
+    const uint32_t *counts, *offsets;
+    int64_t *nnz;    // symbolic: nnz per wave row; numeric: the wave row pointers
+    PStat *ps;       // per-product error words live here
+};
+
+// The row a bin entry stands for.
+struct RowRef {
+    const Prod *P;
+    int pi;
+    int64_t g, i;
+    __device__ __forceinline__ RowRef(const PassArgs &a, uint32_t entry) {
+        g = entry;
+        pi = a.rowprod[g];
+        P = a.prods + pi;
+        i = g - P->row0;
+    }
+    __device__ __forceinline__ uint32_t *err(const PassArgs &a) const { return &a.ps[pi].err; }
+    // numeric: output offset of the row inside its product and its exact length
+    __device__ __forceinline__ int64_t out_off(const PassArgs &a) const { return a.nnz[g] - a.nnz[P->row0]; }
+    __device__ __forceinline__ int64_t out_len(const PassArgs &a) const { return a.nnz[g + 1] - a.nnz[g]; }
+};
+
+template <int T, int W>
+__global__ void __launch_bounds__(W * 32) k_sym_warp(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Stage *sg = (Stage *)smem + wid * 32;
+    uint32_t *keys = (uint32_t *)((Stage *)smem + W * 32) + wid * T;
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        for (int s = lane; s < T; s += 32) keys[s] = EMPTY;
+        __syncwarp();
+        int c = 0;
+        uint32_t *err = R.err(a);
+        for_each_product<32, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane,
+                                    err, [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        if (lane == 0) a.nnz[R.g] = c;
+        __syncwarp();
+    }
+}
+
+template <int T, int W>
+__global__ void __launch_bounds__(W * 32) k_num_warp(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Stage *sg = (Stage *)smem + wid * 32;
+    unsigned long long *vals = (unsigned long long *)((Stage *)smem + W * 32) + wid * T;
+    uint32_t *keys = (uint32_t *)((unsigned long long *)((Stage *)smem + W * 32) + W * T) + wid * T;
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        uint32_t *err = R.err(a);
+        for (int s = lane; s < T; s += 32) {
+            keys[s] = EMPTY;
+            vals[s] = 0;
+        }
+        __syncwarp();
+        for_each_product<32, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane, err,
+                                   [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
+        __syncwarp();
+        // compact occupied slots to the front (in place: writes never pass the read point)
+        int n = 0;
+        for (int s0 = 0; s0 < T; s0 += 32) {
+            const uint32_t k = keys[s0 + lane];
+            const unsigned long long v = vals[s0 + lane];
+            const unsigned bal = __ballot_sync(FULL, k != EMPTY);
+            const int pos = n + __popc(bal & ((1u << lane) - 1u));
+            __syncwarp();
+            if (k != EMPTY) {
+                keys[pos] = k;
+                vals[pos] = v;
+            }
+            n += __popc(bal);
+            __syncwarp();
+        }
+        int Pn = 1;
+        while (Pn < n) Pn <<= 1;
+        for (int s = n + lane; s < Pn; s += 32) keys[s] = EMPTY;
+        __syncwarp();
+        bitonic<32>(keys, vals, Pn, lane);
+        const int64_t o = R.out_off(a), len = R.out_len(a);
+        if (lane == 0 && len != n) atomicOr(err, ERR_COUNT);
+        const int m = (int)min((int64_t)n, len);
+        for (int s = lane; s < m; s += 32) {
+            P.ci[o + s] = (int32_t)keys[s];
+            P.val[o + s] = vals[s];
+        }
+        __syncwarp();
+    }
+}
+
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_sym_block(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    __shared__ int cnt_s;
+    Stage *sg = (Stage *)smem;
+    uint32_t *keys = (uint32_t *)(sg + NT);
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        uint32_t *err = R.err(a);
+        for (int s = threadIdx.x; s < T; s += NT) keys[s] = EMPTY;
+        if (threadIdx.x == 0) cnt_s = 0;
+        __syncthreads();
+        int c = 0;
+        for_each_product<NT, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
+                                    threadIdx.x, err,
+                                    [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt_s, c);
+        __syncthreads();
+        if (threadIdx.x == 0) a.nnz[R.g] = cnt_s;
+        __syncthreads();
+    }
+}
+
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_num_block(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    constexpr int PER = T / NT;  // slots per thread in the compaction
+    Stage *sg = (Stage *)smem;
+    unsigned long long *vals = (unsigned long long *)(sg + NT);
+    uint32_t *keys = (uint32_t *)(vals + T);
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        uint32_t *err = R.err(a);
+        for (int s = threadIdx.x; s < T; s += NT) {
+            keys[s] = EMPTY;
+            vals[s] = 0;
+        }
+        __syncthreads();
+        for_each_product<NT, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
+                                   threadIdx.x, err,
+                                   [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
+        __syncthreads();
+        uint32_t k[PER];
+        unsigned long long v[PER];
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            k[u] = keys[threadIdx.x * PER + u];
+            v[u] = vals[threadIdx.x * PER + u];
+            c += k[u] != EMPTY;
+        }
+        int64_t pos = block_excl_scan<NT>(c, warp_sums, &gtot);
+        const int n = (int)gtot;
+#pragma unroll
+        for (int u = 0; u < PER; u++)
+            if (k[u] != EMPTY) {
+                keys[pos] = k[u];
+                vals[pos] = v[u];
+                pos++;
+            }
+        int Pn = 1;
+        while (Pn < n) Pn <<= 1;
+        __syncthreads();
+        for (int s = n + threadIdx.x; s < Pn; s += NT) keys[s] = EMPTY;
+        __syncthreads();
+        bitonic<NT>(keys, vals, Pn, threadIdx.x);
+        const int64_t o = R.out_off(a), len = R.out_len(a);
+        if (threadIdx.x == 0 && len != n) atomicOr(err, ERR_COUNT);
+        const int m = (int)min((int64_t)n, len);
+        for (int s = threadIdx.x; s < m; s += NT) {
+            P.ci[o + s] = (int32_t)keys[s];
+            P.val[o + s] = vals[s];
+        }
+        __syncthreads();
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sym_dense(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    __shared__ int cnt_s;
+    Stage *sg = (Stage *)smem;
+    uint32_t *bm = (uint32_t *)(sg + NT);
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        uint32_t *err = R.err(a);
+        const int nw = (int)((P.Y.ncols + 31) >> 5);
+        for (int s = threadIdx.x; s < nw; s += NT) bm[s] = 0;
+        if (threadIdx.x == 0) cnt_s = 0;
+        __syncthreads();
+        int c = 0;
+        for_each_product<NT, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
+                                    threadIdx.x, err, [&](uint32_t j, uint64_t) {
+                                        const uint32_t m = 1u << (j & 31);
+                                        c += (atomicOr(bm + (j >> 5), m) & m) == 0;
+                                    });
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt_s, c);
+        __syncthreads();
+        if (threadIdx.x == 0) a.nnz[R.g] = cnt_s;
+        __syncthreads();
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    Stage *sg = (Stage *)smem;
+    unsigned long long *acc = (unsigned long long *)(sg + NT);
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod &P = *R.P;
+        uint32_t *err = R.err(a);
+        const int ncols = (int)P.Y.ncols;
+        const int per = (ncols + NT - 1) / NT;
+        for (int s = threadIdx.x; s < ncols; s += NT) acc[s] = 0;
+        __syncthreads();
+        for_each_product<NT, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
+                                   threadIdx.x, err, [&](uint32_t j, uint64_t v) {
+                                       const unsigned long long old = atomicAdd(acc + j, (unsigned long long)v);
+                                       if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                                   });
+        __syncthreads();
+        // in-order sweep: thread t owns columns [t*per, t*per + per)
+        const int c0 = threadIdx.x * per;
+        const int c1 = min(ncols, c0 + per);
+        int c = 0;
+        for (int s = c0; s < c1; s++) c += acc[s] != 0;
+        int64_t pos = block_excl_scan<NT>(c, warp_sums, &gtot);
+        const int64_t o = R.out_off(a), len = R.out_len(a);
+        if (threadIdx.x == 0 && len != gtot) atomicOr(err, ERR_COUNT);
+        for (int s = c0; s < c1; s++) {
+            const unsigned long long v = acc[s];
+            if (v) {
+                if (pos < len) {
+                    P.ci[o + pos] = s;
+                    P.val[o + pos] = v;
+                }
+                pos++;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ GLOBAL bin: split rows
+
+// Heavy rows and rows too wide for a shared-memory table. Each row's Gustavson products,
+// in the order of its X entries, are cut into work items of PCH products, and the items
+// of all rows are spread over all blocks, so a few huge rows (or one hub Y row) still
+// fill the GPU:
+//   symbolic: every product sets bit j of the row's bitmap (1 bit per output column);
+//             a rank pass turns the bitmap into rank[w] = set bits before word w, and the
+//             row's nnz is the total;
+//   numeric:  a fill pass writes each set bit's column id at its rank (so the row comes
+//             out in ascending column order) and zeroes the value; then every product
+//             adds its count straight into the output slot rank[w] + popc(bits below j).
+// Bitmaps and ranks take 8 bytes per 32 output columns per row (slots of the widest
+// product's size); rows are processed in rounds that fit the scratch cap (one round keeps
+// the symbolic bitmaps for the numeric pass, several rounds rebuild them).
+static constexpr int64_t PCH = 16384;  // Gustavson products per work item
+static constexpr int GNT = 256;        // threads per GLOBAL block
+static constexpr int RW = 8;           // bitmap words per thread in the rank pass
+
+struct GlobArgs {
+    const uint32_t *list;     // wave rows of the GLOBAL bin, in symbolic order
+    const int64_t *item_off;  // R+1 work-item offsets
+    const int64_t *xbase;     // R+1 offsets of each row's X entries in xoff
+    const int64_t *xoff;      // per X entry of a GLOBAL row: global product offset
+    const uint64_t *prod;     // prod_i per wave row
+    int64_t r0, r1;           // rows of this round
+    uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
+    int64_t nw;               // slot size (words)
+};
+
+// Per GLOBAL row: its X entry count and its number of work items.
+__global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const uint64_t *prod, int64_t *xlen,
+                            int64_t *items) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const RowRef Rf(a, list[r]);
+        xlen[r] = Rf.P->X.rp[Rf.i + 1] - Rf.P->X.rp[Rf.i];
+        items[r] = ((int64_t)prod[Rf.g] + PCH - 1) / PCH;
+    }
+}
+
+// The masked Y-row length of every X entry of every GLOBAL row, as one flat array (row r's
+// entries start at xbase[r]); a device-wide exclusive scan then gives each entry's global
+// product offset.
+__global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const int64_t *xbase, int64_t *xoff) {
+    const int64_t xtot = xbase[R];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < xtot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
+        }
+        const RowRef Rf(a, list[lo]);
+        const Prod &P = *Rf.P;
+        const int64_t p = P.X.rp[Rf.i] + (e - xbase[lo]);
+        const int32_t k = __ldg(P.X.ci + p);
+        xoff[e] = bit_of(P.km, (uint32_t)k) ? __ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k) : 0;
+    }
+}
+
+// One work item per block iteration: products [s0, s1) of one row. The X entries that hold
+// them are staged GNT at a time with their product offsets (from xoff); consecutive
+// threads take consecutive products, so a long Y row is read coalesced.
+template <bool NUM>
+__global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
+    __shared__ int64_t s_off[GNT + 1];
+    __shared__ int64_t s_st[GNT];
+    __shared__ uint64_t s_a[GNT];
+    const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
+    for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+        int64_t lo = g.r0, hi = g.r1 - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (g.item_off[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t r = lo;
+        const RowRef Rf(a, g.list[r]);
+        const Prod &P = *Rf.P;
+        if (NUM && !P.val) continue;  // the product failed before its numeric pass
+        uint32_t *err = Rf.err(a);
+        const int64_t xb = P.X.rp[Rf.i], xe = P.X.rp[Rf.i + 1];
+        const int64_t *xo = g.xoff + g.xbase[r];
+        // product offsets are global across the GLOBAL rows: this row's start at xo[0]
+        const int64_t total = __ldg(xo) + (int64_t)g.prod[Rf.g];
+        const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
+        const int64_t s1 = min(total, s0 + PCH);
+        // first X entry whose products reach s0: the last p with xo[p] <= s0
+        int64_t plo = 0, phi = xe - xb - 1;
+        while (plo < phi) {
+            const int64_t mid = (plo + phi + 1) >> 1;
+            if (__ldg(xo + mid) <= s0) plo = mid; else phi = mid - 1;
+        }
+        uint32_t *bm = g.bm + (r - g.r0) * g.nw;
+        const uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        unsigned long long *val = NUM ? (unsigned long long *)P.val + Rf.out_off(a) : nullptr;
+        for (int64_t c0 = xb + plo; c0 < xe; c0 += GNT) {
+            const int64_t base = __ldg(xo + (c0 - xb));
+            if (base >= s1) break;  // uniform: every thread reads the same base
+            const int64_t p = c0 + threadIdx.x;
+            const int nent = (int)min((int64_t)GNT, xe - c0);
+            if (threadIdx.x < nent) {
+                const int32_t k = __ldg(P.X.ci + p);
+                s_off[threadIdx.x] = __ldg(xo + (p - xb)) - base;
+                s_st[threadIdx.x] = __ldg(P.Y.rp + k);
+                s_a[threadIdx.x] = (NUM && P.X.val) ? __ldg(P.X.val + p) : 1ull;
+            }
+            if (threadIdx.x == 0) s_off[nent] = (c0 + nent < xe ? __ldg(xo + (c0 + nent - xb)) : total) - base;
+            __syncthreads();
+            const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
+            for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
+                int l = 0, h = nent - 1;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (s_off[mid] <= f) l = mid; else h = mid - 1;
+                }
+                const int64_t q = s_st[l] + (f - s_off[l]);
+                const uint32_t j = (uint32_t)__ldg(P.Y.ci + q);
+                if (!bit_of(P.cm, j)) continue;
+                if (!NUM) {
+                    atomicOr(bm + (j >> 5), 1u << (j & 31));
+                } else {
+                    const uint64_t av = s_a[l];
+                    const uint64_t bv = P.Y.val ? __ldg(P.Y.val + q) : 1ull;
+                    const uint64_t v = av * bv;
+                    if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+                    const uint32_t w = j >> 5;
+                    const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
+                    const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
+                    if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int numeric) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    for (int64_t r = g.r0 + blockIdx.x; r < g.r1; r += gridDim.x) {
+        const RowRef Rf(a, g.list[r]);
+        const int64_t nw = (Rf.P->Y.ncols + 31) / 32;
+        const uint32_t *bm = g.bm + (r - g.r0) * g.nw;
+        uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        int64_t carry = 0;
+        for (int64_t w0 = 0; w0 < nw; w0 += (int64_t)GNT * RW) {
+            const int64_t wb = w0 + (int64_t)threadIdx.x * RW;
+            int cnt[RW];
+            int c = 0;
+#pragma unroll
+            for (int u = 0; u < RW; u++) {
+                cnt[u] = wb + u < nw ? __popc(bm[wb + u]) : 0;
+                c += cnt[u];
+            }
+            int64_t ex = carry + block_excl_scan<GNT>(c, warp_sums, &gtot);
+#pragma unroll
+            for (int u = 0; u < RW; u++) {
+                if (wb + u < nw) rk[wb + u] = (uint32_t)ex;
+                ex += cnt[u];
+            }
+            carry += gtot;
+        }
+        if (threadIdx.x == 0) {
+            if (!numeric) a.nnz[Rf.g] = carry;
+            else if (Rf.P->ci && Rf.out_len(a) != carry) atomicOr(Rf.err(a), ERR_COUNT);
+        }
+    }
+}
+
+// One thread per bitmap word: the word's set bits become consecutive output entries.
+__global__ void k_glob_fill(PassArgs a, GlobArgs g) {
+    const int64_t total = (g.r1 - g.r0) * g.nw;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = g.bm[x];
+        if (!word) continue;
+        const int64_t slot = x / g.nw, w = x - slot * g.nw;
+        const RowRef Rf(a, g.list[g.r0 + slot]);
+        const Prod &P = *Rf.P;
+        if (!P.ci) continue;
+        int64_t pos = Rf.out_off(a) + g.rank[x];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            P.ci[pos] = (int32_t)(w * 32 + b);
+            P.val[pos] = 0;
+            pos++;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+template <class K>
+static void launch(K kern, unsigned grid, int nt, size_t smem, cudaStream_t s, const PassArgs &a, int bin) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kl(kern, grid, nt, smem, s, a, bin);
+}
+
+static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_blocks) {
+    const unsigned g = (unsigned)((rows_upper + rows_per_block - 1) / rows_per_block);
+    return std::max(1u, std::min(g, (unsigned)max_blocks));
+}
+
+// Launch every non-empty shared-memory bin's kernel of one pass, each grid sized to its
+// bin's rows (capped at a few blocks per SM; the kernels loop over their bin). With prof,
+// CUDA events bracket each launch. GLOBAL runs separately (glob_pass). dense_cols is the
+// widest output among the wave's products that fit the dense bin.
+static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t dense_cols, const Tuning &tun,
+                     cudaStream_t s, Prof *prof) {
+    const bool numeric = pass == 1;
+    const int sms = tun.sm_count;
+    const size_t stage = sizeof(Stage);
+    for (int b = 0; b < B_GLOBAL; b++) {
+        const uint32_t rows = host_counts[b];
+        if (!rows) continue;
+        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][0], s);
+        switch (b) {
+#define WARP_BIN(BIN, T, W)                                                                       \
+    case BIN: {                                                                                   \
+        const unsigned g = blocks_for(rows, W, sms * 8);                                          \
+        if (numeric)                                                                              \
+            launch(k_num_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 12, s, a, BIN); \
+        else                                                                                      \
+            launch(k_sym_warp<T, W>, g, W * 32, W * 32 * stage + (size_t)W * T * 4, s, a, BIN);  \
+        break;                                                                                    \
+    }
+            WARP_BIN(B_W32, 32, 8)
+            WARP_BIN(B_W64, 64, 8)
+            WARP_BIN(B_W128, 128, 8)
+            WARP_BIN(B_W256, 256, 8)
+            WARP_BIN(B_W512, 512, 4)
+            WARP_BIN(B_W1024, 1024, 4)
+#undef WARP_BIN
+#define BLOCK_BIN(BIN, T, NT)                                                          \
+    case BIN: {                                                                        \
+        const unsigned g = blocks_for(rows, 1, sms * 4);                               \
+        if (numeric)                                                                   \
+            launch(k_num_block<T, NT>, g, NT, NT * stage + (size_t)T * 12, s, a, BIN); \
+        else                                                                           \
+            launch(k_sym_block<T, NT>, g, NT, NT * stage + (size_t)T * 4, s, a, BIN);  \
+        break;                                                                         \
+    }
+            BLOCK_BIN(B_K2048, 2048, 256)
+            BLOCK_BIN(B_K4096, 4096, 512)
+            BLOCK_BIN(B_K8192, 8192, 1024)
+#undef BLOCK_BIN
+            case B_DENSE: {
+                const unsigned g = blocks_for(rows, 1, sms * 4);
+                if (numeric)
+                    launch(k_num_dense<256>, g, 256, 256 * stage + (size_t)dense_cols * 8, s, a, B_DENSE);
+                else
+                    launch(k_sym_dense<256>, g, 256, 256 * stage + (size_t)((dense_cols + 31) / 32) * 4, s, a,
+                           B_DENSE);
+                break;
+            }
+        }
+        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][1], s);
+    }
+}
+
+static void prof_collect(Prof *prof, int pass, const BinTally &t) {
+    if (!prof || !prof->on) return;
+    for (int b = 0; b < NBINS; b++) {
+        if (!t.counts[b]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof->ev[pass][b][0], prof->ev[pass][b][1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        KStat &k = prof->k[pass][b];
+        k.launches++;
+        k.ms += ms;
+        k.bytes += (double)t.bytes[b];
+    }
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// State of the GLOBAL bin of one wave across its two passes.
+struct Glob {
+    int64_t R = 0, nw = 0, per_round = 0, rounds = 0;
+    uint32_t *list = nullptr;  // copy of the bin's rows in symbolic order
+    int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr;
+    const uint64_t *prod = nullptr;
+    uint32_t *bm = nullptr, *rank = nullptr;
+    bool kept = false;         // bitmaps of a single round survive into the numeric pass
+};
+
+static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
+    if (g.list) al.free(g.list, s);
+    if (g.item_off) al.free(g.item_off, s);
+    if (g.xbase) al.free(g.xbase, s);
+    if (g.xoff) al.free(g.xoff, s);
+    if (g.bm) al.free(g.bm, s);
+    if (g.rank) al.free(g.rank, s);
+    g = Glob{};
+}
+
+// One pass of the GLOBAL bin (all rounds). pass 0 counts, pass 1 writes the rows.
+static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, cudaStream_t s, Prof *prof) {
+    const unsigned grid = (unsigned)tun.sm_count * 8;
+    if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
+    for (int64_t r0 = 0; r0 < g.R; r0 += g.per_round) {
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bm,
+                          g.rank, g.nw};
+        const int64_t rows = ga.r1 - ga.r0;
+        if (pass == 0 || !g.kept) {
+            cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
+            kl(k_glob_set<false>, grid, GNT, 0, s, a, ga);
+            kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
+        }
+        if (pass == 1) {
+            const int64_t words = rows * g.nw;
+            kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
+               s, a, ga);
+            kl(k_glob_set<true>, grid, GNT, 0, s, a, ga);
+        }
+    }
+    if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
+}
+
+// ------------------------------------------------------------------ host orchestration
+
+int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof) {
+    const int w = (int)in.size();
+    out.assign(w, WaveOut{});
+    if (w == 0) return MP_OK;
+    struct Small {
+        BinTally tally;
+        uint32_t offsets[NBINS + 1];
+        uint32_t cursors[NBINS];
+        uint32_t n_long;
+    };
+    std::vector<Prod> hp(w);
+    std::vector<int64_t> row0s(w + 1, 0);
+    int64_t dense_cols = 0, max_cols = 0;
+    for (int p = 0; p < w; p++) {
+        const WaveIn &x = in[p];
+        Prod &P = hp[p];
+        P.X = x.X;
+        P.Y = x.Y;
+        P.rm = x.rm;
+        P.km = x.km;
+        P.cm = x.cm;
+        P.row0 = row0s[p];
+        row0s[p + 1] = row0s[p] + x.X.nrows;
+        if (x.Y.ncols <= tun.dense_max_cols) dense_cols = std::max<int64_t>(dense_cols, x.Y.ncols);
+        max_cols = std::max<int64_t>(max_cols, x.Y.ncols);
+    }
+    const int64_t M = row0s[w];
+    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows u32[M], rowprod i32[M],
+    // wave nnz / row pointers i64[M+1], product descriptors, row0s, per-product stats, two Smalls
+    const size_t o_prod = 0;
+    const size_t o_bin = align256(o_prod + (size_t)M * 8);
+    const size_t o_list = align256(o_bin + (size_t)M);
+    const size_t o_long = align256(o_list + (size_t)M * 4);
+    const size_t o_rowprod = align256(o_long + (size_t)M * 4);
+    const size_t o_grp = align256(o_rowprod + (size_t)M * 4);
+    const size_t o_prods = align256(o_grp + (size_t)(M + 1) * 8);
+    const size_t o_row0s = align256(o_prods + sizeof(Prod) * w);
+    const size_t o_ps = align256(o_row0s + (size_t)(w + 1) * 8);
+    const size_t o_small = align256(o_ps + sizeof(PStat) * w);
+    const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
+    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy};
+    int rc = MP_OK;
+    Glob gl;
+    PassArgs pa{};
+    Small h_sym, h_num;
+    std::vector<PStat> hps(w);
+    char *ws = (char *)al.alloc(ws_bytes, s);
+    if (!ws) return MP_ERR_NOMEM;
+    uint64_t *prod = (uint64_t *)(ws + o_prod);
+    int8_t *bin = (int8_t *)(ws + o_bin);
+    uint32_t *list = (uint32_t *)(ws + o_list);
+    uint32_t *long_rows = (uint32_t *)(ws + o_long);
+    int32_t *rowprod = (int32_t *)(ws + o_rowprod);
+    int64_t *grp = (int64_t *)(ws + o_grp);
+    Prod *dprods = (Prod *)(ws + o_prods);
+    int64_t *drow0s = (int64_t *)(ws + o_row0s);
+    PStat *ps = (PStat *)(ws + o_ps);
+    Small *sm_sym = (Small *)(ws + o_small);
+    Small *sm_num = sm_sym + 1;
+    auto fail = [&](int code) {
+        for (int p = 0; p < w; p++) {
+            if (hp[p].rp) al.free(hp[p].rp, s);
+            if (hp[p].ci) al.free(hp[p].ci, s);
+            if (hp[p].val) al.free(hp[p].val, s);
+        }
+        glob_release(gl, al, s);
+        al.free(ws, s);
+        out.assign(w, WaveOut{});
+        return code;
+    };
+    auto cuda_ok = [&](cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return true;
+        fprintf(stderr, "mp: %s: %s\n", what, cudaGetErrorString(e));
+        return false;
+    };
+    for (int p = 0; p < w; p++) {
+        hp[p].rp = (int64_t *)al.alloc((size_t)(in[p].X.nrows + 1) * 8, s);
+        if (!hp[p].rp) return fail(MP_ERR_NOMEM);
+        if (in[p].X.nrows == 0 && !cuda_ok(cudaMemsetAsync(hp[p].rp, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
+    }
+    if (!cuda_ok(cudaMemcpyAsync(dprods, hp.data(), sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload") ||
+        !cuda_ok(cudaMemcpyAsync(drow0s, row0s.data(), (size_t)(w + 1) * 8, cudaMemcpyHostToDevice, s), "upload") ||
+        !cuda_ok(cudaMemsetAsync(ps, 0, sizeof(PStat) * w, s), "memset") ||
+        !cuda_ok(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s), "memset"))
+        return fail(MP_ERR_CUDA);
+
+    pa.prods = dprods;
+    pa.rowprod = rowprod;
+    pa.list = list;
+    pa.nnz = grp;
+    pa.ps = ps;
+    // 1. row work, symbolic bins, rows grouped by bin
+    if (M > 0) {
+        const unsigned gr = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
+        kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
+        const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, long_rows, &sm_sym->n_long);
+        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, long_rows, &sm_sym->n_long);
+        kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, M, ba, bin, grp, &sm_sym->tally, ps);
+        kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
+        kl(k_bin_fill, gr, 256, 0, s, bin, M, sm_sym->offsets, sm_sym->cursors, list);
+    }
+    if (!cuda_ok(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
+        !cuda_ok(cudaStreamSynchronize(s), "sync"))
+        return fail(MP_ERR_CUDA);
+    pa.counts = sm_sym->tally.counts;
+    pa.offsets = sm_sym->offsets;
+    // GLOBAL bin set-up: its rows, work items, product offsets, bitmap rounds
+    gl.R = h_sym.tally.counts[B_GLOBAL];
+    if (gl.R) {
+        gl.nw = (max_cols + 31) / 32;
+        const uint64_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
+        gl.per_round = std::max<int64_t>(1, std::min<int64_t>(gl.R, (int64_t)(cap / ((uint64_t)gl.nw * 8))));
+        gl.rounds = (gl.R + gl.per_round - 1) / gl.per_round;
+        gl.kept = gl.rounds == 1;
+        const int64_t xtot = (int64_t)h_sym.tally.xent[B_GLOBAL];
+        gl.prod = prod;
+        gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
+        gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
+        gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
+        gl.xoff = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
+        gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
+        gl.rank = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
+        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff || !gl.bm || !gl.rank) return fail(MP_ERR_NOMEM);
+        if (!cuda_ok(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4,
+                                     cudaMemcpyDeviceToDevice, s), "copy"))
+            return fail(MP_ERR_CUDA);
+        kl(k_glob_prep, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, pa, gl.list, gl.R, prod,
+           gl.xbase, gl.item_off);
+        scan_i64(gl.item_off, gl.item_off, gl.R, al, s);
+        scan_i64(gl.xbase, gl.xbase, gl.R, al, s);
+        kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(xtot, 256), (int64_t)tun.sm_count * 16)),
+           256, 0, s, pa, gl.list, gl.R, gl.xbase, gl.xoff);
+        scan_i64(gl.xoff, gl.xoff, xtot, al, s);
+    }
+    // 2-3. symbolic pass, wave row pointers, per-product row pointers and sizes
+    if (M > 0) run_pass(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof);
+    if (gl.R) glob_pass(0, gl, pa, tun, s, prof);
+    scan_i64(grp, grp, M, al, s);
+    if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
+                  dprods, rowprod, grp, M, ps);
+    if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
+        !cuda_ok(cudaStreamSynchronize(s), "sync"))
+        return fail(MP_ERR_CUDA);
+    prof_collect(prof, 0, h_sym.tally);
+    // per product: status, size guard, output arrays
+    bool any_out = false;
+    for (int p = 0; p < w; p++) {
+        WaveOut &o = out[p];
+        o.products = hps[p].prods;
+        for (int b = 0; b < NBINS; b++) o.sym_bins[b] = hps[p].sym_bins[b];
+        const int64_t nnz = in[p].X.nrows ? hps[p].nnz : 0;
+        if (hps[p].err) {
+            o.status = (hps[p].err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+            continue;
+        }
+        Mat m;
+        m.nrows = in[p].X.nrows;
+        m.ncols = in[p].Y.ncols;
+        m.nnz = nnz;
+        if (max_result_bytes && m.bytes() > max_result_bytes) {
+            o.status = MP_ERR_TOO_LARGE;
+            continue;
+        }
+        hp[p].ci = (int32_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s);
+        hp[p].val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
+        if (!hp[p].ci || !hp[p].val) return fail(MP_ERR_NOMEM);
+        if (nnz) any_out = true;
+    }
+    // 4. numeric pass; products that failed keep null outputs and their rows are skipped
+    if (any_out) {
+        if (!cuda_ok(cudaMemcpyAsync(dprods, hp.data(), sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload"))
+            return fail(MP_ERR_CUDA);
+        const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
+        kl(k_numbin, g, 256, 0, s, dprods, rowprod, grp, prod, M, ba, bin, &sm_num->tally, ps);
+        kl(k_bin_offsets, 1, 32, 0, s, sm_num->tally.counts, sm_num->offsets, sm_num->cursors);
+        kl(k_bin_fill, g, 256, 0, s, bin, M, sm_num->offsets, sm_num->cursors, list);
+        if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
+            !cuda_ok(cudaStreamSynchronize(s), "sync"))
+            return fail(MP_ERR_CUDA);
+        pa.counts = sm_num->tally.counts;
+        pa.offsets = sm_num->offsets;
+        run_pass(1, pa, h_num.tally.counts, dense_cols, tun, s, prof);
+        if (gl.R) glob_pass(1, gl, pa, tun, s, prof);
+        if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
+            !cuda_ok(cudaStreamSynchronize(s), "sync"))
+            return fail(MP_ERR_CUDA);
+        prof_collect(prof, 1, h_num.tally);
+    }
+    if (!cuda_ok(cudaGetLastError(), "launch")) return fail(MP_ERR_CUDA);
+    for (int p = 0; p < w; p++) {
+        WaveOut &o = out[p];
+        for (int b = 0; b < NBINS; b++) o.num_bins[b] = hps[p].num_bins[b];
+        if (!o.status && hps[p].err) o.status = (hps[p].err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+        if (o.status) {
+            if (hp[p].rp) al.free(hp[p].rp, s);
+            if (hp[p].ci) al.free(hp[p].ci, s);
+            if (hp[p].val) al.free(hp[p].val, s);
+            continue;
+        }
+        o.m.nrows = in[p].X.nrows;
+        o.m.ncols = in[p].Y.ncols;
+        o.m.nnz = in[p].X.nrows ? hps[p].nnz : 0;
+        o.m.rp = hp[p].rp;
+        o.m.ci = hp[p].ci;
+        o.m.val = hp[p].val;
+    }
+    glob_release(gl, al, s);
+    al.free(ws, s);
+    return rc;
+}
+
+}  // namespace mp
