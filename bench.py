@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="scholarly", choices=["scholarly"])
+    ap.add_argument("--workload", default="scholarly", choices=["scholarly", "serving"])
+    ap.add_argument("--serve-queries", type=int, default=4000)
+    ap.add_argument("--load", type=float, default=1.0, help="arrival rate / plain-path saturation rate")
+    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=5)
@@ -179,7 +182,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("spgemm.cu", "internal.h"):
+    for f in ("wave.cu", "common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2201_04058_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -188,7 +191,7 @@ def kernel_source_hash():
 def ncu_traffic(kernel_name):
     """DRAM bytes per launch of the kernel from the committed ncu summary, or None when
     the summary is absent or the kernel source changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     try:
         with open(p) as f:
             d = json.load(f)
@@ -321,8 +324,47 @@ def run_engine(args, ws, rank, local):
         torch.cuda.synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, ws, dev)
 
+        # batched form: the same queries as one workload per step (identical sub-chains run
+        # once, every ready product of a plan level in one wave), cache off
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for _ in range(2):
+            rc, tks = mp.mp_submit_batch(eng.ctx, bufs)
+            for t in tks:
+                mp.mp_release(eng.ctx, t)
+        torch.cuda.synchronize()
+        bprod = 0
+        for k in range(args.steps):
+            flush.zero_()
+            bev[k][0].record(stream)
+            rc, tks = mp.mp_submit_batch(eng.ctx, bufs)
+            if rc != mp.MP_OK:
+                raise mp.MPError(rc, "batch")
+            for t in tks:
+                bprod += mp.mp_result_stats(eng.ctx, t)["n_products"]
+                mp.mp_release(eng.ctx, t)
+            bev[k][1].record(stream)
+        torch.cuda.synchronize()
+        bstep_ms = [a.elapsed_time(b) for a, b in bev]
+        btotal_s = reduce_max(sum(bstep_ms) / 1e3, ws, dev)
+
     n_q = len(qs)
     value = ws * n_q * args.steps / total_s
+    # with all of a step's queries arriving together, a query's latency in the plain form
+    # is the time until its own result (the queries before it run first); in the batched
+    # form every query completes with the batch
+    plain_arrival_lat = []
+    for k in range(args.steps):
+        acc = 0.0
+        for x in lat[k * n_q:(k + 1) * n_q]:
+            acc += x
+            plain_arrival_lat.append(acc)
+    batched = {"value": ws * n_q * args.steps / btotal_s, "unit": UNIT, "ms_per_step": 1e3 * btotal_s / args.steps,
+               "speedup_vs_plain": total_s / btotal_s, "products_per_step": bprod / args.steps,
+               "latency_p50_ms": float(np.percentile(bstep_ms, 50)), "latency_p99_ms": float(np.percentile(bstep_ms, 99)),
+               "plain_latency_same_arrivals_p50_ms": float(np.percentile(plain_arrival_lat, 50)),
+               "plain_latency_same_arrivals_p99_ms": float(np.percentile(plain_arrival_lat, 99)),
+               "form": "mp_submit_batch of the step's queries: shared sub-chains once, one wave per plan level"}
     peak, peak_kind = measured_peak()
     dom = max(kstats.items(), key=lambda kv: kv[1]["ms"]) if kstats else None
     roofline = None
@@ -343,7 +385,7 @@ def run_engine(args, ws, rank, local):
            "e2e": {"value": ws * n_q * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": sum(query_bytes(q) for q in qs),
                    "d2h_bytes_per_step": d2h[0] // e2e_steps},
-           "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
+           "batched": batched, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in kstats.items()}}
     if rank == 0 and not args.no_cpu_baseline:
@@ -353,11 +395,91 @@ def run_engine(args, ws, rank, local):
     eng.close()
 
 
+# ---------------------------------------------------------------- serving leg
+
+def run_serving(args, ws, rank, local):
+    """News-shaped HIN and a session query stream (Sec. 4.1.2) arriving as a Poisson
+    process; the serving loop (continuous batching, Overlap-Tree cache under the HBM
+    budget) against the plain one-query-at-a-time chain under the same arrivals."""
+    import torch
+    import gen
+    from paper_2201_04058_b300 import mp
+
+    torch.cuda.set_device(local)
+    hin = gen.config4_hin(seed=4, scale=args.scale)
+    qs, _ = gen.serving_stream(hin, seed=4, n=args.serve_queries)
+    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE)
+    bufs = [plain.query(q) for q in qs]
+    # saturation rate of the plain path: one query at a time, back to back
+    for b in bufs[:20]:
+        _, t = mp.mp_submit(plain.ctx, b)
+        mp.mp_release(plain.ctx, t)
+    n_sat = min(len(bufs), 400)
+    t0 = time.perf_counter()
+    for b in bufs[:n_sat]:
+        _, t = mp.mp_submit(plain.ctx, b)
+        mp.mp_release(plain.ctx, t)
+    sat = n_sat / (time.perf_counter() - t0)
+    rate = args.load * sat
+    arrivals = np.cumsum(gen.stream(4, 950).exponential(1.0 / rate, len(qs)))
+
+    def serve(eng):
+        qb = [eng.query(q) for q in qs]
+        mp.mp_serve_start(eng.ctx)
+        tickets = []
+        start = time.perf_counter()
+        for b, at in zip(qb, arrivals):
+            d = start + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            _, t = mp.mp_submit(eng.ctx, b)
+            tickets.append(t)
+        lat = []
+        for t in tickets:
+            st = mp.mp_wait(eng.ctx, t)
+            if st != mp.MP_OK:
+                raise mp.MPError(st, "served query")
+            lat.append(mp.mp_result_latency(eng.ctx, t))
+        end = time.perf_counter()
+        stats = mp.mp_serve_stats(eng.ctx)
+        for t in tickets:
+            mp.mp_release(eng.ctx, t)
+        mp.mp_serve_stop(eng.ctx)
+        return len(qs) / (end - start), lat, stats
+
+    plain_served = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, max_slots=1)
+    p_qps, p_lat, p_stats = serve(plain_served)
+    plain_served.close()
+    budget = int(args.serve_budget_gb * (1 << 30))
+    served = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, max_slots=64, hbm_budget_bytes=budget)
+    s_qps, s_lat, s_stats = serve(served)
+    cstats = mp.mp_cache_stats(served.ctx)
+    served.close()
+    plain.close()
+    out = {"metric": METRIC, "value": s_qps, "unit": UNIT, "n_gpus": 1, "steps": len(qs), "warmup": 20,
+           "ms_per_step": 1e3 / s_qps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
+           "config": {"workload": "serving: news HIN, session query stream, Poisson arrivals",
+                      "articles": hin["types"]["R"], "persons": hin["types"]["E"], "orgs": hin["types"]["O"],
+                      "locations": hin["types"]["L"], "themes": hin["types"]["H"], "queries": len(qs),
+                      "arrival_rate_qps": rate, "load_vs_plain_saturation": args.load,
+                      "cache": f"ATRAPOS-OTree, {args.serve_budget_gb:g} GB", "max_slots": 64},
+           "p50_ms": float(np.percentile(s_lat, 50)), "p99_ms": float(np.percentile(s_lat, 99)),
+           "served": {"qps": s_qps, "batches": s_stats["batches"], "cache": cstats},
+           "plain": {"saturation_qps": sat, "qps_under_same_arrivals": p_qps,
+                     "p50_ms": float(np.percentile(p_lat, 50)), "p99_ms": float(np.percentile(p_lat, 99))}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args, ws, rank, local)
         return
     run_engine(args, ws, rank, local)
     if ws > 1:

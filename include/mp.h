@@ -156,10 +156,29 @@ int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket);
  * else the first failing query's error (each ticket keeps its own status). */
 int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ticket *tickets);
 
-/* Wait for a ticket's result: MP_OK, the query's own error, or MP_ERR_TIMEOUT. */
+/* Wait for a ticket's result: MP_OK, the query's own error, or MP_ERR_TIMEOUT when it is
+ * not finished within timeout_ms (UINT32_MAX = no limit, 0 = poll). */
 int mp_wait(mp_ctx *ctx, mp_ticket ticket, uint32_t timeout_ms);
 
-/* Shape of a finished result. Any output pointer may be NULL. */
+/* ---- serving (Problem 2 as a live request stream)
+ *
+ * mp_serve_start starts a host thread that serves the workload as it arrives: each round
+ * it takes every submitted query that is waiting (up to mp_config.max_slots) and runs
+ * them as one batch -- one product DAG, shared sub-chains once, one wave per plan level,
+ * the cache (Sec. 3.4) under the HBM byte budget -- while queries that arrive during the
+ * round wait for the next one (continuous batching). While serving, mp_submit and
+ * mp_submit_batch only queue the queries and return tickets at once; results are read
+ * after mp_wait. mp_serve_stop finishes the queued work and stops the thread
+ * (mp_destroy stops it too). Errors: MP_ERR_STATE (not finalised, already serving). */
+int mp_serve_start(mp_ctx *ctx);
+int mp_serve_stop(mp_ctx *ctx);
+/* Rounds run and queries served so far, and queries waiting now. */
+int mp_serve_stats(mp_ctx *ctx, uint64_t *batches, uint64_t *queries, uint64_t *queued);
+/* Host wall time in ms from a ticket's submission to its completion (MP_ERR_STATE while
+ * it is still pending). */
+int mp_result_latency(mp_ctx *ctx, mp_ticket ticket, double *ms);
+
+/* Shape of a finished result (MP_ERR_STATE while pending). Any output pointer may be NULL. */
 int mp_result_info(mp_ctx *ctx, mp_ticket ticket, uint32_t *rows, uint32_t *cols, uint64_t *nnz);
 
 /* Copy a result into caller-owned buffers: row_ptr (rows+1), col (nnz), val (nnz).

@@ -115,6 +115,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     ctx->tun.sm_count = sms;
     ctx->tun.force_class = c.force_bin_class;
     if (c.scratch_bytes) ctx->tun.scratch_cap = c.scratch_bytes;
+    if (check_cuda(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "stream")) return MP_ERR_CUDA;
     ctx->alloc.reset(new PoolAlloc());
     if (c.policy != MP_POLICY_NONE) ctx->cache.reset(new CachePolicy((double)c.hbm_budget_bytes, c.policy));
     cudaEventCreate(&ctx->ev0);
@@ -126,8 +127,10 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
 
 extern "C" void mp_destroy(mp_ctx *ctx) {
     if (!ctx) return;
+    mp_serve_stop(ctx);
     cudaSetDevice(ctx->cfg.device);
     {
+        std::lock_guard<std::mutex> ge(ctx->exec_mu);
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->cache_clear();
         ctx->results.clear();
@@ -139,6 +142,7 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         cudaEventDestroy(ctx->ev1);
         ctx->prof.destroy();
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     }
     delete ctx;
 }
@@ -388,46 +392,163 @@ int mp_ctx::parse(const mp_query *q, Query &out) {
     return MP_OK;
 }
 
-extern "C" int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket) {
-    if (!ctx || !ticket) return MP_ERR_ARG;
-    std::lock_guard<std::mutex> g(ctx->mu);
-    if (!ctx->finalized) return MP_ERR_STATE;
-    cudaSetDevice(ctx->cfg.device);
-    Query qq;
-    int rc = ctx->parse(q, qq);
-    if (rc) return rc;
-    std::vector<Query> qs(1);
-    qs[0] = std::move(qq);
-    std::vector<Result> res(1);
-    rc = ctx->run_batch(qs, res);
-    *ticket = ctx->next_ticket++;
-    ctx->results.emplace(*ticket, std::move(res[0]));
-    return rc;
+// Queue parsed queries for the serving loop; tickets come back at once.
+static int enqueue(mp_ctx *ctx, std::vector<Query> &qs, mp_ticket *tickets) {
+    const auto now = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (size_t i = 0; i < qs.size(); i++) {
+            tickets[i] = ctx->next_ticket++;
+            Result r;
+            r.done = false;
+            ctx->results.emplace(tickets[i], std::move(r));
+        }
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->qmu);
+        for (size_t i = 0; i < qs.size(); i++) ctx->queue.push_back({tickets[i], std::move(qs[i]), now});
+    }
+    ctx->qcv.notify_one();
+    return MP_OK;
 }
 
-extern "C" int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ticket *tickets) {
-    if (!ctx || (n && (!q || !tickets))) return MP_ERR_ARG;
-    std::lock_guard<std::mutex> g(ctx->mu);
-    if (!ctx->finalized) return MP_ERR_STATE;
-    cudaSetDevice(ctx->cfg.device);
-    std::vector<Query> qs(n);
-    for (uint32_t i = 0; i < n; i++) {
-        int rc = ctx->parse(&q[i], qs[i]);
-        if (rc) return rc;
+// Run parsed queries now, on the caller's thread.
+static int run_now(mp_ctx *ctx, std::vector<Query> &qs, mp_ticket *tickets) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<Result> res(qs.size());
+    int first;
+    {
+        std::lock_guard<std::mutex> ge(ctx->exec_mu);
+        cudaSetDevice(ctx->cfg.device);
+        first = ctx->run_batch(qs, res);
     }
-    std::vector<Result> res(n);
-    int first = ctx->run_batch(qs, res);
-    for (uint32_t i = 0; i < n; i++) {
+    const double lat = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (size_t i = 0; i < qs.size(); i++) {
         tickets[i] = ctx->next_ticket++;
+        res[i].latency_ms = lat;
         ctx->results.emplace(tickets[i], std::move(res[i]));
     }
     return first;
 }
 
-extern "C" int mp_wait(mp_ctx *ctx, mp_ticket t, uint32_t timeout_ms) {
-    (void)timeout_ms;
+extern "C" int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket) {
+    return mp_submit_batch(ctx, 1, q, ticket);
+}
+
+extern "C" int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ticket *tickets) {
+    if (!ctx || (n && (!q || !tickets))) return MP_ERR_ARG;
+    if (!ctx->finalized) return MP_ERR_STATE;
+    std::vector<Query> qs(n);
+    for (uint32_t i = 0; i < n; i++) {
+        int rc = ctx->parse(&q[i], qs[i]);
+        if (rc) return rc;
+    }
+    bool serving;
+    {
+        std::lock_guard<std::mutex> g(ctx->qmu);
+        serving = ctx->serving;
+    }
+    return serving ? enqueue(ctx, qs, tickets) : run_now(ctx, qs, tickets);
+}
+
+// The serving loop: take every query that has arrived (up to max_slots) as one batch,
+// run it as one product DAG, publish the results; queries that arrive meanwhile wait for
+// the next round (continuous batching).
+void mp_ctx::serve_loop() {
+    cudaSetDevice(cfg.device);
+    for (;;) {
+        std::vector<Pending> batch;
+        {
+            std::unique_lock<std::mutex> lk(qmu);
+            qcv.wait(lk, [&] { return stop_req || !queue.empty(); });
+            if (queue.empty() && stop_req) break;
+            const size_t slots = cfg.max_slots ? cfg.max_slots : 1;
+            while (!queue.empty() && batch.size() < slots) {
+                batch.push_back(std::move(queue.front()));
+                queue.pop_front();
+            }
+        }
+        std::vector<Query> qs(batch.size());
+        for (size_t i = 0; i < batch.size(); i++) qs[i] = std::move(batch[i].q);
+        std::vector<Result> res(batch.size());
+        {
+            std::lock_guard<std::mutex> ge(exec_mu);
+            run_batch(qs, res);
+            batches++;
+            batched_queries += batch.size();
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> g(mu);
+            for (size_t i = 0; i < batch.size(); i++) {
+                auto it = results.find(batch[i].ticket);
+                if (it == results.end()) continue;  // released before it finished
+                res[i].latency_ms = std::chrono::duration<double, std::milli>(t1 - batch[i].t0).count();
+                res[i].done = true;
+                it->second = std::move(res[i]);
+            }
+        }
+        done_cv.notify_all();
+    }
+}
+
+extern "C" int mp_serve_start(mp_ctx *ctx) {
     if (!ctx) return MP_ERR_ARG;
+    if (!ctx->finalized) return MP_ERR_STATE;
+    std::lock_guard<std::mutex> g(ctx->qmu);
+    if (ctx->serving) return MP_ERR_STATE;
+    ctx->stop_req = false;
+    ctx->serving = true;
+    ctx->server = std::thread([ctx] { ctx->serve_loop(); });
+    return MP_OK;
+}
+
+extern "C" int mp_serve_stop(mp_ctx *ctx) {
+    if (!ctx) return MP_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> g(ctx->qmu);
+        if (!ctx->serving) return MP_OK;
+        ctx->stop_req = true;
+    }
+    ctx->qcv.notify_all();
+    if (ctx->server.joinable()) ctx->server.join();
+    std::lock_guard<std::mutex> g(ctx->qmu);
+    ctx->serving = false;
+    return MP_OK;
+}
+
+extern "C" int mp_serve_stats(mp_ctx *ctx, uint64_t *batches, uint64_t *queries, uint64_t *queued) {
+    if (!ctx) return MP_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> ge(ctx->exec_mu);
+        if (batches) *batches = ctx->batches;
+        if (queries) *queries = ctx->batched_queries;
+    }
+    std::lock_guard<std::mutex> g(ctx->qmu);
+    if (queued) *queued = ctx->queue.size();
+    return MP_OK;
+}
+
+extern "C" int mp_result_latency(mp_ctx *ctx, mp_ticket t, double *ms) {
+    if (!ctx || !ms) return MP_ERR_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (!it->second.done) return MP_ERR_STATE;
+    *ms = it->second.latency_ms;
+    return MP_OK;
+}
+
+extern "C" int mp_wait(mp_ctx *ctx, mp_ticket t, uint32_t timeout_ms) {
+    if (!ctx) return MP_ERR_ARG;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto ready = [&] {
+        auto it = ctx->results.find(t);
+        return it == ctx->results.end() || it->second.done;
+    };
+    if (timeout_ms == UINT32_MAX) ctx->done_cv.wait(lk, ready);
+    else if (!ctx->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return MP_ERR_TIMEOUT;
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
     return it->second.status;
@@ -438,6 +559,7 @@ extern "C" int mp_result_info(mp_ctx *ctx, mp_ticket t, uint32_t *rows, uint32_t
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (!it->second.done) return MP_ERR_STATE;
     if (it->second.status) return it->second.status;
     const Mat &m = it->second.m->m;
     if (rows) *rows = (uint32_t)m.nrows;
@@ -452,11 +574,12 @@ extern "C" int mp_result_copy(mp_ctx *ctx, mp_ticket t, int64_t *row_ptr, int32_
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (!it->second.done) return MP_ERR_STATE;
     if (it->second.status) return it->second.status;
     cudaSetDevice(ctx->cfg.device);
     const Mat &m = it->second.m->m;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = ctx->copy_stream;
     if (row_ptr && check_cuda(cudaMemcpyAsync(row_ptr, m.rp, (size_t)(m.nrows + 1) * 8, k, s), "copy"))
         return MP_ERR_CUDA;
     if (m.nnz && col && check_cuda(cudaMemcpyAsync(col, m.ci, (size_t)m.nnz * 4, k, s), "copy"))
@@ -520,7 +643,7 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
     if (!ctx) return MP_ERR_ARG;
     static const char *bins[NBINS] = {"w32", "w64", "w128", "w256", "w512", "w1024",
                                       "k2048", "k4096", "k8192", "dense", "global"};
-    std::lock_guard<std::mutex> g(ctx->mu);
+    std::lock_guard<std::mutex> g(ctx->exec_mu);
     uint32_t w = 0;
     for (int p = 0; p < 2; p++)
         for (int b = 0; b < NBINS; b++) {
@@ -542,7 +665,7 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
 extern "C" int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *inserts,
                               uint64_t *rejected, uint64_t *evictions, uint64_t *bytes, uint64_t *entries) {
     if (!ctx) return MP_ERR_ARG;
-    std::lock_guard<std::mutex> g(ctx->mu);
+    std::lock_guard<std::mutex> g(ctx->exec_mu);
     if (!ctx->cache) return MP_ERR_STATE;
     const auto &c = ctx->cstats;
     if (requests) *requests = c.requests;
@@ -557,7 +680,7 @@ extern "C" int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, u
 
 extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
     if (!ctx) return MP_ERR_ARG;
-    std::lock_guard<std::mutex> g(ctx->mu);
+    std::lock_guard<std::mutex> g(ctx->exec_mu);
     for (int p = 0; p < 2; p++)
         for (int b = 0; b < NBINS; b++) ctx->prof.k[p][b] = KStat{};
     return MP_OK;

@@ -2,8 +2,13 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -55,8 +60,10 @@ struct mp_ctx {
     };
     struct Result {
         int status = 0;
+        bool done = true;         // false while queued or running in the serving loop
         MatPtr m;
         double ms = 0.0;
+        double latency_ms = 0.0;  // submission to completion, host wall clock
         mp::Stats st;
         uint32_t n_products = 0;
         uint32_t cache_hits = 0;
@@ -67,8 +74,24 @@ struct mp_ctx {
 
     mp_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // result copies, so they never wait behind a batch
     bool own_stream = false;
-    std::mutex mu;
+    std::mutex mu;       // tickets and results
+    std::mutex exec_mu;  // the executor and its state (masks, DAG, Overlap Tree, cache, pool)
+    // serving loop (continuous batching)
+    struct Pending {
+        uint64_t ticket;
+        Query q;
+        std::chrono::steady_clock::time_point t0;
+    };
+    std::mutex qmu;
+    std::condition_variable qcv;       // with qmu: work arrived or stop requested
+    std::condition_variable done_cv;   // with mu: a ticket finished
+    std::deque<Pending> queue;
+    std::thread server;
+    bool serving = false, stop_req = false;
+    uint64_t batches = 0, batched_queries = 0;
+    void serve_loop();
     std::vector<NodeType> types;
     std::vector<Prop> props;
     std::vector<Rel> rels;

@@ -121,11 +121,15 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         }
         uint64_t s = 0;
         const bool mine = e - b <= 16;
-        if (mine)
+        if (mine && e > b) {
+            const int32_t *__restrict__ xci = P->X.ci;
+            const int64_t *__restrict__ yrp = P->Y.rp;
+            const uint32_t *__restrict__ km = P->km;
             for (int64_t p = b; p < e; p++) {
-                const int32_t k = __ldg(P->X.ci + p);
-                if (bit_of(P->km, (uint32_t)k)) s += (uint64_t)(__ldg(P->Y.rp + k + 1) - __ldg(P->Y.rp + k));
+                const int32_t k = __ldg(xci + p);
+                if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(yrp + k + 1) - __ldg(yrp + k));
             }
+        }
         if (e - b > LONGX) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)g;
         unsigned coop = __ballot_sync(FULL, !mine && e - b <= LONGX);
         while (coop) {
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(W * 32) k_sym_warp(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         for (int s = lane; s < T; s += 32) keys[s] = EMPTY;
         __syncwarp();
         int c = 0;
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(W * 32) k_num_warp(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         uint32_t *err = R.err(a);
         for (int s = lane; s < T; s += 32) {
             keys[s] = EMPTY;
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(NT) k_sym_block(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         uint32_t *err = R.err(a);
         for (int s = threadIdx.x; s < T; s += NT) keys[s] = EMPTY;
         if (threadIdx.x == 0) cnt_s = 0;
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_num_block(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         uint32_t *err = R.err(a);
         for (int s = threadIdx.x; s < T; s += NT) {
             keys[s] = EMPTY;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(NT) k_sym_dense(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         uint32_t *err = R.err(a);
         const int nw = (int)((P.Y.ncols + 31) >> 5);
         for (int s = threadIdx.x; s < nw; s += NT) bm[s] = 0;
@@ -571,7 +575,7 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
     for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
         const RowRef R(a, a.list[base + r]);
-        const Prod &P = *R.P;
+        const Prod P = *R.P;
         uint32_t *err = R.err(a);
         const int ncols = (int)P.Y.ncols;
         const int per = (ncols + NT - 1) / NT;
@@ -657,7 +661,7 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
             if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
         }
         const RowRef Rf(a, list[lo]);
-        const Prod &P = *Rf.P;
+        const Prod P = *Rf.P;
         const int64_t p = P.X.rp[Rf.i] + (e - xbase[lo]);
         const int32_t k = __ldg(P.X.ci + p);
         xoff[e] = bit_of(P.km, (uint32_t)k) ? __ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k) : 0;
@@ -668,7 +672,7 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // them are staged GNT at a time with their product offsets (from xoff); consecutive
 // threads take consecutive products, so a long Y row is read coalesced.
 template <bool NUM>
-__global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
+__global__ void __launch_bounds__(GNT, NUM ? 5 : 8) k_glob_set(PassArgs a, GlobArgs g) {
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
@@ -680,14 +684,23 @@ __global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
             if (g.item_off[mid] <= t) lo = mid; else hi = mid - 1;
         }
         const int64_t r = lo;
-        const RowRef Rf(a, g.list[r]);
-        const Prod &P = *Rf.P;
-        if (NUM && !P.val) continue;  // the product failed before its numeric pass
-        uint32_t *err = Rf.err(a);
-        const int64_t xb = P.X.rp[Rf.i], xe = P.X.rp[Rf.i + 1];
+        const uint32_t gr = g.list[r];
+        const int pi = a.rowprod[gr];
+        const Prod *PP = a.prods + pi;
+        uint64_t *const pval = PP->val;
+        if (NUM && !pval) continue;  // the product failed before its numeric pass
+        uint32_t *err = &a.ps[pi].err;
+        const int64_t row = (int64_t)gr - PP->row0;
+        const int32_t *__restrict__ xci = PP->X.ci;
+        const uint64_t *__restrict__ xval = PP->X.val;
+        const int64_t *__restrict__ yrp = PP->Y.rp;
+        const int32_t *__restrict__ yci = PP->Y.ci;
+        const uint64_t *__restrict__ yval = PP->Y.val;
+        const uint32_t *__restrict__ cm = PP->cm;
+        const int64_t xb = PP->X.rp[row], xe = PP->X.rp[row + 1];
         const int64_t *xo = g.xoff + g.xbase[r];
         // product offsets are global across the GLOBAL rows: this row's start at xo[0]
-        const int64_t total = __ldg(xo) + (int64_t)g.prod[Rf.g];
+        const int64_t total = __ldg(xo) + (int64_t)g.prod[gr];
         const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
         const int64_t s1 = min(total, s0 + PCH);
         // first X entry whose products reach s0: the last p with xo[p] <= s0
@@ -698,41 +711,53 @@ __global__ void __launch_bounds__(GNT) k_glob_set(PassArgs a, GlobArgs g) {
         }
         uint32_t *bm = g.bm + (r - g.r0) * g.nw;
         const uint32_t *rk = g.rank + (r - g.r0) * g.nw;
-        unsigned long long *val = NUM ? (unsigned long long *)P.val + Rf.out_off(a) : nullptr;
+        unsigned long long *val = NUM ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0]) : nullptr;
         for (int64_t c0 = xb + plo; c0 < xe; c0 += GNT) {
             const int64_t base = __ldg(xo + (c0 - xb));
             if (base >= s1) break;  // uniform: every thread reads the same base
             const int64_t p = c0 + threadIdx.x;
             const int nent = (int)min((int64_t)GNT, xe - c0);
             if (threadIdx.x < nent) {
-                const int32_t k = __ldg(P.X.ci + p);
+                const int32_t k = __ldg(xci + p);
                 s_off[threadIdx.x] = __ldg(xo + (p - xb)) - base;
-                s_st[threadIdx.x] = __ldg(P.Y.rp + k);
-                s_a[threadIdx.x] = (NUM && P.X.val) ? __ldg(P.X.val + p) : 1ull;
+                s_st[threadIdx.x] = __ldg(yrp + k);
+                s_a[threadIdx.x] = (NUM && xval) ? __ldg(xval + p) : 1ull;
             }
             if (threadIdx.x == 0) s_off[nent] = (c0 + nent < xe ? __ldg(xo + (c0 + nent - xb)) : total) - base;
             __syncthreads();
+            // this chunk's products [f0, f1): thread t takes a contiguous run of them, finds
+            // the X entry holding its first product once, then walks forward
             const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
-            for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
+            const int64_t run = (f1 - f0 + GNT - 1) / GNT;
+            int64_t f = f0 + (int64_t)threadIdx.x * run;
+            const int64_t fend = min(f1, f + run);
+            if (f < fend) {
                 int l = 0, h = nent - 1;
                 while (l < h) {
                     const int mid = (l + h + 1) >> 1;
                     if (s_off[mid] <= f) l = mid; else h = mid - 1;
                 }
-                const int64_t q = s_st[l] + (f - s_off[l]);
-                const uint32_t j = (uint32_t)__ldg(P.Y.ci + q);
-                if (!bit_of(P.cm, j)) continue;
-                if (!NUM) {
-                    atomicOr(bm + (j >> 5), 1u << (j & 31));
-                } else {
+                while (f < fend) {
+                    const int64_t seg_end = min(fend, s_off[l + 1]);
+                    const int64_t qb = s_st[l] - s_off[l];
                     const uint64_t av = s_a[l];
-                    const uint64_t bv = P.Y.val ? __ldg(P.Y.val + q) : 1ull;
-                    const uint64_t v = av * bv;
-                    if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
-                    const uint32_t w = j >> 5;
-                    const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
-                    const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
-                    if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                    for (; f < seg_end; f++) {
+                        const int64_t q = qb + f;
+                        const uint32_t j = (uint32_t)__ldg(yci + q);
+                        if (!bit_of(cm, j)) continue;
+                        if (!NUM) {
+                            atomicOr(bm + (j >> 5), 1u << (j & 31));
+                        } else {
+                            const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
+                            const uint64_t v = av * bv;
+                            if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+                            const uint32_t w = j >> 5;
+                            const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
+                            const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v);
+                            if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                        }
+                    }
+                    l++;
                 }
             }
             __syncthreads();
@@ -781,7 +806,7 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
         if (!word) continue;
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const RowRef Rf(a, g.list[g.r0 + slot]);
-        const Prod &P = *Rf.P;
+        const Prod P = *Rf.P;
         if (!P.ci) continue;
         int64_t pos = Rf.out_off(a) + g.rank[x];
         while (word) {

@@ -31,6 +31,7 @@ EXPORTS = [
     "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats",
+    "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency",
 ]
 
 
@@ -96,6 +97,10 @@ def lib():
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
+            "mp_serve_start": (C.c_int, [C.c_void_p]),
+            "mp_serve_stop": (C.c_int, [C.c_void_p]),
+            "mp_serve_stats": (C.c_int, [C.c_void_p, P(U64), P(U64), P(U64)]),
+            "mp_result_latency": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
             "mp_otree_create": (C.c_int, [P(C.c_void_p)]),
             "mp_otree_destroy": (None, [C.c_void_p]),
             "mp_otree_insert": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_void_p]),
@@ -239,8 +244,28 @@ def mp_submit_batch(ctx, queries) -> tuple[int, list[int]]:
     return rc, [int(tk[i]) for i in range(n)]
 
 
-def mp_wait(ctx, ticket: int, timeout_ms: int = 0) -> int:
+def mp_wait(ctx, ticket: int, timeout_ms: int = 0xFFFFFFFF) -> int:
     return lib().mp_wait(ctx, ticket, timeout_ms)
+
+
+def mp_serve_start(ctx):
+    _ck(lib().mp_serve_start(ctx), "mp_serve_start")
+
+
+def mp_serve_stop(ctx):
+    _ck(lib().mp_serve_stop(ctx), "mp_serve_stop")
+
+
+def mp_serve_stats(ctx):
+    b, q, w = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _ck(lib().mp_serve_stats(ctx, C.byref(b), C.byref(q), C.byref(w)), "mp_serve_stats")
+    return {"batches": b.value, "queries": q.value, "queued": w.value}
+
+
+def mp_result_latency(ctx, ticket: int) -> float:
+    ms = C.c_double()
+    _ck(lib().mp_result_latency(ctx, ticket, C.byref(ms)), "mp_result_latency")
+    return ms.value
 
 
 def mp_result_info(ctx, ticket: int):
