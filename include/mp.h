@@ -262,6 +262,42 @@ int mp_cachesim_evicted(mp_cachesim *c, uint32_t i, char *buf, uint32_t cap, uin
 /* Inflation value L, bytes used and items held. */
 int mp_cachesim_state(mp_cachesim *c, double *L, double *used, uint32_t *items);
 
+/* ---- one product row without device allocation
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need a result row -- a serving process whose free device
+ * memory is already handed to its own pool, a latency-critical loop that cannot take the
+ * device synchronisation cudaMalloc/cudaFree may cause, or a runtime that only allows
+ * allocation at set-up. It computes one row
+ *     c = (x restricted to the nodes in km) * Y * diag(cm)
+ * with exact uint64 counts, columns ascending, into buffers the caller owns, and calls no
+ * cudaMalloc, cudaFree or allocating library routine. Its working memory is a fixed
+ * scratch array compiled into the library (a bitmap and a rank word per 32 columns for
+ * up to 16,777,216 output columns, 4 MiB), which every GPU that loads the library holds
+ * until the process exits.
+ *
+ *   device, cuda_stream  GPU ordinal and the cudaStream_t to run on (NULL = default).
+ *   x_len, x_ci, x_val    the row x: x_len column ids (int32, device) and uint64 values
+ *                         (device, or NULL for all ones).
+ *   y_rp, y_ci, y_val     Y in CSR on the device: int64 row pointers, int32 column ids,
+ *                         uint64 values or NULL (all ones). y_cols = Y's column count.
+ *   km, cm                device bitmaps (bit j of word j/32) over Y's rows and columns,
+ *                         or NULL for no mask.
+ *   out_cap, out_ci, out_val  caller's device buffers for up to out_cap entries.
+ *   out_nnz               host: the row's number of entries.
+ * Returns MP_OK; MP_ERR_TOO_LARGE when y_cols exceeds 16,777,216 (nothing runs) or the
+ * row has more than out_cap entries (*out_nnz then holds the size needed and the output
+ * buffers are untouched); MP_ERR_OVERFLOW for a count above 2^64-1; MP_ERR_ARG, MP_ERR_CUDA.
+ * The call is synchronous (it waits for its stream). The first call on a device looks up
+ * the scratch array's device address for that device; make that first call before any
+ * stream capture. All calls share the one scratch array: calls that overlap on the GPU
+ * (other threads or streams) race and must be serialised by the caller. */
+int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_t x_len, const int32_t *x_ci,
+                           const uint64_t *x_val, const int64_t *y_rp, const int32_t *y_ci,
+                           const uint64_t *y_val, uint32_t y_cols, const uint32_t *km,
+                           const uint32_t *cm, uint64_t out_cap, int32_t *out_ci, uint64_t *out_val,
+                           uint64_t *out_nnz);
+
 /* The chain planner alone (host only; Sec. 3.1 Eq. 1 with the Eq. 2 cost and E_ac
  * densities of Sec. 3.2). p factors; factor t is dims[t] x dims[t+1] with nnz[t]
  * non-zeros. known_cost / known_rho (p*p, row-major, NaN = unknown, both NULL = none)

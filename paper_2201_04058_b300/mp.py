@@ -30,7 +30,7 @@ EXPORTS = [
     "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain", "mp_kernel_stats",
     "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
-    "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats",
+    "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency",
 ]
 
@@ -101,6 +101,9 @@ def lib():
             "mp_serve_stop": (C.c_int, [C.c_void_p]),
             "mp_serve_stats": (C.c_int, [C.c_void_p, P(U64), P(U64), P(U64)]),
             "mp_result_latency": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
+            "mp_row_product_noalloc": (C.c_int, [I32, C.c_void_p, U64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p, C.c_void_p, U32, C.c_void_p, C.c_void_p, U64,
+                                                 C.c_void_p, C.c_void_p, P(U64)]),
             "mp_otree_create": (C.c_int, [P(C.c_void_p)]),
             "mp_otree_destroy": (None, [C.c_void_p]),
             "mp_otree_insert": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_void_p]),
@@ -422,6 +425,18 @@ class CacheSim:
 def cache_item_id(types, key):
     """The engine's id string of a cached item (types + constraint key)."""
     return "".join(f"{int(t)}," for t in types) + "#" + key
+
+
+def mp_row_product_noalloc(device, stream, x_len, x_ci, x_val, y_rp, y_ci, y_val, y_cols, km, cm, out_cap,
+                           out_ci, out_val):
+    """One product row into caller-owned device buffers, allocating nothing. Pointer
+    arguments are integer device addresses (0 for NULL). Returns (status, nnz)."""
+    nnz = C.c_uint64()
+    v = lambda x: C.c_void_p(x) if x else None
+    rc = lib().mp_row_product_noalloc(int(device), v(stream), int(x_len), v(x_ci), v(x_val), v(y_rp), v(y_ci),
+                                      v(y_val), int(y_cols), v(km), v(cm), int(out_cap), v(out_ci), v(out_val),
+                                      C.byref(nnz))
+    return rc, nnz.value
 
 
 # ---- convenience wrapper -------------------------------------------------------------
