@@ -59,6 +59,11 @@ extern "C" {
 #define MP_POLICY_LRU 2     /* least recently used */
 #define MP_POLICY_NONE 3    /* no caching */
 
+/* cache insertion policies (Sec. 3.4.1 and the baselines of Sec. 4.1.3) */
+#define MP_INSERT_OTREE 0 /* the whole query + its longest sub-metapath seen at least twice */
+#define MP_INSERT_FINAL 1 /* final query results only (with LRU: the CBS1 baseline) */
+#define MP_INSERT_ALL 2   /* every computed result and intermediate (with LRU: CBS2) */
+
 /* chain-order planners */
 #define MP_PLAN_DP 0            /* Eq. 1 DP with the Eq. 2 cost and E_ac densities */
 #define MP_PLAN_LEFT_TO_RIGHT 1 /* ((A1 A2) A3) ... */
@@ -88,6 +93,7 @@ typedef struct {
     uint64_t scratch_bytes;    /* cap on the global-accumulator scratch (0 = default) */
     uint32_t sample_rows;      /* rows sampled per product by MP_PLAN_DP_SAMPLED */
     uint64_t seed;             /* seed of the sampled-row choice */
+    int32_t insertion;         /* MP_INSERT_* (used when policy != MP_POLICY_NONE) */
 } mp_config;
 
 /* Fill *cfg with defaults: device 0, 8 GiB budget, 64 slots, ATRAPOS policy, DP
@@ -301,12 +307,14 @@ int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_t x_len, co
 /* The chain planner alone (host only; Sec. 3.1 Eq. 1 with the Eq. 2 cost and E_ac
  * densities of Sec. 3.2). p factors; factor t is dims[t] x dims[t+1] with nnz[t]
  * non-zeros. known_cost / known_rho (p*p, row-major, NaN = unknown, both NULL = none)
- * give sub-chains (i, j) whose cost and density are known. split (p*p) receives the
- * chosen split k of every sub-chain (-1 for single factors and known sub-chains);
- * cost (p*p, may be NULL) the optimal costs. Ties keep the smallest k. */
+ * give sub-chains (i, j) whose cost and density are known. rho_fixed (p*p, NaN = none,
+ * or NULL) gives measured result densities (sampled rows) that replace E_ac for those
+ * sub-chains while their cost still follows Eq. 2. split (p*p) receives the chosen split k
+ * of every sub-chain (-1 for single factors and known sub-chains); cost (p*p, may be NULL)
+ * the optimal costs. Ties keep the smallest k. */
 int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, double alpha, double beta,
-                  double gamma, const double *known_cost, const double *known_rho, int32_t *split,
-                  double *cost);
+                  double gamma, const double *known_cost, const double *known_rho, const double *rho_fixed,
+                  int32_t *split, double *cost);
 
 #ifdef __cplusplus
 }

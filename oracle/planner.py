@@ -15,6 +15,10 @@ recorded cost) replace the estimate: a cached result costs its retrieval (0 here
 its exact density; an evicted one costs its recorded recomputation time (end of Sec. 3.2).
 
 Ties go to the smallest split k (the first minimum met when k increases).
+
+Sampled densities (the engine's MP_PLAN_DP_SAMPLED): the exact output size of seeded
+sampled rows of a sub-chain, scaled to all its rows, replaces E_ac for that sub-chain's
+result density; the DP is otherwise unchanged.
 """
 from __future__ import annotations
 
@@ -35,14 +39,18 @@ def sparse_cost(m, n, l, rho_x, rho_y, rho_z, alpha, beta, gamma):
     return alpha * nnz_x + beta * n_op + gamma * nnz_z
 
 
-def chain_dp(dims, leaf_density, product, known=None):
+def chain_dp(dims, leaf_density, product, known=None, rho_fixed=None):
     """Eq. 1. dims[t], dims[t+1] are the sizes of factor t (p = len(dims)-1 factors);
     leaf_density[t] its density; product(m, n, l, rho_x, rho_y) -> (cost, rho_z).
     known maps (i, j) -> (cost, density) for sub-chains whose result is already known.
+    rho_fixed maps (i, j) -> a measured density of that sub-chain's result (for example
+    from sampled rows): the product cost still follows the cost model, but with this
+    density for the result in place of the estimate.
     Returns (C, D, S): cost, density and split matrices (S[i][j] = k, or -1 for leaves and
     known sub-chains)."""
     p = len(dims) - 1
     known = known or {}
+    rho_fixed = rho_fixed or {}
     INF = float("inf")
     C = [[0.0] * p for _ in range(p)]
     D = [[0.0] * p for _ in range(p)]
@@ -57,7 +65,8 @@ def chain_dp(dims, leaf_density, product, known=None):
                 continue
             best, best_k, best_rho = INF, -1, 0.0
             for k in range(i, j):
-                cost, rho = product(dims[i], dims[k + 1], dims[j + 1], D[i][k], D[k + 1][j])
+                cost, rho = product(dims[i], dims[k + 1], dims[j + 1], D[i][k], D[k + 1][j],
+                                    rho_fixed.get((i, j)))
                 total = C[i][k] + C[k + 1][j] + cost
                 if total < best:
                     best, best_k, best_rho = total, k, rho
@@ -65,14 +74,15 @@ def chain_dp(dims, leaf_density, product, known=None):
     return C, D, S
 
 
-def dense_product(m, n, l, rho_x, rho_y):
+def dense_product(m, n, l, rho_x, rho_y, rho_z=None):
     """Sec. 3.1: m*n*l operations; the dense result has density 1."""
     return float(m) * n * l, 1.0
 
 
 def sparse_product(alpha=1.0, beta=1.0, gamma=1.0):
-    def product(m, n, l, rho_x, rho_y):
-        rho_z = eac_density(rho_x, rho_y, n)
+    def product(m, n, l, rho_x, rho_y, rho_z=None):
+        if rho_z is None:
+            rho_z = eac_density(rho_x, rho_y, n)
         return sparse_cost(m, n, l, rho_x, rho_y, rho_z, alpha, beta, gamma), rho_z
 
     return product
@@ -91,12 +101,20 @@ def dense_plan(dims):
     return C[0][-1], plan_tree(S, 0, len(dims) - 2)
 
 
-def sparse_plan(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None):
+def sparse_plan(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None, rho_fixed=None):
     """Plan for factors with sizes dims and nnz counts; returns (cost, tree, C, D, S)."""
     p = len(dims) - 1
     rho = [nnz[t] / (float(dims[t]) * dims[t + 1]) for t in range(p)]
-    C, D, S = chain_dp(dims, rho, sparse_product(alpha, beta, gamma), known)
+    C, D, S = chain_dp(dims, rho, sparse_product(alpha, beta, gamma), known, rho_fixed)
     return C[0][p - 1], plan_tree(S, 0, p - 1), C, D, S
+
+
+def sampled_density(sample_nnz, n_sampled, n_active, n_rows, n_cols):
+    """Density of a product estimated from the exact nnz of n_sampled rows drawn among its
+    n_active non-empty rows (the other rows of its n_rows are empty)."""
+    if n_sampled == 0 or n_rows == 0 or n_cols == 0:
+        return 0.0
+    return (sample_nnz / float(n_sampled)) * n_active / (float(n_rows) * n_cols)
 
 
 def all_trees(i, j):

@@ -79,6 +79,7 @@ extern "C" void mp_config_default(mp_config *c) {
     c->scratch_bytes = 0;
     c->sample_rows = 1024;
     c->seed = 1;
+    c->insertion = MP_INSERT_OTREE;
 }
 
 extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
@@ -87,7 +88,8 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     mp_config c;
     if (cfg) c = *cfg; else mp_config_default(&c);
     if (c.policy < 0 || c.policy > MP_POLICY_NONE || c.planner < 0 || c.planner > MP_PLAN_DP_SAMPLED ||
-        c.force_bin_class < MP_BIN_AUTO || c.force_bin_class > MP_BIN_GLOBAL)
+        c.force_bin_class < MP_BIN_AUTO || c.force_bin_class > MP_BIN_GLOBAL || c.insertion < MP_INSERT_OTREE ||
+        c.insertion > MP_INSERT_ALL)
         return MP_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
@@ -624,15 +626,15 @@ extern "C" int mp_result_stats(mp_ctx *ctx, mp_ticket t, uint64_t *products, uin
 }
 
 extern "C" int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, double alpha, double beta,
-                             double gamma, const double *known_cost, const double *known_rho, int32_t *split,
-                             double *cost) {
+                             double gamma, const double *known_cost, const double *known_rho,
+                             const double *rho_fixed, int32_t *split, double *cost) {
     if (p < 1 || !dims || !nnz || !split) return MP_ERR_ARG;
     if ((known_cost == nullptr) != (known_rho == nullptr)) return MP_ERR_ARG;
     for (uint32_t t = 0; t <= p; t++)
         if (!(dims[t] > 0)) return MP_ERR_ARG;
     std::vector<int> sp((size_t)p * p);
     std::vector<double> c((size_t)p * p), r((size_t)p * p);
-    plan_chain((int)p, dims, nnz, alpha, beta, gamma, known_cost, known_rho, sp.data(), c.data(), r.data());
+    plan_chain((int)p, dims, nnz, alpha, beta, gamma, known_cost, known_rho, rho_fixed, sp.data(), c.data(), r.data());
     for (size_t t = 0; t < sp.size(); t++) split[t] = sp[t];
     if (cost)
         for (size_t t = 0; t < c.size(); t++) cost[t] = c[t];

@@ -111,11 +111,18 @@ struct WaveOut {
     uint32_t sym_bins[NBINS] = {};
     uint32_t num_bins[NBINS] = {};
 };
+// Row sampling for the sampled-density planner: active rows (pass rm, non-empty) of A,
+// and a bitmap of the active rows whose SplitMix64(seed, row) draw is below thr.
+void active_rows(const DCsr &A, const uint32_t *rm, unsigned long long *out, cudaStream_t s);
+void sample_rows(const DCsr &A, const uint32_t *rm, uint64_t seed, uint64_t thr, uint32_t *bm,
+                 unsigned long long *count, cudaStream_t s);
+
 // Run independent products together: one launch per bin and pass for the whole wave.
+// symbolic_only: stop after the symbolic pass; out[p].m holds only nrows, ncols, nnz.
 // Returns MP_OK or a wave-wide error (CUDA, out of memory); per-product errors are in
 // out[p].status.
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
-                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof);
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only = false);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,
@@ -131,8 +138,9 @@ struct PlanNode {
     int k;        // split (-1 for a leaf or a known sub-chain)
 };
 // Fills split[i*p + j]; known_cost / known_rho are p*p arrays, NaN where unknown.
+// rho_fixed (p*p, NaN where none, or nullptr): measured result densities of sub-chains.
 void plan_chain(int p, const double *dims, const double *nnz, double alpha, double beta,
-                double gamma, const double *known_cost, const double *known_rho, int *split,
-                double *cost_out, double *rho_out);
+                double gamma, const double *known_cost, const double *known_rho, const double *rho_fixed,
+                int *split, double *cost_out, double *rho_out);
 
 }  // namespace mp

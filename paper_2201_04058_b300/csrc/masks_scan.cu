@@ -280,4 +280,51 @@ void mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64
     if (n) kl(k_mask_and_in_values, grid_for(n, 256), 256, 0, s, m, prop, n, set, len);
 }
 
+// ------------------------------------------------------------------ row sampling
+
+// SplitMix64 output function (Steele, Lea and Flood, 2014) of the counter seed + (i+1)*phi:
+// the counter-based generator that picks sampled rows.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Rows of A that pass rm and have at least one entry.
+__global__ void k_active_rows(DCsr A, const uint32_t *rm, unsigned long long *out) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.nrows; i += (int64_t)gridDim.x * blockDim.x)
+        c += (bit_of(rm, (uint32_t)i) && A.rp[i + 1] > A.rp[i]) ? 1ull : 0ull;
+    for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// Bitmap of the sampled rows: an active row is sampled when its SplitMix64 draw is below
+// thr (so each active row is kept with probability thr / 2^64); counts the sampled rows.
+__global__ void k_sample_rows(DCsr A, const uint32_t *rm, uint64_t seed, uint64_t thr, uint32_t *bm,
+                              unsigned long long *count) {
+    const int64_t nw = (A.nrows + 31) / 32;
+    for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll; i0 < nw * 32; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + (threadIdx.x & 31) + (threadIdx.x & ~31);
+        bool take = false;
+        if (i < A.nrows && bit_of(rm, (uint32_t)i) && A.rp[i + 1] > A.rp[i]) take = splitmix64(seed, (uint64_t)i) < thr;
+        const unsigned word = __ballot_sync(FULL, take);
+        if ((threadIdx.x & 31) == 0 && i < nw * 32) {
+            bm[i >> 5] = word;
+            if (word) atomicAdd(count, (unsigned long long)__popc(word));
+        }
+    }
+}
+
+void active_rows(const DCsr &A, const uint32_t *rm, unsigned long long *out, cudaStream_t s) {
+    if (A.nrows) kl(k_active_rows, std::min(grid_for(A.nrows, 256), 1184u), 256, 0, s, A, rm, out);
+}
+
+void sample_rows(const DCsr &A, const uint32_t *rm, uint64_t seed, uint64_t thr, uint32_t *bm,
+                 unsigned long long *count, cudaStream_t s) {
+    const int64_t nw = (A.nrows + 31) / 32;
+    if (nw) kl(k_sample_rows, std::min(grid_for(nw * 32, 256), 1184u), 256, 0, s, A, rm, seed, thr, bm, count);
+}
+
 }  // namespace mp

@@ -10,6 +10,8 @@
 // Sub-chains whose result is already known (in the cache, or evicted with a recorded
 // cost) use that cost and exact density instead of the estimate (end of Sec. 3.2).
 // Ties keep the smallest split k. p is at most a few dozen, so O(p^3) is negligible.
+// A measured density of a sub-chain's result (rho_fixed, from sampled rows) replaces E_ac
+// for that sub-chain; its cost still follows Eq. 2.
 #include <cmath>
 #include <limits>
 #include <vector>
@@ -19,8 +21,8 @@
 namespace mp {
 
 void plan_chain(int p, const double *dims, const double *nnz, double alpha, double beta,
-                double gamma, const double *known_cost, const double *known_rho, int *split,
-                double *cost_out, double *rho_out) {
+                double gamma, const double *known_cost, const double *known_rho, const double *rho_fixed,
+                int *split, double *cost_out, double *rho_out) {
     std::vector<double> C((size_t)p * p, 0.0), D((size_t)p * p, 0.0);
     auto at = [p](int i, int j) { return (size_t)i * p + j; };
     for (int i = 0; i < p; i++) {
@@ -42,7 +44,8 @@ void plan_chain(int p, const double *dims, const double *nnz, double alpha, doub
             for (int k = i; k < j; k++) {
                 const double n = dims[k + 1];
                 const double rx = D[at(i, k)], ry = D[at(k + 1, j)];
-                const double rz = 1.0 - std::pow(1.0 - rx * ry, n);
+                const double fixed = rho_fixed ? rho_fixed[at(i, j)] : NAN;
+                const double rz = std::isnan(fixed) ? 1.0 - std::pow(1.0 - rx * ry, n) : fixed;
                 const double nnz_x = m * n * rx;
                 const double n_op = m * n * rx * l * ry;
                 const double nnz_z = m * l * rz;

@@ -178,6 +178,70 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         }
     }
 
+    // sampled densities of every adjacent factor pair (MP_PLAN_DP_SAMPLED): the exact
+    // output size of up to sample_rows seeded rows of the pair's first factor
+    std::vector<std::vector<double>> sampled;
+    if (cfg.planner == MP_PLAN_DP_SAMPLED) {
+        struct Pair { size_t q; int t; };
+        std::vector<Pair> pairs;
+        for (size_t q = 0; q < nq; q++)
+            if (!qstatus[q])
+                for (int t = 0; t + 1 < (int)qs[q].rels.size(); t++) pairs.push_back({q, t});
+        sampled.assign(nq, std::vector<double>());
+        for (size_t q = 0; q < nq; q++) {
+            const size_t p = qs[q].rels.size();
+            sampled[q].assign(p * p, NAN);
+        }
+        if (!pairs.empty()) {
+            const size_t np = pairs.size();
+            unsigned long long *d = (unsigned long long *)alloc->alloc(np * 16, stream);
+            if (!d) return MP_ERR_NOMEM;
+            cudaMemsetAsync(d, 0, np * 16, stream);  // [active rows, sampled rows] per pair
+            for (size_t k = 0; k < np; k++) {
+                const Query &Q = qs[pairs[k].q];
+                active_rows(rels[Q.rels[pairs[k].t]].dev.view(), masks[pairs[k].q][pairs[k].t], d + 2 * k, stream);
+            }
+            std::vector<unsigned long long> h(2 * np);
+            cudaMemcpyAsync(h.data(), d, np * 16, cudaMemcpyDeviceToHost, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+            std::vector<uint32_t *> bms(np, nullptr);
+            std::vector<WaveIn> win(np);
+            const double s_rows = (double)std::max<uint32_t>(cfg.sample_rows, 1);
+            for (size_t k = 0; k < np; k++) {
+                const Query &Q = qs[pairs[k].q];
+                const int t = pairs[k].t;
+                const Mat &A = rels[Q.rels[t]].dev;
+                const double act = (double)h[2 * k];
+                const uint64_t thr = act <= s_rows ? UINT64_MAX : (uint64_t)(s_rows / act * 18446744073709551615.0);
+                bms[k] = (uint32_t *)alloc->alloc((size_t)std::max<int64_t>((A.nrows + 31) / 32, 1) * 4, stream);
+                if (!bms[k]) return MP_ERR_NOMEM;
+                const uint64_t seed = cfg.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(k + 1));
+                sample_rows(A.view(), masks[pairs[k].q][t], seed, thr, bms[k], d + 2 * k + 1, stream);
+                win[k].X = A.view();
+                win[k].Y = rels[Q.rels[t + 1]].dev.view();
+                win[k].rm = bms[k];
+                win[k].km = masks[pairs[k].q][t + 1];
+                win[k].cm = masks[pairs[k].q][t + 2];
+            }
+            std::vector<WaveOut> wout;
+            int rc = spgemm_wave(win, *alloc, tun, stream, 0, wout, nullptr, true);
+            cudaMemcpyAsync(h.data(), d, np * 16, cudaMemcpyDeviceToHost, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess) rc = MP_ERR_CUDA;
+            for (auto *b : bms) alloc->free(b, stream);
+            alloc->free(d, stream);
+            if (rc) return rc;
+            for (size_t k = 0; k < np; k++) {
+                const Query &Q = qs[pairs[k].q];
+                const int t = pairs[k].t;
+                const size_t p = Q.rels.size();
+                const double act = (double)h[2 * k], smp = (double)h[2 * k + 1];
+                const double rows = (double)rels[Q.rels[t]].dev.nrows, cols = (double)rels[Q.rels[t + 1]].dev.ncols;
+                const double dens = smp > 0 ? ((double)wout[k].m.nnz / smp) * act / (rows * cols) : 0.0;
+                if (!wout[k].status) sampled[pairs[k].q][(size_t)t * p + t + 1] = dens;
+            }
+        }
+    }
+
     // Overlap Tree: every query's metapath and suffixes (Sec. 3.3.2)
     if (cache)
         for (size_t q = 0; q < nq; q++)
@@ -239,10 +303,11 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             for (int i = 0; i < p; i++)
                 for (int j = i + 1; j < p; j++) split[(size_t)i * p + j] = split_pure[(size_t)i * p + j] = j - 1;
         } else {
-            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, kc.data(), kr.data(),
+            const double *rf = sampled.empty() ? nullptr : sampled[q].data();
+            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, kc.data(), kr.data(), rf,
                        split.data(), nullptr, D.data());
             // plan of every sub-chain on its own, for known sub-chains that still need computing
-            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr,
+            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr, rf,
                        split_pure.data(), nullptr, nullptr);
         }
         // register nodes bottom-up
@@ -299,8 +364,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     }
 
     // cache candidates: the longest computed sub-metapath of each query seen at least twice
+    // (MP_INSERT_OTREE), none (MP_INSERT_FINAL), or every computed node (MP_INSERT_ALL)
     std::vector<int> candidate(nq, -1);
-    if (cache) {
+    if (cache && cfg.insertion == MP_INSERT_ALL)
+        for (auto &nd : nodes)
+            if (!nd.from_cache && !nd.filter) nd.keep = true;
+    if (cache && cfg.insertion == MP_INSERT_OTREE) {
         for (size_t q = 0; q < nq; q++) {
             if (root[q] < 0) continue;
             int best = -1;
@@ -465,6 +534,9 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             offer(nodes[root[q]]);
             if (candidate[q] >= 0) offer(nodes[candidate[q]]);
         }
+        if (cfg.insertion == MP_INSERT_ALL)
+            for (auto &nd : nodes)
+                if (nd.keep) offer(nd);
     }
     for (auto &m : masks) free_masks(m);
     nodes.clear();

@@ -673,6 +673,7 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // threads take consecutive products, so a long Y row is read coalesced.
 static constexpr int WIN = 2048;        // products per window of the product -> entry map
 static constexpr int WPT = WIN / GNT;   // map slots per thread in the prefix max
+static constexpr int UN = 4;            // products in flight per thread
 
 // Exclusive max-scan of one int per thread over a block of T threads (-1 for thread 0).
 template <int T>
@@ -694,7 +695,7 @@ __device__ __forceinline__ int block_excl_max(int v, int *warp_max) {
 }
 
 template <bool NUM>
-__global__ void __launch_bounds__(GNT, NUM ? 5 : 8) k_glob_set(PassArgs a, GlobArgs g) {
+__global__ void __launch_bounds__(GNT, NUM ? 3 : 6) k_glob_set(PassArgs a, GlobArgs g) {
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
@@ -780,22 +781,45 @@ __global__ void __launch_bounds__(GNT, NUM ? 5 : 8) k_glob_set(PassArgs a, GlobA
 #pragma unroll
                 for (int u = 0; u < WPT; u++) s_map[threadIdx.x * WPT + u] = max(carry, v[u]);
                 __syncthreads();
-                for (int64_t f = w0 + threadIdx.x; f < w1; f += GNT) {
-                    const int l = s_map[f - w0];
-                    const int64_t q = s_st[l] + (f - s_off[l]);
-                    const uint32_t j = (uint32_t)__ldg(yci + q);
-                    if (!bit_of(cm, j)) continue;
+                // UN products per thread per round, their loads issued together
+                for (int64_t fb = w0 + threadIdx.x; fb < w1; fb += (int64_t)GNT * UN) {
+                    int64_t q[UN];
+                    uint32_t j[UN];
+                    uint64_t av[UN];
+                    bool ok[UN];
+#pragma unroll
+                    for (int u = 0; u < UN; u++) {
+                        const int64_t f = fb + (int64_t)u * GNT;
+                        ok[u] = f < w1;
+                        const int l = ok[u] ? s_map[f - w0] : 0;
+                        q[u] = s_st[l] + (f - s_off[l]);
+                        av[u] = s_a[l];
+                    }
+#pragma unroll
+                    for (int u = 0; u < UN; u++) j[u] = ok[u] ? (uint32_t)__ldg(yci + q[u]) : 0u;
+#pragma unroll
+                    for (int u = 0; u < UN; u++) ok[u] = ok[u] && bit_of(cm, j[u]);
                     if (!NUM) {
-                        atomicOr(bm + (j >> 5), 1u << (j & 31));
+#pragma unroll
+                        for (int u = 0; u < UN; u++)
+                            if (ok[u]) atomicOr(bm + (j[u] >> 5), 1u << (j[u] & 31));
                     } else {
-                        const uint64_t av = s_a[l];
-                        const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
-                        const uint64_t v2 = av * bv;
-                        if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
-                        const uint32_t w = j >> 5;
-                        const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
-                        const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v2);
-                        if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
+                        uint64_t bv[UN];
+                        uint32_t pos[UN];
+#pragma unroll
+                        for (int u = 0; u < UN; u++) {
+                            bv[u] = (ok[u] && yval) ? __ldg(yval + q[u]) : 1ull;
+                            const uint32_t w = j[u] >> 5;
+                            pos[u] = ok[u] ? __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j[u] & 31)) - 1u)) : 0u;
+                        }
+#pragma unroll
+                        for (int u = 0; u < UN; u++) {
+                            if (!ok[u]) continue;
+                            const uint64_t v2 = av[u] * bv[u];
+                            if (__umul64hi(av[u], bv[u])) atomicOr(err, ERR_OVERFLOW);
+                            const unsigned long long old = atomicAdd(val + pos[u], (unsigned long long)v2);
+                            if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
+                        }
                     }
                 }
                 __syncthreads();
@@ -995,7 +1019,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
 // ------------------------------------------------------------------ host orchestration
 
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
-                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof) {
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only) {
     const int w = (int)in.size();
     out.assign(w, WaveOut{});
     if (w == 0) return MP_OK;
@@ -1140,6 +1164,21 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         !cuda_ok(cudaStreamSynchronize(s), "sync"))
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);
+    if (symbolic_only) {
+        for (int p = 0; p < w; p++) {
+            WaveOut &o = out[p];
+            o.products = hps[p].prods;
+            for (int b = 0; b < NBINS; b++) o.sym_bins[b] = hps[p].sym_bins[b];
+            if (hps[p].err) o.status = (hps[p].err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+            o.m.nrows = in[p].X.nrows;
+            o.m.ncols = in[p].Y.ncols;
+            o.m.nnz = in[p].X.nrows ? hps[p].nnz : 0;
+            al.free(hp[p].rp, s);
+        }
+        glob_release(gl, al, s);
+        al.free(ws, s);
+        return MP_OK;
+    }
     // per product: status, size guard, output arrays
     bool any_out = false;
     for (int p = 0; p < w; p++) {

@@ -19,6 +19,7 @@ MP_ERR_ARG, MP_ERR_STATE, MP_ERR_BUDGET, MP_ERR_TOO_LARGE, MP_ERR_OVERFLOW = -1,
 MP_ERR_TIMEOUT, MP_ERR_CUDA, MP_ERR_NOMEM, MP_ERR_NOTFOUND, MP_ERR_INTERNAL = -6, -7, -8, -9, -10
 MP_POLICY_ATRAPOS, MP_POLICY_PGDS, MP_POLICY_LRU, MP_POLICY_NONE = 0, 1, 2, 3
 MP_PLAN_DP, MP_PLAN_LEFT_TO_RIGHT, MP_PLAN_DP_SAMPLED = 0, 1, 2
+MP_INSERT_OTREE, MP_INSERT_FINAL, MP_INSERT_ALL = 0, 1, 2
 MP_BIN_AUTO, MP_BIN_WARP_HASH, MP_BIN_BLOCK_HASH, MP_BIN_DENSE, MP_BIN_GLOBAL = -1, 0, 1, 2, 3
 MP_OP_RANGE, MP_OP_EQ, MP_OP_IN = 0, 1, 2
 NBINS = 11
@@ -40,7 +41,8 @@ class mp_config(C.Structure):
                 ("policy", C.c_int32), ("planner", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("force_bin_class", C.c_int32), ("max_result_bytes", C.c_uint64),
-                ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64)]
+                ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64),
+                ("insertion", C.c_int32)]
 
 
 class mp_constraint(C.Structure):
@@ -118,7 +120,7 @@ def lib():
             "mp_cachesim_evicted": (C.c_int, [C.c_void_p, U32, C.c_char_p, U32, P(U32)]),
             "mp_cachesim_state": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_double), P(U32)]),
             "mp_plan_chain": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
-                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -307,9 +309,9 @@ def mp_result_stats(ctx, ticket: int):
     return {"products": prod.value, "sym_bins": sb, "num_bins": nb, "n_products": npr.value}
 
 
-def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None):
+def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None, rho_fixed=None):
     """Splits (p x p int32) and costs (p x p float64) of the C++ planner. known maps
-    (i, j) -> (cost, density)."""
+    (i, j) -> (cost, density); rho_fixed maps (i, j) -> measured result density."""
     dims = np.ascontiguousarray(dims, np.float64)
     nnz = np.ascontiguousarray(nnz, np.float64)
     p = nnz.size
@@ -319,10 +321,15 @@ def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None):
         kr = np.full((p, p), np.nan)
         for (i, j), (c, r) in known.items():
             kc[i, j], kr[i, j] = c, r
+    rf = None
+    if rho_fixed:
+        rf = np.full((p, p), np.nan)
+        for (i, j), r in rho_fixed.items():
+            rf[i, j] = r
     split = np.zeros((p, p), np.int32)
     cost = np.zeros((p, p), np.float64)
-    _ck(lib().mp_plan_chain(p, _ptr(dims), _ptr(nnz), alpha, beta, gamma, _ptr(kc), _ptr(kr), _ptr(split),
-                            _ptr(cost)), "mp_plan_chain")
+    _ck(lib().mp_plan_chain(p, _ptr(dims), _ptr(nnz), alpha, beta, gamma, _ptr(kc), _ptr(kr), _ptr(rf),
+                            _ptr(split), _ptr(cost)), "mp_plan_chain")
     return split, cost
 
 

@@ -115,3 +115,22 @@ def test_long_metapaths_with_squeezed_cache(c1, cuda_ok):
                     assert_same(e.run(q), w, (policy, "".join(q["types"])))
         finally:
             e.close()
+
+
+@pytest.mark.parametrize("insertion,policy", [(1, 2), (2, 2), (2, 0), (1, 1)])
+def test_cache_baselines_match_oracle(c1, batch_queries, cuda_ok, insertion, policy):
+    """Final-results-only + LRU (CBS1) and all-intermediates + LRU (CBS2), and the other
+    combinations, change what is cached, never the results."""
+    mp = _mp()
+    qs, want = batch_queries
+    e = mp.Engine(c1[0], policy=policy, insertion=insertion, hbm_budget_bytes=3 << 20)
+    try:
+        for rnd in range(2):
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g, w in zip(qs, res, want):
+                assert_same(g, w, (insertion, policy, rnd, "".join(q["types"])))
+        st = mp.mp_cache_stats(e.ctx)
+        assert st["inserts"] > 0
+    finally:
+        e.close()

@@ -95,14 +95,21 @@ def test_planners_agree(c1, cuda_ok):
     qs = gen.random_queries(c1[0], 7, 15, lengths=(4, 7), p_cons=0.3)
     e_dp = mp.Engine(c1[0], planner=mp.MP_PLAN_DP, policy=mp.MP_POLICY_NONE)
     e_lr = mp.Engine(c1[0], planner=mp.MP_PLAN_LEFT_TO_RIGHT, policy=mp.MP_POLICY_NONE)
+    e_sp = mp.Engine(c1[0], planner=mp.MP_PLAN_DP_SAMPLED, policy=mp.MP_POLICY_NONE, sample_rows=64)
     try:
         for q in qs:
             want = OC.evaluate(c1[1], q)
             assert_same(e_dp.run(q), want, "dp")
             assert_same(e_lr.run(q), want, "left-to-right")
+            assert_same(e_sp.run(q), want, "dp, sampled densities")
+        rc, got = e_sp.run_batch(qs)
+        assert rc == 0
+        for q, g in zip(qs, got):
+            assert_same(g, OC.evaluate(c1[1], q), "sampled, batch")
     finally:
         e_dp.close()
         e_lr.close()
+        e_sp.close()
 
 
 def test_long_metapaths_through_hubs(c1, c1_engines):
@@ -161,6 +168,17 @@ def test_overflow_is_an_error_not_a_wrap(cuda_ok):
 def c2_small(cuda_ok):
     h = gen.config2_hin(scale=0.01)
     return h, OracleHIN(h)
+
+
+def test_scaled_scholarly_workload_sampled_planner(c2_small):
+    mp = _mp()
+    h, o = c2_small
+    e = mp.Engine(h, planner=mp.MP_PLAN_DP_SAMPLED, policy=mp.MP_POLICY_NONE)
+    try:
+        for q in gen.config2_queries(h, seed=2, n_anchor_a=32, n_anchor_t=4):
+            assert_same(e.run(q), OC.evaluate(o, q), ("sampled", "".join(q["types"])))
+    finally:
+        e.close()
 
 
 @pytest.mark.parametrize("force", BIN_CLASSES)

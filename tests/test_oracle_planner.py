@@ -101,3 +101,24 @@ def test_known_subchain_is_reused():
     assert c1 < c0
     assert t1 == (0, (1, 3, "known"))
     assert D[1][3] == 0.5
+
+
+def test_fixed_density_changes_only_the_result_density():
+    """A measured density replaces E_ac for that sub-chain: with the E_ac value itself the
+    plan is unchanged; with a much denser measurement the DP avoids materialising it."""
+    dims = [100, 100000, 100, 100000, 100]
+    nnz = [5000, 5000, 5000, 5000]
+    c0, t0, C0, D0, S0 = PL.sparse_plan(dims, nnz)
+    c1, t1, C1, D1, S1 = PL.sparse_plan(dims, nnz, rho_fixed={(1, 2): D0[1][2]})
+    assert c1 == pytest.approx(c0) and t1 == t0
+    c2, t2, C2, D2, S2 = PL.sparse_plan(dims, nnz, rho_fixed={(1, 2): 0.9})
+    assert D2[1][2] == 0.9
+    assert C2[1][2] > C0[1][2]
+
+
+def test_sampled_density_scaling():
+    # every row sampled: the exact density
+    assert PL.sampled_density(30, 10, 10, 10, 50) == pytest.approx(30 / 500)
+    # 10 of 100 non-empty rows sampled in a 1000-row matrix
+    assert PL.sampled_density(30, 10, 100, 1000, 50) == pytest.approx(300 / 50000)
+    assert PL.sampled_density(0, 0, 10, 10, 10) == 0.0

@@ -37,8 +37,12 @@ def test_engine_planner_matches_oracle(seed):
         i = int(rng.integers(0, p - 1))
         j = int(rng.integers(i + 1, p))
         known = {(i, j): (float(rng.uniform(0, 1e6)), float(rng.uniform(0, 0.1)))}
-    c_o, t_o, C, D, S = PL.sparse_plan(list(dims), list(nnz), a, b, g, known)
-    split, cost = mp.mp_plan_chain(dims, nnz, a, b, g, known)
+    fixed = None
+    if p >= 2 and seed % 2 == 1:
+        i = int(rng.integers(0, p - 1))
+        fixed = {(i, i + 1): float(10.0 ** rng.uniform(-6, -1))}
+    c_o, t_o, C, D, S = PL.sparse_plan(list(dims), list(nnz), a, b, g, known, fixed)
+    split, cost = mp.mp_plan_chain(dims, nnz, a, b, g, known, fixed)
     assert cost[0, p - 1] == pytest.approx(c_o, rel=1e-9)
     # the engine's split at every sub-chain is optimal under the oracle's recursion
     for ln in range(2, p + 1):
@@ -49,5 +53,5 @@ def test_engine_planner_matches_oracle(seed):
                 continue
             k = int(split[i, j])
             prod = PL.sparse_product(a, b, g)
-            c, _ = prod(dims[i], dims[k + 1], dims[j + 1], D[i][k], D[k + 1][j])
+            c, _ = prod(dims[i], dims[k + 1], dims[j + 1], D[i][k], D[k + 1][j], (fixed or {}).get((i, j)))
             assert C[i][k] + C[k + 1][j] + c == pytest.approx(C[i][j], rel=1e-9)
