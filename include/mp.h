@@ -94,6 +94,7 @@ typedef struct {
     uint32_t sample_rows;      /* rows sampled per product by MP_PLAN_DP_SAMPLED */
     uint64_t seed;             /* seed of the sampled-row choice */
     int32_t insertion;         /* MP_INSERT_* (used when policy != MP_POLICY_NONE) */
+    const char *tune_file;     /* NULL, or a file written by mp_autotune to load at create */
 } mp_config;
 
 /* Fill *cfg with defaults: device 0, 8 GiB budget, 64 slots, ATRAPOS policy, DP
@@ -200,6 +201,19 @@ int mp_release(mp_ctx *ctx, mp_ticket ticket);
 int mp_result_time(mp_ctx *ctx, mp_ticket ticket, double *ms);
 
 const char *mp_strerror(int code);
+
+/* ---- autotuning
+ *
+ * Times the given workload (run `reps` times per candidate, cache bypassed) over a grid of
+ * row-bin thresholds -- the smallest row sent to the dense shared-memory bin and the
+ * product count above which a row is split over many blocks -- and keeps the fastest. It
+ * then runs each query once and fits the Eq. 2 coefficients alpha, beta, gamma to the
+ * measured product times by least squares (Sec. 3.2), so planner costs and recorded cache
+ * costs are in milliseconds. The result applies to this context at once and, when
+ * out_path is not NULL, is written there as JSON for mp_config.tune_file. *best_ms (may
+ * be NULL) receives the best candidate's time per run. Results never change. */
+int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t reps, const char *out_path,
+                double *best_ms);
 
 /* ---- diagnostics */
 

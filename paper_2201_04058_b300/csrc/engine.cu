@@ -80,6 +80,7 @@ extern "C" void mp_config_default(mp_config *c) {
     c->sample_rows = 1024;
     c->seed = 1;
     c->insertion = MP_INSERT_OTREE;
+    c->tune_file = nullptr;
 }
 
 extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
@@ -120,6 +121,29 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     if (check_cuda(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "stream")) return MP_ERR_CUDA;
     ctx->alloc.reset(new PoolAlloc());
     if (c.policy != MP_POLICY_NONE) ctx->cache.reset(new CachePolicy((double)c.hbm_budget_bytes, c.policy));
+    if (c.tune_file) {
+        if (FILE *f = fopen(c.tune_file, "r")) {
+            char buf[4096];
+            const size_t n = fread(buf, 1, sizeof(buf) - 1, f);
+            fclose(f);
+            buf[n] = 0;
+            auto num = [&](const char *key, double *v) {
+                const char *p = strstr(buf, key);
+                if (p && (p = strchr(p, ':'))) *v = strtod(p + 1, nullptr);
+            };
+            double dmu = ctx->tun.dense_min_u, hv = (double)ctx->tun.heavy;
+            num("\"dense_min_u\"", &dmu);
+            num("\"heavy\"", &hv);
+            num("\"alpha\"", &ctx->cfg.alpha);
+            num("\"beta\"", &ctx->cfg.beta);
+            num("\"gamma\"", &ctx->cfg.gamma);
+            ctx->tun.dense_min_u = (int)dmu;
+            ctx->tun.heavy = (uint64_t)hv;
+        } else {
+            return MP_ERR_NOTFOUND;
+        }
+        ctx->cfg.tune_file = nullptr;  // the caller's string is not kept
+    }
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
     if (!ctx->prof.init()) return MP_ERR_CUDA;
@@ -529,6 +553,114 @@ extern "C" int mp_serve_stats(mp_ctx *ctx, uint64_t *batches, uint64_t *queries,
     }
     std::lock_guard<std::mutex> g(ctx->qmu);
     if (queued) *queued = ctx->queue.size();
+    return MP_OK;
+}
+
+// Least squares for y ~ a*x0 + b*x1 + c*x2 (normal equations, Cramer's rule).
+static bool fit3(const std::vector<std::array<double, 4>> &s, double out[3]) {
+    double A[3][3] = {}, B[3] = {};
+    for (auto &r : s)
+        for (int i = 0; i < 3; i++) {
+            B[i] += r[i] * r[3];
+            for (int j = 0; j < 3; j++) A[i][j] += r[i] * r[j];
+        }
+    auto det = [](double M[3][3]) {
+        return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    };
+    const double d = det(A);
+    if (!(std::fabs(d) > 0)) return false;
+    for (int k = 0; k < 3; k++) {
+        double M[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) M[i][j] = j == k ? B[i] : A[i][j];
+        out[k] = det(M) / d;
+    }
+    return true;
+}
+
+extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t reps, const char *out_path,
+                           double *best_ms) {
+    if (!ctx || !n || !q) return MP_ERR_ARG;
+    if (!ctx->finalized) return MP_ERR_STATE;
+    std::vector<Query> parsed(n);
+    for (uint32_t i = 0; i < n; i++) {
+        int rc = ctx->parse(&q[i], parsed[i]);
+        if (rc) return rc;
+    }
+    if (reps == 0) reps = 1;
+    std::lock_guard<std::mutex> ge(ctx->exec_mu);
+    cudaSetDevice(ctx->cfg.device);
+    std::unique_ptr<CachePolicy> saved_cache(ctx->cache.release());  // timings without cache hits
+    const Tuning base = ctx->tun;
+    const int dmu[] = {64, 256, 1024};
+    const uint64_t heavy[] = {16384, 65536, 262144};
+    double best = INFINITY;
+    Tuning best_t = base;
+    std::string log;
+    int rc = MP_OK;
+    for (int a : dmu)
+        for (uint64_t h : heavy) {
+            ctx->tun = base;
+            ctx->tun.dense_min_u = a;
+            ctx->tun.heavy = h;
+            std::vector<double> ts;
+            for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
+                std::vector<Query> qs = parsed;
+                std::vector<Result> res(n);
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = ctx->run_batch(qs, res);
+                const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                if (r) ts.push_back(ms);  // the first run warms up
+            }
+            if (rc) break;
+            std::sort(ts.begin(), ts.end());
+            const double med = ts[ts.size() / 2];
+            char line[160];
+            snprintf(line, sizeof(line), "%s{\"dense_min_u\": %d, \"heavy\": %llu, \"ms\": %.4f}", log.empty() ? "" : ", ", a,
+                     (unsigned long long)h, med);
+            log += line;
+            if (med < best) {
+                best = med;
+                best_t = ctx->tun;
+            }
+        }
+    ctx->tun = rc ? base : best_t;
+    // Eq. 2 coefficients from per-product times, each query run on its own
+    double coef[3] = {ctx->cfg.alpha, ctx->cfg.beta, ctx->cfg.gamma};
+    bool fitted = false;
+    if (!rc) {
+        ctx->fit_samples.clear();
+        ctx->collect_fit = true;
+        for (uint32_t i = 0; i < n && !rc; i++) {
+            std::vector<Query> qs(1, parsed[i]);
+            std::vector<Result> res(1);
+            rc = ctx->run_batch(qs, res);
+        }
+        ctx->collect_fit = false;
+        double c[3];
+        if (!rc && ctx->fit_samples.size() >= 3 && fit3(ctx->fit_samples, c)) {
+            // a cost model with a negative weight would reward work: keep those terms at a floor
+            for (int k = 0; k < 3; k++) coef[k] = c[k] > 1e-12 ? c[k] : 1e-12;
+            ctx->cfg.alpha = coef[0];
+            ctx->cfg.beta = coef[1];
+            ctx->cfg.gamma = coef[2];
+            fitted = true;
+        }
+        ctx->fit_samples.clear();
+    }
+    ctx->cache.reset(saved_cache.release());
+    if (rc) return rc;
+    if (best_ms) *best_ms = best;
+    if (out_path) {
+        FILE *f = fopen(out_path, "w");
+        if (!f) return MP_ERR_ARG;
+        fprintf(f, "{\"dense_min_u\": %d, \"heavy\": %llu, \"alpha\": %.9g, \"beta\": %.9g, \"gamma\": %.9g, "
+                   "\"fitted\": %s, \"best_ms\": %.4f, \"candidates\": [%s]}\n",
+                ctx->tun.dense_min_u, (unsigned long long)ctx->tun.heavy, coef[0], coef[1], coef[2],
+                fitted ? "true" : "false", best, log.c_str());
+        fclose(f);
+    }
     return MP_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -92,6 +93,11 @@ struct mp_ctx {
     bool serving = false, stop_req = false;
     uint64_t batches = 0, batched_queries = 0;
     void serve_loop();
+    // nnz of masked base factors already counted: (relation, row key, column key) -> nnz
+    std::unordered_map<std::string, double> leaf_memo;
+    // per-product samples (nnz(X), N_op, nnz(Z), ms) for the Eq. 2 fit of mp_autotune
+    bool collect_fit = false;
+    std::vector<std::array<double, 4>> fit_samples;
     std::vector<NodeType> types;
     std::vector<Prop> props;
     std::vector<Rel> rels;

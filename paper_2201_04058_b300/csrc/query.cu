@@ -138,7 +138,8 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     std::vector<int> qstatus(nq, MP_OK);
     for (size_t q = 0; q < nq; q++) qstatus[q] = build_masks(qs[q], masks[q]);
 
-    // exact nnz of every masked base factor, for the planner: one device array, one sync
+    // exact nnz of every masked base factor, for the planner: one device array, one sync;
+    // counts already seen (same relation, same constraints at both ends) come from a memo
     std::vector<std::vector<double>> leaf(nq);
     {
         size_t total = 0;
@@ -147,33 +148,50 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (!d) return MP_ERR_NOMEM;
         cudaMemsetAsync(d, 0, std::max<size_t>(total, 1) * 8, stream);
         std::vector<void *> tmp;
+        std::vector<std::string> keys(total);
+        std::unordered_map<std::string, size_t> first;  // key -> slot counted in this batch
         size_t off = 0;
+        bool any = false;
         for (size_t q = 0; q < nq; q++) {
             const int p = (int)qs[q].rels.size();
-            leaf[q].assign(p, 0.0);
+            leaf[q].assign(p, -1.0);
             for (int t = 0; t < p; t++) {
                 const Mat &A = rels[qs[q].rels[t]].dev;
-                if (!qstatus[q] && (masks[q][t] || masks[q][t + 1])) {
-                    uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
-                    if (!lr) return MP_ERR_NOMEM;
-                    cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
-                    masked_nnz(A.view(), masks[q][t], masks[q][t + 1], d + off + t, lr, lr + A.nrows, stream);
-                    tmp.push_back(lr);
-                } else {
-                    leaf[q][t] = -1.0;  // unmasked: the relation's nnz
+                if (qstatus[q] || !(masks[q][t] || masks[q][t + 1])) continue;
+                std::string &key = keys[off + t];
+                key = std::to_string(qs[q].rels[t]) + "|" + qs[q].pos_keys[t] + "|" + qs[q].pos_keys[t + 1];
+                auto m = leaf_memo.find(key);
+                if (m != leaf_memo.end()) {
+                    leaf[q][t] = m->second;
+                    continue;
                 }
+                if (first.count(key)) continue;
+                first.emplace(key, off + t);
+                uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
+                if (!lr) return MP_ERR_NOMEM;
+                cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
+                masked_nnz(A.view(), masks[q][t], masks[q][t + 1], d + off + t, lr, lr + A.nrows, stream);
+                tmp.push_back(lr);
+                any = true;
             }
             off += p;
         }
-        std::vector<unsigned long long> h(std::max<size_t>(total, 1));
-        cudaMemcpyAsync(h.data(), d, std::max<size_t>(total, 1) * 8, cudaMemcpyDeviceToHost, stream);
-        if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+        std::vector<unsigned long long> h(std::max<size_t>(total, 1), 0);
+        if (any) {
+            cudaMemcpyAsync(h.data(), d, std::max<size_t>(total, 1) * 8, cudaMemcpyDeviceToHost, stream);
+            if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+        }
         for (void *x : tmp) alloc->free(x, stream);
         alloc->free(d, stream);
+        if (leaf_memo.size() > 65536) leaf_memo.clear();
+        for (auto &kv : first) leaf_memo[kv.first] = (double)h[kv.second];
         off = 0;
         for (size_t q = 0; q < nq; q++) {
-            for (size_t t = 0; t < qs[q].rels.size(); t++)
-                leaf[q][t] = leaf[q][t] < 0 ? (double)rels[qs[q].rels[t]].dev.nnz : (double)h[off + t];
+            for (size_t t = 0; t < qs[q].rels.size(); t++) {
+                if (leaf[q][t] >= 0) continue;
+                const std::string &key = keys[off + t];
+                leaf[q][t] = key.empty() ? (double)rels[qs[q].rels[t]].dev.nnz : leaf_memo[key];
+            }
             off += qs[q].rels.size();
         }
     }
@@ -467,8 +485,9 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                             (nd.right >= 0 && !nodes[nd.right].from_cache ? nodes[nd.right].subtree_ms : 0.0);
             if (!o.status) {
                 // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
-                nd.c_ops = cfg.alpha * (double)(nd.left >= 0 ? nodes[nd.left].res->m.nnz : rels[qs[nd.q].rels[nd.i]].dev.nnz) +
-                           cfg.beta * (double)o.products + cfg.gamma * (double)o.m.nnz;
+                const double nnz_x = (double)(nd.left >= 0 ? nodes[nd.left].res->m.nnz : rels[qs[nd.q].rels[nd.i]].dev.nnz);
+                nd.c_ops = cfg.alpha * nnz_x + cfg.beta * (double)o.products + cfg.gamma * (double)o.m.nnz;
+                if (collect_fit) fit_samples.push_back({nnz_x, (double)o.products, (double)o.m.nnz, nd.ms});
                 nd.res = wrap(o.m);
             }
             release_operands(nd);

@@ -671,37 +671,11 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // One work item per block iteration: products [s0, s1) of one row. The X entries that hold
 // them are staged GNT at a time with their product offsets (from xoff); consecutive
 // threads take consecutive products, so a long Y row is read coalesced.
-static constexpr int WIN = 2048;        // products per window of the product -> entry map
-static constexpr int WPT = WIN / GNT;   // map slots per thread in the prefix max
-static constexpr int UN = 4;            // products in flight per thread
-
-// Exclusive max-scan of one int per thread over a block of T threads (-1 for thread 0).
-template <int T>
-__device__ __forceinline__ int block_excl_max(int v, int *warp_max) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, d);
-        if (lane >= d) x = max(x, y);
-    }
-    if (lane == 31) warp_max[wid] = x;
-    __syncthreads();
-    int before = -1;
-    for (int w = 0; w < wid; w++) before = max(before, warp_max[w]);
-    const int ex = max(before, __shfl_up_sync(FULL, x, 1));
-    const int r = lane == 0 ? before : ex;
-    __syncthreads();
-    return r;
-}
-
 template <bool NUM>
-__global__ void __launch_bounds__(GNT, NUM ? 3 : 6) k_glob_set(PassArgs a, GlobArgs g) {
+__global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
-    __shared__ int s_map[WIN];
-    __shared__ int s_wmax[GNT / 32];
-    for (int x = threadIdx.x; x < WIN; x += GNT) s_map[x] = -1;
     const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
     for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         int64_t lo = g.r0, hi = g.r1 - 1;
@@ -751,80 +725,30 @@ __global__ void __launch_bounds__(GNT, NUM ? 3 : 6) k_glob_set(PassArgs a, GlobA
             }
             if (threadIdx.x == 0) s_off[nent] = (c0 + nent < xe ? __ldg(xo + (c0 + nent - xb)) : total) - base;
             __syncthreads();
-            // this chunk's products [f0, f1), in windows of WIN: each window gets a map from
-            // product to X entry (entries mark where they start, a block-wide prefix max
-            // fills the rest), then consecutive threads take consecutive products
+            // this chunk's products [f0, f1): consecutive threads take consecutive products
+            // (coalesced Y reads); each finds its X entry by binary search in shared memory
             const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
-            for (int64_t w0 = f0; w0 < f1; w0 += WIN) {
-                const int64_t w1 = min(f1, w0 + WIN);
-                if (threadIdx.x < nent) {
-                    const int64_t st = s_off[threadIdx.x];
-                    if (st > w0 && st < w1 && s_off[threadIdx.x + 1] > st) s_map[st - w0] = threadIdx.x;
+            for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
+                int l = 0, h = nent - 1;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (s_off[mid] <= f) l = mid; else h = mid - 1;
                 }
-                if (threadIdx.x == 0) {  // the entry holding product w0
-                    int l = 0, h = nent - 1;
-                    while (l < h) {
-                        const int mid = (l + h + 1) >> 1;
-                        if (s_off[mid] <= w0) l = mid; else h = mid - 1;
-                    }
-                    s_map[0] = l;
+                const int64_t q = s_st[l] + (f - s_off[l]);
+                const uint32_t j = (uint32_t)__ldg(yci + q);
+                if (!bit_of(cm, j)) continue;
+                if (!NUM) {
+                    atomicOr(bm + (j >> 5), 1u << (j & 31));
+                } else {
+                    const uint64_t av = s_a[l];
+                    const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
+                    const uint64_t v2 = av * bv;
+                    if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+                    const uint32_t w = j >> 5;
+                    const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
+                    const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v2);
+                    if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
                 }
-                __syncthreads();
-                int v[WPT];
-                int run = -1;
-#pragma unroll
-                for (int u = 0; u < WPT; u++) {
-                    run = max(run, s_map[threadIdx.x * WPT + u]);
-                    v[u] = run;
-                }
-                const int carry = block_excl_max<GNT>(run, s_wmax);
-#pragma unroll
-                for (int u = 0; u < WPT; u++) s_map[threadIdx.x * WPT + u] = max(carry, v[u]);
-                __syncthreads();
-                // UN products per thread per round, their loads issued together
-                for (int64_t fb = w0 + threadIdx.x; fb < w1; fb += (int64_t)GNT * UN) {
-                    int64_t q[UN];
-                    uint32_t j[UN];
-                    uint64_t av[UN];
-                    bool ok[UN];
-#pragma unroll
-                    for (int u = 0; u < UN; u++) {
-                        const int64_t f = fb + (int64_t)u * GNT;
-                        ok[u] = f < w1;
-                        const int l = ok[u] ? s_map[f - w0] : 0;
-                        q[u] = s_st[l] + (f - s_off[l]);
-                        av[u] = s_a[l];
-                    }
-#pragma unroll
-                    for (int u = 0; u < UN; u++) j[u] = ok[u] ? (uint32_t)__ldg(yci + q[u]) : 0u;
-#pragma unroll
-                    for (int u = 0; u < UN; u++) ok[u] = ok[u] && bit_of(cm, j[u]);
-                    if (!NUM) {
-#pragma unroll
-                        for (int u = 0; u < UN; u++)
-                            if (ok[u]) atomicOr(bm + (j[u] >> 5), 1u << (j[u] & 31));
-                    } else {
-                        uint64_t bv[UN];
-                        uint32_t pos[UN];
-#pragma unroll
-                        for (int u = 0; u < UN; u++) {
-                            bv[u] = (ok[u] && yval) ? __ldg(yval + q[u]) : 1ull;
-                            const uint32_t w = j[u] >> 5;
-                            pos[u] = ok[u] ? __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j[u] & 31)) - 1u)) : 0u;
-                        }
-#pragma unroll
-                        for (int u = 0; u < UN; u++) {
-                            if (!ok[u]) continue;
-                            const uint64_t v2 = av[u] * bv[u];
-                            if (__umul64hi(av[u], bv[u])) atomicOr(err, ERR_OVERFLOW);
-                            const unsigned long long old = atomicAdd(val + pos[u], (unsigned long long)v2);
-                            if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
-                        }
-                    }
-                }
-                __syncthreads();
-                for (int x = threadIdx.x; x < WIN; x += GNT) s_map[x] = -1;
-                __syncthreads();
             }
             __syncthreads();
         }

@@ -32,7 +32,7 @@ EXPORTS = [
     "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
-    "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency",
+    "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune",
 ]
 
 
@@ -42,7 +42,7 @@ class mp_config(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("force_bin_class", C.c_int32), ("max_result_bytes", C.c_uint64),
                 ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64),
-                ("insertion", C.c_int32)]
+                ("insertion", C.c_int32), ("tune_file", C.c_char_p)]
 
 
 class mp_constraint(C.Structure):
@@ -99,6 +99,7 @@ def lib():
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
+            "mp_autotune": (C.c_int, [C.c_void_p, U32, P(mp_query), U32, C.c_char_p, P(C.c_double)]),
             "mp_serve_start": (C.c_int, [C.c_void_p]),
             "mp_serve_stop": (C.c_int, [C.c_void_p]),
             "mp_serve_stats": (C.c_int, [C.c_void_p, P(U64), P(U64), P(U64)]),
@@ -251,6 +252,16 @@ def mp_submit_batch(ctx, queries) -> tuple[int, list[int]]:
 
 def mp_wait(ctx, ticket: int, timeout_ms: int = 0xFFFFFFFF) -> int:
     return lib().mp_wait(ctx, ticket, timeout_ms)
+
+
+def mp_autotune(ctx, queries, reps=2, out_path=None):
+    """Tune bin thresholds and fit Eq. 2 on a workload; returns the best time per run (ms)."""
+    n = len(queries)
+    arr = (mp_query * max(1, n))(*[q.q for q in queries])
+    best = C.c_double()
+    _ck(lib().mp_autotune(ctx, n, arr, int(reps), None if out_path is None else out_path.encode(), C.byref(best)),
+        "mp_autotune")
+    return best.value
 
 
 def mp_serve_start(ctx):
@@ -457,7 +468,7 @@ class Engine:
     def __init__(self, hin, **cfg_fields):
         self.cfg = mp_config_default()
         for k, v in cfg_fields.items():
-            setattr(self.cfg, k, v)
+            setattr(self.cfg, k, v.encode() if isinstance(v, str) else v)
         self.ctx = mp_create(self.cfg)
         self.type_id = {}
         for name, n in hin["types"].items():
