@@ -725,18 +725,10 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
             }
             if (threadIdx.x == 0) s_off[nent] = (c0 + nent < xe ? __ldg(xo + (c0 + nent - xb)) : total) - base;
             __syncthreads();
-            // this chunk's products [f0, f1): consecutive threads take consecutive products
-            // (coalesced Y reads); each finds its X entry by binary search in shared memory
             const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
-            for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
-                int l = 0, h = nent - 1;
-                while (l < h) {
-                    const int mid = (l + h + 1) >> 1;
-                    if (s_off[mid] <= f) l = mid; else h = mid - 1;
-                }
-                const int64_t q = s_st[l] + (f - s_off[l]);
+            auto product = [&](int l, int64_t q) {
                 const uint32_t j = (uint32_t)__ldg(yci + q);
-                if (!bit_of(cm, j)) continue;
+                if (!bit_of(cm, j)) return;
                 if (!NUM) {
                     atomicOr(bm + (j >> 5), 1u << (j & 31));
                 } else {
@@ -748,6 +740,25 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
                     const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
                     const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v2);
                     if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
+                }
+            };
+            if (s_off[nent] <= 8 * (int64_t)nent) {
+                // short Y rows: each thread walks the products of its own X entry
+                if ((int)threadIdx.x < nent) {
+                    const int l = threadIdx.x;
+                    const int64_t lo_f = max(s_off[l], f0), hi_f = min(s_off[l + 1], f1);
+                    for (int64_t f = lo_f; f < hi_f; f++) product(l, s_st[l] + (f - s_off[l]));
+                }
+            } else {
+                // long Y rows: consecutive threads take consecutive products (coalesced Y
+                // reads); each finds its X entry by binary search in shared memory
+                for (int64_t f = f0 + threadIdx.x; f < f1; f += GNT) {
+                    int l = 0, h = nent - 1;
+                    while (l < h) {
+                        const int mid = (l + h + 1) >> 1;
+                        if (s_off[mid] <= f) l = mid; else h = mid - 1;
+                    }
+                    product(l, s_st[l] + (f - s_off[l]));
                 }
             }
             __syncthreads();
