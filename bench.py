@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="scholarly", choices=["scholarly", "serving"])
+    ap.add_argument("--workload", default="scholarly", choices=["scholarly", "serving", "batched", "stress"])
+    ap.add_argument("--pool", type=int, default=40, help="template pool of the batched workload")
     ap.add_argument("--serve-queries", type=int, default=4000)
     ap.add_argument("--load", type=float, default=1.0, help="arrival rate / plain-path saturation rate")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
@@ -471,6 +472,108 @@ def run_serving(args, ws, rank, local):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- small-HIN legs
+
+def _time_plain(mp, eng, bufs, reps):
+    """One query at a time; returns (seconds per pass, products per pass)."""
+    import torch
+    for b in bufs:
+        _, t = mp.mp_submit(eng.ctx, b)
+        mp.mp_release(eng.ctx, t)
+    torch.cuda.synchronize()
+    prods = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for b in bufs:
+            rc, t = mp.mp_submit(eng.ctx, b)
+            if rc != mp.MP_OK:
+                raise mp.MPError(rc, "query")
+            prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
+            mp.mp_release(eng.ctx, t)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, prods / reps
+
+
+def _time_batch(mp, eng, bufs, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        _, ts = mp.mp_submit_batch(eng.ctx, bufs)
+        for t in ts:
+            mp.mp_release(eng.ctx, t)
+    torch.cuda.synchronize()
+    prods = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc, ts = mp.mp_submit_batch(eng.ctx, bufs)
+        if rc != mp.MP_OK:
+            raise mp.MPError(rc, "batch")
+        for t in ts:
+            prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
+            mp.mp_release(eng.ctx, t)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, prods / reps
+
+
+def run_small(args, local):
+    """Batched workload (256 Zipf-drawn queries) or stress workload (64 long metapaths) on
+    the 2,000-paper HIN: plain one-at-a-time chain vs one batch (shared sub-chains once,
+    one wave per level) vs batch with the Overlap-Tree cache."""
+    import torch
+    import gen
+    from paper_2201_04058_b300 import mp
+    torch.cuda.set_device(local)
+    hin = gen.config1_hin()
+    if args.workload == "batched":
+        qs = gen.batched_queries(seed=3, n=256, pool=args.pool)
+        name = f"batched: 256 queries of length 3-7, Zipf(1.1) over a pool of {args.pool} templates"
+    else:
+        qs = gen.long_queries(5, 64)
+        name = "stress: 64 metapaths of length 7-9 through venues and topics"
+    reps = max(1, args.steps)
+    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE)
+    bufs = [plain.query(q) for q in qs]
+    p_s, p_prod = _time_plain(mp, plain, bufs, reps)
+    b_s, b_prod = _time_batch(mp, plain, bufs, reps)
+    tune = os.path.join(ROOT, "gpurun_out", f"tune_{args.workload}.json")
+    os.makedirs(os.path.dirname(tune), exist_ok=True)
+    mp.mp_autotune(plain.ctx, bufs, reps=2, out_path=tune)
+    bt_s, _ = _time_batch(mp, plain, bufs, reps)
+    ks, launches0 = mp.mp_kernel_stats(plain.ctx)
+    plain.close()
+    out_c = {}
+    budgets = {"8GB": 8 << 30}
+    if args.workload == "stress":
+        # 25 % of the bytes of all distinct intermediates forces evictions
+        e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, insertion=mp.MP_INSERT_ALL, hbm_budget_bytes=1 << 40)
+        rc, ts = mp.mp_submit_batch(e.ctx, [e.query(q) for q in qs])
+        for t in ts:
+            mp.mp_release(e.ctx, t)
+        budgets["25pct"] = max(1 << 20, mp.mp_cache_stats(e.ctx)["bytes"] // 4)
+        e.close()
+    for label, budget in budgets.items():
+        for pol in (mp.MP_POLICY_ATRAPOS, mp.MP_POLICY_PGDS, mp.MP_POLICY_LRU):
+            e = mp.Engine(hin, device=local, policy=pol, hbm_budget_bytes=int(budget))
+            eb = [e.query(q) for q in qs]
+            cold_s, cold_p = _time_batch(mp, e, eb, 1, warm=0)  # the first pass fills the cache
+            warm_s, warm_p = _time_batch(mp, e, eb, reps, warm=0)
+            out_c[f"{label}/{['atrapos', 'pgds', 'lru'][pol]}"] = {
+                "first_pass_qps": len(qs) / cold_s, "replay_qps": len(qs) / warm_s,
+                "replay_products": warm_p, "cache": mp.mp_cache_stats(e.ctx)}
+            e.close()
+    res = {"metric": METRIC, "value": len(qs) / b_s, "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": 1,
+           "ms_per_step": 1e3 * b_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
+           "config": {"workload": name, "papers": 2000, "authors": 1500, "venues": 50, "topics": 200,
+                      "queries_per_step": len(qs)},
+           "plain": {"qps": len(qs) / p_s, "products": p_prod},
+           "batched": {"qps": len(qs) / b_s, "products": b_prod,
+                       "duplicate_product_fraction": 1.0 - b_prod / max(p_prod, 1),
+                       "speedup_vs_plain": p_s / b_s},
+           "batched_autotuned": {"qps": len(qs) / bt_s, "tune": json.load(open(tune))},
+           "cached_replays": out_c}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -480,6 +583,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             run_serving(args, ws, rank, local)
+        return
+    if args.workload in ("batched", "stress"):
+        if rank == 0:
+            run_small(args, local)
         return
     run_engine(args, ws, rank, local)
     if ws > 1:

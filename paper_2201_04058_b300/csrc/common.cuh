@@ -37,11 +37,12 @@ __host__ __device__ __forceinline__ int next_pow2_log(uint64_t x) {
 }
 
 // Bin of a row with prod Gustavson products and at most u output entries (u >= 1), for
-// an output of ncols columns. Hash tables are sized T >= 2u (load factor <= 1/2). Rows
-// with more than `heavy` products, or whose output is too wide for a shared-memory
-// table, go to GLOBAL, where the row is split over many blocks.
+// an output of ncols columns. Hash tables are sized T >= 2u (load factor <= 1/2). A row
+// goes to a one-warp bin only if it has at most warp_prod products (else 32 threads would
+// grind through it alone); rows with more than `heavy` products, or whose output is too
+// wide for a shared-memory table, go to GLOBAL, where the row is split over many blocks.
 __host__ __device__ __forceinline__ int bin_for(uint64_t prod, uint64_t u, int64_t ncols, int dense_max_cols,
-                                                int dense_min_u, uint64_t heavy, int force) {
+                                                int dense_min_u, uint64_t heavy, uint64_t warp_prod, int force) {
     if ((uint64_t)ncols < u) u = (uint64_t)ncols;
     const bool dense_ok = ncols <= dense_max_cols;
     int e = next_pow2_log(2 * u);
@@ -63,8 +64,8 @@ __host__ __device__ __forceinline__ int bin_for(uint64_t prod, uint64_t u, int64
     }
     if (prod > heavy) return B_GLOBAL;
     if (dense_ok && u >= (uint64_t)dense_min_u) return B_DENSE;
-    if (e <= 10) return B_W32 + (e - 5);
-    if (e <= 13) return B_K2048 + (e - 11);
+    if (e <= 10 && prod <= warp_prod) return B_W32 + (e - 5);
+    if (e <= 13) return B_K2048 + (e < 11 ? 0 : e - 11);
     return dense_ok ? B_DENSE : B_GLOBAL;
 }
 

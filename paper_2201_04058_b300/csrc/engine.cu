@@ -118,6 +118,27 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     ctx->tun.sm_count = sms;
     ctx->tun.force_class = c.force_bin_class;
     if (c.scratch_bytes) ctx->tun.scratch_cap = c.scratch_bytes;
+    // optional overrides of the kernel tuning, "key=value,..." (for measuring variants)
+    if (const char *e = getenv("MP_TUNING")) {
+        std::string t(e);
+        size_t a = 0;
+        while (a < t.size()) {
+            size_t b = t.find(',', a);
+            if (b == std::string::npos) b = t.size();
+            const std::string kv = t.substr(a, b - a);
+            const size_t eq = kv.find('=');
+            if (eq != std::string::npos) {
+                const std::string k = kv.substr(0, eq);
+                const long long v = atoll(kv.c_str() + eq + 1);
+                if (k == "combine") ctx->tun.combine = (int)v;
+                else if (k == "short_walk") ctx->tun.short_walk = (int)v;
+                else if (k == "warp_prod") ctx->tun.warp_prod = (uint64_t)v;
+                else if (k == "heavy") ctx->tun.heavy = (uint64_t)v;
+                else if (k == "dense_min_u") ctx->tun.dense_min_u = (int)v;
+            }
+            a = b + 1;
+        }
+    }
     if (check_cuda(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "stream")) return MP_ERR_CUDA;
     ctx->alloc.reset(new PoolAlloc());
     if (c.policy != MP_POLICY_NONE) ctx->cache.reset(new CachePolicy((double)c.hbm_budget_bytes, c.policy));
@@ -132,8 +153,13 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 if (p && (p = strchr(p, ':'))) *v = strtod(p + 1, nullptr);
             };
             double dmu = ctx->tun.dense_min_u, hv = (double)ctx->tun.heavy;
+            double cb = ctx->tun.combine, sw = ctx->tun.short_walk;
             num("\"dense_min_u\"", &dmu);
             num("\"heavy\"", &hv);
+            num("\"combine\"", &cb);
+            num("\"short_walk\"", &sw);
+            ctx->tun.combine = (int)cb;
+            ctx->tun.short_walk = (int)sw;
             num("\"alpha\"", &ctx->cfg.alpha);
             num("\"beta\"", &ctx->cfg.beta);
             num("\"gamma\"", &ctx->cfg.gamma);
@@ -625,6 +651,33 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
                 best_t = ctx->tun;
             }
         }
+    // the split-row kernel variants at the best thresholds
+    for (int v = 0; v < 4 && !rc; v++) {
+        ctx->tun = best_t;
+        ctx->tun.combine = v & 1;
+        ctx->tun.short_walk = (v >> 1) & 1;
+        if (ctx->tun.combine == best_t.combine && ctx->tun.short_walk == best_t.short_walk) continue;
+        std::vector<double> ts;
+        for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
+            std::vector<Query> qs = parsed;
+            std::vector<Result> res(n);
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = ctx->run_batch(qs, res);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (r) ts.push_back(ms);
+        }
+        if (rc) break;
+        std::sort(ts.begin(), ts.end());
+        const double med = ts[ts.size() / 2];
+        char line[200];
+        snprintf(line, sizeof(line), ", {\"combine\": %d, \"short_walk\": %d, \"ms\": %.4f}", ctx->tun.combine,
+                 ctx->tun.short_walk, med);
+        log += line;
+        if (med < best) {
+            best = med;
+            best_t = ctx->tun;
+        }
+    }
     ctx->tun = rc ? base : best_t;
     // Eq. 2 coefficients from per-product times, each query run on its own
     double coef[3] = {ctx->cfg.alpha, ctx->cfg.beta, ctx->cfg.gamma};
@@ -655,10 +708,11 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
     if (out_path) {
         FILE *f = fopen(out_path, "w");
         if (!f) return MP_ERR_ARG;
-        fprintf(f, "{\"dense_min_u\": %d, \"heavy\": %llu, \"alpha\": %.9g, \"beta\": %.9g, \"gamma\": %.9g, "
-                   "\"fitted\": %s, \"best_ms\": %.4f, \"candidates\": [%s]}\n",
-                ctx->tun.dense_min_u, (unsigned long long)ctx->tun.heavy, coef[0], coef[1], coef[2],
-                fitted ? "true" : "false", best, log.c_str());
+        fprintf(f, "{\"dense_min_u\": %d, \"heavy\": %llu, \"combine\": %d, \"short_walk\": %d, "
+                   "\"alpha\": %.9g, \"beta\": %.9g, \"gamma\": %.9g, \"fitted\": %s, \"best_ms\": %.4f, "
+                   "\"candidates\": [%s]}\n",
+                ctx->tun.dense_min_u, (unsigned long long)ctx->tun.heavy, ctx->tun.combine, ctx->tun.short_walk,
+                coef[0], coef[1], coef[2], fitted ? "true" : "false", best, log.c_str());
         fclose(f);
     }
     return MP_OK;

@@ -40,6 +40,9 @@ struct Tuning {
     int dense_min_u = 256;       // ... and a row bound of at least this many entries
     int force_class = -1;        // -1 auto, else MP_BIN_* class
     uint64_t heavy = 65536;      // rows with more Gustavson products go to GLOBAL
+    uint64_t warp_prod = 4096;   // rows with more products skip the one-warp bins
+    int combine = 1;             // split-row kernel: shared-memory combining of hot outputs
+    int short_walk = 1;          // split-row kernel: one thread per X entry on short Y rows
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     int sm_count = 148;
 };

@@ -73,7 +73,7 @@ struct PStat {
 
 struct BinArgs {
     int dense_max_cols, dense_min_u, force;
-    uint64_t heavy;
+    uint64_t heavy, warp_prod;
 };
 
 // Per-bin tallies of one pass over the wave: rows, X entries, Gustavson products, output
@@ -215,7 +215,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
             s = prod[g];
             if (s) {
                 const int64_t i = g - P.row0;
-                b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.force);
+                b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.warp_prod, ba.force);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
                 atomicAdd(&hc[b], 1u);
                 atomicAdd(&hx[b], xe);
@@ -271,7 +271,8 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                 if (bin[g] == B_GLOBAL) {
                     b = B_GLOBAL;
                 } else {
-                    b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.force);
+                    b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.warp_prod,
+                                ba.force);
                     if (b == B_GLOBAL) atomicOr(&ps[pi].err, ERR_PROBE);  // cannot happen: nnz <= the bound
                 }
                 const int64_t i = g - P.row0;
@@ -627,6 +628,7 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
 static constexpr int64_t PCH = 16384;  // Gustavson products per work item
 static constexpr int GNT = 256;        // threads per GLOBAL block
 static constexpr int RW = 8;           // bitmap words per thread in the rank pass
+static constexpr int CSLOT = 1024;     // shared-memory combining slots per work item
 
 struct GlobArgs {
     const uint32_t *list;     // wave rows of the GLOBAL bin, in symbolic order
@@ -637,6 +639,7 @@ struct GlobArgs {
     int64_t r0, r1;           // rows of this round
     uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
     int64_t nw;               // slot size (words)
+    int short_walk;           // walk chunks of short Y rows one X entry per thread
 };
 
 // Per GLOBAL row: its X entry count and its number of work items.
@@ -671,11 +674,20 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // One work item per block iteration: products [s0, s1) of one row. The X entries that hold
 // them are staged GNT at a time with their product offsets (from xoff); consecutive
 // threads take consecutive products, so a long Y row is read coalesced.
-template <bool NUM>
+template <bool NUM, bool COMB>
 __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
+    // combining table for the item's hot outputs: key = bitmap word (symbolic) or output
+    // column (numeric); first come claims a slot, other keys go straight to global memory
+    __shared__ uint32_t s_key[CSLOT];
+    __shared__ unsigned long long s_acc[CSLOT];
+    for (int x = threadIdx.x; x < CSLOT; x += GNT) {
+        s_key[x] = EMPTY;
+        s_acc[x] = 0;
+    }
+    __syncthreads();
     const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
     for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         int64_t lo = g.r0, hi = g.r1 - 1;
@@ -729,20 +741,42 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
             auto product = [&](int l, int64_t q) {
                 const uint32_t j = (uint32_t)__ldg(yci + q);
                 if (!bit_of(cm, j)) return;
+                unsigned long long add;
                 if (!NUM) {
-                    atomicOr(bm + (j >> 5), 1u << (j & 31));
+                    add = 1ull << (j & 31);
                 } else {
                     const uint64_t av = s_a[l];
                     const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
-                    const uint64_t v2 = av * bv;
+                    add = av * bv;
                     if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+                }
+                const uint32_t k = NUM ? j : (j >> 5);
+                const uint32_t slot = (k * 0x9E3779B1u) >> (32 - 10);
+                uint32_t cur = EMPTY - 1;
+                if (COMB) {
+                    cur = ((volatile uint32_t *)s_key)[slot];
+                    if (cur == EMPTY) {
+                        const uint32_t old = atomicCAS(s_key + slot, EMPTY, k);
+                        cur = old == EMPTY ? k : old;
+                    }
+                }
+                if (COMB && cur == k) {
+                    if (!NUM) {
+                        atomicOr((unsigned int *)&s_acc[slot], (unsigned int)add);
+                    } else {
+                        const unsigned long long old = atomicAdd(s_acc + slot, add);
+                        if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                    }
+                } else if (!NUM) {
+                    atomicOr(bm + k, (uint32_t)add);
+                } else {
                     const uint32_t w = j >> 5;
                     const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
-                    const unsigned long long old = atomicAdd(val + pos, (unsigned long long)v2);
-                    if (old + v2 < old) atomicOr(err, ERR_OVERFLOW);
+                    const unsigned long long old = atomicAdd(val + pos, add);
+                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
                 }
             };
-            if (s_off[nent] <= 8 * (int64_t)nent) {
+            if (g.short_walk && s_off[nent] <= 8 * (int64_t)nent) {
                 // short Y rows: each thread walks the products of its own X entry
                 if ((int)threadIdx.x < nent) {
                     const int l = threadIdx.x;
@@ -763,6 +797,23 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
             }
             __syncthreads();
         }
+        // flush the combining table into the row, reset it for the next item
+        for (int x = threadIdx.x; COMB && x < CSLOT; x += GNT) {
+            const uint32_t k = s_key[x];
+            if (k == EMPTY) continue;
+            if (!NUM) {
+                atomicOr(bm + k, (uint32_t)s_acc[x]);
+            } else {
+                const uint32_t w = k >> 5;
+                const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (k & 31)) - 1u));
+                const unsigned long long v = s_acc[x];
+                const unsigned long long old = atomicAdd(val + pos, v);
+                if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+            }
+            s_key[x] = EMPTY;
+            s_acc[x] = 0;
+        }
+        __syncthreads();
     }
 }
 
@@ -934,18 +985,20 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     for (int64_t r0 = 0; r0 < g.R; r0 += g.per_round) {
         const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bm,
-                          g.rank, g.nw};
+                          g.rank, g.nw, tun.short_walk};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
-            kl(k_glob_set<false>, grid, GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_set<false, true>, grid, GNT, 0, s, a, ga);
+            else kl(k_glob_set<false, false>, grid, GNT, 0, s, a, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
             kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
                s, a, ga);
-            kl(k_glob_set<true>, grid, GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_set<true, true>, grid, GNT, 0, s, a, ga);
+            else kl(k_glob_set<true, false>, grid, GNT, 0, s, a, ga);
         }
     }
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
@@ -994,7 +1047,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_ps = align256(o_row0s + (size_t)(w + 1) * 8);
     const size_t o_small = align256(o_ps + sizeof(PStat) * w);
     const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
-    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy};
+    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod};
     int rc = MP_OK;
     Glob gl;
     PassArgs pa{};

@@ -29,8 +29,9 @@ def test_autotune_persists_and_keeps_results(cuda_ok, tmp_path):
     finally:
         e.close()
     d = json.load(open(path))
-    assert len(d["candidates"]) == 9
+    assert len(d["candidates"]) == 12  # 9 threshold pairs, then 3 more kernel variants
     assert d["dense_min_u"] in (64, 256, 1024) and d["heavy"] in (16384, 65536, 262144)
+    assert d["combine"] in (0, 1) and d["short_walk"] in (0, 1)
     assert min(c["ms"] for c in d["candidates"]) == pytest.approx(d["best_ms"])
     assert d["alpha"] > 0 and d["beta"] > 0 and d["gamma"] > 0
     e2 = mp.Engine(h, policy=mp.MP_POLICY_NONE, tune_file=path)

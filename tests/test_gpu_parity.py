@@ -212,3 +212,20 @@ def test_copy_to_device_buffers(c1, c1_engines):
     np.testing.assert_array_equal(rp.cpu().numpy(), want[0])
     np.testing.assert_array_equal(ci.cpu().numpy(), want[1])
     np.testing.assert_array_equal(val.cpu().numpy().view(np.uint64), want[2])
+
+
+@pytest.mark.parametrize("combine,short_walk", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatch):
+    """The split-row (GLOBAL) kernel's variants -- shared-memory combining of hot outputs
+    on or off, one-thread-per-entry walk of short Y rows on or off -- give identical
+    results."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"combine={combine},short_walk={short_walk}")
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (combine, short_walk, "".join(q["types"])))
+        finally:
+            e.close()
