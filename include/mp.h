@@ -208,8 +208,9 @@ const char *mp_strerror(int code);
  * row-bin thresholds -- the smallest row sent to the dense shared-memory bin and the
  * product count above which a row is split over many blocks -- and keeps the fastest. It
  * then runs each query once and fits the Eq. 2 coefficients alpha, beta, gamma to the
- * measured product times by least squares (Sec. 3.2), so planner costs and recorded cache
- * costs are in milliseconds. The result applies to this context at once and, when
+ * measured product times by least squares (Sec. 3.2), and keeps the fit (costs then in
+ * milliseconds) only if the workload re-timed with it is not slower. Split-row kernel
+ * variants are swept too. The result applies to this context at once and, when
  * out_path is not NULL, is written there as JSON for mp_config.tune_file. *best_ms (may
  * be NULL) receives the best candidate's time per run. Results never change. */
 int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t reps, const char *out_path,

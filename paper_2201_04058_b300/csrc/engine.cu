@@ -652,11 +652,12 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
             }
         }
     // the split-row kernel variants at the best thresholds
+    const int comb0 = best_t.combine, walk0 = best_t.short_walk;
     for (int v = 0; v < 4 && !rc; v++) {
         ctx->tun = best_t;
         ctx->tun.combine = v & 1;
         ctx->tun.short_walk = (v >> 1) & 1;
-        if (ctx->tun.combine == best_t.combine && ctx->tun.short_walk == best_t.short_walk) continue;
+        if (ctx->tun.combine == comb0 && ctx->tun.short_walk == walk0) continue;
         std::vector<double> ts;
         for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
             std::vector<Query> qs = parsed;
@@ -694,11 +695,38 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
         double c[3];
         if (!rc && ctx->fit_samples.size() >= 3 && fit3(ctx->fit_samples, c)) {
             // a cost model with a negative weight would reward work: keep those terms at a floor
-            for (int k = 0; k < 3; k++) coef[k] = c[k] > 1e-12 ? c[k] : 1e-12;
-            ctx->cfg.alpha = coef[0];
-            ctx->cfg.beta = coef[1];
-            ctx->cfg.gamma = coef[2];
-            fitted = true;
+            double fitc[3];
+            for (int k = 0; k < 3; k++) fitc[k] = c[k] > 1e-12 ? c[k] : 1e-12;
+            // keep the fit only if the plans it chooses do not make the workload slower
+            const double old_c[3] = {ctx->cfg.alpha, ctx->cfg.beta, ctx->cfg.gamma};
+            ctx->cfg.alpha = fitc[0];
+            ctx->cfg.beta = fitc[1];
+            ctx->cfg.gamma = fitc[2];
+            std::vector<double> ts;
+            for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
+                std::vector<Query> qs = parsed;
+                std::vector<Result> res(n);
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = ctx->run_batch(qs, res);
+                const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                if (r) ts.push_back(ms);
+            }
+            if (!rc) {
+                std::sort(ts.begin(), ts.end());
+                const double med = ts[ts.size() / 2];
+                char line[200];
+                snprintf(line, sizeof(line), ", {\"fitted_eq2\": true, \"ms\": %.4f}", med);
+                log += line;
+                if (med <= best) {
+                    best = med;
+                    for (int k = 0; k < 3; k++) coef[k] = fitc[k];
+                    fitted = true;
+                } else {
+                    ctx->cfg.alpha = old_c[0];
+                    ctx->cfg.beta = old_c[1];
+                    ctx->cfg.gamma = old_c[2];
+                }
+            }
         }
         ctx->fit_samples.clear();
     }

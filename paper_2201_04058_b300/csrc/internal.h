@@ -42,7 +42,7 @@ struct Tuning {
     uint64_t heavy = 65536;      // rows with more Gustavson products go to GLOBAL
     uint64_t warp_prod = 4096;   // rows with more products skip the one-warp bins
     int combine = 1;             // split-row kernel: shared-memory combining of hot outputs
-    int short_walk = 1;          // split-row kernel: one thread per X entry on short Y rows
+    int short_walk = 0;          // split-row kernel: one thread per X entry on short Y rows
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     int sm_count = 148;
 };
