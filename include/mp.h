@@ -123,6 +123,14 @@ int mp_add_relation(mp_ctx *ctx, int32_t src_type, int32_t dst_type, uint64_t n_
 /* Build the device CSR of every relation and upload properties. No adds after this. */
 int mp_finalize_hin(mp_ctx *ctx);
 
+/* Save a finalised context's HIN (node types, properties, every relation's CSR in both
+ * directions) to a binary file, and load one into a fresh context instead of the
+ * mp_add_* calls; mp_finalize_hin then uploads it without rebuilding the CSRs.
+ * Errors: MP_ERR_STATE (save before finalize, load into a non-empty context),
+ * MP_ERR_NOTFOUND (no file), MP_ERR_ARG (unreadable or malformed file). */
+int mp_hin_save(mp_ctx *ctx, const char *path);
+int mp_hin_load(mp_ctx *ctx, const char *path);
+
 /* Look-ups by name. */
 int mp_type_id(mp_ctx *ctx, const char *name, int32_t *type_id);
 int mp_property_id(mp_ctx *ctx, int32_t type_id, const char *prop, int32_t *prop_id);

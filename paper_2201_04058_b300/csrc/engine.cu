@@ -35,9 +35,13 @@ using Result = mp_ctx::Result;
 namespace mp {
 
 struct PoolAlloc final : Alloc {
-    size_t live = 0;
+    // failure injection for tests: after this many more successful allocations, every
+    // allocation fails (UINT64_MAX = never)
+    uint64_t fail_after = UINT64_MAX;
     void *alloc(size_t bytes, cudaStream_t s) override {
         void *p = nullptr;
+        if (fail_after == 0) return nullptr;
+        if (fail_after != UINT64_MAX) fail_after--;
         if (bytes == 0) bytes = 16;
         if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
             cudaGetLastError();
@@ -135,6 +139,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "warp_prod") ctx->tun.warp_prod = (uint64_t)v;
                 else if (k == "heavy") ctx->tun.heavy = (uint64_t)v;
                 else if (k == "dense_min_u") ctx->tun.dense_min_u = (int)v;
+                else if (k == "fail_alloc_after_finalize") ctx->fail_alloc_after = (uint64_t)v;
             }
             a = b + 1;
         }
@@ -283,14 +288,19 @@ extern "C" int mp_finalize_hin(mp_ctx *ctx) {
     cudaStream_t s = ctx->stream;
     for (size_t r = 0; r < ctx->rels.size(); r += 2) {
         auto &f = ctx->rels[r];
-        auto &b = ctx->rels[r + 1];
         for (int dir = 0; dir < 2; dir++) {
-            auto &R = dir == 0 ? f : b;
+            auto &R = ctx->rels[r + dir];
             const uint32_t nr = ctx->types[R.src].count, nc = ctx->types[R.dst].count;
             std::vector<int64_t> rp;
             std::vector<int32_t> ci;
-            if (dir == 0) build_csr(f.s, f.d, nr, rp, ci);
-            else build_csr(f.d, f.s, nr, rp, ci);
+            if (!R.hrp.empty()) {  // loaded from a saved HIN
+                rp.swap(R.hrp);
+                ci.swap(R.hci);
+            } else if (dir == 0) {
+                build_csr(f.s, f.d, nr, rp, ci);
+            } else {
+                build_csr(f.d, f.s, nr, rp, ci);
+            }
             Mat &m = R.dev;
             m.nrows = nr;
             m.ncols = nc;
@@ -319,6 +329,103 @@ extern "C" int mp_finalize_hin(mp_ctx *ctx) {
     }
     if (check_cuda(cudaStreamSynchronize(s), "upload")) return MP_ERR_CUDA;
     ctx->finalized = true;
+    if (ctx->fail_alloc_after != UINT64_MAX) static_cast<PoolAlloc *>(ctx->alloc.get())->fail_after = ctx->fail_alloc_after;
+    return MP_OK;
+}
+
+// ---- saved HINs: "MPHIN1", then node types, properties and every relation's CSR (both
+// directions), all little-endian
+static bool wr(FILE *f, const void *p, size_t n) { return fwrite(p, 1, n, f) == n; }
+static bool rd(FILE *f, void *p, size_t n) { return fread(p, 1, n, f) == n; }
+
+extern "C" int mp_hin_save(mp_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> ge(ctx->exec_mu);
+    if (!ctx->finalized) return MP_ERR_STATE;
+    cudaSetDevice(ctx->cfg.device);
+    FILE *f = fopen(path, "wb");
+    if (!f) return MP_ERR_ARG;
+    bool ok = wr(f, "MPHIN1", 6);
+    uint64_t n = ctx->types.size();
+    ok = ok && wr(f, &n, 8);
+    for (auto &t : ctx->types) {
+        uint64_t l = t.name.size();
+        ok = ok && wr(f, &l, 8) && wr(f, t.name.data(), l) && wr(f, &t.count, 4);
+    }
+    n = ctx->props.size();
+    ok = ok && wr(f, &n, 8);
+    for (auto &p : ctx->props) {
+        uint64_t l = p.name.size();
+        ok = ok && wr(f, &p.type, 4) && wr(f, &l, 8) && wr(f, p.name.data(), l) &&
+             wr(f, p.host.data(), p.host.size() * 4);
+    }
+    n = ctx->rels.size();
+    ok = ok && wr(f, &n, 8);
+    for (auto &r : ctx->rels) {
+        const Mat &m = r.dev;
+        std::vector<int64_t> rp((size_t)m.nrows + 1);
+        std::vector<int32_t> ci((size_t)m.nnz);
+        if (cudaMemcpy(rp.data(), m.rp, rp.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (m.nnz && cudaMemcpy(ci.data(), m.ci, ci.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            fclose(f);
+            return MP_ERR_CUDA;
+        }
+        const int64_t nnz = m.nnz;
+        ok = ok && wr(f, &r.src, 4) && wr(f, &r.dst, 4) && wr(f, &nnz, 8) && wr(f, rp.data(), rp.size() * 8) &&
+             wr(f, ci.data(), ci.size() * 4);
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? MP_OK : MP_ERR_ARG;
+}
+
+extern "C" int mp_hin_load(mp_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->finalized || !ctx->types.empty() || !ctx->rels.empty()) return MP_ERR_STATE;
+    FILE *f = fopen(path, "rb");
+    if (!f) return MP_ERR_NOTFOUND;
+    char magic[6];
+    bool ok = rd(f, magic, 6) && memcmp(magic, "MPHIN1", 6) == 0;
+    uint64_t n = 0;
+    ok = ok && rd(f, &n, 8) && n < (1u << 20);
+    for (uint64_t i = 0; ok && i < n; i++) {
+        uint64_t l = 0;
+        ok = rd(f, &l, 8) && l < 4096;
+        std::string name(ok ? l : 0, ' ');
+        uint32_t cnt = 0;
+        ok = ok && rd(f, &name[0], l) && rd(f, &cnt, 4);
+        if (ok) ctx->types.push_back({name, cnt});
+    }
+    ok = ok && rd(f, &n, 8) && n < (1u << 20);
+    for (uint64_t i = 0; ok && i < n; i++) {
+        mp_ctx::Prop p;
+        uint64_t l = 0;
+        ok = rd(f, &p.type, 4) && p.type >= 0 && p.type < (int)ctx->types.size() && rd(f, &l, 8) && l < 4096;
+        if (!ok) break;
+        p.name.assign(l, ' ');
+        p.host.resize(ctx->types[p.type].count);
+        ok = rd(f, &p.name[0], l) && rd(f, p.host.data(), p.host.size() * 4);
+        if (ok) ctx->props.push_back(std::move(p));
+    }
+    ok = ok && rd(f, &n, 8) && n % 2 == 0 && n < (1u << 20);
+    for (uint64_t i = 0; ok && i < n; i++) {
+        mp_ctx::Rel r;
+        int64_t nnz = 0;
+        ok = rd(f, &r.src, 4) && rd(f, &r.dst, 4) && r.src >= 0 && r.dst >= 0 && r.src < (int)ctx->types.size() &&
+             r.dst < (int)ctx->types.size() && rd(f, &nnz, 8) && nnz >= 0;
+        if (!ok) break;
+        r.hrp.resize((size_t)ctx->types[r.src].count + 1);
+        r.hci.resize((size_t)nnz);
+        ok = rd(f, r.hrp.data(), r.hrp.size() * 8) && rd(f, r.hci.data(), r.hci.size() * 4) && r.hrp.back() == nnz;
+        if (ok) ctx->rels.push_back(std::move(r));
+    }
+    fclose(f);
+    if (!ok) {
+        ctx->types.clear();
+        ctx->props.clear();
+        ctx->rels.clear();
+        return MP_ERR_ARG;
+    }
     return MP_OK;
 }
 

@@ -47,6 +47,8 @@ struct mp_ctx {
     struct Rel {
         int32_t src = -1, dst = -1;
         std::vector<uint32_t> s, d;  // staged edges (forward relations only), dropped at finalize
+        std::vector<int64_t> hrp;    // CSR read from a saved HIN (both directions), dropped at finalize
+        std::vector<int32_t> hci;
         mp::Mat dev;                 // 0/1 CSR, val == nullptr
     };
     struct Constraint {
@@ -97,6 +99,7 @@ struct mp_ctx {
     std::unordered_map<std::string, double> leaf_memo;
     // per-product samples (nnz(X), N_op, nnz(Z), ms) for the Eq. 2 fit of mp_autotune
     bool collect_fit = false;
+    uint64_t fail_alloc_after = UINT64_MAX;  // test hook: allocations allowed after finalize
     std::vector<std::array<double, 4>> fit_samples;
     std::vector<NodeType> types;
     std::vector<Prop> props;

@@ -73,7 +73,11 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
             if (!prop) {
                 uint32_t *tmp = (uint32_t *)alloc->alloc(std::max<size_t>(nw, 1) * 4, stream);
                 uint32_t *dset = (uint32_t *)alloc->alloc(std::max<int64_t>(len, 1) * 4, stream);
-                if (!tmp || !dset) return MP_ERR_NOMEM;
+                if (!tmp || !dset) {
+                    if (tmp) alloc->free(tmp, stream);
+                    if (dset) alloc->free(dset, stream);
+                    return MP_ERR_NOMEM;
+                }
                 if (len) cudaMemcpyAsync(dset, c.set.data(), len * 4, cudaMemcpyHostToDevice, stream);
                 mask_and_set(m, tmp, dset, len, cnt, stream);
                 alloc->free(tmp, stream);
@@ -137,6 +141,14 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     std::vector<std::vector<uint32_t *>> masks(nq);
     std::vector<int> qstatus(nq, MP_OK);
     for (size_t q = 0; q < nq; q++) qstatus[q] = build_masks(qs[q], masks[q]);
+    // a batch-wide failure before the products run: every query reports it, nothing leaks
+    auto fail_all = [&](int rc) {
+        for (size_t q = 0; q < nq; q++) rs[q].status = qstatus[q] ? qstatus[q] : rc;
+        for (auto &m : masks) free_masks(m);
+        cudaEventRecord(ev1, stream);
+        cudaEventSynchronize(ev1);
+        return rc;
+    };
 
     // exact nnz of every masked base factor, for the planner: one device array, one sync;
     // counts already seen (same relation, same constraints at both ends) come from a memo
@@ -145,9 +157,13 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         size_t total = 0;
         for (auto &q : qs) total += q.rels.size();
         unsigned long long *d = (unsigned long long *)alloc->alloc(std::max<size_t>(total, 1) * 8, stream);
-        if (!d) return MP_ERR_NOMEM;
+        if (!d) return fail_all(MP_ERR_NOMEM);
         cudaMemsetAsync(d, 0, std::max<size_t>(total, 1) * 8, stream);
         std::vector<void *> tmp;
+        auto free_tmp = [&] {
+            for (void *x : tmp) alloc->free(x, stream);
+            alloc->free(d, stream);
+        };
         std::vector<std::string> keys(total);
         std::unordered_map<std::string, size_t> first;  // key -> slot counted in this batch
         size_t off = 0;
@@ -168,7 +184,10 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 if (first.count(key)) continue;
                 first.emplace(key, off + t);
                 uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
-                if (!lr) return MP_ERR_NOMEM;
+                if (!lr) {
+                    free_tmp();
+                    return fail_all(MP_ERR_NOMEM);
+                }
                 cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
                 masked_nnz(A.view(), masks[q][t], masks[q][t + 1], d + off + t, lr, lr + A.nrows, stream);
                 tmp.push_back(lr);
@@ -179,10 +198,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         std::vector<unsigned long long> h(std::max<size_t>(total, 1), 0);
         if (any) {
             cudaMemcpyAsync(h.data(), d, std::max<size_t>(total, 1) * 8, cudaMemcpyDeviceToHost, stream);
-            if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+            if (cudaStreamSynchronize(stream) != cudaSuccess) {
+                free_tmp();
+                return fail_all(MP_ERR_CUDA);
+            }
         }
-        for (void *x : tmp) alloc->free(x, stream);
-        alloc->free(d, stream);
+        free_tmp();
         if (leaf_memo.size() > 65536) leaf_memo.clear();
         for (auto &kv : first) leaf_memo[kv.first] = (double)h[kv.second];
         off = 0;
@@ -213,7 +234,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (!pairs.empty()) {
             const size_t np = pairs.size();
             unsigned long long *d = (unsigned long long *)alloc->alloc(np * 16, stream);
-            if (!d) return MP_ERR_NOMEM;
+            if (!d) return fail_all(MP_ERR_NOMEM);
             cudaMemsetAsync(d, 0, np * 16, stream);  // [active rows, sampled rows] per pair
             for (size_t k = 0; k < np; k++) {
                 const Query &Q = qs[pairs[k].q];
@@ -221,7 +242,10 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             }
             std::vector<unsigned long long> h(2 * np);
             cudaMemcpyAsync(h.data(), d, np * 16, cudaMemcpyDeviceToHost, stream);
-            if (cudaStreamSynchronize(stream) != cudaSuccess) return MP_ERR_CUDA;
+            if (cudaStreamSynchronize(stream) != cudaSuccess) {
+                alloc->free(d, stream);
+                return fail_all(MP_ERR_CUDA);
+            }
             std::vector<uint32_t *> bms(np, nullptr);
             std::vector<WaveIn> win(np);
             const double s_rows = (double)std::max<uint32_t>(cfg.sample_rows, 1);
@@ -232,7 +256,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 const double act = (double)h[2 * k];
                 const uint64_t thr = act <= s_rows ? UINT64_MAX : (uint64_t)(s_rows / act * 18446744073709551615.0);
                 bms[k] = (uint32_t *)alloc->alloc((size_t)std::max<int64_t>((A.nrows + 31) / 32, 1) * 4, stream);
-                if (!bms[k]) return MP_ERR_NOMEM;
+                if (!bms[k]) {
+                    for (auto *b : bms)
+                        if (b) alloc->free(b, stream);
+                    alloc->free(d, stream);
+                    return fail_all(MP_ERR_NOMEM);
+                }
                 const uint64_t seed = cfg.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(k + 1));
                 sample_rows(A.view(), masks[pairs[k].q][t], seed, thr, bms[k], d + 2 * k + 1, stream);
                 win[k].X = A.view();
@@ -247,7 +276,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             if (cudaStreamSynchronize(stream) != cudaSuccess) rc = MP_ERR_CUDA;
             for (auto *b : bms) alloc->free(b, stream);
             alloc->free(d, stream);
-            if (rc) return rc;
+            if (rc) return fail_all(rc);
             for (size_t k = 0; k < np; k++) {
                 const Query &Q = qs[pairs[k].q];
                 const int t = pairs[k].t;
@@ -493,6 +522,10 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             release_operands(nd);
         }
     }
+
+    // nodes a failed wave never reached carry its error
+    for (auto &nd : nodes)
+        if (!nd.res && !nd.status) nd.status = wave_rc ? wave_rc : MP_ERR_INTERNAL;
 
     // results, statistics, cache insertion (Sec. 3.4.1) under the replacement policy
     int first = MP_OK;

@@ -32,7 +32,8 @@ EXPORTS = [
     "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
-    "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune",
+    "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
+    "mp_hin_load",
 ]
 
 
@@ -99,6 +100,8 @@ def lib():
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
+            "mp_hin_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+            "mp_hin_load": (C.c_int, [C.c_void_p, C.c_char_p]),
             "mp_autotune": (C.c_int, [C.c_void_p, U32, P(mp_query), U32, C.c_char_p, P(C.c_double)]),
             "mp_serve_start": (C.c_int, [C.c_void_p]),
             "mp_serve_stop": (C.c_int, [C.c_void_p]),
@@ -186,6 +189,14 @@ def mp_add_relation(ctx, src_type: int, dst_type: int, src, dst) -> int:
 
 def mp_finalize_hin(ctx):
     _ck(lib().mp_finalize_hin(ctx), "mp_finalize_hin")
+
+
+def mp_hin_save(ctx, path: str):
+    _ck(lib().mp_hin_save(ctx, path.encode()), "mp_hin_save")
+
+
+def mp_hin_load(ctx, path: str):
+    _ck(lib().mp_hin_load(ctx, path.encode()), "mp_hin_load")
 
 
 def mp_type_id(ctx, name: str) -> int:
