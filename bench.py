@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="scholarly", choices=["scholarly", "serving", "batched", "stress"])
-    ap.add_argument("--pool", type=int, default=40, help="template pool of the batched workload")
+    ap.add_argument("--pool", type=int, default=500, help="template pool of the batched workload")
+    ap.add_argument("--anchor-p", type=float, default=0.75,
+                    help="share of batched queries with a first-node entity of interest")
     ap.add_argument("--serve-queries", type=int, default=4000)
     ap.add_argument("--load", type=float, default=1.0, help="arrival rate / plain-path saturation rate")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
@@ -524,8 +526,9 @@ def run_small(args, local):
     torch.cuda.set_device(local)
     hin = gen.config1_hin()
     if args.workload == "batched":
-        qs = gen.batched_queries(seed=3, n=256, pool=args.pool)
-        name = f"batched: 256 queries of length 3-7, Zipf(1.1) over a pool of {args.pool} templates"
+        qs = gen.batched_queries(seed=3, n=256, pool=args.pool, anchor_p=args.anchor_p)
+        name = (f"batched: 256 queries of length 3-7, Zipf(1.1) over a pool of {args.pool} templates, "
+                f"{args.anchor_p:.0%} anchored on one of 16 entities")
     else:
         qs = gen.long_queries(5, 64)
         name = "stress: 64 metapaths of length 7-9 through venues and topics"

@@ -124,9 +124,13 @@ def scholarly_hin(n_p, n_a, n_v, n_t, seed, *, s_author=1.2, s_topic=1.0,
     return {"types": {"P": n_p, "A": n_a, "V": n_v, "T": n_t}, "relations": rels, "props": props}
 
 
+CONFIG1_COUNTS = {"P": 2000, "A": 1500, "V": 50, "T": 200}
+
+
 def config1_hin(seed: int = 1):
     """2,000 papers, 1,500 authors, 50 venues, 200 topics."""
-    return scholarly_hin(2000, 1500, 50, 200, seed)
+    c = CONFIG1_COUNTS
+    return scholarly_hin(c["P"], c["A"], c["V"], c["T"], seed)
 
 
 def config2_hin(seed: int = 2, scale: float = 1.0):
@@ -245,10 +249,15 @@ YEAR_RANGES = ((2000, 2021), (1990, 2010), (2010, 2020), (1980, 2000))
 
 def batched_queries(seed: int = 3, n: int = 256, pool: int = 40, s: float = 1.1,
                     lengths=(3, 7), star=SCHOLARLY_STAR, prop=("P", "year"),
-                    ranges=YEAR_RANGES):
+                    ranges=YEAR_RANGES, anchor_p: float = 0.0, n_anchors: int = 16,
+                    counts=None):
     """n queries drawn Zipf(s) from a seeded pool of templates; a template is a
     schema walk of length in [lengths] plus, with probability 1/2, one year range
-    (from a small set) on every position of the constrained type."""
+    (from a small set) on every position of the constrained type. With probability
+    anchor_p a drawn query also fixes its first node to one of n_anchors seeded
+    entities of that type (an id-equality constraint: the entity of interest of a
+    session, Sec. 4.2); sub-chains away from the first position stay shared. counts
+    gives the node count of each type (default: the 2,000-paper scholarly HIN)."""
     g = stream(seed, 600)
     templates = []
     for _ in range(pool):
@@ -260,7 +269,19 @@ def batched_queries(seed: int = 3, n: int = 256, pool: int = 40, s: float = 1.1,
             cons = _year_on_every(types, prop[0], lo, hi, prop[1])
         templates.append({"types": types, "constraints": cons})
     pick = zipf_sampler(pool, s, stream(seed, 601))(stream(seed, 602), n)
-    return [templates[int(i)] for i in pick]
+    out = [templates[int(i)] for i in pick]
+    if anchor_p > 0.0:
+        ga = stream(seed, 603)
+        counts = dict(counts or CONFIG1_COUNTS)
+        anchors = {t: ga.choice(c, size=min(n_anchors, c), replace=False)
+                   for t, c in counts.items()}
+        for qi, q in enumerate(out):
+            if ga.random() < anchor_p:
+                t = q["types"][0]
+                a = int(anchors[t][int(ga.integers(len(anchors[t])))])
+                out[qi] = {"types": q["types"], "constraints": list(q["constraints"]) +
+                           [{"pos": 0, "prop": None, "op": "eq", "lo": a}]}
+    return out
 
 
 def long_queries(seed: int = 5, n: int = 64):

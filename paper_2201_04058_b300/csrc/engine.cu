@@ -140,6 +140,8 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "heavy") ctx->tun.heavy = (uint64_t)v;
                 else if (k == "dense_min_u") ctx->tun.dense_min_u = (int)v;
                 else if (k == "fail_alloc_after_finalize") ctx->fail_alloc_after = (uint64_t)v;
+                else if (k == "glob_dense") ctx->tun.glob_dense = strtod(kv.c_str() + eq + 1, nullptr);
+                else if (k == "dense_scratch") ctx->tun.dense_scratch_cap = (uint64_t)v;
             }
             a = b + 1;
         }

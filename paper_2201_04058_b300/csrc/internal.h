@@ -44,6 +44,10 @@ struct Tuning {
     int combine = 1;             // split-row kernel: shared-memory combining of hot outputs
     int short_walk = 0;          // split-row kernel: one thread per X entry on short Y rows
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
+    // GLOBAL rows with prod_i >= glob_dense * ncols accumulate their counts in a dense u64
+    // row (one pass gives both the size and the values); 0 turns the dense rows off
+    double glob_dense = 0.5;
+    uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
     int sm_count = 148;
 };
 
@@ -131,9 +135,9 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,
            const Tuning &tun, cudaStream_t s, Mat *out);
 
-// Exclusive scan of n int64 values in[0..n) into out[0..n], out[n] = total. in may
-// alias out.
-void scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s);
+// Exclusive scan of n int64 values into out[0..n] (out[n] = total); in may equal out.
+// MP_ERR_NOMEM (nothing launched) when its partial-sum workspace cannot be allocated.
+int scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s);
 
 // Eq. 1 / Eq. 2 chain planner (planner.cpp).
 struct PlanNode {

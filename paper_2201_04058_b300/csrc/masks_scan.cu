@@ -176,17 +176,19 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int64_t *in, int64_
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = part[nb];
 }
 
-void scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s) {
+int scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s) {
     if (n == 0) {
         cudaMemsetAsync(out, 0, sizeof(int64_t), s);
-        return;
+        return MP_OK;
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *part = (int64_t *)al.alloc((size_t)(nb + 1) * sizeof(int64_t), s);
+    if (!part) return MP_ERR_NOMEM;
     kl(k_scan_tiles, (unsigned)nb, SCAN_T, 0, s, in, n, part);
     kl(k_scan_parts, 1, 1024, 0, s, part, nb);
     kl(k_scan_apply, (unsigned)nb, SCAN_T, 0, s, in, out, n, part, nb);
     al.free(part, s);
+    return MP_OK;
 }
 
 // ------------------------------------------------------------------ length-2 metapaths
@@ -245,7 +247,7 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
     if (!out->rp) return MP_ERR_NOMEM;
     unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(m * 32, 256), (int64_t)tun.sm_count * 32));
     if (m) kl(k_filter_count, g, 256, 0, s, A, rm, cm, out->rp);
-    scan_i64(out->rp, out->rp, m, al, s);
+    if (scan_i64(out->rp, out->rp, m, al, s)) return MP_ERR_NOMEM;
     int64_t nnz = 0;
     CK(cudaMemcpyAsync(&nnz, out->rp + m, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

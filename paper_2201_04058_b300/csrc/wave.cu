@@ -74,16 +74,27 @@ struct PStat {
 struct BinArgs {
     int dense_max_cols, dense_min_u, force;
     uint64_t heavy, warp_prod;
+    double gdense;  // GLOBAL rows with prod_i >= gdense * gcols take a dense row (0 = none)
+    int64_t gcols;  // width of a dense row: the widest output of the wave
 };
+
+// A GLOBAL row that accumulates in a dense u64 row of width gcols: its products are at least
+// gdense times that width, so zeroing and scanning the dense row costs little next to them.
+__device__ __forceinline__ bool glob_dense_row(double gdense, uint64_t prod_i, int64_t gcols) {
+    return gdense > 0.0 && (double)prod_i >= gdense * (double)gcols;
+}
 
 // Per-bin tallies of one pass over the wave: rows, X entries, Gustavson products, output
 // entries and the algorithmic bytes of the bin's kernel.
 struct BinTally {
     uint32_t counts[NBINS];
     unsigned long long xent[NBINS], prods[NBINS], outn[NBINS], bytes[NBINS];
+    uint32_t gdense;  // GLOBAL rows that qualify for a dense row
 };
 
 static constexpr int64_t LONGX = 8192;  // X rows longer than this are summed by all blocks
+// Marks a GLOBAL row with a dense slot between the partition and the numeric binning.
+static constexpr int8_t B_GDENSE = 100;
 
 // ------------------------------------------------------------------ row work + bins
 
@@ -191,7 +202,7 @@ __device__ __forceinline__ void agg_add_u32(uint32_t *counter_base, int key, boo
 // bin. Tallies per bin (for the byte model) and per product (products, rows per bin).
 __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uint64_t *prod, int64_t M, BinArgs ba,
                             int8_t *bin, int64_t *nnz, BinTally *tally, PStat *ps) {
-    __shared__ uint32_t hc[NBINS];
+    __shared__ uint32_t hc[NBINS], hd;
     __shared__ unsigned long long hx[NBINS], hp[NBINS], hb[NBINS];
     constexpr int NP = 8;  // products aggregated in shared memory per chunk of rows
     __shared__ unsigned long long sp[NP];
@@ -201,6 +212,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
         hp[threadIdx.x] = 0;
         hb[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) hd = 0;
     __syncthreads();
     for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < M; g0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = g0 + threadIdx.x;
@@ -218,6 +230,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
                 b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.warp_prod, ba.force);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
                 atomicAdd(&hc[b], 1u);
+                if (b == B_GLOBAL && glob_dense_row(ba.gdense, s, ba.gcols)) atomicAdd(&hd, 1u);
                 atomicAdd(&hx[b], xe);
                 atomicAdd(&hp[b], (unsigned long long)s);
                 // symbolic bytes: X row pointers + nnz write, per X entry its column id and the
@@ -244,6 +257,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
         atomicAdd(tally->prods + t, hp[t]);
         atomicAdd(tally->bytes + t, hb[t]);
     }
+    if (t == 0 && hd) atomicAdd(&tally->gdense, hd);
 }
 
 // Numeric bins from the exact row sizes (grp = wave row pointers); rows the symbolic pass
@@ -267,8 +281,9 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
             pi = rowprod[g];
             const Prod &P = prods[pi];
             const int64_t z = P.ci ? grp[g + 1] - grp[g] : 0;  // no outputs: product failed
+            const bool dense = bin[g] == B_GDENSE;
             if (z) {
-                if (bin[g] == B_GLOBAL) {
+                if (bin[g] == B_GLOBAL || dense) {
                     b = B_GLOBAL;
                 } else {
                     b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.warp_prod,
@@ -283,9 +298,13 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                 atomicAdd(&hp[b], pr);
                 atomicAdd(&ho[b], (unsigned long long)z);
                 // numeric bytes: X and C row pointers, per X entry its column id (+ value) and
-                // two Y row pointers, per product a Y column id (+ value), per output 12 bytes
-                atomicAdd(&hb[b], 32ull + xe * (20ull + (P.X.val ? 8ull : 0ull)) +
-                                      pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 12ull);
+                // two Y row pointers, per product a Y column id (+ value), per output 12 bytes;
+                // a dense row gathered in the symbolic pass only reads its counts and writes
+                if (dense)
+                    atomicAdd(&hb[b], 16ull + (unsigned long long)z * 20ull);
+                else
+                    atomicAdd(&hb[b], 32ull + xe * (20ull + (P.X.val ? 8ull : 0ull)) +
+                                          pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 12ull);
             }
             bin[g] = (int8_t)b;
         }
@@ -640,7 +659,35 @@ struct GlobArgs {
     uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
     int64_t nw;               // slot size (words)
     int short_walk;           // walk chunks of short Y rows one X entry per thread
+    unsigned long long *dval; // dense rows: (r1 - r0) slots of dcols counts each
+    int64_t dcols;
 };
+
+// Dense-row GLOBAL rows first: the rows that qualify go to the front of dst (in any order),
+// the others to the back. cnt (two counters) starts at zero. The first nd front rows take
+// dense slots: their bin is marked B_GDENSE until the numeric binning, and the symbolic
+// pass's byte tally gains the X and Y values they read there.
+__global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const uint32_t *src, int64_t R,
+                             const uint64_t *prod, double gdense, int64_t gcols, int64_t nd, uint32_t *dst,
+                             uint32_t *cnt, int8_t *bin, BinTally *tally) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t gr = src[r];
+        if (!glob_dense_row(gdense, prod[gr], gcols)) {
+            dst[R - 1 - atomicAdd(cnt + 1, 1u)] = gr;
+            continue;
+        }
+        const uint32_t pos = atomicAdd(cnt, 1u);
+        dst[pos] = gr;
+        if ((int64_t)pos < nd) {
+            bin[gr] = B_GDENSE;
+            const Prod &P = prods[rowprod[gr]];
+            const int64_t i = gr - P.row0;
+            const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
+            const unsigned long long extra = xe * (P.X.val ? 8ull : 0ull) + prod[gr] * (P.Y.val ? 8ull : 0ull);
+            if (extra) atomicAdd(tally->bytes + B_GLOBAL, extra);
+        }
+    }
+}
 
 // Per GLOBAL row: its X entry count and its number of work items.
 __global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const uint64_t *prod, int64_t *xlen,
@@ -674,8 +721,14 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // One work item per block iteration: products [s0, s1) of one row. The X entries that hold
 // them are staged GNT at a time with their product offsets (from xoff); consecutive
 // threads take consecutive products, so a long Y row is read coalesced.
-template <bool NUM, bool COMB>
-__global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
+// MODE G_SYM sets the row's bitmap bits; G_NUM adds the counts into the output row at the
+// positions the bitmap ranks give; G_DENSE adds the counts into the row's dense slot and
+// sets a column's bitmap bit when its first count lands (every count is >= 1), so one pass
+// gives both the row's size and its values.
+enum { G_SYM = 0, G_NUM = 1, G_DENSE = 2 };
+template <int MODE, bool COMB>
+__global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
+    constexpr bool NUM = MODE != G_SYM;
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
@@ -700,7 +753,7 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
         const int pi = a.rowprod[gr];
         const Prod *PP = a.prods + pi;
         uint64_t *const pval = PP->val;
-        if (NUM && !pval) continue;  // the product failed before its numeric pass
+        if (MODE == G_NUM && !pval) continue;  // the product failed before its numeric pass
         uint32_t *err = &a.ps[pi].err;
         const int64_t row = (int64_t)gr - PP->row0;
         const int32_t *__restrict__ xci = PP->X.ci;
@@ -723,7 +776,9 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
         }
         uint32_t *bm = g.bm + (r - g.r0) * g.nw;
         const uint32_t *rk = g.rank + (r - g.r0) * g.nw;
-        unsigned long long *val = NUM ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0]) : nullptr;
+        unsigned long long *val = MODE == G_NUM    ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0])
+                                  : MODE == G_DENSE ? g.dval + (r - g.r0) * g.dcols
+                                                    : nullptr;
         for (int64_t c0 = xb + plo; c0 < xe; c0 += GNT) {
             const int64_t base = __ldg(xo + (c0 - xb));
             if (base >= s1) break;  // uniform: every thread reads the same base
@@ -769,6 +824,10 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
                     }
                 } else if (!NUM) {
                     atomicOr(bm + k, (uint32_t)add);
+                } else if (MODE == G_DENSE) {
+                    const unsigned long long old = atomicAdd(val + j, add);
+                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                    if (old == 0) atomicOr(bm + (j >> 5), 1u << (j & 31));
                 } else {
                     const uint32_t w = j >> 5;
                     const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
@@ -803,6 +862,11 @@ __global__ void __launch_bounds__(GNT, NUM ? 4 : 8) k_glob_set(PassArgs a, GlobA
             if (k == EMPTY) continue;
             if (!NUM) {
                 atomicOr(bm + k, (uint32_t)s_acc[x]);
+            } else if (MODE == G_DENSE) {
+                const unsigned long long v = s_acc[x];
+                const unsigned long long old = atomicAdd(val + k, v);
+                if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                if (old == 0) atomicOr(bm + (k >> 5), 1u << (k & 31));
             } else {
                 const uint32_t w = k >> 5;
                 const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (k & 31)) - 1u));
@@ -866,6 +930,30 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
             word &= word - 1;
             P.ci[pos] = (int32_t)(w * 32 + b);
             P.val[pos] = 0;
+            pos++;
+        }
+    }
+}
+
+// Dense rows: one thread per bitmap word; the word's set bits become consecutive output
+// entries with their counts from the dense slot.
+__global__ void k_glob_dfill(PassArgs a, GlobArgs g) {
+    const int64_t total = (g.r1 - g.r0) * g.nw;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = g.bm[x];
+        if (!word) continue;
+        const int64_t slot = x / g.nw, w = x - slot * g.nw;
+        const RowRef Rf(a, g.list[g.r0 + slot]);
+        const Prod P = *Rf.P;
+        if (!P.ci) continue;
+        const unsigned long long *dv = g.dval + slot * g.dcols;
+        int64_t pos = Rf.out_off(a) + g.rank[x];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int64_t j = w * 32 + b;
+            P.ci[pos] = (int32_t)j;
+            P.val[pos] = dv[j];
             pos++;
         }
     }
@@ -959,13 +1047,17 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// State of the GLOBAL bin of one wave across its two passes.
+// State of the GLOBAL bin of one wave across its two passes. Rows [0, nd) of list take
+// dense slots (one pass in the symbolic phase, a fill in the numeric phase); rows
+// [nd, R) take bitmap rounds.
 struct Glob {
-    int64_t R = 0, nw = 0, per_round = 0, rounds = 0;
-    uint32_t *list = nullptr;  // copy of the bin's rows in symbolic order
+    int64_t R = 0, nw = 0, per_round = 0, rounds = 0, nd = 0, dcols = 0;
+    uint32_t *list = nullptr;  // the bin's rows, dense-row candidates first
     int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr;
     const uint64_t *prod = nullptr;
     uint32_t *bm = nullptr, *rank = nullptr;
+    uint32_t *dbm = nullptr, *drank = nullptr;
+    unsigned long long *dval = nullptr;
     bool kept = false;         // bitmaps of a single round survive into the numeric pass
 };
 
@@ -976,6 +1068,9 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.xoff) al.free(g.xoff, s);
     if (g.bm) al.free(g.bm, s);
     if (g.rank) al.free(g.rank, s);
+    if (g.dbm) al.free(g.dbm, s);
+    if (g.drank) al.free(g.drank, s);
+    if (g.dval) al.free(g.dval, s);
     g = Glob{};
 }
 
@@ -983,22 +1078,37 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
 static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, cudaStream_t s, Prof *prof) {
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
-    for (int64_t r0 = 0; r0 < g.R; r0 += g.per_round) {
+    if (g.nd) {
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, 0, g.nd, g.dbm, g.drank, g.nw, tun.short_walk,
+                          g.dval, g.dcols};
+        const int64_t words = g.nd * g.nw;
+        if (pass == 0) {
+            cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
+            cudaMemsetAsync(g.dbm, 0, (size_t)words * 4, s);
+            if (tun.combine) kl(k_glob_set<G_DENSE, true>, grid, GNT, 0, s, a, ga);
+            else kl(k_glob_set<G_DENSE, false>, grid, GNT, 0, s, a, ga);
+            kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
+        } else {
+            kl(k_glob_dfill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256,
+               0, s, a, ga);
+        }
+    }
+    for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
         const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bm,
-                          g.rank, g.nw, tun.short_walk};
+                          g.rank, g.nw, tun.short_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
-            if (tun.combine) kl(k_glob_set<false, true>, grid, GNT, 0, s, a, ga);
-            else kl(k_glob_set<false, false>, grid, GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_set<G_SYM, true>, grid, GNT, 0, s, a, ga);
+            else kl(k_glob_set<G_SYM, false>, grid, GNT, 0, s, a, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
             kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
                s, a, ga);
-            if (tun.combine) kl(k_glob_set<true, true>, grid, GNT, 0, s, a, ga);
-            else kl(k_glob_set<true, false>, grid, GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_set<G_NUM, true>, grid, GNT, 0, s, a, ga);
+            else kl(k_glob_set<G_NUM, false>, grid, GNT, 0, s, a, ga);
         }
     }
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
@@ -1047,7 +1157,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_ps = align256(o_row0s + (size_t)(w + 1) * 8);
     const size_t o_small = align256(o_ps + sizeof(PStat) * w);
     const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
-    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod};
+    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod, tun.glob_dense,
+                     max_cols};
     int rc = MP_OK;
     Glob gl;
     PassArgs pa{};
@@ -1118,9 +1229,15 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     gl.R = h_sym.tally.counts[B_GLOBAL];
     if (gl.R) {
         gl.nw = (max_cols + 31) / 32;
+        // dense rows: as many of the qualifying rows as the dense scratch holds at once
+        const int64_t nd_all = std::min<int64_t>(gl.R, (int64_t)h_sym.tally.gdense);
+        gl.dcols = max_cols;
+        const uint64_t dslot = (uint64_t)gl.dcols * 8 + (uint64_t)gl.nw * 8;
+        gl.nd = std::min<int64_t>(nd_all, (int64_t)(tun.dense_scratch_cap / dslot));
+        const int64_t rb = gl.R - gl.nd;
         const uint64_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
-        gl.per_round = std::max<int64_t>(1, std::min<int64_t>(gl.R, (int64_t)(cap / ((uint64_t)gl.nw * 8))));
-        gl.rounds = (gl.R + gl.per_round - 1) / gl.per_round;
+        gl.per_round = rb ? std::max<int64_t>(1, std::min<int64_t>(rb, (int64_t)(cap / ((uint64_t)gl.nw * 8)))) : 0;
+        gl.rounds = rb ? (rb + gl.per_round - 1) / gl.per_round : 0;
         gl.kept = gl.rounds == 1;
         const int64_t xtot = (int64_t)h_sym.tally.xent[B_GLOBAL];
         gl.prod = prod;
@@ -1128,27 +1245,47 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xoff = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
-        gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
-        gl.rank = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
-        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff || !gl.bm || !gl.rank) return fail(MP_ERR_NOMEM);
-        if (!cuda_ok(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4,
-                                     cudaMemcpyDeviceToDevice, s), "copy"))
+        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff) return fail(MP_ERR_NOMEM);
+        if (rb) {
+            gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
+            gl.rank = (uint32_t *)al.alloc((size_t)(gl.per_round * gl.nw + 2) * 4, s);
+            if (!gl.bm || !gl.rank) return fail(MP_ERR_NOMEM);
+        }
+        if (gl.nd) {
+            gl.dbm = (uint32_t *)al.alloc((size_t)gl.nd * gl.nw * 4, s);
+            gl.drank = (uint32_t *)al.alloc((size_t)(gl.nd * gl.nw + 2) * 4, s);
+            gl.dval = (unsigned long long *)al.alloc((size_t)gl.nd * gl.dcols * 8, s);
+            if (!gl.dbm || !gl.drank || !gl.dval) return fail(MP_ERR_NOMEM);
+        }
+        if (nd_all) {
+            // qualifying rows first (the two counters live in the rank buffer's first
+            // words, allocated with two spare words, until the partition is done)
+            uint32_t *cnt = gl.nd ? gl.drank : gl.rank;
+            if (!cuda_ok(cudaMemsetAsync(cnt, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
+            kl(k_glob_split, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s,
+               (const Prod *)dprods, (const int32_t *)rowprod, (const uint32_t *)(list + h_sym.offsets[B_GLOBAL]),
+               gl.R, (const uint64_t *)prod, tun.glob_dense, max_cols, gl.nd, gl.list, cnt, bin, &sm_sym->tally);
+        } else if (!cuda_ok(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4,
+                                            cudaMemcpyDeviceToDevice, s), "copy")) {
             return fail(MP_ERR_CUDA);
+        }
         kl(k_glob_prep, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, pa, gl.list, gl.R, prod,
            gl.xbase, gl.item_off);
-        scan_i64(gl.item_off, gl.item_off, gl.R, al, s);
-        scan_i64(gl.xbase, gl.xbase, gl.R, al, s);
+        if (scan_i64(gl.item_off, gl.item_off, gl.R, al, s) || scan_i64(gl.xbase, gl.xbase, gl.R, al, s))
+            return fail(MP_ERR_NOMEM);
         kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(xtot, 256), (int64_t)tun.sm_count * 16)),
            256, 0, s, pa, gl.list, gl.R, gl.xbase, gl.xoff);
-        scan_i64(gl.xoff, gl.xoff, xtot, al, s);
+        if (scan_i64(gl.xoff, gl.xoff, xtot, al, s)) return fail(MP_ERR_NOMEM);
     }
     // 2-3. symbolic pass, wave row pointers, per-product row pointers and sizes
     if (M > 0) run_pass(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof);
     if (gl.R) glob_pass(0, gl, pa, tun, s, prof);
-    scan_i64(grp, grp, M, al, s);
+    if (scan_i64(grp, grp, M, al, s)) return fail(MP_ERR_NOMEM);
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
                   dprods, rowprod, grp, M, ps);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
+        !cuda_ok(cudaMemcpyAsync(h_sym.tally.bytes, sm_sym->tally.bytes, sizeof(h_sym.tally.bytes),
+                                 cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaStreamSynchronize(s), "sync"))
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);

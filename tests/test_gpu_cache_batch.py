@@ -21,7 +21,7 @@ def c1():
 
 @pytest.fixture(scope="module")
 def batch_queries(c1):
-    qs = gen.batched_queries(seed=3, n=64, pool=20)
+    qs = gen.batched_queries(seed=3, n=64, pool=20, anchor_p=0.5)
     return qs, [OC.evaluate(c1[1], q) for q in qs]
 
 

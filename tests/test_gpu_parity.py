@@ -229,3 +229,35 @@ def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatc
                 assert_same(e.run(q), OC.evaluate(o, q), (combine, short_walk, "".join(q["types"])))
         finally:
             e.close()
+
+
+@pytest.mark.parametrize("combine,glob_dense,dense_scratch", [
+    (1, 0, 0),            # dense rows off: every split row takes bitmap rounds
+    (1, 1e-9, 0),         # every split row takes a dense row
+    (0, 1e-9, 0),         # ... without the shared-memory combining table
+    (1, 1e-9, 200000),    # the dense scratch holds a few rows; the rest take bitmap rounds
+    (1, 1e-9, 1),         # no dense row fits: rows qualify, all take bitmap rounds
+    (1, 0.5, 0),          # the default threshold
+])
+def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, monkeypatch):
+    """Split rows that accumulate in a dense u64 row (one pass for size and values, a fill
+    afterwards) give the oracle's results, alone and mixed with bitmap rows when the dense
+    scratch runs out, one query at a time and as one batch. (The overflow test above runs
+    its forced split rows through dense rows under the default threshold.)"""
+    mp = _mp()
+    tune = f"combine={combine},glob_dense={glob_dense}"
+    if dense_scratch:
+        tune += f",dense_scratch={dense_scratch}"
+    monkeypatch.setenv("MP_TUNING", tune)
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (tune, "".join(q["types"])))
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g in zip(qs, res):
+                assert_same(g, OC.evaluate(o, q), (tune, "batch", "".join(q["types"])))
+        finally:
+            e.close()
