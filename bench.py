@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--load", type=float, default=1.0, help="arrival rate / plain-path saturation rate")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--planner", default="eac", choices=list(PLANNERS),
+                    help="chain planner of the scholarly workload (Eq. 1 DP with E_ac, MNC sketches, "
+                         "sampled rows, or left to right)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=5)
     return ap.parse_args()
@@ -89,6 +92,11 @@ def barrier(ws):
 
 
 # ---------------------------------------------------------------- workload
+
+# planner name -> (mp_config.planner value, description)
+PLANNERS = {"eac": (0, "Eq.1 DP, Eq.2 cost, E_ac"), "ltr": (1, "left to right"),
+            "sampled": (2, "Eq.1 DP, Eq.2 cost, sampled-row densities"),
+            "mnc": (3, "Eq.1 DP, Eq.2 cost, MNC count sketches")}
 
 def workload(name, scale):
     import gen
@@ -262,8 +270,9 @@ def run_engine(args, ws, rank, local):
     dist_init(ws, "nccl")
     dev = torch.device("cuda", local)
     hin, qs, cfg = workload(args.workload, args.scale)
+    planner, cfg["planner"] = PLANNERS[args.planner]
     stream = torch.cuda.Stream(device=dev)
-    eng = mp.Engine(hin, device=local, cuda_stream=stream.cuda_stream, policy=mp.MP_POLICY_NONE)
+    eng = mp.Engine(hin, device=local, cuda_stream=stream.cuda_stream, policy=mp.MP_POLICY_NONE, planner=planner)
     bufs = [eng.query(q) for q in qs]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
@@ -283,6 +292,12 @@ def run_engine(args, ws, rank, local):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
+        # planning cost alone: every query of a step planned (sketches, sums, DP) without
+        # running its products
+        t0 = time.perf_counter()
+        for b in bufs:
+            mp.mp_plan_query(eng.ctx, b)
+        plan_ms = 1e3 * (time.perf_counter() - t0) / len(bufs)
 
         # device-timed steps, L2 flushed between them
         mp.mp_kernel_stats_reset(eng.ctx)
@@ -385,6 +400,7 @@ def run_engine(args, ws, rank, local):
            "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
            "config": dict(cfg, parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "plan_ms_per_query": plan_ms,
            "e2e": {"value": ws * n_q * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": sum(query_bytes(q) for q in qs),
                    "d2h_bytes_per_step": d2h[0] // e2e_steps},

@@ -68,13 +68,15 @@ extern "C" {
 #define MP_PLAN_DP 0            /* Eq. 1 DP with the Eq. 2 cost and E_ac densities */
 #define MP_PLAN_LEFT_TO_RIGHT 1 /* ((A1 A2) A3) ... */
 #define MP_PLAN_DP_SAMPLED 2    /* Eq. 1 DP, densities from per-row nnz sampling */
+#define MP_PLAN_DP_MNC 3        /* Eq. 1 DP, result sizes from MNC count sketches */
 
 /* row-bin classes, for mp_config.force_bin_class (tests and the autotuner) */
 #define MP_BIN_AUTO (-1)
 #define MP_BIN_WARP_HASH 0  /* one warp per row, shared-memory hash table */
 #define MP_BIN_BLOCK_HASH 1 /* one block per row, shared-memory hash table */
 #define MP_BIN_DENSE 2      /* one block per row, dense shared-memory accumulator */
-#define MP_BIN_GLOBAL 3     /* one block per row, dense accumulator in global scratch */
+#define MP_BIN_GLOBAL 3     /* split rows: fixed-size work items over all blocks, a bitmap +
+                               rank or a dense count row per row in global scratch */
 
 typedef struct mp_ctx mp_ctx;
 typedef uint64_t mp_ticket;
@@ -246,7 +248,8 @@ int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *in
  * dense, global. ms sums the device time between CUDA events recorded on the launch
  * stream around each launch; bytes sums the algorithmic bytes of the launches (X row
  * pointers, X entries with the two Y row pointers each looks up, one Y column id (and
- * value, numeric pass) per Gustavson product, 12 bytes per output entry). Up to cap
+ * value, in the pass that adds the counts: the numeric pass, or the symbolic pass for
+ * split rows with a dense count row) per Gustavson product, 12 bytes per output entry). Up to cap
  * entries are written; *n receives the number written. *launches receives every kernel
  * launch this library made in the process (all kernels, not only the passes). */
 typedef struct {
@@ -338,6 +341,37 @@ int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_t x_len, co
 int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, double alpha, double beta,
                   double gamma, const double *known_cost, const double *known_rho, const double *rho_fixed,
                   int32_t *split, double *cost);
+
+/* The plan the context's planner (mp_config.planner) makes for one query in the current
+ * cache state, without running any product and without touching the Overlap Tree or the
+ * cache (an "explain"). For a query of p factors, *p_out = p, split (p*p, row-major)
+ * receives the chosen split k of every sub-chain (i, j) (-1 for single factors and known
+ * sub-chains) and nnz (p*p) the planner's size estimate of every sub-chain result (exact
+ * masked nnz on the diagonal). Either array may be NULL. MP_ERR_ARG when p*p > cap (p_out
+ * is still set) or on a NULL ctx, query or p_out; a query's own error otherwise. Blocks
+ * like a query run outside the serving loop. */
+int mp_plan_query(mp_ctx *ctx, const mp_query *q, uint32_t cap, int32_t *split, double *nnz, uint32_t *p_out);
+
+/* The MNC sketch planner alone (host only). Sec. 3.2 compares E_ac with MNC, which
+ * estimates a product's size from count sketches of its operands: per leaf factor t
+ * (dims[t] x dims[t+1]) hr[t] holds its row counts (dims[t] entries), hc[t] its column
+ * counts (dims[t+1]), her[t] per row the entries whose column holds a single entry, and
+ * hec[t] per column the entries whose row holds a single entry (all host arrays, read
+ * only). The estimate of X Y: the product count when every row of X or every column of Y
+ * holds at most one entry; for two leaves, the entries in single-entry rows of X and
+ * single-entry columns of Y counted exactly plus the density map
+ * p (1 - prod_t (1 - c[t] r[t] / p)) over the remaining p cells; otherwise the density
+ * map over (non-empty rows of X) x (non-empty columns of Y). A product's sketch keeps its
+ * left operand's row shape and its right operand's column shape, scaled to the estimate.
+ * known_cost / known_nnz (p*p, NaN = unknown, both NULL = none): known sub-chains, which
+ * enter with a uniform sketch of their size. split (p*p) receives the splits as in
+ * mp_plan_chain; cost and nnz (p*p, may be NULL) the costs (Eq. 1 with the Eq. 2 cost)
+ * and the estimated result sizes. MP_ERR_ARG when p is 0 or a required array is NULL.
+ * (The engine's MP_PLAN_DP_MNC computes the same sketches and sums on the GPU.) */
+int mp_plan_chain_mnc(uint32_t p, const double *dims, const uint32_t *const *hr, const uint32_t *const *hc,
+                      const uint32_t *const *her, const uint32_t *const *hec, double alpha, double beta,
+                      double gamma, const double *known_cost, const double *known_nnz, int32_t *split,
+                      double *cost, double *nnz);
 
 #ifdef __cplusplus
 }

@@ -124,10 +124,11 @@ def propagate(a: Sketch, b: Sketch, s: float) -> Sketch:
     return Sketch(hr, hc)
 
 
-def mnc_plan(dims, leaves, alpha=1.0, beta=1.0, gamma=1.0, known=None):
+def mnc_plan(dims, leaves, alpha=1.0, beta=1.0, gamma=1.0, known=None, totals=None):
     """Eq. 1 over sketches. dims[t], dims[t+1]: sizes of factor t; leaves[t]: its exact
     Sketch; known maps (i, j) -> (cost, nnz) for sub-chains whose result is known.
-    Returns (cost, tree, C, N, S): cost, estimated nnz and split matrices."""
+    Returns (cost, tree, C, N, S): cost, estimated nnz and split matrices. A dict passed
+    as totals receives the total cost of every candidate split, keyed (i, j, k)."""
     p = len(dims) - 1
     known = known or {}
     INF = float("inf")
@@ -156,6 +157,8 @@ def mnc_plan(dims, leaves, alpha=1.0, beta=1.0, gamma=1.0, known=None):
                 ry = y.nnz / (float(n) * l)
                 rz = z / (float(m) * l)
                 total = C[i][k] + C[k + 1][j] + PL.sparse_cost(m, n, l, rx, ry, rz, alpha, beta, gamma)
+                if totals is not None:
+                    totals[(i, j, k)] = total
                 if total < best:
                     best, best_k, best_z = total, k, z
             C[i][j], N[i][j], S[i][j] = best, best_z, best_k

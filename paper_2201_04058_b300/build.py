@@ -8,7 +8,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmp.so")
-SOURCES = ["masks_scan.cu", "wave.cu", "query.cu", "engine.cu", "planner.cpp", "otree.cpp", "sim_abi.cpp", "noalloc.cu"]
+SOURCES = ["masks_scan.cu", "wave.cu", "mnc.cu", "query.cu", "engine.cu", "planner.cpp", "otree.cpp", "sim_abi.cpp",
+           "noalloc.cu"]
 HEADERS = ["internal.h", "engine.h", "otree.h", "common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -92,7 +92,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     *out = nullptr;
     mp_config c;
     if (cfg) c = *cfg; else mp_config_default(&c);
-    if (c.policy < 0 || c.policy > MP_POLICY_NONE || c.planner < 0 || c.planner > MP_PLAN_DP_SAMPLED ||
+    if (c.policy < 0 || c.policy > MP_POLICY_NONE || c.planner < 0 || c.planner > MP_PLAN_DP_MNC ||
         c.force_bin_class < MP_BIN_AUTO || c.force_bin_class > MP_BIN_GLOBAL || c.insertion < MP_INSERT_OTREE ||
         c.insertion > MP_INSERT_ALL)
         return MP_ERR_ARG;
@@ -591,6 +591,32 @@ static int run_now(mp_ctx *ctx, std::vector<Query> &qs, mp_ticket *tickets) {
         ctx->results.emplace(tickets[i], std::move(res[i]));
     }
     return first;
+}
+
+extern "C" int mp_plan_query(mp_ctx *ctx, const mp_query *q, uint32_t cap, int32_t *split, double *nnz,
+                             uint32_t *p_out) {
+    if (!ctx || !q || !p_out) return MP_ERR_ARG;
+    if (!ctx->finalized) return MP_ERR_STATE;
+    std::vector<Query> qs(1);
+    int rc = ctx->parse(q, qs[0]);
+    if (rc) return rc;
+    std::vector<Result> res(1);
+    std::lock_guard<std::mutex> ge(ctx->exec_mu);
+    cudaSetDevice(ctx->cfg.device);
+    ctx->explain = mp_ctx::Explain{};
+    ctx->explain.on = true;
+    rc = ctx->run_batch(qs, res);
+    ctx->explain.on = false;
+    if (rc) return rc;
+    if (res[0].status) return res[0].status;
+    const uint32_t p = (uint32_t)ctx->explain.p;
+    *p_out = p;
+    if ((uint64_t)p * p > cap) return MP_ERR_ARG;
+    for (size_t t = 0; t < (size_t)p * p; t++) {
+        if (split) split[t] = ctx->explain.split[t];
+        if (nnz) nnz[t] = ctx->explain.nnz[t];
+    }
+    return MP_OK;
 }
 
 extern "C" int mp_submit(mp_ctx *ctx, const mp_query *q, mp_ticket *ticket) {

@@ -120,6 +120,14 @@ struct mp_ctx {
     int build_masks(const Query &q, std::vector<uint32_t *> &masks);
     void free_masks(std::vector<uint32_t *> &masks);
     int run_batch(std::vector<Query> &qs, std::vector<Result> &rs);
+    // set by mp_plan_query: run_batch plans its first query, keeps the plan here and runs
+    // no product (and leaves the Overlap Tree and the cache untouched)
+    struct Explain {
+        bool on = false;
+        int p = 0;
+        std::vector<int> split;
+        std::vector<double> nnz;
+    } explain;
     MatPtr wrap(const mp::Mat &m);
     void free_mat(mp::Mat &m);
     void release_result(Result &r);

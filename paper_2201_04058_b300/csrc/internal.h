@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 namespace mp {
@@ -83,6 +84,7 @@ struct Mat {
     int64_t *rp = nullptr;
     int32_t *ci = nullptr;
     uint64_t *val = nullptr;   // nullptr only for base relations
+    uint64_t vmax = 1;         // upper bound on the values (1: 0/1 pattern; UINT64_MAX: none known)
     size_t bytes() const { return (size_t)(nrows + 1) * 8 + (size_t)nnz * 12; }
     DCsr view() const { return DCsr{rp, ci, val, nrows, ncols}; }
 };
@@ -110,6 +112,7 @@ void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned 
 struct WaveIn {
     DCsr X, Y;
     const uint32_t *rm = nullptr, *km = nullptr, *cm = nullptr;
+    uint64_t ymax = 1;  // upper bound on Y's values (Mat::vmax of Y)
 };
 struct WaveOut {
     int status = 0;  // MP_OK, MP_ERR_OVERFLOW, MP_ERR_TOO_LARGE, ...
@@ -149,5 +152,96 @@ struct PlanNode {
 void plan_chain(int p, const double *dims, const double *nnz, double alpha, double beta,
                 double gamma, const double *known_cost, const double *known_rho, const double *rho_fixed,
                 int *split, double *cost_out, double *rho_out);
+
+// MNC sketch planner (planner.cpp): Eq. 1 with the Eq. 2 cost, the result size of every
+// product estimated from count sketches of its operands (MNC, the estimator Sec. 3.2
+// compares E_ac with). Leaves carry exact sketches; a product's sketch keeps its left
+// operand's row shape and its right operand's column shape, scaled to the estimate; a
+// known sub-chain carries a uniform sketch of its exact size.
+struct MncLeaf {     // summary of a leaf's exact sketch (row counts hr, column counts hc)
+    double nnz;      // sum of hr
+    double nzr, maxr, r2;  // rows with hr > 0, max hr, rows with hr >= 2
+    double nzc, maxc, c2;  // the same over columns
+};
+struct MncPair {     // leaf k and leaf k+1 meeting over the node type at position k+1
+    double dot;      // sum_t hc_k[t] hr_k+1[t] (Gustavson products of the leaf product)
+    double known;    // sum hec_k hr_k+1 + sum (hc_k - hec_k) her_k+1 (exactly counted part)
+    double ls_ext;   // sum_t log(1 - (hc_k - hec_k)[t] (hr_k+1 - her_k+1)[t] / p2), -inf if a
+                     // term covers every cell, with p2 = r2_k * c2_k+1 (0 when p2 = 0)
+};
+// The density-map log-sum a DP level asks for: sum_t log(1 - x w[t]) over the inner type
+// of pair `pair`, with w = hc_k hr_k+1 (MNC_W_PAIR), hc_k (MNC_W_COL) or hr_k+1 (MNC_W_ROW).
+enum { MNC_W_PAIR = 0, MNC_W_COL = 1, MNC_W_ROW = 2 };
+struct MncReq {
+    int pair, kind;
+    double x;
+};
+// Device side of the MNC planner (mnc.cu): exact sketches of masked leaf factors, the
+// per-pair sums, and the log-sums a DP level asks for.
+struct MncLeafIn {
+    DCsr A, AT;                   // the factor and its transpose (the reverse relation)
+    const uint32_t *rm, *cm;      // masks of its two end positions (nullptr = none)
+};
+class MncDevice {
+  public:
+    MncDevice(Alloc &al, cudaStream_t s, int sm_count) : al_(al), s_(s), sms_(sm_count) {}
+    ~MncDevice();
+    int leaf(const MncLeafIn &in);   // index of a new leaf (its sketch is built by prepare)
+    int pair(int a, int b);          // leaf a's columns meet leaf b's rows
+    int prepare();                   // builds sketches and pair sums; one sync. MP_* code
+    const MncLeaf &leaf_stat(int i) const { return lstat_[i]; }
+    const MncPair &pair_stat(int i) const { return pstat_[i]; }
+    // ls[r] = sum_t log(1 - x w[t]) for requests whose .pair indexes pairs of this object
+    int eval(const std::vector<MncReq> &req, std::vector<double> &ls);
+  private:
+    struct Leaf {
+        MncLeafIn in;
+        uint32_t *hr = nullptr, *hc = nullptr, *her = nullptr, *hec = nullptr;
+    };
+    Alloc &al_;
+    cudaStream_t s_;
+    int sms_;
+    std::vector<Leaf> leaves_;
+    std::vector<std::pair<int, int>> pairs_;
+    std::vector<MncLeaf> lstat_;
+    std::vector<MncPair> pstat_;
+    unsigned long long *sum_ = nullptr;  // 8 per leaf: row sum, nz, max, >= 2; column the same
+    void *req_ = nullptr;                // device request buffer (and results)
+    size_t req_cap_ = 0;
+};
+
+class MncPlan {
+  public:
+    MncPlan(int p, const double *dims, const MncLeaf *leaves, const MncPair *pairs, double alpha, double beta,
+            double gamma, const double *known_cost, const double *known_nnz);
+    // sub-chains of length len (2..p): first the log-sums they need (appended to out, in
+    // an order resolve() expects back), then resolve() with those sums
+    void requests(int len, std::vector<MncReq> &out);
+    void resolve(int len, const double *ls);
+    int p;
+    std::vector<int> split;            // p*p, -1 for leaves and known sub-chains
+    std::vector<double> cost, nnz;     // p*p
+  private:
+    struct Sk {
+        double nnz;
+        int ra, ca;      // row / column anchor leaf, -1 for a uniform sketch
+        double fr, fc;   // scale of the anchor's counts (a uniform sketch: the value itself)
+        bool exact;
+    };
+    struct Cand {
+        int k;
+        int need;        // index into the level's log-sums, -1 when none is needed
+        double est_fixed, p3;
+        double ls_const; // host log-sum of a uniform-by-uniform product
+    };
+    std::vector<double> dims_;
+    const MncLeaf *leaves_;
+    const MncPair *pairs_;
+    double alpha_, beta_, gamma_;
+    const double *known_cost_, *known_nnz_;
+    std::vector<Sk> sk_;
+    std::vector<std::vector<Cand>> cand_;  // per sub-chain of the current level
+    size_t at(int i, int j) const { return (size_t)i * p + j; }
+};
 
 }  // namespace mp

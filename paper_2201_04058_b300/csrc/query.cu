@@ -17,6 +17,8 @@
 #include <cmath>
 #include <cstdio>
 #include <functional>
+#include <map>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -289,8 +291,43 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         }
     }
 
+    // MNC sketches (MP_PLAN_DP_MNC): one exact sketch per distinct masked leaf, the fixed
+    // sums of every adjacent leaf pair, all in one pass and one sync
+    MncDevice mnc(*alloc, stream, tun.sm_count);
+    std::vector<std::vector<int>> mleaf(nq), mpair(nq);
+    if (cfg.planner == MP_PLAN_DP_MNC) {
+        std::unordered_map<std::string, int> lidx;
+        std::map<std::pair<int, int>, int> pidx;
+        for (size_t q = 0; q < nq; q++) {
+            if (qstatus[q]) continue;
+            const Query &Q = qs[q];
+            const int p = (int)Q.rels.size();
+            mleaf[q].assign(p, -1);
+            mpair[q].assign(p, -1);
+            for (int t = 0; t < p; t++) {
+                const std::string key =
+                    std::to_string(Q.rels[t]) + "|" + Q.pos_keys[t] + "|" + Q.pos_keys[t + 1];
+                auto it = lidx.find(key);
+                if (it == lidx.end()) {
+                    MncLeafIn in{rels[Q.rels[t]].dev.view(), rels[Q.rels[t] ^ 1].dev.view(), masks[q][t],
+                                 masks[q][t + 1]};
+                    it = lidx.emplace(key, mnc.leaf(in)).first;
+                }
+                mleaf[q][t] = it->second;
+            }
+            for (int k = 0; k + 1 < p; k++) {
+                const std::pair<int, int> key(mleaf[q][k], mleaf[q][k + 1]);
+                auto it = pidx.find(key);
+                if (it == pidx.end()) it = pidx.emplace(key, mnc.pair(key.first, key.second)).first;
+                mpair[q][k] = it->second;
+            }
+        }
+        const int rc = mnc.prepare();
+        if (rc) return fail_all(rc);
+    }
+
     // Overlap Tree: every query's metapath and suffixes (Sec. 3.3.2)
-    if (cache)
+    if (cache && !explain.on)
         for (size_t q = 0; q < nq; q++)
             if (!qstatus[q]) otree.insert(qs[q].types, qs[q].pos_keys);
 
@@ -304,6 +341,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         const int n = (int)Q.types.size(), p = n - 1;
         std::vector<double> dims(n);
         for (int t = 0; t < n; t++) dims[t] = (double)types[Q.types[t]].count;
+        if (p == 1 && explain.on) {
+            explain.p = 1;
+            explain.split.assign(1, -1);
+            explain.nnz.assign(1, leaf[q][0] >= 0 ? leaf[q][0] : (double)rels[Q.rels[0]].dev.nnz);
+            return fail_all(MP_OK);
+        }
         if (p == 1) {
             PNode nd;
             nd.id = "filter#" + std::to_string(q);
@@ -349,6 +392,38 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (cfg.planner == MP_PLAN_LEFT_TO_RIGHT) {
             for (int i = 0; i < p; i++)
                 for (int j = i + 1; j < p; j++) split[(size_t)i * p + j] = split_pure[(size_t)i * p + j] = j - 1;
+        } else if (cfg.planner == MP_PLAN_DP_MNC) {
+            // the plan with the known sub-chains and the plan of every sub-chain on its
+            // own, level by level; each level's log-sums in one launch
+            std::vector<MncLeaf> lv(p);
+            std::vector<MncPair> pv(p, MncPair{0, 0, 0});
+            for (int t = 0; t < p; t++) lv[t] = mnc.leaf_stat(mleaf[q][t]);
+            for (int t = 0; t + 1 < p; t++) pv[t] = mnc.pair_stat(mpair[q][t]);
+            std::vector<double> kz((size_t)p * p, NAN);
+            for (int i = 0; i < p; i++)
+                for (int j = i + 1; j < p; j++)
+                    if (!std::isnan(kc[(size_t)i * p + j]))
+                        kz[(size_t)i * p + j] = kr[(size_t)i * p + j] * dims[i] * dims[j + 1];
+            MncPlan known(p, dims.data(), lv.data(), pv.data(), cfg.alpha, cfg.beta, cfg.gamma, kc.data(),
+                          kz.data());
+            MncPlan pure(p, dims.data(), lv.data(), pv.data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr);
+            for (int len = 2; len <= p; len++) {
+                std::vector<MncReq> req;
+                known.requests(len, req);
+                pure.requests(len, req);
+                for (MncReq &r : req) r.pair = mpair[q][r.pair];
+                std::vector<double> ls;
+                const int rc = mnc.eval(req, ls);
+                if (rc) return fail_all(rc);
+                known.resolve(len, ls.data());
+                pure.resolve(len, ls.data());
+            }
+            for (size_t t = 0; t < (size_t)p * p; t++) {
+                split[t] = known.split[t];
+                split_pure[t] = pure.split[t];
+                const int i = (int)(t / p), j = (int)(t % p);
+                D[t] = j >= i ? known.nnz[t] / (dims[i] * dims[j + 1]) : 0.0;
+            }
         } else {
             const double *rf = sampled.empty() ? nullptr : sampled[q].data();
             plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, kc.data(), kr.data(), rf,
@@ -356,6 +431,15 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             // plan of every sub-chain on its own, for known sub-chains that still need computing
             plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr, rf,
                        split_pure.data(), nullptr, nullptr);
+        }
+        if (explain.on) {
+            explain.p = p;
+            explain.split = split;
+            explain.nnz.assign((size_t)p * p, 0.0);
+            for (int i = 0; i < p; i++)
+                for (int j = i; j < p; j++)
+                    explain.nnz[(size_t)i * p + j] = D[(size_t)i * p + j] * dims[i] * dims[j + 1];
+            return fail_all(MP_OK);
         }
         // register nodes bottom-up
         std::function<int(int, int)> reg = [&](int i, int j) -> int {
@@ -478,6 +562,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             WaveIn in;
             in.X = nd.left >= 0 ? nodes[nd.left].res->m.view() : rels[Q.rels[i]].dev.view();
             in.Y = nd.right >= 0 ? nodes[nd.right].res->m.view() : rels[Q.rels[j]].dev.view();
+            in.ymax = nd.right >= 0 ? nodes[nd.right].res->m.vmax : 1;
             // a base factor enters with the masks of its end positions; a node's result
             // already carries them (0/1 diagonals are idempotent)
             in.rm = nd.left < 0 ? M[i] : nullptr;

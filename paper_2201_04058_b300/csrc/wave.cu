@@ -60,12 +60,15 @@ struct Prod {
     int64_t *rp;    // output row pointers (X.nrows + 1)
     int32_t *ci;    // output column ids (after the symbolic pass)
     uint64_t *val;  // output counts
+    uint64_t ymax;  // upper bound on Y's values
 };
 
 // Per-product counters kept on the device.
 struct PStat {
     unsigned long long prods;
     long long nnz;
+    unsigned long long xsmax;  // bits of the largest row sum of X (a non-negative double)
+    uint32_t unsafe;           // some row's sum times ymax reaches 2^63: counts are checked
     uint32_t err;
     uint32_t sym_bins[NBINS];
     uint32_t num_bins[NBINS];
@@ -92,7 +95,8 @@ struct BinTally {
     uint32_t gdense;  // GLOBAL rows that qualify for a dense row
 };
 
-static constexpr int64_t LONGX = 8192;  // X rows longer than this are summed by all blocks
+static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed by several blocks
+static constexpr int64_t LONGCH = 16384; // X entries per block of a long row
 // Marks a GLOBAL row with a dense slot between the partition and the numeric binning.
 static constexpr int8_t B_GDENSE = 100;
 
@@ -113,8 +117,8 @@ __global__ void k_rowprod(const int64_t *row0s, int w, int64_t M, int32_t *rowpr
 // prod_i of every wave row. Each lane takes one of 32 consecutive rows; rows longer than
 // 16 entries are summed by the whole warp, one after the other, and rows longer than
 // LONGX are queued for k_rowwork_long.
-__global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, uint32_t *long_rows,
-                          uint32_t *n_long) {
+__global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, double *xsum,
+                          uint32_t *long_rows, uint32_t *n_long) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -131,14 +135,17 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
             }
         }
         uint64_t s = 0;
+        double xs = 0.0;  // the row's sum of X values: x_ik <= xs bounds every product and sum
         const bool mine = e - b <= 16;
         if (mine && e > b) {
             const int32_t *__restrict__ xci = P->X.ci;
+            const uint64_t *__restrict__ xv = P->X.val;
             const int64_t *__restrict__ yrp = P->Y.rp;
             const uint32_t *__restrict__ km = P->km;
             for (int64_t p = b; p < e; p++) {
                 const int32_t k = __ldg(xci + p);
                 if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(yrp + k + 1) - __ldg(yrp + k));
+                xs += xv ? (double)__ldg(xv + p) : 1.0;
             }
         }
         if (e - b > LONGX) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)g;
@@ -150,41 +157,71 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
             const int32_t pi = __shfl_sync(FULL, g < M ? rowprod[g] : 0, src);
             const Prod &Q = prods[pi];
             uint64_t c = 0;
+            double cx = 0.0;
             for (int64_t p = bb + lane; p < ee; p += 32) {
                 const int32_t k = __ldg(Q.X.ci + p);
                 if (bit_of(Q.km, (uint32_t)k)) c += (uint64_t)(__ldg(Q.Y.rp + k + 1) - __ldg(Q.Y.rp + k));
+                cx += Q.X.val ? (double)__ldg(Q.X.val + p) : 1.0;
             }
-            for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
-            if (lane == src) s = c;
+            for (int d = 16; d; d >>= 1) {
+                c += __shfl_xor_sync(FULL, c, d);
+                cx += __shfl_xor_sync(FULL, cx, d);
+            }
+            if (lane == src) {
+                s = c;
+                xs = cx;
+            }
         }
-        if (g < M) prod[g] = (e - b > LONGX) ? 0 : s;
+        if (g < M) {
+            prod[g] = (e - b > LONGX) ? 0 : s;
+            xsum[g] = (e - b > LONGX) ? 0.0 : xs;
+        }
     }
 }
 
-// The queued long rows: every block takes a strided share of every long row's entries.
-__global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, const uint32_t *long_rows,
-                               const uint32_t *n_long) {
+// The queued long rows: row r is shared by ceil(len / LONGCH) consecutive blocks (modulo
+// the grid) starting at a block that depends on r, so long rows spread over the grid and a
+// row only as long as a few chunks does not make every block stop at it.
+__global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
+                               const uint32_t *long_rows, const uint32_t *n_long) {
     __shared__ unsigned long long red[32];
+    __shared__ double redx[32];
     const uint32_t n = *n_long;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t G = gridDim.x;
     for (uint32_t r = 0; r < n; r++) {
         const uint32_t g = long_rows[r];
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
         const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
+        const int64_t nb = std::min<int64_t>(G, (e - b + LONGCH - 1) / LONGCH);
+        const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
+        if (off >= nb) continue;  // uniform over the block
         unsigned long long s = 0;
-        for (int64_t p = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e;
-             p += (int64_t)gridDim.x * blockDim.x) {
+        double x = 0.0;
+        for (int64_t p = b + off * (int64_t)blockDim.x + threadIdx.x; p < e; p += nb * blockDim.x) {
             const int32_t k = __ldg(P.X.ci + p);
             if (bit_of(P.km, (uint32_t)k)) s += (unsigned long long)(__ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k));
+            x += P.X.val ? (double)__ldg(P.X.val + p) : 1.0;
         }
-        for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
-        if (lane == 0) red[wid] = s;
+        for (int d = 16; d; d >>= 1) {
+            s += __shfl_xor_sync(FULL, s, d);
+            x += __shfl_xor_sync(FULL, x, d);
+        }
+        if (lane == 0) {
+            red[wid] = s;
+            redx[wid] = x;
+        }
         __syncthreads();
         if (wid == 0) {
             s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
-            for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+            x = lane < (int)(blockDim.x >> 5) ? redx[lane] : 0.0;
+            for (int d = 16; d; d >>= 1) {
+                s += __shfl_xor_sync(FULL, s, d);
+                x += __shfl_xor_sync(FULL, x, d);
+            }
             if (lane == 0 && s) atomicAdd((unsigned long long *)(prod + g), s);
+            if (lane == 0 && x > 0.0) atomicAdd(xsum + g, x);
         }
         __syncthreads();
     }
@@ -200,12 +237,12 @@ __device__ __forceinline__ void agg_add_u32(uint32_t *counter_base, int key, boo
 
 // Symbolic bin of every wave row from prod_i; rows without products get nnz_i = 0 and no
 // bin. Tallies per bin (for the byte model) and per product (products, rows per bin).
-__global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uint64_t *prod, int64_t M, BinArgs ba,
-                            int8_t *bin, int64_t *nnz, BinTally *tally, PStat *ps) {
+__global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uint64_t *prod, const double *xsum,
+                            int64_t M, BinArgs ba, int8_t *bin, int64_t *nnz, BinTally *tally, PStat *ps) {
     __shared__ uint32_t hc[NBINS], hd;
     __shared__ unsigned long long hx[NBINS], hp[NBINS], hb[NBINS];
     constexpr int NP = 8;  // products aggregated in shared memory per chunk of rows
-    __shared__ unsigned long long sp[NP];
+    __shared__ unsigned long long sp[NP], sx[NP];
     if (threadIdx.x < NBINS) {
         hc[threadIdx.x] = 0;
         hx[threadIdx.x] = 0;
@@ -217,7 +254,10 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
     for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x; g0 < M; g0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = g0 + threadIdx.x;
         const int pfirst = rowprod[g0];
-        if (threadIdx.x < NP) sp[threadIdx.x] = 0;
+        if (threadIdx.x < NP) {
+            sp[threadIdx.x] = 0;
+            sx[threadIdx.x] = 0;
+        }
         __syncthreads();
         int b = -1, pi = 0;
         uint64_t s = 0;
@@ -236,8 +276,18 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
                 // symbolic bytes: X row pointers + nnz write, per X entry its column id and the
                 // two Y row pointers, per product one Y column id
                 atomicAdd(&hb[b], 24ull + xe * 20ull + (unsigned long long)s * 4ull);
-                if (pi - pfirst < NP) atomicAdd(&sp[pi - pfirst], (unsigned long long)s);
-                else atomicAdd(&ps[pi].prods, (unsigned long long)s);
+                // a row whose X sum times Y's value bound reaches 2^63 may overflow: its
+                // product's counts take the checked (carry-detecting) additions
+                const double xs = xsum[g];
+                if (xs * (double)P.ymax >= 9223372036854775808.0) atomicOr(&ps[pi].unsafe, 1u);
+                const unsigned long long xb = (unsigned long long)__double_as_longlong(xs);
+                if (pi - pfirst < NP) {
+                    atomicAdd(&sp[pi - pfirst], (unsigned long long)s);
+                    atomicMax(&sx[pi - pfirst], xb);
+                } else {
+                    atomicAdd(&ps[pi].prods, (unsigned long long)s);
+                    atomicMax(&ps[pi].xsmax, xb);
+                }
             } else {
                 nnz[g] = 0;
             }
@@ -246,7 +296,10 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
         // rows per (product, bin), aggregated over lanes with the same pair
         agg_add_u32(&ps[0].sym_bins[0], pi * (int)(sizeof(PStat) / 4) + b, b >= 0, 1u);
         __syncthreads();
-        if (threadIdx.x < NP && sp[threadIdx.x]) atomicAdd(&ps[pfirst + threadIdx.x].prods, sp[threadIdx.x]);
+        if (threadIdx.x < NP && sp[threadIdx.x]) {
+            atomicAdd(&ps[pfirst + threadIdx.x].prods, sp[threadIdx.x]);
+            atomicMax(&ps[pfirst + threadIdx.x].xsmax, sx[threadIdx.x]);
+        }
         __syncthreads();
     }
     __syncthreads();
@@ -641,9 +694,16 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
 //   numeric:  a fill pass writes each set bit's column id at its rank (so the row comes
 //             out in ascending column order) and zeroes the value; then every product
 //             adds its count straight into the output slot rank[w] + popc(bits below j).
-// Bitmaps and ranks take 8 bytes per 32 output columns per row (slots of the widest
-// product's size); rows are processed in rounds that fit the scratch cap (one round keeps
-// the symbolic bitmaps for the numeric pass, several rounds rebuild them).
+// A bitmap word and its rank sit side by side (8 bytes per 32 output columns per row, slots
+// of the widest product's size), so the numeric pass finds a slot with one load; rows are
+// processed in rounds that fit the scratch cap (one round keeps the symbolic bitmaps for
+// the numeric pass, several rounds rebuild them).
+// Rows with at least glob_dense times as many products as the widest output instead add
+// their counts into a dense u64 row in the symbolic pass; a scan of the dense row then
+// gives the bitmap, the rank pass the size, and the numeric pass only copies the counts.
+// Counts are added without carry checks (fire-and-forget atomics) when the product's row
+// sums of X times the bound on Y's values stay below 2^63; otherwise every addition checks
+// its carry and an overflow fails the product.
 static constexpr int64_t PCH = 16384;  // Gustavson products per work item
 static constexpr int GNT = 256;        // threads per GLOBAL block
 static constexpr int RW = 8;           // bitmap words per thread in the rank pass
@@ -656,7 +716,7 @@ struct GlobArgs {
     const int64_t *xoff;      // per X entry of a GLOBAL row: global product offset
     const uint64_t *prod;     // prod_i per wave row
     int64_t r0, r1;           // rows of this round
-    uint32_t *bm, *rank;      // (r1 - r0) slots of nw words each
+    uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
     int64_t nw;               // slot size (words)
     int short_walk;           // walk chunks of short Y rows one X entry per thread
     unsigned long long *dval; // dense rows: (r1 - r0) slots of dcols counts each
@@ -722,9 +782,8 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // them are staged GNT at a time with their product offsets (from xoff); consecutive
 // threads take consecutive products, so a long Y row is read coalesced.
 // MODE G_SYM sets the row's bitmap bits; G_NUM adds the counts into the output row at the
-// positions the bitmap ranks give; G_DENSE adds the counts into the row's dense slot and
-// sets a column's bitmap bit when its first count lands (every count is >= 1), so one pass
-// gives both the row's size and its values.
+// positions the bitmap ranks give; G_DENSE adds the counts into the row's dense slot (the
+// bitmap comes from a scan of the slot afterwards: every count is >= 1).
 enum { G_SYM = 0, G_NUM = 1, G_DENSE = 2 };
 template <int MODE, bool COMB>
 __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
@@ -755,6 +814,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArg
         uint64_t *const pval = PP->val;
         if (MODE == G_NUM && !pval) continue;  // the product failed before its numeric pass
         uint32_t *err = &a.ps[pi].err;
+        const bool chk = a.ps[pi].unsafe != 0;  // uniform over the item
         const int64_t row = (int64_t)gr - PP->row0;
         const int32_t *__restrict__ xci = PP->X.ci;
         const uint64_t *__restrict__ xval = PP->X.val;
@@ -774,8 +834,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArg
             const int64_t mid = (plo + phi + 1) >> 1;
             if (__ldg(xo + mid) <= s0) plo = mid; else phi = mid - 1;
         }
-        uint32_t *bm = g.bm + (r - g.r0) * g.nw;
-        const uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        uint2 *bmr = g.bmr + (r - g.r0) * g.nw;
         unsigned long long *val = MODE == G_NUM    ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0])
                                   : MODE == G_DENSE ? g.dval + (r - g.r0) * g.dcols
                                                     : nullptr;
@@ -803,7 +862,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArg
                     const uint64_t av = s_a[l];
                     const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
                     add = av * bv;
-                    if (__umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+                    if (chk && __umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
                 }
                 const uint32_t k = NUM ? j : (j >> 5);
                 const uint32_t slot = (k * 0x9E3779B1u) >> (32 - 10);
@@ -818,21 +877,28 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArg
                 if (COMB && cur == k) {
                     if (!NUM) {
                         atomicOr((unsigned int *)&s_acc[slot], (unsigned int)add);
-                    } else {
+                    } else if (chk) {
                         const unsigned long long old = atomicAdd(s_acc + slot, add);
                         if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                    } else {
+                        atomicAdd(s_acc + slot, add);
                     }
                 } else if (!NUM) {
-                    atomicOr(bm + k, (uint32_t)add);
-                } else if (MODE == G_DENSE) {
-                    const unsigned long long old = atomicAdd(val + j, add);
-                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
-                    if (old == 0) atomicOr(bm + (j >> 5), 1u << (j & 31));
+                    atomicOr(&bmr[k].x, (uint32_t)add);
                 } else {
-                    const uint32_t w = j >> 5;
-                    const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (j & 31)) - 1u));
-                    const unsigned long long old = atomicAdd(val + pos, add);
-                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                    unsigned long long *dst;
+                    if (MODE == G_DENSE) {
+                        dst = val + j;
+                    } else {
+                        const uint2 br = __ldg(bmr + (j >> 5));
+                        dst = val + br.y + __popc(br.x & ((1u << (j & 31)) - 1u));
+                    }
+                    if (chk) {
+                        const unsigned long long old = atomicAdd(dst, add);
+                        if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                    } else {
+                        atomicAdd(dst, add);
+                    }
                 }
             };
             if (g.short_walk && s_off[nent] <= 8 * (int64_t)nent) {
@@ -861,18 +927,22 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArg
             const uint32_t k = s_key[x];
             if (k == EMPTY) continue;
             if (!NUM) {
-                atomicOr(bm + k, (uint32_t)s_acc[x]);
-            } else if (MODE == G_DENSE) {
-                const unsigned long long v = s_acc[x];
-                const unsigned long long old = atomicAdd(val + k, v);
-                if (old + v < old) atomicOr(err, ERR_OVERFLOW);
-                if (old == 0) atomicOr(bm + (k >> 5), 1u << (k & 31));
+                atomicOr(&bmr[k].x, (uint32_t)s_acc[x]);
             } else {
-                const uint32_t w = k >> 5;
-                const uint32_t pos = __ldg(rk + w) + __popc(__ldg(bm + w) & ((1u << (k & 31)) - 1u));
+                unsigned long long *dst;
+                if (MODE == G_DENSE) {
+                    dst = val + k;
+                } else {
+                    const uint2 br = __ldg(bmr + (k >> 5));
+                    dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
+                }
                 const unsigned long long v = s_acc[x];
-                const unsigned long long old = atomicAdd(val + pos, v);
-                if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                if (chk) {
+                    const unsigned long long old = atomicAdd(dst, v);
+                    if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                } else {
+                    atomicAdd(dst, v);
+                }
             }
             s_key[x] = EMPTY;
             s_acc[x] = 0;
@@ -887,8 +957,7 @@ __global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int n
     for (int64_t r = g.r0 + blockIdx.x; r < g.r1; r += gridDim.x) {
         const RowRef Rf(a, g.list[r]);
         const int64_t nw = (Rf.P->Y.ncols + 31) / 32;
-        const uint32_t *bm = g.bm + (r - g.r0) * g.nw;
-        uint32_t *rk = g.rank + (r - g.r0) * g.nw;
+        uint2 *bmr = g.bmr + (r - g.r0) * g.nw;
         int64_t carry = 0;
         for (int64_t w0 = 0; w0 < nw; w0 += (int64_t)GNT * RW) {
             const int64_t wb = w0 + (int64_t)threadIdx.x * RW;
@@ -896,13 +965,13 @@ __global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int n
             int c = 0;
 #pragma unroll
             for (int u = 0; u < RW; u++) {
-                cnt[u] = wb + u < nw ? __popc(bm[wb + u]) : 0;
+                cnt[u] = wb + u < nw ? __popc(bmr[wb + u].x) : 0;
                 c += cnt[u];
             }
             int64_t ex = carry + block_excl_scan<GNT>(c, warp_sums, &gtot);
 #pragma unroll
             for (int u = 0; u < RW; u++) {
-                if (wb + u < nw) rk[wb + u] = (uint32_t)ex;
+                if (wb + u < nw) bmr[wb + u].y = (uint32_t)ex;
                 ex += cnt[u];
             }
             carry += gtot;
@@ -918,13 +987,14 @@ __global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int n
 __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
     const int64_t total = (g.r1 - g.r0) * g.nw;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t word = g.bm[x];
+        const uint2 br = g.bmr[x];
+        uint32_t word = br.x;
         if (!word) continue;
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const RowRef Rf(a, g.list[g.r0 + slot]);
         const Prod P = *Rf.P;
         if (!P.ci) continue;
-        int64_t pos = Rf.out_off(a) + g.rank[x];
+        int64_t pos = Rf.out_off(a) + br.y;
         while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
@@ -935,19 +1005,35 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
     }
 }
 
+// Dense rows: one warp per bitmap word; lane i reads column 32w + i of the dense slot
+// (coalesced) and the ballot of the non-zero counts is the word.
+__global__ void k_glob_dscan(GlobArgs g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (g.r1 - g.r0) * g.nw;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < total; x += nwarps) {
+        const int64_t slot = x / g.nw, w = x - slot * g.nw;
+        const int64_t j = w * 32 + lane;
+        const bool nz = j < g.dcols && g.dval[slot * g.dcols + j] != 0;
+        const unsigned word = __ballot_sync(FULL, nz);
+        if (lane == 0) g.bmr[x] = make_uint2(word, 0u);
+    }
+}
+
 // Dense rows: one thread per bitmap word; the word's set bits become consecutive output
 // entries with their counts from the dense slot.
 __global__ void k_glob_dfill(PassArgs a, GlobArgs g) {
     const int64_t total = (g.r1 - g.r0) * g.nw;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t word = g.bm[x];
+        const uint2 br = g.bmr[x];
+        uint32_t word = br.x;
         if (!word) continue;
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const RowRef Rf(a, g.list[g.r0 + slot]);
         const Prod P = *Rf.P;
         if (!P.ci) continue;
         const unsigned long long *dv = g.dval + slot * g.dcols;
-        int64_t pos = Rf.out_off(a) + g.rank[x];
+        int64_t pos = Rf.out_off(a) + br.y;
         while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
@@ -1055,8 +1141,7 @@ struct Glob {
     uint32_t *list = nullptr;  // the bin's rows, dense-row candidates first
     int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr;
     const uint64_t *prod = nullptr;
-    uint32_t *bm = nullptr, *rank = nullptr;
-    uint32_t *dbm = nullptr, *drank = nullptr;
+    uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
     bool kept = false;         // bitmaps of a single round survive into the numeric pass
 };
@@ -1066,10 +1151,8 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.item_off) al.free(g.item_off, s);
     if (g.xbase) al.free(g.xbase, s);
     if (g.xoff) al.free(g.xoff, s);
-    if (g.bm) al.free(g.bm, s);
-    if (g.rank) al.free(g.rank, s);
-    if (g.dbm) al.free(g.dbm, s);
-    if (g.drank) al.free(g.drank, s);
+    if (g.bmr) al.free(g.bmr, s);
+    if (g.dbmr) al.free(g.dbmr, s);
     if (g.dval) al.free(g.dval, s);
     g = Glob{};
 }
@@ -1079,14 +1162,15 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, 0, g.nd, g.dbm, g.drank, g.nw, tun.short_walk,
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, 0, g.nd, g.dbmr, g.nw, tun.short_walk,
                           g.dval, g.dcols};
         const int64_t words = g.nd * g.nw;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
-            cudaMemsetAsync(g.dbm, 0, (size_t)words * 4, s);
             if (tun.combine) kl(k_glob_set<G_DENSE, true>, grid, GNT, 0, s, a, ga);
             else kl(k_glob_set<G_DENSE, false>, grid, GNT, 0, s, a, ga);
+            kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
+               256, 0, s, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
         } else {
             kl(k_glob_dfill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256,
@@ -1094,11 +1178,11 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         }
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bm,
-                          g.rank, g.nw, tun.short_walk, nullptr, 0};
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bmr,
+                          g.nw, tun.short_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
-            cudaMemsetAsync(g.bm, 0, (size_t)rows * g.nw * 4, s);
+            cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
             if (tun.combine) kl(k_glob_set<G_SYM, true>, grid, GNT, 0, s, a, ga);
             else kl(k_glob_set<G_SYM, false>, grid, GNT, 0, s, a, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
@@ -1138,6 +1222,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         P.rm = x.rm;
         P.km = x.km;
         P.cm = x.cm;
+        P.ymax = x.ymax;
         P.row0 = row0s[p];
         row0s[p + 1] = row0s[p] + x.X.nrows;
         if (x.Y.ncols <= tun.dense_max_cols) dense_cols = std::max<int64_t>(dense_cols, x.Y.ncols);
@@ -1145,14 +1230,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     }
     const int64_t M = row0s[w];
     // workspace: prod u64[M], bins i8[M], row list u32[M], long rows u32[M], rowprod i32[M],
-    // wave nnz / row pointers i64[M+1], product descriptors, row0s, per-product stats, two Smalls
+    // wave nnz / row pointers i64[M+1], X row sums f64[M], product descriptors, row0s,
+    // per-product stats, two Smalls
     const size_t o_prod = 0;
     const size_t o_bin = align256(o_prod + (size_t)M * 8);
     const size_t o_list = align256(o_bin + (size_t)M);
     const size_t o_long = align256(o_list + (size_t)M * 4);
     const size_t o_rowprod = align256(o_long + (size_t)M * 4);
     const size_t o_grp = align256(o_rowprod + (size_t)M * 4);
-    const size_t o_prods = align256(o_grp + (size_t)(M + 1) * 8);
+    const size_t o_xsum = align256(o_grp + (size_t)(M + 1) * 8);
+    const size_t o_prods = align256(o_xsum + (size_t)M * 8);
     const size_t o_row0s = align256(o_prods + sizeof(Prod) * w);
     const size_t o_ps = align256(o_row0s + (size_t)(w + 1) * 8);
     const size_t o_small = align256(o_ps + sizeof(PStat) * w);
@@ -1172,6 +1259,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     uint32_t *long_rows = (uint32_t *)(ws + o_long);
     int32_t *rowprod = (int32_t *)(ws + o_rowprod);
     int64_t *grp = (int64_t *)(ws + o_grp);
+    double *xsum = (double *)(ws + o_xsum);
     Prod *dprods = (Prod *)(ws + o_prods);
     int64_t *drow0s = (int64_t *)(ws + o_row0s);
     PStat *ps = (PStat *)(ws + o_ps);
@@ -1214,9 +1302,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned gr = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
         kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, long_rows, &sm_sym->n_long);
-        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, long_rows, &sm_sym->n_long);
-        kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, M, ba, bin, grp, &sm_sym->tally, ps);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, &sm_sym->n_long);
+        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum, long_rows,
+           &sm_sym->n_long);
+        kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, M, ba, bin, grp, &sm_sym->tally,
+           ps);
         kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
         kl(k_bin_fill, gr, 256, 0, s, bin, M, sm_sym->offsets, sm_sym->cursors, list);
     }
@@ -1247,20 +1337,18 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.xoff = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
         if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff) return fail(MP_ERR_NOMEM);
         if (rb) {
-            gl.bm = (uint32_t *)al.alloc((size_t)gl.per_round * gl.nw * 4, s);
-            gl.rank = (uint32_t *)al.alloc((size_t)(gl.per_round * gl.nw + 2) * 4, s);
-            if (!gl.bm || !gl.rank) return fail(MP_ERR_NOMEM);
+            gl.bmr = (uint2 *)al.alloc((size_t)gl.per_round * gl.nw * 8, s);
+            if (!gl.bmr) return fail(MP_ERR_NOMEM);
         }
         if (gl.nd) {
-            gl.dbm = (uint32_t *)al.alloc((size_t)gl.nd * gl.nw * 4, s);
-            gl.drank = (uint32_t *)al.alloc((size_t)(gl.nd * gl.nw + 2) * 4, s);
+            gl.dbmr = (uint2 *)al.alloc((size_t)gl.nd * gl.nw * 8, s);
             gl.dval = (unsigned long long *)al.alloc((size_t)gl.nd * gl.dcols * 8, s);
-            if (!gl.dbm || !gl.drank || !gl.dval) return fail(MP_ERR_NOMEM);
+            if (!gl.dbmr || !gl.dval) return fail(MP_ERR_NOMEM);
         }
         if (nd_all) {
-            // qualifying rows first (the two counters live in the rank buffer's first
-            // words, allocated with two spare words, until the partition is done)
-            uint32_t *cnt = gl.nd ? gl.drank : gl.rank;
+            // qualifying rows first (the two counters live in the first bitmap/rank pair,
+            // which the symbolic pass overwrites, until the partition is done)
+            uint32_t *cnt = (uint32_t *)(gl.nd ? gl.dbmr : gl.bmr);
             if (!cuda_ok(cudaMemsetAsync(cnt, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
             kl(k_glob_split, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s,
                (const Prod *)dprods, (const int32_t *)rowprod, (const uint32_t *)(list + h_sym.offsets[B_GLOBAL]),
@@ -1362,6 +1450,12 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         o.m.nrows = in[p].X.nrows;
         o.m.ncols = in[p].Y.ncols;
         o.m.nnz = in[p].X.nrows ? hps[p].nnz : 0;
+        // every count is at most (row sum of X) * (bound on Y's values); the row sums are
+        // double sums, so the bound carries a relative margin far above their rounding
+        double xsmax;
+        memcpy(&xsmax, &hps[p].xsmax, sizeof xsmax);
+        const double vb = xsmax * (double)in[p].ymax * (1.0 + 1e-6);
+        o.m.vmax = hps[p].unsafe || !(vb < 9.2e18) ? UINT64_MAX : (uint64_t)vb + 1;
         o.m.rp = hp[p].rp;
         o.m.ci = hp[p].ci;
         o.m.val = hp[p].val;

@@ -18,7 +18,7 @@ MP_OK = 0
 MP_ERR_ARG, MP_ERR_STATE, MP_ERR_BUDGET, MP_ERR_TOO_LARGE, MP_ERR_OVERFLOW = -1, -2, -3, -4, -5
 MP_ERR_TIMEOUT, MP_ERR_CUDA, MP_ERR_NOMEM, MP_ERR_NOTFOUND, MP_ERR_INTERNAL = -6, -7, -8, -9, -10
 MP_POLICY_ATRAPOS, MP_POLICY_PGDS, MP_POLICY_LRU, MP_POLICY_NONE = 0, 1, 2, 3
-MP_PLAN_DP, MP_PLAN_LEFT_TO_RIGHT, MP_PLAN_DP_SAMPLED = 0, 1, 2
+MP_PLAN_DP, MP_PLAN_LEFT_TO_RIGHT, MP_PLAN_DP_SAMPLED, MP_PLAN_DP_MNC = 0, 1, 2, 3
 MP_INSERT_OTREE, MP_INSERT_FINAL, MP_INSERT_ALL = 0, 1, 2
 MP_BIN_AUTO, MP_BIN_WARP_HASH, MP_BIN_BLOCK_HASH, MP_BIN_DENSE, MP_BIN_GLOBAL = -1, 0, 1, 2, 3
 MP_OP_RANGE, MP_OP_EQ, MP_OP_IN = 0, 1, 2
@@ -33,7 +33,7 @@ EXPORTS = [
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
-    "mp_hin_load",
+    "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query",
 ]
 
 
@@ -89,6 +89,7 @@ def lib():
             "mp_property_id": (C.c_int, [C.c_void_p, I32, C.c_char_p, P(I32)]),
             "mp_relation_id": (C.c_int, [C.c_void_p, I32, I32, P(I32)]),
             "mp_submit": (C.c_int, [C.c_void_p, P(mp_query), P(U64)]),
+            "mp_plan_query": (C.c_int, [C.c_void_p, P(mp_query), U32, C.c_void_p, C.c_void_p, P(U32)]),
             "mp_submit_batch": (C.c_int, [C.c_void_p, U32, P(mp_query), P(U64)]),
             "mp_wait": (C.c_int, [C.c_void_p, U64, U32]),
             "mp_result_info": (C.c_int, [C.c_void_p, U64, P(U32), P(U32), P(U64)]),
@@ -125,6 +126,9 @@ def lib():
             "mp_cachesim_state": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_double), P(U32)]),
             "mp_plan_chain": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+            "mp_plan_chain_mnc": (C.c_int, [U32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -242,6 +246,20 @@ def make_query(types, rels=None, constraints=()):
     return _QueryBuf(types, rels, list(constraints))
 
 
+def mp_plan_query(ctx, query: _QueryBuf):
+    """(split p x p int32, estimated sizes p x p float64) of the context's planner for one
+    query, without running it."""
+    p = C.c_uint32()
+    rc = lib().mp_plan_query(ctx, C.byref(query.q), 0, None, None, C.byref(p))
+    if rc not in (MP_OK, MP_ERR_ARG) or p.value == 0:
+        _ck(rc, "mp_plan_query")
+    n = p.value
+    split = np.zeros((n, n), np.int32)
+    nnz = np.zeros((n, n), np.float64)
+    _ck(lib().mp_plan_query(ctx, C.byref(query.q), n * n, _ptr(split), _ptr(nnz), C.byref(p)), "mp_plan_query")
+    return split, nnz
+
+
 def mp_submit(ctx, query: _QueryBuf) -> tuple[int, int]:
     """Returns (status, ticket); the ticket is valid even when the status is an error."""
     t = C.c_uint64()
@@ -353,6 +371,31 @@ def mp_plan_chain(dims, nnz, alpha=1.0, beta=1.0, gamma=1.0, known=None, rho_fix
     _ck(lib().mp_plan_chain(p, _ptr(dims), _ptr(nnz), alpha, beta, gamma, _ptr(kc), _ptr(kr), _ptr(rf),
                             _ptr(split), _ptr(cost)), "mp_plan_chain")
     return split, cost
+
+
+def mp_plan_chain_mnc(dims, sketches, alpha=1.0, beta=1.0, gamma=1.0, known=None):
+    """Splits (p x p int32), costs and estimated sizes (p x p float64) of the C++ MNC
+    planner. sketches[t] = (hr, hc, her, hec) count vectors of leaf factor t; known maps
+    (i, j) -> (cost, nnz)."""
+    dims = np.ascontiguousarray(dims, np.float64)
+    p = len(sketches)
+    vecs = [[np.ascontiguousarray(v, np.uint32) for v in sk] for sk in sketches]
+    arrs = []
+    for f in range(4):
+        a = (C.c_void_p * p)(*[vecs[t][f].ctypes.data for t in range(p)])
+        arrs.append(a)
+    kc = kz = None
+    if known:
+        kc = np.full((p, p), np.nan)
+        kz = np.full((p, p), np.nan)
+        for (i, j), (c, z) in known.items():
+            kc[i, j], kz[i, j] = c, z
+    split = np.zeros((p, p), np.int32)
+    cost = np.zeros((p, p), np.float64)
+    nnz = np.zeros((p, p), np.float64)
+    _ck(lib().mp_plan_chain_mnc(p, _ptr(dims), *arrs, alpha, beta, gamma, _ptr(kc), _ptr(kz), _ptr(split),
+                                _ptr(cost), _ptr(nnz)), "mp_plan_chain_mnc")
+    return split, cost, nnz
 
 
 def mp_kernel_stats(ctx):
@@ -509,6 +552,10 @@ class Engine:
 
     def submit(self, q):
         return mp_submit(self.ctx, self.query(q))
+
+    def plan(self, q):
+        """The planner's (split, estimated sizes) for q; no product runs."""
+        return mp_plan_query(self.ctx, self.query(q))
 
     def submit_batch(self, qs):
         return mp_submit_batch(self.ctx, [self.query(q) for q in qs])

@@ -138,11 +138,17 @@ def test_unknown_relation_rejected(c1, c1_engines):
     assert ex.value.code == mp.MP_ERR_NOTFOUND
 
 
-def test_overflow_is_an_error_not_a_wrap(cuda_ok):
+@pytest.mark.parametrize("tuning", ["", "glob_dense=0", "glob_dense=0,combine=0", "combine=0"])
+def test_overflow_is_an_error_not_a_wrap(cuda_ok, tuning, monkeypatch):
     """A complete bipartite 100 x 100 relation: a metapath ABAB... of length n has
     100^(n-2) instances between every pair of end nodes; at n = 12 that is 10^20 > 2^64,
-    so the count cannot be represented, while n = 11 (10^18) fits."""
+    so the count cannot be represented, while n = 11 (10^18) fits. Split rows run as
+    dense rows (default) and as bitmap rows (glob_dense=0), with and without the
+    shared-memory combining table; the last product of n = 12 is the one whose bound
+    forces carry-checked additions."""
     mp = _mp()
+    if tuning:
+        monkeypatch.setenv("MP_TUNING", tuning)
     n = 100
     s = np.repeat(np.arange(n, dtype=np.uint32), n)
     d = np.tile(np.arange(n, dtype=np.uint32), n)
