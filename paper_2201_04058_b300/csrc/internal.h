@@ -47,7 +47,7 @@ struct Tuning {
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     // GLOBAL rows with prod_i >= glob_dense * ncols accumulate their counts in a dense u64
     // row (one pass gives both the size and the values); 0 turns the dense rows off
-    double glob_dense = 0.5;
+    double glob_dense = 1.0;
     uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
     int sm_count = 148;
 };

@@ -28,21 +28,57 @@ namespace mp {
 
 namespace {
 
+static constexpr int64_t MNC_LONG = 4096;  // rows longer than this are shared by all blocks
+
 // out[i] = 0 for rows outside rm; else the entries of row i whose column passes cm and,
-// with ref, whose column has ref == 1. One warp per row.
-__global__ void k_mnc_rows(DCsr A, const uint32_t *rm, const uint32_t *cm, const uint32_t *ref, uint32_t *out) {
+// with ref, whose column has ref == 1. One warp per row; rows longer than MNC_LONG get 0
+// here and are queued (long_rows, *n_long) for k_mnc_rows_long.
+__global__ void k_mnc_rows(DCsr A, const uint32_t *rm, const uint32_t *cm, const uint32_t *ref, uint32_t *out,
+                           uint32_t *long_rows, uint32_t *n_long) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < A.nrows; i += nwarps) {
         uint32_t c = 0;
+        const int64_t b = A.rp[i], e = A.rp[i + 1];
         if (bit_of(rm, (uint32_t)i)) {
-            for (int64_t p = A.rp[i] + lane; p < A.rp[i + 1]; p += 32) {
-                const uint32_t j = (uint32_t)__ldg(A.ci + p);
-                c += bit_of(cm, j) && (!ref || __ldg(ref + j) == 1u);
+            if (e - b > MNC_LONG) {
+                if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)i;
+            } else {
+                for (int64_t p = b + lane; p < e; p += 32) {
+                    const uint32_t j = (uint32_t)__ldg(A.ci + p);
+                    c += bit_of(cm, j) && (!ref || __ldg(ref + j) == 1u);
+                }
             }
         }
         for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
         if (lane == 0) out[i] = c;
+    }
+}
+
+// The queued long rows: every block takes a strided share of every long row's entries and
+// adds its count into out[i] (which k_mnc_rows set to 0).
+__global__ void k_mnc_rows_long(DCsr A, const uint32_t *cm, const uint32_t *ref, uint32_t *out,
+                                const uint32_t *long_rows, const uint32_t *n_long) {
+    __shared__ uint32_t red[32];
+    const uint32_t n = *n_long;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t r = 0; r < n; r++) {
+        const int64_t i = long_rows[r];
+        uint32_t c = 0;
+        for (int64_t p = A.rp[i] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < A.rp[i + 1];
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const uint32_t j = (uint32_t)__ldg(A.ci + p);
+            c += bit_of(cm, j) && (!ref || __ldg(ref + j) == 1u);
+        }
+        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+        if (lane == 0) red[wid] = c;
+        __syncthreads();
+        if (wid == 0) {
+            c = lane < (int)(blockDim.x >> 5) ? red[lane] : 0u;
+            for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+            if (lane == 0 && c) atomicAdd(out + i, c);
+        }
+        __syncthreads();
     }
 }
 
@@ -176,6 +212,19 @@ int MncDevice::prepare() {
     if (!sum_) return MP_ERR_NOMEM;
     cudaMemsetAsync(sum_, 0, nl * 8 * sizeof(unsigned long long), s_);
     const unsigned gmax = (unsigned)sms_ * 8;
+    // one long-row queue (+ its counter) for every row-count pass, reused in stream order
+    int64_t qmax = 1;
+    for (const Leaf &L : leaves_) qmax = std::max(qmax, std::max(L.in.A.nrows, L.in.A.ncols));
+    uint32_t *lq = (uint32_t *)al_.alloc((size_t)(qmax + 1) * 4, s_);
+    if (!lq) return MP_ERR_NOMEM;
+    auto rows = [&](const DCsr &A, const uint32_t *rm, const uint32_t *cm, const uint32_t *ref, uint32_t *out) {
+        if (!A.nrows) return;
+        cudaMemsetAsync(lq + qmax, 0, 4, s_);
+        kl(k_mnc_rows, std::max(1u, std::min(gmax, grid_for(A.nrows * 32, 256))), 256, 0, s_, A, rm, cm, ref, out,
+           lq, lq + qmax);
+        kl(k_mnc_rows_long, (unsigned)sms_ * 4, 256, 0, s_, A, cm, ref, out, (const uint32_t *)lq,
+           (const uint32_t *)(lq + qmax));
+    };
     for (size_t l = 0; l < nl; l++) {
         Leaf &L = leaves_[l];
         const int64_t m = L.in.A.nrows, n = L.in.A.ncols;
@@ -183,18 +232,20 @@ int MncDevice::prepare() {
         L.her = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(m, 1) * 4, s_);
         L.hc = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
         L.hec = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
-        if (!L.hr || !L.her || !L.hc || !L.hec) return MP_ERR_NOMEM;
-        const unsigned gr = std::max(1u, std::min(gmax, grid_for(m * 32, 256)));
-        const unsigned gc = std::max(1u, std::min(gmax, grid_for(n * 32, 256)));
-        if (m) kl(k_mnc_rows, gr, 256, 0, s_, L.in.A, L.in.rm, L.in.cm, (const uint32_t *)nullptr, L.hr);
-        if (n) kl(k_mnc_rows, gc, 256, 0, s_, L.in.AT, L.in.cm, L.in.rm, (const uint32_t *)nullptr, L.hc);
-        if (m) kl(k_mnc_rows, gr, 256, 0, s_, L.in.A, L.in.rm, L.in.cm, (const uint32_t *)L.hc, L.her);
-        if (n) kl(k_mnc_rows, gc, 256, 0, s_, L.in.AT, L.in.cm, L.in.rm, (const uint32_t *)L.hr, L.hec);
+        if (!L.hr || !L.her || !L.hc || !L.hec) {
+            al_.free(lq, s_);
+            return MP_ERR_NOMEM;
+        }
+        rows(L.in.A, L.in.rm, L.in.cm, nullptr, L.hr);
+        rows(L.in.AT, L.in.cm, L.in.rm, nullptr, L.hc);
+        rows(L.in.A, L.in.rm, L.in.cm, L.hc, L.her);
+        rows(L.in.AT, L.in.cm, L.in.rm, L.hr, L.hec);
         if (m) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(m, 256))), 256, 0, s_, (const uint32_t *)L.hr, m,
                   sum_ + 8 * l);
         if (n) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(n, 256))), 256, 0, s_, (const uint32_t *)L.hc, n,
                   sum_ + 8 * l + 4);
     }
+    al_.free(lq, s_);  // stream-ordered: after the passes above
     // per pair: product count, the two exactly counted parts, the remaining log-sum
     std::vector<DevReq> rq;
     for (size_t p = 0; p < np; p++) {

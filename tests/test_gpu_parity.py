@@ -243,7 +243,8 @@ def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatc
     (0, 1e-9, 0),         # ... without the shared-memory combining table
     (1, 1e-9, 200000),    # the dense scratch holds a few rows; the rest take bitmap rounds
     (1, 1e-9, 1),         # no dense row fits: rows qualify, all take bitmap rounds
-    (1, 0.5, 0),          # the default threshold
+    (1, 0.5, 0),          # half the default threshold
+    (1, 1.0, 0),          # the default threshold
 ])
 def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, monkeypatch):
     """Split rows that accumulate in a dense u64 row (one pass for size and values, a fill
