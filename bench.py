@@ -406,7 +406,9 @@ def run_engine(args, ws, rank, local):
                    "d2h_bytes_per_step": d2h[0] // e2e_steps},
            "batched": batched, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                           "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)} for k, v in kstats.items()}}
+                           "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                           "Gproducts_per_s": round(v["products"] / max(v["ms"], 1e-9) / 1e6, 2)}
+                       for k, v in kstats.items()}}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(hin, qs, args.cpu_sample_queries)
     if rank == 0:
@@ -578,6 +580,17 @@ def run_small(args, local):
             out_c[f"{label}/{['atrapos', 'pgds', 'lru'][pol]}"] = {
                 "first_pass_qps": len(qs) / cold_s, "replay_qps": len(qs) / warm_s,
                 "replay_products": warm_p, "cache": mp.mp_cache_stats(e.ctx)}
+            e.close()
+        if label == "25pct":
+            # the same budget with a second tier in host memory as large as everything
+            e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, hbm_budget_bytes=int(budget),
+                          host_tier_bytes=int(4 * budget))
+            eb = [e.query(q) for q in qs]
+            cold_s, cold_p = _time_batch(mp, e, eb, 1, warm=0)
+            warm_s, warm_p = _time_batch(mp, e, eb, reps, warm=0)
+            out_c[f"{label}/atrapos+host_tier"] = {
+                "first_pass_qps": len(qs) / cold_s, "replay_qps": len(qs) / warm_s, "replay_products": warm_p,
+                "cache": mp.mp_cache_stats(e.ctx), "host_tier": mp.mp_host_tier_stats(e.ctx)}
             e.close()
     res = {"metric": METRIC, "value": len(qs) / b_s, "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": 1,
            "ms_per_step": 1e3 * b_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

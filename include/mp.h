@@ -97,6 +97,9 @@ typedef struct {
     uint64_t seed;             /* seed of the sampled-row choice */
     int32_t insertion;         /* MP_INSERT_* (used when policy != MP_POLICY_NONE) */
     const char *tune_file;     /* NULL, or a file written by mp_autotune to load at create */
+    uint64_t host_tier_bytes;  /* second cache tier in pinned host memory for results the
+                                  device cache evicts (0 = off); a later plan may copy one
+                                  back instead of recomputing it */
 } mp_config;
 
 /* Fill *cfg with defaults: device 0, 8 GiB budget, 64 slots, ATRAPOS policy, DP
@@ -242,6 +245,13 @@ int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t 
 int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *inserts, uint64_t *rejected,
                    uint64_t *evictions, uint64_t *bytes, uint64_t *entries);
 
+/* Host-tier counters since mp_create (mp_config.host_tier_bytes): results stored after a
+ * device-cache eviction, results copied back instead of recomputed, entries dropped to make
+ * room (least recently used first), bytes and entries held. Any pointer may be NULL.
+ * MP_ERR_STATE when there is no cache or no host tier. */
+int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t *drops, uint64_t *bytes,
+                       uint64_t *entries);
+
 /* Per-kernel counters of the SpGEMM passes since the last reset: one entry per (pass,
  * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
  * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),
@@ -257,6 +267,7 @@ typedef struct {
     uint64_t launches;
     double ms;
     double bytes;
+    double products;  /* Gustavson scalar products of the rows the launches processed */
 } mp_kernel_stat;
 int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, uint32_t *n, uint64_t *launches);
 int mp_kernel_stats_reset(mp_ctx *ctx);

@@ -1005,6 +1005,7 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
                 out[w].launches = k.launches;
                 out[w].ms = k.ms;
                 out[w].bytes = k.bytes;
+                out[w].products = k.prods;
                 w++;
             }
         }
@@ -1026,6 +1027,20 @@ extern "C" int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, u
     if (evictions) *evictions = c.evictions;
     if (bytes) *bytes = (uint64_t)ctx->cache->used();
     if (entries) *entries = (uint64_t)ctx->cache->size();
+    return MP_OK;
+}
+
+extern "C" int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t *drops,
+                                  uint64_t *bytes, uint64_t *entries) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->exec_mu);
+    if (!ctx->cache || !ctx->cfg.host_tier_bytes) return MP_ERR_STATE;
+    const auto &h = ctx->htier;
+    if (stores) *stores = h.stores;
+    if (loads) *loads = h.loads;
+    if (drops) *drops = h.drops;
+    if (bytes) *bytes = (uint64_t)h.bytes;
+    if (entries) *entries = (uint64_t)h.items.size();
     return MP_OK;
 }
 

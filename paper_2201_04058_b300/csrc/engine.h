@@ -115,6 +115,30 @@ struct mp_ctx {
     mp::OverlapTree otree;
     std::unique_ptr<mp::CachePolicy> cache;  // null when cfg.policy == MP_POLICY_NONE
     CacheCounters cstats;
+    // Second cache tier in pinned host memory (mp_config.host_tier_bytes): a result the
+    // device cache evicts is copied down; a later plan may treat it as known at the cost of
+    // copying it back, and then loads it instead of recomputing it. Least recently used
+    // entries leave when the tier is full.
+    struct HostEntry {
+        std::vector<int32_t> types;
+        std::string key;
+        mp::Mat shape;        // sizes and value bound (its pointers are unused)
+        void *buf = nullptr;  // pinned: row pointers | column ids | counts
+        size_t bytes = 0;
+        double c_ms = 0.0, c_ops = 0.0;  // recorded computation time and Eq. 2 cost
+        uint64_t seq = 0;
+    };
+    struct HostTier {
+        std::unordered_map<std::string, HostEntry> items;
+        size_t bytes = 0;
+        uint64_t seq = 0, stores = 0, loads = 0, drops = 0;
+        double h2d_gbs = 20.0;  // running estimate of the copy-back rate
+    } htier;
+    void htier_store(const std::string &id, const MatPtr &m, const std::vector<int32_t> &types,
+                     const std::string &key, double c_ms, double c_ops);
+    MatPtr htier_load(const std::string &id);
+    double htier_cost(const std::string &id) const;  // Eq. 2 units, NaN when absent
+    void htier_clear();
 
     int parse(const mp_query *q, Query &out);
     int build_masks(const Query &q, std::vector<uint32_t *> &masks);

@@ -65,7 +65,7 @@ struct Stats {
 // algorithmic bytes of the work the launch did (see spgemm.cu for the byte model).
 struct KStat {
     uint64_t launches = 0;
-    double ms = 0.0, bytes = 0.0;
+    double ms = 0.0, bytes = 0.0, prods = 0.0;
 };
 struct Prof {
     bool on = true;

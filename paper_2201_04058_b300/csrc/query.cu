@@ -20,6 +20,7 @@
 #include <map>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "engine.h"
@@ -52,6 +53,107 @@ void mp_ctx::release_result(Result &r) { r.m.reset(); }
 
 void mp_ctx::cache_clear() {
     if (cache) cache->clear();
+    htier_clear();
+}
+
+void mp_ctx::htier_clear() {
+    for (auto &kv : htier.items) cudaFreeHost(kv.second.buf);
+    htier.items.clear();
+    htier.bytes = 0;
+}
+
+void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vector<int32_t> &types,
+                         const std::string &key, double c_ms, double c_ops) {
+    const size_t cap = (size_t)cfg.host_tier_bytes;
+    if (!cap || !m) return;
+    auto it = htier.items.find(id);
+    if (it != htier.items.end()) {  // already held (loaded back earlier): refresh it
+        it->second.seq = ++htier.seq;
+        return;
+    }
+    const Mat &A = m->m;
+    const size_t brp = (size_t)(A.nrows + 1) * 8, bci = (size_t)A.nnz * 4, bval = (size_t)A.nnz * 8;
+    const size_t bytes = brp + bci + bval;
+    if ((double)bytes > 0.8 * (double)cap) return;  // the 80 % rule of the device cache
+    while (htier.bytes + bytes > cap && !htier.items.empty()) {
+        auto lru = htier.items.begin();
+        for (auto x = htier.items.begin(); x != htier.items.end(); ++x)
+            if (x->second.seq < lru->second.seq) lru = x;
+        cudaFreeHost(lru->second.buf);
+        htier.bytes -= lru->second.bytes;
+        htier.items.erase(lru);
+        htier.drops++;
+    }
+    void *buf = nullptr;
+    if (cudaMallocHost(&buf, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    char *b = (char *)buf;
+    cudaMemcpyAsync(b, A.rp, brp, cudaMemcpyDeviceToHost, stream);
+    if (A.nnz) {
+        cudaMemcpyAsync(b + brp, A.ci, bci, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(b + brp + bci, A.val, bval, cudaMemcpyDeviceToHost, stream);
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaFreeHost(buf);
+        return;
+    }
+    HostEntry e;
+    e.types = types;
+    e.key = key;
+    e.shape = A;
+    e.shape.rp = nullptr;
+    e.shape.ci = nullptr;
+    e.shape.val = nullptr;
+    e.buf = buf;
+    e.bytes = bytes;
+    e.c_ms = c_ms;
+    e.c_ops = c_ops;
+    e.seq = ++htier.seq;
+    htier.bytes += bytes;
+    htier.items.emplace(id, std::move(e));
+    htier.stores++;
+}
+
+double mp_ctx::htier_cost(const std::string &id) const {
+    auto it = htier.items.find(id);
+    if (it == htier.items.end()) return NAN;
+    // the recorded cost scaled by (copy-back time / computation time), at most the cost
+    const HostEntry &e = it->second;
+    const double copy_ms = (double)e.bytes / (htier.h2d_gbs * 1e6);
+    return e.c_ms > 0 ? e.c_ops * std::min(1.0, copy_ms / e.c_ms) : e.c_ops;
+}
+
+MatPtr mp_ctx::htier_load(const std::string &id) {
+    auto it = htier.items.find(id);
+    if (it == htier.items.end()) return nullptr;
+    HostEntry &e = it->second;
+    Mat m = e.shape;
+    const size_t brp = (size_t)(m.nrows + 1) * 8, bci = (size_t)m.nnz * 4, bval = (size_t)m.nnz * 8;
+    m.rp = (int64_t *)alloc->alloc(brp, stream);
+    m.ci = (int32_t *)alloc->alloc(std::max<size_t>(bci, 4), stream);
+    m.val = (uint64_t *)alloc->alloc(std::max<size_t>(bval, 8), stream);
+    if (!m.rp || !m.ci || !m.val) {
+        free_mat(m);
+        return nullptr;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const char *b = (const char *)e.buf;
+    cudaMemcpyAsync(m.rp, b, brp, cudaMemcpyHostToDevice, stream);
+    if (m.nnz) {
+        cudaMemcpyAsync(m.ci, b + brp, bci, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(m.val, b + brp + bci, bval, cudaMemcpyHostToDevice, stream);
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        free_mat(m);
+        return nullptr;
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > 0.05) htier.h2d_gbs = 0.8 * htier.h2d_gbs + 0.2 * ((double)e.bytes / (ms * 1e6));
+    e.seq = ++htier.seq;
+    htier.loads++;
+    return wrap(m);
 }
 
 int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
@@ -116,6 +218,7 @@ struct PNode {
     int level = 0;
     MatPtr res;
     bool from_cache = false;
+    bool from_host = false;     // copied back from the host tier (offered to the cache again)
     bool filter = false;        // length-2 query: diag(M_1) A diag(M_2)
     int consumers = 0;
     bool keep = false;          // a query's result or a cache candidate
@@ -334,6 +437,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     // plans and the product DAG
     std::vector<PNode> nodes;
     std::unordered_map<std::string, int> by_id;
+    std::unordered_set<std::string> host_known;  // sub-chains planned as copies from the host tier
     std::vector<int> root(nq, -1);
     for (size_t q = 0; q < nq; q++) {
         if (qstatus[q]) continue;
@@ -378,6 +482,13 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                     if (ci) {
                         kc[(size_t)i * p + j] = 0.0;
                         kr[(size_t)i * p + j] = (double)std::static_pointer_cast<DevMat>(ci->payload)->m.nnz / cells;
+                        continue;
+                    }
+                    const double hcost = htier_cost(id);
+                    if (!std::isnan(hcost)) {  // in the host tier: the cost of copying it back
+                        kc[(size_t)i * p + j] = hcost;
+                        kr[(size_t)i * p + j] = (double)htier.items[id].shape.nnz / cells;
+                        host_known.insert(id);
                         continue;
                     }
                     OTEntry *e = otree.entry(ty.data(), ty.size(), key);
@@ -478,6 +589,22 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 }
             }
             int k = split[(size_t)i * p + j];
+            if (k < 0 && host_known.count(id)) {
+                const HostEntry &he = htier.items[id];
+                const double c_ms = he.c_ms, c_ops = he.c_ops;
+                MatPtr hm = htier_load(id);
+                if (hm) {
+                    nd.res = hm;
+                    nd.from_cache = nd.from_host = true;
+                    nd.level = 0;
+                    nd.subtree_ms = c_ms;
+                    nd.c_ops = c_ops;
+                    const int idx = (int)nodes.size();
+                    nodes.push_back(std::move(nd));
+                    by_id.emplace(id, idx);
+                    return idx;
+                }
+            }
             if (k < 0) k = split_pure[(size_t)i * p + j];  // known (evicted) but not at hand: compute it
             nd.k = k;
             const int l = reg(i, k);
@@ -644,7 +771,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     }
     if (cache) {
         auto offer = [&](PNode &nd) {
-            if (nd.from_cache || nd.filter || nd.status || !nd.res) return;
+            if ((nd.from_cache && !nd.from_host) || nd.filter || nd.status || !nd.res) return;
             const double f = (double)otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
             std::vector<CacheItem> ev;
             cstats.requests++;
@@ -664,6 +791,8 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             for (auto &it : ev) {
                 OTEntry *ee = otree.entry(it.types.data(), it.types.size(), it.key);
                 if (ee) ee->cached = false;
+                htier_store(it.id, std::static_pointer_cast<DevMat>(it.payload), it.types, it.key, it.c,
+                            ee ? ee->c_ops : 0.0);
             }
         };
         for (size_t q = 0; q < nq; q++) {

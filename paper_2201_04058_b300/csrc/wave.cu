@@ -348,7 +348,7 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                 const unsigned long long pr = prod[g];
                 atomicAdd(&hc[b], 1u);
                 atomicAdd(&hx[b], xe);
-                atomicAdd(&hp[b], pr);
+                if (!dense) atomicAdd(&hp[b], pr);  // a dense row's products ran in the symbolic pass
                 atomicAdd(&ho[b], (unsigned long long)z);
                 // numeric bytes: X and C row pointers, per X entry its column id (+ value) and
                 // two Y row pointers, per product a Y column id (+ value), per output 12 bytes;
@@ -1128,6 +1128,7 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
         k.launches++;
         k.ms += ms;
         k.bytes += (double)t.bytes[b];
+        k.prods += (double)t.prods[b];
     }
 }
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
-    "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query",
+    "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query", "mp_host_tier_stats",
 ]
 
 
@@ -43,7 +43,7 @@ class mp_config(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("force_bin_class", C.c_int32), ("max_result_bytes", C.c_uint64),
                 ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64),
-                ("insertion", C.c_int32), ("tune_file", C.c_char_p)]
+                ("insertion", C.c_int32), ("tune_file", C.c_char_p), ("host_tier_bytes", C.c_uint64)]
 
 
 class mp_constraint(C.Structure):
@@ -57,7 +57,8 @@ class mp_query(C.Structure):
 
 
 class mp_kernel_stat(C.Structure):
-    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("ms", C.c_double), ("bytes", C.c_double),
+                ("products", C.c_double)]
 
 
 class MPError(RuntimeError):
@@ -101,6 +102,7 @@ def lib():
             "mp_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, U32, P(U32), P(U64)]),
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
+            "mp_host_tier_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 5),
             "mp_hin_save": (C.c_int, [C.c_void_p, C.c_char_p]),
             "mp_hin_load": (C.c_int, [C.c_void_p, C.c_char_p]),
             "mp_autotune": (C.c_int, [C.c_void_p, U32, P(mp_query), U32, C.c_char_p, P(C.c_double)]),
@@ -399,12 +401,12 @@ def mp_plan_chain_mnc(dims, sketches, alpha=1.0, beta=1.0, gamma=1.0, known=None
 
 
 def mp_kernel_stats(ctx):
-    """({name: {"launches", "ms", "bytes"}}, total kernel launches of the library)."""
+    """({name: {"launches", "ms", "bytes", "products"}}, total kernel launches of the library)."""
     arr = (mp_kernel_stat * 64)()
     n, launches = C.c_uint32(), C.c_uint64()
     _ck(lib().mp_kernel_stats(ctx, arr, 64, C.byref(n), C.byref(launches)), "mp_kernel_stats")
-    return ({arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
-             for i in range(n.value)}, launches.value)
+    return ({arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
+                                    "products": arr[i].products} for i in range(n.value)}, launches.value)
 
 
 def mp_cache_stats(ctx):
@@ -412,6 +414,12 @@ def mp_cache_stats(ctx):
     _ck(lib().mp_cache_stats(ctx, *[C.byref(x) for x in v]), "mp_cache_stats")
     return dict(zip(("requests", "hits", "inserts", "rejected", "evictions", "bytes", "entries"),
                     (x.value for x in v)))
+
+
+def mp_host_tier_stats(ctx):
+    v = [C.c_uint64() for _ in range(5)]
+    _ck(lib().mp_host_tier_stats(ctx, *[C.byref(x) for x in v]), "mp_host_tier_stats")
+    return dict(zip(("stores", "loads", "drops", "bytes", "entries"), (x.value for x in v)))
 
 
 def mp_kernel_stats_reset(ctx):

@@ -134,3 +134,30 @@ def test_cache_baselines_match_oracle(c1, batch_queries, cuda_ok, insertion, pol
         assert st["inserts"] > 0
     finally:
         e.close()
+
+
+@pytest.mark.parametrize("host_bytes", [256 << 20, 256 << 10])
+def test_host_tier_results_and_reuse(c1, batch_queries, cuda_ok, host_bytes):
+    """A device cache far too small for the batch's intermediates, every computed node
+    offered (CBS2), and a second tier in host memory: evicted results go down, later plans
+    copy some back instead of recomputing them, and every result stays the oracle's. A host
+    tier smaller than the evicted results drops its least recently used entries."""
+    mp = _mp()
+    qs, want = batch_queries
+    e = mp.Engine(c1[0], policy=mp.MP_POLICY_ATRAPOS, hbm_budget_bytes=2 << 20, host_tier_bytes=host_bytes,
+                  insertion=mp.MP_INSERT_ALL)
+    try:
+        for rnd in range(3):
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g, w in zip(qs, res, want):
+                assert_same(g, w, ("host tier", host_bytes, rnd, "".join(q["types"])))
+        st = mp.mp_host_tier_stats(e.ctx)
+        assert st["stores"] > 0
+        assert st["bytes"] <= host_bytes
+        if host_bytes >= (256 << 20):
+            assert st["loads"] > 0
+        else:
+            assert st["drops"] > 0 or st["entries"] == st["stores"]
+    finally:
+        e.close()
