@@ -142,6 +142,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "fail_alloc_after_finalize") ctx->fail_alloc_after = (uint64_t)v;
                 else if (k == "glob_dense") ctx->tun.glob_dense = strtod(kv.c_str() + eq + 1, nullptr);
                 else if (k == "dense_scratch") ctx->tun.dense_scratch_cap = (uint64_t)v;
+                else if (k == "glob_occ") ctx->tun.glob_occ = (int)v;
             }
             a = b + 1;
         }

@@ -49,6 +49,7 @@ struct Tuning {
     // row (one pass gives both the size and the values); 0 turns the dense rows off
     double glob_dense = 1.0;
     uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
+    int glob_occ = 4;  // resident blocks per SM of the count-adding split-row kernels (4 or 6)
     int sm_count = 148;
 };
 

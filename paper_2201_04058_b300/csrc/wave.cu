@@ -194,7 +194,7 @@ __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
         const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
-        const int64_t nb = std::min<int64_t>(G, (e - b + LONGCH - 1) / LONGCH);
+        const int64_t nb = min(G, (e - b + LONGCH - 1) / LONGCH);
         const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
         if (off >= nb) continue;  // uniform over the block
         unsigned long long s = 0;
@@ -785,8 +785,8 @@ __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const i
 // positions the bitmap ranks give; G_DENSE adds the counts into the row's dense slot (the
 // bitmap comes from a scan of the slot afterwards: every count is >= 1).
 enum { G_SYM = 0, G_NUM = 1, G_DENSE = 2 };
-template <int MODE, bool COMB>
-__global__ void __launch_bounds__(GNT, MODE != G_SYM ? 4 : 8) k_glob_set(PassArgs a, GlobArgs g) {
+template <int MODE, bool COMB, int OCC>
+__global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassArgs a, GlobArgs g) {
     constexpr bool NUM = MODE != G_SYM;
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
@@ -1158,6 +1158,22 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     g = Glob{};
 }
 
+// The split-row kernel in the variant the tuning asks for: combining table on or off, and
+// for the count-adding modes 4 or 6 resident blocks per SM (64 or 40 registers a thread).
+// One block per resident slot: the blocks loop over the work items.
+template <int MODE>
+static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga) {
+    const int occ = MODE == G_SYM ? 8 : tun.glob_occ >= 6 ? 6 : 4;
+    const unsigned grid = (unsigned)(tun.sm_count * occ);
+    if (MODE != G_SYM && occ == 6) {
+        if (tun.combine) kl(k_glob_set<MODE, true, 6>, grid, GNT, 0, s, a, ga);
+        else kl(k_glob_set<MODE, false, 6>, grid, GNT, 0, s, a, ga);
+    } else {
+        if (tun.combine) kl(k_glob_set<MODE, true, 4>, grid, GNT, 0, s, a, ga);
+        else kl(k_glob_set<MODE, false, 4>, grid, GNT, 0, s, a, ga);
+    }
+}
+
 // One pass of the GLOBAL bin (all rounds). pass 0 counts, pass 1 writes the rows.
 static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, cudaStream_t s, Prof *prof) {
     const unsigned grid = (unsigned)tun.sm_count * 8;
@@ -1168,8 +1184,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         const int64_t words = g.nd * g.nw;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
-            if (tun.combine) kl(k_glob_set<G_DENSE, true>, grid, GNT, 0, s, a, ga);
-            else kl(k_glob_set<G_DENSE, false>, grid, GNT, 0, s, a, ga);
+            glob_set<G_DENSE>(tun, s, a, ga);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
                256, 0, s, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
@@ -1184,16 +1199,14 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
-            if (tun.combine) kl(k_glob_set<G_SYM, true>, grid, GNT, 0, s, a, ga);
-            else kl(k_glob_set<G_SYM, false>, grid, GNT, 0, s, a, ga);
+            glob_set<G_SYM>(tun, s, a, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
             kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
                s, a, ga);
-            if (tun.combine) kl(k_glob_set<G_NUM, true>, grid, GNT, 0, s, a, ga);
-            else kl(k_glob_set<G_NUM, false>, grid, GNT, 0, s, a, ga);
+            glob_set<G_NUM>(tun, s, a, ga);
         }
     }
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);

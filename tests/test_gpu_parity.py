@@ -237,22 +237,24 @@ def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatc
             e.close()
 
 
-@pytest.mark.parametrize("combine,glob_dense,dense_scratch", [
-    (1, 0, 0),            # dense rows off: every split row takes bitmap rounds
-    (1, 1e-9, 0),         # every split row takes a dense row
-    (0, 1e-9, 0),         # ... without the shared-memory combining table
-    (1, 1e-9, 200000),    # the dense scratch holds a few rows; the rest take bitmap rounds
-    (1, 1e-9, 1),         # no dense row fits: rows qualify, all take bitmap rounds
-    (1, 0.5, 0),          # half the default threshold
-    (1, 1.0, 0),          # the default threshold
+@pytest.mark.parametrize("combine,glob_dense,dense_scratch,occ", [
+    (1, 0, 0, 4),            # dense rows off: every split row takes bitmap rounds
+    (1, 1e-9, 0, 4),         # every split row takes a dense row
+    (0, 1e-9, 0, 4),         # ... without the shared-memory combining table
+    (1, 1e-9, 200000, 4),    # the dense scratch holds a few rows; the rest take bitmap rounds
+    (1, 1e-9, 1, 4),         # no dense row fits: rows qualify, all take bitmap rounds
+    (1, 0.5, 0, 4),          # half the default threshold
+    (1, 1.0, 0, 4),          # the default threshold
+    (1, 1e-9, 200000, 6),    # 6 resident blocks per SM (40 registers) for the adding kernels
+    (0, 0, 0, 6),
 ])
-def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, monkeypatch):
+def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, occ, monkeypatch):
     """Split rows that accumulate in a dense u64 row (one pass for size and values, a fill
     afterwards) give the oracle's results, alone and mixed with bitmap rows when the dense
     scratch runs out, one query at a time and as one batch. (The overflow test above runs
     its forced split rows through dense rows under the default threshold.)"""
     mp = _mp()
-    tune = f"combine={combine},glob_dense={glob_dense}"
+    tune = f"combine={combine},glob_dense={glob_dense},glob_occ={occ}"
     if dense_scratch:
         tune += f",dense_scratch={dense_scratch}"
     monkeypatch.setenv("MP_TUNING", tune)
