@@ -143,6 +143,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "glob_dense") ctx->tun.glob_dense = strtod(kv.c_str() + eq + 1, nullptr);
                 else if (k == "dense_scratch") ctx->tun.dense_scratch_cap = (uint64_t)v;
                 else if (k == "glob_occ") ctx->tun.glob_occ = (int)v;
+                else if (k == "seg_walk") ctx->tun.seg_walk = (int)v;
             }
             a = b + 1;
         }
@@ -161,13 +162,17 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 if (p && (p = strchr(p, ':'))) *v = strtod(p + 1, nullptr);
             };
             double dmu = ctx->tun.dense_min_u, hv = (double)ctx->tun.heavy;
-            double cb = ctx->tun.combine, sw = ctx->tun.short_walk;
+            double cb = ctx->tun.combine, sw = ctx->tun.short_walk, gw = ctx->tun.seg_walk, oc = ctx->tun.glob_occ;
             num("\"dense_min_u\"", &dmu);
             num("\"heavy\"", &hv);
             num("\"combine\"", &cb);
             num("\"short_walk\"", &sw);
+            num("\"seg_walk\"", &gw);
+            num("\"glob_occ\"", &oc);
             ctx->tun.combine = (int)cb;
             ctx->tun.short_walk = (int)sw;
+            ctx->tun.seg_walk = (int)gw;
+            ctx->tun.glob_occ = (int)oc;
             num("\"alpha\"", &ctx->cfg.alpha);
             num("\"beta\"", &ctx->cfg.beta);
             num("\"gamma\"", &ctx->cfg.gamma);
@@ -787,13 +792,14 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
                 best_t = ctx->tun;
             }
         }
-    // the split-row kernel variants at the best thresholds
-    const int comb0 = best_t.combine, walk0 = best_t.short_walk;
+    // the split-row kernel variants at the best thresholds, one knob flipped at a time from
+    // the best so far: combining table, short-row walk, segment walk, 4 or 6 blocks per SM
     for (int v = 0; v < 4 && !rc; v++) {
         ctx->tun = best_t;
-        ctx->tun.combine = v & 1;
-        ctx->tun.short_walk = (v >> 1) & 1;
-        if (ctx->tun.combine == comb0 && ctx->tun.short_walk == walk0) continue;
+        if (v == 0) ctx->tun.combine ^= 1;
+        if (v == 1) ctx->tun.short_walk ^= 1;
+        if (v == 2) ctx->tun.seg_walk ^= 1;
+        if (v == 3) ctx->tun.glob_occ = ctx->tun.glob_occ >= 6 ? 4 : 6;
         std::vector<double> ts;
         for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
             std::vector<Query> qs = parsed;
@@ -807,8 +813,9 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
         std::sort(ts.begin(), ts.end());
         const double med = ts[ts.size() / 2];
         char line[200];
-        snprintf(line, sizeof(line), ", {\"combine\": %d, \"short_walk\": %d, \"ms\": %.4f}", ctx->tun.combine,
-                 ctx->tun.short_walk, med);
+        snprintf(line, sizeof(line),
+                 ", {\"combine\": %d, \"short_walk\": %d, \"seg_walk\": %d, \"glob_occ\": %d, \"ms\": %.4f}",
+                 ctx->tun.combine, ctx->tun.short_walk, ctx->tun.seg_walk, ctx->tun.glob_occ, med);
         log += line;
         if (med < best) {
             best = med;
@@ -873,10 +880,12 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
         FILE *f = fopen(out_path, "w");
         if (!f) return MP_ERR_ARG;
         fprintf(f, "{\"dense_min_u\": %d, \"heavy\": %llu, \"combine\": %d, \"short_walk\": %d, "
+                   "\"seg_walk\": %d, \"glob_occ\": %d, "
                    "\"alpha\": %.9g, \"beta\": %.9g, \"gamma\": %.9g, \"fitted\": %s, \"best_ms\": %.4f, "
                    "\"candidates\": [%s]}\n",
                 ctx->tun.dense_min_u, (unsigned long long)ctx->tun.heavy, ctx->tun.combine, ctx->tun.short_walk,
-                coef[0], coef[1], coef[2], fitted ? "true" : "false", best, log.c_str());
+                ctx->tun.seg_walk, ctx->tun.glob_occ, coef[0], coef[1], coef[2], fitted ? "true" : "false", best,
+                log.c_str());
         fclose(f);
     }
     return MP_OK;

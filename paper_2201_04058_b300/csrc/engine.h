@@ -7,6 +7,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -117,26 +118,32 @@ struct mp_ctx {
     CacheCounters cstats;
     // Second cache tier in pinned host memory (mp_config.host_tier_bytes): a result the
     // device cache evicts is copied down; a later plan may treat it as known at the cost of
-    // copying it back, and then loads it instead of recomputing it. Least recently used
-    // entries leave when the tier is full.
+    // copying it back, and then loads it instead of recomputing it. The tier is one pinned
+    // arena (allocated at the first store) with a first-fit allocator; least recently used
+    // entries leave when no free block fits.
     struct HostEntry {
         std::vector<int32_t> types;
         std::string key;
         mp::Mat shape;        // sizes and value bound (its pointers are unused)
-        void *buf = nullptr;  // pinned: row pointers | column ids | counts
+        size_t off = 0;       // in the arena: row pointers | column ids | counts
         size_t bytes = 0;
         double c_ms = 0.0, c_ops = 0.0;  // recorded computation time and Eq. 2 cost
         uint64_t seq = 0;
     };
     struct HostTier {
+        char *arena = nullptr;
+        size_t cap = 0;
+        std::map<size_t, size_t> free_blocks;  // offset -> size, coalesced
         std::unordered_map<std::string, HostEntry> items;
         size_t bytes = 0;
         uint64_t seq = 0, stores = 0, loads = 0, drops = 0;
-        double h2d_gbs = 20.0;  // running estimate of the copy-back rate
+        double h2d_gbs = 0.0;  // measured once when the arena is made
     } htier;
+    bool htier_reserve(size_t bytes, size_t *off);  // evicts LRU entries until a block fits
+    void htier_release(size_t off, size_t bytes);
     void htier_store(const std::string &id, const MatPtr &m, const std::vector<int32_t> &types,
                      const std::string &key, double c_ms, double c_ops);
-    MatPtr htier_load(const std::string &id);
+    MatPtr htier_load(const std::string &id);        // stream-ordered copy back, no sync
     double htier_cost(const std::string &id) const;  // Eq. 2 units, NaN when absent
     void htier_clear();
 

@@ -57,9 +57,52 @@ void mp_ctx::cache_clear() {
 }
 
 void mp_ctx::htier_clear() {
-    for (auto &kv : htier.items) cudaFreeHost(kv.second.buf);
+    if (htier.arena) {
+        cudaStreamSynchronize(stream);  // no copy back may still read the arena
+        cudaFreeHost(htier.arena);
+    }
+    htier.arena = nullptr;
+    htier.cap = 0;
+    htier.free_blocks.clear();
     htier.items.clear();
     htier.bytes = 0;
+}
+
+void mp_ctx::htier_release(size_t off, size_t bytes) {
+    auto it = htier.free_blocks.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != htier.free_blocks.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        htier.free_blocks.erase(nx);
+    }
+    if (it != htier.free_blocks.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            htier.free_blocks.erase(it);
+        }
+    }
+}
+
+bool mp_ctx::htier_reserve(size_t bytes, size_t *off) {
+    for (;;) {
+        for (auto &fb : htier.free_blocks)
+            if (fb.second >= bytes) {
+                *off = fb.first;
+                const size_t rest = fb.second - bytes, at = fb.first + bytes;
+                htier.free_blocks.erase(fb.first);
+                if (rest) htier.free_blocks.emplace(at, rest);
+                return true;
+            }
+        if (htier.items.empty()) return false;
+        auto lru = htier.items.begin();
+        for (auto x = htier.items.begin(); x != htier.items.end(); ++x)
+            if (x->second.seq < lru->second.seq) lru = x;
+        htier_release(lru->second.off, lru->second.bytes);
+        htier.bytes -= lru->second.bytes;
+        htier.items.erase(lru);
+        htier.drops++;
+    }
 }
 
 void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vector<int32_t> &types,
@@ -71,33 +114,47 @@ void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vect
         it->second.seq = ++htier.seq;
         return;
     }
+    if (!htier.arena) {
+        // the arena, and the copy-back rate the planner prices a load with
+        if (cudaMallocHost((void **)&htier.arena, cap) != cudaSuccess) {
+            cudaGetLastError();
+            htier.arena = nullptr;
+            return;
+        }
+        htier.cap = cap;
+        htier.free_blocks.clear();
+        htier.free_blocks.emplace(0, cap);
+        const size_t probe = std::min<size_t>(cap, 64u << 20);
+        void *d = alloc->alloc(probe, stream);
+        if (d) {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);  // warm the path
+            cudaEventRecord(e0, stream);
+            cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);
+            cudaEventRecord(e1, stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms > 0.f) htier.h2d_gbs = (double)probe / (ms * 1e6);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            alloc->free(d, stream);
+        }
+        if (htier.h2d_gbs <= 0.0) htier.h2d_gbs = 20.0;
+    }
     const Mat &A = m->m;
     const size_t brp = (size_t)(A.nrows + 1) * 8, bci = (size_t)A.nnz * 4, bval = (size_t)A.nnz * 8;
-    const size_t bytes = brp + bci + bval;
+    const size_t bytes = (brp + bci + bval + 15) & ~(size_t)15;
     if ((double)bytes > 0.8 * (double)cap) return;  // the 80 % rule of the device cache
-    while (htier.bytes + bytes > cap && !htier.items.empty()) {
-        auto lru = htier.items.begin();
-        for (auto x = htier.items.begin(); x != htier.items.end(); ++x)
-            if (x->second.seq < lru->second.seq) lru = x;
-        cudaFreeHost(lru->second.buf);
-        htier.bytes -= lru->second.bytes;
-        htier.items.erase(lru);
-        htier.drops++;
-    }
-    void *buf = nullptr;
-    if (cudaMallocHost(&buf, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    char *b = (char *)buf;
+    size_t off = 0;
+    if (!htier_reserve(bytes, &off)) return;
+    char *b = htier.arena + off;
     cudaMemcpyAsync(b, A.rp, brp, cudaMemcpyDeviceToHost, stream);
     if (A.nnz) {
         cudaMemcpyAsync(b + brp, A.ci, bci, cudaMemcpyDeviceToHost, stream);
         cudaMemcpyAsync(b + brp + bci, A.val, bval, cudaMemcpyDeviceToHost, stream);
-    }
-    if (cudaStreamSynchronize(stream) != cudaSuccess) {
-        cudaFreeHost(buf);
-        return;
     }
     HostEntry e;
     e.types = types;
@@ -106,7 +163,7 @@ void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vect
     e.shape.rp = nullptr;
     e.shape.ci = nullptr;
     e.shape.val = nullptr;
-    e.buf = buf;
+    e.off = off;
     e.bytes = bytes;
     e.c_ms = c_ms;
     e.c_ops = c_ops;
@@ -138,19 +195,14 @@ MatPtr mp_ctx::htier_load(const std::string &id) {
         free_mat(m);
         return nullptr;
     }
-    const auto t0 = std::chrono::steady_clock::now();
-    const char *b = (const char *)e.buf;
+    // ordered on the stream before every kernel that reads the result; the arena block
+    // stays put until the batch ends (stores and drops happen after the batch's waves)
+    const char *b = htier.arena + e.off;
     cudaMemcpyAsync(m.rp, b, brp, cudaMemcpyHostToDevice, stream);
     if (m.nnz) {
         cudaMemcpyAsync(m.ci, b + brp, bci, cudaMemcpyHostToDevice, stream);
         cudaMemcpyAsync(m.val, b + brp + bci, bval, cudaMemcpyHostToDevice, stream);
     }
-    if (cudaStreamSynchronize(stream) != cudaSuccess) {
-        free_mat(m);
-        return nullptr;
-    }
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (ms > 0.05) htier.h2d_gbs = 0.8 * htier.h2d_gbs + 0.2 * ((double)e.bytes / (ms * 1e6));
     e.seq = ++htier.seq;
     htier.loads++;
     return wrap(m);

@@ -708,6 +708,8 @@ static constexpr int64_t PCH = 16384;  // Gustavson products per work item
 static constexpr int GNT = 256;        // threads per GLOBAL block
 static constexpr int RW = 8;           // bitmap words per thread in the rank pass
 static constexpr int CSLOT = 1024;     // shared-memory combining slots per work item
+static constexpr int SEG = 256;        // products per warp segment in the segment walk
+static constexpr int SEGMIN = 32;      // mean products per staged X entry for the segment walk
 
 struct GlobArgs {
     const uint32_t *list;     // wave rows of the GLOBAL bin, in symbolic order
@@ -719,6 +721,7 @@ struct GlobArgs {
     uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
     int64_t nw;               // slot size (words)
     int short_walk;           // walk chunks of short Y rows one X entry per thread
+    int seg_walk;             // walk chunks of long Y rows one warp per segment
     unsigned long long *dval; // dense rows: (r1 - r0) slots of dcols counts each
     int64_t dcols;
 };
@@ -791,6 +794,8 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
     __shared__ int64_t s_off[GNT + 1];
     __shared__ int64_t s_st[GNT];
     __shared__ uint64_t s_a[GNT];
+    __shared__ int32_t s_seg[GNT];  // segment walk: first segment of each staged X entry
+    __shared__ int64_t s_wsum[32], s_gtot;
     // combining table for the item's hot outputs: key = bitmap word (symbolic) or output
     // column (numeric); first come claims a slot, other keys go straight to global memory
     __shared__ uint32_t s_key[CSLOT];
@@ -907,6 +912,32 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
                     const int l = threadIdx.x;
                     const int64_t lo_f = max(s_off[l], f0), hi_f = min(s_off[l + 1], f1);
                     for (int64_t f = lo_f; f < hi_f; f++) product(l, s_st[l] + (f - s_off[l]));
+                }
+            } else if (g.seg_walk && s_off[nent] >= SEGMIN * (int64_t)nent) {
+                // long Y rows: the X entries' products are cut into segments of up to SEG;
+                // a warp takes a segment (its X entry found once per segment) and its lanes
+                // read the Y row coalesced
+                int cnt = 0;
+                if ((int)threadIdx.x < nent) {
+                    const int l = threadIdx.x;
+                    const int64_t lo_f = max(s_off[l], f0), hi_f = min(s_off[l + 1], f1);
+                    cnt = hi_f > lo_f ? (int)((hi_f - lo_f + SEG - 1) / SEG) : 0;
+                }
+                const int64_t ex = block_excl_scan<GNT>(cnt, s_wsum, &s_gtot);
+                if ((int)threadIdx.x < nent) s_seg[threadIdx.x] = (int32_t)ex;
+                __syncthreads();
+                const int nseg = (int)s_gtot;
+                const int lane = threadIdx.x & 31;
+                for (int sg = threadIdx.x >> 5; sg < nseg; sg += GNT / 32) {
+                    // the last entry whose first segment is at or before sg (it has segments)
+                    int l = 0, h = nent - 1;
+                    while (l < h) {
+                        const int mid = (l + h + 1) >> 1;
+                        if (s_seg[mid] <= sg) l = mid; else h = mid - 1;
+                    }
+                    const int64_t b0 = max(s_off[l], f0) + (int64_t)(sg - s_seg[l]) * SEG;
+                    const int64_t b1 = min(b0 + SEG, min(s_off[l + 1], f1));
+                    for (int64_t f = b0 + lane; f < b1; f += 32) product(l, s_st[l] + (f - s_off[l]));
                 }
             } else {
                 // long Y rows: consecutive threads take consecutive products (coalesced Y
@@ -1165,7 +1196,10 @@ template <int MODE>
 static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga) {
     const int occ = MODE == G_SYM ? 8 : tun.glob_occ >= 6 ? 6 : 4;
     const unsigned grid = (unsigned)(tun.sm_count * occ);
-    if (MODE != G_SYM && occ == 6) {
+    if constexpr (MODE == G_SYM) {
+        if (tun.combine) kl(k_glob_set<MODE, true, 8>, grid, GNT, 0, s, a, ga);
+        else kl(k_glob_set<MODE, false, 8>, grid, GNT, 0, s, a, ga);
+    } else if (occ == 6) {
         if (tun.combine) kl(k_glob_set<MODE, true, 6>, grid, GNT, 0, s, a, ga);
         else kl(k_glob_set<MODE, false, 6>, grid, GNT, 0, s, a, ga);
     } else {
@@ -1180,7 +1214,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
         const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, 0, g.nd, g.dbmr, g.nw, tun.short_walk,
-                          g.dval, g.dcols};
+                          tun.seg_walk, g.dval, g.dcols};
         const int64_t words = g.nd * g.nw;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
@@ -1195,7 +1229,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
         const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bmr,
-                          g.nw, tun.short_walk, nullptr, 0};
+                          g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);

@@ -29,10 +29,12 @@ def test_autotune_persists_and_keeps_results(cuda_ok, tmp_path):
     finally:
         e.close()
     d = json.load(open(path))
-    # 9 threshold pairs, 3 more kernel variants, and the re-timed Eq. 2 fit
-    assert len(d["candidates"]) in (12, 13)
+    # 9 threshold pairs, 4 kernel variants (one knob flipped at a time), and the re-timed
+    # Eq. 2 fit when there is one
+    assert len(d["candidates"]) in (13, 14)
     assert d["dense_min_u"] in (64, 256, 1024) and d["heavy"] in (16384, 65536, 262144)
-    assert d["combine"] in (0, 1) and d["short_walk"] in (0, 1)
+    assert d["combine"] in (0, 1) and d["short_walk"] in (0, 1) and d["seg_walk"] in (0, 1)
+    assert d["glob_occ"] in (4, 6)
     assert min(c["ms"] for c in d["candidates"]) == pytest.approx(d["best_ms"])
     assert d["alpha"] > 0 and d["beta"] > 0 and d["gamma"] > 0
     if not d["fitted"]:

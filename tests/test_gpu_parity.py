@@ -248,13 +248,14 @@ def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatc
     (1, 1e-9, 200000, 6),    # 6 resident blocks per SM (40 registers) for the adding kernels
     (0, 0, 0, 6),
 ])
-def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, occ, monkeypatch):
+@pytest.mark.parametrize("seg_walk", [0, 1])
+def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, occ, seg_walk, monkeypatch):
     """Split rows that accumulate in a dense u64 row (one pass for size and values, a fill
     afterwards) give the oracle's results, alone and mixed with bitmap rows when the dense
     scratch runs out, one query at a time and as one batch. (The overflow test above runs
     its forced split rows through dense rows under the default threshold.)"""
     mp = _mp()
-    tune = f"combine={combine},glob_dense={glob_dense},glob_occ={occ}"
+    tune = f"combine={combine},glob_dense={glob_dense},glob_occ={occ},seg_walk={seg_walk}"
     if dense_scratch:
         tune += f",dense_scratch={dense_scratch}"
     monkeypatch.setenv("MP_TUNING", tune)
