@@ -186,6 +186,8 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
     if (!ctx->prof.init()) return MP_ERR_CUDA;
+    // the host tier's pinned arena is made here, not inside a query
+    if (ctx->cache && c.host_tier_bytes && !ctx->htier_init()) return MP_ERR_NOMEM;
     *out = ctx.release();
     return MP_OK;
 }
@@ -203,6 +205,8 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         for (auto &p : ctx->props)
             if (p.dev) ctx->alloc->free(p.dev, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->htier.arena) cudaFreeHost(ctx->htier.arena);
+        ctx->htier.arena = nullptr;
         cudaEventDestroy(ctx->ev0);
         cudaEventDestroy(ctx->ev1);
         ctx->prof.destroy();

@@ -139,6 +139,7 @@ struct mp_ctx {
         uint64_t seq = 0, stores = 0, loads = 0, drops = 0;
         double h2d_gbs = 0.0;  // measured once when the arena is made
     } htier;
+    bool htier_init();  // the pinned arena and the measured copy-back rate
     bool htier_reserve(size_t bytes, size_t *off);  // evicts LRU entries until a block fits
     void htier_release(size_t off, size_t bytes);
     void htier_store(const std::string &id, const MatPtr &m, const std::vector<int32_t> &types,

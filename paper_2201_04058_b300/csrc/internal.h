@@ -44,7 +44,7 @@ struct Tuning {
     uint64_t warp_prod = 4096;   // rows with more products skip the one-warp bins
     int combine = 1;             // split-row kernel: shared-memory combining of hot outputs
     int short_walk = 0;          // split-row kernel: one thread per X entry on short Y rows
-    int seg_walk = 0;            // split-row kernel: one warp per segment on long Y rows
+    int seg_walk = 1;            // split-row kernel: one warp per segment on long Y rows
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     // GLOBAL rows with prod_i >= glob_dense * ncols accumulate their counts in a dense u64
     // row (one pass gives both the size and the values); 0 turns the dense rows off

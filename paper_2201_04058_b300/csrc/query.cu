@@ -57,15 +57,44 @@ void mp_ctx::cache_clear() {
 }
 
 void mp_ctx::htier_clear() {
-    if (htier.arena) {
-        cudaStreamSynchronize(stream);  // no copy back may still read the arena
-        cudaFreeHost(htier.arena);
-    }
-    htier.arena = nullptr;
-    htier.cap = 0;
+    if (htier.arena) cudaStreamSynchronize(stream);  // no copy may still use the arena
     htier.free_blocks.clear();
+    if (htier.cap) htier.free_blocks.emplace(0, htier.cap);
     htier.items.clear();
     htier.bytes = 0;
+}
+
+bool mp_ctx::htier_init() {
+    const size_t cap = (size_t)cfg.host_tier_bytes;
+    if (cudaMallocHost((void **)&htier.arena, cap) != cudaSuccess) {
+        cudaGetLastError();
+        htier.arena = nullptr;
+        return false;
+    }
+    htier.cap = cap;
+    htier.free_blocks.clear();
+    htier.free_blocks.emplace(0, cap);
+    // the copy-back rate the planner prices a load with: one timed copy of up to 64 MB
+    const size_t probe = std::min<size_t>(cap, 64u << 20);
+    void *d = alloc->alloc(probe, stream);
+    if (d) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);  // warm the path
+        cudaEventRecord(e0, stream);
+        cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);
+        cudaEventRecord(e1, stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.f) htier.h2d_gbs = (double)probe / (ms * 1e6);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        alloc->free(d, stream);
+    }
+    if (htier.h2d_gbs <= 0.0) htier.h2d_gbs = 20.0;
+    return true;
 }
 
 void mp_ctx::htier_release(size_t off, size_t bytes) {
@@ -114,36 +143,7 @@ void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vect
         it->second.seq = ++htier.seq;
         return;
     }
-    if (!htier.arena) {
-        // the arena, and the copy-back rate the planner prices a load with
-        if (cudaMallocHost((void **)&htier.arena, cap) != cudaSuccess) {
-            cudaGetLastError();
-            htier.arena = nullptr;
-            return;
-        }
-        htier.cap = cap;
-        htier.free_blocks.clear();
-        htier.free_blocks.emplace(0, cap);
-        const size_t probe = std::min<size_t>(cap, 64u << 20);
-        void *d = alloc->alloc(probe, stream);
-        if (d) {
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);  // warm the path
-            cudaEventRecord(e0, stream);
-            cudaMemcpyAsync(d, htier.arena, probe, cudaMemcpyHostToDevice, stream);
-            cudaEventRecord(e1, stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms > 0.f) htier.h2d_gbs = (double)probe / (ms * 1e6);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            alloc->free(d, stream);
-        }
-        if (htier.h2d_gbs <= 0.0) htier.h2d_gbs = 20.0;
-    }
+    if (!htier.arena) return;
     const Mat &A = m->m;
     const size_t brp = (size_t)(A.nrows + 1) * 8, bci = (size_t)A.nnz * 4, bval = (size_t)A.nnz * 8;
     const size_t bytes = (brp + bci + bval + 15) & ~(size_t)15;

@@ -859,7 +859,10 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
             const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
             auto product = [&](int l, int64_t q) {
                 const uint32_t j = (uint32_t)__ldg(yci + q);
-                if (!bit_of(cm, j)) return;
+                // the column mask: the symbolic bitmap needs it exactly; when counts cannot
+                // overflow, the adding modes leave it to the bitmap (G_NUM: a cleared bit)
+                // or to the dense row's scan (G_DENSE), which saves a dependent load
+                if ((!NUM || chk) && !bit_of(cm, j)) return;
                 unsigned long long add;
                 if (!NUM) {
                     add = 1ull << (j & 31);
@@ -896,6 +899,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
                         dst = val + j;
                     } else {
                         const uint2 br = __ldg(bmr + (j >> 5));
+                        if (!((br.x >> (j & 31)) & 1u)) return;  // a masked-out column
                         dst = val + br.y + __popc(br.x & ((1u << (j & 31)) - 1u));
                     }
                     if (chk) {
@@ -965,7 +969,13 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
                     dst = val + k;
                 } else {
                     const uint2 br = __ldg(bmr + (k >> 5));
-                    dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
+                    if ((br.x >> (k & 31)) & 1u) {
+                        dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
+                    } else {  // a masked-out column combined in the table
+                        s_key[x] = EMPTY;
+                        s_acc[x] = 0;
+                        continue;
+                    }
                 }
                 const unsigned long long v = s_acc[x];
                 if (chk) {
@@ -1038,14 +1048,17 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
 
 // Dense rows: one warp per bitmap word; lane i reads column 32w + i of the dense slot
 // (coalesced) and the ballot of the non-zero counts is the word.
-__global__ void k_glob_dscan(GlobArgs g) {
+__global__ void k_glob_dscan(PassArgs a, GlobArgs g) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (g.r1 - g.r0) * g.nw;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < total; x += nwarps) {
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const int64_t j = w * 32 + lane;
-        const bool nz = j < g.dcols && g.dval[slot * g.dcols + j] != 0;
+        // the row's column mask applies here (the adding pass skips it when counts cannot
+        // overflow); a masked-out column's count is dropped
+        const uint32_t *cm = a.prods[a.rowprod[g.list[g.r0 + slot]]].cm;
+        const bool nz = j < g.dcols && g.dval[slot * g.dcols + j] != 0 && bit_of(cm, (uint32_t)j);
         const unsigned word = __ballot_sync(FULL, nz);
         if (lane == 0) g.bmr[x] = make_uint2(word, 0u);
     }
@@ -1220,7 +1233,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
             glob_set<G_DENSE>(tun, s, a, ga);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
-               256, 0, s, ga);
+               256, 0, s, a, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
         } else {
             kl(k_glob_dfill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256,
