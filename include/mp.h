@@ -210,6 +210,18 @@ int mp_result_copy(mp_ctx *ctx, mp_ticket ticket, int64_t *row_ptr, int32_t *col
 /* Drop a ticket and its result. */
 int mp_release(mp_ctx *ctx, mp_ticket ticket);
 
+/* mp_result_copy without waiting: the copies are queued on the context's copy stream and
+ * the call returns at once, so the next query can run while the result travels. The
+ * destination buffers must stay valid, and must not be read, until mp_result_copy_wait
+ * returns for the ticket (host buffers should be pinned for the copy to overlap); wait
+ * before mp_release (a release first still frees the device memory only after the copy,
+ * but leaves nothing to wait on). Errors as mp_result_copy. */
+int mp_result_copy_async(mp_ctx *ctx, mp_ticket ticket, int64_t *row_ptr, int32_t *col, uint64_t *val,
+                         int on_device);
+/* Blocks until the ticket's last asynchronous copy has landed (MP_OK at once if none).
+ * MP_ERR_NOTFOUND for an unknown or released ticket. */
+int mp_result_copy_wait(mp_ctx *ctx, mp_ticket ticket);
+
 /* Device time in milliseconds spent on the ticket's query (products it ran itself). */
 int mp_result_time(mp_ctx *ctx, mp_ticket ticket, double *ms);
 

@@ -200,6 +200,12 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         std::lock_guard<std::mutex> ge(ctx->exec_mu);
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->cache_clear();
+        ctx->mnc_memo.clear();
+        for (auto &kv : ctx->results)
+            if (kv.second.copy_ev) {
+                cudaEventSynchronize(kv.second.copy_ev);
+                cudaEventDestroy(kv.second.copy_ev);
+            }
         ctx->results.clear();
         for (auto &r : ctx->rels) ctx->free_mat(r.dev);
         for (auto &p : ctx->props)
@@ -954,11 +960,55 @@ extern "C" int mp_result_copy(mp_ctx *ctx, mp_ticket t, int64_t *row_ptr, int32_
     return check_cuda(cudaStreamSynchronize(s), "copy");
 }
 
+extern "C" int mp_result_copy_async(mp_ctx *ctx, mp_ticket t, int64_t *row_ptr, int32_t *col, uint64_t *val,
+                                    int on_device) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->results.find(t);
+    if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (!it->second.done) return MP_ERR_STATE;
+    if (it->second.status) return it->second.status;
+    cudaSetDevice(ctx->cfg.device);
+    const Mat &m = it->second.m->m;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t s = ctx->copy_stream;
+    if (!it->second.copy_ev &&
+        check_cuda(cudaEventCreateWithFlags(&it->second.copy_ev, cudaEventDisableTiming), "event"))
+        return MP_ERR_CUDA;
+    if (row_ptr && check_cuda(cudaMemcpyAsync(row_ptr, m.rp, (size_t)(m.nrows + 1) * 8, k, s), "copy"))
+        return MP_ERR_CUDA;
+    if (m.nnz && col && check_cuda(cudaMemcpyAsync(col, m.ci, (size_t)m.nnz * 4, k, s), "copy"))
+        return MP_ERR_CUDA;
+    if (m.nnz && val && check_cuda(cudaMemcpyAsync(val, m.val, (size_t)m.nnz * 8, k, s), "copy"))
+        return MP_ERR_CUDA;
+    return check_cuda(cudaEventRecord(it->second.copy_ev, s), "event");
+}
+
+extern "C" int mp_result_copy_wait(mp_ctx *ctx, mp_ticket t) {
+    if (!ctx) return MP_ERR_ARG;
+    cudaEvent_t ev = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->results.find(t);
+        if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+        ev = it->second.copy_ev;
+    }
+    if (!ev) return MP_OK;
+    return check_cuda(cudaEventSynchronize(ev), "copy");
+}
+
 extern "C" int mp_release(mp_ctx *ctx, mp_ticket t) {
     if (!ctx) return MP_ERR_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
     auto it = ctx->results.find(t);
     if (it == ctx->results.end()) return MP_ERR_NOTFOUND;
+    if (it->second.copy_ev) {
+        // the result's device memory is freed in the order of the context's stream: let
+        // that stream first wait for an asynchronous copy still reading it
+        cudaSetDevice(ctx->cfg.device);
+        cudaStreamWaitEvent(ctx->stream, it->second.copy_ev, 0);
+        cudaEventDestroy(it->second.copy_ev);
+    }
     ctx->results.erase(it);
     return MP_OK;
 }

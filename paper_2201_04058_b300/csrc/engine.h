@@ -71,6 +71,7 @@ struct mp_ctx {
         mp::Stats st;
         uint32_t n_products = 0;
         uint32_t cache_hits = 0;
+        cudaEvent_t copy_ev = nullptr;  // recorded after an asynchronous copy's last chunk
     };
     struct CacheCounters {
         uint64_t requests = 0, hits = 0, inserts = 0, rejected = 0, evictions = 0;
@@ -98,6 +99,16 @@ struct mp_ctx {
     void serve_loop();
     // nnz of masked base factors already counted: (relation, row key, column key) -> nnz
     std::unordered_map<std::string, double> leaf_memo;
+    // MNC sketches of masked base factors already built (same key), least recently used
+    // first out above a byte cap
+    struct MncMemo {
+        mp::MncSketchPtr sk;
+        uint64_t seq = 0;
+    };
+    std::unordered_map<std::string, MncMemo> mnc_memo;
+    size_t mnc_memo_bytes = 0;
+    uint64_t mnc_memo_seq = 0;
+    static constexpr size_t MNC_MEMO_CAP = 4ull << 30;
     // per-product samples (nnz(X), N_op, nnz(Z), ms) for the Eq. 2 fit of mp_autotune
     bool collect_fit = false;
     uint64_t fail_alloc_after = UINT64_MAX;  // test hook: allocations allowed after finalize

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <utility>
 #include <vector>
 
@@ -184,21 +185,44 @@ struct MncLeafIn {
     DCsr A, AT;                   // the factor and its transpose (the reverse relation)
     const uint32_t *rm, *cm;      // masks of its two end positions (nullptr = none)
 };
+// A leaf's exact sketch on the device (kept across batches by the context's memo).
+struct MncSketch {
+    Alloc *al = nullptr;
+    cudaStream_t s = nullptr;
+    uint32_t *hr = nullptr, *hc = nullptr, *her = nullptr, *hec = nullptr;
+    unsigned long long raw[8] = {};  // row sum, non-zero, max, >= 2; the same over columns
+    MncLeaf stat{};
+    size_t bytes = 0;
+    ~MncSketch() {
+        if (!al) return;
+        al->free(hr, s);
+        al->free(hc, s);
+        al->free(her, s);
+        al->free(hec, s);
+    }
+};
+using MncSketchPtr = std::shared_ptr<MncSketch>;
+
 class MncDevice {
   public:
     MncDevice(Alloc &al, cudaStream_t s, int sm_count) : al_(al), s_(s), sms_(sm_count) {}
     ~MncDevice();
-    int leaf(const MncLeafIn &in);   // index of a new leaf (its sketch is built by prepare)
+    // index of a leaf: with a sketch already built (from an earlier batch), or a new one
+    // that prepare() builds
+    int leaf(const MncLeafIn &in, MncSketchPtr known = nullptr);
     int pair(int a, int b);          // leaf a's columns meet leaf b's rows
     int prepare();                   // builds sketches and pair sums; one sync. MP_* code
     const MncLeaf &leaf_stat(int i) const { return lstat_[i]; }
     const MncPair &pair_stat(int i) const { return pstat_[i]; }
+    MncSketchPtr sketch(int i) const { return leaves_[i].sk; }
+    bool built(int i) const { return leaves_[i].build; }
     // ls[r] = sum_t log(1 - x w[t]) for requests whose .pair indexes pairs of this object
     int eval(const std::vector<MncReq> &req, std::vector<double> &ls);
   private:
     struct Leaf {
         MncLeafIn in;
-        uint32_t *hr = nullptr, *hc = nullptr, *her = nullptr, *hec = nullptr;
+        MncSketchPtr sk;
+        bool build = true;
     };
     Alloc &al_;
     cudaStream_t s_;

@@ -183,18 +183,16 @@ __global__ void k_mnc_sums(const DevReq *req, double *sum_w, double *sum_ls, uns
 }  // namespace
 
 MncDevice::~MncDevice() {
-    for (Leaf &L : leaves_) {
-        al_.free(L.hr, s_);
-        al_.free(L.hc, s_);
-        al_.free(L.her, s_);
-        al_.free(L.hec, s_);
-    }
     if (sum_) al_.free(sum_, s_);
     if (req_) al_.free(req_, s_);
 }
 
-int MncDevice::leaf(const MncLeafIn &in) {
-    leaves_.push_back(Leaf{in});
+int MncDevice::leaf(const MncLeafIn &in, MncSketchPtr known) {
+    Leaf L;
+    L.in = in;
+    L.build = !known;
+    L.sk = known ? known : std::make_shared<MncSketch>();
+    leaves_.push_back(L);
     return (int)leaves_.size() - 1;
 }
 
@@ -211,6 +209,10 @@ int MncDevice::prepare() {
     sum_ = (unsigned long long *)al_.alloc(nl * 8 * sizeof(unsigned long long), s_);
     if (!sum_) return MP_ERR_NOMEM;
     cudaMemsetAsync(sum_, 0, nl * 8 * sizeof(unsigned long long), s_);
+    for (size_t l = 0; l < nl; l++)  // sketches from an earlier batch: their summaries as they were
+        if (!leaves_[l].build)
+            cudaMemcpyAsync(sum_ + 8 * l, leaves_[l].sk->raw, sizeof(leaves_[l].sk->raw), cudaMemcpyHostToDevice,
+                            s_);
     const unsigned gmax = (unsigned)sms_ * 8;
     // one long-row queue (+ its counter) for every row-count pass, reused in stream order
     int64_t qmax = 1;
@@ -227,30 +229,35 @@ int MncDevice::prepare() {
     };
     for (size_t l = 0; l < nl; l++) {
         Leaf &L = leaves_[l];
+        if (!L.build) continue;
+        MncSketch &K = *L.sk;
         const int64_t m = L.in.A.nrows, n = L.in.A.ncols;
-        L.hr = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(m, 1) * 4, s_);
-        L.her = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(m, 1) * 4, s_);
-        L.hc = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
-        L.hec = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
-        if (!L.hr || !L.her || !L.hc || !L.hec) {
+        K.al = &al_;
+        K.s = s_;
+        K.hr = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(m, 1) * 4, s_);
+        K.her = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(m, 1) * 4, s_);
+        K.hc = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
+        K.hec = (uint32_t *)al_.alloc((size_t)std::max<int64_t>(n, 1) * 4, s_);
+        K.bytes = (size_t)(std::max<int64_t>(m, 1) + std::max<int64_t>(n, 1)) * 8;
+        if (!K.hr || !K.her || !K.hc || !K.hec) {
             al_.free(lq, s_);
             return MP_ERR_NOMEM;
         }
-        rows(L.in.A, L.in.rm, L.in.cm, nullptr, L.hr);
-        rows(L.in.AT, L.in.cm, L.in.rm, nullptr, L.hc);
-        rows(L.in.A, L.in.rm, L.in.cm, L.hc, L.her);
-        rows(L.in.AT, L.in.cm, L.in.rm, L.hr, L.hec);
-        if (m) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(m, 256))), 256, 0, s_, (const uint32_t *)L.hr, m,
+        rows(L.in.A, L.in.rm, L.in.cm, nullptr, K.hr);
+        rows(L.in.AT, L.in.cm, L.in.rm, nullptr, K.hc);
+        rows(L.in.A, L.in.rm, L.in.cm, K.hc, K.her);
+        rows(L.in.AT, L.in.cm, L.in.rm, K.hr, K.hec);
+        if (m) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(m, 256))), 256, 0, s_, (const uint32_t *)K.hr, m,
                   sum_ + 8 * l);
-        if (n) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(n, 256))), 256, 0, s_, (const uint32_t *)L.hc, n,
+        if (n) kl(k_mnc_summary, std::max(1u, std::min(gmax, grid_for(n, 256))), 256, 0, s_, (const uint32_t *)K.hc, n,
                   sum_ + 8 * l + 4);
     }
     al_.free(lq, s_);  // stream-ordered: after the passes above
     // per pair: product count, the two exactly counted parts, the remaining log-sum
     std::vector<DevReq> rq;
     for (size_t p = 0; p < np; p++) {
-        const Leaf &A = leaves_[pairs_[p].first], &B = leaves_[pairs_[p].second];
-        const int64_t n = A.in.A.ncols;
+        const MncSketch &A = *leaves_[pairs_[p].first].sk, &B = *leaves_[pairs_[p].second].sk;
+        const int64_t n = leaves_[pairs_[p].first].in.A.ncols;
         rq.push_back(DevReq{A.hc, nullptr, B.hr, nullptr, n, 0.0, nullptr, nullptr});
         rq.push_back(DevReq{A.hec, nullptr, B.hr, nullptr, n, 0.0, nullptr, nullptr});
         rq.push_back(DevReq{A.hc, A.hec, B.her, nullptr, n, 0.0, nullptr, nullptr});
@@ -287,6 +294,10 @@ int MncDevice::prepare() {
         const unsigned long long *h = hs.data() + 8 * l;
         lstat_[l] = MncLeaf{(double)h[0], (double)h[1], (double)h[2], (double)h[3],
                             (double)h[5], (double)h[6], (double)h[7]};
+        if (leaves_[l].build) {
+            memcpy(leaves_[l].sk->raw, h, sizeof(leaves_[l].sk->raw));
+            leaves_[l].sk->stat = lstat_[l];
+        }
     }
     for (size_t p = 0; p < np; p++) {
         MncPair &P = pstat_[p];
@@ -313,9 +324,10 @@ int MncDevice::eval(const std::vector<MncReq> &req, std::vector<double> &ls) {
     std::vector<DevReq> rq(nr);
     int64_t nmax = 1;
     for (size_t r = 0; r < nr; r++) {
-        const Leaf &A = leaves_[pairs_[req[r].pair].first], &B = leaves_[pairs_[req[r].pair].second];
+        const MncSketch &A = *leaves_[pairs_[req[r].pair].first].sk, &B = *leaves_[pairs_[req[r].pair].second].sk;
         rq[r] = DevReq{req[r].kind != MNC_W_ROW ? A.hc : nullptr, nullptr,
-                       req[r].kind != MNC_W_COL ? B.hr : nullptr, nullptr, A.in.A.ncols, req[r].x, nullptr, nullptr};
+                       req[r].kind != MNC_W_COL ? B.hr : nullptr, nullptr,
+                       leaves_[pairs_[req[r].pair].first].in.A.ncols, req[r].x, nullptr, nullptr};
         nmax = std::max(nmax, rq[r].n);
     }
     DevReq *dq = (DevReq *)req_;

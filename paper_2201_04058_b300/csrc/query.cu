@@ -452,6 +452,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     std::vector<std::vector<int>> mleaf(nq), mpair(nq);
     if (cfg.planner == MP_PLAN_DP_MNC) {
         std::unordered_map<std::string, int> lidx;
+        std::vector<std::string> lkey;  // per leaf of `mnc`
         std::map<std::pair<int, int>, int> pidx;
         for (size_t q = 0; q < nq; q++) {
             if (qstatus[q]) continue;
@@ -466,7 +467,14 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 if (it == lidx.end()) {
                     MncLeafIn in{rels[Q.rels[t]].dev.view(), rels[Q.rels[t] ^ 1].dev.view(), masks[q][t],
                                  masks[q][t + 1]};
-                    it = lidx.emplace(key, mnc.leaf(in)).first;
+                    auto mm = mnc_memo.find(key);
+                    MncSketchPtr known;
+                    if (mm != mnc_memo.end()) {
+                        known = mm->second.sk;
+                        mm->second.seq = ++mnc_memo_seq;
+                    }
+                    it = lidx.emplace(key, mnc.leaf(in, known)).first;
+                    lkey.push_back(key);
                 }
                 mleaf[q][t] = it->second;
             }
@@ -479,6 +487,21 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         }
         const int rc = mnc.prepare();
         if (rc) return fail_all(rc);
+        // keep the new sketches for later batches
+        for (size_t l = 0; l < lkey.size(); l++) {
+            if (!mnc.built((int)l)) continue;
+            MncSketchPtr sk = mnc.sketch((int)l);
+            if (sk->bytes > MNC_MEMO_CAP / 2) continue;
+            while (mnc_memo_bytes + sk->bytes > MNC_MEMO_CAP && !mnc_memo.empty()) {
+                auto lru = mnc_memo.begin();
+                for (auto x = mnc_memo.begin(); x != mnc_memo.end(); ++x)
+                    if (x->second.seq < lru->second.seq) lru = x;
+                mnc_memo_bytes -= lru->second.sk->bytes;
+                mnc_memo.erase(lru);
+            }
+            mnc_memo[lkey[l]] = MncMemo{sk, ++mnc_memo_seq};
+            mnc_memo_bytes += sk->bytes;
+        }
     }
 
     // Overlap Tree: every query's metapath and suffixes (Sec. 3.3.2)

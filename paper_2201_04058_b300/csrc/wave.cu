@@ -118,7 +118,7 @@ __global__ void k_rowprod(const int64_t *row0s, int w, int64_t M, int32_t *rowpr
 // 16 entries are summed by the whole warp, one after the other, and rows longer than
 // LONGX are queued for k_rowwork_long.
 __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, double *xsum,
-                          uint32_t *long_rows, uint32_t *n_long) {
+                          uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -148,7 +148,11 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
                 xs += xv ? (double)__ldg(xv + p) : 1.0;
             }
         }
-        if (e - b > LONGX) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)g;
+        if (e - b > LONGX) {
+            const uint32_t at = atomicAdd(n_long, 1u);
+            long_rows[at] = (uint32_t)g;
+            long_nb[at] = (uint32_t)((e - b + LONGCH - 1) / LONGCH);  // blocks that share it
+        }
         unsigned coop = __ballot_sync(FULL, !mine && e - b <= LONGX);
         while (coop) {
             const int src = __ffs(coop) - 1;
@@ -183,20 +187,20 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
 // the grid) starting at a block that depends on r, so long rows spread over the grid and a
 // row only as long as a few chunks does not make every block stop at it.
 __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
-                               const uint32_t *long_rows, const uint32_t *n_long) {
+                               const uint32_t *long_rows, const uint32_t *long_nb, const uint32_t *n_long) {
     __shared__ unsigned long long red[32];
     __shared__ double redx[32];
     const uint32_t n = *n_long;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t G = gridDim.x;
     for (uint32_t r = 0; r < n; r++) {
+        const int64_t nb = min(G, (int64_t)long_nb[r]);
+        const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
+        if (off >= nb) continue;  // uniform over the block
         const uint32_t g = long_rows[r];
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
         const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
-        const int64_t nb = min(G, (e - b + LONGCH - 1) / LONGCH);
-        const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
-        if (off >= nb) continue;  // uniform over the block
         unsigned long long s = 0;
         double x = 0.0;
         for (int64_t p = b + off * (int64_t)blockDim.x + threadIdx.x; p < e; p += nb * blockDim.x) {
@@ -859,10 +863,8 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
             const int64_t f0 = max(s0 - base, (int64_t)0), f1 = min(s1 - base, s_off[nent]);
             auto product = [&](int l, int64_t q) {
                 const uint32_t j = (uint32_t)__ldg(yci + q);
-                // the column mask: the symbolic bitmap needs it exactly; when counts cannot
-                // overflow, the adding modes leave it to the bitmap (G_NUM: a cleared bit)
-                // or to the dense row's scan (G_DENSE), which saves a dependent load
-                if ((!NUM || chk) && !bit_of(cm, j)) return;
+                // the column mask first: a masked-out product costs one bit load, no atomic
+                if (!bit_of(cm, j)) return;
                 unsigned long long add;
                 if (!NUM) {
                     add = 1ull << (j & 31);
@@ -899,7 +901,6 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
                         dst = val + j;
                     } else {
                         const uint2 br = __ldg(bmr + (j >> 5));
-                        if (!((br.x >> (j & 31)) & 1u)) return;  // a masked-out column
                         dst = val + br.y + __popc(br.x & ((1u << (j & 31)) - 1u));
                     }
                     if (chk) {
@@ -969,13 +970,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
                     dst = val + k;
                 } else {
                     const uint2 br = __ldg(bmr + (k >> 5));
-                    if ((br.x >> (k & 31)) & 1u) {
-                        dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
-                    } else {  // a masked-out column combined in the table
-                        s_key[x] = EMPTY;
-                        s_acc[x] = 0;
-                        continue;
-                    }
+                    dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
                 }
                 const unsigned long long v = s_acc[x];
                 if (chk) {
@@ -1048,17 +1043,14 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
 
 // Dense rows: one warp per bitmap word; lane i reads column 32w + i of the dense slot
 // (coalesced) and the ballot of the non-zero counts is the word.
-__global__ void k_glob_dscan(PassArgs a, GlobArgs g) {
+__global__ void k_glob_dscan(GlobArgs g) {
     const int lane = threadIdx.x & 31;
     const int64_t total = (g.r1 - g.r0) * g.nw;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < total; x += nwarps) {
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const int64_t j = w * 32 + lane;
-        // the row's column mask applies here (the adding pass skips it when counts cannot
-        // overflow); a masked-out column's count is dropped
-        const uint32_t *cm = a.prods[a.rowprod[g.list[g.r0 + slot]]].cm;
-        const bool nz = j < g.dcols && g.dval[slot * g.dcols + j] != 0 && bit_of(cm, (uint32_t)j);
+        const bool nz = j < g.dcols && g.dval[slot * g.dcols + j] != 0;
         const unsigned word = __ballot_sync(FULL, nz);
         if (lane == 0) g.bmr[x] = make_uint2(word, 0u);
     }
@@ -1233,7 +1225,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
             glob_set<G_DENSE>(tun, s, a, ga);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
-               256, 0, s, a, ga);
+               256, 0, s, ga);
             kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
         } else {
             kl(k_glob_dfill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256,
@@ -1290,14 +1282,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         max_cols = std::max<int64_t>(max_cols, x.Y.ncols);
     }
     const int64_t M = row0s[w];
-    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows u32[M], rowprod i32[M],
+    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows and their block counts
+    // u32[M] each, rowprod i32[M],
     // wave nnz / row pointers i64[M+1], X row sums f64[M], product descriptors, row0s,
     // per-product stats, two Smalls
     const size_t o_prod = 0;
     const size_t o_bin = align256(o_prod + (size_t)M * 8);
     const size_t o_list = align256(o_bin + (size_t)M);
     const size_t o_long = align256(o_list + (size_t)M * 4);
-    const size_t o_rowprod = align256(o_long + (size_t)M * 4);
+    const size_t o_longnb = align256(o_long + (size_t)M * 4);
+    const size_t o_rowprod = align256(o_longnb + (size_t)M * 4);
     const size_t o_grp = align256(o_rowprod + (size_t)M * 4);
     const size_t o_xsum = align256(o_grp + (size_t)(M + 1) * 8);
     const size_t o_prods = align256(o_xsum + (size_t)M * 8);
@@ -1318,6 +1312,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     int8_t *bin = (int8_t *)(ws + o_bin);
     uint32_t *list = (uint32_t *)(ws + o_list);
     uint32_t *long_rows = (uint32_t *)(ws + o_long);
+    uint32_t *long_nb = (uint32_t *)(ws + o_longnb);
     int32_t *rowprod = (int32_t *)(ws + o_rowprod);
     int64_t *grp = (int64_t *)(ws + o_grp);
     double *xsum = (double *)(ws + o_xsum);
@@ -1363,9 +1358,9 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned gr = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
         kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, &sm_sym->n_long);
-        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum, long_rows,
-           &sm_sym->n_long);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, long_nb, &sm_sym->n_long);
+        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum,
+           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long);
         kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, M, ba, bin, grp, &sm_sym->tally,
            ps);
         kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);

@@ -33,7 +33,8 @@ EXPORTS = [
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
-    "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query", "mp_host_tier_stats",
+    "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query", "mp_host_tier_stats", "mp_result_copy_async",
+    "mp_result_copy_wait",
 ]
 
 
@@ -96,6 +97,8 @@ def lib():
             "mp_result_info": (C.c_int, [C.c_void_p, U64, P(U32), P(U32), P(U64)]),
             "mp_result_copy": (C.c_int, [C.c_void_p, U64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
             "mp_release": (C.c_int, [C.c_void_p, U64]),
+            "mp_result_copy_async": (C.c_int, [C.c_void_p, U64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+            "mp_result_copy_wait": (C.c_int, [C.c_void_p, U64]),
             "mp_result_time": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
             "mp_strerror": (C.c_char_p, [C.c_int]),
             "mp_result_stats": (C.c_int, [C.c_void_p, U64, P(U64), C.c_void_p, C.c_void_p, P(U32)]),
@@ -331,6 +334,23 @@ def mp_result_copy(ctx, ticket: int, row_ptr=None, col=None, val=None, on_device
         return C.c_void_p(a.ctypes.data)
     _ck(lib().mp_result_copy(ctx, ticket, addr(row_ptr), addr(col), addr(val), 1 if on_device else 0),
         "mp_result_copy")
+
+
+def mp_result_copy_async(ctx, ticket: int, row_ptr=None, col=None, val=None, on_device: bool = False):
+    """Queue the copy and return; the buffers (integer addresses, or arrays kept alive by
+    the caller) must not be read before mp_result_copy_wait."""
+    def addr(a):
+        if a is None:
+            return None
+        if isinstance(a, int):
+            return C.c_void_p(a)
+        return C.c_void_p(a.ctypes.data)
+    _ck(lib().mp_result_copy_async(ctx, ticket, addr(row_ptr), addr(col), addr(val), 1 if on_device else 0),
+        "mp_result_copy_async")
+
+
+def mp_result_copy_wait(ctx, ticket: int):
+    _ck(lib().mp_result_copy_wait(ctx, ticket), "mp_result_copy_wait")
 
 
 def mp_release(ctx, ticket: int):

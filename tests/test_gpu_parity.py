@@ -271,3 +271,35 @@ def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, 
                 assert_same(g, OC.evaluate(o, q), (tune, "batch", "".join(q["types"])))
         finally:
             e.close()
+
+
+def test_async_copy_overlaps_next_query(c1, c1_engines):
+    """Results copied with mp_result_copy_async while the next queries run equal the
+    oracle's once mp_result_copy_wait returns; a ticket released right after its copy was
+    queued does not disturb the copy (its memory is freed after the copy)."""
+    mp = _mp()
+    e = c1_engines[-1]
+    qs = gen.long_queries(5, 3) + [gen.config1_query()]
+    bufs, tks = [], []
+    for q in qs:
+        rc, t = e.submit(q)
+        assert rc == 0
+        rows, cols, nnz = mp.mp_result_info(e.ctx, t)
+        b = (np.empty(rows + 1, np.int64), np.empty(nnz, np.int32), np.empty(nnz, np.uint64))
+        mp.mp_result_copy_async(e.ctx, t, *b)
+        bufs.append(b)
+        tks.append(t)
+    for q, t, b in zip(qs, tks, bufs):
+        mp.mp_result_copy_wait(e.ctx, t)
+        mp.mp_release(e.ctx, t)
+        assert_same(b, OC.evaluate(c1[1], q), ("async", "".join(q["types"])))
+    rc, t = e.submit(qs[0])
+    rows, cols, nnz = mp.mp_result_info(e.ctx, t)
+    b = (np.empty(rows + 1, np.int64), np.empty(nnz, np.int32), np.empty(nnz, np.uint64))
+    mp.mp_result_copy_async(e.ctx, t, *b)
+    mp.mp_release(e.ctx, t)
+    rc2, t2 = e.submit(qs[1])  # reuses freed memory only after the copy above
+    e.release(t2)
+    import torch
+    torch.cuda.synchronize()
+    assert_same(b, OC.evaluate(c1[1], qs[0]), "released early")
