@@ -114,6 +114,33 @@ __global__ void k_rowprod(const int64_t *row0s, int w, int64_t M, int32_t *rowpr
     }
 }
 
+// Over the X entries p = p0, p0 + st, ... < e of one row: the masked Y-row lengths (the row's
+// Gustavson products) into s and the X values (1 for a pattern X) into x. Four entries are
+// loaded before their Y row pointers are, so four dependent gathers are in flight.
+__device__ __forceinline__ void row_sums(const Prod &P, int64_t p0, int64_t e, int64_t st, uint64_t &s,
+                                         double &x) {
+    const int32_t *__restrict__ xci = P.X.ci;
+    const uint64_t *__restrict__ xv = P.X.val;
+    const int64_t *__restrict__ yrp = P.Y.rp;
+    const uint32_t *__restrict__ km = P.km;
+    int64_t p = p0;
+    for (; p + 3 * st < e; p += 4 * st) {
+        int32_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + u * st);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (bit_of(km, (uint32_t)k[u])) s += (uint64_t)(__ldg(yrp + k[u] + 1) - __ldg(yrp + k[u]));
+            x += xv ? (double)__ldg(xv + p + u * st) : 1.0;
+        }
+    }
+    for (; p < e; p += st) {
+        const int32_t k = __ldg(xci + p);
+        if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(yrp + k + 1) - __ldg(yrp + k));
+        x += xv ? (double)__ldg(xv + p) : 1.0;
+    }
+}
+
 // prod_i of every wave row. Each lane takes one of 32 consecutive rows; rows longer than
 // 16 entries are summed by the whole warp, one after the other, and rows longer than
 // LONGX are queued for k_rowwork_long.
@@ -137,17 +164,7 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         uint64_t s = 0;
         double xs = 0.0;  // the row's sum of X values: x_ik <= xs bounds every product and sum
         const bool mine = e - b <= 16;
-        if (mine && e > b) {
-            const int32_t *__restrict__ xci = P->X.ci;
-            const uint64_t *__restrict__ xv = P->X.val;
-            const int64_t *__restrict__ yrp = P->Y.rp;
-            const uint32_t *__restrict__ km = P->km;
-            for (int64_t p = b; p < e; p++) {
-                const int32_t k = __ldg(xci + p);
-                if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(yrp + k + 1) - __ldg(yrp + k));
-                xs += xv ? (double)__ldg(xv + p) : 1.0;
-            }
-        }
+        if (mine && e > b) row_sums(*P, b, e, 1, s, xs);
         if (e - b > LONGX) {
             const uint32_t at = atomicAdd(n_long, 1u);
             long_rows[at] = (uint32_t)g;
@@ -162,11 +179,7 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
             const Prod &Q = prods[pi];
             uint64_t c = 0;
             double cx = 0.0;
-            for (int64_t p = bb + lane; p < ee; p += 32) {
-                const int32_t k = __ldg(Q.X.ci + p);
-                if (bit_of(Q.km, (uint32_t)k)) c += (uint64_t)(__ldg(Q.Y.rp + k + 1) - __ldg(Q.Y.rp + k));
-                cx += Q.X.val ? (double)__ldg(Q.X.val + p) : 1.0;
-            }
+            row_sums(Q, bb + lane, ee, 32, c, cx);
             for (int d = 16; d; d >>= 1) {
                 c += __shfl_xor_sync(FULL, c, d);
                 cx += __shfl_xor_sync(FULL, cx, d);
@@ -201,13 +214,9 @@ __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
         const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
-        unsigned long long s = 0;
+        uint64_t s = 0;
         double x = 0.0;
-        for (int64_t p = b + off * (int64_t)blockDim.x + threadIdx.x; p < e; p += nb * blockDim.x) {
-            const int32_t k = __ldg(P.X.ci + p);
-            if (bit_of(P.km, (uint32_t)k)) s += (unsigned long long)(__ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k));
-            x += P.X.val ? (double)__ldg(P.X.val + p) : 1.0;
-        }
+        row_sums(P, b + off * (int64_t)blockDim.x + threadIdx.x, e, nb * (int64_t)blockDim.x, s, x);
         for (int d = 16; d; d >>= 1) {
             s += __shfl_xor_sync(FULL, s, d);
             x += __shfl_xor_sync(FULL, x, d);
