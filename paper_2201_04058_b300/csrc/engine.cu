@@ -144,6 +144,7 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "dense_scratch") ctx->tun.dense_scratch_cap = (uint64_t)v;
                 else if (k == "glob_occ") ctx->tun.glob_occ = (int)v;
                 else if (k == "seg_walk") ctx->tun.seg_walk = (int)v;
+                else if (k == "graphs") ctx->tun.graphs = (int)v;
             }
             a = b + 1;
         }
@@ -201,6 +202,7 @@ extern "C" void mp_destroy(mp_ctx *ctx) {
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->cache_clear();
         ctx->mnc_memo.clear();
+        ctx->wcache.clear(*ctx->alloc, ctx->stream);
         for (auto &kv : ctx->results)
             if (kv.second.copy_ev) {
                 cudaEventSynchronize(kv.second.copy_ev);

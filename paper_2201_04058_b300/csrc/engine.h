@@ -122,6 +122,7 @@ struct mp_ctx {
     std::unique_ptr<mp::Alloc> alloc;
     mp::Tuning tun;
     mp::Prof prof;
+    mp::WaveCache wcache;  // persistent wave workspace and the bin passes' CUDA graphs
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
     mp::OverlapTree otree;

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <memory>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -52,6 +53,7 @@ struct Tuning {
     double glob_dense = 1.0;
     uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
     int glob_occ = 6;  // resident blocks per SM of the count-adding split-row kernels (4 or 6)
+    int graphs = 1;    // shared-memory bin passes replayed as CUDA graphs, one per wave shape
     int sm_count = 148;
 };
 
@@ -134,8 +136,24 @@ void sample_rows(const DCsr &A, const uint32_t *rm, uint64_t seed, uint64_t thr,
 // symbolic_only: stop after the symbolic pass; out[p].m holds only nrows, ncols, nnz.
 // Returns MP_OK or a wave-wide error (CUDA, out of memory); per-product errors are in
 // out[p].status.
+// Persistent state of the wave executor: one workspace laid out for a row and product
+// capacity (so its addresses stay put from wave to wave), and the CUDA graphs of the
+// shared-memory bin passes captured on it, one per wave shape (pass, set of non-empty bins,
+// dense-bin width class, profiling on or off). Growing the workspace drops the graphs.
+struct WaveCache {
+    char *ws = nullptr;
+    int64_t mcap = 0;
+    int wcap = 0;
+    std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+    uint64_t captures = 0, replays = 0;
+    bool broken = false;  // a capture failed: plain launches from then on
+    void drop_graphs();
+    void clear(Alloc &al, cudaStream_t s);
+};
+
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
-                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only = false);
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only = false,
+                WaveCache *wc = nullptr);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,

@@ -428,7 +428,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 win[k].cm = masks[pairs[k].q][t + 2];
             }
             std::vector<WaveOut> wout;
-            int rc = spgemm_wave(win, *alloc, tun, stream, 0, wout, nullptr, true);
+            int rc = spgemm_wave(win, *alloc, tun, stream, 0, wout, nullptr, true, &wcache);
             cudaMemcpyAsync(h.data(), d, np * 16, cudaMemcpyDeviceToHost, stream);
             if (cudaStreamSynchronize(stream) != cudaSuccess) rc = MP_ERR_CUDA;
             for (auto *b : bms) alloc->free(b, stream);
@@ -776,7 +776,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (members.empty()) continue;
         std::vector<WaveOut> wout;
         auto t0 = std::chrono::steady_clock::now();
-        wave_rc = spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof);
+        wave_rc = spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof, false, &wcache);
         const double wave_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         double wave_prod = 0.0;
         for (auto &o : wout) wave_prod += (double)o.products;

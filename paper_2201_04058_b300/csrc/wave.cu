@@ -1092,10 +1092,15 @@ __global__ void k_glob_dfill(PassArgs a, GlobArgs g) {
 
 // ------------------------------------------------------------------ launch helpers
 
+// Set while a pass only prepares its kernels' shared-memory attributes (before a capture,
+// where the attribute calls are kept out of the captured stream).
+static thread_local bool g_attrs_only = false, g_capturing = false;
+
 template <class K>
 static void launch(K kern, unsigned grid, int nt, size_t smem, cudaStream_t s, const PassArgs &a, int bin) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kl(kern, grid, nt, smem, s, a, bin);
+    if (smem > 48 * 1024 && !g_capturing)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!g_attrs_only) kl(kern, grid, nt, smem, s, a, bin);
 }
 
 static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_blocks) {
@@ -1104,17 +1109,19 @@ static unsigned blocks_for(uint32_t rows_upper, int rows_per_block, int max_bloc
 }
 
 // Launch every non-empty shared-memory bin's kernel of one pass, each grid sized to its
-// bin's rows (capped at a few blocks per SM; the kernels loop over their bin). With prof,
-// CUDA events bracket each launch. GLOBAL runs separately (glob_pass). dense_cols is the
-// widest output among the wave's products that fit the dense bin.
+// bin's rows (capped at a few blocks per SM; the kernels loop over their bin, reading its
+// row count from the device), or at the cap for every bin when fixed_grid (a captured
+// graph serves every wave of the same shape). With prof, CUDA events bracket each launch.
+// GLOBAL runs separately (glob_pass). dense_cols is the widest output among the wave's
+// products that fit the dense bin (it sizes the dense kernels' shared memory).
 static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t dense_cols, const Tuning &tun,
-                     cudaStream_t s, Prof *prof) {
+                     cudaStream_t s, Prof *prof, bool fixed_grid = false) {
     const bool numeric = pass == 1;
     const int sms = tun.sm_count;
     const size_t stage = sizeof(Stage);
     for (int b = 0; b < B_GLOBAL; b++) {
-        const uint32_t rows = host_counts[b];
-        if (!rows) continue;
+        if (!host_counts[b]) continue;
+        const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[b];
         if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][0], s);
         switch (b) {
 #define WARP_BIN(BIN, T, W)                                                                       \
@@ -1158,6 +1165,69 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
         }
         if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][1], s);
     }
+}
+
+void WaveCache::drop_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+}
+
+void WaveCache::clear(Alloc &al, cudaStream_t s) {
+    drop_graphs();
+    if (ws) al.free(ws, s);
+    ws = nullptr;
+    mcap = 0;
+    wcap = 0;
+}
+
+// One shared-memory bin pass through a CUDA graph: the wave's shape (pass, non-empty bins,
+// dense width class, profiling) picks a graph captured once with fixed grids on the
+// persistent workspace, so the launches and their arguments are the same for every wave
+// of that shape; the kernels read their bins' row counts from the device. Falls back to
+// plain launches if a capture fails.
+static void run_pass_graph(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t dense_cols,
+                           const Tuning &tun, cudaStream_t s, Prof *prof, WaveCache &wc) {
+    uint32_t mask = 0;
+    for (int b = 0; b < B_GLOBAL; b++)
+        if (host_counts[b]) mask |= 1u << b;
+    if (!mask) return;
+    int64_t dcls = 0;
+    if (mask & (1u << B_DENSE)) {
+        dcls = 32;
+        while (dcls < dense_cols) dcls <<= 1;
+    }
+    const bool timed = prof && prof->on;
+    const uint64_t key = (uint64_t)pass | ((uint64_t)mask << 1) | ((uint64_t)dcls << 16) | ((uint64_t)timed << 62);
+    auto it = wc.graphs.find(key);
+    if (it == wc.graphs.end()) {
+        g_attrs_only = true;  // shared-memory attributes outside the capture
+        run_pass(pass, a, host_counts, dcls, tun, s, nullptr, true);
+        g_attrs_only = false;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        const uint64_t l0 = g_launches.load();
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            g_capturing = true;
+            run_pass(pass, a, host_counts, dcls, tun, s, prof, true);
+            g_capturing = false;
+            ok = cudaStreamEndCapture(s, &g) == cudaSuccess && g;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        g_launches.fetch_sub(g_launches.load() - l0);  // replays are counted below
+        if (!ok) {
+            cudaGetLastError();
+            wc.broken = true;
+            run_pass(pass, a, host_counts, dense_cols, tun, s, prof);
+            return;
+        }
+        it = wc.graphs.emplace(key, ex).first;
+        wc.captures++;
+    }
+    cudaGraphLaunch(it->second, s);
+    g_launches.fetch_add((uint64_t)__builtin_popcount(mask), std::memory_order_relaxed);
+    wc.replays++;
 }
 
 static void prof_collect(Prof *prof, int pass, const BinTally &t) {
@@ -1263,7 +1333,8 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
 // ------------------------------------------------------------------ host orchestration
 
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
-                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only) {
+                uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only,
+                WaveCache *wc) {
     const int w = (int)in.size();
     out.assign(w, WaveOut{});
     if (w == 0) return MP_OK;
@@ -1291,22 +1362,38 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         max_cols = std::max<int64_t>(max_cols, x.Y.ncols);
     }
     const int64_t M = row0s[w];
+    // with graphs, the workspace persists (laid out for the cache's capacities, grown by
+    // half again when a wave needs more; growing drops the graphs captured on it)
+    const bool graphs = wc && tun.graphs && !wc->broken;
+    int64_t Mc = M;
+    int wcp = w;
+    if (graphs) {
+        if (!wc->ws || M > wc->mcap || w > wc->wcap) {
+            wc->drop_graphs();
+            if (wc->ws) al.free(wc->ws, s);
+            wc->ws = nullptr;
+            wc->mcap = std::max<int64_t>(M, wc->mcap + wc->mcap / 2);
+            wc->wcap = std::max(w, 2 * wc->wcap);
+        }
+        Mc = wc->mcap;
+        wcp = wc->wcap;
+    }
     // workspace: prod u64[M], bins i8[M], row list u32[M], long rows and their block counts
     // u32[M] each, rowprod i32[M],
     // wave nnz / row pointers i64[M+1], X row sums f64[M], product descriptors, row0s,
-    // per-product stats, two Smalls
+    // per-product stats, two Smalls (M, w: the capacities when the workspace persists)
     const size_t o_prod = 0;
-    const size_t o_bin = align256(o_prod + (size_t)M * 8);
-    const size_t o_list = align256(o_bin + (size_t)M);
-    const size_t o_long = align256(o_list + (size_t)M * 4);
-    const size_t o_longnb = align256(o_long + (size_t)M * 4);
-    const size_t o_rowprod = align256(o_longnb + (size_t)M * 4);
-    const size_t o_grp = align256(o_rowprod + (size_t)M * 4);
-    const size_t o_xsum = align256(o_grp + (size_t)(M + 1) * 8);
-    const size_t o_prods = align256(o_xsum + (size_t)M * 8);
-    const size_t o_row0s = align256(o_prods + sizeof(Prod) * w);
-    const size_t o_ps = align256(o_row0s + (size_t)(w + 1) * 8);
-    const size_t o_small = align256(o_ps + sizeof(PStat) * w);
+    const size_t o_bin = align256(o_prod + (size_t)Mc * 8);
+    const size_t o_list = align256(o_bin + (size_t)Mc);
+    const size_t o_long = align256(o_list + (size_t)Mc * 4);
+    const size_t o_longnb = align256(o_long + (size_t)Mc * 4);
+    const size_t o_rowprod = align256(o_longnb + (size_t)Mc * 4);
+    const size_t o_grp = align256(o_rowprod + (size_t)Mc * 4);
+    const size_t o_xsum = align256(o_grp + (size_t)(Mc + 1) * 8);
+    const size_t o_prods = align256(o_xsum + (size_t)Mc * 8);
+    const size_t o_row0s = align256(o_prods + sizeof(Prod) * wcp);
+    const size_t o_ps = align256(o_row0s + (size_t)(wcp + 1) * 8);
+    const size_t o_small = align256(o_ps + sizeof(PStat) * wcp);
     const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
     const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod, tun.glob_dense,
                      max_cols};
@@ -1315,8 +1402,12 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     PassArgs pa{};
     Small h_sym, h_num;
     std::vector<PStat> hps(w);
-    char *ws = (char *)al.alloc(ws_bytes, s);
+    char *ws = graphs ? wc->ws : (char *)al.alloc(ws_bytes, s);
+    if (graphs && !ws) ws = wc->ws = (char *)al.alloc(ws_bytes, s);
     if (!ws) return MP_ERR_NOMEM;
+    auto ws_free = [&] {
+        if (!graphs) al.free(ws, s);
+    };
     uint64_t *prod = (uint64_t *)(ws + o_prod);
     int8_t *bin = (int8_t *)(ws + o_bin);
     uint32_t *list = (uint32_t *)(ws + o_list);
@@ -1337,7 +1428,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             if (hp[p].val) al.free(hp[p].val, s);
         }
         glob_release(gl, al, s);
-        al.free(ws, s);
+        ws_free();
         out.assign(w, WaveOut{});
         return code;
     };
@@ -1431,7 +1522,10 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         if (scan_i64(gl.xoff, gl.xoff, xtot, al, s)) return fail(MP_ERR_NOMEM);
     }
     // 2-3. symbolic pass, wave row pointers, per-product row pointers and sizes
-    if (M > 0) run_pass(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof);
+    if (M > 0) {
+        if (graphs) run_pass_graph(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof, *wc);
+        else run_pass(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof);
+    }
     if (gl.R) glob_pass(0, gl, pa, tun, s, prof);
     if (scan_i64(grp, grp, M, al, s)) return fail(MP_ERR_NOMEM);
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
@@ -1454,7 +1548,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             al.free(hp[p].rp, s);
         }
         glob_release(gl, al, s);
-        al.free(ws, s);
+        ws_free();
         return MP_OK;
     }
     // per product: status, size guard, output arrays
@@ -1494,7 +1588,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             return fail(MP_ERR_CUDA);
         pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
-        run_pass(1, pa, h_num.tally.counts, dense_cols, tun, s, prof);
+        if (graphs) run_pass_graph(1, pa, h_num.tally.counts, dense_cols, tun, s, prof, *wc);
+        else run_pass(1, pa, h_num.tally.counts, dense_cols, tun, s, prof);
         if (gl.R) glob_pass(1, gl, pa, tun, s, prof);
         if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
             !cuda_ok(cudaStreamSynchronize(s), "sync"))
@@ -1526,7 +1621,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         o.m.val = hp[p].val;
     }
     glob_release(gl, al, s);
-    al.free(ws, s);
+    ws_free();
     return rc;
 }
 

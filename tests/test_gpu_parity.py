@@ -303,3 +303,28 @@ def test_async_copy_overlaps_next_query(c1, c1_engines):
     import torch
     torch.cuda.synchronize()
     assert_same(b, OC.evaluate(c1[1], qs[0]), "released early")
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_bin_passes_as_graphs(c1, graphs, monkeypatch):
+    """The shared-memory bin passes replayed as CUDA graphs (one per wave shape, captured on
+    the first wave of that shape) and launched directly give the oracle's results, for every
+    forced bin class and for batches whose waves have many shapes, run twice so the second
+    run replays every graph."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"graphs={graphs}")
+    h, o = c1
+    qs = gen.random_queries(h, 31, 12, lengths=(3, 7)) + gen.long_queries(5, 3)
+    want = [OC.evaluate(o, q) for q in qs]
+    for force in BIN_CLASSES:
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
+        try:
+            for rnd in range(2):
+                for q, w in zip(qs, want):
+                    assert_same(e.run(q), w, (graphs, force, rnd, "".join(q["types"])))
+                rc, res = e.run_batch(qs)
+                assert rc == 0
+                for q, g, w in zip(qs, res, want):
+                    assert_same(g, w, (graphs, force, rnd, "batch", "".join(q["types"])))
+        finally:
+            e.close()
