@@ -418,6 +418,7 @@ def run_engine(args, ws, rank, local):
                    "h2d_bytes_per_step": sum(query_bytes(q) for q in qs),
                    "d2h_bytes_per_step": d2h[0] // e2e_steps},
            "batched": batched, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
+           "graphs": mp.mp_graph_stats(eng.ctx),
            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
                            "Gproducts_per_s": round(v["products"] / max(v["ms"], 1e-9) / 1e6, 2)}

@@ -257,6 +257,11 @@ int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t 
 int mp_cache_stats(mp_ctx *ctx, uint64_t *requests, uint64_t *hits, uint64_t *inserts, uint64_t *rejected,
                    uint64_t *evictions, uint64_t *bytes, uint64_t *entries);
 
+/* CUDA graphs of the shared-memory bin passes since mp_create: graphs captured (one per
+ * wave shape: pass, non-empty bins, dense-bin width class) and passes replayed from them.
+ * Any pointer may be NULL. Both stay 0 with MP_TUNING=graphs=0. */
+int mp_graph_stats(mp_ctx *ctx, uint64_t *captures, uint64_t *replays);
+
 /* Host-tier counters since mp_create (mp_config.host_tier_bytes): results stored after a
  * device-cache eviction, results copied back instead of recomputed, entries dropped to make
  * room (least recently used first), bytes and entries held. Any pointer may be NULL.

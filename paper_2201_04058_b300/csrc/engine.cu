@@ -1110,6 +1110,14 @@ extern "C" int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads
     return MP_OK;
 }
 
+extern "C" int mp_graph_stats(mp_ctx *ctx, uint64_t *captures, uint64_t *replays) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> g(ctx->exec_mu);
+    if (captures) *captures = ctx->wcache.captures;
+    if (replays) *replays = ctx->wcache.replays;
+    return MP_OK;
+}
+
 extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
     if (!ctx) return MP_ERR_ARG;
     std::lock_guard<std::mutex> g(ctx->exec_mu);

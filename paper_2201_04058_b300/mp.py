@@ -34,7 +34,7 @@ EXPORTS = [
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
     "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query", "mp_host_tier_stats", "mp_result_copy_async",
-    "mp_result_copy_wait",
+    "mp_result_copy_wait", "mp_graph_stats",
 ]
 
 
@@ -106,6 +106,7 @@ def lib():
             "mp_kernel_stats_reset": (C.c_int, [C.c_void_p]),
             "mp_cache_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 7),
             "mp_host_tier_stats": (C.c_int, [C.c_void_p] + [P(U64)] * 5),
+            "mp_graph_stats": (C.c_int, [C.c_void_p, P(U64), P(U64)]),
             "mp_hin_save": (C.c_int, [C.c_void_p, C.c_char_p]),
             "mp_hin_load": (C.c_int, [C.c_void_p, C.c_char_p]),
             "mp_autotune": (C.c_int, [C.c_void_p, U32, P(mp_query), U32, C.c_char_p, P(C.c_double)]),
@@ -440,6 +441,12 @@ def mp_host_tier_stats(ctx):
     v = [C.c_uint64() for _ in range(5)]
     _ck(lib().mp_host_tier_stats(ctx, *[C.byref(x) for x in v]), "mp_host_tier_stats")
     return dict(zip(("stores", "loads", "drops", "bytes", "entries"), (x.value for x in v)))
+
+
+def mp_graph_stats(ctx):
+    c, r = C.c_uint64(), C.c_uint64()
+    _ck(lib().mp_graph_stats(ctx, C.byref(c), C.byref(r)), "mp_graph_stats")
+    return {"captures": c.value, "replays": r.value}
 
 
 def mp_kernel_stats_reset(ctx):

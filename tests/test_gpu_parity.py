@@ -326,5 +326,10 @@ def test_bin_passes_as_graphs(c1, graphs, monkeypatch):
                 assert rc == 0
                 for q, g, w in zip(qs, res, want):
                     assert_same(g, w, (graphs, force, rnd, "batch", "".join(q["types"])))
+            st = mp.mp_graph_stats(e.ctx)
+            if graphs:
+                assert st["captures"] > 0 and st["replays"] > st["captures"], st
+            else:
+                assert st == {"captures": 0, "replays": 0}, st
         finally:
             e.close()
