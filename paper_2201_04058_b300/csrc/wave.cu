@@ -1122,7 +1122,8 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
     for (int b = 0; b < B_GLOBAL; b++) {
         if (!host_counts[b]) continue;
         const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[b];
-        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][0], s);
+        // inside a capture the records become event-record nodes, so replays time the bins
+        if (prof && prof->on) cudaEventRecordWithFlags(prof->ev[pass][b][0], s, g_capturing ? cudaEventRecordExternal : 0);
         switch (b) {
 #define WARP_BIN(BIN, T, W)                                                                       \
     case BIN: {                                                                                   \
@@ -1163,7 +1164,7 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
                 break;
             }
         }
-        if (prof && prof->on) cudaEventRecord(prof->ev[pass][b][1], s);
+        if (prof && prof->on) cudaEventRecordWithFlags(prof->ev[pass][b][1], s, g_capturing ? cudaEventRecordExternal : 0);
     }
 }
 
@@ -1206,17 +1207,24 @@ static void run_pass_graph(int pass, const PassArgs &a, const uint32_t *host_cou
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ex = nullptr;
         const uint64_t l0 = g_launches.load();
-        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        const char *step = "begin capture";
+        if (e == cudaSuccess) {
             g_capturing = true;
             run_pass(pass, a, host_counts, dcls, tun, s, prof, true);
             g_capturing = false;
-            ok = cudaStreamEndCapture(s, &g) == cudaSuccess && g;
+            e = cudaStreamEndCapture(s, &g);
+            step = "end capture";
         }
-        if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&ex, g, 0);
+            step = "instantiate";
+        }
         if (g) cudaGraphDestroy(g);
         g_launches.fetch_sub(g_launches.load() - l0);  // replays are counted below
-        if (!ok) {
+        if (e != cudaSuccess) {
+            fprintf(stderr, "mp: bin-pass graph %s: %s; launching directly from now on\n", step,
+                    cudaGetErrorString(e));
             cudaGetLastError();
             wc.broken = true;
             run_pass(pass, a, host_counts, dense_cols, tun, s, prof);
