@@ -327,9 +327,10 @@ def test_bin_passes_as_graphs(c1, graphs, monkeypatch):
                 for q, g, w in zip(qs, res, want):
                     assert_same(g, w, (graphs, force, rnd, "batch", "".join(q["types"])))
             st = mp.mp_graph_stats(e.ctx)
-            if graphs:
-                assert st["captures"] > 0 and st["replays"] > st["captures"], st
-            else:
-                assert st == {"captures": 0, "replays": 0}, st
+            if graphs and force != mp.MP_BIN_GLOBAL:
+                assert st["captures"] > 0 and st["replays"] > st["captures"], (force, st)
+            elif not graphs:
+                assert st == {"captures": 0, "replays": 0}, (force, st)
+            # every row forced into the split-row bin leaves no shared-memory pass to capture
         finally:
             e.close()
