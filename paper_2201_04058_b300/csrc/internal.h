@@ -53,7 +53,7 @@ struct Tuning {
     double glob_dense = 1.0;
     uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
     int glob_occ = 6;  // resident blocks per SM of the count-adding split-row kernels (4 or 6)
-    int graphs = 1;    // shared-memory bin passes replayed as CUDA graphs, one per wave shape
+    int graphs = 0;    // shared-memory bin passes replayed as CUDA graphs, one per wave shape
     int sm_count = 148;
 };
 
