@@ -996,35 +996,71 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
     }
 }
 
-__global__ void __launch_bounds__(GNT) k_glob_rank(PassArgs a, GlobArgs g, int numeric) {
+// The rank pass in parallel over chunks of RCH words of every row slot (one block each), so a
+// few very wide rows do not leave the GPU to a few blocks: (1) set bits per chunk, (2) one
+// warp per row scans its chunks (the row's size), (3) each chunk writes its words' ranks.
+static constexpr int64_t RCH = (int64_t)GNT * RW;  // words per chunk
+
+__global__ void __launch_bounds__(GNT) k_glob_csum(GlobArgs g, int64_t nch, int64_t *csum) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t gtot;
-    for (int64_t r = g.r0 + blockIdx.x; r < g.r1; r += gridDim.x) {
-        const RowRef Rf(a, g.list[r]);
-        const int64_t nw = (Rf.P->Y.ncols + 31) / 32;
-        uint2 *bmr = g.bmr + (r - g.r0) * g.nw;
-        int64_t carry = 0;
-        for (int64_t w0 = 0; w0 < nw; w0 += (int64_t)GNT * RW) {
-            const int64_t wb = w0 + (int64_t)threadIdx.x * RW;
-            int cnt[RW];
-            int c = 0;
+    const int64_t total = (g.r1 - g.r0) * nch;
+    for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+        const int64_t slot = c / nch, w0 = (c - slot * nch) * RCH + (int64_t)threadIdx.x * RW;
+        const uint2 *bmr = g.bmr + slot * g.nw;
+        int cnt = 0;
 #pragma unroll
-            for (int u = 0; u < RW; u++) {
-                cnt[u] = wb + u < nw ? __popc(bmr[wb + u].x) : 0;
-                c += cnt[u];
+        for (int u = 0; u < RW; u++) cnt += w0 + u < g.nw ? __popc(bmr[w0 + u].x) : 0;
+        block_excl_scan<GNT>(cnt, warp_sums, &gtot);
+        if (threadIdx.x == 0) csum[c] = gtot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_glob_rowscan(PassArgs a, GlobArgs g, int64_t nch, int64_t *csum, int numeric) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < g.r1 - g.r0; r += nwarps) {
+        int64_t *cs = csum + r * nch, carry = 0;
+        for (int64_t c0 = 0; c0 < nch; c0 += 32) {
+            const int64_t v = c0 + lane < nch ? cs[c0 + lane] : 0;
+            int64_t x = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL, x, d);
+                if (lane >= d) x += y;
             }
-            int64_t ex = carry + block_excl_scan<GNT>(c, warp_sums, &gtot);
-#pragma unroll
-            for (int u = 0; u < RW; u++) {
-                if (wb + u < nw) bmr[wb + u].y = (uint32_t)ex;
-                ex += cnt[u];
-            }
-            carry += gtot;
+            if (c0 + lane < nch) cs[c0 + lane] = carry + x - v;  // exclusive
+            carry += __shfl_sync(FULL, x, 31);
         }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
+            const RowRef Rf(a, g.list[g.r0 + r]);
             if (!numeric) a.nnz[Rf.g] = carry;
             else if (Rf.P->ci && Rf.out_len(a) != carry) atomicOr(Rf.err(a), ERR_COUNT);
         }
+    }
+}
+
+__global__ void __launch_bounds__(GNT) k_glob_crank(GlobArgs g, int64_t nch, const int64_t *csum) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    const int64_t total = (g.r1 - g.r0) * nch;
+    for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+        const int64_t slot = c / nch, w0 = (c - slot * nch) * RCH + (int64_t)threadIdx.x * RW;
+        uint2 *bmr = g.bmr + slot * g.nw;
+        int cnt[RW];
+        int sum = 0;
+#pragma unroll
+        for (int u = 0; u < RW; u++) {
+            cnt[u] = w0 + u < g.nw ? __popc(bmr[w0 + u].x) : 0;
+            sum += cnt[u];
+        }
+        int64_t ex = csum[c] + block_excl_scan<GNT>(sum, warp_sums, &gtot);
+#pragma unroll
+        for (int u = 0; u < RW; u++) {
+            if (w0 + u < g.nw) bmr[w0 + u].y = (uint32_t)ex;
+            ex += cnt[u];
+        }
+        __syncthreads();
     }
 }
 
@@ -1267,8 +1303,22 @@ struct Glob {
     const uint64_t *prod = nullptr;
     uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
+    int64_t *csum = nullptr;   // rank pass: per chunk of a row slot, its set bits, then its offset
     bool kept = false;         // bitmaps of a single round survive into the numeric pass
 };
+
+// The rank pass of rows [ga.r0, ga.r1): chunk sums, per-row scans (the rows' sizes, or the
+// numeric pass's size check), chunk ranks.
+static void glob_rank(const Glob &g, const PassArgs &a, const GlobArgs &ga, int numeric, unsigned grid,
+                      cudaStream_t s) {
+    const int64_t nch = (g.nw + RCH - 1) / RCH;
+    const int64_t chunks = (ga.r1 - ga.r0) * nch;
+    const unsigned gc = (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)grid * 2));
+    kl(k_glob_csum, gc, GNT, 0, s, ga, nch, g.csum);
+    kl(k_glob_rowscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for((ga.r1 - ga.r0) * 32, 256), grid)),
+       256, 0, s, a, ga, nch, g.csum, numeric);
+    kl(k_glob_crank, gc, GNT, 0, s, ga, nch, (const int64_t *)g.csum);
+}
 
 static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.list) al.free(g.list, s);
@@ -1278,6 +1328,7 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.bmr) al.free(g.bmr, s);
     if (g.dbmr) al.free(g.dbmr, s);
     if (g.dval) al.free(g.dval, s);
+    if (g.csum) al.free(g.csum, s);
     g = Glob{};
 }
 
@@ -1313,7 +1364,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
             glob_set<G_DENSE>(tun, s, a, ga);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
                256, 0, s, ga);
-            kl(k_glob_rank, (unsigned)std::min<int64_t>(g.nd, grid), GNT, 0, s, a, ga, 0);
+            glob_rank(g, a, ga, 0, grid, s);
         } else {
             kl(k_glob_dfill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256,
                0, s, a, ga);
@@ -1326,7 +1377,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
             glob_set<G_SYM>(tun, s, a, ga);
-            kl(k_glob_rank, (unsigned)std::min<int64_t>(rows, grid), GNT, 0, s, a, ga, pass);
+            glob_rank(g, a, ga, pass, grid, s);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
@@ -1508,6 +1559,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             gl.dbmr = (uint2 *)al.alloc((size_t)gl.nd * gl.nw * 8, s);
             gl.dval = (unsigned long long *)al.alloc((size_t)gl.nd * gl.dcols * 8, s);
             if (!gl.dbmr || !gl.dval) return fail(MP_ERR_NOMEM);
+        }
+        {
+            const int64_t nch = (gl.nw + RCH - 1) / RCH;
+            gl.csum = (int64_t *)al.alloc((size_t)std::max<int64_t>(gl.per_round, gl.nd) * nch * 8 + 8, s);
+            if (!gl.csum) return fail(MP_ERR_NOMEM);
         }
         if (nd_all) {
             // qualifying rows first (the two counters live in the first bitmap/rank pair,
