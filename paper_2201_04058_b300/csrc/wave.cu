@@ -779,33 +779,18 @@ __global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const u
 // entries start at xbase[r]); a device-wide exclusive scan then gives each entry's global
 // product offset.
 __global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const int64_t *xbase, int64_t *xoff) {
-    // a block takes tiles of blockDim entries; one thread finds the rows of the tile's first
-    // and last entries, so every entry searches only that (usually one-row) range
-    __shared__ int64_t t_lo, t_hi;
     const int64_t xtot = xbase[R];
-    auto row_of = [&](int64_t e, int64_t lo, int64_t hi) {  // the last row r in [lo, hi] with xbase[r] <= e
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < xtot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = R - 1;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
             if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
         }
-        return lo;
-    };
-    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < xtot; e0 += (int64_t)gridDim.x * blockDim.x) {
-        if (threadIdx.x == 0) {
-            t_lo = row_of(e0, 0, R - 1);
-            t_hi = row_of(min(e0 + (int64_t)blockDim.x, xtot) - 1, t_lo, R - 1);
-        }
-        __syncthreads();
-        const int64_t e = e0 + threadIdx.x;
-        if (e < xtot) {
-            const int64_t r = row_of(e, t_lo, t_hi);
-            const RowRef Rf(a, list[r]);
-            const Prod &P = *Rf.P;
-            const int64_t p = P.X.rp[Rf.i] + (e - xbase[r]);
-            const int32_t k = __ldg(P.X.ci + p);
-            xoff[e] = bit_of(P.km, (uint32_t)k) ? __ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k) : 0;
-        }
-        __syncthreads();
+        const RowRef Rf(a, list[lo]);
+        const Prod P = *Rf.P;
+        const int64_t p = P.X.rp[Rf.i] + (e - xbase[lo]);
+        const int32_t k = __ldg(P.X.ci + p);
+        xoff[e] = bit_of(P.km, (uint32_t)k) ? __ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k) : 0;
     }
 }
 
