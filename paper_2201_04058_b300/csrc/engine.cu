@@ -679,6 +679,7 @@ void mp_ctx::serve_loop() {
         std::vector<Result> res(batch.size());
         {
             std::lock_guard<std::mutex> ge(exec_mu);
+            TraceRange serve_range("mp.serve_batch");
             run_batch(qs, res);
             batches++;
             batched_queries += batch.size();
@@ -760,6 +761,7 @@ static bool fit3(const std::vector<std::array<double, 4>> &s, double out[3]) {
 
 extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t reps, const char *out_path,
                            double *best_ms) {
+    TraceRange tune_range("mp.autotune");
     if (!ctx || !n || !q) return MP_ERR_ARG;
     if (!ctx->finalized) return MP_ERR_STATE;
     std::vector<Query> parsed(n);

@@ -15,6 +15,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mp.h"
 #include "internal.h"
 #include "otree.h"
@@ -33,6 +35,15 @@ struct DevMat {
     }
 };
 using MatPtr = std::shared_ptr<DevMat>;
+
+// A named NVTX range for the scope (a batch, its planning, each wave, the cache offers, a
+// serving batch): visible on a profiler's timeline, free when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 struct mp_ctx {
     struct NodeType {

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <unordered_map>
 #include <unordered_set>
@@ -293,6 +294,7 @@ std::vector<int32_t> subchain_types(const Query &q, int i, int j) {
 }  // namespace
 
 int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
+    TraceRange batch_range("mp.batch");
     const size_t nq = qs.size();
     cudaEventRecord(ev0, stream);
     std::vector<std::vector<uint32_t *>> masks(nq);
@@ -510,6 +512,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             if (!qstatus[q]) otree.insert(qs[q].types, qs[q].pos_keys);
 
     // plans and the product DAG
+    std::unique_ptr<TraceRange> plan_range(new TraceRange("mp.plan"));
     std::vector<PNode> nodes;
     std::unordered_map<std::string, int> by_id;
     std::unordered_set<std::string> host_known;  // sub-chains planned as copies from the host tier
@@ -696,6 +699,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         nodes[root[q]].keep = true;
     }
 
+    plan_range.reset();
     // cache candidates: the longest computed sub-metapath of each query seen at least twice
     // (MP_INSERT_OTREE), none (MP_INSERT_FINAL), or every computed node (MP_INSERT_ALL)
     std::vector<int> candidate(nq, -1);
@@ -733,6 +737,9 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     };
     int wave_rc = MP_OK;
     for (int lvl = 1; lvl <= max_level && wave_rc == MP_OK; lvl++) {
+        char wave_name[32];
+        snprintf(wave_name, sizeof(wave_name), "mp.wave level %d", lvl);
+        TraceRange wave_range(wave_name);
         std::vector<int> members;
         std::vector<WaveIn> win;
         for (size_t x = 0; x < nodes.size(); x++) {
@@ -845,6 +852,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (r.status && first == MP_OK) first = r.status;
     }
     if (cache) {
+        TraceRange offer_range("mp.cache_offers");
         auto offer = [&](PNode &nd) {
             if ((nd.from_cache && !nd.from_host) || nd.filter || nd.status || !nd.res) return;
             const double f = (double)otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
