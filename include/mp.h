@@ -346,13 +346,20 @@ int mp_cachesim_state(mp_cachesim *c, double *L, double *used, uint32_t *items);
  *                         or NULL for no mask.
  *   out_cap, out_ci, out_val  caller's device buffers for up to out_cap entries.
  *   out_nnz               host: the row's number of entries.
+ * Preconditions: every x_ci entry is a row of Y (0 <= k < rows of Y, so y_rp[k + 1] can be
+ * read) and km, when given, has a bit for it; every y_ci entry lies in [0, y_cols).
  * Returns MP_OK; MP_ERR_TOO_LARGE when y_cols exceeds 16,777,216 (nothing runs) or the
  * row has more than out_cap entries (*out_nnz then holds the size needed and the output
- * buffers are untouched); MP_ERR_OVERFLOW for a count above 2^64-1; MP_ERR_ARG, MP_ERR_CUDA.
- * The call is synchronous (it waits for its stream). The first call on a device looks up
- * the scratch array's device address for that device; make that first call before any
- * stream capture. All calls share the one scratch array: calls that overlap on the GPU
- * (other threads or streams) race and must be serialised by the caller. */
+ * buffers are untouched); MP_ERR_OVERFLOW for a count above 2^64-1; MP_ERR_ARG for a NULL
+ * required pointer, a negative x_ci entry or a y_ci entry outside [0, y_cols) (those ids
+ * are checked on the device and never used as indexes); MP_ERR_STATE when cuda_stream is
+ * being captured into a CUDA graph; MP_ERR_CUDA when one of its own launches or copies
+ * fails (errors left by the caller's earlier work are neither reported nor cleared).
+ * The call is synchronous: it waits for its stream twice, so it must not be made while
+ * that stream is being captured. The first call on a device looks up the scratch array's
+ * device address for that device. All calls share the one scratch array, whose contents
+ * the next call overwrites: calls that overlap on the GPU (other threads or streams) race
+ * and must be serialised by the caller. */
 int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_t x_len, const int32_t *x_ci,
                            const uint64_t *x_val, const int64_t *y_rp, const int32_t *y_ci,
                            const uint64_t *y_val, uint32_t y_cols, const uint32_t *km,

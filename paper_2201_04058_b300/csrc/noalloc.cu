@@ -21,12 +21,15 @@
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
 namespace mp {
 
 // Scratch: a bitmap and a rank word per 32 output columns, then two status words.
+// ERR_RANGE (status bit): an input id outside its stated range; the call returns MP_ERR_ARG.
+static constexpr unsigned long long ERR_RANGE = 8ull;
 static constexpr uint32_t NOALLOC_MAX_COLS = 1u << 24;
 static constexpr uint32_t NOALLOC_WORDS = NOALLOC_MAX_COLS / 32;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[2 * NOALLOC_WORDS + 64];
@@ -42,6 +45,7 @@ struct NoallocRow {
     const uint64_t *y_val;
     const uint32_t *km, *cm;
     uint32_t nw;
+    uint32_t ncols;  // y_cols: column ids at or above it are rejected
 };
 
 __global__ void k_na_clear(uint32_t *bm, uint32_t nw, unsigned long long *status) {
@@ -49,16 +53,27 @@ __global__ void k_na_clear(uint32_t *bm, uint32_t nw, unsigned long long *status
     if (blockIdx.x == 0 && threadIdx.x < 2) status[threadIdx.x] = 0;
 }
 
-// Blocks take X entries in turn; a block's threads walk that entry's Y row.
+// Blocks take X entries in turn; a block's threads walk that entry's Y row. A column id
+// outside [0, y_cols) or a negative row id is never used as an index: it sets ERR_RANGE and
+// is skipped.
 template <bool NUM>
 __global__ void k_na_products(NoallocRow r, uint32_t *bm, const uint32_t *rank, unsigned long long *out_val,
                               unsigned long long *status) {
     for (uint64_t p = blockIdx.x; p < r.x_len; p += gridDim.x) {
         const int32_t k = r.x_ci[p];
+        if (k < 0) {
+            if (threadIdx.x == 0) atomicOr(status + 1, (unsigned long long)ERR_RANGE);
+            continue;
+        }
         if (!bit_of(r.km, (uint32_t)k)) continue;
         const uint64_t a = (NUM && r.x_val) ? r.x_val[p] : 1ull;
         for (int64_t q = r.y_rp[k] + threadIdx.x; q < r.y_rp[k + 1]; q += blockDim.x) {
-            const uint32_t j = (uint32_t)r.y_ci[q];
+            const int32_t jc = r.y_ci[q];
+            if (jc < 0 || (uint32_t)jc >= r.ncols) {
+                atomicOr(status + 1, (unsigned long long)ERR_RANGE);
+                continue;
+            }
+            const uint32_t j = (uint32_t)jc;
             if (!bit_of(r.cm, j)) continue;
             if (!NUM) {
                 atomicOr(bm + (j >> 5), 1u << (j & 31));
@@ -133,6 +148,20 @@ static int noalloc_scratch(int device, uint32_t **out) {
     return MP_OK;
 }
 
+// Launches one kernel and returns that launch's own error, so an error left behind by the
+// caller's earlier, unrelated work is neither reported as ours nor cleared.
+template <class... P, class... A>
+static cudaError_t na_launch(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A... args) {
+    const std::tuple<P...> typed(args...);
+    void *argv[sizeof...(P)];
+    std::apply([&](const auto &...x) {
+        size_t i = 0;
+        ((argv[i++] = (void *)&x), ...);
+    }, typed);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, 0, s);
+}
+
 extern "C" int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_t x_len, const int32_t *x_ci,
                                       const uint64_t *x_val, const int64_t *y_rp, const int32_t *y_ci,
                                       const uint64_t *y_val, uint32_t y_cols, const uint32_t *km,
@@ -146,50 +175,53 @@ extern "C" int mp_row_product_noalloc(int32_t device, void *cuda_stream, uint64_
     }
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return MP_ERR_CUDA;
-    if (cur != device && cudaSetDevice(device) != cudaSuccess) {
-        cudaGetLastError();
-        return MP_ERR_ARG;
-    }
+    if (cur != device && cudaSetDevice(device) != cudaSuccess) return MP_ERR_ARG;
+    auto done = [&](int code) {
+        if (cur != device) cudaSetDevice(cur);
+        return code;
+    };
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the call waits for its stream, which a stream under capture cannot do
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return done(MP_ERR_CUDA);
+    if (cap != cudaStreamCaptureStatusNone) return done(MP_ERR_STATE);
     uint32_t *scr = nullptr;
     int rc = noalloc_scratch(device, &scr);
-    if (rc) {
-        if (cur != device) cudaSetDevice(cur);
-        return rc;
-    }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (rc) return done(rc);
     const uint32_t nw = (y_cols + 31) / 32;
     uint32_t *bm = scr, *rank = scr + NOALLOC_WORDS;
     unsigned long long *status = (unsigned long long *)(scr + 2 * NOALLOC_WORDS);  // [nnz, error bits]
-    const NoallocRow r{x_len, x_ci, x_val, y_rp, y_ci, y_val, km, cm, nw};
+    const NoallocRow r{x_len, x_ci, x_val, y_rp, y_ci, y_val, km, cm, nw, y_cols};
     const unsigned gw = std::max(1u, std::min(grid_for(nw, 256), 1184u));
     const unsigned gx = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(x_len, 1184));
+    unsigned long long *no_val = nullptr;
     unsigned long long h[2] = {0, 0};
-    kl(k_na_clear, gw, 256, 0, s, bm, nw, status);
-    if (x_len) kl(k_na_products<false>, gx, 256, 0, s, r, bm, (const uint32_t *)rank, (unsigned long long *)nullptr,
-                  status);
-    kl(k_na_rank, 1, 1024, 0, s, (const uint32_t *)bm, rank, nw, status);
+    if (na_launch(k_na_clear, gw, 256, s, bm, nw, status) != cudaSuccess) return done(MP_ERR_CUDA);
+    if (x_len && na_launch(k_na_products<false>, gx, 256, s, r, bm, (const uint32_t *)rank, no_val, status) !=
+                     cudaSuccess)
+        return done(MP_ERR_CUDA);
+    if (na_launch(k_na_rank, 1, 1024, s, (const uint32_t *)bm, rank, nw, status) != cudaSuccess)
+        return done(MP_ERR_CUDA);
     if (cudaMemcpyAsync(h, status, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        rc = MP_ERR_CUDA;
-    } else if (h[0] > out_cap) {
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return done(MP_ERR_CUDA);
+    if (h[1] & ERR_RANGE) return done(MP_ERR_ARG);
+    if (h[0] > out_cap) {
         *out_nnz = h[0];
-        rc = MP_ERR_TOO_LARGE;
-    } else {
-        if (h[0] && (!out_ci || !out_val)) {
-            rc = MP_ERR_ARG;
-        } else if (h[0]) {
-            kl(k_na_fill, gw, 256, 0, s, (const uint32_t *)bm, (const uint32_t *)rank, nw, out_ci, out_val);
-            kl(k_na_products<true>, gx, 256, 0, s, r, bm, (const uint32_t *)rank, (unsigned long long *)out_val,
-               status);
-            if (cudaMemcpyAsync(h + 1, status + 1, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                rc = MP_ERR_CUDA;
-            else if (h[1] & ERR_OVERFLOW)
-                rc = MP_ERR_OVERFLOW;
-        }
-        if (!rc) *out_nnz = h[0];
+        return done(MP_ERR_TOO_LARGE);
     }
-    if (cudaGetLastError() != cudaSuccess && !rc) rc = MP_ERR_CUDA;
-    if (cur != device) cudaSetDevice(cur);
-    return rc;
+    if (h[0] && (!out_ci || !out_val)) return done(MP_ERR_ARG);
+    if (h[0]) {
+        if (na_launch(k_na_fill, gw, 256, s, (const uint32_t *)bm, (const uint32_t *)rank, nw, out_ci, out_val) !=
+                cudaSuccess ||
+            na_launch(k_na_products<true>, gx, 256, s, r, bm, (const uint32_t *)rank, (unsigned long long *)out_val,
+                      status) != cudaSuccess)
+            return done(MP_ERR_CUDA);
+        if (cudaMemcpyAsync(h + 1, status + 1, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return done(MP_ERR_CUDA);
+        if (h[1] & ERR_OVERFLOW) return done(MP_ERR_OVERFLOW);
+    }
+    *out_nnz = h[0];
+    return done(MP_OK);
 }
