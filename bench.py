@@ -24,6 +24,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -569,8 +570,7 @@ def run_small(args, local):
     bufs = [plain.query(q) for q in qs]
     p_s, p_prod = _time_plain(mp, plain, bufs, reps)
     b_s, b_prod = _time_batch(mp, plain, bufs, reps)
-    tune = os.path.join(ROOT, "gpurun_out", f"tune_{args.workload}.json")
-    os.makedirs(os.path.dirname(tune), exist_ok=True)
+    tune = os.path.join(tempfile.mkdtemp(prefix="mp_tune_"), f"tune_{args.workload}.json")
     mp.mp_autotune(plain.ctx, bufs, reps=2, out_path=tune)
     bt_s, _ = _time_batch(mp, plain, bufs, reps)
     ks, launches0 = mp.mp_kernel_stats(plain.ctx)
