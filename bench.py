@@ -1,20 +1,28 @@
 """Benchmark of the metapath-query engine on one B300 (or N independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
-                    [--workload scholarly] [--scale S] [--no-cpu-baseline]
+                    [--workload scholarly|serving|batched|stress] [--scale S]
+                    [--no-cpu-baseline] [--no-extra] [--serve-queries N]
 
-Workload "scholarly": a seeded scholarly-shaped HIN with 5 M papers, 4 M authors, 5 k
-venues and 50 k topics (Zipf author/topic degrees, one venue per paper, a uniform year
-per paper) and twenty constrained queries, four each of APA, APVPA, APTPA, TPAPT and
-VPTPV with year in [2010, 2020] on every paper position; all but APA are anchored on a
-seeded set of first-node entities. One step evaluates all twenty queries, each planned
-by the Eq. 1 / Eq. 2 DP, through the engine's C ABI. The HIN stays resident in HBM
-(ingestion is not query time, as in Sec. 4.1.4); L2 is flushed between steps.
+Workload "scholarly" (the default and the headline): a seeded scholarly-shaped HIN with
+5 M papers, 4 M authors, 5 k venues and 50 k topics (Zipf author/topic degrees, one venue
+per paper, a uniform year per paper) and twenty constrained queries, four each of APA,
+APVPA, APTPA, TPAPT and VPTPV with year in [2010, 2020] on every paper position; all but
+APA are anchored on a seeded set of first-node entities. One step evaluates all twenty
+queries, each planned by the Eq. 1 / Eq. 2 DP, through the engine's C ABI. The HIN stays
+resident in HBM (ingestion is not query time, as in Sec. 4.1.4); L2 is flushed between
+steps.
 
 Prints one JSON line: queries/s (value), per-query latency p50/p99, the end-to-end rate
-with results copied to pinned host memory, the dominant kernel's achieved bandwidth
-against the measured HBM peak, clocks sampled during the timed region, the CPU oracle's
-rate on a bounded sample, and the number of kernel launches.
+with results copied to pinned host memory, the batched form of the same step, the
+dominant kernel's achieved bandwidth against the measured HBM peak, clocks sampled during
+the timed region, the CPU oracle's rate on a bounded sample, and the number of kernel
+launches. Unless --no-extra, the line also carries "configs": compact measurements of the
+other workloads, each with its own clock record, dominant kernel and CPU oracle sample --
+the 2,000-paper HIN's plain APTPA query, its batched workload (256 queries) and stress
+workload (64 long metapaths, with cache replays), and the serving workload on the
+10 M-article news HIN at four arrival rates relative to the plain path's saturation
+(served with and without the cache, and the plain path, under the same arrivals).
 """
 from __future__ import annotations
 
@@ -47,8 +55,10 @@ def parse():
     ap.add_argument("--pool", type=int, default=500, help="template pool of the batched workload")
     ap.add_argument("--anchor-p", type=float, default=0.75,
                     help="share of batched queries with a first-node entity of interest")
-    ap.add_argument("--serve-queries", type=int, default=4000)
-    ap.add_argument("--load", type=float, default=1.0, help="arrival rate / plain-path saturation rate")
+    ap.add_argument("--serve-queries", type=int, default=2000,
+                    help="queries per arrival rate of the serving workload (a sample of its 100 k stream)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="the scholarly workload only (no summaries of the other configurations)")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--planner", default="eac", choices=list(PLANNERS),
@@ -426,40 +436,240 @@ def run_engine(args, ws, rank, local):
                        for k, v in kstats.items()}}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(hin, qs, args.cpu_sample_queries)
+    eng.close()
+    if rank == 0 and not args.no_extra and args.scale == 1.0:
+        # the other configurations, each with its own clocks, roofline and CPU oracle sample
+        del hin
+        out["configs"] = {
+            "1_plain": leg_plain_config1(mp, local, peak, peak_kind),
+            "3_batched": leg_small(mp, local, "batched", peak, peak_kind),
+            "5_stress": leg_small(mp, local, "stress", peak, peak_kind),
+            "4_serving": leg_serving(mp, local, peak, peak_kind, n=args.serve_queries),
+        }
     if rank == 0:
         print(json.dumps(out), flush=True)
-    eng.close()
 
 
-# ---------------------------------------------------------------- serving leg
+# ---------------------------------------------------------------- the other configurations
+#
+# Each leg below returns a compact summary (queries/s, p50/p99, a clock record sampled in
+# its timed region, the dominant kernel's bandwidth and the CPU oracle on a bounded sample)
+# that the default run folds into its JSON line under "configs"; --workload serving,
+# batched or stress prints one leg's full line instead.
 
-def run_serving(args, ws, rank, local):
-    """News-shaped HIN and a session query stream (Sec. 4.1.2) arriving as a Poisson
-    process; the serving loop (continuous batching, Overlap-Tree cache under the HBM
-    budget) against the plain one-query-at-a-time chain under the same arrivals."""
+def _roofline(mp, ctx, peak, peak_kind, note):
+    ks, _ = mp.mp_kernel_stats(ctx)
+    if not ks:
+        return None
+    name, k = max(ks.items(), key=lambda kv: kv[1]["ms"])
+    if k["ms"] <= 0:
+        return None
+    ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+            "note": note}
+
+
+def _pct(xs, q):
+    return float(np.percentile(xs, q)) if len(xs) else None
+
+
+def _oracle_sample(hin, qs, budget_s=6.0, max_q=None):
+    """The CPU oracle as it stands on the first queries of a workload, until budget_s of
+    host time is spent; returns (queries/s, the sample's description)."""
+    from oracle import chain as OC
+    from oracle.hin import OracleHIN
+    o = OracleHIN(hin)
+    n = 0
+    t0 = time.perf_counter()
+    for q in qs[:max_q or len(qs)]:
+        OC.evaluate(o, q)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of the {len(qs)} queries, single thread, {dt:.1f} s"}
+
+
+def _plain_pass(mp, eng, bufs):
+    """One query at a time, all queries ready at once: per-query wall latency from the
+    start (the queries before it run first) and products run."""
+    lat, prods = [], 0
+    t0 = time.perf_counter()
+    for b in bufs:
+        rc, t = mp.mp_submit(eng.ctx, b)
+        if rc != mp.MP_OK:
+            raise mp.MPError(rc, "query")
+        prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
+        mp.mp_release(eng.ctx, t)
+        lat.append(time.perf_counter() - t0)
+    return time.perf_counter() - t0, lat, prods
+
+
+def _batch_pass(mp, eng, bufs):
+    prods = 0
+    t0 = time.perf_counter()
+    rc, ts = mp.mp_submit_batch(eng.ctx, bufs)
+    if rc != mp.MP_OK:
+        raise mp.MPError(rc, "batch")
+    for t in ts:
+        prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
+        mp.mp_release(eng.ctx, t)
+    return time.perf_counter() - t0, prods
+
+
+def leg_plain_config1(mp, local, peak, peak_kind, reps=300):
+    """The 2,000-paper HIN, one unconstrained APTPA query at a time (1500 x 1500 result)."""
     import torch
     import gen
-    from paper_2201_04058_b300 import mp
+    hin = gen.config1_hin()
+    q = gen.config1_query()
+    e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE)
+    b = e.query(q)
+    for _ in range(10):
+        _, t = mp.mp_submit(e.ctx, b)
+        mp.mp_release(e.ctx, t)
+    torch.cuda.synchronize()
+    mp.mp_kernel_stats_reset(e.ctx)
+    lat = []
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            t1 = time.perf_counter()
+            rc, t = mp.mp_submit(e.ctx, b)
+            if rc != mp.MP_OK:
+                raise mp.MPError(rc, "APTPA")
+            mp.mp_release(e.ctx, t)
+            lat.append(1e3 * (time.perf_counter() - t1))
+        dt = time.perf_counter() - t0
+    roof = _roofline(mp, e.ctx, peak, peak_kind, "2,000-paper HIN: the working set sits in L2")
+    e.close()
+    return {"workload": "2,000-paper scholarly HIN, unconstrained APTPA, one query at a time",
+            "qps": reps / dt, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "clocks": clk.summary(),
+            "roofline": roof, "cpu_baseline": _oracle_sample(hin, [q] * 50, budget_s=3.0)}
 
-    torch.cuda.set_device(local)
-    hin = gen.config4_hin(seed=4, scale=args.scale)
-    qs, _ = gen.serving_stream(hin, seed=4, n=args.serve_queries)
+
+def leg_small(mp, local, which, peak, peak_kind, reps=3, pool=500, anchor_p=0.75, full=False):
+    """Batched workload (256 Zipf-drawn queries) or stress workload (64 long metapaths) on
+    the 2,000-paper HIN: the plain one-at-a-time chain vs one batch (shared sub-chains
+    once, one wave per level), autotuned, and replays through the Overlap-Tree cache."""
+    import torch
+    import gen
+    hin = gen.config1_hin()
+    if which == "batched":
+        qs = gen.batched_queries(seed=3, n=256, pool=pool, anchor_p=anchor_p)
+        name = (f"batched: 256 queries of length 3-7, Zipf(1.1) over a pool of {pool} templates, "
+                f"{anchor_p:.0%} anchored on one of 16 entities, 2,000-paper HIN")
+    else:
+        qs = gen.long_queries(5, 64)
+        name = "stress: 64 metapaths of length 7-9 through venues and topics, 2,000-paper HIN"
     plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE)
     bufs = [plain.query(q) for q in qs]
-    # saturation rate of the plain path: one query at a time, back to back
+    _plain_pass(mp, plain, bufs)
+    _batch_pass(mp, plain, bufs)
+    torch.cuda.synchronize()
+    mp.mp_kernel_stats_reset(plain.ctx)
+    p_s, b_s, p_lat, b_lat = [], [], [], []
+    with Clocks(local) as clk:
+        for _ in range(reps):
+            dt, lat, p_prod = _plain_pass(mp, plain, bufs)
+            p_s.append(dt)
+            p_lat += lat
+        for _ in range(reps):
+            dt, b_prod = _batch_pass(mp, plain, bufs)
+            b_s.append(dt)
+            b_lat += [dt] * len(bufs)  # every query of a batch completes with the batch
+    roof = _roofline(mp, plain.ctx, peak, peak_kind, "2,000-paper HIN: the working set sits in L2")
+    tune = os.path.join(tempfile.mkdtemp(prefix="mp_tune_"), f"tune_{which}.json")
+    mp.mp_autotune(plain.ctx, bufs, reps=2, out_path=tune)
+    bt = min(_batch_pass(mp, plain, bufs)[0] for _ in range(reps))
+    plain.close()
+    n = len(qs)
+    out = {"workload": name, "queries": n,
+           "plain": {"qps": n / float(np.median(p_s)), "p50_ms": 1e3 * _pct(p_lat, 50),
+                     "p99_ms": 1e3 * _pct(p_lat, 99), "products": p_prod},
+           "batched": {"qps": n / float(np.median(b_s)), "p50_ms": 1e3 * _pct(b_lat, 50),
+                       "p99_ms": 1e3 * _pct(b_lat, 99), "products": b_prod,
+                       "duplicate_product_fraction": 1.0 - b_prod / max(p_prod, 1)},
+           "batched_autotuned_qps": n / bt, "latency": "all queries arrive together; plain: time to each "
+                                                       "query's own result, batched: the batch's time",
+           "clocks": clk.summary(), "roofline": roof,
+           "cpu_baseline": _oracle_sample(hin, qs, budget_s=4.0)}
+    # replays through the cache: the first pass fills it, later passes reuse it
+    budgets = {"8GB": 8 << 30}
+    if which == "stress":
+        # 25 % of the bytes of all distinct intermediates forces evictions
+        e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, insertion=mp.MP_INSERT_ALL,
+                      cache_bytes=1 << 40, hbm_budget_bytes=1 << 40)
+        rc, ts = mp.mp_submit_batch(e.ctx, [e.query(q) for q in qs])
+        for t in ts:
+            mp.mp_release(e.ctx, t)
+        budgets["25pct"] = max(1 << 20, mp.mp_cache_stats(e.ctx)["bytes"] // 4)
+        e.close()
+    replays = {}
+    pols = (mp.MP_POLICY_ATRAPOS, mp.MP_POLICY_PGDS, mp.MP_POLICY_LRU) if full or which == "stress" else \
+        (mp.MP_POLICY_ATRAPOS,)
+    for label, budget in budgets.items():
+        for pol in pols:
+            e = mp.Engine(hin, device=local, policy=pol, cache_bytes=int(budget))
+            eb = [e.query(q) for q in qs]
+            cold_s, _ = _batch_pass(mp, e, eb)
+            warm = [_batch_pass(mp, e, eb) for _ in range(reps)]
+            replays[f"{label}/{['atrapos', 'pgds', 'lru'][pol]}"] = {
+                "first_pass_qps": n / cold_s, "replay_qps": n / float(np.median([w[0] for w in warm])),
+                "replay_products": warm[-1][1], "cache": mp.mp_cache_stats(e.ctx) if full else None}
+            e.close()
+        if label == "25pct" and full:
+            # the same budget with a second tier in host memory as large as everything
+            e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, cache_bytes=int(budget),
+                          host_tier_bytes=int(4 * budget))
+            eb = [e.query(q) for q in qs]
+            cold_s, _ = _batch_pass(mp, e, eb)
+            warm = [_batch_pass(mp, e, eb) for _ in range(reps)]
+            replays[f"{label}/atrapos+host_tier"] = {
+                "first_pass_qps": n / cold_s, "replay_qps": n / float(np.median([w[0] for w in warm])),
+                "replay_products": warm[-1][1], "cache": mp.mp_cache_stats(e.ctx),
+                "host_tier": mp.mp_host_tier_stats(e.ctx)}
+            e.close()
+    out["cached_replays"] = replays
+    if full:
+        out["batched_autotuned"] = {"qps": n / bt, "tune": json.load(open(tune))}
+    return out
+
+
+def leg_serving(mp, local, peak, peak_kind, scale=1.0, n=2000, loads=(0.5, 0.8, 1.0, 1.5), budget_gb=60.0):
+    """News-shaped HIN (10 M articles, 2 M persons, 1 M organisations, 200 k locations, 20 k
+    themes) and the session query stream of Sec. 4.1.2 arriving as a Poisson process at
+    several rates relative to the plain path's saturation: the serving loop (continuous
+    batching) with and without the Overlap-Tree cache against the plain one-query-at-a-time
+    chain under the same arrivals. A seeded sample of n queries of the 100 k stream."""
+    import torch
+    import gen
+    t_setup = time.perf_counter()
+    hin = gen.config4_hin(seed=4, scale=scale)
+    stream_q, _ = gen.serving_stream(hin, seed=4, n=100_000)
+    qs = stream_q[:n]
+    path = os.path.join(tempfile.mkdtemp(prefix="mp_news_"), "news.hin")
+    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, max_slots=1)
+    plain.save(path)
+    names = {"types": hin["types"], "props": {k: None for k in hin["props"]}}
+    del hin
+    bufs = [plain.query(q) for q in qs]
     for b in bufs[:20]:
         _, t = mp.mp_submit(plain.ctx, b)
         mp.mp_release(plain.ctx, t)
-    n_sat = min(len(bufs), 400)
+    torch.cuda.synchronize()
+    n_sat = min(len(bufs), 500)
     t0 = time.perf_counter()
     for b in bufs[:n_sat]:
         _, t = mp.mp_submit(plain.ctx, b)
         mp.mp_release(plain.ctx, t)
     sat = n_sat / (time.perf_counter() - t0)
-    rate = args.load * sat
-    arrivals = np.cumsum(gen.stream(4, 950).exponential(1.0 / rate, len(qs)))
+    setup_s = time.perf_counter() - t_setup
+    budget = int(budget_gb * (1 << 30))
 
-    def serve(eng):
+    def serve(eng, arrivals):
         qb = [eng.query(q) for q in qs]
         mp.mp_serve_start(eng.ctx)
         tickets = []
@@ -477,147 +687,67 @@ def run_serving(args, ws, rank, local):
                 raise mp.MPError(st, "served query")
             lat.append(mp.mp_result_latency(eng.ctx, t))
         end = time.perf_counter()
-        stats = mp.mp_serve_stats(eng.ctx)
         for t in tickets:
             mp.mp_release(eng.ctx, t)
+        ct = mp.mp_serve_counters(eng.ctx)
         mp.mp_serve_stop(eng.ctx)
-        return len(qs) / (end - start), lat, stats
+        return {"qps": len(qs) / (end - start), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "joined": ct["joined"], "max_inflight": ct["max_inflight"]}
 
-    plain_served = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, max_slots=1)
-    p_qps, p_lat, p_stats = serve(plain_served)
-    plain_served.close()
-    budget = int(args.serve_budget_gb * (1 << 30))
-    served = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, max_slots=64, hbm_budget_bytes=budget)
-    s_qps, s_lat, s_stats = serve(served)
-    cstats = mp.mp_cache_stats(served.ctx)
-    served.close()
+    nocache = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_NONE, max_slots=64,
+                        hbm_budget_bytes=budget)
+    rates = {}
+    for load in loads:
+        rate = load * sat
+        arrivals = np.cumsum(gen.stream(4, 950, int(load * 100)).exponential(1.0 / rate, len(qs)))
+        cached = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_ATRAPOS, max_slots=64,
+                           hbm_budget_bytes=budget)
+        with Clocks(local) as clk:
+            arms = {"plain": serve(plain, arrivals), "served_no_cache": serve(nocache, arrivals),
+                    "served_cache": serve(cached, arrivals)}
+        arms["served_cache"]["cache_hits"] = mp.mp_cache_stats(cached.ctx)["hits"]
+        cached.close()
+        rates[f"{load:g}x"] = dict(arms, arrival_qps=rate, clocks=clk.summary())
+    nocache.close()
     plain.close()
-    out = {"metric": METRIC, "value": s_qps, "unit": UNIT, "n_gpus": 1, "steps": len(qs), "warmup": 20,
-           "ms_per_step": 1e3 / s_qps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
-           "config": {"workload": "serving: news HIN, session query stream, Poisson arrivals",
-                      "articles": hin["types"]["R"], "persons": hin["types"]["E"], "orgs": hin["types"]["O"],
-                      "locations": hin["types"]["L"], "themes": hin["types"]["H"], "queries": len(qs),
-                      "arrival_rate_qps": rate, "load_vs_plain_saturation": args.load,
-                      "cache": f"ATRAPOS-OTree, {args.serve_budget_gb:g} GB", "max_slots": 64},
-           "p50_ms": float(np.percentile(s_lat, 50)), "p99_ms": float(np.percentile(s_lat, 99)),
-           "served": {"qps": s_qps, "batches": s_stats["batches"], "cache": cstats},
-           "plain": {"saturation_qps": sat, "qps_under_same_arrivals": p_qps,
-                     "p50_ms": float(np.percentile(p_lat, 50)), "p99_ms": float(np.percentile(p_lat, 99))}}
-    print(json.dumps(out), flush=True)
+    try:
+        os.remove(path)
+    except OSError:
+        pass
+    return {"workload": "serving: news HIN, session query stream (anchor entity, date window on every "
+                        "article position), Poisson arrivals",
+            "articles": names["types"]["R"], "persons": names["types"]["E"], "orgs": names["types"]["O"],
+            "locations": names["types"]["L"], "themes": names["types"]["H"],
+            "queries_per_rate": len(qs), "sample": f"first {len(qs)} queries of the seeded 100,000-query stream",
+            "plain_saturation_qps": sat, "cache": f"ATRAPOS-OTree, {budget_gb:g} GB budget", "max_slots": 64,
+            "rates": rates, "setup_s": setup_s,
+            "cpu_baseline": None, "cpu_baseline_note": "not run: the oracle would first build the CSR of "
+                                                       "180 M edges in numpy (minutes of host time)"}
 
 
-# ---------------------------------------------------------------- small-HIN legs
-
-def _time_plain(mp, eng, bufs, reps):
-    """One query at a time; returns (seconds per pass, products per pass)."""
-    import torch
-    for b in bufs:
-        _, t = mp.mp_submit(eng.ctx, b)
-        mp.mp_release(eng.ctx, t)
-    torch.cuda.synchronize()
-    prods = 0
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        for b in bufs:
-            rc, t = mp.mp_submit(eng.ctx, b)
-            if rc != mp.MP_OK:
-                raise mp.MPError(rc, "query")
-            prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
-            mp.mp_release(eng.ctx, t)
-    torch.cuda.synchronize()
-    return (time.perf_counter() - t0) / reps, prods / reps
-
-
-def _time_batch(mp, eng, bufs, reps, warm=1):
-    import torch
-    for _ in range(warm):
-        _, ts = mp.mp_submit_batch(eng.ctx, bufs)
-        for t in ts:
-            mp.mp_release(eng.ctx, t)
-    torch.cuda.synchronize()
-    prods = 0
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        rc, ts = mp.mp_submit_batch(eng.ctx, bufs)
-        if rc != mp.MP_OK:
-            raise mp.MPError(rc, "batch")
-        for t in ts:
-            prods += mp.mp_result_stats(eng.ctx, t)["n_products"]
-            mp.mp_release(eng.ctx, t)
-    torch.cuda.synchronize()
-    return (time.perf_counter() - t0) / reps, prods / reps
-
-
-def run_small(args, local):
-    """Batched workload (256 Zipf-drawn queries) or stress workload (64 long metapaths) on
-    the 2,000-paper HIN: plain one-at-a-time chain vs one batch (shared sub-chains once,
-    one wave per level) vs batch with the Overlap-Tree cache."""
-    import torch
-    import gen
+def run_leg(args, local):
+    """--workload serving | batched | stress: one leg's full JSON line."""
     from paper_2201_04058_b300 import mp
+    import torch
     torch.cuda.set_device(local)
-    hin = gen.config1_hin()
-    if args.workload == "batched":
-        qs = gen.batched_queries(seed=3, n=256, pool=args.pool, anchor_p=args.anchor_p)
-        name = (f"batched: 256 queries of length 3-7, Zipf(1.1) over a pool of {args.pool} templates, "
-                f"{args.anchor_p:.0%} anchored on one of 16 entities")
+    peak, kind = measured_peak()
+    if args.workload == "serving":
+        d = leg_serving(mp, local, peak, kind, scale=args.scale, n=args.serve_queries,
+                        budget_gb=args.serve_budget_gb)
+        head = d["rates"].get("1.5x") or list(d["rates"].values())[-1]
+        value, p99 = head["served_cache"]["qps"], head["served_cache"]["p99_ms"]
+        cfg = {"workload": d["workload"], "queries": d["queries_per_rate"]}
     else:
-        qs = gen.long_queries(5, 64)
-        name = "stress: 64 metapaths of length 7-9 through venues and topics"
-    reps = max(1, args.steps)
-    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE)
-    bufs = [plain.query(q) for q in qs]
-    p_s, p_prod = _time_plain(mp, plain, bufs, reps)
-    b_s, b_prod = _time_batch(mp, plain, bufs, reps)
-    tune = os.path.join(tempfile.mkdtemp(prefix="mp_tune_"), f"tune_{args.workload}.json")
-    mp.mp_autotune(plain.ctx, bufs, reps=2, out_path=tune)
-    bt_s, _ = _time_batch(mp, plain, bufs, reps)
-    ks, launches0 = mp.mp_kernel_stats(plain.ctx)
-    plain.close()
-    out_c = {}
-    budgets = {"8GB": 8 << 30}
-    if args.workload == "stress":
-        # 25 % of the bytes of all distinct intermediates forces evictions
-        e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, insertion=mp.MP_INSERT_ALL, hbm_budget_bytes=1 << 40)
-        rc, ts = mp.mp_submit_batch(e.ctx, [e.query(q) for q in qs])
-        for t in ts:
-            mp.mp_release(e.ctx, t)
-        budgets["25pct"] = max(1 << 20, mp.mp_cache_stats(e.ctx)["bytes"] // 4)
-        e.close()
-    for label, budget in budgets.items():
-        for pol in (mp.MP_POLICY_ATRAPOS, mp.MP_POLICY_PGDS, mp.MP_POLICY_LRU):
-            e = mp.Engine(hin, device=local, policy=pol, hbm_budget_bytes=int(budget))
-            eb = [e.query(q) for q in qs]
-            cold_s, cold_p = _time_batch(mp, e, eb, 1, warm=0)  # the first pass fills the cache
-            warm_s, warm_p = _time_batch(mp, e, eb, reps, warm=0)
-            out_c[f"{label}/{['atrapos', 'pgds', 'lru'][pol]}"] = {
-                "first_pass_qps": len(qs) / cold_s, "replay_qps": len(qs) / warm_s,
-                "replay_products": warm_p, "cache": mp.mp_cache_stats(e.ctx)}
-            e.close()
-        if label == "25pct":
-            # the same budget with a second tier in host memory as large as everything
-            e = mp.Engine(hin, device=local, policy=mp.MP_POLICY_ATRAPOS, hbm_budget_bytes=int(budget),
-                          host_tier_bytes=int(4 * budget))
-            eb = [e.query(q) for q in qs]
-            cold_s, cold_p = _time_batch(mp, e, eb, 1, warm=0)
-            warm_s, warm_p = _time_batch(mp, e, eb, reps, warm=0)
-            out_c[f"{label}/atrapos+host_tier"] = {
-                "first_pass_qps": len(qs) / cold_s, "replay_qps": len(qs) / warm_s, "replay_products": warm_p,
-                "cache": mp.mp_cache_stats(e.ctx), "host_tier": mp.mp_host_tier_stats(e.ctx)}
-            e.close()
-    res = {"metric": METRIC, "value": len(qs) / b_s, "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": 1,
-           "ms_per_step": 1e3 * b_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "u64", "data": "synthetic (seeded generator; no dataset)",
-           "config": {"workload": name, "papers": 2000, "authors": 1500, "venues": 50, "topics": 200,
-                      "queries_per_step": len(qs)},
-           "plain": {"qps": len(qs) / p_s, "products": p_prod},
-           "batched": {"qps": len(qs) / b_s, "products": b_prod,
-                       "duplicate_product_fraction": 1.0 - b_prod / max(p_prod, 1),
-                       "speedup_vs_plain": p_s / b_s},
-           "batched_autotuned": {"qps": len(qs) / bt_s, "tune": json.load(open(tune))},
-           "cached_replays": out_c}
-    print(json.dumps(res), flush=True)
+        d = leg_small(mp, local, args.workload, peak, kind, reps=max(1, args.steps), pool=args.pool,
+                      anchor_p=args.anchor_p, full=True)
+        value, p99 = d["batched"]["qps"], d["batched"]["p99_ms"]
+        cfg = {"workload": d["workload"], "queries_per_step": d["queries"]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
+           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic (seeded generator; no dataset)", "config": cfg, "p99_ms": p99,
+           "clocks": d.get("clocks") or head.get("clocks"), "roofline": d.get("roofline"),
+           "cpu_baseline": d.get("cpu_baseline"), "detail": d}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -626,13 +756,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "serving":
+    if args.workload in ("serving", "batched", "stress"):
         if rank == 0:
-            run_serving(args, ws, rank, local)
-        return
-    if args.workload in ("batched", "stress"):
-        if rank == 0:
-            run_small(args, local)
+            run_leg(args, local)
         return
     run_engine(args, ws, rank, local)
     if ws > 1:

@@ -78,13 +78,25 @@ extern "C" {
 #define MP_BIN_GLOBAL 3     /* split rows: fixed-size work items over all blocks, a bitmap +
                                rank or a dense count row per row in global scratch */
 
+/* Overlap-Tree constructions (Sec. 3.3.2); both give the same tree */
+#define MP_OTREE_NAIVE 0  /* the suffix-by-suffix insertion of Sec. 3.3.2 */
+#define MP_OTREE_ONLINE 1 /* Ukkonen's on-line construction (footnote of Sec. 3.3.2) */
+
 typedef struct mp_ctx mp_ctx;
 typedef uint64_t mp_ticket;
 
 typedef struct {
     int32_t device;            /* CUDA device ordinal */
-    uint64_t hbm_budget_bytes; /* bytes the cache may hold (Sec. 3.4 cache size) */
-    uint32_t max_slots;        /* queries admitted at once by the serving loop */
+    uint64_t hbm_budget_bytes; /* HBM byte budget of the queries' data: results held by
+                                  tickets, intermediates in flight and cache entries (the
+                                  HIN and the transient product workspace are not counted;
+                                  0 = no limit). Every product's exact result bytes are
+                                  charged before its arrays are made; when they do not fit,
+                                  the cache evicts its policy's victims first, and a product
+                                  that still cannot fit fails its query with MP_ERR_BUDGET.
+                                  The serving loop admits new queries only while the planned
+                                  result bytes of those in flight are below it. */
+    uint32_t max_slots;        /* queries in flight at once in the serving loop */
     int32_t policy;            /* MP_POLICY_* */
     int32_t planner;           /* MP_PLAN_* */
     void *cuda_stream;         /* cudaStream_t to launch on; NULL = the library's own */
@@ -100,10 +112,27 @@ typedef struct {
     uint64_t host_tier_bytes;  /* second cache tier in pinned host memory for results the
                                   device cache evicts (0 = off); a later plan may copy one
                                   back instead of recomputing it */
+    uint64_t cache_bytes;      /* capacity of the cache (the cache size of Sec. 3.4), within
+                                  the budget; 0 = the whole hbm_budget_bytes */
+    int32_t otree_construction; /* MP_OTREE_ONLINE (default) or MP_OTREE_NAIVE */
+    /* Optional device allocator for every device buffer the context makes (HIN, masks,
+     * results, intermediates, workspaces), e.g. PyTorch's caching allocator, so that one
+     * pool serves the caller and the engine. alloc returns `bytes` of device memory on
+     * the context's device, usable in the order of `stream` (the context's cudaStream_t),
+     * or NULL when it cannot; free gives back a buffer alloc returned, in the order of
+     * `stream`: work queued on `stream` before the call may still use it, and the buffer
+     * may serve later allocations on that stream. Both are called from the thread that
+     * runs the query (the caller's, or the serving loop's), never concurrently for one
+     * context. Both NULL (the default): the CUDA stream-ordered pool. Setting one alone is
+     * MP_ERR_ARG at mp_create. */
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *alloc_user;          /* passed to alloc and free as `user` */
 } mp_config;
 
-/* Fill *cfg with defaults: device 0, 8 GiB budget, 64 slots, ATRAPOS policy, DP
- * planner, alpha = beta = gamma = 1, automatic bins, no size guard. */
+/* Fill *cfg with defaults: device 0, 8 GiB budget (the cache may use all of it), 64 slots,
+ * ATRAPOS policy, DP planner, alpha = beta = gamma = 1, automatic bins, no size guard,
+ * on-line Overlap-Tree construction, the CUDA stream-ordered pool. */
 void mp_config_default(mp_config *cfg);
 
 /* Create a context on cfg->device. Errors: MP_ERR_ARG, MP_ERR_CUDA. */
@@ -182,18 +211,30 @@ int mp_wait(mp_ctx *ctx, mp_ticket ticket, uint32_t timeout_ms);
 
 /* ---- serving (Problem 2 as a live request stream)
  *
- * mp_serve_start starts a host thread that serves the workload as it arrives: each round
- * it takes every submitted query that is waiting (up to mp_config.max_slots) and runs
- * them as one batch -- one product DAG, shared sub-chains once, one wave per plan level,
- * the cache (Sec. 3.4) under the HBM byte budget -- while queries that arrive during the
- * round wait for the next one (continuous batching). While serving, mp_submit and
- * mp_submit_batch only queue the queries and return tickets at once; results are read
- * after mp_wait. mp_serve_stop finishes the queued work and stops the thread
- * (mp_destroy stops it too). Errors: MP_ERR_STATE (not finalised, already serving). */
+ * mp_serve_start starts a host thread that serves the workload as it arrives, with
+ * continuous batching. Every turn it admits the queries that have arrived, while fewer
+ * than mp_config.max_slots are in flight and the planned result bytes of those in flight
+ * are below the HBM budget: their plans join one product DAG with the queries already in
+ * flight (a sub-chain that is on its way or held is shared, a cached one is reused,
+ * Sec. 3.4). It then runs one wave -- every product whose operands are ready, of any
+ * query, in one set of launches -- and publishes every query whose result is complete.
+ * A query that arrives while others are on the GPU therefore starts at the next wave,
+ * beside their later products. While serving, mp_submit and mp_submit_batch only queue
+ * the queries and return tickets at once; results are read after mp_wait.
+ * mp_serve_stop finishes the queued work and stops the thread (mp_destroy stops it too).
+ * Errors: MP_ERR_STATE (not finalised, already serving). */
 int mp_serve_start(mp_ctx *ctx);
 int mp_serve_stop(mp_ctx *ctx);
-/* Rounds run and queries served so far, and queries waiting now. */
+/* Admission groups (turns that admitted at least one query) and queries served so far,
+ * and queries waiting for admission now. */
 int mp_serve_stats(mp_ctx *ctx, uint64_t *batches, uint64_t *queries, uint64_t *queued);
+/* Waves the serving loop has run, queries it admitted while other queries were in flight
+ * (their products joined waves beside the in-flight ones), and the most queries in flight
+ * at once. Any pointer may be NULL. */
+int mp_serve_counters(mp_ctx *ctx, uint64_t *waves, uint64_t *joined, uint64_t *max_inflight);
+/* Bytes charged to the HBM budget now (results held by tickets, intermediates in flight,
+ * cache entries) and the most charged at once since mp_create. Any pointer may be NULL. */
+int mp_budget_stats(mp_ctx *ctx, uint64_t *held, uint64_t *peak);
 /* Host wall time in ms from a ticket's submission to its completion (MP_ERR_STATE while
  * it is still pending). */
 int mp_result_latency(mp_ctx *ctx, mp_ticket ticket, double *ms);
@@ -297,7 +338,11 @@ int mp_kernel_stats_reset(mp_ctx *ctx);
  * inserted metapath (NULL or "" = unconstrained); keys of sub-metapaths are the
  * descriptions of their positions, renumbered from 0, as "i:<desc>" joined by '|'. */
 typedef struct mp_otree mp_otree;
+/* A tree built by the naive insertion (mp_otree_create) or by the construction given
+ * (mp_otree_create_ex: MP_OTREE_NAIVE or MP_OTREE_ONLINE, else MP_ERR_ARG). Both give the
+ * same tree, frequencies and constraint entries; a tree keeps its construction. */
 int mp_otree_create(mp_otree **out);
+int mp_otree_create_ex(int32_t construction, mp_otree **out);
 void mp_otree_destroy(mp_otree *t);
 /* Insert a metapath and all its suffixes (Sec. 3.3.2). */
 int mp_otree_insert(mp_otree *t, uint32_t n, const int32_t *types, const char *const *pos_keys);

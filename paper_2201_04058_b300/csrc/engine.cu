@@ -35,9 +35,6 @@ using Result = mp_ctx::Result;
 namespace mp {
 
 struct PoolAlloc final : Alloc {
-    // failure injection for tests: after this many more successful allocations, every
-    // allocation fails (UINT64_MAX = never)
-    uint64_t fail_after = UINT64_MAX;
     void *alloc(size_t bytes, cudaStream_t s) override {
         void *p = nullptr;
         if (fail_after == 0) return nullptr;
@@ -51,6 +48,24 @@ struct PoolAlloc final : Alloc {
     }
     void free(void *p, cudaStream_t s) override {
         if (p) cudaFreeAsync(p, s);
+    }
+};
+
+// The caller's allocator (mp_config.alloc / .free), e.g. PyTorch's caching allocator.
+struct HookAlloc final : Alloc {
+    void *(*fa)(size_t, void *, void *);
+    void (*ff)(void *, void *, void *);
+    void *user;
+    HookAlloc(void *(*a)(size_t, void *, void *), void (*f)(void *, void *, void *), void *u)
+        : fa(a), ff(f), user(u) {}
+    void *alloc(size_t bytes, cudaStream_t s) override {
+        if (fail_after == 0) return nullptr;
+        if (fail_after != UINT64_MAX) fail_after--;
+        if (bytes == 0) bytes = 16;
+        return fa(bytes, (void *)s, user);
+    }
+    void free(void *p, cudaStream_t s) override {
+        if (p) ff(p, (void *)s, user);
     }
 };
 
@@ -85,6 +100,11 @@ extern "C" void mp_config_default(mp_config *c) {
     c->seed = 1;
     c->insertion = MP_INSERT_OTREE;
     c->tune_file = nullptr;
+    c->cache_bytes = 0;
+    c->otree_construction = MP_OTREE_ONLINE;
+    c->alloc = nullptr;
+    c->free = nullptr;
+    c->alloc_user = nullptr;
 }
 
 extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
@@ -94,7 +114,8 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
     if (cfg) c = *cfg; else mp_config_default(&c);
     if (c.policy < 0 || c.policy > MP_POLICY_NONE || c.planner < 0 || c.planner > MP_PLAN_DP_MNC ||
         c.force_bin_class < MP_BIN_AUTO || c.force_bin_class > MP_BIN_GLOBAL || c.insertion < MP_INSERT_OTREE ||
-        c.insertion > MP_INSERT_ALL)
+        c.insertion > MP_INSERT_ALL || (c.otree_construction != MP_OTREE_NAIVE && c.otree_construction != MP_OTREE_ONLINE) ||
+        (!c.alloc) != (!c.free))
         return MP_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
@@ -145,13 +166,23 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "glob_occ") ctx->tun.glob_occ = (int)v;
                 else if (k == "seg_walk") ctx->tun.seg_walk = (int)v;
                 else if (k == "graphs") ctx->tun.graphs = (int)v;
+                else if (k == "lbs") ctx->tun.lbs = (int)v;
+                else if (k == "lbs_occ") ctx->tun.lbs_occ = (int)v;
             }
             a = b + 1;
         }
     }
     if (check_cuda(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "stream")) return MP_ERR_CUDA;
-    ctx->alloc.reset(new PoolAlloc());
-    if (c.policy != MP_POLICY_NONE) ctx->cache.reset(new CachePolicy((double)c.hbm_budget_bytes, c.policy));
+    if (c.alloc) ctx->alloc.reset(new HookAlloc(c.alloc, c.free, c.alloc_user));
+    else ctx->alloc.reset(new PoolAlloc());
+    ctx->otree = OverlapTree(c.otree_construction == MP_OTREE_ONLINE ? OverlapTree::ONLINE : OverlapTree::NAIVE);
+    if (c.policy != MP_POLICY_NONE) {
+        // the cache's capacity (Sec. 3.4 cache size) within the HBM budget
+        uint64_t cap = c.cache_bytes ? c.cache_bytes : c.hbm_budget_bytes;
+        if (c.hbm_budget_bytes && cap > c.hbm_budget_bytes) cap = c.hbm_budget_bytes;
+        if (!cap) cap = UINT64_MAX / 2;
+        ctx->cache.reset(new CachePolicy((double)cap, c.policy));
+    }
     if (c.tune_file) {
         if (FILE *f = fopen(c.tune_file, "r")) {
             char buf[4096];
@@ -306,21 +337,39 @@ extern "C" int mp_finalize_hin(mp_ctx *ctx) {
     if (ctx->finalized) return MP_ERR_STATE;
     cudaSetDevice(ctx->cfg.device);
     cudaStream_t s = ctx->stream;
-    for (size_t r = 0; r < ctx->rels.size(); r += 2) {
+    // host CSRs of every relation in both directions, built on host threads (ingestion;
+    // Sec. 4.1.4 leaves it out of query time), then uploaded one by one
+    const size_t nrel = ctx->rels.size();
+    std::vector<std::vector<int64_t>> hrp(nrel);
+    std::vector<std::vector<int32_t>> hci(nrel);
+    {
+        std::vector<std::thread> th;
+        for (size_t x = 0; x < nrel; x++) {
+            auto &R = ctx->rels[x];
+            if (!R.hrp.empty()) {  // loaded from a saved HIN
+                hrp[x].swap(R.hrp);
+                hci[x].swap(R.hci);
+                continue;
+            }
+            auto &f = ctx->rels[x & ~(size_t)1];
+            const uint32_t nr = ctx->types[R.src].count;
+            const bool fwd = (x & 1) == 0;
+            th.emplace_back([&, x, nr, fwd] {
+                if (fwd) build_csr(f.s, f.d, nr, hrp[x], hci[x]);
+                else build_csr(f.d, f.s, nr, hrp[x], hci[x]);
+            });
+        }
+        for (auto &t : th) t.join();
+    }
+    for (size_t r = 0; r < nrel; r += 2) {
         auto &f = ctx->rels[r];
         for (int dir = 0; dir < 2; dir++) {
             auto &R = ctx->rels[r + dir];
             const uint32_t nr = ctx->types[R.src].count, nc = ctx->types[R.dst].count;
             std::vector<int64_t> rp;
             std::vector<int32_t> ci;
-            if (!R.hrp.empty()) {  // loaded from a saved HIN
-                rp.swap(R.hrp);
-                ci.swap(R.hci);
-            } else if (dir == 0) {
-                build_csr(f.s, f.d, nr, rp, ci);
-            } else {
-                build_csr(f.d, f.s, nr, rp, ci);
-            }
+            rp.swap(hrp[r + dir]);
+            ci.swap(hci[r + dir]);
             Mat &m = R.dev;
             m.nrows = nr;
             m.ncols = nc;
@@ -349,7 +398,7 @@ extern "C" int mp_finalize_hin(mp_ctx *ctx) {
     }
     if (check_cuda(cudaStreamSynchronize(s), "upload")) return MP_ERR_CUDA;
     ctx->finalized = true;
-    if (ctx->fail_alloc_after != UINT64_MAX) static_cast<PoolAlloc *>(ctx->alloc.get())->fail_after = ctx->fail_alloc_after;
+    if (ctx->fail_alloc_after != UINT64_MAX) ctx->alloc->fail_after = ctx->fail_alloc_after;
     return MP_OK;
 }
 
@@ -657,45 +706,66 @@ extern "C" int mp_submit_batch(mp_ctx *ctx, uint32_t n, const mp_query *q, mp_ti
     return serving ? enqueue(ctx, qs, tickets) : run_now(ctx, qs, tickets);
 }
 
-// The serving loop: take every query that has arrived (up to max_slots) as one batch,
-// run it as one product DAG, publish the results; queries that arrive meanwhile wait for
-// the next round (continuous batching).
+// The serving loop (continuous batching). Every turn it admits the queries that have
+// arrived, as far as free slots (mp_config.max_slots) and the HBM budget allow: their
+// plans join the product DAG of the queries already in flight, sharing any sub-chain
+// that is on its way or held. It then runs one wave -- every product whose operands are
+// ready, whichever query it belongs to, in one set of launches -- and publishes each
+// query whose result is complete. A query that arrives while others are on the GPU thus
+// starts with the next wave, beside their later products, instead of waiting for them
+// to finish. Admission by bytes: new queries wait while the planned result bytes of the
+// queries in flight exceed the budget (one query is always admitted when none is in
+// flight); the exact size of every product is charged before its arrays are made, where
+// the cache yields first (MP_ERR_BUDGET only when the query's work cannot fit at all).
 void mp_ctx::serve_loop() {
     cudaSetDevice(cfg.device);
+    const size_t slots = cfg.max_slots ? cfg.max_slots : 1;
+    const double budget = cfg.hbm_budget_bytes ? (double)cfg.hbm_budget_bytes : INFINITY;
     for (;;) {
         std::vector<Pending> batch;
         {
             std::unique_lock<std::mutex> lk(qmu);
-            qcv.wait(lk, [&] { return stop_req || !queue.empty(); });
-            if (queue.empty() && stop_req) break;
-            const size_t slots = cfg.max_slots ? cfg.max_slots : 1;
-            while (!queue.empty() && batch.size() < slots) {
+            qcv.wait(lk, [&] { return stop_req || !queue.empty() || inflight > 0; });
+            if (queue.empty() && stop_req && inflight == 0) break;
+            while (!queue.empty() && inflight + batch.size() < slots &&
+                   (inflight + batch.size() == 0 || inflight_bytes < budget)) {
                 batch.push_back(std::move(queue.front()));
                 queue.pop_front();
             }
         }
-        std::vector<Query> qs(batch.size());
-        for (size_t i = 0; i < batch.size(); i++) qs[i] = std::move(batch[i].q);
-        std::vector<Result> res(batch.size());
+        std::vector<Flight> done;
         {
             std::lock_guard<std::mutex> ge(exec_mu);
-            TraceRange serve_range("mp.serve_batch");
-            run_batch(qs, res);
-            batches++;
-            batched_queries += batch.size();
-        }
-        const auto t1 = std::chrono::steady_clock::now();
-        {
-            std::lock_guard<std::mutex> g(mu);
-            for (size_t i = 0; i < batch.size(); i++) {
-                auto it = results.find(batch[i].ticket);
-                if (it == results.end()) continue;  // released before it finished
-                res[i].latency_ms = std::chrono::duration<double, std::milli>(t1 - batch[i].t0).count();
-                res[i].done = true;
-                it->second = std::move(res[i]);
+            TraceRange serve_range("mp.serve_turn");
+            if (!batch.empty()) {
+                std::vector<Query> qs(batch.size());
+                std::vector<uint64_t> tk(batch.size());
+                std::vector<std::chrono::steady_clock::time_point> t0s(batch.size());
+                for (size_t i = 0; i < batch.size(); i++) {
+                    qs[i] = std::move(batch[i].q);
+                    tk[i] = batch[i].ticket;
+                    t0s[i] = batch[i].t0;
+                }
+                std::vector<int64_t> ids;
+                const size_t before = ex.flights.size();
+                if (before) serve_joined += qs.size();  // joining work already on the GPU
+                admit(qs, tk, t0s, ids);
+                batches++;
+                serve_max_inflight = std::max<uint64_t>(serve_max_inflight, ex.flights.size());
             }
+            finish_flights(done);  // queries served from the cache or failed at admission
+            if (!ex.flights.empty()) {
+                serve_waves++;
+                const int rc = run_wave();
+                if (rc) abort_nodes(rc);
+                finish_flights(done);
+            }
+            batched_queries += done.size();
+            std::lock_guard<std::mutex> g(qmu);
+            inflight = ex.flights.size();
+            inflight_bytes = ex.est_bytes;
         }
-        done_cv.notify_all();
+        if (!done.empty()) publish(done);
     }
 }
 
@@ -733,6 +803,22 @@ extern "C" int mp_serve_stats(mp_ctx *ctx, uint64_t *batches, uint64_t *queries,
     }
     std::lock_guard<std::mutex> g(ctx->qmu);
     if (queued) *queued = ctx->queue.size();
+    return MP_OK;
+}
+
+extern "C" int mp_serve_counters(mp_ctx *ctx, uint64_t *waves, uint64_t *joined, uint64_t *max_inflight) {
+    if (!ctx) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> ge(ctx->exec_mu);
+    if (waves) *waves = ctx->serve_waves;
+    if (joined) *joined = ctx->serve_joined;
+    if (max_inflight) *max_inflight = ctx->serve_max_inflight;
+    return MP_OK;
+}
+
+extern "C" int mp_budget_stats(mp_ctx *ctx, uint64_t *held, uint64_t *peak) {
+    if (!ctx) return MP_ERR_ARG;
+    if (held) *held = (uint64_t)std::max<int64_t>(0, ctx->held.load());
+    if (peak) *peak = (uint64_t)std::max<int64_t>(0, ctx->held_peak.load());
     return MP_OK;
 }
 

@@ -6,6 +6,8 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <deque>
 #include <map>
 #include <memory>
@@ -22,12 +24,16 @@
 #include "otree.h"
 
 // A device CSR shared by results, cache entries and in-flight products; freed (stream
-// ordered) when the last holder lets go. Base relations are never owned.
+// ordered) when the last holder lets go. Base relations are never owned. Its bytes stay
+// charged to the context's HBM budget (held) while it lives.
 struct DevMat {
     mp::Mat m;
     mp::Alloc *al = nullptr;
     cudaStream_t s = nullptr;
+    std::atomic<int64_t> *held = nullptr;
+    int64_t charged = 0;
     ~DevMat() {
+        if (held) held->fetch_sub(charged);
         if (!al) return;
         if (m.rp) al->free(m.rp, s);
         if (m.ci) al->free(m.ci, s);
@@ -106,7 +112,12 @@ struct mp_ctx {
     std::deque<Pending> queue;
     std::thread server;
     bool serving = false, stop_req = false;
-    uint64_t batches = 0, batched_queries = 0;
+    size_t inflight = 0;          // with qmu: queries admitted by the serving loop, not yet finished
+    double inflight_bytes = 0.0;  // with qmu: their planned result bytes
+    uint64_t batches = 0, batched_queries = 0;  // admission groups of the serving loop, queries served
+    uint64_t serve_waves = 0;         // waves the serving loop ran
+    uint64_t serve_joined = 0;        // queries admitted while others were in flight
+    uint64_t serve_max_inflight = 0;  // most queries in flight at once
     void serve_loop();
     // nnz of masked base factors already counted: (relation, row key, column key) -> nnz
     std::unordered_map<std::string, double> leaf_memo;
@@ -174,7 +185,97 @@ struct mp_ctx {
     int parse(const mp_query *q, Query &out);
     int build_masks(const Query &q, std::vector<uint32_t *> &masks);
     void free_masks(std::vector<uint32_t *> &masks);
+
+    // ---- the executor: a product DAG that queries join as they are admitted (query.cu)
+    //
+    // A query in flight: its parsed form and masks (shared with the nodes it registered,
+    // which may outlive it when later queries reuse them), its plan's root and cache
+    // candidate, and the counters of its result.
+    struct QState {
+        mp_ctx *ctx = nullptr;
+        Query q;
+        std::vector<uint32_t *> masks;
+        ~QState();
+    };
+    struct Flight {
+        int64_t id = -1;
+        std::shared_ptr<QState> qs;
+        int64_t root = -1, candidate = -1;
+        std::vector<int64_t> keeps;  // nodes it keeps until it finishes: root, candidates
+        int status = MP_OK;
+        uint64_t ticket = 0;
+        std::chrono::steady_clock::time_point t0;
+        double est_bytes = 0.0;  // planned bytes of the results it computes
+        Result r;
+        bool finished = false;
+    };
+    // One sub-chain of some query's plan: factors i..j of the registering query
+    // (positions i..j+1), split at k; children are node ids (-1 = the base factor).
+    struct PNode {
+        std::string id;
+        std::vector<int32_t> types;
+        std::string key;
+        int64_t flight = -1;
+        std::shared_ptr<QState> qs;
+        int i = 0, j = 0, k = 0;
+        int64_t left = -1, right = -1;
+        MatPtr res;
+        bool done = false;
+        bool from_cache = false;
+        bool from_host = false;   // copied back from the host tier (offered to the cache again)
+        bool filter = false;      // length-2 query: diag(M_1) A diag(M_2)
+        int consumers = 0;        // parents that have not run yet
+        int keepers = 0;          // flights that offer it to the cache when they finish
+        int status = MP_OK;
+        double ms = 0.0;          // device time of this node's own product
+        double subtree_ms = 0.0;  // of every product this node's computation needed
+        double c_ops = 0.0;       // Eq. 2 with the product's actual counts
+        double rho_est = 0.0;     // planner density estimate (for later queries)
+        mp::Stats st;
+    };
+    struct Exec {
+        std::unordered_map<int64_t, PNode> nodes;
+        std::unordered_map<std::string, int64_t> by_id;  // sub-chains whose result is on its way or held
+        std::map<int64_t, Flight> flights;               // admitted, not yet finished
+        int64_t next_node = 0, next_flight = 0;
+        double est_bytes = 0.0;                          // planned bytes of the flights
+    } ex;
+    // Plans the queries and joins their products to the DAG; returns the flight ids (in
+    // order). A query that fails before planning gets a flight with its status.
+    int admit(std::vector<Query> &qs, const std::vector<uint64_t> &tickets,
+              const std::vector<std::chrono::steady_clock::time_point> &t0s, std::vector<int64_t> &ids);
+    // One wave: every node whose operands are ready, in one set of launches.
+    int run_wave();
+    // Flights whose root is done: results, statistics, cache offers; moved to `done`.
+    void finish_flights(std::vector<Flight> &done);
+    // a node of the DAG; a missing id is a broken invariant of the executor, reported and
+    // fatal (never a silently made empty node)
+    PNode &node(int64_t id) {
+        auto it = ex.nodes.find(id);
+        if (it == ex.nodes.end()) {
+            fprintf(stderr, "mp: internal error: product node %lld is gone\n", (long long)id);
+            abort();
+        }
+        return it->second;
+    }
+    void release_node(int64_t id);  // drop a node nobody needs any more
+    void abort_nodes(int rc);       // a failed wave: every node not run yet fails with rc
+    // results of finished serving flights into their tickets (wakes mp_wait)
+    void publish(std::vector<Flight> &done);
     int run_batch(std::vector<Query> &qs, std::vector<Result> &rs);
+
+    // ---- the HBM byte budget (mp_config.hbm_budget_bytes): bytes of results and
+    // intermediates alive (held by tickets, cache entries or the DAG); the cache yields
+    std::atomic<int64_t> held{0};
+    std::atomic<int64_t> held_peak{0};
+    void note_held() {
+        int64_t h = held.load(), p = held_peak.load();
+        while (h > p && !held_peak.compare_exchange_weak(p, h)) {
+        }
+    }
+    int reserve_bytes(int64_t bytes);    // MP_OK (charged) or MP_ERR_BUDGET
+    void unreserve_bytes(int64_t bytes);
+    bool evict_one();                    // the cache's victim, to make room for work
     // set by mp_plan_query: run_batch plans its first query, keeps the plan here and runs
     // no product (and leaves the Overlap Tree and the cache untouched)
     struct Explain {
@@ -183,7 +284,7 @@ struct mp_ctx {
         std::vector<int> split;
         std::vector<double> nnz;
     } explain;
-    MatPtr wrap(const mp::Mat &m);
+    MatPtr wrap(const mp::Mat &m, bool charged = false);
     void free_mat(mp::Mat &m);
     void release_result(Result &r);
     void cache_clear();

@@ -47,6 +47,8 @@ struct Tuning {
     int combine = 1;             // split-row kernel: shared-memory combining of hot outputs
     int short_walk = 0;          // split-row kernel: one thread per X entry on short Y rows
     int seg_walk = 1;            // split-row kernel: one warp per segment on long Y rows
+    int lbs = 1;                 // split-row kernel: warp-level product walk (0: block-staged walk)
+    int lbs_occ = 6;             // resident blocks per SM of the warp-walk count-adding passes (6 or 4)
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     // GLOBAL rows with prod_i >= glob_dense * ncols accumulate their counts in a dense u64
     // row (one pass gives both the size and the values); 0 turns the dense rows off
@@ -94,8 +96,10 @@ struct Mat {
     DCsr view() const { return DCsr{rp, ci, val, nrows, ncols}; }
 };
 
-// Stream-ordered device allocation used for results and workspaces.
+// Stream-ordered device allocation used for results and workspaces. fail_after (tests):
+// after this many more successful allocations every allocation fails (UINT64_MAX = never).
 struct Alloc {
+    uint64_t fail_after = UINT64_MAX;
     virtual void *alloc(size_t bytes, cudaStream_t s) = 0;
     virtual void free(void *p, cudaStream_t s) = 0;
     virtual ~Alloc() = default;
@@ -151,9 +155,18 @@ struct WaveCache {
     void clear(Alloc &al, cudaStream_t s);
 };
 
+// The HBM byte budget as the wave executor sees it: each product's exact result bytes are
+// reserved once its size is known and before its arrays are made; MP_ERR_BUDGET fails that
+// product alone. A reservation of a product that then fails is returned.
+struct Budget {
+    virtual int reserve(int64_t bytes) = 0;
+    virtual void unreserve(int64_t bytes) = 0;
+    virtual ~Budget() = default;
+};
+
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
                 uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only = false,
-                WaveCache *wc = nullptr);
+                WaveCache *wc = nullptr, Budget *bud = nullptr);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,

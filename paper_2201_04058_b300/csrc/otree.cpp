@@ -1,11 +1,12 @@
 // Overlap Tree (Sec. 3.3) and the cache replacement policies of Sec. 3.4 (Alg. 1).
 //
-// The tree is a generalised suffix tree over the workload's metapaths built by the naive
-// insertion of Sec. 3.3.2: for each query, the whole metapath and every proper suffix,
-// each ended by the query's own terminator, is walked from the root; a walk that stops
-// inside an edge splits it with a new internal node and the rest of the suffix becomes a
-// new leaf. Each node on the walk counts one more occurrence (f), so f is the number of
-// leaves below a node. Each node also keeps a constraints index (Sec. 3.3.4): per
+// The tree is a generalised suffix tree over the workload's metapaths, built either by the
+// naive insertion of Sec. 3.3.2 (for each query, the whole metapath and every proper
+// suffix, each ended by the query's own terminator, is walked from the root; a walk that
+// stops inside an edge splits it with a new internal node and the rest of the suffix
+// becomes a new leaf) or on-line with Ukkonen's algorithm (the footnote of Sec. 3.3.2);
+// both give the same tree. Each node on the path to a suffix's leaf counts one more
+// occurrence (f), so f is the number of leaves below a node. Each node also keeps a constraints index (Sec. 3.3.4): per
 // canonical constraint key of its positions, the entry (f, p, c, rho).
 #include "otree.h"
 
@@ -46,95 +47,168 @@ std::string restrict_key(const std::string &key, size_t len) {
     return out;
 }
 
-OverlapTree::OverlapTree() { nodes_.emplace_back(); }
+OverlapTree::OverlapTree(int construction) : construction_(construction == ONLINE ? ONLINE : NAIVE) {
+    nodes_.emplace_back();
+}
 
 uint64_t OverlapTree::insert(const std::vector<int32_t> &types, const std::vector<std::string> &pos_keys) {
     const uint64_t q = queries_++;
     std::vector<int32_t> s(types);
     s.push_back(-(int32_t)(q + 1));
-    const size_t n = types.size();
-    for (size_t k = 0; k < n; k++) {
-        std::vector<int32_t> suf(s.begin() + k, s.end());
-        insert_suffix(suf, k, n, pos_keys);
-    }
+    const int32_t sid = (int32_t)strs_.size();
+    strs_.push_back(std::move(s));
+    if (construction_ == ONLINE) insert_online(sid, types.size(), pos_keys);
+    else insert_naive(sid, types.size(), pos_keys);
     return q;
 }
 
-void OverlapTree::insert_suffix(const std::vector<int32_t> &suf, size_t start, size_t n,
-                                const std::vector<std::string> &pos_keys) {
-    int32_t node = 0;
-    size_t i = 0;
-    std::vector<int32_t> path;
-    for (;;) {
-        auto it = nodes_[node].children.find(suf[i]);
-        if (it == nodes_[node].children.end()) {
-            Node leaf;
-            leaf.parent = node;
-            leaf.label.assign(suf.begin() + i, suf.end());
-            leaf.depth = nodes_[node].depth + (int32_t)(suf.size() - i);
-            const int32_t id = (int32_t)nodes_.size();
-            nodes_.push_back(std::move(leaf));
-            nodes_[node].children[suf[i]] = id;
-            leaves_++;
-            path.push_back(id);
-            break;
+int32_t OverlapTree::new_leaf(int32_t parent, int32_t sid, int32_t lo) {
+    Node leaf;
+    leaf.parent = parent;
+    leaf.sid = sid;
+    leaf.lo = lo;
+    leaf.hi = (int32_t)strs_[sid].size();
+    leaf.depth = nodes_[parent].depth + (leaf.hi - lo);
+    const int32_t id = (int32_t)nodes_.size();
+    const int32_t first = strs_[sid][lo];
+    nodes_.push_back(std::move(leaf));
+    nodes_[parent].children[first] = id;
+    leaves_++;
+    return id;
+}
+
+int32_t OverlapTree::split(int32_t parent, int32_t child, size_t j) {
+    Node mid;
+    mid.parent = parent;
+    mid.sid = nodes_[child].sid;
+    mid.lo = nodes_[child].lo;
+    mid.hi = nodes_[child].lo + (int32_t)j;
+    mid.depth = nodes_[parent].depth + (int32_t)j;
+    mid.f = nodes_[child].f;
+    for (const auto &kv : nodes_[child].cidx) mid.cidx[restrict_key(kv.first, (size_t)mid.depth)].f += kv.second.f;
+    const int32_t mid_id = (int32_t)nodes_.size();
+    const int32_t first = sym(child, 0);
+    nodes_.push_back(std::move(mid));
+    Node &c = nodes_[child];
+    c.lo += (int32_t)j;
+    // a leaf that now hangs by its terminator alone: its string minus the terminator is
+    // the new node's string, so its cache bookkeeping moves up
+    if (c.hi - c.lo == 1 && strs_[c.sid][c.lo] < 0) {
+        for (auto &kv : c.cidx) {
+            OTEntry &m = nodes_[mid_id].cidx[kv.first];
+            m.cached = kv.second.cached;
+            m.c_ms = kv.second.c_ms;
+            m.c_ops = kv.second.c_ops;
+            m.nnz = kv.second.nnz;
+            kv.second.cached = false;
         }
-        const int32_t child = it->second;
-        const std::vector<int32_t> &lab = nodes_[child].label;
-        size_t j = 0;
-        while (j < lab.size() && i + j < suf.size() && lab[j] == suf[i + j]) j++;
-        if (j == lab.size()) {
-            node = child;
-            i += j;
-            path.push_back(child);
-            continue;
-        }
-        // split the edge into `child` after j symbols
-        Node mid;
-        mid.parent = node;
-        mid.label.assign(lab.begin(), lab.begin() + j);
-        mid.depth = nodes_[node].depth + (int32_t)j;
-        mid.f = nodes_[child].f;
-        for (const auto &kv : nodes_[child].cidx) mid.cidx[restrict_key(kv.first, (size_t)mid.depth)].f += kv.second.f;
-        const int32_t mid_id = (int32_t)nodes_.size();
-        nodes_.push_back(std::move(mid));
-        Node &c = nodes_[child];
-        std::vector<int32_t> rest(c.label.begin() + j, c.label.end());
-        // a leaf that now hangs by its terminator alone: its string minus the terminator
-        // is the new node's string, so its cache bookkeeping moves up
-        if (rest.size() == 1 && rest[0] < 0) {
-            for (auto &kv : c.cidx) {
-                OTEntry &m = nodes_[mid_id].cidx[kv.first];
-                m.cached = kv.second.cached;
-                m.c_ms = kv.second.c_ms;
-                m.c_ops = kv.second.c_ops;
-                m.nnz = kv.second.nnz;
-                kv.second.cached = false;
-            }
-        }
-        c.label = rest;
-        c.parent = mid_id;
-        nodes_[mid_id].children[rest[0]] = child;
-        nodes_[node].children[suf[i]] = mid_id;
-        Node leaf;
-        leaf.parent = mid_id;
-        leaf.label.assign(suf.begin() + i + j, suf.end());
-        leaf.depth = nodes_[mid_id].depth + (int32_t)(suf.size() - i - j);
-        const int32_t leaf_id = (int32_t)nodes_.size();
-        const int32_t first = leaf.label[0];
-        nodes_.push_back(std::move(leaf));
-        nodes_[mid_id].children[first] = leaf_id;
-        leaves_++;
-        path.push_back(mid_id);
-        path.push_back(leaf_id);
-        break;
     }
-    for (int32_t x : path) {
+    c.parent = mid_id;
+    nodes_[mid_id].children[strs_[c.sid][c.lo]] = child;
+    nodes_[parent].children[first] = mid_id;
+    return mid_id;
+}
+
+void OverlapTree::count_up(int32_t leaf, size_t start, size_t n, const std::vector<std::string> &pos_keys) {
+    for (int32_t x = leaf; x > 0; x = nodes_[x].parent) {
         Node &nd = nodes_[x];
         nd.f++;
         const size_t len = std::min((size_t)nd.depth, n - start);
         nd.cidx[window_key(pos_keys, start, len)].f++;
     }
+}
+
+// Sec. 3.3.2: each suffix (terminator included) walks from the root along the longest
+// matching path; a walk that stops inside an edge splits it; the rest becomes a new leaf.
+void OverlapTree::insert_naive(int32_t sid, size_t n, const std::vector<std::string> &pos_keys) {
+    const std::vector<int32_t> &s = strs_[sid];
+    const size_t m = s.size();
+    for (size_t k = 0; k < n; k++) {
+        int32_t node = 0;
+        size_t i = k;
+        int32_t leaf = -1;
+        for (;;) {
+            auto it = nodes_[node].children.find(s[i]);
+            if (it == nodes_[node].children.end()) {
+                leaf = new_leaf(node, sid, (int32_t)i);
+                break;
+            }
+            const int32_t child = it->second;
+            const size_t len = edge_len(child);
+            size_t j = 0;
+            while (j < len && i + j < m && sym(child, j) == s[i + j]) j++;
+            if (j == len) {
+                node = child;
+                i += j;
+                continue;
+            }
+            const int32_t mid = split(node, child, j);
+            leaf = new_leaf(mid, sid, (int32_t)(i + j));
+            break;
+        }
+        count_up(leaf, k, n, pos_keys);
+    }
+}
+
+// Ukkonen's on-line construction, continued over the tree of the earlier metapaths (a
+// generalised suffix tree: every earlier string ends with its own terminator, so all its
+// suffixes are leaves already). One phase per symbol i extends every pending suffix by
+// s[i]: the active point (node, edge, length) marks the longest pending suffix still
+// implicit; an extension either finds s[i] already there (the phase ends), or adds a leaf
+// at the active point, splitting an edge when the point is inside one; suffix links take
+// the active point from one pending suffix to the next without walking from the root.
+// Leaves of this metapath get their full label at once (they only ever grow to its end).
+// The terminator phase makes every suffix a leaf; the suffix made of the terminator alone
+// is not kept (the tree holds the metapath and its proper suffixes, Sec. 3.3.2).
+void OverlapTree::insert_online(int32_t sid, size_t n, const std::vector<std::string> &pos_keys) {
+    const std::vector<int32_t> &s = strs_[sid];
+    const size_t m = s.size();
+    std::vector<std::pair<int32_t, size_t>> made;  // (leaf, start of its suffix)
+    int32_t an = 0;   // active node
+    size_t ae = 0;    // active edge: index into s of its first symbol
+    size_t al = 0;    // active length
+    size_t rem = 0;   // suffixes still to be made explicit
+    for (size_t i = 0; i < m; i++) {
+        const int32_t c = s[i];
+        rem++;
+        int32_t need_link = -1;  // the internal node made last in this phase
+        while (rem > 0) {
+            if (al == 0) ae = i;
+            auto it = nodes_[an].children.find(s[ae]);
+            const size_t start = i + 1 - rem;
+            if (it == nodes_[an].children.end()) {
+                if (!(start == n && an == 0)) made.emplace_back(new_leaf(an, sid, (int32_t)i), start);
+                if (need_link >= 0) nodes_[need_link].link = an;
+                need_link = -1;
+            } else {
+                const int32_t nxt = it->second;
+                const size_t el = edge_len(nxt);
+                if (al >= el) {  // walk down to the next node
+                    ae += el;
+                    al -= el;
+                    an = nxt;
+                    continue;
+                }
+                if (sym(nxt, al) == c) {  // already there: this phase is done
+                    if (need_link >= 0) nodes_[need_link].link = an;
+                    al++;
+                    break;
+                }
+                const int32_t mid = split(an, nxt, al);
+                made.emplace_back(new_leaf(mid, sid, (int32_t)i), start);
+                if (need_link >= 0) nodes_[need_link].link = mid;
+                need_link = mid;
+            }
+            rem--;
+            if (an == 0 && al > 0) {
+                al--;
+                ae = i + 1 - rem;
+            } else if (an != 0) {
+                an = nodes_[an].link;
+            }
+        }
+    }
+    for (const auto &lk : made) count_up(lk.first, lk.second, n, pos_keys);
 }
 
 int32_t OverlapTree::locate(const int32_t *s, size_t n, bool *exact) const {
@@ -145,15 +219,15 @@ int32_t OverlapTree::locate(const int32_t *s, size_t n, bool *exact) const {
         auto it = nodes_[node].children.find(s[i]);
         if (it == nodes_[node].children.end()) return -1;
         const int32_t child = it->second;
-        const std::vector<int32_t> &lab = nodes_[child].label;
+        const size_t len = edge_len(child);
         size_t j = 0;
-        while (j < lab.size() && i + j < n) {
-            if (lab[j] != s[i + j]) return -1;
+        while (j < len && i + j < n) {
+            if (sym(child, j) != s[i + j]) return -1;
             j++;
         }
         i += j;
         if (i == n) {
-            *exact = j == lab.size();
+            *exact = j == len;
             return child;
         }
         node = child;
@@ -178,7 +252,7 @@ OTEntry *OverlapTree::entry(const int32_t *s, size_t n, const std::string &key) 
     const int32_t x = locate(s, n, &exact);
     if (x < 0) return nullptr;
     Node &nd = nodes_[x];
-    const bool leaf_match = nd.children.empty() && !nd.label.empty() && nd.label.back() < 0 &&
+    const bool leaf_match = nd.children.empty() && nd.hi > nd.lo && strs_[nd.sid][nd.hi - 1] < 0 &&
                             (size_t)nd.depth == n + 1;
     if (!(exact && (size_t)nd.depth == n) && !leaf_match) return nullptr;
     auto it = nd.cidx.find(key);
@@ -230,6 +304,28 @@ bool CachePolicy::in_subtree(const CacheItem &p, const CacheItem &e) {
     return restrict_key(e.key, p.types.size()) == p.key;
 }
 
+bool CachePolicy::evict_victim(CacheItem *out) {
+    if (items_.empty()) return false;
+    auto victim = items_.begin();
+    for (auto it = items_.begin(); it != items_.end(); ++it) {
+        const CacheItem &a = it->second, &b = victim->second;
+        const bool better = policy_ == LRU ? a.seq < b.seq : (a.h < b.h || (a.h == b.h && a.seq < b.seq));
+        if (better) victim = it;
+    }
+    CacheItem q = std::move(victim->second);
+    items_.erase(victim);
+    used_ -= q.s;
+    if (policy_ != LRU) L_ = q.h;
+    if (policy_ == ATRAPOS)
+        for (auto &kv : items_)
+            if (in_subtree(q, kv.second)) {
+                kv.second.c += q.c;
+                util(kv.second);
+            }
+    *out = std::move(q);
+    return true;
+}
+
 CacheItem *CachePolicy::find(const std::string &id) {
     auto it = items_.find(id);
     return it == items_.end() ? nullptr : &it->second;
@@ -261,22 +357,8 @@ CachePolicy::Outcome CachePolicy::request(const std::vector<int32_t> &types, con
     }
     if (s > max_fraction_ * capacity_) return REJECTED;
     while (used_ + s > capacity_ && !items_.empty()) {
-        auto victim = items_.begin();
-        for (auto it = items_.begin(); it != items_.end(); ++it) {
-            const CacheItem &a = it->second, &b = victim->second;
-            const bool better = policy_ == LRU ? a.seq < b.seq : (a.h < b.h || (a.h == b.h && a.seq < b.seq));
-            if (better) victim = it;
-        }
-        CacheItem q = std::move(victim->second);
-        items_.erase(victim);
-        used_ -= q.s;
-        if (policy_ != LRU) L_ = q.h;
-        if (policy_ == ATRAPOS)
-            for (auto &kv : items_)
-                if (in_subtree(q, kv.second)) {
-                    kv.second.c += q.c;
-                    util(kv.second);
-                }
+        CacheItem q;
+        evict_victim(&q);
         if (evicted) evicted->push_back(std::move(q));
     }
     CacheItem p;

@@ -24,11 +24,19 @@ struct OTEntry {
 };
 
 // Generalised suffix tree over metapaths; symbols are node type ids (>= 0), the
-// terminator of query q is -(q+1). Insertion is the naive suffix-by-suffix walk of
-// Sec. 3.3.2; every node on a walk counts one occurrence.
+// terminator of query q is -(q+1). Every node on the path from the root to a suffix's
+// leaf counts one occurrence of that suffix. Two constructions give the same tree:
+//   NAIVE   the suffix-by-suffix walk of Sec. 3.3.2 (each suffix from the root);
+//   ONLINE  Ukkonen's on-line construction (the faster approach the footnote of Sec.
+//           3.3.2 points to): one left-to-right pass over the metapath with an active
+//           point and suffix links, so the walks that reach known prefixes are skipped.
+// A tree keeps one construction for its life (the on-line one needs the suffix links of
+// every internal node, which the naive walk does not set).
 class OverlapTree {
   public:
-    OverlapTree();
+    enum Construction { NAIVE = 0, ONLINE = 1 };
+    explicit OverlapTree(int construction = NAIVE);
+    int construction() const { return construction_; }
     // Insert a metapath with one constraint description per position ("" = none).
     uint64_t insert(const std::vector<int32_t> &types, const std::vector<std::string> &pos_keys);
     // Occurrences of s among inserted metapaths; with key, only those whose
@@ -47,17 +55,27 @@ class OverlapTree {
   private:
     struct Node {
         int32_t parent = -1;
-        std::vector<int32_t> label;
+        int32_t sid = -1, lo = 0, hi = 0;  // edge label: strs_[sid][lo, hi)
+        int32_t link = 0;                  // suffix link (ONLINE; internal nodes)
         std::unordered_map<int32_t, int32_t> children;
         uint64_t f = 0;
         int32_t depth = 0;
         std::unordered_map<std::string, OTEntry> cidx;
     };
+    int construction_;
     std::vector<Node> nodes_;
+    std::vector<std::vector<int32_t>> strs_;  // every inserted metapath with its terminator
     size_t leaves_ = 0;
     uint64_t queries_ = 0;
-    void insert_suffix(const std::vector<int32_t> &suf, size_t start, size_t n,
-                       const std::vector<std::string> &pos_keys);
+    int32_t sym(int32_t x, size_t j) const { return strs_[nodes_[x].sid][nodes_[x].lo + j]; }
+    size_t edge_len(int32_t x) const { return (size_t)(nodes_[x].hi - nodes_[x].lo); }
+    int32_t new_leaf(int32_t parent, int32_t sid, int32_t lo);
+    // cut the edge into `child` after j symbols with a new node; returns it
+    int32_t split(int32_t parent, int32_t child, size_t j);
+    // one occurrence of the suffix starting at `start` on the leaf and every ancestor
+    void count_up(int32_t leaf, size_t start, size_t n, const std::vector<std::string> &pos_keys);
+    void insert_naive(int32_t sid, size_t n, const std::vector<std::string> &pos_keys);
+    void insert_online(int32_t sid, size_t n, const std::vector<std::string> &pos_keys);
     // node at or just below the end of s, and whether s ends exactly there; -1 if absent
     int32_t locate(const int32_t *s, size_t n, bool *exact) const;
 };
@@ -85,6 +103,9 @@ class CachePolicy {
     Outcome request(const std::vector<int32_t> &types, const std::string &key, double f, double c, double s,
                     std::shared_ptr<void> payload, std::vector<CacheItem> *evicted);
     CacheItem *find(const std::string &id);
+    // Evict the policy's victim (as a request that needs room would), into *out; false
+    // when the cache is empty. Used when queries need the bytes the cache holds.
+    bool evict_victim(CacheItem *out);
     static std::string make_id(const std::vector<int32_t> &types, const std::string &key);
     double used() const { return used_; }
     double capacity() const { return capacity_; }

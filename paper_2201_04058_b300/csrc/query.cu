@@ -35,11 +35,17 @@ void mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64
                         int64_t len, cudaStream_t s);
 }
 
-MatPtr mp_ctx::wrap(const Mat &m) {
+MatPtr mp_ctx::wrap(const Mat &m, bool charged) {
     auto p = std::make_shared<DevMat>();
     p->m = m;
     p->al = alloc.get();
     p->s = stream;
+    p->held = &held;
+    p->charged = (int64_t)m.bytes();
+    if (!charged) {
+        held.fetch_add(p->charged);
+        note_held();
+    }
     return p;
 }
 
@@ -186,27 +192,36 @@ double mp_ctx::htier_cost(const std::string &id) const {
 MatPtr mp_ctx::htier_load(const std::string &id) {
     auto it = htier.items.find(id);
     if (it == htier.items.end()) return nullptr;
-    HostEntry &e = it->second;
-    Mat m = e.shape;
+    it->second.seq = ++htier.seq;  // most recently used: the last the host tier would drop
+    const Mat shape = it->second.shape;
+    // the budget first (the cache may yield, and its evictions may store into the host tier)
+    if (reserve_bytes((int64_t)shape.bytes())) return nullptr;  // the budget cannot hold it: recompute
+    it = htier.items.find(id);
+    if (it == htier.items.end()) {
+        unreserve_bytes((int64_t)shape.bytes());
+        return nullptr;
+    }
+    const HostEntry &e = it->second;
+    Mat m = shape;
     const size_t brp = (size_t)(m.nrows + 1) * 8, bci = (size_t)m.nnz * 4, bval = (size_t)m.nnz * 8;
     m.rp = (int64_t *)alloc->alloc(brp, stream);
     m.ci = (int32_t *)alloc->alloc(std::max<size_t>(bci, 4), stream);
     m.val = (uint64_t *)alloc->alloc(std::max<size_t>(bval, 8), stream);
     if (!m.rp || !m.ci || !m.val) {
+        unreserve_bytes((int64_t)shape.bytes());
         free_mat(m);
         return nullptr;
     }
-    // ordered on the stream before every kernel that reads the result; the arena block
-    // stays put until the batch ends (stores and drops happen after the batch's waves)
+    // ordered on the stream before every kernel that reads the result; a later store that
+    // reuses this arena block copies into it on the same stream, after this copy
     const char *b = htier.arena + e.off;
     cudaMemcpyAsync(m.rp, b, brp, cudaMemcpyHostToDevice, stream);
     if (m.nnz) {
         cudaMemcpyAsync(m.ci, b + brp, bci, cudaMemcpyHostToDevice, stream);
         cudaMemcpyAsync(m.val, b + brp + bci, bval, cudaMemcpyHostToDevice, stream);
     }
-    e.seq = ++htier.seq;
     htier.loads++;
-    return wrap(m);
+    return wrap(m, true);
 }
 
 int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
@@ -261,28 +276,6 @@ void mp_ctx::free_masks(std::vector<uint32_t *> &masks) {
 
 namespace {
 
-// One sub-chain of some query's plan: factors i..j of query q (positions i..j+1).
-struct PNode {
-    std::string id;
-    std::vector<int32_t> types;
-    std::string key;
-    int q = -1, i = 0, j = 0, k = 0;  // registering query, its factor range and split
-    int left = -1, right = -1;  // child node indices; -1 = the base factor itself
-    int level = 0;
-    MatPtr res;
-    bool from_cache = false;
-    bool from_host = false;     // copied back from the host tier (offered to the cache again)
-    bool filter = false;        // length-2 query: diag(M_1) A diag(M_2)
-    int consumers = 0;
-    bool keep = false;          // a query's result or a cache candidate
-    int status = MP_OK;
-    double ms = 0.0;            // device time of this node's own product
-    double subtree_ms = 0.0;    // of every product this node's computation needed
-    double c_ops = 0.0;         // Eq. 2 with the product's actual counts
-    double rho_est = 0.0;       // planner density estimate (for batch-mates)
-    mp::Stats st;
-};
-
 std::string subchain_key(const Query &q, int i, int j) {
     return window_key(q.pos_keys, (size_t)i, (size_t)(j - i + 2));
 }
@@ -293,19 +286,79 @@ std::vector<int32_t> subchain_types(const Query &q, int i, int j) {
 
 }  // namespace
 
-int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
-    TraceRange batch_range("mp.batch");
-    const size_t nq = qs.size();
-    cudaEventRecord(ev0, stream);
-    std::vector<std::vector<uint32_t *>> masks(nq);
+mp_ctx::QState::~QState() {
+    if (ctx) ctx->free_masks(masks);
+}
+
+// ------------------------------------------------------------------ HBM byte budget
+
+bool mp_ctx::evict_one() {
+    if (!cache) return false;
+    CacheItem it;
+    if (!cache->evict_victim(&it)) return false;
+    cstats.evictions++;
+    OTEntry *ee = otree.entry(it.types.data(), it.types.size(), it.key);
+    if (ee) ee->cached = false;
+    htier_store(it.id, std::static_pointer_cast<DevMat>(it.payload), it.types, it.key, it.c, ee ? ee->c_ops : 0.0);
+    return true;
+}
+
+// Charge `bytes` of a result about to be made to the budget; cache entries are evicted
+// (the policy's victims first) while the budget cannot hold it. A budget of 0 is no limit.
+int mp_ctx::reserve_bytes(int64_t bytes) {
+    const int64_t budget = (int64_t)cfg.hbm_budget_bytes;
+    if (budget > 0) {
+        while (held.load() + bytes > budget && evict_one()) {
+        }
+        if (held.load() + bytes > budget) return MP_ERR_BUDGET;
+    }
+    held.fetch_add(bytes);
+    note_held();
+    return MP_OK;
+}
+
+void mp_ctx::unreserve_bytes(int64_t bytes) { held.fetch_sub(bytes); }
+
+namespace {
+// The budget as the wave executor sees it.
+struct CtxBudget final : mp::Budget {
+    mp_ctx *c;
+    explicit CtxBudget(mp_ctx *x) : c(x) {}
+    int reserve(int64_t bytes) override { return c->reserve_bytes(bytes); }
+    void unreserve(int64_t bytes) override { c->unreserve_bytes(bytes); }
+};
+}  // namespace
+
+// ------------------------------------------------------------------ the executor
+
+int mp_ctx::admit(std::vector<Query> &qs_in, const std::vector<uint64_t> &tickets,
+                  const std::vector<std::chrono::steady_clock::time_point> &t0s, std::vector<int64_t> &ids) {
+    const size_t nq = qs_in.size();
+    ids.assign(nq, -1);
+    std::vector<std::shared_ptr<QState>> st(nq);
     std::vector<int> qstatus(nq, MP_OK);
-    for (size_t q = 0; q < nq; q++) qstatus[q] = build_masks(qs[q], masks[q]);
-    // a batch-wide failure before the products run: every query reports it, nothing leaks
+    for (size_t q = 0; q < nq; q++) {
+        st[q] = std::make_shared<QState>();
+        st[q]->ctx = this;
+        st[q]->q = std::move(qs_in[q]);
+        qstatus[q] = build_masks(st[q]->q, st[q]->masks);
+    }
+    std::vector<Flight *> fl(nq);
+    for (size_t q = 0; q < nq; q++) {
+        const int64_t id = ex.next_flight++;
+        Flight &f = ex.flights[id];
+        f.id = id;
+        f.qs = st[q];
+        f.status = qstatus[q];
+        f.ticket = tickets[q];
+        f.t0 = t0s[q];
+        ids[q] = id;
+        fl[q] = &f;  // std::map: stable while other flights come and go
+    }
+    // a failure before the products join the DAG: every query of this admission reports it
     auto fail_all = [&](int rc) {
-        for (size_t q = 0; q < nq; q++) rs[q].status = qstatus[q] ? qstatus[q] : rc;
-        for (auto &m : masks) free_masks(m);
-        cudaEventRecord(ev1, stream);
-        cudaEventSynchronize(ev1);
+        for (size_t q = 0; q < nq; q++)
+            if (!fl[q]->status) fl[q]->status = rc;
         return rc;
     };
 
@@ -314,7 +367,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     std::vector<std::vector<double>> leaf(nq);
     {
         size_t total = 0;
-        for (auto &q : qs) total += q.rels.size();
+        for (auto &x : st) total += x->q.rels.size();
         unsigned long long *d = (unsigned long long *)alloc->alloc(std::max<size_t>(total, 1) * 8, stream);
         if (!d) return fail_all(MP_ERR_NOMEM);
         cudaMemsetAsync(d, 0, std::max<size_t>(total, 1) * 8, stream);
@@ -328,13 +381,13 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         size_t off = 0;
         bool any = false;
         for (size_t q = 0; q < nq; q++) {
-            const int p = (int)qs[q].rels.size();
+            const int p = (int)st[q]->q.rels.size();
             leaf[q].assign(p, -1.0);
             for (int t = 0; t < p; t++) {
-                const Mat &A = rels[qs[q].rels[t]].dev;
-                if (qstatus[q] || !(masks[q][t] || masks[q][t + 1])) continue;
+                const Mat &A = rels[st[q]->q.rels[t]].dev;
+                if (qstatus[q] || !(st[q]->masks[t] || st[q]->masks[t + 1])) continue;
                 std::string &key = keys[off + t];
-                key = std::to_string(qs[q].rels[t]) + "|" + qs[q].pos_keys[t] + "|" + qs[q].pos_keys[t + 1];
+                key = std::to_string(st[q]->q.rels[t]) + "|" + st[q]->q.pos_keys[t] + "|" + st[q]->q.pos_keys[t + 1];
                 auto m = leaf_memo.find(key);
                 if (m != leaf_memo.end()) {
                     leaf[q][t] = m->second;
@@ -348,7 +401,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                     return fail_all(MP_ERR_NOMEM);
                 }
                 cudaMemsetAsync(lr + A.nrows, 0, 4, stream);
-                masked_nnz(A.view(), masks[q][t], masks[q][t + 1], d + off + t, lr, lr + A.nrows, stream);
+                masked_nnz(A.view(), st[q]->masks[t], st[q]->masks[t + 1], d + off + t, lr, lr + A.nrows, stream);
                 tmp.push_back(lr);
                 any = true;
             }
@@ -367,12 +420,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         for (auto &kv : first) leaf_memo[kv.first] = (double)h[kv.second];
         off = 0;
         for (size_t q = 0; q < nq; q++) {
-            for (size_t t = 0; t < qs[q].rels.size(); t++) {
+            for (size_t t = 0; t < st[q]->q.rels.size(); t++) {
                 if (leaf[q][t] >= 0) continue;
                 const std::string &key = keys[off + t];
-                leaf[q][t] = key.empty() ? (double)rels[qs[q].rels[t]].dev.nnz : leaf_memo[key];
+                leaf[q][t] = key.empty() ? (double)rels[st[q]->q.rels[t]].dev.nnz : leaf_memo[key];
             }
-            off += qs[q].rels.size();
+            off += st[q]->q.rels.size();
         }
     }
 
@@ -384,10 +437,10 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         std::vector<Pair> pairs;
         for (size_t q = 0; q < nq; q++)
             if (!qstatus[q])
-                for (int t = 0; t + 1 < (int)qs[q].rels.size(); t++) pairs.push_back({q, t});
+                for (int t = 0; t + 1 < (int)st[q]->q.rels.size(); t++) pairs.push_back({q, t});
         sampled.assign(nq, std::vector<double>());
         for (size_t q = 0; q < nq; q++) {
-            const size_t p = qs[q].rels.size();
+            const size_t p = st[q]->q.rels.size();
             sampled[q].assign(p * p, NAN);
         }
         if (!pairs.empty()) {
@@ -396,8 +449,8 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             if (!d) return fail_all(MP_ERR_NOMEM);
             cudaMemsetAsync(d, 0, np * 16, stream);  // [active rows, sampled rows] per pair
             for (size_t k = 0; k < np; k++) {
-                const Query &Q = qs[pairs[k].q];
-                active_rows(rels[Q.rels[pairs[k].t]].dev.view(), masks[pairs[k].q][pairs[k].t], d + 2 * k, stream);
+                const Query &Q = st[pairs[k].q]->q;
+                active_rows(rels[Q.rels[pairs[k].t]].dev.view(), st[pairs[k].q]->masks[pairs[k].t], d + 2 * k, stream);
             }
             std::vector<unsigned long long> h(2 * np);
             cudaMemcpyAsync(h.data(), d, np * 16, cudaMemcpyDeviceToHost, stream);
@@ -409,7 +462,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             std::vector<WaveIn> win(np);
             const double s_rows = (double)std::max<uint32_t>(cfg.sample_rows, 1);
             for (size_t k = 0; k < np; k++) {
-                const Query &Q = qs[pairs[k].q];
+                const Query &Q = st[pairs[k].q]->q;
                 const int t = pairs[k].t;
                 const Mat &A = rels[Q.rels[t]].dev;
                 const double act = (double)h[2 * k];
@@ -422,12 +475,12 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                     return fail_all(MP_ERR_NOMEM);
                 }
                 const uint64_t seed = cfg.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(k + 1));
-                sample_rows(A.view(), masks[pairs[k].q][t], seed, thr, bms[k], d + 2 * k + 1, stream);
+                sample_rows(A.view(), st[pairs[k].q]->masks[t], seed, thr, bms[k], d + 2 * k + 1, stream);
                 win[k].X = A.view();
                 win[k].Y = rels[Q.rels[t + 1]].dev.view();
                 win[k].rm = bms[k];
-                win[k].km = masks[pairs[k].q][t + 1];
-                win[k].cm = masks[pairs[k].q][t + 2];
+                win[k].km = st[pairs[k].q]->masks[t + 1];
+                win[k].cm = st[pairs[k].q]->masks[t + 2];
             }
             std::vector<WaveOut> wout;
             int rc = spgemm_wave(win, *alloc, tun, stream, 0, wout, nullptr, true, &wcache);
@@ -437,7 +490,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             alloc->free(d, stream);
             if (rc) return fail_all(rc);
             for (size_t k = 0; k < np; k++) {
-                const Query &Q = qs[pairs[k].q];
+                const Query &Q = st[pairs[k].q]->q;
                 const int t = pairs[k].t;
                 const size_t p = Q.rels.size();
                 const double act = (double)h[2 * k], smp = (double)h[2 * k + 1];
@@ -458,7 +511,7 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         std::map<std::pair<int, int>, int> pidx;
         for (size_t q = 0; q < nq; q++) {
             if (qstatus[q]) continue;
-            const Query &Q = qs[q];
+            const Query &Q = st[q]->q;
             const int p = (int)Q.rels.size();
             mleaf[q].assign(p, -1);
             mpair[q].assign(p, -1);
@@ -467,8 +520,8 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                     std::to_string(Q.rels[t]) + "|" + Q.pos_keys[t] + "|" + Q.pos_keys[t + 1];
                 auto it = lidx.find(key);
                 if (it == lidx.end()) {
-                    MncLeafIn in{rels[Q.rels[t]].dev.view(), rels[Q.rels[t] ^ 1].dev.view(), masks[q][t],
-                                 masks[q][t + 1]};
+                    MncLeafIn in{rels[Q.rels[t]].dev.view(), rels[Q.rels[t] ^ 1].dev.view(), st[q]->masks[t],
+                                 st[q]->masks[t + 1]};
                     auto mm = mnc_memo.find(key);
                     MncSketchPtr known;
                     if (mm != mnc_memo.end()) {
@@ -509,17 +562,17 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
     // Overlap Tree: every query's metapath and suffixes (Sec. 3.3.2)
     if (cache && !explain.on)
         for (size_t q = 0; q < nq; q++)
-            if (!qstatus[q]) otree.insert(qs[q].types, qs[q].pos_keys);
+            if (!qstatus[q]) otree.insert(st[q]->q.types, st[q]->q.pos_keys);
 
-    // plans and the product DAG
+    // plans, and the queries' products joined to the DAG: a sub-chain whose result is on
+    // its way or held (in flight for an earlier query) becomes a shared node
     std::unique_ptr<TraceRange> plan_range(new TraceRange("mp.plan"));
-    std::vector<PNode> nodes;
-    std::unordered_map<std::string, int> by_id;
     std::unordered_set<std::string> host_known;  // sub-chains planned as copies from the host tier
-    std::vector<int> root(nq, -1);
     for (size_t q = 0; q < nq; q++) {
         if (qstatus[q]) continue;
-        const Query &Q = qs[q];
+        const Query &Q = st[q]->q;
+        Flight &F = *fl[q];
+        const int64_t fid = ids[q];
         const int n = (int)Q.types.size(), p = n - 1;
         std::vector<double> dims(n);
         for (int t = 0; t < n; t++) dims[t] = (double)types[Q.types[t]].count;
@@ -531,17 +584,20 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         }
         if (p == 1) {
             PNode nd;
-            nd.id = "filter#" + std::to_string(q);
-            nd.q = (int)q;
+            nd.id = "filter#" + std::to_string(fid);
+            nd.flight = fid;
+            nd.qs = st[q];
             nd.filter = true;
-            nd.level = 1;
-            nd.keep = true;
-            root[q] = (int)nodes.size();
-            nodes.push_back(std::move(nd));
+            nd.keepers = 1;
+            F.keeps.push_back(ex.next_node);
+            F.est_bytes = (dims[0] + 1) * 8.0 + 12.0 * (leaf[q][0] >= 0 ? leaf[q][0] : (double)rels[Q.rels[0]].dev.nnz);
+            const int64_t nid = ex.next_node++;
+            ex.nodes.emplace(nid, std::move(nd));
+            F.root = nid;
+            ex.est_bytes += F.est_bytes;
             continue;
         }
-        // sub-chains already known: in the cache, computed earlier in this batch, or
-        // evicted with a recorded cost
+        // sub-chains already known: in the cache, in flight, or evicted with a recorded cost
         std::vector<double> kc((size_t)p * p, NAN), kr((size_t)p * p, NAN);
         for (int i = 0; i < p; i++)
             for (int j = i + 1; j < p; j++) {
@@ -549,10 +605,14 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 const std::string key = subchain_key(Q, i, j);
                 const std::string id = CachePolicy::make_id(ty, key);
                 const double cells = dims[i] * dims[j + 1];
-                auto it = by_id.find(id);
-                if (it != by_id.end()) {
+                auto it = ex.by_id.find(id);
+                if (it != ex.by_id.end() && node(it->second).status) {  // failed: compute anew
+                    ex.by_id.erase(it);
+                    it = ex.by_id.end();
+                }
+                if (it != ex.by_id.end()) {
                     kc[(size_t)i * p + j] = 0.0;
-                    kr[(size_t)i * p + j] = nodes[it->second].rho_est;
+                    kr[(size_t)i * p + j] = node(it->second).rho_est;
                     continue;
                 }
                 if (cache) {
@@ -581,6 +641,10 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
         if (cfg.planner == MP_PLAN_LEFT_TO_RIGHT) {
             for (int i = 0; i < p; i++)
                 for (int j = i + 1; j < p; j++) split[(size_t)i * p + j] = split_pure[(size_t)i * p + j] = j - 1;
+            // sizes for the byte estimate: E_ac densities
+            std::vector<int> tmp((size_t)p * p);
+            plan_chain(p, dims.data(), leaf[q].data(), cfg.alpha, cfg.beta, cfg.gamma, nullptr, nullptr, nullptr,
+                       tmp.data(), nullptr, D.data());
         } else if (cfg.planner == MP_PLAN_DP_MNC) {
             // the plan with the known sub-chains and the plan of every sub-chain on its
             // own, level by level; each level's log-sums in one launch
@@ -631,21 +695,28 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
             return fail_all(MP_OK);
         }
         // register nodes bottom-up
-        std::function<int(int, int)> reg = [&](int i, int j) -> int {
+        std::function<int64_t(int, int)> reg = [&](int i, int j) -> int64_t {
             if (i == j) return -1;
             const std::vector<int32_t> ty = subchain_types(Q, i, j);
             const std::string key = subchain_key(Q, i, j);
             const std::string id = CachePolicy::make_id(ty, key);
-            auto it = by_id.find(id);
-            if (it != by_id.end()) {
-                nodes[it->second].consumers++;
+            auto it = ex.by_id.find(id);
+            if (it != ex.by_id.end() && node(it->second).status) {
+                ex.by_id.erase(it);
+                it = ex.by_id.end();
+            }
+            if (it != ex.by_id.end()) {
+                PNode &x = node(it->second);
+                x.consumers++;
+                if (x.from_cache) F.r.cache_hits++;
                 return it->second;
             }
             PNode nd;
             nd.id = id;
             nd.types = ty;
             nd.key = key;
-            nd.q = (int)q;
+            nd.flight = fid;
+            nd.qs = st[q];
             nd.i = i;
             nd.j = j;
             nd.consumers = 1;
@@ -655,15 +726,16 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 if (ci) {
                     nd.res = std::static_pointer_cast<DevMat>(ci->payload);
                     nd.from_cache = true;
-                    nd.level = 0;
+                    nd.done = true;
                     cstats.requests++;
                     cstats.hits++;
+                    F.r.cache_hits++;
                     cache->request(ty, key, (double)otree.frequency(ty.data(), ty.size(), &key), ci->c, ci->s,
                                    nullptr, nullptr);
-                    const int idx = (int)nodes.size();
-                    nodes.push_back(std::move(nd));
-                    by_id.emplace(id, idx);
-                    return idx;
+                    const int64_t nid = ex.next_node++;
+                    ex.nodes.emplace(nid, std::move(nd));
+                    ex.by_id.emplace(id, nid);
+                    return nid;
                 }
             }
             int k = split[(size_t)i * p + j];
@@ -674,221 +746,334 @@ int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
                 if (hm) {
                     nd.res = hm;
                     nd.from_cache = nd.from_host = true;
-                    nd.level = 0;
+                    nd.done = true;
                     nd.subtree_ms = c_ms;
                     nd.c_ops = c_ops;
-                    const int idx = (int)nodes.size();
-                    nodes.push_back(std::move(nd));
-                    by_id.emplace(id, idx);
-                    return idx;
+                    F.r.cache_hits++;
+                    const int64_t nid = ex.next_node++;
+                    ex.nodes.emplace(nid, std::move(nd));
+                    ex.by_id.emplace(id, nid);
+                    return nid;
                 }
             }
             if (k < 0) k = split_pure[(size_t)i * p + j];  // known (evicted) but not at hand: compute it
             nd.k = k;
-            const int l = reg(i, k);
-            const int r = reg(k + 1, j);
-            nd.left = l;
-            nd.right = r;
-            nd.level = 1 + std::max(l >= 0 ? nodes[l].level : 0, r >= 0 ? nodes[r].level : 0);
-            const int idx = (int)nodes.size();
-            nodes.push_back(std::move(nd));
-            by_id.emplace(id, idx);
-            return idx;
+            nd.left = reg(i, k);
+            nd.right = reg(k + 1, j);
+            // planned bytes of the result: row pointers and the estimated entries
+            F.est_bytes += (dims[i] + 1) * 8.0 + 12.0 * D[(size_t)i * p + j] * dims[i] * dims[j + 1];
+            const int64_t nid = ex.next_node++;
+            ex.nodes.emplace(nid, std::move(nd));
+            ex.by_id.emplace(id, nid);
+            return nid;
         };
-        root[q] = reg(0, p - 1);
-        nodes[root[q]].keep = true;
+        F.root = reg(0, p - 1);
+        {
+            PNode &rt = node(F.root);
+            rt.consumers--;  // no parent reads a query's result: its flight keeps it
+            rt.keepers++;
+            F.keeps.push_back(F.root);
+        }
+        ex.est_bytes += F.est_bytes;
     }
-
     plan_range.reset();
     // cache candidates: the longest computed sub-metapath of each query seen at least twice
-    // (MP_INSERT_OTREE), none (MP_INSERT_FINAL), or every computed node (MP_INSERT_ALL)
-    std::vector<int> candidate(nq, -1);
-    if (cache && cfg.insertion == MP_INSERT_ALL)
-        for (auto &nd : nodes)
-            if (!nd.from_cache && !nd.filter) nd.keep = true;
-    if (cache && cfg.insertion == MP_INSERT_OTREE) {
-        for (size_t q = 0; q < nq; q++) {
-            if (root[q] < 0) continue;
-            int best = -1;
-            std::function<void(int)> walk = [&](int x) {
+    // (MP_INSERT_OTREE), none (MP_INSERT_FINAL), or every node the query computes
+    // (MP_INSERT_ALL); each is kept until its query finishes and offers it
+    for (size_t q = 0; q < nq; q++) {
+        Flight &F = *fl[q];
+        if (!cache || F.root < 0 || node(F.root).filter) continue;
+        if (cfg.insertion == MP_INSERT_OTREE) {
+            int64_t best = -1;
+            // the query's own products: a node already done (computed for a query admitted
+            // earlier) ends the walk, as its operands may be gone
+            std::function<void(int64_t)> walk = [&](int64_t x) {
                 if (x < 0) return;
-                const PNode &nd = nodes[x];
-                if (x != root[q] && !nd.from_cache && !nd.filter) {
+                const PNode &nd = node(x);
+                if (x != F.root && !nd.from_cache && !nd.filter) {
                     const uint64_t f = otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
-                    if (f >= 2 && (best < 0 || nd.types.size() > nodes[best].types.size())) best = x;
+                    if (f >= 2 && (best < 0 || nd.types.size() > node(best).types.size())) best = x;
                 }
+                if (nd.done) return;
                 walk(nd.left);
                 walk(nd.right);
             };
-            walk(root[q]);
-            candidate[q] = best;
-            if (best >= 0) nodes[best].keep = true;
+            walk(F.root);
+            F.candidate = best;
+            if (best >= 0) {
+                node(best).keepers++;
+                F.keeps.push_back(best);
+            }
+        } else if (cfg.insertion == MP_INSERT_ALL) {
+            for (auto &kv : ex.nodes)
+                if (kv.second.flight == ids[q] && !kv.second.from_cache && kv.first != F.root) {
+                    kv.second.keepers++;
+                    F.keeps.push_back(kv.first);
+                }
+            std::sort(F.keeps.begin() + 1, F.keeps.end());
         }
     }
+    return MP_OK;
+}
 
-    // run the DAG level by level; every product of a level runs in one wave
-    int max_level = 0;
-    for (auto &nd : nodes) max_level = std::max(max_level, nd.level);
-    auto release_operands = [&](PNode &nd) {
-        for (int c : {nd.left, nd.right}) {
+// A wave failed as a whole (a CUDA error, device memory exhausted): every product not run
+// yet carries its error, and nothing is left waiting for them.
+void mp_ctx::abort_nodes(int rc) {
+    for (auto &kv : ex.nodes)
+        if (!kv.second.done) {
+            kv.second.status = rc;
+            kv.second.done = true;
+        }
+    std::vector<int64_t> ids;
+    for (auto &kv : ex.nodes) {
+        kv.second.consumers = 0;  // every parent is done now
+        ids.push_back(kv.first);
+    }
+    for (int64_t id : ids) release_node(id);
+}
+
+void mp_ctx::release_node(int64_t id) {
+    auto it = ex.nodes.find(id);
+    if (it == ex.nodes.end()) return;
+    PNode &nd = it->second;
+    if (!nd.done || nd.consumers > 0 || nd.keepers > 0) return;
+    auto b = ex.by_id.find(nd.id);
+    if (b != ex.by_id.end() && b->second == id) ex.by_id.erase(b);
+    ex.nodes.erase(it);
+}
+
+int mp_ctx::run_wave() {
+    std::vector<int64_t> ready;
+    for (auto &kv : ex.nodes) {
+        const PNode &nd = kv.second;
+        if (nd.done) continue;
+        if (nd.left >= 0 && !node(nd.left).done) continue;
+        if (nd.right >= 0 && !node(nd.right).done) continue;
+        ready.push_back(kv.first);
+    }
+    if (ready.empty()) return MP_OK;
+    std::sort(ready.begin(), ready.end());  // registration order: waves are reproducible
+    TraceRange wave_range("mp.wave");
+    auto finish_node = [&](int64_t id) {
+        PNode &nd = node(id);
+        nd.done = true;
+        auto fit = ex.flights.find(nd.flight);
+        if (fit != ex.flights.end() && !nd.from_cache) {
+            Result &r = fit->second.r;
+            r.st.products += nd.st.products;
+            r.st.nnz += nd.st.nnz;
+            for (int b = 0; b < NBINS; b++) {
+                r.st.sym_bins[b] += nd.st.sym_bins[b];
+                r.st.num_bins[b] += nd.st.num_bins[b];
+            }
+            r.n_products += nd.filter ? 0 : 1;
+            r.ms += nd.ms;
+        }
+        for (int64_t c : {nd.left, nd.right}) {
             if (c < 0) continue;
-            if (--nodes[c].consumers <= 0 && !nodes[c].keep) nodes[c].res.reset();
+            node(c).consumers--;
+            release_node(c);
+        }
+        release_node(id);  // a node whose query gave up on it meanwhile
+    };
+    CtxBudget bud(this);
+    std::vector<int64_t> members;
+    std::vector<WaveIn> win;
+    for (int64_t id : ready) {
+        PNode &nd = node(id);
+        const Query &Q = nd.qs->q;
+        const auto &M = nd.qs->masks;
+        if (nd.filter) {
+            auto t0 = std::chrono::steady_clock::now();
+            Mat C;
+            nd.status = filter(rels[Q.rels[0]].dev.view(), M[0], M[1], *alloc, tun, stream, &C);
+            nd.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            nd.subtree_ms = nd.ms;
+            if (!nd.status && reserve_bytes((int64_t)C.bytes())) nd.status = MP_ERR_BUDGET;
+            if (!nd.status) nd.res = wrap(C, true);
+            else free_mat(C);
+            finish_node(id);
+            continue;
+        }
+        const int ls = nd.left >= 0 ? node(nd.left).status : MP_OK;
+        const int rs = nd.right >= 0 ? node(nd.right).status : MP_OK;
+        if (ls || rs) {
+            nd.status = ls ? ls : rs;
+            finish_node(id);
+            continue;
+        }
+        const int i = nd.i, j = nd.j, k = nd.k;
+        WaveIn in;
+        in.X = nd.left >= 0 ? node(nd.left).res->m.view() : rels[Q.rels[i]].dev.view();
+        in.Y = nd.right >= 0 ? node(nd.right).res->m.view() : rels[Q.rels[j]].dev.view();
+        in.ymax = nd.right >= 0 ? node(nd.right).res->m.vmax : 1;
+        // a base factor enters with the masks of its end positions; a node's result
+        // already carries them (0/1 diagonals are idempotent)
+        in.rm = nd.left < 0 ? M[i] : nullptr;
+        in.km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
+        in.cm = nd.right < 0 ? M[j + 1] : nullptr;
+        members.push_back(id);
+        win.push_back(in);
+    }
+    if (members.empty()) return MP_OK;
+    std::vector<WaveOut> wout;
+    auto t0 = std::chrono::steady_clock::now();
+    const int wave_rc =
+        spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof, false, &wcache, &bud);
+    const double wave_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    double wave_prod = 0.0;
+    for (auto &o : wout) wave_prod += (double)o.products;
+    for (size_t t = 0; t < members.size(); t++) {
+        PNode &nd = node(members[t]);
+        if (wave_rc) {
+            nd.status = wave_rc;
+            finish_node(members[t]);
+            continue;
+        }
+        WaveOut &o = wout[t];
+        nd.status = o.status;
+        nd.st.products = o.products;
+        nd.st.nnz = (uint64_t)o.m.nnz;
+        for (int b = 0; b < NBINS; b++) {
+            nd.st.sym_bins[b] = o.sym_bins[b];
+            nd.st.num_bins[b] = o.num_bins[b];
+        }
+        // the wave's time, shared in proportion to the products each member ran
+        nd.ms = wave_prod > 0 ? wave_ms * (double)o.products / wave_prod : wave_ms / (double)members.size();
+        const PNode *L = nd.left >= 0 ? &node(nd.left) : nullptr;
+        const PNode *R = nd.right >= 0 ? &node(nd.right) : nullptr;
+        nd.subtree_ms = nd.ms + (L && !L->from_cache ? L->subtree_ms : 0.0) + (R && !R->from_cache ? R->subtree_ms : 0.0);
+        if (!o.status) {
+            // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
+            const double nnz_x = (double)(L ? L->res->m.nnz : rels[nd.qs->q.rels[nd.i]].dev.nnz);
+            nd.c_ops = cfg.alpha * nnz_x + cfg.beta * (double)o.products + cfg.gamma * (double)o.m.nnz;
+            if (collect_fit) fit_samples.push_back({nnz_x, (double)o.products, (double)o.m.nnz, nd.ms});
+            nd.res = wrap(o.m, true);  // its bytes were charged before its arrays were made
+        }
+        finish_node(members[t]);
+    }
+    return wave_rc;
+}
+
+void mp_ctx::finish_flights(std::vector<Flight> &done) {
+    std::vector<int64_t> fin;
+    for (auto &kv : ex.flights) {
+        const Flight &F = kv.second;
+        if (F.status || F.root < 0 || node(F.root).done) fin.push_back(kv.first);
+    }
+    if (fin.empty()) return;
+    std::unique_ptr<TraceRange> offer_range(cache ? new TraceRange("mp.cache_offers") : nullptr);
+    // Sec. 3.4.1: the query's result and its cache candidate are offered to the replacement
+    // policy (Alg. 1)
+    auto offer = [&](PNode &nd) {
+        if ((nd.from_cache && !nd.from_host) || nd.filter || nd.status || !nd.res) return;
+        const double f = (double)otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
+        std::vector<CacheItem> ev;
+        cstats.requests++;
+        auto out = cache->request(nd.types, nd.key, f, nd.subtree_ms, (double)nd.res->m.bytes(),
+                                  std::static_pointer_cast<void>(nd.res), &ev);
+        if (out == CachePolicy::INSERTED) cstats.inserts++;
+        if (out == CachePolicy::REJECTED) cstats.rejected++;
+        if (out == CachePolicy::HIT) cstats.hits++;
+        cstats.evictions += ev.size();
+        OTEntry *e = otree.entry(nd.types.data(), nd.types.size(), nd.key);
+        if (e) {
+            e->cached = out != CachePolicy::REJECTED;
+            e->c_ms = nd.subtree_ms;
+            e->c_ops = nd.c_ops;
+            e->nnz = (double)nd.res->m.nnz;
+        }
+        for (auto &it : ev) {
+            OTEntry *ee = otree.entry(it.types.data(), it.types.size(), it.key);
+            if (ee) ee->cached = false;
+            htier_store(it.id, std::static_pointer_cast<DevMat>(it.payload), it.types, it.key, it.c,
+                        ee ? ee->c_ops : 0.0);
         }
     };
-    int wave_rc = MP_OK;
-    for (int lvl = 1; lvl <= max_level && wave_rc == MP_OK; lvl++) {
-        char wave_name[32];
-        snprintf(wave_name, sizeof(wave_name), "mp.wave level %d", lvl);
-        TraceRange wave_range(wave_name);
-        std::vector<int> members;
-        std::vector<WaveIn> win;
-        for (size_t x = 0; x < nodes.size(); x++) {
-            PNode &nd = nodes[x];
-            if (nd.level != lvl || nd.res) continue;
-            const Query &Q = qs[nd.q];
-            const auto &M = masks[nd.q];
-            if (nd.filter) {
-                auto t0 = std::chrono::steady_clock::now();
-                Mat C;
-                nd.status = filter(rels[Q.rels[0]].dev.view(), M[0], M[1], *alloc, tun, stream, &C);
-                nd.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-                nd.subtree_ms = nd.ms;
-                if (!nd.status) nd.res = wrap(C);
-                else free_mat(C);
-                continue;
-            }
-            if (nd.left >= 0 && nodes[nd.left].status) {
-                nd.status = nodes[nd.left].status;
-                release_operands(nd);
-                continue;
-            }
-            if (nd.right >= 0 && nodes[nd.right].status) {
-                nd.status = nodes[nd.right].status;
-                release_operands(nd);
-                continue;
-            }
-            const int i = nd.i, j = nd.j, k = nd.k;
-            WaveIn in;
-            in.X = nd.left >= 0 ? nodes[nd.left].res->m.view() : rels[Q.rels[i]].dev.view();
-            in.Y = nd.right >= 0 ? nodes[nd.right].res->m.view() : rels[Q.rels[j]].dev.view();
-            in.ymax = nd.right >= 0 ? nodes[nd.right].res->m.vmax : 1;
-            // a base factor enters with the masks of its end positions; a node's result
-            // already carries them (0/1 diagonals are idempotent)
-            in.rm = nd.left < 0 ? M[i] : nullptr;
-            in.km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
-            in.cm = nd.right < 0 ? M[j + 1] : nullptr;
-            members.push_back((int)x);
-            win.push_back(in);
-        }
-        if (members.empty()) continue;
-        std::vector<WaveOut> wout;
-        auto t0 = std::chrono::steady_clock::now();
-        wave_rc = spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof, false, &wcache);
-        const double wave_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        double wave_prod = 0.0;
-        for (auto &o : wout) wave_prod += (double)o.products;
-        for (size_t t = 0; t < members.size(); t++) {
-            PNode &nd = nodes[members[t]];
-            if (wave_rc) {
-                nd.status = wave_rc;
-                release_operands(nd);
-                continue;
-            }
-            WaveOut &o = wout[t];
-            nd.status = o.status;
-            nd.st.products = o.products;
-            nd.st.nnz = (uint64_t)o.m.nnz;
-            for (int b = 0; b < NBINS; b++) {
-                nd.st.sym_bins[b] = o.sym_bins[b];
-                nd.st.num_bins[b] = o.num_bins[b];
-            }
-            // the wave's time, shared in proportion to the products each member ran
-            nd.ms = wave_prod > 0 ? wave_ms * (double)o.products / wave_prod : wave_ms / (double)members.size();
-            nd.subtree_ms = nd.ms + (nd.left >= 0 && !nodes[nd.left].from_cache ? nodes[nd.left].subtree_ms : 0.0) +
-                            (nd.right >= 0 && !nodes[nd.right].from_cache ? nodes[nd.right].subtree_ms : 0.0);
-            if (!o.status) {
-                // Eq. 2 with the actual counts: alpha nnz(X) + beta N_op + gamma nnz(Z)
-                const double nnz_x = (double)(nd.left >= 0 ? nodes[nd.left].res->m.nnz : rels[qs[nd.q].rels[nd.i]].dev.nnz);
-                nd.c_ops = cfg.alpha * nnz_x + cfg.beta * (double)o.products + cfg.gamma * (double)o.m.nnz;
-                if (collect_fit) fit_samples.push_back({nnz_x, (double)o.products, (double)o.m.nnz, nd.ms});
-                nd.res = wrap(o.m);
-            }
-            release_operands(nd);
-        }
-    }
-
-    // nodes a failed wave never reached carry its error
-    for (auto &nd : nodes)
-        if (!nd.res && !nd.status) nd.status = wave_rc ? wave_rc : MP_ERR_INTERNAL;
-
-    // results, statistics, cache insertion (Sec. 3.4.1) under the replacement policy
-    int first = MP_OK;
-    for (size_t q = 0; q < nq; q++) {
-        Result &r = rs[q];
-        if (qstatus[q]) {
-            r.status = qstatus[q];
+    for (int64_t fid : fin) {
+        Flight &F = ex.flights[fid];
+        Result &r = F.r;
+        if (F.status) {
+            r.status = F.status;
         } else {
-            PNode &rt = nodes[root[q]];
+            PNode &rt = node(F.root);
             r.status = rt.status;
             if (!rt.status) r.m = rt.res;
-            std::function<void(int)> acc = [&](int x) {
-                if (x < 0) return;
-                const PNode &nd = nodes[x];
-                if (nd.q == (int)q && !nd.from_cache) {
-                    r.st.products += nd.st.products;
-                    r.st.nnz += nd.st.nnz;
-                    for (int b = 0; b < NBINS; b++) {
-                        r.st.sym_bins[b] += nd.st.sym_bins[b];
-                        r.st.num_bins[b] += nd.st.num_bins[b];
-                    }
-                    r.n_products += nd.filter ? 0 : 1;
-                }
-                if (nd.from_cache) r.cache_hits++;
-                acc(nd.left);
-                acc(nd.right);
-            };
-            acc(root[q]);
+            // the result first, then the candidate (or, with MP_INSERT_ALL, every node
+            // the query computed, in registration order)
+            if (cache)
+                for (int64_t x : F.keeps) offer(node(x));
         }
-        if (r.status && first == MP_OK) first = r.status;
+        for (int64_t x : F.keeps) {
+            node(x).keepers--;
+            release_node(x);
+        }
+        ex.est_bytes -= F.est_bytes;
+        F.finished = true;
+        done.push_back(std::move(F));
+        ex.flights.erase(fid);
     }
-    if (cache) {
-        TraceRange offer_range("mp.cache_offers");
-        auto offer = [&](PNode &nd) {
-            if ((nd.from_cache && !nd.from_host) || nd.filter || nd.status || !nd.res) return;
-            const double f = (double)otree.frequency(nd.types.data(), nd.types.size(), &nd.key);
-            std::vector<CacheItem> ev;
-            cstats.requests++;
-            auto out = cache->request(nd.types, nd.key, f, nd.subtree_ms, (double)nd.res->m.bytes(),
-                                      std::static_pointer_cast<void>(nd.res), &ev);
-            if (out == CachePolicy::INSERTED) cstats.inserts++;
-            if (out == CachePolicy::REJECTED) cstats.rejected++;
-            if (out == CachePolicy::HIT) cstats.hits++;
-            cstats.evictions += ev.size();
-            OTEntry *e = otree.entry(nd.types.data(), nd.types.size(), nd.key);
-            if (e) {
-                e->cached = out != CachePolicy::REJECTED;
-                e->c_ms = nd.subtree_ms;
-                e->c_ops = nd.c_ops;
-                e->nnz = (double)nd.res->m.nnz;
-            }
-            for (auto &it : ev) {
-                OTEntry *ee = otree.entry(it.types.data(), it.types.size(), it.key);
-                if (ee) ee->cached = false;
-                htier_store(it.id, std::static_pointer_cast<DevMat>(it.payload), it.types, it.key, it.c,
-                            ee ? ee->c_ops : 0.0);
-            }
-        };
+    if (ex.flights.empty()) ex.est_bytes = 0.0;
+}
+
+void mp_ctx::publish(std::vector<Flight> &done) {
+    const auto t1 = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> g(mu);
+        for (Flight &f : done) {
+            auto it = results.find(f.ticket);
+            if (it == results.end()) continue;  // released before it finished
+            f.r.latency_ms = std::chrono::duration<double, std::milli>(t1 - f.t0).count();
+            f.r.done = true;
+            it->second = std::move(f.r);
+        }
+    }
+    done_cv.notify_all();
+}
+
+int mp_ctx::run_batch(std::vector<Query> &qs, std::vector<Result> &rs) {
+    TraceRange batch_range("mp.batch");
+    const size_t nq = qs.size();
+    cudaEventRecord(ev0, stream);
+    std::vector<int64_t> ids;
+    std::vector<uint64_t> tk(nq, 0);
+    std::vector<std::chrono::steady_clock::time_point> t0s(nq, std::chrono::steady_clock::now());
+    const int arc = admit(qs, tk, t0s, ids);
+    std::unordered_map<int64_t, size_t> mine;
+    for (size_t q = 0; q < nq; q++) mine.emplace(ids[q], q);
+    if (explain.on) {
         for (size_t q = 0; q < nq; q++) {
-            if (root[q] < 0) continue;
-            offer(nodes[root[q]]);
-            if (candidate[q] >= 0) offer(nodes[candidate[q]]);
+            rs[q].status = ex.flights[ids[q]].status;
+            ex.flights.erase(ids[q]);
         }
-        if (cfg.insertion == MP_INSERT_ALL)
-            for (auto &nd : nodes)
-                if (nd.keep) offer(nd);
+        cudaEventRecord(ev1, stream);
+        cudaEventSynchronize(ev1);
+        return arc;
     }
-    for (auto &m : masks) free_masks(m);
-    nodes.clear();
+    // waves until every query of this batch has finished (flights of the serving loop that
+    // finish meanwhile are published as usual)
+    size_t left = nq;
+    int first = MP_OK;
+    for (int guard = 0; left > 0; guard++) {
+        std::vector<Flight> done;
+        finish_flights(done);
+        std::vector<Flight> others;
+        for (Flight &f : done) {
+            auto m = mine.find(f.id);
+            if (m == mine.end()) {
+                others.push_back(std::move(f));
+                continue;
+            }
+            rs[m->second] = std::move(f.r);
+            left--;
+        }
+        if (!others.empty()) publish(others);
+        if (left == 0) break;
+        const int wrc = run_wave();
+        if (wrc || guard > 100000) abort_nodes(wrc ? wrc : MP_ERR_INTERNAL);
+    }
+    for (size_t q = 0; q < nq; q++)
+        if (rs[q].status && first == MP_OK) first = rs[q].status;
     cudaEventRecord(ev1, stream);
     cudaError_t e = cudaEventSynchronize(ev1);
     float ms = 0.f;

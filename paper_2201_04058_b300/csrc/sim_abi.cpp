@@ -9,6 +9,7 @@
 
 struct mp_otree {
     mp::OverlapTree t;
+    explicit mp_otree(int construction) : t(construction) {}
 };
 
 struct mp_cachesim {
@@ -17,9 +18,11 @@ struct mp_cachesim {
     mp_cachesim(double cap, int pol) : c(cap, pol) {}
 };
 
-extern "C" int mp_otree_create(mp_otree **out) {
-    if (!out) return MP_ERR_ARG;
-    *out = new mp_otree();
+extern "C" int mp_otree_create(mp_otree **out) { return mp_otree_create_ex(MP_OTREE_NAIVE, out); }
+
+extern "C" int mp_otree_create_ex(int32_t construction, mp_otree **out) {
+    if (!out || (construction != MP_OTREE_NAIVE && construction != MP_OTREE_ONLINE)) return MP_ERR_ARG;
+    *out = new mp_otree(construction == MP_OTREE_ONLINE ? mp::OverlapTree::ONLINE : mp::OverlapTree::NAIVE);
     return MP_OK;
 }
 

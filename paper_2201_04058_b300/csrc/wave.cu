@@ -996,6 +996,190 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
     }
 }
 
+// The same split-row pass with a warp-level product walk (the default). Each of a block's
+// warps takes a run of SUB consecutive products of the block's work item and finds the X
+// entry holding the run's first product by a 32-way search over the row's product offsets.
+// It then holds 32 X entries at a time in registers (Y row start, product offset, value)
+// and walks their products 32 at a time: lane i takes product w + i and finds the entry
+// that holds it by a 5-step shuffle search over the 32 lanes' offsets. Consecutive lanes
+// read consecutive entries of a Y row (coalesced when Y rows are long), no lane idles when
+// Y rows are short, and nothing is staged block-wide: the warps only meet to flush the
+// combining table at the end of an item.
+static constexpr int SUB = (int)(PCH / (GNT / 32));  // products per warp run
+
+template <int MODE, bool COMB, int OCC>
+__global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
+    constexpr bool NUM = MODE != G_SYM;
+    __shared__ uint32_t s_key[CSLOT];
+    __shared__ unsigned long long s_acc[CSLOT];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int x = threadIdx.x; x < CSLOT; x += GNT) {
+        s_key[x] = EMPTY;
+        s_acc[x] = 0;
+    }
+    __syncthreads();
+    const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
+    for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+        int64_t lo = g.r0, hi = g.r1 - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (g.item_off[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t r = lo;
+        const uint32_t gr = g.list[r];
+        const int pi = a.rowprod[gr];
+        const Prod *PP = a.prods + pi;
+        uint64_t *const pval = PP->val;
+        if (MODE == G_NUM && !pval) continue;  // the product failed before its numeric pass
+        uint32_t *err = &a.ps[pi].err;
+        const bool chk = a.ps[pi].unsafe != 0;  // uniform over the item
+        const int64_t row = (int64_t)gr - PP->row0;
+        const int32_t *__restrict__ xci = PP->X.ci;
+        const uint64_t *__restrict__ xval = PP->X.val;
+        const int64_t *__restrict__ yrp = PP->Y.rp;
+        const int32_t *__restrict__ yci = PP->Y.ci;
+        const uint64_t *__restrict__ yval = PP->Y.val;
+        const uint32_t *__restrict__ cm = PP->cm;
+        const int64_t xb = PP->X.rp[row], xlen = PP->X.rp[row + 1] - xb;
+        const int64_t *__restrict__ xo = g.xoff + g.xbase[r];
+        // product offsets are global across the GLOBAL rows: this row's start at xo[0]
+        const int64_t total = __ldg(xo) + (int64_t)g.prod[gr];
+        const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
+        const int64_t s1 = min(total, s0 + PCH);
+        const int64_t ws0 = s0 + (int64_t)wid * SUB, ws1 = min(s1, ws0 + SUB);
+        uint2 *bmr = g.bmr + (r - g.r0) * g.nw;
+        unsigned long long *val = MODE == G_NUM    ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0])
+                                  : MODE == G_DENSE ? g.dval + (r - g.r0) * g.dcols
+                                                    : nullptr;
+        auto product = [&](uint64_t av, int64_t q) {
+            const uint32_t j = (uint32_t)__ldg(yci + q);
+            // the column mask first: a masked-out product costs one bit load, no atomic
+            if (!bit_of(cm, j)) return;
+            unsigned long long add;
+            if (!NUM) {
+                add = 1ull << (j & 31);
+            } else {
+                const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
+                add = av * bv;
+                if (chk && __umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+            }
+            const uint32_t k = NUM ? j : (j >> 5);
+            const uint32_t slot = (k * 0x9E3779B1u) >> (32 - 10);
+            uint32_t cur = EMPTY - 1;
+            if (COMB) {
+                cur = ((volatile uint32_t *)s_key)[slot];
+                if (cur == EMPTY) {
+                    const uint32_t old = atomicCAS(s_key + slot, EMPTY, k);
+                    cur = old == EMPTY ? k : old;
+                }
+            }
+            if (COMB && cur == k) {
+                if (!NUM) {
+                    atomicOr((unsigned int *)&s_acc[slot], (unsigned int)add);
+                } else if (chk) {
+                    const unsigned long long old = atomicAdd(s_acc + slot, add);
+                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                } else {
+                    atomicAdd(s_acc + slot, add);
+                }
+            } else if (!NUM) {
+                atomicOr(&bmr[k].x, (uint32_t)add);
+            } else {
+                unsigned long long *dst;
+                if (MODE == G_DENSE) {
+                    dst = val + j;
+                } else {
+                    const uint2 br = __ldg(bmr + (j >> 5));
+                    dst = val + br.y + __popc(br.x & ((1u << (j & 31)) - 1u));
+                }
+                if (chk) {
+                    const unsigned long long old = atomicAdd(dst, add);
+                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                } else {
+                    atomicAdd(dst, add);
+                }
+            }
+        };
+        if (ws0 < ws1) {
+            // the last X entry p of the row with xo[p] <= ws0, 32 probes per step
+            int64_t plo = 0, phi = xlen - 1;
+            while (phi - plo >= 32) {
+                const int64_t step = (phi - plo + 31) / 32;
+                const int64_t probe = min(plo + (int64_t)lane * step, phi);
+                const unsigned m = __ballot_sync(FULL, __ldg(xo + probe) <= ws0);
+                const int kk = 31 - __clz(m);
+                if (kk < 31) phi = min(plo + (int64_t)(kk + 1) * step, phi) - 1;
+                plo = min(plo + (int64_t)kk * step, phi);
+            }
+            {
+                const int64_t probe = plo + lane;
+                const unsigned m = __ballot_sync(FULL, probe <= phi && __ldg(xo + min(probe, phi)) <= ws0);
+                plo += 31 - __clz(m);
+            }
+            int64_t p = plo, f = ws0;
+            while (f < ws1 && p < xlen) {
+                const int64_t e = p + lane;
+                const bool ok = e < xlen;
+                const int64_t off = ok ? __ldg(xo + e) : total;
+                int64_t base = 0;  // Y position of this entry's product f is base + f
+                uint64_t av = 1;
+                if (ok) {
+                    const int32_t kx = __ldg(xci + xb + e);
+                    base = __ldg(yrp + kx) - off;
+                    if (NUM && xval) av = __ldg(xval + xb + e);
+                }
+                int64_t gend = 0;  // first product after the 32 entries
+                if (lane == 31) gend = e + 1 < xlen ? __ldg(xo + e + 1) : total;
+                gend = __shfl_sync(FULL, gend, 31);
+                const int64_t lim = min(ws1, gend);
+                for (int64_t w = f; w < lim; w += 32) {
+                    const int64_t fj = w + lane;
+                    // the last lane whose entry starts at or before product fj
+                    const int rel = (int)max((int64_t)-1, min(off - w, (int64_t)32));
+                    int src = 0;
+#pragma unroll
+                    for (int st = 16; st; st >>= 1) {
+                        const int v = __shfl_sync(FULL, rel, src + st);
+                        if (v <= lane) src += st;
+                    }
+                    const int64_t q = __shfl_sync(FULL, base, src) + fj;
+                    const uint64_t ax = NUM ? __shfl_sync(FULL, av, src) : 1ull;
+                    if (fj < lim) product(ax, q);
+                }
+                f = max(f, lim);
+                p += 32;
+            }
+        }
+        __syncthreads();
+        // flush the combining table into the row, reset it for the next item
+        for (int x = threadIdx.x; COMB && x < CSLOT; x += GNT) {
+            const uint32_t k = s_key[x];
+            if (k == EMPTY) continue;
+            if (!NUM) {
+                atomicOr(&bmr[k].x, (uint32_t)s_acc[x]);
+            } else {
+                unsigned long long *dst;
+                if (MODE == G_DENSE) {
+                    dst = val + k;
+                } else {
+                    const uint2 br = __ldg(bmr + (k >> 5));
+                    dst = val + br.y + __popc(br.x & ((1u << (k & 31)) - 1u));
+                }
+                const unsigned long long v = s_acc[x];
+                if (chk) {
+                    const unsigned long long old = atomicAdd(dst, v);
+                    if (old + v < old) atomicOr(err, ERR_OVERFLOW);
+                } else {
+                    atomicAdd(dst, v);
+                }
+            }
+            s_key[x] = EMPTY;
+            s_acc[x] = 0;
+        }
+        __syncthreads();
+    }
+}
+
 // The rank pass in parallel over chunks of RCH words of every row slot (one block each), so a
 // few very wide rows do not leave the GPU to a few blocks: (1) set bits per chunk, (2) one
 // warp per row scans its chunks (the row's size), (3) each chunk writes its words' ranks.
@@ -1332,23 +1516,40 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     g = Glob{};
 }
 
-// The split-row kernel in the variant the tuning asks for: combining table on or off, and
-// for the count-adding modes 4 or 6 resident blocks per SM (64 or 40 registers a thread).
+// The split-row kernel in the variant the tuning asks for: warp-level product walk (default)
+// or block-staged walk, combining table on or off, and for the count-adding modes 4 or 6
+// resident blocks per SM (64 or 40 registers a thread).
 // One block per resident slot: the blocks loop over the work items.
 template <int MODE>
 static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga) {
     const int occ = MODE == G_SYM ? 8 : tun.glob_occ >= 6 ? 6 : 4;
     const unsigned grid = (unsigned)(tun.sm_count * occ);
-    if constexpr (MODE == G_SYM) {
-        if (tun.combine) kl(k_glob_set<MODE, true, 8>, grid, GNT, 0, s, a, ga);
-        else kl(k_glob_set<MODE, false, 8>, grid, GNT, 0, s, a, ga);
-    } else if (occ == 6) {
-        if (tun.combine) kl(k_glob_set<MODE, true, 6>, grid, GNT, 0, s, a, ga);
-        else kl(k_glob_set<MODE, false, 6>, grid, GNT, 0, s, a, ga);
-    } else {
-        if (tun.combine) kl(k_glob_set<MODE, true, 4>, grid, GNT, 0, s, a, ga);
-        else kl(k_glob_set<MODE, false, 4>, grid, GNT, 0, s, a, ga);
+#define GLOB_SET_VARIANT(K)                                                       \
+    if constexpr (MODE == G_SYM) {                                                \
+        if (tun.combine) kl(K<MODE, true, 8>, grid, GNT, 0, s, a, ga);           \
+        else kl(K<MODE, false, 8>, grid, GNT, 0, s, a, ga);                      \
+    } else if (occ == 6) {                                                        \
+        if (tun.combine) kl(K<MODE, true, 6>, grid, GNT, 0, s, a, ga);           \
+        else kl(K<MODE, false, 6>, grid, GNT, 0, s, a, ga);                      \
+    } else {                                                                      \
+        if (tun.combine) kl(K<MODE, true, 4>, grid, GNT, 0, s, a, ga);           \
+        else kl(K<MODE, false, 4>, grid, GNT, 0, s, a, ga);                      \
     }
+    if (tun.lbs) {
+        // the bitmap pass at 6 blocks per SM (40 registers), the count-adding passes at
+        // lbs_occ (4: 64 registers; 6 spills a few values of the shuffle walk)
+        const int lo = MODE == G_SYM || tun.lbs_occ >= 6 ? 6 : 4;
+        if (lo == 6) {
+            if (tun.combine) kl(k_glob_lbs<MODE, true, 6>, (unsigned)(tun.sm_count * 6), GNT, 0, s, a, ga);
+            else kl(k_glob_lbs<MODE, false, 6>, (unsigned)(tun.sm_count * 6), GNT, 0, s, a, ga);
+        } else {
+            if (tun.combine) kl(k_glob_lbs<MODE, true, 4>, (unsigned)(tun.sm_count * 4), GNT, 0, s, a, ga);
+            else kl(k_glob_lbs<MODE, false, 4>, (unsigned)(tun.sm_count * 4), GNT, 0, s, a, ga);
+        }
+    } else {
+        GLOB_SET_VARIANT(k_glob_set)
+    }
+#undef GLOB_SET_VARIANT
 }
 
 // One pass of the GLOBAL bin (all rounds). pass 0 counts, pass 1 writes the rows.
@@ -1393,7 +1594,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
 
 int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cudaStream_t s,
                 uint64_t max_result_bytes, std::vector<WaveOut> &out, Prof *prof, bool symbolic_only,
-                WaveCache *wc) {
+                WaveCache *wc, Budget *bud) {
     const int w = (int)in.size();
     out.assign(w, WaveOut{});
     if (w == 0) return MP_OK;
@@ -1461,6 +1662,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     PassArgs pa{};
     Small h_sym, h_num;
     std::vector<PStat> hps(w);
+    std::vector<int64_t> reserved(w, 0);  // budget bytes charged for each product's result
+    auto unreserve = [&](int p) {
+        if (bud && reserved[p]) bud->unreserve(reserved[p]);
+        reserved[p] = 0;
+    };
     char *ws = graphs ? wc->ws : (char *)al.alloc(ws_bytes, s);
     if (graphs && !ws) ws = wc->ws = (char *)al.alloc(ws_bytes, s);
     if (!ws) return MP_ERR_NOMEM;
@@ -1482,6 +1688,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     Small *sm_num = sm_sym + 1;
     auto fail = [&](int code) {
         for (int p = 0; p < w; p++) {
+            unreserve(p);
             if (hp[p].rp) al.free(hp[p].rp, s);
             if (hp[p].ci) al.free(hp[p].ci, s);
             if (hp[p].val) al.free(hp[p].val, s);
@@ -1634,6 +1841,13 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             o.status = MP_ERR_TOO_LARGE;
             continue;
         }
+        if (bud) {
+            if (bud->reserve((int64_t)m.bytes())) {
+                o.status = MP_ERR_BUDGET;
+                continue;
+            }
+            reserved[p] = (int64_t)m.bytes();
+        }
         hp[p].ci = (int32_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s);
         hp[p].val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
         if (!hp[p].ci || !hp[p].val) return fail(MP_ERR_NOMEM);
@@ -1666,6 +1880,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         for (int b = 0; b < NBINS; b++) o.num_bins[b] = hps[p].num_bins[b];
         if (!o.status && hps[p].err) o.status = (hps[p].err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
         if (o.status) {
+            unreserve(p);
             if (hp[p].rp) al.free(hp[p].rp, s);
             if (hp[p].ci) al.free(hp[p].ci, s);
             if (hp[p].val) al.free(hp[p].val, s);

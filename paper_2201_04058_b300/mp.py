@@ -29,12 +29,12 @@ EXPORTS = [
     "mp_add_relation", "mp_finalize_hin", "mp_type_id", "mp_property_id", "mp_relation_id",
     "mp_submit", "mp_submit_batch", "mp_wait", "mp_result_info", "mp_result_copy", "mp_release",
     "mp_result_time", "mp_strerror", "mp_result_stats", "mp_plan_chain", "mp_kernel_stats",
-    "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
+    "mp_kernel_stats_reset", "mp_otree_create", "mp_otree_create_ex", "mp_otree_destroy", "mp_otree_insert", "mp_otree_frequency",
     "mp_otree_info", "mp_cachesim_create", "mp_cachesim_destroy", "mp_cachesim_request", "mp_cachesim_entry",
     "mp_cachesim_evicted", "mp_cachesim_state", "mp_cache_stats", "mp_row_product_noalloc",
     "mp_serve_start", "mp_serve_stop", "mp_serve_stats", "mp_result_latency", "mp_autotune", "mp_hin_save",
     "mp_hin_load", "mp_plan_chain_mnc", "mp_plan_query", "mp_host_tier_stats", "mp_result_copy_async",
-    "mp_result_copy_wait", "mp_graph_stats",
+    "mp_result_copy_wait", "mp_graph_stats", "mp_serve_counters", "mp_budget_stats",
 ]
 
 
@@ -44,7 +44,49 @@ class mp_config(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("force_bin_class", C.c_int32), ("max_result_bytes", C.c_uint64),
                 ("scratch_bytes", C.c_uint64), ("sample_rows", C.c_uint32), ("seed", C.c_uint64),
-                ("insertion", C.c_int32), ("tune_file", C.c_char_p), ("host_tier_bytes", C.c_uint64)]
+                ("insertion", C.c_int32), ("tune_file", C.c_char_p), ("host_tier_bytes", C.c_uint64),
+                ("cache_bytes", C.c_uint64), ("otree_construction", C.c_int32),
+                ("alloc", C.c_void_p), ("free", C.c_void_p), ("alloc_user", C.c_void_p)]
+
+
+# mp_config.alloc / .free
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class TorchAllocator:
+    """mp_config.alloc / .free backed by PyTorch's CUDA caching allocator, so the engine's
+    device buffers come from the same pool as the caller's tensors. Keep the object alive
+    as long as the context that uses it. Counts the live allocations it made."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.calls = 0
+
+        def _alloc(nbytes, stream, user):
+            try:
+                p = self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+            except RuntimeError:
+                return None
+            self.live[p] = int(nbytes)
+            self.calls += 1
+            return p
+
+        def _free(ptr, stream, user):
+            if ptr:
+                self.live.pop(int(ptr), None)
+                self.torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+    def install(self, cfg):
+        cfg.alloc = C.cast(self.alloc_fn, C.c_void_p)
+        cfg.free = C.cast(self.free_fn, C.c_void_p)
+        cfg.alloc_user = None
 
 
 class mp_constraint(C.Structure):
@@ -113,11 +155,14 @@ def lib():
             "mp_serve_start": (C.c_int, [C.c_void_p]),
             "mp_serve_stop": (C.c_int, [C.c_void_p]),
             "mp_serve_stats": (C.c_int, [C.c_void_p, P(U64), P(U64), P(U64)]),
+            "mp_serve_counters": (C.c_int, [C.c_void_p, P(U64), P(U64), P(U64)]),
+            "mp_budget_stats": (C.c_int, [C.c_void_p, P(U64), P(U64)]),
             "mp_result_latency": (C.c_int, [C.c_void_p, U64, P(C.c_double)]),
             "mp_row_product_noalloc": (C.c_int, [I32, C.c_void_p, U64, C.c_void_p, C.c_void_p, C.c_void_p,
                                                  C.c_void_p, C.c_void_p, U32, C.c_void_p, C.c_void_p, U64,
                                                  C.c_void_p, C.c_void_p, P(U64)]),
             "mp_otree_create": (C.c_int, [P(C.c_void_p)]),
+            "mp_otree_create_ex": (C.c_int, [I32, P(C.c_void_p)]),
             "mp_otree_destroy": (None, [C.c_void_p]),
             "mp_otree_insert": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_void_p]),
             "mp_otree_frequency": (C.c_int, [C.c_void_p, U32, C.c_void_p, C.c_char_p, P(U64)]),
@@ -313,6 +358,18 @@ def mp_serve_stats(ctx):
     return {"batches": b.value, "queries": q.value, "queued": w.value}
 
 
+def mp_serve_counters(ctx):
+    w, j, m = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _ck(lib().mp_serve_counters(ctx, C.byref(w), C.byref(j), C.byref(m)), "mp_serve_counters")
+    return {"waves": w.value, "joined": j.value, "max_inflight": m.value}
+
+
+def mp_budget_stats(ctx):
+    h, p = C.c_uint64(), C.c_uint64()
+    _ck(lib().mp_budget_stats(ctx, C.byref(h), C.byref(p)), "mp_budget_stats")
+    return {"held": h.value, "peak": p.value}
+
+
 def mp_result_latency(ctx, ticket: int) -> float:
     ms = C.c_double()
     _ck(lib().mp_result_latency(ctx, ticket, C.byref(ms)), "mp_result_latency")
@@ -453,12 +510,16 @@ def mp_kernel_stats_reset(ctx):
     _ck(lib().mp_kernel_stats_reset(ctx), "mp_kernel_stats_reset")
 
 
-class OTree:
-    """Host-only Overlap Tree replay (mp_otree_*)."""
+MP_OTREE_NAIVE, MP_OTREE_ONLINE = 0, 1
 
-    def __init__(self):
+
+class OTree:
+    """Host-only Overlap Tree replay (mp_otree_*), built by the naive insertion or on-line
+    (Ukkonen)."""
+
+    def __init__(self, construction: int = MP_OTREE_NAIVE):
         self.h = C.c_void_p()
-        _ck(lib().mp_otree_create(C.byref(self.h)), "mp_otree_create")
+        _ck(lib().mp_otree_create_ex(int(construction), C.byref(self.h)), "mp_otree_create_ex")
 
     def insert(self, types, pos_keys=None):
         t = np.ascontiguousarray(types, np.int32)
@@ -554,22 +615,36 @@ _OPS = {"range": MP_OP_RANGE, "eq": MP_OP_EQ, "in": MP_OP_IN}
 class Engine:
     """One context with a HIN loaded from a generator dict (see the ``gen`` module)."""
 
-    def __init__(self, hin, **cfg_fields):
+    def __init__(self, hin, allocator=None, load_path=None, **cfg_fields):
+        """hin: a generator dict (types, relations, props); with load_path, the HIN comes
+        from a file mp_hin_save wrote instead (hin then only names its types and props)."""
         self.cfg = mp_config_default()
         for k, v in cfg_fields.items():
             setattr(self.cfg, k, v.encode() if isinstance(v, str) else v)
+        self.allocator = allocator  # e.g. TorchAllocator: kept alive with the context
+        if allocator is not None:
+            allocator.install(self.cfg)
         self.ctx = mp_create(self.cfg)
         self.type_id = {}
-        for name, n in hin["types"].items():
-            self.type_id[name] = mp_add_node_type(self.ctx, name, n)
         self.prop_id = {}
-        for (t, p), vals in hin["props"].items():
-            mp_add_property_i32(self.ctx, self.type_id[t], p, vals)
-        for a, b, s, d in hin["relations"]:
-            mp_add_relation(self.ctx, self.type_id[a], self.type_id[b], s, d)
-        mp_finalize_hin(self.ctx)
+        if load_path is not None:
+            mp_hin_load(self.ctx, load_path)
+            mp_finalize_hin(self.ctx)
+            for name in hin["types"]:
+                self.type_id[name] = mp_type_id(self.ctx, name)
+        else:
+            for name, n in hin["types"].items():
+                self.type_id[name] = mp_add_node_type(self.ctx, name, n)
+            for (t, p), vals in hin["props"].items():
+                mp_add_property_i32(self.ctx, self.type_id[t], p, vals)
+            for a, b, s, d in hin["relations"]:
+                mp_add_relation(self.ctx, self.type_id[a], self.type_id[b], s, d)
+            mp_finalize_hin(self.ctx)
         for (t, p) in hin["props"]:
             self.prop_id[(t, p)] = mp_property_id(self.ctx, self.type_id[t], p)
+
+    def save(self, path):
+        mp_hin_save(self.ctx, path)
 
     def query(self, q):
         cons = []

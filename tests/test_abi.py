@@ -46,3 +46,40 @@ def test_bad_arguments_rejected_on_host():
     from paper_2201_04058_b300 import mp
     with pytest.raises(mp.MPError):
         mp.mp_plan_chain([4, 0, 3], [1, 1])
+
+
+def test_config_layout_and_new_fields():
+    """The ctypes mp_config is exactly as large as the C struct: mp_config_default writes
+    every field and nothing past the end; defaults of the budget, cache, Overlap-Tree and
+    allocator fields."""
+    import ctypes as C
+    from paper_2201_04058_b300 import mp
+    n = C.sizeof(mp.mp_config)
+    buf = (C.c_uint8 * (n + 64))(*([0xAB] * (n + 64)))
+    mp.lib().mp_config_default(C.cast(buf, C.POINTER(mp.mp_config)))
+    assert all(b == 0xAB for b in bytes(buf)[n:]), "mp_config_default wrote past the ctypes struct"
+    assert bytes(buf)[n - 8:n] == b"\0" * 8  # alloc_user, the last field, was written
+    c = mp.mp_config_default()
+    assert c.otree_construction == mp.MP_OTREE_ONLINE and c.cache_bytes == 0
+    assert not c.alloc and not c.free and not c.alloc_user
+    assert c.hbm_budget_bytes == 8 << 30
+
+
+def test_allocator_hooks_must_come_in_pairs():
+    from paper_2201_04058_b300 import mp
+    c = mp.mp_config_default()
+    fn = mp.ALLOC_FN(lambda n, s, u: None)
+    c.alloc = C_cast(fn)
+    with pytest.raises(mp.MPError) as e:
+        mp.mp_create(c)
+    assert e.value.code == mp.MP_ERR_ARG
+    c = mp.mp_config_default()
+    c.otree_construction = 7
+    with pytest.raises(mp.MPError) as e:
+        mp.mp_create(c)
+    assert e.value.code == mp.MP_ERR_ARG
+
+
+def C_cast(fn):
+    import ctypes as C
+    return C.cast(fn, C.c_void_p)

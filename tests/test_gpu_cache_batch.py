@@ -35,7 +35,7 @@ def _mp():
 def test_batch_matches_oracle_every_policy(c1, batch_queries, cuda_ok, policy, budget):
     mp = _mp()
     qs, want = batch_queries
-    e = mp.Engine(c1[0], policy=policy, hbm_budget_bytes=budget)
+    e = mp.Engine(c1[0], policy=policy, cache_bytes=budget)
     try:
         for rnd in range(2):  # the second round meets a warm cache
             rc, res = e.run_batch(qs)
@@ -108,7 +108,7 @@ def test_long_metapaths_with_squeezed_cache(c1, cuda_ok):
     qs = gen.long_queries(5, 16)
     want = [OC.evaluate(c1[1], q) for q in qs]
     for policy, budget in ((3, 1 << 30), (0, 6 << 20), (1, 6 << 20), (2, 6 << 20)):
-        e = mp.Engine(c1[0], policy=policy, hbm_budget_bytes=budget)
+        e = mp.Engine(c1[0], policy=policy, cache_bytes=budget)
         try:
             for rnd in range(2):
                 for q, w in zip(qs, want):
@@ -123,7 +123,7 @@ def test_cache_baselines_match_oracle(c1, batch_queries, cuda_ok, insertion, pol
     combinations, change what is cached, never the results."""
     mp = _mp()
     qs, want = batch_queries
-    e = mp.Engine(c1[0], policy=policy, insertion=insertion, hbm_budget_bytes=3 << 20)
+    e = mp.Engine(c1[0], policy=policy, insertion=insertion, cache_bytes=3 << 20)
     try:
         for rnd in range(2):
             rc, res = e.run_batch(qs)
@@ -144,7 +144,7 @@ def test_host_tier_results_and_reuse(c1, batch_queries, cuda_ok, host_bytes):
     tier smaller than the evicted results drops its least recently used entries."""
     mp = _mp()
     qs, want = batch_queries
-    e = mp.Engine(c1[0], policy=mp.MP_POLICY_ATRAPOS, hbm_budget_bytes=2 << 20, host_tier_bytes=host_bytes,
+    e = mp.Engine(c1[0], policy=mp.MP_POLICY_ATRAPOS, cache_bytes=2 << 20, host_tier_bytes=host_bytes,
                   insertion=mp.MP_INSERT_ALL)
     try:
         for rnd in range(3):

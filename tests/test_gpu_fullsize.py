@@ -88,3 +88,11 @@ def test_batched_form_equals_plain(full):
     assert rc == 0
     for q, g, w in zip(qs, got, res):
         assert_same(g, w, "".join(q["types"]))
+
+
+def test_every_result_matches_oracle(full, ohin):
+    """Every full-size result, element by element, against the oracle's whole CSR (about
+    half a minute of single-threaded host time for the twenty queries)."""
+    h, qs, eng, res = full
+    for qi, (q, got) in enumerate(zip(qs, res)):
+        assert_same(got, OC.evaluate(ohin, q), f"query {qi} {''.join(q['types'])}")

@@ -1,29 +1,33 @@
 """GPU: the serving loop (continuous batching). Queries submitted one by one with random
-gaps are served in rounds; each result equals the same query evaluated alone (bit for
-bit), and rounds hold several queries."""
+gaps join the product DAG while others are on the GPU; every result equals the CPU
+oracle's bit for bit, and queries were admitted while others were in flight."""
 import time
 
 import numpy as np
 import pytest
 
 import gen
+from oracle import chain as OC
+from oracle.hin import OracleHIN
 
 from test_gpu_parity import assert_same
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("policy", [0, 3])
-def test_stream_results_equal_alone(cuda_ok, policy):
-    from paper_2201_04058_b300 import mp
+@pytest.fixture(scope="module")
+def c1():
     h = gen.config1_hin()
+    return h, OracleHIN(h)
+
+
+@pytest.mark.parametrize("policy", [0, 3])
+def test_stream_results_match_oracle(c1, cuda_ok, policy):
+    from paper_2201_04058_b300 import mp
+    h, o = c1
     qs = gen.batched_queries(seed=7, n=120, pool=25)
-    alone = mp.Engine(h, policy=mp.MP_POLICY_NONE)
-    try:
-        want = [alone.run(q) for q in qs]
-    finally:
-        alone.close()
-    e = mp.Engine(h, policy=policy, max_slots=16, hbm_budget_bytes=8 << 20)
+    want = [OC.evaluate(o, q) for q in qs]
+    e = mp.Engine(h, policy=policy, max_slots=16, cache_bytes=8 << 20)
     try:
         mp.mp_serve_start(e.ctx)
         rng = np.random.default_rng(0)
@@ -40,10 +44,39 @@ def test_stream_results_equal_alone(cuda_ok, policy):
             mp.mp_release(e.ctx, t)
         st = mp.mp_serve_stats(e.ctx)
         assert st["queries"] == len(qs) and st["queued"] == 0
-        assert st["batches"] < len(qs)  # some rounds served several queries
+        assert st["batches"] < len(qs)  # some admission groups held several queries
+        ct = mp.mp_serve_counters(e.ctx)
+        assert ct["joined"] > 0  # queries joined work already on the GPU
+        assert 1 < ct["max_inflight"] <= 16
         mp.mp_serve_stop(e.ctx)
         # after stopping, submission runs synchronously again
         assert_same(e.run(qs[0]), want[0], "after stop")
+        # only cache entries stay charged to the budget once every result is released
+        held = mp.mp_budget_stats(e.ctx)["held"]
+        assert held == (mp.mp_cache_stats(e.ctx)["bytes"] if policy == 0 else 0)
+    finally:
+        e.close()
+
+
+def test_stream_in_one_burst_overlaps(c1, cuda_ok):
+    """A burst larger than the slots: later queries are admitted as earlier ones finish,
+    beside the products of those still in flight; results exact, slots never exceeded."""
+    from paper_2201_04058_b300 import mp
+    h, o = c1
+    qs = gen.long_queries(9, 24) + gen.batched_queries(seed=8, n=40, pool=30, anchor_p=0.5)
+    e = mp.Engine(h, policy=mp.MP_POLICY_NONE, max_slots=6)
+    try:
+        mp.mp_serve_start(e.ctx)
+        rc, ts = e.submit_batch(qs)
+        assert rc == mp.MP_OK
+        for q, t in zip(qs, ts):
+            assert mp.mp_wait(e.ctx, t) == mp.MP_OK
+            assert_same(e.fetch(t), OC.evaluate(o, q), "".join(q["types"]))
+            e.release(t)
+        ct = mp.mp_serve_counters(e.ctx)
+        assert ct["max_inflight"] <= 6
+        assert ct["joined"] > 0
+        assert mp.mp_budget_stats(e.ctx)["held"] == 0
     finally:
         e.close()
 

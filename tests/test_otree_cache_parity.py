@@ -28,11 +28,9 @@ def _pos_keys(q, c):
     return ["&".join(c[i]) if i in c else "" for i in range(len(q))]
 
 
-@pytest.mark.parametrize("seed", range(12))
-def test_tree_frequencies_match_oracle(seed):
+def _check_tree(qs, cons, construction):
     from paper_2201_04058_b300 import mp
-    qs, cons = _workload(seed)
-    ot, et = OverlapTree(), mp.OTree()
+    ot, et = OverlapTree(), mp.OTree(construction)
     for q, c in zip(qs, cons):
         ot.insert(q, c)
         et.insert(q, _pos_keys(q, c))
@@ -48,6 +46,34 @@ def test_tree_frequencies_match_oracle(seed):
         for key in keys:
             assert et.frequency(s, key) == ot.frequency(s, key), (s, key)
     assert et.frequency((9, 9)) == 0
+
+
+@pytest.mark.parametrize("construction", [0, 1])
+@pytest.mark.parametrize("seed", range(12))
+def test_tree_frequencies_match_oracle(seed, construction):
+    """Both constructions of the engine's tree (the naive insertion of Sec. 3.3.2 and the
+    on-line Ukkonen construction its footnote points to) against the oracle's tree."""
+    qs, cons = _workload(seed)
+    _check_tree(qs, cons, construction)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_online_tree_on_repetitive_metapaths(seed):
+    """Long metapaths over two or three symbols (runs like ABABAB and AAAA, where suffix
+    links and walk-downs matter most), and repeated whole queries."""
+    rng = np.random.default_rng(500 + seed)
+    qs, cons = [], []
+    for _ in range(30):
+        L = int(rng.integers(1, 13))
+        period = int(rng.integers(1, 4))
+        base = rng.integers(0, 2 + seed % 2, period)
+        q = tuple(int(base[i % period]) for i in range(L))
+        if rng.random() < 0.2 and qs:
+            q = qs[int(rng.integers(len(qs)))]
+        c = {i: (f"p0in{int(rng.integers(0, 2))}",) for i in range(L) if rng.random() < 0.2}
+        qs.append(q)
+        cons.append(c)
+    _check_tree(qs, cons, 1)
 
 
 @pytest.mark.parametrize("policy,seed", list(itertools.product([0, 1, 2], range(10))))
