@@ -651,7 +651,8 @@ def leg_serving(mp, local, peak, peak_kind, scale=1.0, n=2000, loads=(0.5, 0.8, 
     stream_q, _ = gen.serving_stream(hin, seed=4, n=100_000)
     qs = stream_q[:n]
     path = os.path.join(tempfile.mkdtemp(prefix="mp_news_"), "news.hin")
-    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, max_slots=1)
+    budget = int(budget_gb * (1 << 30))
+    plain = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, max_slots=1, hbm_budget_bytes=budget)
     plain.save(path)
     names = {"types": hin["types"], "props": {k: None for k in hin["props"]}}
     del hin
@@ -667,28 +668,33 @@ def leg_serving(mp, local, peak, peak_kind, scale=1.0, n=2000, loads=(0.5, 0.8, 
         mp.mp_release(plain.ctx, t)
     sat = n_sat / (time.perf_counter() - t0)
     setup_s = time.perf_counter() - t_setup
-    budget = int(budget_gb * (1 << 30))
 
     def serve(eng, arrivals):
         qb = [eng.query(q) for q in qs]
         mp.mp_serve_start(eng.ctx)
-        tickets = []
+        tickets, done = [], []
+
+        def finish(t, i):
+            st = mp.mp_wait(eng.ctx, t)
+            if st != mp.MP_OK:
+                raise mp.MPError(st, f"served query {i}")
+            ms = mp.mp_result_latency(eng.ctx, t)
+            mp.mp_release(eng.ctx, t)
+            return ms
+
         start = time.perf_counter()
-        for b, at in zip(qb, arrivals):
+        for i, (b, at) in enumerate(zip(qb, arrivals)):
             d = start + at - time.perf_counter()
             if d > 0:
                 time.sleep(d)
             _, t = mp.mp_submit(eng.ctx, b)
-            tickets.append(t)
-        lat = []
-        for t in tickets:
-            st = mp.mp_wait(eng.ctx, t)
-            if st != mp.MP_OK:
-                raise mp.MPError(st, "served query")
-            lat.append(mp.mp_result_latency(eng.ctx, t))
+            tickets.append((t, i))
+            # a client that got its result lets it go (results held by tickets count against
+            # the budget): release the finished ones as the stream goes on
+            while tickets and mp.mp_wait(eng.ctx, tickets[0][0], 0) != mp.MP_ERR_TIMEOUT:
+                done.append(finish(*tickets.pop(0)))
+        lat = done + [finish(t, i) for t, i in tickets]
         end = time.perf_counter()
-        for t in tickets:
-            mp.mp_release(eng.ctx, t)
         ct = mp.mp_serve_counters(eng.ctx)
         mp.mp_serve_stop(eng.ctx)
         return {"qps": len(qs) / (end - start), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),

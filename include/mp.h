@@ -314,7 +314,8 @@ int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t 
 /* Per-kernel counters of the SpGEMM passes since the last reset: one entry per (pass,
  * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
  * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),
- * dense, global. ms sums the device time between CUDA events recorded on the launch
+ * dense, global, or pool (the persistent launch that drains the warp-hash and 2048-slot
+ * bins when that mode is on; those bins then have no entries of their own). ms sums the device time between CUDA events recorded on the launch
  * stream around each launch; bytes sums the algorithmic bytes of the launches (X row
  * pointers, X entries with the two Y row pointers each looks up, one Y column id (and
  * value, in the pass that adds the counts: the numeric pass, or the symbolic pass for

@@ -168,6 +168,8 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "graphs") ctx->tun.graphs = (int)v;
                 else if (k == "lbs") ctx->tun.lbs = (int)v;
                 else if (k == "lbs_occ") ctx->tun.lbs_occ = (int)v;
+                else if (k == "pool") ctx->tun.pool = (int)v;
+
             }
             a = b + 1;
         }
@@ -195,6 +197,11 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
             };
             double dmu = ctx->tun.dense_min_u, hv = (double)ctx->tun.heavy;
             double cb = ctx->tun.combine, sw = ctx->tun.short_walk, gw = ctx->tun.seg_walk, oc = ctx->tun.glob_occ;
+            double lb = ctx->tun.lbs, lo = ctx->tun.lbs_occ;
+            num("\"lbs\"", &lb);
+            num("\"lbs_occ\"", &lo);
+            ctx->tun.lbs = (int)lb;
+            ctx->tun.lbs_occ = (int)lo;
             num("\"dense_min_u\"", &dmu);
             num("\"heavy\"", &hv);
             num("\"combine\"", &cb);
@@ -893,13 +900,17 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
             }
         }
     // the split-row kernel variants at the best thresholds, one knob flipped at a time from
-    // the best so far: combining table, short-row walk, segment walk, 4 or 6 blocks per SM
-    for (int v = 0; v < 4 && !rc; v++) {
+    // the best so far: combining table, warp-level or block-staged product walk, blocks per
+    // SM of the warp walk's adding passes, and (staged walk) its segment walk and occupancy
+    for (int v = 0; v < 5 && !rc; v++) {
         ctx->tun = best_t;
         if (v == 0) ctx->tun.combine ^= 1;
-        if (v == 1) ctx->tun.short_walk ^= 1;
-        if (v == 2) ctx->tun.seg_walk ^= 1;
-        if (v == 3) ctx->tun.glob_occ = ctx->tun.glob_occ >= 6 ? 4 : 6;
+        if (v == 1) ctx->tun.lbs ^= 1;
+        if (v == 2 && !ctx->tun.lbs) continue;
+        if (v == 2) ctx->tun.lbs_occ = ctx->tun.lbs_occ >= 6 ? 4 : 6;
+        if (v >= 3 && ctx->tun.lbs) continue;
+        if (v == 3) ctx->tun.seg_walk ^= 1;
+        if (v == 4) ctx->tun.glob_occ = ctx->tun.glob_occ >= 6 ? 4 : 6;
         std::vector<double> ts;
         for (uint32_t r = 0; r < reps + 1 && !rc; r++) {
             std::vector<Query> qs = parsed;
@@ -914,8 +925,9 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
         const double med = ts[ts.size() / 2];
         char line[200];
         snprintf(line, sizeof(line),
-                 ", {\"combine\": %d, \"short_walk\": %d, \"seg_walk\": %d, \"glob_occ\": %d, \"ms\": %.4f}",
-                 ctx->tun.combine, ctx->tun.short_walk, ctx->tun.seg_walk, ctx->tun.glob_occ, med);
+                 ", {\"combine\": %d, \"lbs\": %d, \"lbs_occ\": %d, \"seg_walk\": %d, \"glob_occ\": %d, "
+                 "\"ms\": %.4f}",
+                 ctx->tun.combine, ctx->tun.lbs, ctx->tun.lbs_occ, ctx->tun.seg_walk, ctx->tun.glob_occ, med);
         log += line;
         if (med < best) {
             best = med;
@@ -980,12 +992,12 @@ extern "C" int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t 
         FILE *f = fopen(out_path, "w");
         if (!f) return MP_ERR_ARG;
         fprintf(f, "{\"dense_min_u\": %d, \"heavy\": %llu, \"combine\": %d, \"short_walk\": %d, "
-                   "\"seg_walk\": %d, \"glob_occ\": %d, "
+                   "\"seg_walk\": %d, \"glob_occ\": %d, \"lbs\": %d, \"lbs_occ\": %d, "
                    "\"alpha\": %.9g, \"beta\": %.9g, \"gamma\": %.9g, \"fitted\": %s, \"best_ms\": %.4f, "
                    "\"candidates\": [%s]}\n",
                 ctx->tun.dense_min_u, (unsigned long long)ctx->tun.heavy, ctx->tun.combine, ctx->tun.short_walk,
-                ctx->tun.seg_walk, ctx->tun.glob_occ, coef[0], coef[1], coef[2], fitted ? "true" : "false", best,
-                log.c_str());
+                ctx->tun.seg_walk, ctx->tun.glob_occ, ctx->tun.lbs, ctx->tun.lbs_occ, coef[0], coef[1], coef[2],
+                fitted ? "true" : "false", best, log.c_str());
         fclose(f);
     }
     return MP_OK;
@@ -1151,11 +1163,11 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
     std::lock_guard<std::mutex> g(ctx->exec_mu);
     uint32_t w = 0;
     for (int p = 0; p < 2; p++)
-        for (int b = 0; b < NBINS; b++) {
-            const KStat &k = ctx->prof.k[p][b];
+        for (int b = 0; b <= NBINS; b++) {
+            const KStat &k = b < NBINS ? ctx->prof.k[p][b] : ctx->prof.pool[p];
             if (!k.launches) continue;
             if (out && w < cap) {
-                snprintf(out[w].name, sizeof(out[w].name), "%s_%s", p ? "num" : "sym", bins[b]);
+                snprintf(out[w].name, sizeof(out[w].name), "%s_%s", p ? "num" : "sym", b < NBINS ? bins[b] : "pool");
                 out[w].launches = k.launches;
                 out[w].ms = k.ms;
                 out[w].bytes = k.bytes;
@@ -1209,8 +1221,10 @@ extern "C" int mp_graph_stats(mp_ctx *ctx, uint64_t *captures, uint64_t *replays
 extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
     if (!ctx) return MP_ERR_ARG;
     std::lock_guard<std::mutex> g(ctx->exec_mu);
-    for (int p = 0; p < 2; p++)
+    for (int p = 0; p < 2; p++) {
         for (int b = 0; b < NBINS; b++) ctx->prof.k[p][b] = KStat{};
+        ctx->prof.pool[p] = KStat{};
+    }
     return MP_OK;
 }
 

@@ -19,6 +19,7 @@ struct DCsr {
     const int32_t *ci = nullptr;
     const uint64_t *val = nullptr;
     int64_t nrows = 0, ncols = 0;
+    int64_t nnz = 0;
 };
 
 // Row-bin classes. Warp-hash bins hold one row per warp in a shared-memory table of T
@@ -56,6 +57,7 @@ struct Tuning {
     uint64_t dense_scratch_cap = 16ull << 30;  // bytes of dense rows (+ bitmap, rank) per wave
     int glob_occ = 6;  // resident blocks per SM of the count-adding split-row kernels (4 or 6)
     int graphs = 0;    // shared-memory bin passes replayed as CUDA graphs, one per wave shape
+    int pool = 1;      // warp-hash and 2048-slot bins in one persistent launch per pass
     int sm_count = 148;
 };
 
@@ -78,6 +80,10 @@ struct Prof {
     bool on = true;
     cudaEvent_t ev[2][NBINS][2] = {};
     KStat k[2][NBINS];
+    // the pooled launch of the warp-hash and 2048-slot bins (Tuning::pool), per pass
+    cudaEvent_t pev[2][2] = {};
+    KStat pool[2];
+    bool pool_ran[2] = {false, false};
     bool init();
     void destroy();
 };
@@ -93,7 +99,7 @@ struct Mat {
     uint64_t *val = nullptr;   // nullptr only for base relations
     uint64_t vmax = 1;         // upper bound on the values (1: 0/1 pattern; UINT64_MAX: none known)
     size_t bytes() const { return (size_t)(nrows + 1) * 8 + (size_t)nnz * 12; }
-    DCsr view() const { return DCsr{rp, ci, val, nrows, ncols}; }
+    DCsr view() const { return DCsr{rp, ci, val, nrows, ncols, nnz}; }
 };
 
 // Stream-ordered device allocation used for results and workspaces. fail_after (tests):

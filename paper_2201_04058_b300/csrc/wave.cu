@@ -38,18 +38,24 @@ namespace mp {
 std::atomic<uint64_t> g_launches{0};
 
 bool Prof::init() {
-    for (int p = 0; p < 2; p++)
+    for (int p = 0; p < 2; p++) {
         for (int b = 0; b < NBINS; b++)
             for (int e = 0; e < 2; e++)
                 if (cudaEventCreate(&ev[p][b][e]) != cudaSuccess) return false;
+        for (int e = 0; e < 2; e++)
+            if (cudaEventCreate(&pev[p][e]) != cudaSuccess) return false;
+    }
     return true;
 }
 
 void Prof::destroy() {
-    for (int p = 0; p < 2; p++)
+    for (int p = 0; p < 2; p++) {
         for (int b = 0; b < NBINS; b++)
             for (int e = 0; e < 2; e++)
                 if (ev[p][b][e]) cudaEventDestroy(ev[p][b][e]);
+        for (int e = 0; e < 2; e++)
+            if (pev[p][e]) cudaEventDestroy(pev[p][e]);
+    }
 }
 
 // One product of a wave, as the kernels see it.
@@ -61,6 +67,7 @@ struct Prod {
     int32_t *ci;    // output column ids (after the symbolic pass)
     uint64_t *val;  // output counts
     uint64_t ymax;  // upper bound on Y's values
+    int64_t xe0;    // first slot of this product's X entries in the wave's per-entry arrays
 };
 
 // Per-product counters kept on the device.
@@ -77,14 +84,14 @@ struct PStat {
 struct BinArgs {
     int dense_max_cols, dense_min_u, force;
     uint64_t heavy, warp_prod;
-    double gdense;  // GLOBAL rows with prod_i >= gdense * gcols take a dense row (0 = none)
-    int64_t gcols;  // width of a dense row: the widest output of the wave
+    double gdense;  // GLOBAL rows with prod_i >= gdense * (their output's width) take a dense row
 };
 
-// A GLOBAL row that accumulates in a dense u64 row of width gcols: its products are at least
-// gdense times that width, so zeroing and scanning the dense row costs little next to them.
-__device__ __forceinline__ bool glob_dense_row(double gdense, uint64_t prod_i, int64_t gcols) {
-    return gdense > 0.0 && (double)prod_i >= gdense * (double)gcols;
+// A GLOBAL row that accumulates in a dense u64 row as wide as its output (ncols): its
+// products are at least gdense times that width, so zeroing and scanning the dense row
+// costs little next to them.
+__device__ __forceinline__ bool glob_dense_row(double gdense, uint64_t prod_i, int64_t ncols) {
+    return gdense > 0.0 && (double)prod_i >= gdense * (double)ncols;
 }
 
 // Per-bin tallies of one pass over the wave: rows, X entries, Gustavson products, output
@@ -93,6 +100,7 @@ struct BinTally {
     uint32_t counts[NBINS];
     unsigned long long xent[NBINS], prods[NBINS], outn[NBINS], bytes[NBINS];
     uint32_t gdense;  // GLOBAL rows that qualify for a dense row
+    unsigned long long gd_cols, gb_cols;  // widest output among them, and among the other GLOBAL rows
 };
 
 static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed by several blocks
@@ -198,9 +206,13 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
 
 // The queued long rows: row r is shared by ceil(len / LONGCH) consecutive blocks (modulo
 // the grid) starting at a block that depends on r, so long rows spread over the grid and a
-// row only as long as a few chunks does not make every block stop at it.
+// row only as long as a few chunks does not make every block stop at it. Each X entry's
+// masked Y-row length and Y-row start are kept (xl, xs at the entry's wave slot): a long
+// row is usually split over blocks later, and its product walk then reads them in order
+// instead of looking them up again.
 __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
-                               const uint32_t *long_rows, const uint32_t *long_nb, const uint32_t *n_long) {
+                               const uint32_t *long_rows, const uint32_t *long_nb, const uint32_t *n_long,
+                               int64_t *xl, int64_t *xs, int64_t xcap) {
     __shared__ unsigned long long red[32];
     __shared__ double redx[32];
     const uint32_t n = *n_long;
@@ -214,9 +226,47 @@ __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
         const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
+        const int32_t *__restrict__ xci = P.X.ci;
+        const uint64_t *__restrict__ xv = P.X.val;
+        const int64_t *__restrict__ yrp = P.Y.rp;
+        const uint32_t *__restrict__ km = P.km;
         uint64_t s = 0;
         double x = 0.0;
-        row_sums(P, b + off * (int64_t)blockDim.x + threadIdx.x, e, nb * (int64_t)blockDim.x, s, x);
+        const int64_t st = nb * (int64_t)blockDim.x;
+        int64_t p = b + off * (int64_t)blockDim.x + threadIdx.x;
+        // four entries' gathers in flight at a time
+        for (; p + 3 * st < e; p += 4 * st) {
+            int32_t k[4];
+            int64_t y0[4], y1[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + u * st);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                y0[u] = __ldg(yrp + k[u]);
+                y1[u] = __ldg(yrp + k[u] + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t len = bit_of(km, (uint32_t)k[u]) ? y1[u] - y0[u] : 0;
+                s += (uint64_t)len;
+                x += xv ? (double)__ldg(xv + p + u * st) : 1.0;
+                if (xl && P.xe0 + p + u * st < xcap) {
+                    xl[P.xe0 + p + u * st] = len;
+                    xs[P.xe0 + p + u * st] = y0[u];
+                }
+            }
+        }
+        for (; p < e; p += st) {
+            const int32_t k = __ldg(xci + p);
+            const int64_t y0 = __ldg(yrp + k);
+            const int64_t len = bit_of(km, (uint32_t)k) ? __ldg(yrp + k + 1) - y0 : 0;
+            s += (uint64_t)len;
+            x += xv ? (double)__ldg(xv + p) : 1.0;
+            if (xl && P.xe0 + p < xcap) {
+                xl[P.xe0 + p] = len;
+                xs[P.xe0 + p] = y0;
+            }
+        }
         for (int d = 16; d; d >>= 1) {
             s += __shfl_xor_sync(FULL, s, d);
             x += __shfl_xor_sync(FULL, x, d);
@@ -283,7 +333,12 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
                 b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.warp_prod, ba.force);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
                 atomicAdd(&hc[b], 1u);
-                if (b == B_GLOBAL && glob_dense_row(ba.gdense, s, ba.gcols)) atomicAdd(&hd, 1u);
+                if (b == B_GLOBAL) {
+                    // dense-row and bitmap scratch are as wide as the widest output of each kind
+                    const bool d = glob_dense_row(ba.gdense, s, P.Y.ncols);
+                    if (d) atomicAdd(&hd, 1u);
+                    atomicMax(d ? &tally->gd_cols : &tally->gb_cols, (unsigned long long)P.Y.ncols);
+                }
                 atomicAdd(&hx[b], xe);
                 atomicAdd(&hp[b], (unsigned long long)s);
                 // symbolic bytes: X row pointers + nnz write, per X entry its column id and the
@@ -442,6 +497,7 @@ struct PassArgs {
     const uint32_t *counts, *offsets;
     int64_t *nnz;    // symbolic: nnz per wave row; numeric: the wave row pointers
     PStat *ps;       // per-product error words live here
+    unsigned *pool_head;  // work queue of the pooled pass (zeroed before its launch)
 };
 
 // The row a bin entry stands for.
@@ -461,6 +517,25 @@ struct RowRef {
     __device__ __forceinline__ int64_t out_len(const PassArgs &a) const { return a.nnz[g + 1] - a.nnz[g]; }
 };
 
+// One row of each shared-memory bin. The per-bin kernels below loop over their bin's rows
+// with these; the pooled pass (k_bins_pool) calls them for the tiles it takes from a queue.
+
+// Warp-hash symbolic: one warp counts the distinct columns of a row in a T-slot set.
+template <int T>
+__device__ __forceinline__ void sym_warp_row(const PassArgs &a, uint32_t entry, Stage *sg, uint32_t *keys, int lane) {
+    const RowRef R(a, entry);
+    const Prod P = *R.P;
+    for (int s = lane; s < T; s += 32) keys[s] = EMPTY;
+    __syncwarp();
+    int c = 0;
+    uint32_t *err = R.err(a);
+    for_each_product<32, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane, err,
+                                [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
+    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+    if (lane == 0) a.nnz[R.g] = c;
+    __syncwarp();
+}
+
 template <int T, int W>
 __global__ void __launch_bounds__(W * 32) k_sym_warp(PassArgs a, int bin) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -468,19 +543,52 @@ __global__ void __launch_bounds__(W * 32) k_sym_warp(PassArgs a, int bin) {
     Stage *sg = (Stage *)smem + wid * 32;
     uint32_t *keys = (uint32_t *)((Stage *)smem + W * 32) + wid * T;
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
-        const RowRef R(a, a.list[base + r]);
-        const Prod P = *R.P;
-        for (int s = lane; s < T; s += 32) keys[s] = EMPTY;
+    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) sym_warp_row<T>(a, a.list[base + r], sg, keys, lane);
+}
+
+// Warp-hash numeric: one warp sums a row's counts in a T-slot map, then compacts and sorts it.
+template <int T>
+__device__ __forceinline__ void num_warp_row(const PassArgs &a, uint32_t entry, Stage *sg, unsigned long long *vals,
+                                             uint32_t *keys, int lane) {
+    const RowRef R(a, entry);
+    const Prod P = *R.P;
+    uint32_t *err = R.err(a);
+    for (int s = lane; s < T; s += 32) {
+        keys[s] = EMPTY;
+        vals[s] = 0;
+    }
+    __syncwarp();
+    for_each_product<32, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane, err,
+                               [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
+    __syncwarp();
+    // compact occupied slots to the front (in place: writes never pass the read point)
+    int n = 0;
+    for (int s0 = 0; s0 < T; s0 += 32) {
+        const uint32_t k = keys[s0 + lane];
+        const unsigned long long v = vals[s0 + lane];
+        const unsigned bal = __ballot_sync(FULL, k != EMPTY);
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
         __syncwarp();
-        int c = 0;
-        uint32_t *err = R.err(a);
-        for_each_product<32, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane,
-                                    err, [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
-        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
-        if (lane == 0) a.nnz[R.g] = c;
+        if (k != EMPTY) {
+            keys[pos] = k;
+            vals[pos] = v;
+        }
+        n += __popc(bal);
         __syncwarp();
     }
+    int Pn = 1;
+    while (Pn < n) Pn <<= 1;
+    for (int s = n + lane; s < Pn; s += 32) keys[s] = EMPTY;
+    __syncwarp();
+    bitonic<32>(keys, vals, Pn, lane);
+    const int64_t o = R.out_off(a), len = R.out_len(a);
+    if (lane == 0 && len != n) atomicOr(err, ERR_COUNT);
+    const int m = (int)min((int64_t)n, len);
+    for (int s = lane; s < m; s += 32) {
+        P.ci[o + s] = (int32_t)keys[s];
+        P.val[o + s] = vals[s];
+    }
+    __syncwarp();
 }
 
 template <int T, int W>
@@ -491,47 +599,28 @@ __global__ void __launch_bounds__(W * 32) k_num_warp(PassArgs a, int bin) {
     unsigned long long *vals = (unsigned long long *)((Stage *)smem + W * 32) + wid * T;
     uint32_t *keys = (uint32_t *)((unsigned long long *)((Stage *)smem + W * 32) + W * T) + wid * T;
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W) {
-        const RowRef R(a, a.list[base + r]);
-        const Prod P = *R.P;
-        uint32_t *err = R.err(a);
-        for (int s = lane; s < T; s += 32) {
-            keys[s] = EMPTY;
-            vals[s] = 0;
-        }
-        __syncwarp();
-        for_each_product<32, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, nullptr, nullptr, lane, err,
-                                   [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
-        __syncwarp();
-        // compact occupied slots to the front (in place: writes never pass the read point)
-        int n = 0;
-        for (int s0 = 0; s0 < T; s0 += 32) {
-            const uint32_t k = keys[s0 + lane];
-            const unsigned long long v = vals[s0 + lane];
-            const unsigned bal = __ballot_sync(FULL, k != EMPTY);
-            const int pos = n + __popc(bal & ((1u << lane) - 1u));
-            __syncwarp();
-            if (k != EMPTY) {
-                keys[pos] = k;
-                vals[pos] = v;
-            }
-            n += __popc(bal);
-            __syncwarp();
-        }
-        int Pn = 1;
-        while (Pn < n) Pn <<= 1;
-        for (int s = n + lane; s < Pn; s += 32) keys[s] = EMPTY;
-        __syncwarp();
-        bitonic<32>(keys, vals, Pn, lane);
-        const int64_t o = R.out_off(a), len = R.out_len(a);
-        if (lane == 0 && len != n) atomicOr(err, ERR_COUNT);
-        const int m = (int)min((int64_t)n, len);
-        for (int s = lane; s < m; s += 32) {
-            P.ci[o + s] = (int32_t)keys[s];
-            P.val[o + s] = vals[s];
-        }
-        __syncwarp();
-    }
+    for (uint32_t r = blockIdx.x * W + wid; r < cnt; r += gridDim.x * W)
+        num_warp_row<T>(a, a.list[base + r], sg, vals, keys, lane);
+}
+
+// Block-hash symbolic: one block counts the distinct columns of a row in a T-slot set.
+template <int T, int NT>
+__device__ __forceinline__ void sym_block_row(const PassArgs &a, uint32_t entry, Stage *sg, uint32_t *keys,
+                                              int64_t *warp_sums, int64_t *gtot, int *cnt_s) {
+    const RowRef R(a, entry);
+    const Prod P = *R.P;
+    uint32_t *err = R.err(a);
+    for (int s = threadIdx.x; s < T; s += NT) keys[s] = EMPTY;
+    if (threadIdx.x == 0) *cnt_s = 0;
+    __syncthreads();
+    int c = 0;
+    for_each_product<NT, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, gtot, warp_sums, threadIdx.x,
+                                err, [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
+    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt_s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) a.nnz[R.g] = *cnt_s;
+    __syncthreads();
 }
 
 template <int T, int NT>
@@ -543,23 +632,59 @@ __global__ void __launch_bounds__(NT) k_sym_block(PassArgs a, int bin) {
     Stage *sg = (Stage *)smem;
     uint32_t *keys = (uint32_t *)(sg + NT);
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
-        const RowRef R(a, a.list[base + r]);
-        const Prod P = *R.P;
-        uint32_t *err = R.err(a);
-        for (int s = threadIdx.x; s < T; s += NT) keys[s] = EMPTY;
-        if (threadIdx.x == 0) cnt_s = 0;
-        __syncthreads();
-        int c = 0;
-        for_each_product<NT, false>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
-                                    threadIdx.x, err,
-                                    [&](uint32_t j, uint64_t) { c += hset_insert(keys, T - 1, j, err); });
-        for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(FULL, c, d);
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt_s, c);
-        __syncthreads();
-        if (threadIdx.x == 0) a.nnz[R.g] = cnt_s;
-        __syncthreads();
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x)
+        sym_block_row<T, NT>(a, a.list[base + r], sg, keys, warp_sums, &gtot, &cnt_s);
+}
+
+// Block-hash numeric: one block sums a row's counts in a T-slot map, compacts and sorts it.
+template <int T, int NT>
+__device__ __forceinline__ void num_block_row(const PassArgs &a, uint32_t entry, Stage *sg, unsigned long long *vals,
+                                              uint32_t *keys, int64_t *warp_sums, int64_t *gtot) {
+    constexpr int PER = T / NT;  // slots per thread in the compaction
+    const RowRef R(a, entry);
+    const Prod P = *R.P;
+    uint32_t *err = R.err(a);
+    for (int s = threadIdx.x; s < T; s += NT) {
+        keys[s] = EMPTY;
+        vals[s] = 0;
     }
+    __syncthreads();
+    for_each_product<NT, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, gtot, warp_sums,
+                               threadIdx.x, err,
+                               [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
+    __syncthreads();
+    uint32_t k[PER];
+    unsigned long long v[PER];
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < PER; u++) {
+        k[u] = keys[threadIdx.x * PER + u];
+        v[u] = vals[threadIdx.x * PER + u];
+        c += k[u] != EMPTY;
+    }
+    int64_t pos = block_excl_scan<NT>(c, warp_sums, gtot);
+    const int n = (int)*gtot;
+#pragma unroll
+    for (int u = 0; u < PER; u++)
+        if (k[u] != EMPTY) {
+            keys[pos] = k[u];
+            vals[pos] = v[u];
+            pos++;
+        }
+    int Pn = 1;
+    while (Pn < n) Pn <<= 1;
+    __syncthreads();
+    for (int s = n + threadIdx.x; s < Pn; s += NT) keys[s] = EMPTY;
+    __syncthreads();
+    bitonic<NT>(keys, vals, Pn, threadIdx.x);
+    const int64_t o = R.out_off(a), len = R.out_len(a);
+    if (threadIdx.x == 0 && len != n) atomicOr(err, ERR_COUNT);
+    const int m = (int)min((int64_t)n, len);
+    for (int s = threadIdx.x; s < m; s += NT) {
+        P.ci[o + s] = (int32_t)keys[s];
+        P.val[o + s] = vals[s];
+    }
+    __syncthreads();
 }
 
 template <int T, int NT>
@@ -567,57 +692,12 @@ __global__ void __launch_bounds__(NT) k_num_block(PassArgs a, int bin) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t gtot;
-    constexpr int PER = T / NT;  // slots per thread in the compaction
     Stage *sg = (Stage *)smem;
     unsigned long long *vals = (unsigned long long *)(sg + NT);
     uint32_t *keys = (uint32_t *)(vals + T);
     const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
-    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x) {
-        const RowRef R(a, a.list[base + r]);
-        const Prod P = *R.P;
-        uint32_t *err = R.err(a);
-        for (int s = threadIdx.x; s < T; s += NT) {
-            keys[s] = EMPTY;
-            vals[s] = 0;
-        }
-        __syncthreads();
-        for_each_product<NT, true>(P.X, P.Y, P.km, P.cm, P.X.rp[R.i], P.X.rp[R.i + 1], sg, &gtot, warp_sums,
-                                   threadIdx.x, err,
-                                   [&](uint32_t j, uint64_t v) { hmap_add(keys, vals, T - 1, j, v, err); });
-        __syncthreads();
-        uint32_t k[PER];
-        unsigned long long v[PER];
-        int c = 0;
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            k[u] = keys[threadIdx.x * PER + u];
-            v[u] = vals[threadIdx.x * PER + u];
-            c += k[u] != EMPTY;
-        }
-        int64_t pos = block_excl_scan<NT>(c, warp_sums, &gtot);
-        const int n = (int)gtot;
-#pragma unroll
-        for (int u = 0; u < PER; u++)
-            if (k[u] != EMPTY) {
-                keys[pos] = k[u];
-                vals[pos] = v[u];
-                pos++;
-            }
-        int Pn = 1;
-        while (Pn < n) Pn <<= 1;
-        __syncthreads();
-        for (int s = n + threadIdx.x; s < Pn; s += NT) keys[s] = EMPTY;
-        __syncthreads();
-        bitonic<NT>(keys, vals, Pn, threadIdx.x);
-        const int64_t o = R.out_off(a), len = R.out_len(a);
-        if (threadIdx.x == 0 && len != n) atomicOr(err, ERR_COUNT);
-        const int m = (int)min((int64_t)n, len);
-        for (int s = threadIdx.x; s < m; s += NT) {
-            P.ci[o + s] = (int32_t)keys[s];
-            P.val[o + s] = vals[s];
-        }
-        __syncthreads();
-    }
+    for (uint32_t r = blockIdx.x; r < cnt; r += gridDim.x)
+        num_block_row<T, NT>(a, a.list[base + r], sg, vals, keys, warp_sums, &gtot);
 }
 
 template <int NT>
@@ -695,6 +775,101 @@ __global__ void __launch_bounds__(NT) k_num_dense(PassArgs a, int bin) {
     }
 }
 
+// ------------------------------------------------------------------ pooled shared-memory pass
+
+// One persistent launch for the warp-hash bins and the 2048-slot block-hash bin of a pass:
+// its blocks (256 threads, as many as fit on the SMs) take tiles from a device queue --
+// largest tables first -- until every row of those bins is done: a block-hash tile is one
+// row for the whole block, a warp-hash tile one row per warp (8 warps, or 4 for the 512-
+// and 1024-slot tables, whose shared memory then stays at the size of the per-bin kernel).
+// It replaces up to seven launches per pass and lets the bins' rows share the SMs instead
+// of running one bin after the other. The bins' row counts are read on the device, so one
+// launch shape serves every wave (and a captured graph of it every replay).
+static constexpr int POOL_BINS = 7;
+__constant__ int8_t c_pool_order[POOL_BINS] = {B_K2048, B_W1024, B_W512, B_W256, B_W128, B_W64, B_W32};
+
+__host__ __device__ __forceinline__ bool pool_bin(int b) { return b <= B_K2048; }
+__host__ __device__ __forceinline__ int pool_warps(int b) { return b >= B_W512 ? 4 : 8; }
+__host__ __device__ __forceinline__ int pool_rows_per_tile(int b) { return b == B_K2048 ? 1 : pool_warps(b); }
+// shared memory a bin needs in the pooled kernel
+__host__ __device__ __forceinline__ size_t pool_smem(int b, bool numeric) {
+    const size_t stage = sizeof(Stage);
+    if (b == B_K2048) return 256 * stage + (size_t)2048 * (numeric ? 12 : 4);
+    const size_t T = (size_t)32 << b, W = (size_t)pool_warps(b);
+    return W * 32 * stage + W * T * (numeric ? 12 : 4);
+}
+
+template <bool NUM>
+__global__ void __launch_bounds__(256) k_bins_pool(PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t gtot;
+    __shared__ int cnt_s;
+    __shared__ uint32_t s_start[POOL_BINS + 1];
+    __shared__ uint32_t s_tile;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < POOL_BINS; k++) {
+            s_start[k] = acc;
+            const int b = c_pool_order[k];
+            const uint32_t rpt = (uint32_t)pool_rows_per_tile(b);
+            acc += (a.counts[b] + rpt - 1) / rpt;
+        }
+        s_start[POOL_BINS] = acc;
+    }
+    __syncthreads();
+    const uint32_t total = s_start[POOL_BINS];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.pool_head, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        __syncthreads();  // every thread has the tile before thread 0 takes the next
+        if (t >= total) break;
+        int k = 0;
+        while (t >= s_start[k + 1]) k++;
+        const int b = c_pool_order[k];
+        const uint32_t lt = t - s_start[k];
+        const uint32_t cnt = a.counts[b], base = a.offsets[b];
+        if (b == B_K2048) {
+            Stage *sg = (Stage *)smem;
+            if (!NUM) {
+                sym_block_row<2048, 256>(a, a.list[base + lt], sg, (uint32_t *)(sg + 256), warp_sums, &gtot, &cnt_s);
+            } else {
+                unsigned long long *vals = (unsigned long long *)(sg + 256);
+                num_block_row<2048, 256>(a, a.list[base + lt], sg, vals, (uint32_t *)(vals + 2048), warp_sums, &gtot);
+            }
+        } else {
+            const int W = pool_warps(b);
+            const uint32_t r = lt * (uint32_t)W + (uint32_t)wid;
+            if (wid < W && r < cnt) {
+                Stage *sg = (Stage *)smem + wid * 32;
+                unsigned char *tab = (unsigned char *)((Stage *)smem + W * 32);
+                switch (b) {
+#define POOL_WARP(BIN, T)                                                                                   \
+    case BIN:                                                                                               \
+        if (!NUM)                                                                                           \
+            sym_warp_row<T>(a, a.list[base + r], sg, (uint32_t *)tab + wid * T, lane);                       \
+        else                                                                                                \
+            num_warp_row<T>(a, a.list[base + r], sg, (unsigned long long *)tab + wid * T,                    \
+                            (uint32_t *)((unsigned long long *)tab + W * T) + wid * T, lane);               \
+        break;
+                    POOL_WARP(B_W32, 32)
+                    POOL_WARP(B_W64, 64)
+                    POOL_WARP(B_W128, 128)
+                    POOL_WARP(B_W256, 256)
+                    POOL_WARP(B_W512, 512)
+                    POOL_WARP(B_W1024, 1024)
+#undef POOL_WARP
+                    default:
+                        break;
+                }
+            }
+        }
+        __syncthreads();  // the tables are reused by the next tile
+    }
+}
+
 // ------------------------------------------------------------------ GLOBAL bin: split rows
 
 // Heavy rows and rows too wide for a shared-memory table. Each row's Gustavson products,
@@ -729,6 +904,7 @@ struct GlobArgs {
     const int64_t *item_off;  // R+1 work-item offsets
     const int64_t *xbase;     // R+1 offsets of each row's X entries in xoff
     const int64_t *xoff;      // per X entry of a GLOBAL row: global product offset
+    const int64_t *ys;        // per X entry of a GLOBAL row: its Y row's start
     const uint64_t *prod;     // prod_i per wave row
     int64_t r0, r1;           // rows of this round
     uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
@@ -744,11 +920,11 @@ struct GlobArgs {
 // dense slots: their bin is marked B_GDENSE until the numeric binning, and the symbolic
 // pass's byte tally gains the X and Y values they read there.
 __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const uint32_t *src, int64_t R,
-                             const uint64_t *prod, double gdense, int64_t gcols, int64_t nd, uint32_t *dst,
+                             const uint64_t *prod, double gdense, int64_t nd, uint32_t *dst,
                              uint32_t *cnt, int8_t *bin, BinTally *tally) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t gr = src[r];
-        if (!glob_dense_row(gdense, prod[gr], gcols)) {
+        if (!glob_dense_row(gdense, prod[gr], prods[rowprod[gr]].Y.ncols)) {
             dst[R - 1 - atomicAdd(cnt + 1, 1u)] = gr;
             continue;
         }
@@ -777,20 +953,93 @@ __global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const u
 
 // The masked Y-row length of every X entry of every GLOBAL row, as one flat array (row r's
 // entries start at xbase[r]); a device-wide exclusive scan then gives each entry's global
-// product offset.
-__global__ void k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R, const int64_t *xbase, int64_t *xoff) {
+// product offset. Beside it, ys keeps each entry's Y-row start, so the product walks read
+// both in order. Entries of long rows take both from the row-work pass (xl, xs); the
+// others look them up. A block takes XCH consecutive entries at a time: it finds the rows
+// they belong to once (usually one or two) and keeps each row's pointers in shared memory.
+static constexpr int64_t XCH = 2048;  // entries per block iteration
+static constexpr int XSEG = 64;       // rows per iteration kept in shared memory
+
+__global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R,
+                                                   const int64_t *__restrict__ xbase, const int64_t *__restrict__ xl,
+                                                   const int64_t *__restrict__ xs, int64_t *__restrict__ xoff,
+                                                   int64_t *__restrict__ ys) {
+    struct Seg {
+        const int32_t *xci;
+        const int64_t *yrp;
+        const uint32_t *km;
+        int64_t e0;  // first entry of the row in the flat array, minus the row's start in X.ci
+        int64_t xe;  // the row's first wave entry slot (xl, xs), minus its first flat entry
+        int lng;     // a long row: its lengths and Y starts were kept by the row-work pass
+    };
+    __shared__ Seg seg[XSEG];
+    __shared__ int64_t s_lo[XSEG + 1];
+    __shared__ int64_t s_r0;
+    __shared__ int s_n;
     const int64_t xtot = xbase[R];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < xtot; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = R - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
+    for (int64_t c0 = blockIdx.x * XCH; c0 < xtot; c0 += (int64_t)gridDim.x * XCH) {
+        const int64_t c1 = min(xtot, c0 + XCH);
+        if (threadIdx.x == 0) {
+            int64_t lo = 0, hi = R - 1;  // the row of entry c0: the last r with xbase[r] <= c0
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (xbase[mid] <= c0) lo = mid; else hi = mid - 1;
+            }
+            int64_t r1 = lo;  // the row of entry c1 - 1
+            hi = R - 1;
+            while (r1 < hi) {
+                const int64_t mid = (r1 + hi + 1) >> 1;
+                if (xbase[mid] <= c1 - 1) r1 = mid; else hi = mid - 1;
+            }
+            s_r0 = lo;
+            s_n = (int)min((int64_t)XSEG, r1 - lo + 1);
         }
-        const RowRef Rf(a, list[lo]);
-        const Prod P = *Rf.P;
-        const int64_t p = P.X.rp[Rf.i] + (e - xbase[lo]);
-        const int32_t k = __ldg(P.X.ci + p);
-        xoff[e] = bit_of(P.km, (uint32_t)k) ? __ldg(P.Y.rp + k + 1) - __ldg(P.Y.rp + k) : 0;
+        __syncthreads();
+        const int64_t r0 = s_r0;
+        const int n = s_n;
+        if ((int)threadIdx.x < n) {
+            const RowRef Rf(a, list[r0 + threadIdx.x]);
+            const Prod *P = Rf.P;
+            const int64_t xb = P->X.rp[Rf.i], len = P->X.rp[Rf.i + 1] - xb;
+            const int64_t fb = xbase[r0 + threadIdx.x];
+            seg[threadIdx.x] = Seg{P->X.ci, P->Y.rp, P->km, fb - xb, P->xe0 + xb - fb, xl && len > LONGX};
+            s_lo[threadIdx.x] = fb;
+            if ((int)threadIdx.x == n - 1) s_lo[n] = xbase[r0 + n];
+        }
+        __syncthreads();
+        for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+            int64_t len = 0, y0 = 0;
+            if (e < s_lo[n]) {  // within the rows kept in shared memory
+                int l = 0, h = n - 1;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (s_lo[mid] <= e) l = mid; else h = mid - 1;
+                }
+                const Seg &sg = seg[l];
+                if (sg.lng) {
+                    len = xl[sg.xe + e];
+                    y0 = xs[sg.xe + e];
+                } else {
+                    const int32_t k = __ldg(sg.xci + (e - sg.e0));
+                    y0 = __ldg(sg.yrp + k);
+                    if (bit_of(sg.km, (uint32_t)k)) len = __ldg(sg.yrp + k + 1) - y0;
+                }
+            } else {  // more rows in this stretch than shared memory keeps: find the row
+                int64_t lo = r0 + n, hi = R - 1;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg(xbase + mid) <= e) lo = mid; else hi = mid - 1;
+                }
+                const RowRef Rf(a, list[lo]);
+                const Prod *P = Rf.P;
+                const int32_t k = __ldg(P->X.ci + P->X.rp[Rf.i] + (e - xbase[lo]));
+                y0 = __ldg(P->Y.rp + k);
+                if (bit_of(P->km, (uint32_t)k)) len = __ldg(P->Y.rp + k + 1) - y0;
+            }
+            xoff[e] = len;
+            ys[e] = y0;
+        }
+        __syncthreads();
     }
 }
 
@@ -1034,14 +1283,13 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         uint32_t *err = &a.ps[pi].err;
         const bool chk = a.ps[pi].unsafe != 0;  // uniform over the item
         const int64_t row = (int64_t)gr - PP->row0;
-        const int32_t *__restrict__ xci = PP->X.ci;
         const uint64_t *__restrict__ xval = PP->X.val;
-        const int64_t *__restrict__ yrp = PP->Y.rp;
         const int32_t *__restrict__ yci = PP->Y.ci;
         const uint64_t *__restrict__ yval = PP->Y.val;
         const uint32_t *__restrict__ cm = PP->cm;
         const int64_t xb = PP->X.rp[row], xlen = PP->X.rp[row + 1] - xb;
         const int64_t *__restrict__ xo = g.xoff + g.xbase[r];
+        const int64_t *__restrict__ ysr = g.ys + g.xbase[r];
         // product offsets are global across the GLOBAL rows: this row's start at xo[0]
         const int64_t total = __ldg(xo) + (int64_t)g.prod[gr];
         const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
@@ -1124,15 +1372,27 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                 int64_t base = 0;  // Y position of this entry's product f is base + f
                 uint64_t av = 1;
                 if (ok) {
-                    const int32_t kx = __ldg(xci + xb + e);
-                    base = __ldg(yrp + kx) - off;
+                    base = __ldg(ysr + e) - off;
                     if (NUM && xval) av = __ldg(xval + xb + e);
                 }
                 int64_t gend = 0;  // first product after the 32 entries
                 if (lane == 31) gend = e + 1 < xlen ? __ldg(xo + e + 1) : total;
                 gend = __shfl_sync(FULL, gend, 31);
                 const int64_t lim = min(ws1, gend);
-                for (int64_t w = f; w < lim; w += 32) {
+                for (int64_t w = f; w < lim;) {
+                    // the entry holding product w (the last lane whose entry starts at or
+                    // before it) and where the next entry starts: while one entry holds the
+                    // whole window (long Y rows), its lanes read its Y row with no search
+                    const int cur = __popc(__ballot_sync(FULL, off <= w)) - 1;
+                    int64_t nxt = __shfl_sync(FULL, off, min(cur + 1, 31));
+                    if (cur == 31) nxt = gend;
+                    const int64_t run_end = min(nxt, lim);
+                    if (run_end >= w + 32) {  // uniform over the warp; at least one full window
+                        const int64_t b = __shfl_sync(FULL, base, cur);
+                        const uint64_t ax = NUM ? __shfl_sync(FULL, av, cur) : 1ull;
+                        for (; w + 32 <= run_end; w += 32) product(ax, b + w + lane);
+                        continue;
+                    }
                     const int64_t fj = w + lane;
                     // the last lane whose entry starts at or before product fj
                     const int rel = (int)max((int64_t)-1, min(off - w, (int64_t)32));
@@ -1145,6 +1405,7 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                     const int64_t q = __shfl_sync(FULL, base, src) + fj;
                     const uint64_t ax = NUM ? __shfl_sync(FULL, av, src) : 1ull;
                     if (fj < lim) product(ax, q);
+                    w += 32;
                 }
                 f = max(f, lim);
                 p += 32;
@@ -1339,8 +1600,38 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
     const bool numeric = pass == 1;
     const int sms = tun.sm_count;
     const size_t stage = sizeof(Stage);
+    // the pooled kernel for the warp-hash and 2048-slot bins (tun.pool), sized to the largest
+    // table among them that this pass uses
+    bool pooled = false;
+    if (tun.pool) {
+        size_t smem = 0;
+        for (int b = 0; b < B_GLOBAL; b++)
+            if (pool_bin(b) && host_counts[b]) smem = std::max(smem, pool_smem(b, numeric));
+        if (smem) {
+            pooled = true;
+            if (prof && prof->on) {
+                prof->pool_ran[pass] = true;
+                cudaEventRecordWithFlags(prof->pev[pass][0], s, g_capturing ? cudaEventRecordExternal : 0);
+            }
+            auto kern = numeric ? k_bins_pool<true> : k_bins_pool<false>;
+            if (smem > 48 * 1024 && !g_capturing)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            if (!g_attrs_only) {
+                cudaMemsetAsync(a.pool_head, 0, sizeof(unsigned), s);
+                kl(kern, (unsigned)(sms * per_sm), 256, smem, s, a);
+            }
+            if (prof && prof->on)
+                cudaEventRecordWithFlags(prof->pev[pass][1], s, g_capturing ? cudaEventRecordExternal : 0);
+        }
+    }
     for (int b = 0; b < B_GLOBAL; b++) {
         if (!host_counts[b]) continue;
+        if (pooled && pool_bin(b)) continue;
         const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[b];
         // inside a capture the records become event-record nodes, so replays time the bins
         if (prof && prof->on) cudaEventRecordWithFlags(prof->ev[pass][b][0], s, g_capturing ? cudaEventRecordExternal : 0);
@@ -1460,8 +1751,15 @@ static void run_pass_graph(int pass, const PassArgs &a, const uint32_t *host_cou
 
 static void prof_collect(Prof *prof, int pass, const BinTally &t) {
     if (!prof || !prof->on) return;
+    const bool pooled = prof->pool_ran[pass];
+    prof->pool_ran[pass] = false;
     for (int b = 0; b < NBINS; b++) {
         if (!t.counts[b]) continue;
+        if (pooled && pool_bin(b)) {  // timed as one launch below
+            prof->pool[pass].bytes += (double)t.bytes[b];
+            prof->pool[pass].prods += (double)t.prods[b];
+            continue;
+        }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, prof->ev[pass][b][0], prof->ev[pass][b][1]) != cudaSuccess) {
             cudaGetLastError();
@@ -1473,6 +1771,15 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
         k.bytes += (double)t.bytes[b];
         k.prods += (double)t.prods[b];
     }
+    if (pooled) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof->pev[pass][0], prof->pev[pass][1]) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        prof->pool[pass].launches++;
+        prof->pool[pass].ms += ms;
+    }
 }
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1482,8 +1789,9 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // [nd, R) take bitmap rounds.
 struct Glob {
     int64_t R = 0, nw = 0, per_round = 0, rounds = 0, nd = 0, dcols = 0;
+    int64_t nwd = 0;  // bitmap words per dense-row slot
     uint32_t *list = nullptr;  // the bin's rows, dense-row candidates first
-    int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr;
+    int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr, *ys = nullptr;
     const uint64_t *prod = nullptr;
     uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
@@ -1495,7 +1803,7 @@ struct Glob {
 // numeric pass's size check), chunk ranks.
 static void glob_rank(const Glob &g, const PassArgs &a, const GlobArgs &ga, int numeric, unsigned grid,
                       cudaStream_t s) {
-    const int64_t nch = (g.nw + RCH - 1) / RCH;
+    const int64_t nch = (ga.nw + RCH - 1) / RCH;
     const int64_t chunks = (ga.r1 - ga.r0) * nch;
     const unsigned gc = (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)grid * 2));
     kl(k_glob_csum, gc, GNT, 0, s, ga, nch, g.csum);
@@ -1509,6 +1817,7 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
     if (g.item_off) al.free(g.item_off, s);
     if (g.xbase) al.free(g.xbase, s);
     if (g.xoff) al.free(g.xoff, s);
+    if (g.ys) al.free(g.ys, s);
     if (g.bmr) al.free(g.bmr, s);
     if (g.dbmr) al.free(g.dbmr, s);
     if (g.dval) al.free(g.dval, s);
@@ -1539,12 +1848,13 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
         // the bitmap pass at 6 blocks per SM (40 registers), the count-adding passes at
         // lbs_occ (4: 64 registers; 6 spills a few values of the shuffle walk)
         const int lo = MODE == G_SYM || tun.lbs_occ >= 6 ? 6 : 4;
+        const unsigned g = (unsigned)(tun.sm_count * lo);
         if (lo == 6) {
-            if (tun.combine) kl(k_glob_lbs<MODE, true, 6>, (unsigned)(tun.sm_count * 6), GNT, 0, s, a, ga);
-            else kl(k_glob_lbs<MODE, false, 6>, (unsigned)(tun.sm_count * 6), GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_lbs<MODE, true, 6>, g, GNT, 0, s, a, ga);
+            else kl(k_glob_lbs<MODE, false, 6>, g, GNT, 0, s, a, ga);
         } else {
-            if (tun.combine) kl(k_glob_lbs<MODE, true, 4>, (unsigned)(tun.sm_count * 4), GNT, 0, s, a, ga);
-            else kl(k_glob_lbs<MODE, false, 4>, (unsigned)(tun.sm_count * 4), GNT, 0, s, a, ga);
+            if (tun.combine) kl(k_glob_lbs<MODE, true, 4>, g, GNT, 0, s, a, ga);
+            else kl(k_glob_lbs<MODE, false, 4>, g, GNT, 0, s, a, ga);
         }
     } else {
         GLOB_SET_VARIANT(k_glob_set)
@@ -1557,9 +1867,9 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, 0, g.nd, g.dbmr, g.nw, tun.short_walk,
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys, g.prod, 0, g.nd, g.dbmr, g.nwd, tun.short_walk,
                           tun.seg_walk, g.dval, g.dcols};
-        const int64_t words = g.nd * g.nw;
+        const int64_t words = g.nd * g.nwd;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
             glob_set<G_DENSE>(tun, s, a, ga);
@@ -1572,7 +1882,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         }
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bmr,
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bmr,
                           g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
@@ -1603,13 +1913,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         uint32_t offsets[NBINS + 1];
         uint32_t cursors[NBINS];
         uint32_t n_long;
+        unsigned pool_head;  // the pooled pass's work queue
     };
     std::vector<Prod> hp(w);
     std::vector<int64_t> row0s(w + 1, 0);
-    int64_t dense_cols = 0, max_cols = 0;
+    int64_t dense_cols = 0, max_cols = 0, xe_total = 0;
     for (int p = 0; p < w; p++) {
         const WaveIn &x = in[p];
         Prod &P = hp[p];
+        P.xe0 = xe_total;
+        xe_total += x.X.nnz;
         P.X = x.X;
         P.Y = x.Y;
         P.rm = x.rm;
@@ -1655,14 +1968,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_ps = align256(o_row0s + (size_t)(wcp + 1) * 8);
     const size_t o_small = align256(o_ps + sizeof(PStat) * wcp);
     const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
-    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod, tun.glob_dense,
-                     max_cols};
+    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod, tun.glob_dense};
     int rc = MP_OK;
     Glob gl;
     PassArgs pa{};
     Small h_sym, h_num;
     std::vector<PStat> hps(w);
     std::vector<int64_t> reserved(w, 0);  // budget bytes charged for each product's result
+    // per X entry of the long rows: masked Y-row length and Y-row start (only when a row
+    // can be long; slots by the entry's position in the wave)
+    int64_t *xl = nullptr, *xs = nullptr;
     auto unreserve = [&](int p) {
         if (bud && reserved[p]) bud->unreserve(reserved[p]);
         reserved[p] = 0;
@@ -1687,6 +2002,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     Small *sm_sym = (Small *)(ws + o_small);
     Small *sm_num = sm_sym + 1;
     auto fail = [&](int code) {
+        if (xl) al.free(xl, s);
+        if (xs) al.free(xs, s);
         for (int p = 0; p < w; p++) {
             unreserve(p);
             if (hp[p].rp) al.free(hp[p].rp, s);
@@ -1714,6 +2031,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         !cuda_ok(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s), "memset"))
         return fail(MP_ERR_CUDA);
 
+    if (!symbolic_only && xe_total > LONGX) {
+        xl = (int64_t *)al.alloc((size_t)xe_total * 8, s);
+        xs = (int64_t *)al.alloc((size_t)xe_total * 8, s);
+        if (!xl || !xs) return fail(MP_ERR_NOMEM);
+    }
     pa.prods = dprods;
     pa.rowprod = rowprod;
     pa.list = list;
@@ -1726,7 +2048,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
         kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, long_nb, &sm_sym->n_long);
         kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum,
-           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long);
+           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long, xl, xs,
+           xe_total);
         kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, M, ba, bin, grp, &sm_sym->tally,
            ps);
         kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
@@ -1737,15 +2060,19 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         return fail(MP_ERR_CUDA);
     pa.counts = sm_sym->tally.counts;
     pa.offsets = sm_sym->offsets;
+    pa.pool_head = &sm_sym->pool_head;
     // GLOBAL bin set-up: its rows, work items, product offsets, bitmap rounds
     gl.R = h_sym.tally.counts[B_GLOBAL];
     if (gl.R) {
-        gl.nw = (max_cols + 31) / 32;
-        // dense rows: as many of the qualifying rows as the dense scratch holds at once
+        // dense rows: as many of the qualifying rows as the dense scratch holds at once, each
+        // slot as wide as the widest output among them; bitmap slots as wide as the widest
+        // output among the rows that take bitmap rounds
         const int64_t nd_all = std::min<int64_t>(gl.R, (int64_t)h_sym.tally.gdense);
-        gl.dcols = max_cols;
-        const uint64_t dslot = (uint64_t)gl.dcols * 8 + (uint64_t)gl.nw * 8;
-        gl.nd = std::min<int64_t>(nd_all, (int64_t)(tun.dense_scratch_cap / dslot));
+        gl.dcols = nd_all ? (int64_t)h_sym.tally.gd_cols : 0;
+        gl.nwd = (gl.dcols + 31) / 32;
+        const uint64_t dslot = (uint64_t)gl.dcols * 8 + (uint64_t)gl.nwd * 8;
+        gl.nd = nd_all ? std::min<int64_t>(nd_all, (int64_t)(tun.dense_scratch_cap / dslot)) : 0;
+        gl.nw = (std::max<int64_t>((int64_t)h_sym.tally.gb_cols, gl.nd < nd_all ? gl.dcols : 0) + 31) / 32;
         const int64_t rb = gl.R - gl.nd;
         const uint64_t cap = tun.scratch_cap ? tun.scratch_cap : (4ull << 30);
         gl.per_round = rb ? std::max<int64_t>(1, std::min<int64_t>(rb, (int64_t)(cap / ((uint64_t)gl.nw * 8)))) : 0;
@@ -1757,19 +2084,20 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xoff = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
-        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff) return fail(MP_ERR_NOMEM);
+        gl.ys = (int64_t *)al.alloc((size_t)(xtot + 1) * 8, s);
+        if (!gl.list || !gl.item_off || !gl.xbase || !gl.xoff || !gl.ys) return fail(MP_ERR_NOMEM);
         if (rb) {
             gl.bmr = (uint2 *)al.alloc((size_t)gl.per_round * gl.nw * 8, s);
             if (!gl.bmr) return fail(MP_ERR_NOMEM);
         }
         if (gl.nd) {
-            gl.dbmr = (uint2 *)al.alloc((size_t)gl.nd * gl.nw * 8, s);
+            gl.dbmr = (uint2 *)al.alloc((size_t)gl.nd * gl.nwd * 8, s);
             gl.dval = (unsigned long long *)al.alloc((size_t)gl.nd * gl.dcols * 8, s);
             if (!gl.dbmr || !gl.dval) return fail(MP_ERR_NOMEM);
         }
         {
-            const int64_t nch = (gl.nw + RCH - 1) / RCH;
-            gl.csum = (int64_t *)al.alloc((size_t)std::max<int64_t>(gl.per_round, gl.nd) * nch * 8 + 8, s);
+            const int64_t nch = (gl.nw + RCH - 1) / RCH, nchd = (gl.nwd + RCH - 1) / RCH;
+            gl.csum = (int64_t *)al.alloc((size_t)std::max<int64_t>(gl.per_round * nch, gl.nd * nchd) * 8 + 8, s);
             if (!gl.csum) return fail(MP_ERR_NOMEM);
         }
         if (nd_all) {
@@ -1779,7 +2107,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             if (!cuda_ok(cudaMemsetAsync(cnt, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
             kl(k_glob_split, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s,
                (const Prod *)dprods, (const int32_t *)rowprod, (const uint32_t *)(list + h_sym.offsets[B_GLOBAL]),
-               gl.R, (const uint64_t *)prod, tun.glob_dense, max_cols, gl.nd, gl.list, cnt, bin, &sm_sym->tally);
+               gl.R, (const uint64_t *)prod, tun.glob_dense, gl.nd, gl.list, cnt, bin, &sm_sym->tally);
         } else if (!cuda_ok(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4,
                                             cudaMemcpyDeviceToDevice, s), "copy")) {
             return fail(MP_ERR_CUDA);
@@ -1788,10 +2116,15 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
            gl.xbase, gl.item_off);
         if (scan_i64(gl.item_off, gl.item_off, gl.R, al, s) || scan_i64(gl.xbase, gl.xbase, gl.R, al, s))
             return fail(MP_ERR_NOMEM);
-        kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(xtot, 256), (int64_t)tun.sm_count * 16)),
-           256, 0, s, pa, gl.list, gl.R, gl.xbase, gl.xoff);
+        kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>((xtot + XCH - 1) / XCH, (int64_t)tun.sm_count * 8)),
+           256, 0, s, pa, (const uint32_t *)gl.list, gl.R, (const int64_t *)gl.xbase, (const int64_t *)xl,
+           (const int64_t *)xs, gl.xoff, gl.ys);
         if (scan_i64(gl.xoff, gl.xoff, xtot, al, s)) return fail(MP_ERR_NOMEM);
     }
+    // the long rows' per-entry lengths and Y starts have served the split-row set-up
+    if (xl) al.free(xl, s);
+    if (xs) al.free(xs, s);
+    xl = xs = nullptr;
     // 2-3. symbolic pass, wave row pointers, per-product row pointers and sizes
     if (M > 0) {
         if (graphs) run_pass_graph(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof, *wc);
@@ -1866,6 +2199,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             return fail(MP_ERR_CUDA);
         pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
+        pa.pool_head = &sm_num->pool_head;
         if (graphs) run_pass_graph(1, pa, h_num.tally.counts, dense_cols, tun, s, prof, *wc);
         else run_pass(1, pa, h_num.tally.counts, dense_cols, tun, s, prof);
         if (gl.R) glob_pass(1, gl, pa, tun, s, prof);

@@ -112,26 +112,27 @@ def test_cache_yields_to_work(c1, cuda_ok):
         assert b["peak"] <= budget and b["held"] == st["bytes"]
     finally:
         e.close()
-    # a budget just above one query's own working set: the first query's cached result
-    # must give way to the second query's work
-    q1 = gen.config1_query()
-    q2 = {"types": list("APTPA"), "constraints": gen._year_on_every(list("APTPA"), "P", 2000, 2015)}
-    need = 0
-    for q in (q1, q2):
-        probe = mp.Engine(c1[0], policy=mp.MP_POLICY_NONE, hbm_budget_bytes=0)
-        try:
-            probe.run(q)
-            need = max(need, mp.mp_budget_stats(probe.ctx)["peak"])
-        finally:
-            probe.close()
-    budget = need + (1 << 20)
+    # a budget twice one query's own working set: once cached results leave less room
+    # than the next query needs, the cache must give some of them up
+    q2 = gen.config1_query()
+    probe = mp.Engine(c1[0], policy=mp.MP_POLICY_NONE, hbm_budget_bytes=0)
+    try:
+        probe.run(q2)
+        need = mp.mp_budget_stats(probe.ctx)["peak"]
+    finally:
+        probe.close()
+    budget = 2 * need
     e = mp.Engine(c1[0], policy=mp.MP_POLICY_ATRAPOS, hbm_budget_bytes=budget)
     try:
-        assert_same(e.run(q1), OC.evaluate(c1[1], q1), "first query")
-        held = mp.mp_cache_stats(e.ctx)["bytes"]
-        assert held > (1 << 20)  # its result is cached
+        for k in range(40):  # fill the cache with other APTPA results (year windows)
+            lo = 1980 + k
+            qk = {"types": list("APTPA"), "constraints": gen._year_on_every(list("APTPA"), "P", lo, lo + 12)}
+            assert_same(e.run(qk), OC.evaluate(c1[1], qk), ("fill", k))
+            if mp.mp_cache_stats(e.ctx)["bytes"] > budget - need:
+                break
+        assert mp.mp_cache_stats(e.ctx)["bytes"] > budget - need  # less room left than q2 needs
         before = mp.mp_cache_stats(e.ctx)["evictions"]
-        assert_same(e.run(q2), OC.evaluate(c1[1], q2), "second query: the cache yields")
+        assert_same(e.run(q2), OC.evaluate(c1[1], q2), "the cache yields")
         assert mp.mp_cache_stats(e.ctx)["evictions"] > before
         assert mp.mp_budget_stats(e.ctx)["peak"] <= budget
     finally:

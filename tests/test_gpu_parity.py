@@ -220,13 +220,13 @@ def test_copy_to_device_buffers(c1, c1_engines):
     np.testing.assert_array_equal(val.cpu().numpy().view(np.uint64), want[2])
 
 
-@pytest.mark.parametrize("combine,short_walk", [(0, 0), (0, 1), (1, 0), (1, 1)])
-def test_split_row_kernel_variants(c1, c2_small, combine, short_walk, monkeypatch):
-    """The split-row (GLOBAL) kernel's variants -- shared-memory combining of hot outputs
-    on or off, one-thread-per-entry walk of short Y rows on or off -- give identical
-    results."""
+@pytest.mark.parametrize("lbs,combine,short_walk", [(1, 0, 0), (1, 1, 0), (0, 0, 0), (0, 0, 1), (0, 1, 0), (0, 1, 1)])
+def test_split_row_kernel_variants(c1, c2_small, lbs, combine, short_walk, monkeypatch):
+    """The split-row (GLOBAL) kernel's variants -- warp-level or block-staged product walk,
+    shared-memory combining of hot outputs on or off, one-thread-per-entry walk of short Y
+    rows on or off (staged walk) -- give identical results."""
     mp = _mp()
-    monkeypatch.setenv("MP_TUNING", f"combine={combine},short_walk={short_walk}")
+    monkeypatch.setenv("MP_TUNING", f"lbs={lbs},combine={combine},short_walk={short_walk}")
     for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()]),
                        (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
         e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
@@ -255,7 +255,7 @@ def test_split_row_dense_rows(c1, c2_small, combine, glob_dense, dense_scratch, 
     scratch runs out, one query at a time and as one batch. (The overflow test above runs
     its forced split rows through dense rows under the default threshold.)"""
     mp = _mp()
-    tune = f"combine={combine},glob_dense={glob_dense},glob_occ={occ},seg_walk={seg_walk}"
+    tune = f"combine={combine},glob_dense={glob_dense},glob_occ={occ},lbs_occ={occ},seg_walk={seg_walk}"
     if dense_scratch:
         tune += f",dense_scratch={dense_scratch}"
     monkeypatch.setenv("MP_TUNING", tune)
@@ -332,5 +332,32 @@ def test_bin_passes_as_graphs(c1, graphs, monkeypatch):
             elif not graphs:
                 assert st == {"captures": 0, "replays": 0}, (force, st)
             # every row forced into the split-row bin leaves no shared-memory pass to capture
+        finally:
+            e.close()
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_pooled_bin_pass(c1, graphs, monkeypatch):
+    """The warp-hash and 2048-slot bins drained by one persistent launch per pass (a device
+    work queue, largest tables first), directly and replayed as graphs, give the oracle's
+    results for every forced bin class, alone and in batches, run twice."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"pool=1,graphs={graphs}")
+    h, o = c1
+    qs = gen.random_queries(h, 41, 14, lengths=(2, 7)) + gen.long_queries(5, 3) + [gen.config1_query()]
+    want = [OC.evaluate(o, q) for q in qs]
+    for force in BIN_CLASSES:
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
+        try:
+            for rnd in range(2):
+                for q, w in zip(qs, want):
+                    assert_same(e.run(q), w, ("pool", graphs, force, rnd, "".join(q["types"])))
+                rc, res = e.run_batch(qs)
+                assert rc == 0
+                for q, g, w in zip(qs, res, want):
+                    assert_same(g, w, ("pool", graphs, force, rnd, "batch", "".join(q["types"])))
+            names = set(mp.mp_kernel_stats(e.ctx)[0])
+            if force in (-1, 0, 1):
+                assert "sym_pool" in names and "num_pool" in names, names
         finally:
             e.close()
