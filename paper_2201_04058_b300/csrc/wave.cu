@@ -149,11 +149,14 @@ __device__ __forceinline__ void row_sums(const Prod &P, int64_t p0, int64_t e, i
     }
 }
 
-// prod_i of every wave row. Each lane takes one of 32 consecutive rows; rows longer than
-// 16 entries are summed by the whole warp, one after the other, and rows longer than
-// LONGX are queued for k_rowwork_long.
+// prod_i of every wave row. Each lane takes one of 32 consecutive rows and sums rows of up
+// to 16 entries itself; longer rows are queued: up to LONGX entries for k_rowwork_mid (one
+// warp per row), beyond that for k_rowwork_long (several blocks per row).
+static constexpr int64_t SHORTX = 16;  // X rows up to this long are summed by one lane
+
 __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, double *xsum,
-                          uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long) {
+                          uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long, uint32_t *mid_rows,
+                          uint32_t *n_mid) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -171,35 +174,91 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         }
         uint64_t s = 0;
         double xs = 0.0;  // the row's sum of X values: x_ik <= xs bounds every product and sum
-        const bool mine = e - b <= 16;
-        if (mine && e > b) row_sums(*P, b, e, 1, s, xs);
+        if (e - b <= SHORTX && e > b) row_sums(*P, b, e, 1, s, xs);
         if (e - b > LONGX) {
             const uint32_t at = atomicAdd(n_long, 1u);
             long_rows[at] = (uint32_t)g;
             long_nb[at] = (uint32_t)((e - b + LONGCH - 1) / LONGCH);  // blocks that share it
         }
-        unsigned coop = __ballot_sync(FULL, !mine && e - b <= LONGX);
-        while (coop) {
-            const int src = __ffs(coop) - 1;
-            coop &= coop - 1;
-            const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
-            const int32_t pi = __shfl_sync(FULL, g < M ? rowprod[g] : 0, src);
-            const Prod &Q = prods[pi];
-            uint64_t c = 0;
-            double cx = 0.0;
-            row_sums(Q, bb + lane, ee, 32, c, cx);
-            for (int d = 16; d; d >>= 1) {
-                c += __shfl_xor_sync(FULL, c, d);
-                cx += __shfl_xor_sync(FULL, cx, d);
+        const bool mid = e - b > SHORTX && e - b <= LONGX;
+        const unsigned mm = __ballot_sync(FULL, mid);
+        if (mm) {  // warp-aggregated append to the mid-row queue
+            const int leader = __ffs(mm) - 1;
+            uint32_t at = 0;
+            if (lane == leader) at = atomicAdd(n_mid, (uint32_t)__popc(mm));
+            at = __shfl_sync(FULL, at, leader);
+            if (mid) mid_rows[at + __popc(mm & ((1u << lane) - 1u))] = (uint32_t)g;
+        }
+        if (g < M && e - b <= SHORTX) {
+            prod[g] = s;
+            xsum[g] = xs;
+        } else if (g < M && e - b > LONGX) {
+            prod[g] = 0;  // k_rowwork_long adds its blocks' sums
+            xsum[g] = 0.0;
+        }
+    }
+}
+
+// The queued mid-length rows, one warp each (all warps of the grid in parallel), with four
+// dependent gathers in flight per lane; each X entry's masked Y-row length and Y-row start
+// are kept (xl, xs at the entry's wave slot) for the product walk.
+__global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
+                              const uint32_t *mid_rows, const uint32_t *n_mid, int64_t *xl, int64_t *xs,
+                              int64_t xcap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *n_mid;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
+        const uint32_t g = mid_rows[r];
+        const Prod &P = prods[rowprod[g]];
+        const int64_t i = g - P.row0;
+        const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
+        const int32_t *__restrict__ xci = P.X.ci;
+        const uint64_t *__restrict__ xv = P.X.val;
+        const int64_t *__restrict__ yrp = P.Y.rp;
+        const uint32_t *__restrict__ km = P.km;
+        uint64_t s = 0;
+        double x = 0.0;
+        int64_t p = b + lane;
+        for (; p + 96 < e; p += 128) {
+            int32_t k[4];
+            int64_t y0[4], y1[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                y0[u] = __ldg(yrp + k[u]);
+                y1[u] = __ldg(yrp + k[u] + 1);
             }
-            if (lane == src) {
-                s = c;
-                xs = cx;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t len = bit_of(km, (uint32_t)k[u]) ? y1[u] - y0[u] : 0;
+                s += (uint64_t)len;
+                x += xv ? (double)__ldg(xv + p + 32 * u) : 1.0;
+                if (xl && P.xe0 + p + 32 * u < xcap) {
+                    xl[P.xe0 + p + 32 * u] = len;
+                    xs[P.xe0 + p + 32 * u] = y0[u];
+                }
             }
         }
-        if (g < M) {
-            prod[g] = (e - b > LONGX) ? 0 : s;
-            xsum[g] = (e - b > LONGX) ? 0.0 : xs;
+        for (; p < e; p += 32) {
+            const int32_t k = __ldg(xci + p);
+            const int64_t y0 = __ldg(yrp + k);
+            const int64_t len = bit_of(km, (uint32_t)k) ? __ldg(yrp + k + 1) - y0 : 0;
+            s += (uint64_t)len;
+            x += xv ? (double)__ldg(xv + p) : 1.0;
+            if (xl && P.xe0 + p < xcap) {
+                xl[P.xe0 + p] = len;
+                xs[P.xe0 + p] = y0;
+            }
+        }
+        for (int d = 16; d; d >>= 1) {
+            s += __shfl_xor_sync(FULL, s, d);
+            x += __shfl_xor_sync(FULL, x, d);
+        }
+        if (lane == 0) {
+            prod[g] = s;
+            xsum[g] = x;
         }
     }
 }
@@ -970,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *l
         const uint32_t *km;
         int64_t e0;  // first entry of the row in the flat array, minus the row's start in X.ci
         int64_t xe;  // the row's first wave entry slot (xl, xs), minus its first flat entry
-        int lng;     // a long row: its lengths and Y starts were kept by the row-work pass
+        int lng;     // a row longer than SHORTX: the row-work pass kept its lengths and Y starts
     };
     __shared__ Seg seg[XSEG];
     __shared__ int64_t s_lo[XSEG + 1];
@@ -1002,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *l
             const Prod *P = Rf.P;
             const int64_t xb = P->X.rp[Rf.i], len = P->X.rp[Rf.i + 1] - xb;
             const int64_t fb = xbase[r0 + threadIdx.x];
-            seg[threadIdx.x] = Seg{P->X.ci, P->Y.rp, P->km, fb - xb, P->xe0 + xb - fb, xl && len > LONGX};
+            seg[threadIdx.x] = Seg{P->X.ci, P->Y.rp, P->km, fb - xb, P->xe0 + xb - fb, xl && len > SHORTX};
             s_lo[threadIdx.x] = fb;
             if ((int)threadIdx.x == n - 1) s_lo[n] = xbase[r0 + n];
         }
@@ -1255,6 +1314,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
 // Y rows are short, and nothing is staged block-wide: the warps only meet to flush the
 // combining table at the end of an item.
 static constexpr int SUB = (int)(PCH / (GNT / 32));  // products per warp run
+static constexpr unsigned LANE_RUN = 4;  // most products per entry for the lane-per-entry walk
 
 template <int MODE, bool COMB, int OCC>
 __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
@@ -1379,6 +1439,21 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                 if (lane == 31) gend = e + 1 < xlen ? __ldg(xo + e + 1) : total;
                 gend = __shfl_sync(FULL, gend, 31);
                 const int64_t lim = min(ws1, gend);
+                // short Y rows (papers to authors, topics or venues): when no entry has more
+                // than LANE_RUN products in [f, lim), each lane walks its own entry's products
+                // (no search); otherwise windows of 32 consecutive products
+                int64_t nxt_e = __shfl_down_sync(FULL, off, 1);
+                if (lane == 31) nxt_e = gend;
+                const int64_t my_lo = max(off, f), my_hi = min(nxt_e, lim);
+                const int my_n = my_hi > my_lo ? (int)min(my_hi - my_lo, (int64_t)1 << 20) : 0;
+                const unsigned run = __reduce_max_sync(FULL, (unsigned)my_n);
+                if (run <= LANE_RUN) {
+                    for (int u = 0; u < (int)run; u++)
+                        if (u < my_n) product(av, base + my_lo + u);
+                    f = max(f, lim);
+                    p += 32;
+                    continue;
+                }
                 for (int64_t w = f; w < lim;) {
                     // the entry holding product w (the last lane whose entry starts at or
                     // before it) and where the next entry starts: while one entry holds the
@@ -1912,7 +1987,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         BinTally tally;
         uint32_t offsets[NBINS + 1];
         uint32_t cursors[NBINS];
-        uint32_t n_long;
+        uint32_t n_long, n_mid;
         unsigned pool_head;  // the pooled pass's work queue
     };
     std::vector<Prod> hp(w);
@@ -1960,7 +2035,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_list = align256(o_bin + (size_t)Mc);
     const size_t o_long = align256(o_list + (size_t)Mc * 4);
     const size_t o_longnb = align256(o_long + (size_t)Mc * 4);
-    const size_t o_rowprod = align256(o_longnb + (size_t)Mc * 4);
+    const size_t o_mid = align256(o_longnb + (size_t)Mc * 4);
+    const size_t o_rowprod = align256(o_mid + (size_t)Mc * 4);
     const size_t o_grp = align256(o_rowprod + (size_t)Mc * 4);
     const size_t o_xsum = align256(o_grp + (size_t)(Mc + 1) * 8);
     const size_t o_prods = align256(o_xsum + (size_t)Mc * 8);
@@ -1993,6 +2069,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     uint32_t *list = (uint32_t *)(ws + o_list);
     uint32_t *long_rows = (uint32_t *)(ws + o_long);
     uint32_t *long_nb = (uint32_t *)(ws + o_longnb);
+    uint32_t *mid_rows = (uint32_t *)(ws + o_mid);
     int32_t *rowprod = (int32_t *)(ws + o_rowprod);
     int64_t *grp = (int64_t *)(ws + o_grp);
     double *xsum = (double *)(ws + o_xsum);
@@ -2031,7 +2108,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         !cuda_ok(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s), "memset"))
         return fail(MP_ERR_CUDA);
 
-    if (!symbolic_only && xe_total > LONGX) {
+    if (!symbolic_only && xe_total > SHORTX) {
         xl = (int64_t *)al.alloc((size_t)xe_total * 8, s);
         xs = (int64_t *)al.alloc((size_t)xe_total * 8, s);
         if (!xl || !xs) return fail(MP_ERR_NOMEM);
@@ -2046,7 +2123,10 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned gr = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
         kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, long_nb, &sm_sym->n_long);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, long_nb, &sm_sym->n_long, mid_rows,
+           &sm_sym->n_mid);
+        kl(k_rowwork_mid, (unsigned)tun.sm_count * 8, 256, 0, s, dprods, rowprod, prod, xsum, (const uint32_t *)mid_rows,
+           (const uint32_t *)&sm_sym->n_mid, xl, xs, xe_total);
         kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum,
            (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long, xl, xs,
            xe_total);
