@@ -66,6 +66,10 @@ def parse():
                          "sampled rows, or left to right)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-queries", type=int, default=5)
+    ap.add_argument("--kernel-probe", default=None, metavar="IDX",
+                    help="comma list of scholarly query indices (or 'all'): run each once, plain form, on "
+                         "a fresh engine and print the kernel counters of each (a small, fixed set of "
+                         "launches for an ncu capture to compare with); no timing")
     return ap.parse_args()
 
 
@@ -208,6 +212,14 @@ def kernel_source_hash():
         with open(os.path.join(ROOT, "paper_2201_04058_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def dominant_kernel(kstats):
+    """The single kernel with the most device time. The "*_global" entries time a whole
+    split-row pass (set-up, walk and rank kernels together), so they are reported but not
+    chosen; the walk kernels inside them are ("walk_sym", "walk_num", "walk_dense")."""
+    single = {k: v for k, v in (kstats or {}).items() if not k.endswith("_global") and v["ms"] > 0}
+    return max(single.items(), key=lambda kv: kv[1]["ms"]) if single else None
 
 
 def ncu_traffic(kernel_name):
@@ -408,7 +420,7 @@ def run_engine(args, ws, rank, local):
                "plain_latency_same_arrivals_p99_ms": float(np.percentile(plain_arrival_lat, 99)),
                "form": "mp_submit_batch of the step's queries: shared sub-chains once, one wave per plan level"}
     peak, peak_kind = measured_peak()
-    dom = max(kstats.items(), key=lambda kv: kv[1]["ms"]) if kstats else None
+    dom = dominant_kernel(kstats)
     roofline = None
     if dom:
         name, k = dom
@@ -459,9 +471,10 @@ def run_engine(args, ws, rank, local):
 
 def _roofline(mp, ctx, peak, peak_kind, note):
     ks, _ = mp.mp_kernel_stats(ctx)
-    if not ks:
+    dom = dominant_kernel(ks)
+    if not dom:
         return None
-    name, k = max(ks.items(), key=lambda kv: kv[1]["ms"])
+    name, k = dom
     if k["ms"] <= 0:
         return None
     ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
@@ -756,9 +769,40 @@ def run_leg(args, local):
     print(json.dumps(out), flush=True)
 
 
+def run_kernel_probe(args, local):
+    """--kernel-probe: the chosen scholarly queries, each run once in the plain form on a
+    fresh engine (no warm-up, nothing cached), with the engine's per-kernel counters printed
+    for each: launches, algorithmic bytes and Gustavson products. A profiler capture of the
+    same command sees exactly these launches, so its DRAM bytes compare with the bytes here
+    launch for launch."""
+    import torch
+    from paper_2201_04058_b300 import mp
+    torch.cuda.set_device(local)
+    hin, qs, cfg = workload(args.workload, args.scale)
+    idx = list(range(len(qs))) if args.kernel_probe == "all" else [int(x) for x in args.kernel_probe.split(",")]
+    eng = mp.Engine(hin, device=local, policy=mp.MP_POLICY_NONE, planner=PLANNERS[args.planner][0])
+    per = []
+    for i in idx:
+        mp.mp_kernel_stats_reset(eng.ctx)
+        rc, t = mp.mp_submit(eng.ctx, eng.query(qs[i]))
+        if rc != mp.MP_OK:
+            raise mp.MPError(rc, "query")
+        mp.mp_release(eng.ctx, t)
+        ks, _ = mp.mp_kernel_stats(eng.ctx)
+        per.append({"query": i, "types": "".join(qs[i]["types"]),
+                    "kernels": {k: {"launches": v["launches"], "bytes": v["bytes"], "products": v["products"],
+                                    "ms": v["ms"]} for k, v in ks.items()}})
+    eng.close()
+    print(json.dumps({"kernel_probe": per, "config": dict(cfg, scale=args.scale)}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.kernel_probe is not None:
+        if rank == 0:
+            run_kernel_probe(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

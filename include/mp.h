@@ -315,13 +315,19 @@ int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t 
  * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
  * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),
  * dense, global, or pool (the persistent launch that drains the warp-hash and 2048-slot
- * bins when that mode is on; those bins then have no entries of their own). ms sums the device time between CUDA events recorded on the launch
- * stream around each launch; bytes sums the algorithmic bytes of the launches (X row
- * pointers, X entries with the two Y row pointers each looks up, one Y column id (and
- * value, in the pass that adds the counts: the numeric pass, or the symbolic pass for
- * split rows with a dense count row) per Gustavson product, 12 bytes per output entry). Up to cap
- * entries are written; *n receives the number written. *launches receives every kernel
- * launch this library made in the process (all kernels, not only the passes). */
+ * bins when that mode is on; those bins then have no entries of their own). The "global"
+ * entries time a whole split-row pass (set-up, product walk and rank kernels); the walk
+ * kernels inside it have entries of their own: "walk_sym" (bitmap rows, counting),
+ * "walk_num" (bitmap rows, adding counts) and "walk_dense" (rows with a dense count row).
+ * ms sums the device time between CUDA events recorded on the launch stream around each
+ * launch; bytes sums the algorithmic bytes of the launches (X row pointers, X entries with
+ * the two Y row pointers each looks up, one Y column id (and value, in the pass that adds
+ * the counts: the numeric pass, or the symbolic pass for split rows with a dense count
+ * row) per Gustavson product, 12 bytes per output entry; a walk counts 16 bytes per X
+ * entry (its product offset and Y-row start), plus its value when it adds counts, and 8
+ * per output count it adds). Up to cap entries are written; *n receives the number
+ * written. *launches receives every kernel launch this library made in the process (all
+ * kernels, not only the passes). */
 typedef struct {
     char name[32];
     uint64_t launches;

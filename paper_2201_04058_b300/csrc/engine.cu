@@ -1162,19 +1162,24 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
                                       "k2048", "k4096", "k8192", "dense", "global"};
     std::lock_guard<std::mutex> g(ctx->exec_mu);
     uint32_t w = 0;
+    auto put = [&](const char *name, const KStat &k) {
+        if (!k.launches || !out || w >= cap) return;
+        snprintf(out[w].name, sizeof(out[w].name), "%s", name);
+        out[w].launches = k.launches;
+        out[w].ms = k.ms;
+        out[w].bytes = k.bytes;
+        out[w].products = k.prods;
+        w++;
+    };
+    char name[32];
     for (int p = 0; p < 2; p++)
         for (int b = 0; b <= NBINS; b++) {
-            const KStat &k = b < NBINS ? ctx->prof.k[p][b] : ctx->prof.pool[p];
-            if (!k.launches) continue;
-            if (out && w < cap) {
-                snprintf(out[w].name, sizeof(out[w].name), "%s_%s", p ? "num" : "sym", b < NBINS ? bins[b] : "pool");
-                out[w].launches = k.launches;
-                out[w].ms = k.ms;
-                out[w].bytes = k.bytes;
-                out[w].products = k.prods;
-                w++;
-            }
+            snprintf(name, sizeof(name), "%s_%s", p ? "num" : "sym", b < NBINS ? bins[b] : "pool");
+            put(name, b < NBINS ? ctx->prof.k[p][b] : ctx->prof.pool[p]);
         }
+    put("walk_sym", ctx->prof.walk[0]);
+    put("walk_num", ctx->prof.walk[1]);
+    put("walk_dense", ctx->prof.walk[2]);
     if (n) *n = w;
     if (launches) *launches = g_launches.load();
     return MP_OK;
@@ -1225,6 +1230,7 @@ extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
         for (int b = 0; b < NBINS; b++) ctx->prof.k[p][b] = KStat{};
         ctx->prof.pool[p] = KStat{};
     }
+    for (int m = 0; m < 3; m++) ctx->prof.walk[m] = KStat{};
     return MP_OK;
 }
 

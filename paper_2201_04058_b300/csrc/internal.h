@@ -84,6 +84,14 @@ struct Prof {
     cudaEvent_t pev[2][2] = {};
     KStat pool[2];
     bool pool_ran[2] = {false, false};
+    // the split-row product walk kernels alone: [0] symbolic (bitmap rows), [1] numeric,
+    // [2] dense rows; events around each launch of a wave (up to WALK_EV per mode)
+    static constexpr int WALK_EV = 16;
+    cudaEvent_t wev[3][WALK_EV][2] = {};
+    int wn[3] = {0, 0, 0};
+    bool wmiss[3] = {false, false, false};
+    double wlast[3][2] = {};  // pass 0's walk bytes and products of the current wave
+    KStat walk[3];
     bool init();
     void destroy();
 };

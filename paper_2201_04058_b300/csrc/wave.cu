@@ -45,6 +45,10 @@ bool Prof::init() {
         for (int e = 0; e < 2; e++)
             if (cudaEventCreate(&pev[p][e]) != cudaSuccess) return false;
     }
+    for (int m = 0; m < 3; m++)
+        for (int k = 0; k < WALK_EV; k++)
+            for (int e = 0; e < 2; e++)
+                if (cudaEventCreate(&wev[m][k][e]) != cudaSuccess) return false;
     return true;
 }
 
@@ -56,6 +60,10 @@ void Prof::destroy() {
         for (int e = 0; e < 2; e++)
             if (pev[p][e]) cudaEventDestroy(pev[p][e]);
     }
+    for (int m = 0; m < 3; m++)
+        for (int k = 0; k < WALK_EV; k++)
+            for (int e = 0; e < 2; e++)
+                if (wev[m][k][e]) cudaEventDestroy(wev[m][k][e]);
 }
 
 // One product of a wave, as the kernels see it.
@@ -101,6 +109,11 @@ struct BinTally {
     unsigned long long xent[NBINS], prods[NBINS], outn[NBINS], bytes[NBINS];
     uint32_t gdense;  // GLOBAL rows that qualify for a dense row
     unsigned long long gd_cols, gb_cols;  // widest output among them, and among the other GLOBAL rows
+    // the split-row product walks alone ([0] bitmap rows' symbolic, [1] their numeric, [2]
+    // dense rows): algorithmic bytes (per X entry its product offset, Y-row start and value
+    // when the walk adds counts; per product the Y column id and value; per output entry the
+    // count the numeric walk adds) and Gustavson products
+    unsigned long long wbytes[3], wprods[3];
 };
 
 static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed by several blocks
@@ -397,6 +410,9 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
                     const bool d = glob_dense_row(ba.gdense, s, P.Y.ncols);
                     if (d) atomicAdd(&hd, 1u);
                     atomicMax(d ? &tally->gd_cols : &tally->gb_cols, (unsigned long long)P.Y.ncols);
+                    // the bitmap walk's bytes (a row that takes a dense slot moves them later)
+                    atomicAdd(&tally->wbytes[0], xe * 16ull + (unsigned long long)s * 4ull);
+                    atomicAdd(&tally->wprods[0], (unsigned long long)s);
                 }
                 atomicAdd(&hx[b], xe);
                 atomicAdd(&hp[b], (unsigned long long)s);
@@ -485,6 +501,11 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                 else
                     atomicAdd(&hb[b], 32ull + xe * (20ull + (P.X.val ? 8ull : 0ull)) +
                                           pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 12ull);
+                if (b == B_GLOBAL && !dense) {
+                    atomicAdd(&tally->wbytes[1], xe * (16ull + (P.X.val ? 8ull : 0ull)) +
+                                                     pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 8ull);
+                    atomicAdd(&tally->wprods[1], pr);
+                }
             }
             bin[g] = (int8_t)b;
         }
@@ -996,6 +1017,11 @@ __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const ui
             const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
             const unsigned long long extra = xe * (P.X.val ? 8ull : 0ull) + prod[gr] * (P.Y.val ? 8ull : 0ull);
             if (extra) atomicAdd(tally->bytes + B_GLOBAL, extra);
+            const unsigned long long sym = xe * 16ull + prod[gr] * 4ull;
+            atomicAdd(&tally->wbytes[0], (unsigned long long)0 - sym);  // no longer a bitmap walk
+            atomicAdd(&tally->wprods[0], (unsigned long long)0 - prod[gr]);
+            atomicAdd(&tally->wbytes[2], sym + extra);
+            atomicAdd(&tally->wprods[2], (unsigned long long)prod[gr]);
         }
     }
 }
@@ -1314,7 +1340,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
 // Y rows are short, and nothing is staged block-wide: the warps only meet to flush the
 // combining table at the end of an item.
 static constexpr int SUB = (int)(PCH / (GNT / 32));  // products per warp run
-static constexpr unsigned LANE_RUN = 4;  // most products per entry for the lane-per-entry walk
+static constexpr unsigned LANE_RUN = 8;  // most products per entry for the lane-per-entry walk
 
 template <int MODE, bool COMB, int OCC>
 __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
@@ -1359,15 +1385,15 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         unsigned long long *val = MODE == G_NUM    ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0])
                                   : MODE == G_DENSE ? g.dval + (r - g.r0) * g.dcols
                                                     : nullptr;
-        auto product = [&](uint64_t av, int64_t q) {
-            const uint32_t j = (uint32_t)__ldg(yci + q);
+        // one scalar product x_ik * Y[k, j], its column j and Y value bv already loaded (the
+        // callers issue several products' loads before applying any)
+        auto apply = [&](uint64_t av, uint32_t j, uint64_t bv) {
             // the column mask first: a masked-out product costs one bit load, no atomic
             if (!bit_of(cm, j)) return;
             unsigned long long add;
             if (!NUM) {
                 add = 1ull << (j & 31);
             } else {
-                const uint64_t bv = yval ? __ldg(yval + q) : 1ull;
                 add = av * bv;
                 if (chk && __umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
             }
@@ -1408,6 +1434,8 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                 }
             }
         };
+        auto yv = [&](int64_t q) -> uint64_t { return (NUM && yval) ? __ldg(yval + q) : 1ull; };
+        auto product = [&](uint64_t av, int64_t q) { apply(av, (uint32_t)__ldg(yci + q), yv(q)); };
         if (ws0 < ws1) {
             // the last X entry p of the row with xo[p] <= ws0, 32 probes per step
             int64_t plo = 0, phi = xlen - 1;
@@ -1448,8 +1476,20 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                 const int my_n = my_hi > my_lo ? (int)min(my_hi - my_lo, (int64_t)1 << 20) : 0;
                 const unsigned run = __reduce_max_sync(FULL, (unsigned)my_n);
                 if (run <= LANE_RUN) {
-                    for (int u = 0; u < (int)run; u++)
-                        if (u < my_n) product(av, base + my_lo + u);
+                    if (NUM && yval) {  // valued Y (an earlier result): one product at a time
+                        for (int u = 0; u < (int)run; u++)
+                            if (u < my_n) product(av, base + my_lo + u);
+                    } else {  // four products' column loads in flight per lane, then applied
+                        for (int u0 = 0; u0 < (int)run; u0 += 4) {
+                            uint32_t jj[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++)
+                                if (u0 + u < my_n) jj[u] = (uint32_t)__ldg(yci + base + my_lo + u0 + u);
+#pragma unroll
+                            for (int u = 0; u < 4; u++)
+                                if (u0 + u < my_n) apply(av, jj[u], 1ull);
+                        }
+                    }
                     f = max(f, lim);
                     p += 32;
                     continue;
@@ -1465,6 +1505,13 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                     if (run_end >= w + 32) {  // uniform over the warp; at least one full window
                         const int64_t b = __shfl_sync(FULL, base, cur);
                         const uint64_t ax = NUM ? __shfl_sync(FULL, av, cur) : 1ull;
+                        if (!(NUM && yval))
+                            for (; w + 64 <= run_end; w += 64) {  // two windows' loads in flight
+                                const uint32_t j0 = (uint32_t)__ldg(yci + b + w + lane);
+                                const uint32_t j1 = (uint32_t)__ldg(yci + b + w + 32 + lane);
+                                apply(ax, j0, 1ull);
+                                apply(ax, j1, 1ull);
+                            }
                         for (; w + 32 <= run_end; w += 32) product(ax, b + w + lane);
                         continue;
                     }
@@ -1826,6 +1873,30 @@ static void run_pass_graph(int pass, const PassArgs &a, const uint32_t *host_cou
 
 static void prof_collect(Prof *prof, int pass, const BinTally &t) {
     if (!prof || !prof->on) return;
+    // the split-row walks of this pass: symbolic and dense after pass 0, numeric after pass 1
+    // (and the symbolic walk again when pass 1 recounts bitmap rows it could not keep)
+    for (int m = 0; m < 3; m++) {
+        if (!prof->wn[m] || (pass == 0 && m == 1) || (pass == 1 && m == 2)) continue;
+        if (prof->wmiss[m]) {  // some launches went untimed: this wave's walk is left out
+            prof->wn[m] = 0;
+            prof->wmiss[m] = false;
+            continue;
+        }
+        double ms = 0.0;
+        for (int k = 0; k < prof->wn[m]; k++) {
+            float x = 0.f;
+            if (cudaEventElapsedTime(&x, prof->wev[m][k][0], prof->wev[m][k][1]) == cudaSuccess) ms += x;
+            else cudaGetLastError();
+        }
+        if (pass == 0) prof->wlast[m][0] = (double)t.wbytes[m], prof->wlast[m][1] = (double)t.wprods[m];
+        const bool again = pass == 1 && m == 0;  // the recount walks pass 0's bytes once more
+        KStat &w = prof->walk[m];
+        w.launches += (uint64_t)prof->wn[m];
+        w.ms += ms;
+        w.bytes += again ? prof->wlast[0][0] : (double)t.wbytes[m];
+        w.prods += again ? prof->wlast[0][1] : (double)t.wprods[m];
+        prof->wn[m] = 0;
+    }
     const bool pooled = prof->pool_ran[pass];
     prof->pool_ran[pass] = false;
     for (int b = 0; b < NBINS; b++) {
@@ -1938,6 +2009,18 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
 }
 
 // One pass of the GLOBAL bin (all rounds). pass 0 counts, pass 1 writes the rows.
+// A split-row walk launch, bracketed by CUDA events when profiling (its own time, apart
+// from the set-up and rank kernels of the pass).
+template <int MODE>
+static void glob_walk(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga, Prof *prof) {
+    const int m = MODE == G_SYM ? 0 : MODE == G_NUM ? 1 : 2;
+    const bool timed = prof && prof->on && prof->wn[m] < Prof::WALK_EV;
+    if (prof && prof->on && !timed) prof->wmiss[m] = true;  // more rounds than events: no stat
+    if (timed) cudaEventRecord(prof->wev[m][prof->wn[m]][0], s);
+    glob_set<MODE>(tun, s, a, ga);
+    if (timed) cudaEventRecord(prof->wev[m][prof->wn[m]++][1], s);
+}
+
 static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, cudaStream_t s, Prof *prof) {
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
@@ -1947,7 +2030,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         const int64_t words = g.nd * g.nwd;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
-            glob_set<G_DENSE>(tun, s, a, ga);
+            glob_walk<G_DENSE>(tun, s, a, ga, prof);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
                256, 0, s, ga);
             glob_rank(g, a, ga, 0, grid, s);
@@ -1962,14 +2045,14 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
-            glob_set<G_SYM>(tun, s, a, ga);
+            glob_walk<G_SYM>(tun, s, a, ga, prof);
             glob_rank(g, a, ga, pass, grid, s);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
             kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
                s, a, ga);
-            glob_set<G_NUM>(tun, s, a, ga);
+            glob_walk<G_NUM>(tun, s, a, ga, prof);
         }
     }
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
@@ -1983,6 +2066,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const int w = (int)in.size();
     out.assign(w, WaveOut{});
     if (w == 0) return MP_OK;
+    if (prof)  // walk events left by a wave that failed part-way are not this wave's
+        for (int m = 0; m < 3; m++) prof->wn[m] = 0, prof->wmiss[m] = false;
     struct Small {
         BinTally tally;
         uint32_t offsets[NBINS + 1];
@@ -2215,8 +2300,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
                   dprods, rowprod, grp, M, ps);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
-        !cuda_ok(cudaMemcpyAsync(h_sym.tally.bytes, sm_sym->tally.bytes, sizeof(h_sym.tally.bytes),
-                                 cudaMemcpyDeviceToHost, s), "copy") ||
+        !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
+                 "copy") ||
         !cuda_ok(cudaStreamSynchronize(s), "sync"))
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);

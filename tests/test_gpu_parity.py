@@ -361,3 +361,31 @@ def test_pooled_bin_pass(c1, graphs, monkeypatch):
                 assert "sym_pool" in names and "num_pool" in names, names
         finally:
             e.close()
+
+
+@pytest.mark.parametrize("glob_dense", [0, 1e-9])
+def test_walk_kernel_stats(c1, glob_dense, monkeypatch):
+    """The split-row walk kernels have counters of their own inside the split-row pass:
+    their Gustavson products add up to the pass's (bitmap rows plus dense rows), their
+    device time is part of the pass's, and their byte counts are positive."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"glob_dense={glob_dense}")
+    h, o = c1
+    qs = gen.long_queries(5, 6) + [gen.config1_query()]
+    e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+    try:
+        mp.mp_kernel_stats_reset(e.ctx)
+        for q in qs:
+            assert_same(e.run(q), OC.evaluate(o, q), ("walk stats", "".join(q["types"])))
+        ks, _ = mp.mp_kernel_stats(e.ctx)
+        walks = ["walk_dense"] if glob_dense else ["walk_sym", "walk_num"]
+        for w in walks:
+            assert w in ks and ks[w]["launches"] > 0 and ks[w]["bytes"] > 0, (w, ks.get(w))
+        sym_walk = sum(ks[w]["products"] for w in ("walk_sym", "walk_dense") if w in ks)
+        assert sym_walk == ks["sym_global"]["products"]
+        assert sum(ks[w]["ms"] for w in ("walk_sym", "walk_dense") if w in ks) <= ks["sym_global"]["ms"]
+        if not glob_dense:
+            assert ks["walk_num"]["products"] == ks["num_global"]["products"]
+            assert ks["walk_num"]["ms"] <= ks["num_global"]["ms"]
+    finally:
+        e.close()
