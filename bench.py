@@ -216,9 +216,11 @@ def kernel_source_hash():
 
 def dominant_kernel(kstats):
     """The single kernel with the most device time. The "*_global" entries time a whole
-    split-row pass (set-up, walk and rank kernels together), so they are reported but not
-    chosen; the walk kernels inside them are ("walk_sym", "walk_num", "walk_dense")."""
-    single = {k: v for k, v in (kstats or {}).items() if not k.endswith("_global") and v["ms"] > 0}
+    split-row pass (set-up, walk and rank kernels together) and the "stage_*" entries other
+    groups of kernels, so they are reported but not chosen; the walk kernels inside the
+    split-row passes are ("walk_sym", "walk_num", "walk_dense")."""
+    single = {k: v for k, v in (kstats or {}).items()
+              if not k.endswith("_global") and not k.startswith("stage_") and v["ms"] > 0}
     return max(single.items(), key=lambda kv: kv[1]["ms"]) if single else None
 
 

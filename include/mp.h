@@ -285,10 +285,10 @@ int mp_autotune(mp_ctx *ctx, uint32_t n, const mp_query *q, uint32_t reps, const
 /* ---- diagnostics */
 
 /* Work counters of a ticket's query: Gustavson scalar products summed over its sparse
- * products, rows per bin class in the symbolic and numeric passes (11 entries each:
+ * products, rows per bin class in the symbolic and numeric passes (12 entries each:
  * warp-hash tables of 32..1024 slots, block-hash tables of 2048..8192 slots, dense
- * shared-memory, global scratch) and the number of sparse products it ran. Any output
- * pointer may be NULL. */
+ * shared-memory, split rows in global scratch, and rows of at most 16 products taken one
+ * per thread) and the number of sparse products it ran. Any output pointer may be NULL. */
 int mp_result_stats(mp_ctx *ctx, mp_ticket ticket, uint64_t *products, uint32_t *sym_bins,
                     uint32_t *num_bins, uint32_t *n_products);
 
@@ -314,11 +314,15 @@ int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t 
 /* Per-kernel counters of the SpGEMM passes since the last reset: one entry per (pass,
  * bin) kernel that ran, named "sym_<bin>" / "num_<bin>" with <bin> one of w32, w64,
  * w128, w256, w512, w1024 (warp-hash tables), k2048, k4096, k8192 (block-hash tables),
- * dense, global, or pool (the persistent launch that drains the warp-hash and 2048-slot
+ * dense, global, lane (rows of at most 16 products, one per thread), or pool (the persistent launch that drains the warp-hash and 2048-slot
  * bins when that mode is on; those bins then have no entries of their own). The "global"
  * entries time a whole split-row pass (set-up, product walk and rank kernels); the walk
  * kernels inside it have entries of their own: "walk_sym" (bitmap rows, counting),
  * "walk_num" (bitmap rows, adding counts) and "walk_dense" (rows with a dense count row).
+ * "stage_rowwork", "stage_symbin", "stage_globsetup", "stage_rowptr" and "stage_numbin"
+ * time the other stages of a wave (row work, symbolic binning, split-row set-up, wave row
+ * pointers, numeric binning; several kernels each, host gaps between them included; no
+ * bytes).
  * ms sums the device time between CUDA events recorded on the launch stream around each
  * launch; bytes sums the algorithmic bytes of the launches (X row pointers, X entries with
  * the two Y row pointers each looks up, one Y column id (and value, in the pass that adds

@@ -168,6 +168,10 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "graphs") ctx->tun.graphs = (int)v;
                 else if (k == "lbs") ctx->tun.lbs = (int)v;
                 else if (k == "lbs_occ") ctx->tun.lbs_occ = (int)v;
+                else if (k == "dsm_cols") ctx->tun.dsm_cols = (int)v;
+                else if (k == "lane_rows") ctx->tun.lane_rows = (int)v;
+                else if (k == "ew_max") ctx->tun.ew_max = (int)v;
+                else if (k == "row_lens") ctx->tun.row_lens = (int)v;
                 else if (k == "pool") ctx->tun.pool = (int)v;
 
             }
@@ -1158,8 +1162,8 @@ extern "C" int mp_plan_chain(uint32_t p, const double *dims, const double *nnz, 
 
 extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, uint32_t *n, uint64_t *launches) {
     if (!ctx) return MP_ERR_ARG;
-    static const char *bins[NBINS] = {"w32", "w64", "w128", "w256", "w512", "w1024",
-                                      "k2048", "k4096", "k8192", "dense", "global"};
+    static const char *bins[NBINS] = {"w32",   "w64",   "w128",  "w256",  "w512",   "w1024",
+                                      "k2048", "k4096", "k8192", "dense", "global", "lane"};
     std::lock_guard<std::mutex> g(ctx->exec_mu);
     uint32_t w = 0;
     auto put = [&](const char *name, const KStat &k) {
@@ -1180,6 +1184,9 @@ extern "C" int mp_kernel_stats(mp_ctx *ctx, mp_kernel_stat *out, uint32_t cap, u
     put("walk_sym", ctx->prof.walk[0]);
     put("walk_num", ctx->prof.walk[1]);
     put("walk_dense", ctx->prof.walk[2]);
+    static const char *stages[Prof::NSTAGE] = {"stage_rowwork", "stage_symbin", "stage_globsetup", "stage_rowptr",
+                                                "stage_numbin"};
+    for (int st = 0; st < Prof::NSTAGE; st++) put(stages[st], ctx->prof.stage[st]);
     if (n) *n = w;
     if (launches) *launches = g_launches.load();
     return MP_OK;
@@ -1231,6 +1238,7 @@ extern "C" int mp_kernel_stats_reset(mp_ctx *ctx) {
         ctx->prof.pool[p] = KStat{};
     }
     for (int m = 0; m < 3; m++) ctx->prof.walk[m] = KStat{};
+    for (int st = 0; st < Prof::NSTAGE; st++) ctx->prof.stage[st] = KStat{};
     return MP_OK;
 }
 

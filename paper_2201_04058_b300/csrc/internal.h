@@ -24,13 +24,16 @@ struct DCsr {
 
 // Row-bin classes. Warp-hash bins hold one row per warp in a shared-memory table of T
 // slots (T = 32 << b); block-hash bins one row per block with T = 2048 << (b - 6);
-// DENSE one row per block in a shared-memory array as wide as the output; GLOBAL one
-// row per block in a dense accumulator in global scratch.
+// DENSE one row per block in a shared-memory array as wide as the output; GLOBAL rows are
+// split over many blocks (global-memory accumulators); LANE rows (at most LANE_PROD
+// Gustavson products) one row per thread, merged by insertion into a short sorted list.
 enum Bin : int {
     B_W32 = 0, B_W64, B_W128, B_W256, B_W512, B_W1024,
     B_K2048, B_K4096, B_K8192,
-    B_DENSE, B_GLOBAL, NBINS
+    B_DENSE, B_GLOBAL, B_LANE, NBINS
 };
+static constexpr int LANE_PROD = 16;
+static constexpr int LANE_X = 4;  // ... and at most this many X entries
 
 // Device error bits (OR-ed into one status word per product).
 enum : uint32_t {
@@ -50,6 +53,11 @@ struct Tuning {
     int seg_walk = 1;            // split-row kernel: one warp per segment on long Y rows
     int lbs = 1;                 // split-row kernel: warp-level product walk (0: block-staged walk)
     int lbs_occ = 6;             // resident blocks per SM of the warp-walk count-adding passes (6 or 4)
+    int lane_rows = 1;           // rows of at most LANE_PROD products: one thread per row (0: warp-hash bins)
+    int row_lens = 1;            // masked Y-row length arrays for products with X.nnz >= Y.nrows (0: off)
+    int ew_max = 64;             // split rows whose masked Y rows hold at most this many entries are cut
+                                 // into runs of X entries (-1: always runs of products)
+    int dsm_cols = 8192;         // dense split rows this narrow add their counts in a shared-memory row (0: off)
     uint64_t scratch_cap = 4ull << 30;  // bitmap + rank bytes of the GLOBAL bin per round
     // GLOBAL rows with prod_i >= glob_dense * ncols accumulate their counts in a dense u64
     // row (one pass gives both the size and the values); 0 turns the dense rows off
@@ -92,6 +100,13 @@ struct Prof {
     bool wmiss[3] = {false, false, false};
     double wlast[3][2] = {};  // pass 0's walk bytes and products of the current wave
     KStat walk[3];
+    // the other stages of a wave, each a few kernels (device time between events around
+    // them, host gaps included): [0] row work, [1] symbolic binning, [2] split-row set-up,
+    // [3] wave row pointers, [4] numeric binning
+    static constexpr int NSTAGE = 5;
+    cudaEvent_t sev[NSTAGE][2] = {};
+    bool srec[NSTAGE] = {};
+    KStat stage[NSTAGE];
     bool init();
     void destroy();
 };

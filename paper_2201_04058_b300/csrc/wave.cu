@@ -49,6 +49,9 @@ bool Prof::init() {
         for (int k = 0; k < WALK_EV; k++)
             for (int e = 0; e < 2; e++)
                 if (cudaEventCreate(&wev[m][k][e]) != cudaSuccess) return false;
+    for (int t = 0; t < NSTAGE; t++)
+        for (int e = 0; e < 2; e++)
+            if (cudaEventCreate(&sev[t][e]) != cudaSuccess) return false;
     return true;
 }
 
@@ -64,6 +67,9 @@ void Prof::destroy() {
         for (int k = 0; k < WALK_EV; k++)
             for (int e = 0; e < 2; e++)
                 if (wev[m][k][e]) cudaEventDestroy(wev[m][k][e]);
+    for (int t = 0; t < NSTAGE; t++)
+        for (int e = 0; e < 2; e++)
+            if (sev[t][e]) cudaEventDestroy(sev[t][e]);
 }
 
 // One product of a wave, as the kernels see it.
@@ -75,7 +81,11 @@ struct Prod {
     int32_t *ci;    // output column ids (after the symbolic pass)
     uint64_t *val;  // output counts
     uint64_t ymax;  // upper bound on Y's values
-    int64_t xe0;    // first slot of this product's X entries in the wave's per-entry arrays
+    // masked Y-row lengths (ml[k] = |Y row k| when km passes k, else 0), made for a product
+    // without a row mask whose X has at least as many entries as Y has rows, so the row work
+    // gathers one 4-byte word per X entry instead of two row pointers and a mask word; null
+    // otherwise
+    const uint32_t *ml;
 };
 
 // Per-product counters kept on the device.
@@ -93,7 +103,23 @@ struct BinArgs {
     int dense_max_cols, dense_min_u, force;
     uint64_t heavy, warp_prod;
     double gdense;  // GLOBAL rows with prod_i >= gdense * (their output's width) take a dense row
+    int lane;       // rows of at most LANE_PROD products take the one-thread-per-row bin (automatic bins only)
+    int ew_max;     // GLOBAL rows whose masked Y rows are all this short are split by X entries (-1: none)
 };
+
+__device__ __forceinline__ bool lane_row(const BinArgs &ba, uint64_t prod_i, int64_t xe) {
+    return ba.lane && ba.force < 0 && prod_i <= (uint64_t)LANE_PROD && xe <= LANE_X;
+}
+
+// A split row whose masked Y rows hold at most ew_max entries each: its work items are
+// fixed runs of X entries (each entry's Y row found as it is walked) instead of fixed runs
+// of products, so it needs no per-entry product offsets.
+__host__ __device__ __forceinline__ bool entry_split(uint32_t ymax_i, int ew_max) {
+    return (int64_t)ymax_i <= (int64_t)ew_max;
+}
+// algorithmic bytes per X entry of a split-row walk: its column id and Y row pointers when
+// split by entries, its product offset and Y-row start otherwise
+__device__ __forceinline__ unsigned long long walk_xbytes(bool ew) { return ew ? 20ull : 16ull; }
 
 // A GLOBAL row that accumulates in a dense u64 row as wide as its output (ncols): its
 // products are at least gdense times that width, so zeroing and scanning the dense row
@@ -114,6 +140,7 @@ struct BinTally {
     // when the walk adds counts; per product the Y column id and value; per output entry the
     // count the numeric walk adds) and Gustavson products
     unsigned long long wbytes[3], wprods[3];
+    unsigned long long gx_pw;  // X entries of the GLOBAL rows split by products (they need offsets)
 };
 
 static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed by several blocks
@@ -139,37 +166,80 @@ __global__ void k_rowprod(const int64_t *row0s, int w, int64_t M, int32_t *rowpr
 // Gustavson products) into s and the X values (1 for a pattern X) into x. Four entries are
 // loaded before their Y row pointers are, so four dependent gathers are in flight.
 __device__ __forceinline__ void row_sums(const Prod &P, int64_t p0, int64_t e, int64_t st, uint64_t &s,
-                                         double &x) {
+                                         double &x, uint32_t &mx) {
     const int32_t *__restrict__ xci = P.X.ci;
     const uint64_t *__restrict__ xv = P.X.val;
     const int64_t *__restrict__ yrp = P.Y.rp;
     const uint32_t *__restrict__ km = P.km;
     int64_t p = p0;
+    if (const uint32_t *__restrict__ ml = P.ml) {
+        for (; p + 3 * st < e; p += 4 * st) {
+            int32_t k[4];
+            uint32_t l[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + u * st);
+#pragma unroll
+            for (int u = 0; u < 4; u++) l[u] = __ldg(ml + k[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                s += l[u];
+                mx = max(mx, l[u]);
+                x += xv ? (double)__ldg(xv + p + u * st) : 1.0;
+            }
+        }
+        for (; p < e; p += st) {
+            const uint32_t l = __ldg(ml + __ldg(xci + p));
+            s += l;
+            mx = max(mx, l);
+            x += xv ? (double)__ldg(xv + p) : 1.0;
+        }
+        return;
+    }
     for (; p + 3 * st < e; p += 4 * st) {
         int32_t k[4];
+        int64_t y0[4], y1[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + u * st);
+        // the row pointers regardless of the mask, so they load beside the mask words
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            if (bit_of(km, (uint32_t)k[u])) s += (uint64_t)(__ldg(yrp + k[u] + 1) - __ldg(yrp + k[u]));
+            y0[u] = __ldg(yrp + k[u]);
+            y1[u] = __ldg(yrp + k[u] + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t len = bit_of(km, (uint32_t)k[u]) ? y1[u] - y0[u] : 0;
+            s += (uint64_t)len;
+            mx = max(mx, (uint32_t)len);
             x += xv ? (double)__ldg(xv + p + u * st) : 1.0;
         }
     }
     for (; p < e; p += st) {
         const int32_t k = __ldg(xci + p);
-        if (bit_of(km, (uint32_t)k)) s += (uint64_t)(__ldg(yrp + k + 1) - __ldg(yrp + k));
+        const int64_t y0 = __ldg(yrp + k), y1 = __ldg(yrp + k + 1);
+        const int64_t len = bit_of(km, (uint32_t)k) ? y1 - y0 : 0;
+        s += (uint64_t)len;
+        mx = max(mx, (uint32_t)len);
         x += xv ? (double)__ldg(xv + p) : 1.0;
     }
 }
 
-// prod_i of every wave row. Each lane takes one of 32 consecutive rows and sums rows of up
-// to 16 entries itself; longer rows are queued: up to LONGX entries for k_rowwork_mid (one
-// warp per row), beyond that for k_rowwork_long (several blocks per row).
+// ml[k] = masked length of Y row k (0 where the middle mask km drops k), k < n.
+__global__ void k_masked_len(const int64_t *__restrict__ yrp, const uint32_t *__restrict__ km, int64_t n,
+                             uint32_t *__restrict__ ml) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        ml[k] = bit_of(km, (uint32_t)k) ? (uint32_t)min(__ldg(yrp + k + 1) - __ldg(yrp + k), (int64_t)UINT32_MAX) : 0u;
+}
+
+// prod_i of every wave row, with the row's X value sum and its longest masked Y row. Each
+// lane takes one of 32 consecutive rows and sums rows of up to 16 entries itself; longer
+// rows are queued: up to LONGX entries for k_rowwork_mid (one warp per row), beyond that
+// for k_rowwork_long (several blocks per row).
 static constexpr int64_t SHORTX = 16;  // X rows up to this long are summed by one lane
 
 __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, double *xsum,
-                          uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long, uint32_t *mid_rows,
-                          uint32_t *n_mid) {
+                          uint32_t *ymx, uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long,
+                          uint32_t *mid_rows, uint32_t *n_mid) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -187,7 +257,8 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         }
         uint64_t s = 0;
         double xs = 0.0;  // the row's sum of X values: x_ik <= xs bounds every product and sum
-        if (e - b <= SHORTX && e > b) row_sums(*P, b, e, 1, s, xs);
+        uint32_t mx = 0;
+        if (e - b <= SHORTX && e > b) row_sums(*P, b, e, 1, s, xs, mx);
         if (e - b > LONGX) {
             const uint32_t at = atomicAdd(n_long, 1u);
             long_rows[at] = (uint32_t)g;
@@ -205,19 +276,19 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         if (g < M && e - b <= SHORTX) {
             prod[g] = s;
             xsum[g] = xs;
+            ymx[g] = mx;
         } else if (g < M && e - b > LONGX) {
             prod[g] = 0;  // k_rowwork_long adds its blocks' sums
             xsum[g] = 0.0;
+            ymx[g] = 0;
         }
     }
 }
 
 // The queued mid-length rows, one warp each (all warps of the grid in parallel), with four
-// dependent gathers in flight per lane; each X entry's masked Y-row length and Y-row start
-// are kept (xl, xs at the entry's wave slot) for the product walk.
-__global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
-                              const uint32_t *mid_rows, const uint32_t *n_mid, int64_t *xl, int64_t *xs,
-                              int64_t xcap) {
+// dependent gathers in flight per lane.
+__global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum, uint32_t *ymx,
+                              const uint32_t *mid_rows, const uint32_t *n_mid) {
     const int lane = threadIdx.x & 31;
     const uint32_t n = *n_mid;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -225,68 +296,32 @@ __global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_
         const uint32_t g = mid_rows[r];
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
-        const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
-        const int32_t *__restrict__ xci = P.X.ci;
-        const uint64_t *__restrict__ xv = P.X.val;
-        const int64_t *__restrict__ yrp = P.Y.rp;
-        const uint32_t *__restrict__ km = P.km;
         uint64_t s = 0;
         double x = 0.0;
-        int64_t p = b + lane;
-        for (; p + 96 < e; p += 128) {
-            int32_t k[4];
-            int64_t y0[4], y1[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + 32 * u);
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                y0[u] = __ldg(yrp + k[u]);
-                y1[u] = __ldg(yrp + k[u] + 1);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t len = bit_of(km, (uint32_t)k[u]) ? y1[u] - y0[u] : 0;
-                s += (uint64_t)len;
-                x += xv ? (double)__ldg(xv + p + 32 * u) : 1.0;
-                if (xl && P.xe0 + p + 32 * u < xcap) {
-                    xl[P.xe0 + p + 32 * u] = len;
-                    xs[P.xe0 + p + 32 * u] = y0[u];
-                }
-            }
-        }
-        for (; p < e; p += 32) {
-            const int32_t k = __ldg(xci + p);
-            const int64_t y0 = __ldg(yrp + k);
-            const int64_t len = bit_of(km, (uint32_t)k) ? __ldg(yrp + k + 1) - y0 : 0;
-            s += (uint64_t)len;
-            x += xv ? (double)__ldg(xv + p) : 1.0;
-            if (xl && P.xe0 + p < xcap) {
-                xl[P.xe0 + p] = len;
-                xs[P.xe0 + p] = y0;
-            }
-        }
+        uint32_t mx = 0;
+        row_sums(P, P.X.rp[i] + lane, P.X.rp[i + 1], 32, s, x, mx);
         for (int d = 16; d; d >>= 1) {
             s += __shfl_xor_sync(FULL, s, d);
             x += __shfl_xor_sync(FULL, x, d);
         }
+        mx = __reduce_max_sync(FULL, mx);
         if (lane == 0) {
             prod[g] = s;
             xsum[g] = x;
+            ymx[g] = mx;
         }
     }
 }
 
 // The queued long rows: row r is shared by ceil(len / LONGCH) consecutive blocks (modulo
 // the grid) starting at a block that depends on r, so long rows spread over the grid and a
-// row only as long as a few chunks does not make every block stop at it. Each X entry's
-// masked Y-row length and Y-row start are kept (xl, xs at the entry's wave slot): a long
-// row is usually split over blocks later, and its product walk then reads them in order
-// instead of looking them up again.
+// row only as long as a few chunks does not make every block stop at it.
 __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
-                               const uint32_t *long_rows, const uint32_t *long_nb, const uint32_t *n_long,
-                               int64_t *xl, int64_t *xs, int64_t xcap) {
+                               uint32_t *ymx, const uint32_t *long_rows, const uint32_t *long_nb,
+                               const uint32_t *n_long) {
     __shared__ unsigned long long red[32];
     __shared__ double redx[32];
+    __shared__ uint32_t redm[32];
     const uint32_t n = *n_long;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t G = gridDim.x;
@@ -297,66 +332,34 @@ __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64
         const uint32_t g = long_rows[r];
         const Prod &P = prods[rowprod[g]];
         const int64_t i = g - P.row0;
-        const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
-        const int32_t *__restrict__ xci = P.X.ci;
-        const uint64_t *__restrict__ xv = P.X.val;
-        const int64_t *__restrict__ yrp = P.Y.rp;
-        const uint32_t *__restrict__ km = P.km;
         uint64_t s = 0;
         double x = 0.0;
-        const int64_t st = nb * (int64_t)blockDim.x;
-        int64_t p = b + off * (int64_t)blockDim.x + threadIdx.x;
-        // four entries' gathers in flight at a time
-        for (; p + 3 * st < e; p += 4 * st) {
-            int32_t k[4];
-            int64_t y0[4], y1[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) k[u] = __ldg(xci + p + u * st);
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                y0[u] = __ldg(yrp + k[u]);
-                y1[u] = __ldg(yrp + k[u] + 1);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t len = bit_of(km, (uint32_t)k[u]) ? y1[u] - y0[u] : 0;
-                s += (uint64_t)len;
-                x += xv ? (double)__ldg(xv + p + u * st) : 1.0;
-                if (xl && P.xe0 + p + u * st < xcap) {
-                    xl[P.xe0 + p + u * st] = len;
-                    xs[P.xe0 + p + u * st] = y0[u];
-                }
-            }
-        }
-        for (; p < e; p += st) {
-            const int32_t k = __ldg(xci + p);
-            const int64_t y0 = __ldg(yrp + k);
-            const int64_t len = bit_of(km, (uint32_t)k) ? __ldg(yrp + k + 1) - y0 : 0;
-            s += (uint64_t)len;
-            x += xv ? (double)__ldg(xv + p) : 1.0;
-            if (xl && P.xe0 + p < xcap) {
-                xl[P.xe0 + p] = len;
-                xs[P.xe0 + p] = y0;
-            }
-        }
+        uint32_t mx = 0;
+        row_sums(P, P.X.rp[i] + off * (int64_t)blockDim.x + threadIdx.x, P.X.rp[i + 1], nb * (int64_t)blockDim.x, s,
+                 x, mx);
         for (int d = 16; d; d >>= 1) {
             s += __shfl_xor_sync(FULL, s, d);
             x += __shfl_xor_sync(FULL, x, d);
         }
+        mx = __reduce_max_sync(FULL, mx);
         if (lane == 0) {
             red[wid] = s;
             redx[wid] = x;
+            redm[wid] = mx;
         }
         __syncthreads();
         if (wid == 0) {
-            s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
-            x = lane < (int)(blockDim.x >> 5) ? redx[lane] : 0.0;
+            const bool in = lane < (int)(blockDim.x >> 5);
+            s = in ? red[lane] : 0;
+            x = in ? redx[lane] : 0.0;
+            mx = __reduce_max_sync(FULL, in ? redm[lane] : 0u);
             for (int d = 16; d; d >>= 1) {
                 s += __shfl_xor_sync(FULL, s, d);
                 x += __shfl_xor_sync(FULL, x, d);
             }
             if (lane == 0 && s) atomicAdd((unsigned long long *)(prod + g), s);
             if (lane == 0 && x > 0.0) atomicAdd(xsum + g, x);
+            if (lane == 0 && mx) atomicMax(ymx + g, mx);
         }
         __syncthreads();
     }
@@ -373,7 +376,8 @@ __device__ __forceinline__ void agg_add_u32(uint32_t *counter_base, int key, boo
 // Symbolic bin of every wave row from prod_i; rows without products get nnz_i = 0 and no
 // bin. Tallies per bin (for the byte model) and per product (products, rows per bin).
 __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uint64_t *prod, const double *xsum,
-                            int64_t M, BinArgs ba, int8_t *bin, int64_t *nnz, BinTally *tally, PStat *ps) {
+                            const uint32_t *ymx, int64_t M, BinArgs ba, int8_t *bin, int64_t *nnz, BinTally *tally,
+                            PStat *ps) {
     __shared__ uint32_t hc[NBINS], hd;
     __shared__ unsigned long long hx[NBINS], hp[NBINS], hb[NBINS];
     constexpr int NP = 8;  // products aggregated in shared memory per chunk of rows
@@ -402,8 +406,10 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
             s = prod[g];
             if (s) {
                 const int64_t i = g - P.row0;
-                b = bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy, ba.warp_prod, ba.force);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
+                b = lane_row(ba, s, (int64_t)xe) ? B_LANE
+                                                 : bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy,
+                                                           ba.warp_prod, ba.force);
                 atomicAdd(&hc[b], 1u);
                 if (b == B_GLOBAL) {
                     // dense-row and bitmap scratch are as wide as the widest output of each kind
@@ -411,7 +417,9 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
                     if (d) atomicAdd(&hd, 1u);
                     atomicMax(d ? &tally->gd_cols : &tally->gb_cols, (unsigned long long)P.Y.ncols);
                     // the bitmap walk's bytes (a row that takes a dense slot moves them later)
-                    atomicAdd(&tally->wbytes[0], xe * 16ull + (unsigned long long)s * 4ull);
+                    const bool ew = entry_split(ymx[g], ba.ew_max);
+                    if (!ew) atomicAdd(&tally->gx_pw, xe);
+                    atomicAdd(&tally->wbytes[0], xe * walk_xbytes(ew) + (unsigned long long)s * 4ull);
                     atomicAdd(&tally->wprods[0], (unsigned long long)s);
                 }
                 atomicAdd(&hx[b], xe);
@@ -459,7 +467,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
 // Numeric bins from the exact row sizes (grp = wave row pointers); rows the symbolic pass
 // put in GLOBAL stay there (their bitmaps give the output positions).
 __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_t *grp, const uint64_t *prod,
-                         int64_t M, BinArgs ba, int8_t *bin, BinTally *tally, PStat *ps) {
+                         const uint32_t *ymx, int64_t M, BinArgs ba, int8_t *bin, BinTally *tally, PStat *ps) {
     __shared__ uint32_t hc[NBINS];
     __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS], hb[NBINS];
     if (threadIdx.x < NBINS) {
@@ -481,6 +489,8 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
             if (z) {
                 if (bin[g] == B_GLOBAL || dense) {
                     b = B_GLOBAL;
+                } else if (bin[g] == B_LANE) {
+                    b = B_LANE;  // z <= prod_i <= LANE_PROD
                 } else {
                     b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.warp_prod,
                                 ba.force);
@@ -502,7 +512,8 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                     atomicAdd(&hb[b], 32ull + xe * (20ull + (P.X.val ? 8ull : 0ull)) +
                                           pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 12ull);
                 if (b == B_GLOBAL && !dense) {
-                    atomicAdd(&tally->wbytes[1], xe * (16ull + (P.X.val ? 8ull : 0ull)) +
+                    const bool ew = entry_split(ymx[g], ba.ew_max);
+                    atomicAdd(&tally->wbytes[1], xe * (walk_xbytes(ew) + (P.X.val ? 8ull : 0ull)) +
                                                      pr * (4ull + (P.Y.val ? 8ull : 0ull)) + (unsigned long long)z * 8ull);
                     atomicAdd(&tally->wprods[1], pr);
                 }
@@ -596,6 +607,107 @@ struct RowRef {
     __device__ __forceinline__ int64_t out_off(const PassArgs &a) const { return a.nnz[g] - a.nnz[P->row0]; }
     __device__ __forceinline__ int64_t out_len(const PassArgs &a) const { return a.nnz[g + 1] - a.nnz[g]; }
 };
+
+// LANE bin: one thread per row of at most LANE_PROD Gustavson products and LANE_X X
+// entries. The thread walks its row's products (X entries passing the middle mask, their
+// Y rows' entries passing the column mask) and merges each into a sorted list of distinct
+// columns held in shared memory (slot-major, so the threads of a warp never share a bank):
+// insertion from the back, adding the count when the column is already there. The symbolic pass stores the
+// list's length, the numeric pass writes the list (already in column order).
+static constexpr int LANE_NT = 128;  // threads per block of the LANE bin
+
+template <bool NUM>
+__global__ void __launch_bounds__(LANE_NT) k_lane_rows(PassArgs a, int bin) {
+    __shared__ uint32_t s_key[LANE_PROD * LANE_NT];
+    __shared__ unsigned long long s_val[NUM ? LANE_PROD * LANE_NT : 1];
+    const uint32_t cnt = a.counts[bin], base = a.offsets[bin];
+    const int tid = threadIdx.x;
+    uint32_t *key = s_key + tid;
+    unsigned long long *val = s_val + (NUM ? tid : 0);
+    for (uint32_t r = blockIdx.x * LANE_NT + tid; r < cnt; r += gridDim.x * LANE_NT) {
+        const RowRef R(a, a.list[base + r]);
+        const Prod *P = R.P;
+        uint32_t *err = R.err(a);
+        const int32_t *__restrict__ yci = P->Y.ci;
+        const uint64_t *__restrict__ yv = P->Y.val;
+        const uint32_t *__restrict__ cm = P->cm;
+        const int64_t xb = P->X.rp[R.i];
+        const int nx = (int)min((int64_t)LANE_X, P->X.rp[R.i + 1] - xb);  // the bin holds rows of <= LANE_X
+        // every entry's column, then every entry's Y row bounds: independent loads in flight
+        uint32_t kk[LANE_X];
+        int64_t y0[LANE_X], y1[LANE_X];
+#pragma unroll
+        for (int u = 0; u < LANE_X; u++) kk[u] = u < nx ? (uint32_t)__ldg(P->X.ci + xb + u) : 0u;
+#pragma unroll
+        for (int u = 0; u < LANE_X; u++) {
+            y0[u] = y1[u] = 0;
+            if (u < nx) {
+                y0[u] = __ldg(P->Y.rp + kk[u]);
+                y1[u] = __ldg(P->Y.rp + kk[u] + 1);
+            }
+        }
+        int n = 0;
+        auto insert = [&](uint32_t j, unsigned long long v) {
+            int s = n - 1;  // the list is sorted: find j's place from the back
+            while (s >= 0 && key[s * LANE_NT] > j) s--;
+            if (s >= 0 && key[s * LANE_NT] == j) {
+                if (NUM) {
+                    const unsigned long long o = val[s * LANE_NT];
+                    if (o + v < o) atomicOr(err, ERR_OVERFLOW);
+                    val[s * LANE_NT] = o + v;
+                }
+                return;
+            }
+            if (n == LANE_PROD) {  // more products than the row work counted
+                atomicOr(err, ERR_PROBE);
+                return;
+            }
+            for (int t = n - 1; t > s; t--) {
+                key[(t + 1) * LANE_NT] = key[t * LANE_NT];
+                if (NUM) val[(t + 1) * LANE_NT] = val[t * LANE_NT];
+            }
+            key[(s + 1) * LANE_NT] = j;
+            if (NUM) val[(s + 1) * LANE_NT] = v;
+            n++;
+        };
+#pragma unroll
+        for (int u = 0; u < LANE_X; u++) {
+            if (u >= nx || !bit_of(P->km, kk[u])) continue;
+            const uint64_t av = NUM && P->X.val ? __ldg(P->X.val + xb + u) : 1ull;
+            for (int64_t q0 = y0[u]; q0 < y1[u]; q0 += 4) {  // four column loads in flight
+                const int m = (int)min((int64_t)4, y1[u] - q0);
+                uint32_t jj[4];
+                uint64_t bv[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    jj[c] = c < m ? (uint32_t)__ldg(yci + q0 + c) : 0u;
+                    bv[c] = NUM && yv && c < m ? __ldg(yv + q0 + c) : 1ull;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    if (c >= m || !bit_of(cm, jj[c])) continue;
+                    unsigned long long v = 1;
+                    if (NUM) {
+                        v = av * bv[c];
+                        if (__umul64hi(av, bv[c])) atomicOr(err, ERR_OVERFLOW);
+                    }
+                    insert(jj[c], v);
+                }
+            }
+        }
+        if (!NUM) {
+            a.nnz[R.g] = n;
+        } else {
+            const int64_t o = R.out_off(a), len = R.out_len(a);
+            if (len != n) atomicOr(err, ERR_COUNT);
+            const int m = (int)min((int64_t)n, len);
+            for (int s = 0; s < m; s++) {
+                P->ci[o + s] = (int32_t)key[s * LANE_NT];
+                P->val[o + s] = val[s * LANE_NT];
+            }
+        }
+    }
+}
 
 // One row of each shared-memory bin. The per-bin kernels below loop over their bin's rows
 // with these; the pooled pass (k_bins_pool) calls them for the tiles it takes from a queue.
@@ -973,6 +1085,7 @@ __global__ void __launch_bounds__(256) k_bins_pool(PassArgs a) {
 // sums of X times the bound on Y's values stay below 2^63; otherwise every addition checks
 // its carry and an overflow fails the product.
 static constexpr int64_t PCH = 16384;  // Gustavson products per work item
+static constexpr int64_t ECH = 4096;   // X entries per work item of a row split by entries
 static constexpr int GNT = 256;        // threads per GLOBAL block
 static constexpr int RW = 8;           // bitmap words per thread in the rank pass
 static constexpr int CSLOT = 1024;     // shared-memory combining slots per work item
@@ -986,6 +1099,8 @@ struct GlobArgs {
     const int64_t *xoff;      // per X entry of a GLOBAL row: global product offset
     const int64_t *ys;        // per X entry of a GLOBAL row: its Y row's start
     const uint64_t *prod;     // prod_i per wave row
+    const uint32_t *ymx;      // per wave row: its longest masked Y row (entry_split)
+    int ew_max;
     int64_t r0, r1;           // rows of this round
     uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
     int64_t nw;               // slot size (words)
@@ -1000,8 +1115,8 @@ struct GlobArgs {
 // dense slots: their bin is marked B_GDENSE until the numeric binning, and the symbolic
 // pass's byte tally gains the X and Y values they read there.
 __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const uint32_t *src, int64_t R,
-                             const uint64_t *prod, double gdense, int64_t nd, uint32_t *dst,
-                             uint32_t *cnt, int8_t *bin, BinTally *tally) {
+                             const uint64_t *prod, const uint32_t *ymx, int ew_max, double gdense, int64_t nd,
+                             uint32_t *dst, uint32_t *cnt, int8_t *bin, BinTally *tally) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t gr = src[r];
         if (!glob_dense_row(gdense, prod[gr], prods[rowprod[gr]].Y.ncols)) {
@@ -1017,7 +1132,7 @@ __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const ui
             const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
             const unsigned long long extra = xe * (P.X.val ? 8ull : 0ull) + prod[gr] * (P.Y.val ? 8ull : 0ull);
             if (extra) atomicAdd(tally->bytes + B_GLOBAL, extra);
-            const unsigned long long sym = xe * 16ull + prod[gr] * 4ull;
+            const unsigned long long sym = xe * walk_xbytes(entry_split(ymx[gr], ew_max)) + prod[gr] * 4ull;
             atomicAdd(&tally->wbytes[0], (unsigned long long)0 - sym);  // no longer a bitmap walk
             atomicAdd(&tally->wprods[0], (unsigned long long)0 - prod[gr]);
             atomicAdd(&tally->wbytes[2], sym + extra);
@@ -1026,36 +1141,40 @@ __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const ui
     }
 }
 
-// Per GLOBAL row: its X entry count and its number of work items.
-__global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const uint64_t *prod, int64_t *xlen,
-                            int64_t *items) {
+// Per GLOBAL row: its number of work items (ECH X entries each for a row split by entries,
+// PCH products otherwise) and how many product offsets it needs (its X entries, or none).
+__global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const uint64_t *prod, const uint32_t *ymx,
+                            int ew_max, int64_t *xlen, int64_t *items) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const RowRef Rf(a, list[r]);
-        xlen[r] = Rf.P->X.rp[Rf.i + 1] - Rf.P->X.rp[Rf.i];
-        items[r] = ((int64_t)prod[Rf.g] + PCH - 1) / PCH;
+        const int64_t xe = Rf.P->X.rp[Rf.i + 1] - Rf.P->X.rp[Rf.i];
+        if (entry_split(ymx[Rf.g], ew_max)) {
+            xlen[r] = 0;
+            items[r] = (xe + ECH - 1) / ECH;
+        } else {
+            xlen[r] = xe;
+            items[r] = ((int64_t)prod[Rf.g] + PCH - 1) / PCH;
+        }
     }
 }
 
-// The masked Y-row length of every X entry of every GLOBAL row, as one flat array (row r's
-// entries start at xbase[r]); a device-wide exclusive scan then gives each entry's global
-// product offset. Beside it, ys keeps each entry's Y-row start, so the product walks read
-// both in order. Entries of long rows take both from the row-work pass (xl, xs); the
-// others look them up. A block takes XCH consecutive entries at a time: it finds the rows
+// The masked Y-row length of every X entry of every GLOBAL row split by products, as one
+// flat array (row r's entries start at xbase[r]; rows split by entries have none); a
+// device-wide exclusive scan then gives each entry's global product offset. Beside it, ys
+// keeps each entry's Y-row start, so the product walks read both in order. A block takes
+// XCH consecutive entries at a time: it finds the rows
 // they belong to once (usually one or two) and keeps each row's pointers in shared memory.
 static constexpr int64_t XCH = 2048;  // entries per block iteration
 static constexpr int XSEG = 64;       // rows per iteration kept in shared memory
 
 __global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *list, int64_t R,
-                                                   const int64_t *__restrict__ xbase, const int64_t *__restrict__ xl,
-                                                   const int64_t *__restrict__ xs, int64_t *__restrict__ xoff,
+                                                   const int64_t *__restrict__ xbase, int64_t *__restrict__ xoff,
                                                    int64_t *__restrict__ ys) {
     struct Seg {
         const int32_t *xci;
         const int64_t *yrp;
         const uint32_t *km;
         int64_t e0;  // first entry of the row in the flat array, minus the row's start in X.ci
-        int64_t xe;  // the row's first wave entry slot (xl, xs), minus its first flat entry
-        int lng;     // a row longer than SHORTX: the row-work pass kept its lengths and Y starts
     };
     __shared__ Seg seg[XSEG];
     __shared__ int64_t s_lo[XSEG + 1];
@@ -1085,9 +1204,9 @@ __global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *l
         if ((int)threadIdx.x < n) {
             const RowRef Rf(a, list[r0 + threadIdx.x]);
             const Prod *P = Rf.P;
-            const int64_t xb = P->X.rp[Rf.i], len = P->X.rp[Rf.i + 1] - xb;
+            const int64_t xb = P->X.rp[Rf.i];
             const int64_t fb = xbase[r0 + threadIdx.x];
-            seg[threadIdx.x] = Seg{P->X.ci, P->Y.rp, P->km, fb - xb, P->xe0 + xb - fb, xl && len > SHORTX};
+            seg[threadIdx.x] = Seg{P->X.ci, P->Y.rp, P->km, fb - xb};
             s_lo[threadIdx.x] = fb;
             if ((int)threadIdx.x == n - 1) s_lo[n] = xbase[r0 + n];
         }
@@ -1101,14 +1220,9 @@ __global__ void __launch_bounds__(256) k_glob_xlen(PassArgs a, const uint32_t *l
                     if (s_lo[mid] <= e) l = mid; else h = mid - 1;
                 }
                 const Seg &sg = seg[l];
-                if (sg.lng) {
-                    len = xl[sg.xe + e];
-                    y0 = xs[sg.xe + e];
-                } else {
-                    const int32_t k = __ldg(sg.xci + (e - sg.e0));
-                    y0 = __ldg(sg.yrp + k);
-                    if (bit_of(sg.km, (uint32_t)k)) len = __ldg(sg.yrp + k + 1) - y0;
-                }
+                const int32_t k = __ldg(sg.xci + (e - sg.e0));
+                y0 = __ldg(sg.yrp + k);
+                if (bit_of(sg.km, (uint32_t)k)) len = __ldg(sg.yrp + k + 1) - y0;
             } else {  // more rows in this stretch than shared memory keeps: find the row
                 int64_t lo = r0 + n, hi = R - 1;
                 while (lo < hi) {
@@ -1342,19 +1456,56 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
 static constexpr int SUB = (int)(PCH / (GNT / 32));  // products per warp run
 static constexpr unsigned LANE_RUN = 8;  // most products per entry for the lane-per-entry walk
 
-template <int MODE, bool COMB, int OCC>
+//
+// DSM (dense rows only, output no wider than the dynamic shared memory holds): the block keeps
+// a whole dense count row in shared memory, takes a contiguous range of work items (so its
+// items mostly belong to one row), adds every product there, and adds the row's non-zero
+// counts to the global dense row when it moves to another row and at the end: one global
+// atomic per touched column per block instead of one per product.
+//
+// EW: the launch takes only the work items of rows split by X entries (true) or only those
+// of rows split by products (false); a wave with both kinds launches both variants.
+template <int MODE, bool COMB, int OCC, bool DSM = false, bool EW = false>
 __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
     constexpr bool NUM = MODE != G_SYM;
-    __shared__ uint32_t s_key[CSLOT];
-    __shared__ unsigned long long s_acc[CSLOT];
+    static_assert(!DSM || (MODE == G_DENSE && !COMB), "a shared-memory row replaces the combining table");
+    __shared__ uint32_t s_key[COMB ? CSLOT : 1];
+    __shared__ unsigned long long s_acc[COMB ? CSLOT : 1];
+    extern __shared__ unsigned long long s_dense[];  // DSM: g.dcols counts
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int x = threadIdx.x; x < CSLOT; x += GNT) {
+    for (int x = threadIdx.x; COMB && x < CSLOT; x += GNT) {
         s_key[x] = EMPTY;
         s_acc[x] = 0;
     }
+    for (int64_t x = threadIdx.x; DSM && x < g.dcols; x += GNT) s_dense[x] = 0;
     __syncthreads();
     const int64_t t0 = g.item_off[g.r0], t1 = g.item_off[g.r1];
-    for (int64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+    int64_t ta = t0 + blockIdx.x, tb = t1, ts = gridDim.x;
+    if (DSM) {
+        const int64_t per = (t1 - t0 + gridDim.x - 1) / gridDim.x;
+        ta = t0 + (int64_t)blockIdx.x * per;
+        tb = min(t1, ta + per);
+        ts = 1;
+    }
+    // DSM: the row whose counts the shared-memory row holds, and where they go
+    int64_t d_r = -1, d_w = 0;
+    unsigned long long *d_val = nullptr;
+    uint32_t *d_err = nullptr;
+    bool d_chk = false;
+    auto d_flush = [&]() {  // all threads; the caller synchronises before and after
+        for (int64_t x = threadIdx.x; x < d_w; x += GNT) {
+            const unsigned long long v = s_dense[x];
+            if (!v) continue;
+            s_dense[x] = 0;
+            if (d_chk) {
+                const unsigned long long old = atomicAdd(d_val + x, v);
+                if (old + v < old) atomicOr(d_err, ERR_OVERFLOW);
+            } else {
+                atomicAdd(d_val + x, v);
+            }
+        }
+    };
+    for (int64_t t = ta; t < tb; t += ts) {
         int64_t lo = g.r0, hi = g.r1 - 1;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
@@ -1374,17 +1525,22 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         const uint64_t *__restrict__ yval = PP->Y.val;
         const uint32_t *__restrict__ cm = PP->cm;
         const int64_t xb = PP->X.rp[row], xlen = PP->X.rp[row + 1] - xb;
-        const int64_t *__restrict__ xo = g.xoff + g.xbase[r];
-        const int64_t *__restrict__ ysr = g.ys + g.xbase[r];
-        // product offsets are global across the GLOBAL rows: this row's start at xo[0]
-        const int64_t total = __ldg(xo) + (int64_t)g.prod[gr];
-        const int64_t s0 = __ldg(xo) + (t - g.item_off[r]) * PCH;
-        const int64_t s1 = min(total, s0 + PCH);
-        const int64_t ws0 = s0 + (int64_t)wid * SUB, ws1 = min(s1, ws0 + SUB);
+        if (entry_split(g.ymx[gr], g.ew_max) != EW) continue;  // the other variant's item (uniform)
         uint2 *bmr = g.bmr + (r - g.r0) * g.nw;
         unsigned long long *val = MODE == G_NUM    ? (unsigned long long *)pval + (a.nnz[gr] - a.nnz[PP->row0])
                                   : MODE == G_DENSE ? g.dval + (r - g.r0) * g.dcols
                                                     : nullptr;
+        if (DSM && r != d_r) {  // uniform over the block (r follows from t)
+            if (d_r >= 0) {
+                d_flush();
+                __syncthreads();
+            }
+            d_r = r;
+            d_w = PP->Y.ncols;
+            d_val = val;
+            d_err = err;
+            d_chk = chk;
+        }
         // one scalar product x_ik * Y[k, j], its column j and Y value bv already loaded (the
         // callers issue several products' loads before applying any)
         auto apply = [&](uint64_t av, uint32_t j, uint64_t bv) {
@@ -1396,6 +1552,15 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
             } else {
                 add = av * bv;
                 if (chk && __umul64hi(av, bv)) atomicOr(err, ERR_OVERFLOW);
+            }
+            if (DSM) {
+                if (chk) {
+                    const unsigned long long old = atomicAdd(&s_dense[j], add);
+                    if (old + add < old) atomicOr(err, ERR_OVERFLOW);
+                } else {
+                    atomicAdd(&s_dense[j], add);
+                }
+                return;
             }
             const uint32_t k = NUM ? j : (j >> 5);
             const uint32_t slot = (k * 0x9E3779B1u) >> (32 - 10);
@@ -1436,6 +1601,86 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         };
         auto yv = [&](int64_t q) -> uint64_t { return (NUM && yval) ? __ldg(yval + q) : 1ull; };
         auto product = [&](uint64_t av, int64_t q) { apply(av, (uint32_t)__ldg(yci + q), yv(q)); };
+        // a lane's own run of n <= run products from Y position q0 (the lane-per-entry walk):
+        // four column loads in flight per lane when Y is a pattern matrix
+        auto lane_walk = [&](uint64_t av, int64_t q0, int n, int run) {
+            if (NUM && yval) {  // valued Y (an earlier result): one product at a time
+                for (int u = 0; u < run; u++)
+                    if (u < n) product(av, q0 + u);
+                return;
+            }
+            for (int u0 = 0; u0 < run; u0 += 4) {
+                uint32_t jj[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u0 + u < n) jj[u] = (uint32_t)__ldg(yci + q0 + u0 + u);
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u0 + u < n) apply(av, jj[u], 1ull);
+            }
+        };
+        // the lane holding product fj of a group of 32 entries whose products start at offsets
+        // off (ascending over the lanes) relative to window start w: the last lane whose
+        // entry starts at or before fj = w + lane (a 5-step shuffle search)
+        auto holder = [&](int64_t off, int64_t w) {
+            const int rel = (int)max((int64_t)-1, min(off - w, (int64_t)32));
+            int src = 0;
+#pragma unroll
+            for (int st = 16; st; st >>= 1) {
+                const int v = __shfl_sync(FULL, rel, src + st);
+                if (v <= lane) src += st;
+            }
+            return src;
+        };
+        if (EW) {
+            // a row split by X entries: this warp's share of the item's entries, 32 at a time;
+            // each lane looks up its entry's Y row, then the lanes walk their own short runs,
+            // or the group's products in windows of 32 when some run is longer
+            const int64_t e0 = (t - g.item_off[r]) * ECH;
+            const int64_t we0 = e0 + (int64_t)wid * (ECH / (GNT / 32));
+            const int64_t we1 = min(min(xlen, e0 + ECH), we0 + ECH / (GNT / 32));
+            const int32_t *__restrict__ xci = PP->X.ci;
+            const int64_t *__restrict__ yrp = PP->Y.rp;
+            const uint32_t *__restrict__ km = PP->km;
+            for (int64_t p = we0; p < we1; p += 32) {
+                const int64_t e = p + lane;
+                int64_t st = 0, len = 0;
+                uint64_t av = 1;
+                if (e < we1) {  // the row pointers load beside the mask word
+                    const uint32_t k = (uint32_t)__ldg(xci + xb + e);
+                    st = __ldg(yrp + k);
+                    const int64_t y1 = __ldg(yrp + k + 1);
+                    if (NUM && xval) av = __ldg(xval + xb + e);
+                    if (bit_of(km, k)) len = y1 - st;
+                }
+                const unsigned run = __reduce_max_sync(FULL, (unsigned)len);
+                if (run <= LANE_RUN) {
+                    lane_walk(av, st, (int)len, (int)run);
+                    continue;
+                }
+                int64_t x = len;  // inclusive scan of the run lengths over the lanes
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int64_t y = __shfl_up_sync(FULL, x, d);
+                    if (lane >= d) x += y;
+                }
+                const int64_t tot = __shfl_sync(FULL, x, 31), off = x - len, base = st - off;
+                for (int64_t w = 0; w < tot; w += 32) {
+                    const int src = holder(off, w);
+                    const int64_t q = __shfl_sync(FULL, base, src) + w + lane;
+                    const uint64_t ax = NUM ? __shfl_sync(FULL, av, src) : 1ull;
+                    if (w + lane < tot) product(ax, q);
+                }
+            }
+        }
+        const int64_t *__restrict__ xo = g.xoff + g.xbase[r];
+        const int64_t *__restrict__ ysr = g.ys + g.xbase[r];
+        // product offsets are global across the GLOBAL rows split by products: this row's
+        // start at xo[0]
+        const int64_t total = EW ? 0 : __ldg(xo) + (int64_t)g.prod[gr];
+        const int64_t s0 = EW ? 0 : __ldg(xo) + (t - g.item_off[r]) * PCH;
+        const int64_t s1 = min(total, s0 + PCH);
+        const int64_t ws0 = s0 + (int64_t)wid * SUB, ws1 = EW ? ws0 : min(s1, ws0 + SUB);
         if (ws0 < ws1) {
             // the last X entry p of the row with xo[p] <= ws0, 32 probes per step
             int64_t plo = 0, phi = xlen - 1;
@@ -1476,20 +1721,7 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                 const int my_n = my_hi > my_lo ? (int)min(my_hi - my_lo, (int64_t)1 << 20) : 0;
                 const unsigned run = __reduce_max_sync(FULL, (unsigned)my_n);
                 if (run <= LANE_RUN) {
-                    if (NUM && yval) {  // valued Y (an earlier result): one product at a time
-                        for (int u = 0; u < (int)run; u++)
-                            if (u < my_n) product(av, base + my_lo + u);
-                    } else {  // four products' column loads in flight per lane, then applied
-                        for (int u0 = 0; u0 < (int)run; u0 += 4) {
-                            uint32_t jj[4];
-#pragma unroll
-                            for (int u = 0; u < 4; u++)
-                                if (u0 + u < my_n) jj[u] = (uint32_t)__ldg(yci + base + my_lo + u0 + u);
-#pragma unroll
-                            for (int u = 0; u < 4; u++)
-                                if (u0 + u < my_n) apply(av, jj[u], 1ull);
-                        }
-                    }
+                    lane_walk(av, base + my_lo, my_n, (int)run);
                     f = max(f, lim);
                     p += 32;
                     continue;
@@ -1516,14 +1748,7 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
                         continue;
                     }
                     const int64_t fj = w + lane;
-                    // the last lane whose entry starts at or before product fj
-                    const int rel = (int)max((int64_t)-1, min(off - w, (int64_t)32));
-                    int src = 0;
-#pragma unroll
-                    for (int st = 16; st; st >>= 1) {
-                        const int v = __shfl_sync(FULL, rel, src + st);
-                        if (v <= lane) src += st;
-                    }
+                    const int src = holder(off, w);
                     const int64_t q = __shfl_sync(FULL, base, src) + fj;
                     const uint64_t ax = NUM ? __shfl_sync(FULL, av, src) : 1ull;
                     if (fj < lim) product(ax, q);
@@ -1561,6 +1786,7 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         }
         __syncthreads();
     }
+    if (DSM && d_r >= 0) d_flush();
 }
 
 // The rank pass in parallel over chunks of RCH words of every row slot (one block each), so a
@@ -1751,6 +1977,16 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
                 cudaEventRecordWithFlags(prof->pev[pass][1], s, g_capturing ? cudaEventRecordExternal : 0);
         }
     }
+    if (host_counts[B_LANE]) {
+        const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[B_LANE];
+        if (prof && prof->on)
+            cudaEventRecordWithFlags(prof->ev[pass][B_LANE][0], s, g_capturing ? cudaEventRecordExternal : 0);
+        const unsigned g = blocks_for(rows, LANE_NT, sms * 16);
+        if (numeric) launch(k_lane_rows<true>, g, LANE_NT, 0, s, a, (int)B_LANE);
+        else launch(k_lane_rows<false>, g, LANE_NT, 0, s, a, (int)B_LANE);
+        if (prof && prof->on)
+            cudaEventRecordWithFlags(prof->ev[pass][B_LANE][1], s, g_capturing ? cudaEventRecordExternal : 0);
+    }
     for (int b = 0; b < B_GLOBAL; b++) {
         if (!host_counts[b]) continue;
         if (pooled && pool_bin(b)) continue;
@@ -1822,8 +2058,8 @@ void WaveCache::clear(Alloc &al, cudaStream_t s) {
 static void run_pass_graph(int pass, const PassArgs &a, const uint32_t *host_counts, int64_t dense_cols,
                            const Tuning &tun, cudaStream_t s, Prof *prof, WaveCache &wc) {
     uint32_t mask = 0;
-    for (int b = 0; b < B_GLOBAL; b++)
-        if (host_counts[b]) mask |= 1u << b;
+    for (int b = 0; b < NBINS; b++)
+        if (b != B_GLOBAL && host_counts[b]) mask |= 1u << b;
     if (!mask) return;
     int64_t dcls = 0;
     if (mask & (1u << B_DENSE)) {
@@ -1928,6 +2164,29 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
     }
 }
 
+// Events around one stage of a wave (e = 0 start, 1 end); stage_collect adds the stages
+// recorded since the last call once the wave has synchronised.
+static inline void stage_mark(Prof *prof, int st, int e, cudaStream_t s) {
+    if (!prof || !prof->on) return;
+    cudaEventRecord(prof->sev[st][e], s);
+    if (e) prof->srec[st] = true;
+}
+
+static void stage_collect(Prof *prof) {
+    if (!prof || !prof->on) return;
+    for (int st = 0; st < Prof::NSTAGE; st++) {
+        if (!prof->srec[st]) continue;
+        prof->srec[st] = false;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof->sev[st][0], prof->sev[st][1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        prof->stage[st].launches++;
+        prof->stage[st].ms += ms;
+    }
+}
+
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // State of the GLOBAL bin of one wave across its two passes. Rows [0, nd) of list take
@@ -1939,6 +2198,9 @@ struct Glob {
     uint32_t *list = nullptr;  // the bin's rows, dense-row candidates first
     int64_t *item_off = nullptr, *xbase = nullptr, *xoff = nullptr, *ys = nullptr;
     const uint64_t *prod = nullptr;
+    const uint32_t *ymx = nullptr;  // longest masked Y row per wave row
+    int ew_max = -1;                // rows with ymx <= ew_max are split by X entries
+    int kinds = 1;                  // bit 0: rows split by products present, bit 1: by entries
     uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
     int64_t *csum = nullptr;   // rank pass: per chunk of a row slot, its set bits, then its offset
@@ -1975,8 +2237,10 @@ static void glob_release(Glob &g, Alloc &al, cudaStream_t s) {
 // or block-staged walk, combining table on or off, and for the count-adding modes 4 or 6
 // resident blocks per SM (64 or 40 registers a thread).
 // One block per resident slot: the blocks loop over the work items.
+// kinds: bit 0 when the GLOBAL rows include rows split by products, bit 1 rows split by X
+// entries (the warp-level walk launches one variant for each kind present).
 template <int MODE>
-static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga) {
+static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga, int kinds) {
     const int occ = MODE == G_SYM ? 8 : tun.glob_occ >= 6 ? 6 : 4;
     const unsigned grid = (unsigned)(tun.sm_count * occ);
 #define GLOB_SET_VARIANT(K)                                                       \
@@ -1990,17 +2254,37 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
         if (tun.combine) kl(K<MODE, true, 4>, grid, GNT, 0, s, a, ga);           \
         else kl(K<MODE, false, 4>, grid, GNT, 0, s, a, ga);                      \
     }
+    using KF = void (*)(PassArgs, GlobArgs);
+    auto both = [&](KF k_pw, KF k_ew, unsigned grid, size_t sm) {
+        if (kinds & 1) kl(k_pw, grid, GNT, sm, s, a, ga);
+        if (kinds & 2) kl(k_ew, grid, GNT, sm, s, a, ga);
+    };
+    if constexpr (MODE == G_DENSE) {
+        // dense rows narrow enough for a shared-memory row: as many blocks as fit per SM
+        if (tun.lbs && tun.dsm_cols > 0 && ga.dcols > 0 && ga.dcols <= tun.dsm_cols) {
+            const KF k0 = k_glob_lbs<G_DENSE, false, 6, true, false>, k1 = k_glob_lbs<G_DENSE, false, 6, true, true>;
+            const size_t sm = (size_t)ga.dcols * 8;
+            int nb = 0;
+            if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess &&
+                cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k0, GNT, sm) == cudaSuccess && nb > 0) {
+                both(k0, k1, (unsigned)(tun.sm_count * nb), sm);
+                return;
+            }
+            cudaGetLastError();  // no room: the global-row walk below
+        }
+    }
     if (tun.lbs) {
         // the bitmap pass at 6 blocks per SM (40 registers), the count-adding passes at
         // lbs_occ (4: 64 registers; 6 spills a few values of the shuffle walk)
         const int lo = MODE == G_SYM || tun.lbs_occ >= 6 ? 6 : 4;
         const unsigned g = (unsigned)(tun.sm_count * lo);
         if (lo == 6) {
-            if (tun.combine) kl(k_glob_lbs<MODE, true, 6>, g, GNT, 0, s, a, ga);
-            else kl(k_glob_lbs<MODE, false, 6>, g, GNT, 0, s, a, ga);
+            if (tun.combine) both(k_glob_lbs<MODE, true, 6, false, false>, k_glob_lbs<MODE, true, 6, false, true>, g, 0);
+            else both(k_glob_lbs<MODE, false, 6, false, false>, k_glob_lbs<MODE, false, 6, false, true>, g, 0);
         } else {
-            if (tun.combine) kl(k_glob_lbs<MODE, true, 4>, g, GNT, 0, s, a, ga);
-            else kl(k_glob_lbs<MODE, false, 4>, g, GNT, 0, s, a, ga);
+            if (tun.combine) both(k_glob_lbs<MODE, true, 4, false, false>, k_glob_lbs<MODE, true, 4, false, true>, g, 0);
+            else both(k_glob_lbs<MODE, false, 4, false, false>, k_glob_lbs<MODE, false, 4, false, true>, g, 0);
         }
     } else {
         GLOB_SET_VARIANT(k_glob_set)
@@ -2012,12 +2296,12 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
 // A split-row walk launch, bracketed by CUDA events when profiling (its own time, apart
 // from the set-up and rank kernels of the pass).
 template <int MODE>
-static void glob_walk(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga, Prof *prof) {
+static void glob_walk(const Tuning &tun, cudaStream_t s, const PassArgs &a, const GlobArgs &ga, int kinds, Prof *prof) {
     const int m = MODE == G_SYM ? 0 : MODE == G_NUM ? 1 : 2;
     const bool timed = prof && prof->on && prof->wn[m] < Prof::WALK_EV;
     if (prof && prof->on && !timed) prof->wmiss[m] = true;  // more rounds than events: no stat
     if (timed) cudaEventRecord(prof->wev[m][prof->wn[m]][0], s);
-    glob_set<MODE>(tun, s, a, ga);
+    glob_set<MODE>(tun, s, a, ga, kinds);
     if (timed) cudaEventRecord(prof->wev[m][prof->wn[m]++][1], s);
 }
 
@@ -2025,12 +2309,13 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys, g.prod, 0, g.nd, g.dbmr, g.nwd, tun.short_walk,
-                          tun.seg_walk, g.dval, g.dcols};
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff,        g.ys,          g.prod,
+                          g.ymx,  g.ew_max,   0,       g.nd,          g.dbmr,        g.nwd,
+                          tun.short_walk, tun.seg_walk, g.dval, g.dcols};
         const int64_t words = g.nd * g.nwd;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
-            glob_walk<G_DENSE>(tun, s, a, ga, prof);
+            glob_walk<G_DENSE>(tun, s, a, ga, g.kinds, prof);
             kl(k_glob_dscan, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words * 32, 256), grid * 4)),
                256, 0, s, ga);
             glob_rank(g, a, ga, 0, grid, s);
@@ -2040,19 +2325,19 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         }
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys, g.prod, r0, std::min(g.R, r0 + g.per_round), g.bmr,
-                          g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
+        const GlobArgs ga{g.list,         g.item_off,   g.xbase, g.xoff, g.ys, g.prod, g.ymx, g.ew_max, r0,
+                          std::min(g.R, r0 + g.per_round), g.bmr, g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
-            glob_walk<G_SYM>(tun, s, a, ga, prof);
+            glob_walk<G_SYM>(tun, s, a, ga, g.kinds, prof);
             glob_rank(g, a, ga, pass, grid, s);
         }
         if (pass == 1) {
             const int64_t words = rows * g.nw;
             kl(k_glob_fill, (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(words, 256), grid * 4)), 256, 0,
                s, a, ga);
-            glob_walk<G_NUM>(tun, s, a, ga, prof);
+            glob_walk<G_NUM>(tun, s, a, ga, g.kinds, prof);
         }
     }
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][1], s);
@@ -2066,8 +2351,10 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const int w = (int)in.size();
     out.assign(w, WaveOut{});
     if (w == 0) return MP_OK;
-    if (prof)  // walk events left by a wave that failed part-way are not this wave's
+    if (prof) {  // events left by a wave that failed part-way are not this wave's
         for (int m = 0; m < 3; m++) prof->wn[m] = 0, prof->wmiss[m] = false;
+        for (int st = 0; st < Prof::NSTAGE; st++) prof->srec[st] = false;
+    }
     struct Small {
         BinTally tally;
         uint32_t offsets[NBINS + 1];
@@ -2077,12 +2364,17 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     };
     std::vector<Prod> hp(w);
     std::vector<int64_t> row0s(w + 1, 0);
-    int64_t dense_cols = 0, max_cols = 0, xe_total = 0;
+    int64_t dense_cols = 0, max_cols = 0, ml_total = 0;
+    std::vector<int64_t> ml_off(w, -1);  // offset of each product's masked-length array, or -1
     for (int p = 0; p < w; p++) {
         const WaveIn &x = in[p];
         Prod &P = hp[p];
-        P.xe0 = xe_total;
-        xe_total += x.X.nnz;
+        // (a row mask on X usually leaves few rows: then the lengths would cost more to make
+        // than they save)
+        if (tun.row_lens && !x.rm && x.X.nnz >= x.Y.nrows && x.Y.nrows > 0) {
+            ml_off[p] = ml_total;
+            ml_total += (x.Y.nrows + 63) / 64 * 64;  // 256-byte aligned slices
+        }
         P.X = x.X;
         P.Y = x.Y;
         P.rm = x.rm;
@@ -2113,8 +2405,9 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     }
     // workspace: prod u64[M], bins i8[M], row list u32[M], long rows and their block counts
     // u32[M] each, rowprod i32[M],
-    // wave nnz / row pointers i64[M+1], X row sums f64[M], product descriptors, row0s,
-    // per-product stats, two Smalls (M, w: the capacities when the workspace persists)
+    // wave nnz / row pointers i64[M+1], X row sums f64[M], longest masked Y rows u32[M],
+    // product descriptors, row0s, per-product stats, two Smalls (M, w: the capacities when
+    // the workspace persists)
     const size_t o_prod = 0;
     const size_t o_bin = align256(o_prod + (size_t)Mc * 8);
     const size_t o_list = align256(o_bin + (size_t)Mc);
@@ -2124,21 +2417,21 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_rowprod = align256(o_mid + (size_t)Mc * 4);
     const size_t o_grp = align256(o_rowprod + (size_t)Mc * 4);
     const size_t o_xsum = align256(o_grp + (size_t)(Mc + 1) * 8);
-    const size_t o_prods = align256(o_xsum + (size_t)Mc * 8);
+    const size_t o_ymx = align256(o_xsum + (size_t)Mc * 8);
+    const size_t o_prods = align256(o_ymx + (size_t)Mc * 4);
     const size_t o_row0s = align256(o_prods + sizeof(Prod) * wcp);
     const size_t o_ps = align256(o_row0s + (size_t)(wcp + 1) * 8);
     const size_t o_small = align256(o_ps + sizeof(PStat) * wcp);
     const size_t ws_bytes = align256(o_small + sizeof(Small) * 2);
-    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod, tun.glob_dense};
+    // rows split by X entries need the warp-level walk (the staged walk reads product offsets)
+    const BinArgs ba{tun.dense_max_cols, tun.dense_min_u, tun.force_class, tun.heavy, tun.warp_prod,
+                     tun.glob_dense,     tun.lane_rows,   tun.lbs ? tun.ew_max : -1};
     int rc = MP_OK;
     Glob gl;
     PassArgs pa{};
     Small h_sym, h_num;
     std::vector<PStat> hps(w);
     std::vector<int64_t> reserved(w, 0);  // budget bytes charged for each product's result
-    // per X entry of the long rows: masked Y-row length and Y-row start (only when a row
-    // can be long; slots by the entry's position in the wave)
-    int64_t *xl = nullptr, *xs = nullptr;
     auto unreserve = [&](int p) {
         if (bud && reserved[p]) bud->unreserve(reserved[p]);
         reserved[p] = 0;
@@ -2158,14 +2451,15 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     int32_t *rowprod = (int32_t *)(ws + o_rowprod);
     int64_t *grp = (int64_t *)(ws + o_grp);
     double *xsum = (double *)(ws + o_xsum);
+    uint32_t *ymx = (uint32_t *)(ws + o_ymx);
     Prod *dprods = (Prod *)(ws + o_prods);
     int64_t *drow0s = (int64_t *)(ws + o_row0s);
     PStat *ps = (PStat *)(ws + o_ps);
     Small *sm_sym = (Small *)(ws + o_small);
     Small *sm_num = sm_sym + 1;
+    uint32_t *mlbuf = nullptr;  // masked Y-row lengths of the products that use them (row work only)
     auto fail = [&](int code) {
-        if (xl) al.free(xl, s);
-        if (xs) al.free(xs, s);
+        if (mlbuf) al.free(mlbuf, s);
         for (int p = 0; p < w; p++) {
             unreserve(p);
             if (hp[p].rp) al.free(hp[p].rp, s);
@@ -2182,6 +2476,18 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         fprintf(stderr, "mp: %s: %s\n", what, cudaGetErrorString(e));
         return false;
     };
+    if (ml_total) {
+        mlbuf = (uint32_t *)al.alloc((size_t)ml_total * 4, s);
+        if (!mlbuf) return fail(MP_ERR_NOMEM);
+        for (int p = 0; p < w; p++) {
+            if (ml_off[p] < 0) continue;
+            uint32_t *ml = mlbuf + ml_off[p];
+            hp[p].ml = ml;
+            const int64_t n = hp[p].Y.nrows;
+            kl(k_masked_len, (unsigned)std::min<int64_t>(grid_for(n, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
+               (const int64_t *)hp[p].Y.rp, hp[p].km, n, ml);
+        }
+    }
     for (int p = 0; p < w; p++) {
         hp[p].rp = (int64_t *)al.alloc((size_t)(in[p].X.nrows + 1) * 8, s);
         if (!hp[p].rp) return fail(MP_ERR_NOMEM);
@@ -2193,11 +2499,6 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         !cuda_ok(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s), "memset"))
         return fail(MP_ERR_CUDA);
 
-    if (!symbolic_only && xe_total > SHORTX) {
-        xl = (int64_t *)al.alloc((size_t)xe_total * 8, s);
-        xs = (int64_t *)al.alloc((size_t)xe_total * 8, s);
-        if (!xl || !xs) return fail(MP_ERR_NOMEM);
-    }
     pa.prods = dprods;
     pa.rowprod = rowprod;
     pa.list = list;
@@ -2206,19 +2507,26 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     // 1. row work, symbolic bins, rows grouped by bin
     if (M > 0) {
         const unsigned gr = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
+        stage_mark(prof, 0, 0, s);
         kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, long_rows, long_nb, &sm_sym->n_long, mid_rows,
-           &sm_sym->n_mid);
-        kl(k_rowwork_mid, (unsigned)tun.sm_count * 8, 256, 0, s, dprods, rowprod, prod, xsum, (const uint32_t *)mid_rows,
-           (const uint32_t *)&sm_sym->n_mid, xl, xs, xe_total);
-        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum,
-           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long, xl, xs,
-           xe_total);
-        kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, M, ba, bin, grp, &sm_sym->tally,
-           ps);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, ymx, long_rows, long_nb, &sm_sym->n_long,
+           mid_rows, &sm_sym->n_mid);
+        kl(k_rowwork_mid, (unsigned)tun.sm_count * 8, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
+           (const uint32_t *)mid_rows, (const uint32_t *)&sm_sym->n_mid);
+        kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
+           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long);
+        if (mlbuf) {  // only the row work reads the masked lengths (stream-ordered free)
+            al.free(mlbuf, s);
+            mlbuf = nullptr;
+        }
+        stage_mark(prof, 0, 1, s);
+        stage_mark(prof, 1, 0, s);
+        kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, (const uint32_t *)ymx, M, ba, bin,
+           grp, &sm_sym->tally, ps);
         kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
         kl(k_bin_fill, gr, 256, 0, s, bin, M, sm_sym->offsets, sm_sym->cursors, list);
+        stage_mark(prof, 1, 1, s);
     }
     if (!cuda_ok(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaStreamSynchronize(s), "sync"))
@@ -2228,6 +2536,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     pa.pool_head = &sm_sym->pool_head;
     // GLOBAL bin set-up: its rows, work items, product offsets, bitmap rounds
     gl.R = h_sym.tally.counts[B_GLOBAL];
+    if (gl.R) stage_mark(prof, 2, 0, s);
     if (gl.R) {
         // dense rows: as many of the qualifying rows as the dense scratch holds at once, each
         // slot as wide as the widest output among them; bitmap slots as wide as the widest
@@ -2243,8 +2552,12 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.per_round = rb ? std::max<int64_t>(1, std::min<int64_t>(rb, (int64_t)(cap / ((uint64_t)gl.nw * 8)))) : 0;
         gl.rounds = rb ? (rb + gl.per_round - 1) / gl.per_round : 0;
         gl.kept = gl.rounds == 1;
-        const int64_t xtot = (int64_t)h_sym.tally.xent[B_GLOBAL];
+        // product offsets only for the X entries of rows split by products
+        const int64_t xtot = (int64_t)h_sym.tally.gx_pw;
         gl.prod = prod;
+        gl.ymx = ymx;
+        gl.ew_max = ba.ew_max;
+        gl.kinds = (xtot > 0 ? 1 : 0) | ((uint64_t)xtot < h_sym.tally.xent[B_GLOBAL] ? 2 : 0);
         gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
@@ -2272,33 +2585,35 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             if (!cuda_ok(cudaMemsetAsync(cnt, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
             kl(k_glob_split, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s,
                (const Prod *)dprods, (const int32_t *)rowprod, (const uint32_t *)(list + h_sym.offsets[B_GLOBAL]),
-               gl.R, (const uint64_t *)prod, tun.glob_dense, gl.nd, gl.list, cnt, bin, &sm_sym->tally);
+               gl.R, (const uint64_t *)prod, (const uint32_t *)ymx, ba.ew_max, tun.glob_dense, gl.nd, gl.list, cnt, bin,
+               &sm_sym->tally);
         } else if (!cuda_ok(cudaMemcpyAsync(gl.list, list + h_sym.offsets[B_GLOBAL], (size_t)gl.R * 4,
                                             cudaMemcpyDeviceToDevice, s), "copy")) {
             return fail(MP_ERR_CUDA);
         }
         kl(k_glob_prep, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, pa, gl.list, gl.R, prod,
-           gl.xbase, gl.item_off);
+           (const uint32_t *)ymx, ba.ew_max, gl.xbase, gl.item_off);
         if (scan_i64(gl.item_off, gl.item_off, gl.R, al, s) || scan_i64(gl.xbase, gl.xbase, gl.R, al, s))
             return fail(MP_ERR_NOMEM);
-        kl(k_glob_xlen, (unsigned)std::max<int64_t>(1, std::min<int64_t>((xtot + XCH - 1) / XCH, (int64_t)tun.sm_count * 8)),
-           256, 0, s, pa, (const uint32_t *)gl.list, gl.R, (const int64_t *)gl.xbase, (const int64_t *)xl,
-           (const int64_t *)xs, gl.xoff, gl.ys);
-        if (scan_i64(gl.xoff, gl.xoff, xtot, al, s)) return fail(MP_ERR_NOMEM);
+        if (xtot > 0) {
+            kl(k_glob_xlen,
+               (unsigned)std::max<int64_t>(1, std::min<int64_t>((xtot + XCH - 1) / XCH, (int64_t)tun.sm_count * 8)), 256,
+               0, s, pa, (const uint32_t *)gl.list, gl.R, (const int64_t *)gl.xbase, gl.xoff, gl.ys);
+            if (scan_i64(gl.xoff, gl.xoff, xtot, al, s)) return fail(MP_ERR_NOMEM);
+        }
     }
-    // the long rows' per-entry lengths and Y starts have served the split-row set-up
-    if (xl) al.free(xl, s);
-    if (xs) al.free(xs, s);
-    xl = xs = nullptr;
+    if (gl.R) stage_mark(prof, 2, 1, s);
     // 2-3. symbolic pass, wave row pointers, per-product row pointers and sizes
     if (M > 0) {
         if (graphs) run_pass_graph(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof, *wc);
         else run_pass(0, pa, h_sym.tally.counts, dense_cols, tun, s, prof);
     }
     if (gl.R) glob_pass(0, gl, pa, tun, s, prof);
+    stage_mark(prof, 3, 0, s);
     if (scan_i64(grp, grp, M, al, s)) return fail(MP_ERR_NOMEM);
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
                   dprods, rowprod, grp, M, ps);
+    stage_mark(prof, 3, 1, s);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
                  "copy") ||
@@ -2306,6 +2621,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);
     if (symbolic_only) {
+        stage_collect(prof);
         for (int p = 0; p < w; p++) {
             WaveOut &o = out[p];
             o.products = hps[p].prods;
@@ -2356,9 +2672,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         if (!cuda_ok(cudaMemcpyAsync(dprods, hp.data(), sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload"))
             return fail(MP_ERR_CUDA);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
-        kl(k_numbin, g, 256, 0, s, dprods, rowprod, grp, prod, M, ba, bin, &sm_num->tally, ps);
+        stage_mark(prof, 4, 0, s);
+        kl(k_numbin, g, 256, 0, s, dprods, rowprod, grp, prod, (const uint32_t *)ymx, M, ba, bin, &sm_num->tally, ps);
         kl(k_bin_offsets, 1, 32, 0, s, sm_num->tally.counts, sm_num->offsets, sm_num->cursors);
         kl(k_bin_fill, g, 256, 0, s, bin, M, sm_num->offsets, sm_num->cursors, list);
+        stage_mark(prof, 4, 1, s);
         if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
             !cuda_ok(cudaStreamSynchronize(s), "sync"))
             return fail(MP_ERR_CUDA);
@@ -2373,6 +2691,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             return fail(MP_ERR_CUDA);
         prof_collect(prof, 1, h_num.tally);
     }
+    stage_collect(prof);
     if (!cuda_ok(cudaGetLastError(), "launch")) return fail(MP_ERR_CUDA);
     for (int p = 0; p < w; p++) {
         WaveOut &o = out[p];

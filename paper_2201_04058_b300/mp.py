@@ -22,7 +22,7 @@ MP_PLAN_DP, MP_PLAN_LEFT_TO_RIGHT, MP_PLAN_DP_SAMPLED, MP_PLAN_DP_MNC = 0, 1, 2,
 MP_INSERT_OTREE, MP_INSERT_FINAL, MP_INSERT_ALL = 0, 1, 2
 MP_BIN_AUTO, MP_BIN_WARP_HASH, MP_BIN_BLOCK_HASH, MP_BIN_DENSE, MP_BIN_GLOBAL = -1, 0, 1, 2, 3
 MP_OP_RANGE, MP_OP_EQ, MP_OP_IN = 0, 1, 2
-NBINS = 11
+NBINS = 12  # warp hash x6, block hash x3, dense, global, lane
 
 EXPORTS = [
     "mp_config_default", "mp_create", "mp_destroy", "mp_add_node_type", "mp_add_property_i32",

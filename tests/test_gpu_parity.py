@@ -60,6 +60,7 @@ def test_forced_bins_are_used(c1, c1_engines):
     mp = _mp()
     q = gen.config1_query()
     # a forced class takes every row that fits it; larger rows go to the next class up
+    # (the one-thread-per-row class, 11, only takes rows under automatic binning)
     allowed = {0: set(range(0, 11)), 1: set(range(6, 11)), 2: {9, 10}, 3: {10}}
     must = {0: set(range(0, 6)), 1: set(range(6, 9)), 2: {9}, 3: {10}}
     for force in allowed:
@@ -389,3 +390,107 @@ def test_walk_kernel_stats(c1, glob_dense, monkeypatch):
             assert ks["walk_num"]["ms"] <= ks["num_global"]["ms"]
     finally:
         e.close()
+
+
+@pytest.mark.parametrize("dsm_cols", [0, 24, 1 << 13])
+@pytest.mark.parametrize("glob_dense", [1e-9, 1.0])
+def test_dense_rows_in_shared_memory(c1, c2_small, dsm_cols, glob_dense, monkeypatch):
+    """Dense split rows whose output is narrow enough add their counts in a shared-memory
+    row per block and flush it to the dense row on every row change (dsm_cols = 8192, the
+    default); with the variant off (0) or narrower than the outputs (24) they add straight
+    into the global dense row. Same results as the oracle, alone and batched."""
+    mp = _mp()
+    tune = f"dsm_cols={dsm_cols},glob_dense={glob_dense}"
+    monkeypatch.setenv("MP_TUNING", tune)
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (tune, "".join(q["types"])))
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g in zip(qs, res):
+                assert_same(g, OC.evaluate(o, q), (tune, "batch", "".join(q["types"])))
+            ks, _ = mp.mp_kernel_stats(e.ctx)
+            assert "walk_dense" in ks
+        finally:
+            e.close()
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+@pytest.mark.parametrize("lane_rows", [0, 1])
+def test_lane_rows(c1, c2_small, graphs, lane_rows, monkeypatch):
+    """Rows of at most 16 Gustavson products under automatic binning: one thread per row
+    (merged by insertion into a sorted list) or, with the class off, the warp-hash bins;
+    directly and replayed as graphs, alone and batched, the oracle's results. The class
+    takes rows in both passes when on and none when off."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"lane_rows={lane_rows},graphs={graphs}")
+    for (h, o), qs in ((c1, gen.random_queries(c1[0], 43, 14, lengths=(2, 7), p_cons=0.4) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, policy=mp.MP_POLICY_NONE)
+        try:
+            lane = {"sym_bins": 0, "num_bins": 0}
+            for rnd in range(2):
+                for q in qs:
+                    rc, t = e.submit(q)
+                    assert rc == 0
+                    st = mp.mp_result_stats(e.ctx, t)
+                    for k in lane:
+                        lane[k] += int(st[k][11])
+                    assert_same(e.fetch(t), OC.evaluate(o, q), ("lane", lane_rows, graphs, rnd, "".join(q["types"])))
+                    e.release(t)
+                rc, res = e.run_batch(qs)
+                assert rc == 0
+                for q, g in zip(qs, res):
+                    assert_same(g, OC.evaluate(o, q), ("lane batch", lane_rows, graphs, rnd, "".join(q["types"])))
+            if lane_rows:
+                assert lane["sym_bins"] > 0 and lane["num_bins"] > 0, lane
+            else:
+                assert lane == {"sym_bins": 0, "num_bins": 0}, lane
+        finally:
+            e.close()
+
+
+@pytest.mark.parametrize("ew_max", [-1, 0, 4, 64, 1 << 20])
+@pytest.mark.parametrize("glob_dense", [0, 1e-9, 1.0])
+def test_split_rows_by_entries(c1, c2_small, ew_max, glob_dense, monkeypatch):
+    """Split rows whose masked Y rows are all short (at most ew_max entries) are cut into
+    work items of X entries, each entry's Y row looked up as it is walked; the others into
+    items of products with per-entry offsets (ew_max = -1: every row). Bitmap rows, dense
+    rows and a mix, alone and batched: the oracle's results."""
+    mp = _mp()
+    tune = f"ew_max={ew_max},glob_dense={glob_dense}"
+    monkeypatch.setenv("MP_TUNING", tune)
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()] +
+                        gen.random_queries(c1[0], 44, 8, lengths=(2, 6), p_cons=0.5)),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (tune, "".join(q["types"])))
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g in zip(qs, res):
+                assert_same(g, OC.evaluate(o, q), (tune, "batch", "".join(q["types"])))
+        finally:
+            e.close()
+
+
+@pytest.mark.parametrize("row_lens", [0, 1])
+def test_masked_row_lengths(c1, c2_small, row_lens, monkeypatch):
+    """The row work reading precomputed masked Y-row lengths (products without a row mask
+    whose X has at least as many entries as Y has rows) or the Y row pointers and the mask:
+    same bins, same results as the oracle, with and without split rows."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"row_lens={row_lens}")
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + gen.random_queries(c1[0], 45, 10, lengths=(2, 6), p_cons=0.3)),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        for force in (-1, mp.MP_BIN_GLOBAL):
+            e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
+            try:
+                for q in qs:
+                    assert_same(e.run(q), OC.evaluate(o, q), (row_lens, force, "".join(q["types"])))
+            finally:
+                e.close()
