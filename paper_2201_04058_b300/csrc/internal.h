@@ -54,6 +54,8 @@ struct Tuning {
     int lbs = 1;                 // split-row kernel: warp-level product walk (0: block-staged walk)
     int lbs_occ = 6;             // resident blocks per SM of the warp-walk count-adding passes (6 or 4)
     int lane_rows = 1;           // rows of at most LANE_PROD products: one thread per row (0: warp-hash bins)
+    int compact = 1;             // large pattern leaves enter products with their column mask applied (0: off)
+    int64_t compact_min = 1 << 20;  // ... when they hold at least this many entries
     int row_lens = 1;            // masked Y-row length arrays for products with X.nnz >= Y.nrows (0: off)
     int ew_max = 64;             // split rows whose masked Y rows hold at most this many entries are cut
                                  // into runs of X entries (-1: always runs of products)
@@ -198,6 +200,14 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
                 WaveCache *wc = nullptr, Budget *bud = nullptr);
 
 // C = diag(rm) A diag(cm) with every value 1 (a length-2 metapath). Returns MP_* code.
+// B = A diag(m) for a pattern CSR A (rows unchanged, entries in order), into new device
+// arrays the caller frees (*rp_out, *ci_out); out->nnz is A's (an upper bound).
+int compact_cols(const DCsr &A, const uint32_t *m, Alloc &al, const Tuning &tun, cudaStream_t s, DCsr *out,
+                 int64_t **rp_out, int32_t **ci_out);
+// Adds the Gustavson products of diag(rm) X diag(km) Y (Y's column mask not applied) into
+// the device counter *out (zeroed by the caller).
+void raw_products(const DCsr &X, const uint32_t *rm, const uint32_t *km, const int64_t *yrp, const Tuning &tun,
+                  cudaStream_t s, unsigned long long *out);
 int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al,
            const Tuning &tun, cudaStream_t s, Mat *out);
 

@@ -260,6 +260,137 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
     return MP_OK;
 }
 
+// ------------------------------------------------------------------ column-masked copies
+
+// B = A diag(m) for a pattern CSR A: rows unchanged, each row's entries whose column passes
+// m kept in order. Balanced over entries, so a hub row spreads over many blocks: K(e), the
+// number of kept entries before flat position e, gives every kept entry its position and
+// every row its start (B.rp[r] = K(A.rp[r])). Chunks of CC_CH entries tile positions
+// [0, nnz] (the last chunk holds position nnz, where the rows that end the matrix start).
+static constexpr int CC_NT = 256, CC_PER = 8, CC_CH = CC_NT * CC_PER;
+
+__global__ void __launch_bounds__(CC_NT) k_cc_count(const int32_t *__restrict__ ci, int64_t nnz,
+                                                    const uint32_t *__restrict__ m, int64_t nch, int64_t *cnt) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int64_t eb = c * CC_CH + (int64_t)threadIdx.x * CC_PER;
+        int64_t n = 0;
+#pragma unroll
+        for (int t = 0; t < CC_PER; t++)
+            if (eb + t < nnz && bit_of(m, (uint32_t)__ldg(ci + eb + t))) n++;
+        block_excl_scan<CC_NT>(n, ws, &tot);
+        if (threadIdx.x == 0) cnt[c] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(CC_NT) k_cc_fill(const int64_t *__restrict__ rp, int64_t nrows,
+                                                   const int32_t *__restrict__ ci, int64_t nnz,
+                                                   const uint32_t *__restrict__ m, int64_t nch,
+                                                   const int64_t *__restrict__ base, int64_t *rp2, int32_t *ci2) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    __shared__ int32_t pre[CC_CH];  // kept entries of the chunk before each offset
+    __shared__ int64_t s_rlo;
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int64_t e0 = c * CC_CH;
+        const int64_t eb = e0 + (int64_t)threadIdx.x * CC_PER;
+        int32_t j[CC_PER];
+        bool f[CC_PER];
+        int64_t n = 0;
+#pragma unroll
+        for (int t = 0; t < CC_PER; t++) {
+            j[t] = eb + t < nnz ? __ldg(ci + eb + t) : 0;
+            f[t] = eb + t < nnz && bit_of(m, (uint32_t)j[t]);
+            n += f[t];
+        }
+        int64_t local = block_excl_scan<CC_NT>(n, ws, &tot);
+        int64_t k = base[c] + local;
+#pragma unroll
+        for (int t = 0; t < CC_PER; t++) {
+            pre[threadIdx.x * CC_PER + t] = (int32_t)local;
+            if (f[t]) {
+                ci2[k++] = j[t];
+                local++;
+            }
+        }
+        if (threadIdx.x == 0) {  // the first row starting at or after e0
+            int64_t lo = 0, hi = nrows;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (__ldg(rp + mid) < e0) lo = mid + 1; else hi = mid;
+            }
+            s_rlo = lo;
+        }
+        __syncthreads();
+        for (int64_t r = s_rlo + threadIdx.x; r <= nrows; r += CC_NT) {
+            const int64_t a = __ldg(rp + r);
+            if (a >= e0 + CC_CH) break;
+            rp2[r] = base[c] + pre[a - e0];
+        }
+        __syncthreads();
+    }
+}
+
+// The Gustavson products of diag(rm) X diag(km) Y before Y's column mask: the sum over the
+// entries (i, k) of X that pass rm and km of |Y row k|, added into *out. Flat over X's
+// entries (a row with many entries spreads over the grid); an entry's row is found by
+// binary search only when there is a row mask to read.
+__global__ void k_raw_products(DCsr X, const uint32_t *__restrict__ rm, const uint32_t *__restrict__ km,
+                               const int64_t *__restrict__ yrp, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < X.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = (uint32_t)__ldg(X.ci + e);
+        if (!bit_of(km, k)) continue;
+        if (rm) {
+            int64_t lo = 0, hi = X.nrows - 1;  // the last row starting at or before e
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(X.rp + mid) <= e) lo = mid; else hi = mid - 1;
+            }
+            if (!bit_of(rm, (uint32_t)lo)) continue;
+        }
+        s += (unsigned long long)(__ldg(yrp + k + 1) - __ldg(yrp + k));
+    }
+    for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+void raw_products(const DCsr &X, const uint32_t *rm, const uint32_t *km, const int64_t *yrp, const Tuning &tun,
+                  cudaStream_t s, unsigned long long *out) {
+    if (X.nnz <= 0) return;
+    kl(k_raw_products, (unsigned)std::min<int64_t>(grid_for(X.nnz, 256), (int64_t)tun.sm_count * 8), 256, 0, s, X,
+       rm, km, yrp, out);
+}
+
+int compact_cols(const DCsr &A, const uint32_t *m, Alloc &al, const Tuning &tun, cudaStream_t s, DCsr *out,
+                 int64_t **rp_out, int32_t **ci_out) {
+    const int64_t nch = A.nnz / CC_CH + 1;
+    int64_t *cnt = (int64_t *)al.alloc((size_t)(nch + 1) * 8, s);
+    int64_t *rp2 = (int64_t *)al.alloc((size_t)(A.nrows + 1) * 8, s);
+    int32_t *ci2 = (int32_t *)al.alloc((size_t)std::max<int64_t>(A.nnz, 1) * 4, s);  // at most A's entries
+    if (!cnt || !rp2 || !ci2) {
+        if (cnt) al.free(cnt, s);
+        if (rp2) al.free(rp2, s);
+        if (ci2) al.free(ci2, s);
+        return MP_ERR_NOMEM;
+    }
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, (int64_t)tun.sm_count * 8));
+    kl(k_cc_count, g, CC_NT, 0, s, A.ci, A.nnz, m, nch, cnt);
+    if (scan_i64(cnt, cnt, nch, al, s)) {
+        al.free(cnt, s);
+        al.free(rp2, s);
+        al.free(ci2, s);
+        return MP_ERR_NOMEM;
+    }
+    kl(k_cc_fill, g, CC_NT, 0, s, A.rp, A.nrows, A.ci, A.nnz, m, nch, (const int64_t *)cnt, rp2, ci2);
+    al.free(cnt, s);
+    *out = DCsr{rp2, ci2, nullptr, A.nrows, A.ncols, A.nnz};  // nnz: an upper bound (not read back)
+    *rp_out = rp2;
+    *ci_out = ci2;
+    return MP_OK;
+}
+
 __global__ void k_mask_and_in_values(uint32_t *m, const int32_t *prop, int64_t n, const int64_t *set,
                                      int64_t len) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

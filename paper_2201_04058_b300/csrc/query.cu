@@ -879,6 +879,29 @@ int mp_ctx::run_wave() {
     CtxBudget bud(this);
     std::vector<int64_t> members;
     std::vector<WaveIn> win;
+    std::vector<void *> scratch;  // column-masked copies of leaves, freed after the wave
+    std::vector<size_t> ycand;    // wave inputs whose Y copy depends on the products they read
+    auto release_scratch = [&] {
+        for (void *p : scratch) alloc->free(p, stream);
+        scratch.clear();
+    };
+    // A large pattern leaf enters its product with the mask on its columns applied, so the
+    // row work and the walks never read an entry the mask drops: X (no row mask, so all its
+    // rows are read) by the middle mask; Y by the column mask when X holds at least an eighth
+    // as many entries as Y has rows, or otherwise when the products of X with Y, counted
+    // exactly on the device (one count per such product and one synchronisation per wave),
+    // read at least half of Y's entries. The middle or column mask then has nothing left to
+    // drop.
+    auto compact = [&](DCsr &A, const uint32_t *m) {
+        DCsr B;
+        int64_t *rp = nullptr;
+        int32_t *ci = nullptr;
+        if (compact_cols(A, m, *alloc, tun, stream, &B, &rp, &ci)) return false;
+        scratch.push_back(rp);
+        scratch.push_back(ci);
+        A = B;
+        return true;
+    };
     for (int64_t id : ready) {
         PNode &nd = node(id);
         const Query &Q = nd.qs->q;
@@ -912,14 +935,44 @@ int mp_ctx::run_wave() {
         in.rm = nd.left < 0 ? M[i] : nullptr;
         in.km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
         in.cm = nd.right < 0 ? M[j + 1] : nullptr;
+        if (tun.compact) {
+            if (nd.left < 0 && !in.rm && in.km && !in.X.val && in.X.nnz >= tun.compact_min && compact(in.X, in.km))
+                in.km = nullptr;
+            if (nd.right < 0 && in.cm && !in.Y.val && in.Y.nnz >= tun.compact_min) {
+                if (in.X.nnz * 8 >= in.Y.nrows) {
+                    if (compact(in.Y, in.cm)) in.cm = nullptr;
+                } else {
+                    ycand.push_back(win.size());
+                }
+            }
+        }
         members.push_back(id);
         win.push_back(in);
+    }
+    if (!ycand.empty()) {
+        // the products each candidate reads, in one device array and one copy back
+        auto *cnt = (unsigned long long *)alloc->alloc(ycand.size() * 8, stream);
+        std::vector<unsigned long long> h(ycand.size(), 0);
+        bool ok = cnt && cudaMemsetAsync(cnt, 0, ycand.size() * 8, stream) == cudaSuccess;
+        for (size_t c = 0; ok && c < ycand.size(); c++) {
+            const WaveIn &in = win[ycand[c]];
+            raw_products(in.X, in.rm, in.km, in.Y.rp, tun, stream, cnt + c);
+        }
+        ok = ok && cudaMemcpyAsync(h.data(), cnt, ycand.size() * 8, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+             cudaStreamSynchronize(stream) == cudaSuccess;
+        if (cnt) alloc->free(cnt, stream);
+        if (!ok) cudaGetLastError();  // no copies: the masks apply entry by entry
+        for (size_t c = 0; ok && c < ycand.size(); c++) {
+            WaveIn &in = win[ycand[c]];
+            if ((int64_t)h[c] * 2 >= in.Y.nnz && compact(in.Y, in.cm)) in.cm = nullptr;
+        }
     }
     if (members.empty()) return MP_OK;
     std::vector<WaveOut> wout;
     auto t0 = std::chrono::steady_clock::now();
     const int wave_rc =
         spgemm_wave(win, *alloc, tun, stream, cfg.max_result_bytes, wout, &prof, false, &wcache, &bud);
+    release_scratch();
     const double wave_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     double wave_prod = 0.0;
     for (auto &o : wout) wave_prod += (double)o.products;

@@ -494,3 +494,26 @@ def test_masked_row_lengths(c1, c2_small, row_lens, monkeypatch):
                     assert_same(e.run(q), OC.evaluate(o, q), (row_lens, force, "".join(q["types"])))
             finally:
                 e.close()
+
+
+@pytest.mark.parametrize("compact", [0, 1])
+@pytest.mark.parametrize("force", [-1, 3])
+def test_masked_leaves_compacted(c1, c2_small, compact, force, monkeypatch):
+    """Pattern leaves entering a product with the mask on their columns applied (X by the
+    middle mask when X has no row mask, Y by the column mask; here every leaf qualifies),
+    or with the masks applied entry by entry: the oracle's results, alone and batched."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"compact={compact},compact_min=1")
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()] +
+                        gen.random_queries(c1[0], 46, 12, lengths=(2, 7), p_cons=0.6)),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (compact, force, "".join(q["types"])))
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g in zip(qs, res):
+                assert_same(g, OC.evaluate(o, q), (compact, force, "batch", "".join(q["types"])))
+        finally:
+            e.close()
