@@ -269,10 +269,18 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
 // [0, nnz] (the last chunk holds position nnz, where the rows that end the matrix start).
 static constexpr int CC_NT = 256, CC_PER = 8, CC_CH = CC_NT * CC_PER;
 
-__global__ void __launch_bounds__(CC_NT) k_cc_count(const int32_t *__restrict__ ci, int64_t nnz,
-                                                    const uint32_t *__restrict__ m, int64_t nch, int64_t *cnt) {
+// Also records, per chunk, the first row that starts inside it (first[c], -1 when none:
+// the caller fills first with -1 bytes), so the fill pass needs no search for its rows.
+__global__ void __launch_bounds__(CC_NT) k_cc_count(const int64_t *__restrict__ rp, int64_t nrows,
+                                                    const int32_t *__restrict__ ci, int64_t nnz,
+                                                    const uint32_t *__restrict__ m, int64_t nch, int64_t *cnt,
+                                                    int64_t *first) {
     __shared__ int64_t ws[32];
     __shared__ int64_t tot;
+    for (int64_t r = blockIdx.x * (int64_t)CC_NT + threadIdx.x; r <= nrows; r += (int64_t)gridDim.x * CC_NT) {
+        const int64_t c = __ldg(rp + r) / CC_CH;
+        if (r == 0 || __ldg(rp + r - 1) / CC_CH < c) first[c] = r;
+    }
     for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const int64_t eb = c * CC_CH + (int64_t)threadIdx.x * CC_PER;
         int64_t n = 0;
@@ -287,11 +295,11 @@ __global__ void __launch_bounds__(CC_NT) k_cc_count(const int32_t *__restrict__ 
 __global__ void __launch_bounds__(CC_NT) k_cc_fill(const int64_t *__restrict__ rp, int64_t nrows,
                                                    const int32_t *__restrict__ ci, int64_t nnz,
                                                    const uint32_t *__restrict__ m, int64_t nch,
-                                                   const int64_t *__restrict__ base, int64_t *rp2, int32_t *ci2) {
+                                                   const int64_t *__restrict__ base, const int64_t *__restrict__ first,
+                                                   int64_t *rp2, int32_t *ci2) {
     __shared__ int64_t ws[32];
     __shared__ int64_t tot;
     __shared__ int32_t pre[CC_CH];  // kept entries of the chunk before each offset
-    __shared__ int64_t s_rlo;
     for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const int64_t e0 = c * CC_CH;
         const int64_t eb = e0 + (int64_t)threadIdx.x * CC_PER;
@@ -314,16 +322,9 @@ __global__ void __launch_bounds__(CC_NT) k_cc_fill(const int64_t *__restrict__ r
                 local++;
             }
         }
-        if (threadIdx.x == 0) {  // the first row starting at or after e0
-            int64_t lo = 0, hi = nrows;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (__ldg(rp + mid) < e0) lo = mid + 1; else hi = mid;
-            }
-            s_rlo = lo;
-        }
         __syncthreads();
-        for (int64_t r = s_rlo + threadIdx.x; r <= nrows; r += CC_NT) {
+        const int64_t r0 = first[c];  // rows starting in this chunk: r0, r0 + 1, ... (none: -1)
+        for (int64_t r = r0 + threadIdx.x; r0 >= 0 && r <= nrows; r += CC_NT) {
             const int64_t a = __ldg(rp + r);
             if (a >= e0 + CC_CH) break;
             rp2[r] = base[c] + pre[a - e0];
@@ -366,7 +367,8 @@ void raw_products(const DCsr &X, const uint32_t *rm, const uint32_t *km, const i
 int compact_cols(const DCsr &A, const uint32_t *m, Alloc &al, const Tuning &tun, cudaStream_t s, DCsr *out,
                  int64_t **rp_out, int32_t **ci_out) {
     const int64_t nch = A.nnz / CC_CH + 1;
-    int64_t *cnt = (int64_t *)al.alloc((size_t)(nch + 1) * 8, s);
+    int64_t *cnt = (int64_t *)al.alloc((size_t)(2 * nch + 1) * 8, s);  // counts, then first rows
+    int64_t *first = cnt + nch + 1;
     int64_t *rp2 = (int64_t *)al.alloc((size_t)(A.nrows + 1) * 8, s);
     int32_t *ci2 = (int32_t *)al.alloc((size_t)std::max<int64_t>(A.nnz, 1) * 4, s);  // at most A's entries
     if (!cnt || !rp2 || !ci2) {
@@ -376,14 +378,16 @@ int compact_cols(const DCsr &A, const uint32_t *m, Alloc &al, const Tuning &tun,
         return MP_ERR_NOMEM;
     }
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, (int64_t)tun.sm_count * 8));
-    kl(k_cc_count, g, CC_NT, 0, s, A.ci, A.nnz, m, nch, cnt);
+    cudaMemsetAsync(first, 0xff, (size_t)nch * 8, s);
+    kl(k_cc_count, g, CC_NT, 0, s, A.rp, A.nrows, A.ci, A.nnz, m, nch, cnt, first);
     if (scan_i64(cnt, cnt, nch, al, s)) {
         al.free(cnt, s);
         al.free(rp2, s);
         al.free(ci2, s);
         return MP_ERR_NOMEM;
     }
-    kl(k_cc_fill, g, CC_NT, 0, s, A.rp, A.nrows, A.ci, A.nnz, m, nch, (const int64_t *)cnt, rp2, ci2);
+    kl(k_cc_fill, g, CC_NT, 0, s, A.rp, A.nrows, A.ci, A.nnz, m, nch, (const int64_t *)cnt, (const int64_t *)first,
+       rp2, ci2);
     al.free(cnt, s);
     *out = DCsr{rp2, ci2, nullptr, A.nrows, A.ncols, A.nnz};  // nnz: an upper bound (not read back)
     *rp_out = rp2;

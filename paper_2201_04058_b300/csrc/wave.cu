@@ -1866,15 +1866,14 @@ __global__ void k_glob_fill(PassArgs a, GlobArgs g) {
         if (!word) continue;
         const int64_t slot = x / g.nw, w = x - slot * g.nw;
         const RowRef Rf(a, g.list[g.r0 + slot]);
-        const Prod P = *Rf.P;
-        if (!P.ci) continue;
+        int32_t *ci = Rf.P->ci;
+        if (!ci) continue;
+        // column ids in order; the counts were zeroed with the product's count array
         int64_t pos = Rf.out_off(a) + br.y;
         while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
-            P.ci[pos] = (int32_t)(w * 32 + b);
-            P.val[pos] = 0;
-            pos++;
+            ci[pos++] = (int32_t)(w * 32 + b);
         }
     }
 }
@@ -2666,6 +2665,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         hp[p].val = (uint64_t *)al.alloc((size_t)std::max<int64_t>(nnz, 1) * 8, s);
         if (!hp[p].ci || !hp[p].val) return fail(MP_ERR_NOMEM);
         if (nnz) any_out = true;
+        // split rows add their counts with atomics: the counts start at zero (one streaming
+        // memset of the product's counts instead of zeros written entry by entry)
+        if (nnz && hps[p].sym_bins[B_GLOBAL] &&
+            !cuda_ok(cudaMemsetAsync(hp[p].val, 0, (size_t)nnz * 8, s), "memset"))
+            return fail(MP_ERR_CUDA);
     }
     // 4. numeric pass; products that failed keep null outputs and their rows are skipped
     if (any_out) {
