@@ -139,7 +139,7 @@ struct Alloc {
 // ---- masks: bit j of word j >> 5 set = node j passes
 void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s);
 void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
-                    cudaStream_t s);
+                    cudaStream_t s, bool assign = false);
 void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t set_len, int64_t n,
                   cudaStream_t s);
 

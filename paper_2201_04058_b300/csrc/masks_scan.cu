@@ -19,9 +19,10 @@ __global__ void k_mask_fill(uint32_t *m, int64_t nw, uint32_t v, int64_t n) {
     m[w] = x;
 }
 
-// One thread per node; a warp ballot forms one 32-node word.
+// One thread per node; a warp ballot forms one 32-node word, AND-ed into the mask (or
+// stored, for the first constraint of a position).
 __global__ void k_mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo,
-                                 int64_t hi) {
+                                 int64_t hi, int assign) {
     int64_t base = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool ok = false;
@@ -30,7 +31,10 @@ __global__ void k_mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, in
         ok = v >= lo && v <= hi;
     }
     uint32_t word = __ballot_sync(FULL, ok);
-    if ((threadIdx.x & 31) == 0 && i < n) m[(base + (threadIdx.x & ~31)) >> 5] &= word;
+    if ((threadIdx.x & 31) == 0 && i < n) {
+        uint32_t *w = m + ((base + (threadIdx.x & ~31)) >> 5);
+        *w = assign ? word : (*w & word);
+    }
 }
 
 __global__ void k_set_bits(uint32_t *m, const uint32_t *set, int64_t len, int64_t n) {
@@ -52,8 +56,8 @@ void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s) {
 }
 
 void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
-                    cudaStream_t s) {
-    if (n) kl(k_mask_and_range, grid_for(n, 256), 256, 0, s, m, prop, n, lo, hi);
+                    cudaStream_t s, bool assign) {
+    if (n) kl(k_mask_and_range, grid_for(n, 256), 256, 0, s, m, prop, n, lo, hi, (int)assign);
 }
 
 void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t len, int64_t n,
@@ -176,9 +180,37 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int64_t *in, int64_
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = part[nb];
 }
 
+// Short arrays (up to 1024 x SMALL_PER elements) in one block and one launch.
+static constexpr int SMALL_PER = 16;
+
+__global__ void __launch_bounds__(1024) k_scan_small(const int64_t *in, int64_t *out, int64_t n) {
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    const int64_t base = (int64_t)threadIdx.x * SMALL_PER;
+    int64_t v[SMALL_PER];
+    int64_t s = 0;
+#pragma unroll
+    for (int t = 0; t < SMALL_PER; t++) {
+        v[t] = base + t < n ? in[base + t] : 0;
+        s += v[t];
+    }
+    int64_t e = block_excl_scan<1024>(s, ws, &tot);
+    // every read of the block is done (the scan synchronised), so out may alias in
+#pragma unroll
+    for (int t = 0; t < SMALL_PER; t++) {
+        if (base + t < n) out[base + t] = e;
+        e += v[t];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 int scan_i64(const int64_t *in, int64_t *out, int64_t n, Alloc &al, cudaStream_t s) {
     if (n == 0) {
         cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+        return MP_OK;
+    }
+    if (n <= 1024 * SMALL_PER) {
+        kl(k_scan_small, 1, 1024, 0, s, in, out, n);
         return MP_OK;
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;

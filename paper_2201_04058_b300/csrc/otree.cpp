@@ -47,6 +47,30 @@ std::string restrict_key(const std::string &key, size_t len) {
     return out;
 }
 
+// restrict_key(ekey, len) == pkey, without building the restricted key: the parts of ekey
+// whose position is below len, joined by '|', must spell pkey exactly.
+static bool restricted_equals(const std::string &ekey, size_t len, const std::string &pkey) {
+    size_t a = 0, c = 0;  // cursors in ekey and pkey
+    bool any = false;
+    while (a < ekey.size()) {
+        size_t b = ekey.find('|', a);
+        if (b == std::string::npos) b = ekey.size();
+        size_t pos = 0, d = a;
+        while (d < b && ekey[d] >= '0' && ekey[d] <= '9') pos = pos * 10 + (size_t)(ekey[d++] - '0');
+        if (pos < len) {
+            if (any) {
+                if (c >= pkey.size() || pkey[c] != '|') return false;
+                c++;
+            }
+            if (pkey.compare(c, b - a, ekey, a, b - a) != 0) return false;
+            c += b - a;
+            any = true;
+        }
+        a = b + 1;
+    }
+    return c == pkey.size();
+}
+
 OverlapTree::OverlapTree(int construction) : construction_(construction == ONLINE ? ONLINE : NAIVE) {
     nodes_.emplace_back();
 }
@@ -243,7 +267,7 @@ uint64_t OverlapTree::frequency(const int32_t *s, size_t n, const std::string *k
     // every occurrence through x carries a key of at least n positions: restrict and count
     uint64_t f = 0;
     for (const auto &kv : nodes_[x].cidx)
-        if (restrict_key(kv.first, n) == *key) f += kv.second.f;
+        if (restricted_equals(kv.first, n, *key)) f += kv.second.f;
     return f;
 }
 
@@ -301,7 +325,21 @@ std::string CachePolicy::make_id(const std::vector<int32_t> &types, const std::s
 bool CachePolicy::in_subtree(const CacheItem &p, const CacheItem &e) {
     if (p.types.size() >= e.types.size()) return false;
     if (!std::equal(p.types.begin(), p.types.end(), e.types.begin())) return false;
-    return restrict_key(e.key, p.types.size()) == p.key;
+    return restricted_equals(e.key, p.types.size(), p.key);
+}
+
+// f(e) for every item e in p's subtree: only the ids that start with p's types (the range
+// of the ordered map from p's type prefix) are candidates.
+template <class F>
+void CachePolicy::for_subtree(const CacheItem &p, F &&f) {
+    std::string prefix;
+    for (int32_t t : p.types) {
+        prefix += std::to_string(t);
+        prefix += ',';
+    }
+    for (auto it = items_.lower_bound(prefix); it != items_.end() && it->first.compare(0, prefix.size(), prefix) == 0;
+         ++it)
+        if (in_subtree(p, it->second)) f(it->second);
 }
 
 bool CachePolicy::evict_victim(CacheItem *out) {
@@ -317,11 +355,10 @@ bool CachePolicy::evict_victim(CacheItem *out) {
     used_ -= q.s;
     if (policy_ != LRU) L_ = q.h;
     if (policy_ == ATRAPOS)
-        for (auto &kv : items_)
-            if (in_subtree(q, kv.second)) {
-                kv.second.c += q.c;
-                util(kv.second);
-            }
+        for_subtree(q, [&](CacheItem &e) {
+            e.c += q.c;
+            util(e);
+        });
     *out = std::move(q);
     return true;
 }
@@ -374,11 +411,10 @@ CachePolicy::Outcome CachePolicy::request(const std::vector<int32_t> &types, con
     util(p);
     used_ += s;
     if (policy_ == ATRAPOS)
-        for (auto &kv : items_)
-            if (in_subtree(p, kv.second)) {
-                kv.second.c = std::max(0.0, kv.second.c - p.c);
-                util(kv.second);
-            }
+        for_subtree(p, [&](CacheItem &e) {
+            e.c = std::max(0.0, e.c - p.c);
+            util(e);
+        });
     items_.emplace(id, std::move(p));
     return INSERTED;
 }

@@ -1,6 +1,7 @@
 // Overlap Tree (Sec. 3.3) and cache replacement policies (Sec. 3.4, Alg. 1): host side.
 #pragma once
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <string>
 #include <unordered_map>
@@ -120,8 +121,12 @@ class CachePolicy {
     double max_fraction_;
     double L_ = 0.0, used_ = 0.0;
     uint64_t seq_ = 0;
-    std::unordered_map<std::string, CacheItem> items_;
+    // ordered by id, which starts with the item's types: the items whose metapath extends a
+    // given one are one contiguous range (the Overlap-Tree subtree walks visit only it)
+    std::map<std::string, CacheItem> items_;
     static bool in_subtree(const CacheItem &parent, const CacheItem &child);
+    template <class F>
+    void for_subtree(const CacheItem &parent, F &&f);
     void util(CacheItem &e) const { e.h = e.f * e.c / e.s + e.l; }
 };
 

@@ -229,18 +229,28 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
     masks.assign(n, nullptr);
     for (int i = 0; i < n; i++) {
         if (q.cons[i].empty()) continue;
+        // a position of the same type with the same constraints (the canonical key) shares
+        // its mask (every P of a year-windowed metapath, say)
+        for (int j = 0; j < i && !masks[i]; j++)
+            if (masks[j] && q.types[j] == q.types[i] && q.pos_keys[j] == q.pos_keys[i]) masks[i] = masks[j];
+        if (masks[i]) continue;
         const int64_t cnt = types[q.types[i]].count;
         const size_t nw = (size_t)(cnt + 31) / 32;
         uint32_t *m = (uint32_t *)alloc->alloc(std::max<size_t>(nw, 1) * 4, stream);
         if (!m) return MP_ERR_NOMEM;
         masks[i] = m;
-        mask_fill(m, cnt, true, stream);
+        // the first constraint stores its words when it is a range; otherwise all ones first
+        const bool first_range = q.cons[i][0].op == MP_OP_RANGE || q.cons[i][0].op == MP_OP_EQ;
+        if (!first_range) mask_fill(m, cnt, true, stream);
+        bool first = true;
         for (const Constraint &c : q.cons[i]) {
             const int32_t *prop = c.prop >= 0 ? props[c.prop].dev : nullptr;
             if (c.op == MP_OP_RANGE || c.op == MP_OP_EQ) {
-                mask_and_range(m, prop, cnt, c.lo, c.hi, stream);
+                mask_and_range(m, prop, cnt, c.lo, c.hi, stream, first && first_range);
+                first = false;
                 continue;
             }
+            first = false;
             const int64_t len = (int64_t)c.set.size();
             if (!prop) {
                 uint32_t *tmp = (uint32_t *)alloc->alloc(std::max<size_t>(nw, 1) * 4, stream);
@@ -269,8 +279,12 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
 }
 
 void mp_ctx::free_masks(std::vector<uint32_t *> &masks) {
-    for (auto *m : masks)
-        if (m) alloc->free(m, stream);
+    for (size_t i = 0; i < masks.size(); i++) {
+        if (!masks[i]) continue;
+        bool shared = false;  // positions with equal constraints hold one mask
+        for (size_t j = 0; j < i && !shared; j++) shared = masks[j] == masks[i];
+        if (!shared) alloc->free(masks[i], stream);
+    }
     masks.clear();
 }
 

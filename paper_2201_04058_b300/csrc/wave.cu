@@ -533,21 +533,25 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
     }
 }
 
-// counts[0..NBINS) -> offsets[0..NBINS]; cursors reset.
-__global__ void k_bin_offsets(const uint32_t *counts, uint32_t *offsets, uint32_t *cursors) {
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int b = 0; b < NBINS; b++) {
-            offsets[b] = s;
-            s += counts[b];
-            cursors[b] = 0;
-        }
-        offsets[NBINS] = s;
-    }
-}
-
-__global__ void k_bin_fill(const int8_t *bin, int64_t n, const uint32_t *offsets, uint32_t *cursors, uint32_t *list) {
+// Rows grouped by bin: every block derives the bins' offsets from their counts (block 0
+// also stores them, with the total, for the passes and the host); the cursors start at
+// zero (the wave's tallies are zeroed when it begins).
+__global__ void k_bin_fill(const int8_t *bin, int64_t n, const uint32_t *counts, uint32_t *offsets, uint32_t *cursors,
+                           uint32_t *list) {
+    __shared__ uint32_t s_off[NBINS];
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int b = 0; b < NBINS; b++) {
+            s_off[b] = t;
+            t += counts[b];
+        }
+        if (blockIdx.x == 0) {
+            for (int b = 0; b < NBINS; b++) offsets[b] = s_off[b];
+            offsets[NBINS] = t;
+        }
+    }
+    __syncthreads();
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
         const int b = i < n ? bin[i] : -1;
@@ -558,7 +562,7 @@ __global__ void k_bin_fill(const int8_t *bin, int64_t n, const uint32_t *offsets
             if (lane == leader) base = atomicAdd(cursors + b, (uint32_t)__popc(peers));
             base = __shfl_sync(peers, base, leader);
             const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-            list[offsets[b] + base + rank] = (uint32_t)i;
+            list[s_off[b] + base + rank] = (uint32_t)i;
         }
     }
 }
@@ -2523,8 +2527,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         stage_mark(prof, 1, 0, s);
         kl(k_binassign, gr, 256, 0, s, dprods, rowprod, prod, (const double *)xsum, (const uint32_t *)ymx, M, ba, bin,
            grp, &sm_sym->tally, ps);
-        kl(k_bin_offsets, 1, 32, 0, s, sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors);
-        kl(k_bin_fill, gr, 256, 0, s, bin, M, sm_sym->offsets, sm_sym->cursors, list);
+        kl(k_bin_fill, gr, 256, 0, s, bin, M, (const uint32_t *)sm_sym->tally.counts, sm_sym->offsets, sm_sym->cursors,
+           list);
         stage_mark(prof, 1, 1, s);
     }
     if (!cuda_ok(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
@@ -2678,8 +2682,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
         stage_mark(prof, 4, 0, s);
         kl(k_numbin, g, 256, 0, s, dprods, rowprod, grp, prod, (const uint32_t *)ymx, M, ba, bin, &sm_num->tally, ps);
-        kl(k_bin_offsets, 1, 32, 0, s, sm_num->tally.counts, sm_num->offsets, sm_num->cursors);
-        kl(k_bin_fill, g, 256, 0, s, bin, M, sm_num->offsets, sm_num->cursors, list);
+        kl(k_bin_fill, g, 256, 0, s, bin, M, (const uint32_t *)sm_num->tally.counts, sm_num->offsets, sm_num->cursors,
+           list);
         stage_mark(prof, 4, 1, s);
         if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
             !cuda_ok(cudaStreamSynchronize(s), "sync"))
