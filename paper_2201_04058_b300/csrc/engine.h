@@ -38,6 +38,7 @@ struct DevMat {
         if (m.rp) al->free(m.rp, s);
         if (m.ci) al->free(m.ci, s);
         if (m.val) al->free(m.val, s);
+        if (m.arows) al->free(m.arows, s);
     }
 };
 using MatPtr = std::shared_ptr<DevMat>;
@@ -183,8 +184,10 @@ struct mp_ctx {
     void htier_clear();
 
     int parse(const mp_query *q, Query &out);
-    int build_masks(const Query &q, std::vector<uint32_t *> &masks);
+    int build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vector<int32_t *> *rows = nullptr,
+                    std::vector<int64_t> *nrows = nullptr);
     void free_masks(std::vector<uint32_t *> &masks);
+    void free_row_lists(std::vector<int32_t *> &rows, std::vector<int64_t> &nrows);
 
     // ---- the executor: a product DAG that queries join as they are admitted (query.cu)
     //
@@ -195,6 +198,10 @@ struct mp_ctx {
         mp_ctx *ctx = nullptr;
         Query q;
         std::vector<uint32_t *> masks;
+        // per position whose one constraint is a node-id set: the ids, ascending, on the
+        // device (a factor that starts there runs over these rows only), and their count
+        std::vector<int32_t *> rows;
+        std::vector<int64_t> nrows;
         ~QState();
     };
     struct Flight {

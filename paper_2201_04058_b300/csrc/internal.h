@@ -20,6 +20,10 @@ struct DCsr {
     const uint64_t *val = nullptr;
     int64_t nrows = 0, ncols = 0;
     int64_t nnz = 0;
+    // rows that may be non-empty, ascending (null: any row may be); a product over this
+    // matrix then runs over these rows only
+    const int32_t *arows = nullptr;
+    int64_t narows = 0;
 };
 
 // Row-bin classes. Warp-hash bins hold one row per warp in a shared-memory table of T
@@ -54,6 +58,7 @@ struct Tuning {
     int lbs = 1;                 // split-row kernel: warp-level product walk (0: block-staged walk)
     int lbs_occ = 6;             // resident blocks per SM of the warp-walk count-adding passes (6 or 4)
     int lane_rows = 1;           // rows of at most LANE_PROD products: one thread per row (0: warp-hash bins)
+    int row_lists = 1;           // products over X's row list when it is short (0: over all rows)
     int compact = 1;             // large pattern leaves enter products with their column mask applied (0: off)
     int64_t compact_min = 1 << 20;  // ... when they hold at least this many entries
     int row_lens = 1;            // masked Y-row length arrays for products with X.nnz >= Y.nrows (0: off)
@@ -123,8 +128,10 @@ struct Mat {
     int32_t *ci = nullptr;
     uint64_t *val = nullptr;   // nullptr only for base relations
     uint64_t vmax = 1;         // upper bound on the values (1: 0/1 pattern; UINT64_MAX: none known)
+    int32_t *arows = nullptr;  // owned: ascending rows outside which every row is empty (or null)
+    int64_t narows = 0;
     size_t bytes() const { return (size_t)(nrows + 1) * 8 + (size_t)nnz * 12; }
-    DCsr view() const { return DCsr{rp, ci, val, nrows, ncols, nnz}; }
+    DCsr view() const { return DCsr{rp, ci, val, nrows, ncols, nnz, arows, narows}; }
 };
 
 // Stream-ordered device allocation used for results and workspaces. fail_after (tests):
@@ -138,6 +145,7 @@ struct Alloc {
 
 // ---- masks: bit j of word j >> 5 set = node j passes
 void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s);
+void fill_iota(int32_t *d, int64_t lo, int64_t n, cudaStream_t s);  // d[t] = lo + t, t < n
 void mask_and_range(uint32_t *m, const int32_t *prop, int64_t n, int64_t lo, int64_t hi,
                     cudaStream_t s, bool assign = false);
 void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t set_len, int64_t n,

@@ -50,6 +50,15 @@ __global__ void k_and_words(uint32_t *m, const uint32_t *t, int64_t nw) {
 }
 
 
+__global__ void k_iota(int32_t *d, int64_t lo, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) d[t] = (int32_t)(lo + t);
+}
+
+void fill_iota(int32_t *d, int64_t lo, int64_t n, cudaStream_t s) {
+    if (n > 0) kl(k_iota, grid_for(n, 256), 256, 0, s, d, lo, n);
+}
+
 void mask_fill(uint32_t *m, int64_t n, bool ones, cudaStream_t s) {
     int64_t nw = (n + 31) / 32;
     if (nw) kl(k_mask_fill, grid_for(nw, 256), 256, 0, s, m, nw, ones ? FULL : 0u, n);

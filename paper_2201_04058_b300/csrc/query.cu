@@ -53,6 +53,7 @@ void mp_ctx::free_mat(Mat &m) {
     if (m.rp) alloc->free(m.rp, stream);
     if (m.ci) alloc->free(m.ci, stream);
     if (m.val) alloc->free(m.val, stream);
+    if (m.arows) alloc->free(m.arows, stream);
     m = Mat{};
 }
 
@@ -170,6 +171,8 @@ void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vect
     e.shape.rp = nullptr;
     e.shape.ci = nullptr;
     e.shape.val = nullptr;
+    e.shape.arows = nullptr;  // copied back without its row list (any row may be non-empty)
+    e.shape.narows = 0;
     e.off = off;
     e.bytes = bytes;
     e.c_ms = c_ms;
@@ -224,15 +227,22 @@ MatPtr mp_ctx::htier_load(const std::string &id) {
     return wrap(m, true);
 }
 
-int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
+int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vector<int32_t *> *rows,
+                        std::vector<int64_t> *nrows) {
     const int n = (int)q.types.size();
     masks.assign(n, nullptr);
+    if (rows) rows->assign(n, nullptr);
+    if (nrows) nrows->assign(n, 0);
     for (int i = 0; i < n; i++) {
         if (q.cons[i].empty()) continue;
         // a position of the same type with the same constraints (the canonical key) shares
         // its mask (every P of a year-windowed metapath, say)
         for (int j = 0; j < i && !masks[i]; j++)
-            if (masks[j] && q.types[j] == q.types[i] && q.pos_keys[j] == q.pos_keys[i]) masks[i] = masks[j];
+            if (masks[j] && q.types[j] == q.types[i] && q.pos_keys[j] == q.pos_keys[i]) {
+                masks[i] = masks[j];
+                if (rows) (*rows)[i] = (*rows)[j];
+                if (nrows) (*nrows)[i] = (*nrows)[j];
+            }
         if (masks[i]) continue;
         const int64_t cnt = types[q.types[i]].count;
         const size_t nw = (size_t)(cnt + 31) / 32;
@@ -241,6 +251,20 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
         masks[i] = m;
         // the first constraint stores its words when it is a range; otherwise all ones first
         const bool first_range = q.cons[i][0].op == MP_OP_RANGE || q.cons[i][0].op == MP_OP_EQ;
+        if (rows && first_range && q.cons[i].size() == 1 && q.cons[i][0].prop < 0) {
+            // the position's only constraint is a window of node ids: those ids are its row
+            // list when they are few (an anchor entity, say)
+            const int64_t lo = std::max<int64_t>(q.cons[i][0].lo, 0);
+            const int64_t hi = std::min<int64_t>(q.cons[i][0].hi, cnt - 1);
+            const int64_t len = std::max<int64_t>(hi - lo + 1, 0);
+            if (len * 8 <= cnt) {
+                int32_t *d = (int32_t *)alloc->alloc((size_t)std::max<int64_t>(len, 1) * 4, stream);
+                if (!d) return MP_ERR_NOMEM;
+                fill_iota(d, lo, len, stream);
+                (*rows)[i] = d;
+                (*nrows)[i] = len;
+            }
+        }
         if (!first_range) mask_fill(m, cnt, true, stream);
         bool first = true;
         for (const Constraint &c : q.cons[i]) {
@@ -263,7 +287,15 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks) {
                 if (len) cudaMemcpyAsync(dset, c.set.data(), len * 4, cudaMemcpyHostToDevice, stream);
                 mask_and_set(m, tmp, dset, len, cnt, stream);
                 alloc->free(tmp, stream);
-                alloc->free(dset, stream);
+                if (rows && q.cons[i].size() == 1) {
+                    // the position's only constraint: the set (sorted, without repeats since
+                    // parsing) is also its row list, without the ids past the type's count
+                    (*rows)[i] = (int32_t *)dset;
+                    (*nrows)[i] = std::lower_bound(c.set.begin(), c.set.end(), (uint32_t)std::min<int64_t>(cnt, UINT32_MAX)) -
+                                  c.set.begin();
+                } else {
+                    alloc->free(dset, stream);
+                }
             } else {
                 std::vector<int64_t> vs(c.set.begin(), c.set.end());
                 int64_t *dset = (int64_t *)alloc->alloc(std::max<int64_t>(len, 1) * 8, stream);
@@ -301,7 +333,21 @@ std::vector<int32_t> subchain_types(const Query &q, int i, int j) {
 }  // namespace
 
 mp_ctx::QState::~QState() {
-    if (ctx) ctx->free_masks(masks);
+    if (ctx) {
+        ctx->free_masks(masks);
+        ctx->free_row_lists(rows, nrows);
+    }
+}
+
+void mp_ctx::free_row_lists(std::vector<int32_t *> &rows, std::vector<int64_t> &nrows) {
+    for (size_t i = 0; i < rows.size(); i++) {
+        if (!rows[i]) continue;
+        bool shared = false;  // positions with equal constraints hold one list
+        for (size_t j = 0; j < i && !shared; j++) shared = rows[j] == rows[i];
+        if (!shared) alloc->free(rows[i], stream);
+    }
+    rows.clear();
+    nrows.clear();
 }
 
 // ------------------------------------------------------------------ HBM byte budget
@@ -355,7 +401,7 @@ int mp_ctx::admit(std::vector<Query> &qs_in, const std::vector<uint64_t> &ticket
         st[q] = std::make_shared<QState>();
         st[q]->ctx = this;
         st[q]->q = std::move(qs_in[q]);
-        qstatus[q] = build_masks(st[q]->q, st[q]->masks);
+        qstatus[q] = build_masks(st[q]->q, st[q]->masks, &st[q]->rows, &st[q]->nrows);
     }
     std::vector<Flight *> fl(nq);
     for (size_t q = 0; q < nq; q++) {
@@ -949,6 +995,12 @@ int mp_ctx::run_wave() {
         in.rm = nd.left < 0 ? M[i] : nullptr;
         in.km = (nd.left < 0 || nd.right < 0) ? M[k + 1] : nullptr;
         in.cm = nd.right < 0 ? M[j + 1] : nullptr;
+        if (nd.left < 0 && (size_t)i < nd.qs->rows.size() && nd.qs->rows[i]) {
+            // a base factor starting at a position constrained by a node-id set: its rows
+            // outside the set are masked out, so the set is its row list
+            in.X.arows = nd.qs->rows[i];
+            in.X.narows = nd.qs->nrows[i];
+        }
         if (tun.compact) {
             if (nd.left < 0 && !in.rm && in.km && !in.X.val && in.X.nnz >= tun.compact_min && compact(in.X, in.km))
                 in.km = nullptr;

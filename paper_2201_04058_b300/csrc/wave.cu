@@ -77,6 +77,11 @@ struct Prod {
     DCsr X, Y;
     const uint32_t *rm, *km, *cm;
     int64_t row0;   // first wave row of this product
+    // X's rows the product runs over: arows[0..nwr) (ascending) when X comes with a row list
+    // much shorter than its row count, else all nwr = X.nrows rows; rows off the list are
+    // empty in the result
+    const int32_t *arows;
+    int64_t nwr;
     int64_t *rp;    // output row pointers (X.nrows + 1)
     int32_t *ci;    // output column ids (after the symbolic pass)
     uint64_t *val;  // output counts
@@ -147,6 +152,12 @@ static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed b
 static constexpr int64_t LONGCH = 16384; // X entries per block of a long row
 // Marks a GLOBAL row with a dense slot between the partition and the numeric binning.
 static constexpr int8_t B_GDENSE = 100;
+
+// The X row of wave row g of product P.
+__device__ __forceinline__ int64_t xrow(const Prod &P, int64_t g) {
+    const int64_t r = g - P.row0;
+    return P.arows ? (int64_t)__ldg(P.arows + r) : r;
+}
 
 // ------------------------------------------------------------------ row work + bins
 
@@ -249,7 +260,7 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         const Prod *P = nullptr;
         if (g < M) {
             P = prods + rowprod[g];
-            const int64_t i = g - P->row0;
+            const int64_t i = xrow(*P, g);
             if (bit_of(P->rm, (uint32_t)i)) {
                 b = P->X.rp[i];
                 e = P->X.rp[i + 1];
@@ -295,7 +306,7 @@ __global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
         const uint32_t g = mid_rows[r];
         const Prod &P = prods[rowprod[g]];
-        const int64_t i = g - P.row0;
+        const int64_t i = xrow(P, g);
         uint64_t s = 0;
         double x = 0.0;
         uint32_t mx = 0;
@@ -331,7 +342,7 @@ __global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64
         if (off >= nb) continue;  // uniform over the block
         const uint32_t g = long_rows[r];
         const Prod &P = prods[rowprod[g]];
-        const int64_t i = g - P.row0;
+        const int64_t i = xrow(P, g);
         uint64_t s = 0;
         double x = 0.0;
         uint32_t mx = 0;
@@ -405,7 +416,7 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
             const Prod &P = prods[pi];
             s = prod[g];
             if (s) {
-                const int64_t i = g - P.row0;
+                const int64_t i = xrow(P, g);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
                 b = lane_row(ba, s, (int64_t)xe) ? B_LANE
                                                  : bin_for(s, s, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ba.heavy,
@@ -496,7 +507,7 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
                                 ba.force);
                     if (b == B_GLOBAL) atomicOr(&ps[pi].err, ERR_PROBE);  // cannot happen: nnz <= the bound
                 }
-                const int64_t i = g - P.row0;
+                const int64_t i = xrow(P, g);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
                 const unsigned long long pr = prod[g];
                 atomicAdd(&hc[b], 1u);
@@ -568,18 +579,34 @@ __global__ void k_bin_fill(const int8_t *bin, int64_t n, const uint32_t *counts,
 }
 
 // Per-product row pointers from the wave's: rp_p[i] = grp[row0 + i] - grp[row0], and each
-// product's nnz.
+// product's nnz. A product over a row list gets its row pointers from k_rp_expand.
 __global__ void k_rebase(const Prod *prods, const int32_t *rowprod, const int64_t *grp, int64_t M, PStat *ps) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < M; g += (int64_t)gridDim.x * blockDim.x) {
         const int pi = rowprod[g];
         const Prod &P = prods[pi];
-        const int64_t i = g - P.row0;
+        const int64_t r = g - P.row0;
         const int64_t base = grp[P.row0];
-        P.rp[i] = grp[g] - base;
-        if (i == P.X.nrows - 1) {
-            P.rp[i + 1] = grp[g + 1] - base;
+        if (!P.arows) P.rp[r] = grp[g] - base;
+        if (r == P.nwr - 1) {
+            if (!P.arows) P.rp[r + 1] = grp[g + 1] - base;
             ps[pi].nnz = grp[g + 1] - base;
         }
+    }
+}
+
+// Row pointers of a product over a row list: row i's entries start where those of the
+// first listed row at or after i start (the rows off the list are empty).
+__global__ void k_rp_expand(const Prod *P, const int64_t *grp) {
+    const int64_t n = P->X.nrows, na = P->nwr, row0 = P->row0;
+    const int32_t *__restrict__ arows = P->arows;
+    const int64_t base = grp[row0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = na;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)__ldg(arows + mid) < i) lo = mid + 1; else hi = mid;
+        }
+        P->rp[i] = grp[row0 + lo] - base;
     }
 }
 
@@ -604,7 +631,7 @@ struct RowRef {
         g = entry;
         pi = a.rowprod[g];
         P = a.prods + pi;
-        i = g - P->row0;
+        i = xrow(*P, g);
     }
     __device__ __forceinline__ uint32_t *err(const PassArgs &a) const { return &a.ps[pi].err; }
     // numeric: output offset of the row inside its product and its exact length
@@ -1132,7 +1159,7 @@ __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const ui
         if ((int64_t)pos < nd) {
             bin[gr] = B_GDENSE;
             const Prod &P = prods[rowprod[gr]];
-            const int64_t i = gr - P.row0;
+            const int64_t i = xrow(P, gr);
             const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
             const unsigned long long extra = xe * (P.X.val ? 8ull : 0ull) + prod[gr] * (P.Y.val ? 8ull : 0ull);
             if (extra) atomicAdd(tally->bytes + B_GLOBAL, extra);
@@ -1285,7 +1312,7 @@ __global__ void __launch_bounds__(GNT, MODE != G_SYM ? OCC : 8) k_glob_set(PassA
         if (MODE == G_NUM && !pval) continue;  // the product failed before its numeric pass
         uint32_t *err = &a.ps[pi].err;
         const bool chk = a.ps[pi].unsafe != 0;  // uniform over the item
-        const int64_t row = (int64_t)gr - PP->row0;
+        const int64_t row = xrow(*PP, gr);
         const int32_t *__restrict__ xci = PP->X.ci;
         const uint64_t *__restrict__ xval = PP->X.val;
         const int64_t *__restrict__ yrp = PP->Y.rp;
@@ -1523,7 +1550,7 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
         if (MODE == G_NUM && !pval) continue;  // the product failed before its numeric pass
         uint32_t *err = &a.ps[pi].err;
         const bool chk = a.ps[pi].unsafe != 0;  // uniform over the item
-        const int64_t row = (int64_t)gr - PP->row0;
+        const int64_t row = xrow(*PP, gr);
         const uint64_t *__restrict__ xval = PP->X.val;
         const int32_t *__restrict__ yci = PP->Y.ci;
         const uint64_t *__restrict__ yval = PP->Y.val;
@@ -2385,7 +2412,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         P.cm = x.cm;
         P.ymax = x.ymax;
         P.row0 = row0s[p];
-        row0s[p + 1] = row0s[p] + x.X.nrows;
+        // a row list much shorter than X's rows: the product runs over the listed rows only
+        const bool listed = tun.row_lists && x.X.arows && x.X.narows * 8 <= x.X.nrows;
+        P.arows = listed ? x.X.arows : nullptr;
+        P.nwr = listed ? x.X.narows : x.X.nrows;
+        row0s[p + 1] = row0s[p] + P.nwr;
         if (x.Y.ncols <= tun.dense_max_cols) dense_cols = std::max<int64_t>(dense_cols, x.Y.ncols);
         max_cols = std::max<int64_t>(max_cols, x.Y.ncols);
     }
@@ -2616,6 +2647,10 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     if (scan_i64(grp, grp, M, al, s)) return fail(MP_ERR_NOMEM);
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
                   dprods, rowprod, grp, M, ps);
+    for (int p = 0; p < w; p++)
+        if (hp[p].arows)
+            kl(k_rp_expand, (unsigned)std::min<int64_t>(grid_for(in[p].X.nrows + 1, 256), (int64_t)tun.sm_count * 8), 256,
+               0, s, (const Prod *)(dprods + p), (const int64_t *)grp);
     stage_mark(prof, 3, 1, s);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
@@ -2724,6 +2759,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         o.m.rp = hp[p].rp;
         o.m.ci = hp[p].ci;
         o.m.val = hp[p].val;
+        if (hp[p].arows) {  // the result's non-empty rows are on its X's list: it keeps a copy
+            int32_t *ar = (int32_t *)al.alloc((size_t)std::max<int64_t>(hp[p].nwr, 1) * 4, s);
+            if (ar && hp[p].nwr &&
+                !cuda_ok(cudaMemcpyAsync(ar, hp[p].arows, (size_t)hp[p].nwr * 4, cudaMemcpyDeviceToDevice, s), "copy")) {
+                al.free(ar, s);
+                ar = nullptr;
+            }
+            o.m.arows = ar;  // no copy (out of memory): the result simply has no list
+            o.m.narows = ar ? hp[p].nwr : 0;
+        }
     }
     glob_release(gl, al, s);
     ws_free();

@@ -517,3 +517,26 @@ def test_masked_leaves_compacted(c1, c2_small, compact, force, monkeypatch):
                 assert_same(g, OC.evaluate(o, q), (compact, force, "batch", "".join(q["types"])))
         finally:
             e.close()
+
+
+@pytest.mark.parametrize("row_lists", [0, 1])
+@pytest.mark.parametrize("force", [-1, 0, 1, 2, 3])
+def test_row_lists(c1, c2_small, row_lists, force, monkeypatch):
+    """Products whose left factor starts at a position constrained by a node-id set (or is
+    the result of such a product) run over the listed rows only, the other rows' row
+    pointers filled in afterwards; or over all rows. Every bin class, alone and batched,
+    the oracle's results; the results of a list run feed later products."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"row_lists={row_lists}")
+    for (h, o), qs in ((c1, gen.batched_queries(seed=17, n=40, pool=30, anchor_p=0.9) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=force, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (row_lists, force, "".join(q["types"])))
+            rc, res = e.run_batch(qs)
+            assert rc == 0
+            for q, g in zip(qs, res):
+                assert_same(g, OC.evaluate(o, q), (row_lists, force, "batch", "".join(q["types"])))
+        finally:
+            e.close()
