@@ -62,6 +62,7 @@ struct Tuning {
     int compact = 1;             // large pattern leaves enter products with their column mask applied (0: off)
     int64_t compact_min = 1 << 20;  // ... when they hold at least this many entries
     int row_lens = 1;            // masked Y-row length arrays for products with X.nnz >= Y.nrows (0: off)
+    int64_t ech = 4096;          // X entries per work item of a split row cut by entries
     int ew_max = 64;             // split rows whose masked Y rows hold at most this many entries are cut
                                  // into runs of X entries (-1: always runs of products)
     int dsm_cols = 8192;         // dense split rows this narrow add their counts in a shared-memory row (0: off)

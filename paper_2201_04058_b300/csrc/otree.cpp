@@ -264,7 +264,12 @@ uint64_t OverlapTree::frequency(const int32_t *s, size_t n, const std::string *k
     const int32_t x = locate(s, n, &exact);
     if (x < 0) return 0;
     if (!key) return nodes_[x].f;
-    // every occurrence through x carries a key of at least n positions: restrict and count
+    // x's keys cover depth(x) positions: where the sub-metapath ends at x they are the
+    // lookup keys themselves (one map lookup); inside the edge into x, restrict and count
+    if (exact && (size_t)nodes_[x].depth == n) {
+        auto it = nodes_[x].cidx.find(*key);
+        return it == nodes_[x].cidx.end() ? 0 : it->second.f;
+    }
     uint64_t f = 0;
     for (const auto &kv : nodes_[x].cidx)
         if (restricted_equals(kv.first, n, *key)) f += kv.second.f;

@@ -1116,7 +1116,9 @@ __global__ void __launch_bounds__(256) k_bins_pool(PassArgs a) {
 // sums of X times the bound on Y's values stay below 2^63; otherwise every addition checks
 // its carry and an overflow fails the product.
 static constexpr int64_t PCH = 16384;  // Gustavson products per work item
-static constexpr int64_t ECH = 4096;   // X entries per work item of a row split by entries
+// X entries per work item of a row split by entries (Tuning::ech, a multiple of 256): the
+// grid works on about its block count of consecutive items at a time, so smaller items keep
+// fewer rows' accumulators in use at once
 static constexpr int GNT = 256;        // threads per GLOBAL block
 static constexpr int RW = 8;           // bitmap words per thread in the rank pass
 static constexpr int CSLOT = 1024;     // shared-memory combining slots per work item
@@ -1132,6 +1134,7 @@ struct GlobArgs {
     const uint64_t *prod;     // prod_i per wave row
     const uint32_t *ymx;      // per wave row: its longest masked Y row (entry_split)
     int ew_max;
+    int64_t ech;              // X entries per work item of a row split by entries
     int64_t r0, r1;           // rows of this round
     uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
     int64_t nw;               // slot size (words)
@@ -1172,16 +1175,16 @@ __global__ void k_glob_split(const Prod *prods, const int32_t *rowprod, const ui
     }
 }
 
-// Per GLOBAL row: its number of work items (ECH X entries each for a row split by entries,
+// Per GLOBAL row: its number of work items (ech X entries each for a row split by entries,
 // PCH products otherwise) and how many product offsets it needs (its X entries, or none).
 __global__ void k_glob_prep(PassArgs a, const uint32_t *list, int64_t R, const uint64_t *prod, const uint32_t *ymx,
-                            int ew_max, int64_t *xlen, int64_t *items) {
+                            int ew_max, int64_t ech, int64_t *xlen, int64_t *items) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const RowRef Rf(a, list[r]);
         const int64_t xe = Rf.P->X.rp[Rf.i + 1] - Rf.P->X.rp[Rf.i];
         if (entry_split(ymx[Rf.g], ew_max)) {
             xlen[r] = 0;
-            items[r] = (xe + ECH - 1) / ECH;
+            items[r] = (xe + ech - 1) / ech;
         } else {
             xlen[r] = xe;
             items[r] = ((int64_t)prod[Rf.g] + PCH - 1) / PCH;
@@ -1667,9 +1670,9 @@ __global__ void __launch_bounds__(GNT, OCC) k_glob_lbs(PassArgs a, GlobArgs g) {
             // a row split by X entries: this warp's share of the item's entries, 32 at a time;
             // each lane looks up its entry's Y row, then the lanes walk their own short runs,
             // or the group's products in windows of 32 when some run is longer
-            const int64_t e0 = (t - g.item_off[r]) * ECH;
-            const int64_t we0 = e0 + (int64_t)wid * (ECH / (GNT / 32));
-            const int64_t we1 = min(min(xlen, e0 + ECH), we0 + ECH / (GNT / 32));
+            const int64_t e0 = (t - g.item_off[r]) * g.ech;
+            const int64_t we0 = e0 + (int64_t)wid * (g.ech / (GNT / 32));
+            const int64_t we1 = min(min(xlen, e0 + g.ech), we0 + g.ech / (GNT / 32));
             const int32_t *__restrict__ xci = PP->X.ci;
             const int64_t *__restrict__ yrp = PP->Y.rp;
             const uint32_t *__restrict__ km = PP->km;
@@ -2230,6 +2233,7 @@ struct Glob {
     const uint64_t *prod = nullptr;
     const uint32_t *ymx = nullptr;  // longest masked Y row per wave row
     int ew_max = -1;                // rows with ymx <= ew_max are split by X entries
+    int64_t ech = 4096;             // ... into items of this many entries
     int kinds = 1;                  // bit 0: rows split by products present, bit 1: by entries
     uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
@@ -2339,9 +2343,9 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff,        g.ys,          g.prod,
-                          g.ymx,  g.ew_max,   0,       g.nd,          g.dbmr,        g.nwd,
-                          tun.short_walk, tun.seg_walk, g.dval, g.dcols};
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys,           g.prod,       g.ymx,  g.ew_max,
+                          g.ech,  0,          g.nd,    g.dbmr, g.nwd,          tun.short_walk, tun.seg_walk, g.dval,
+                          g.dcols};
         const int64_t words = g.nd * g.nwd;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
@@ -2355,7 +2359,7 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         }
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
-        const GlobArgs ga{g.list,         g.item_off,   g.xbase, g.xoff, g.ys, g.prod, g.ymx, g.ew_max, r0,
+        const GlobArgs ga{g.list,  g.item_off, g.xbase, g.xoff, g.ys, g.prod, g.ymx, g.ew_max, g.ech, r0,
                           std::min(g.R, r0 + g.per_round), g.bmr, g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
@@ -2591,6 +2595,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.prod = prod;
         gl.ymx = ymx;
         gl.ew_max = ba.ew_max;
+        gl.ech = std::max<int64_t>(256, tun.ech / 256 * 256);
         gl.kinds = (xtot > 0 ? 1 : 0) | ((uint64_t)xtot < h_sym.tally.xent[B_GLOBAL] ? 2 : 0);
         gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
@@ -2626,7 +2631,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
             return fail(MP_ERR_CUDA);
         }
         kl(k_glob_prep, (unsigned)std::min<int64_t>(grid_for(gl.R, 256), 1024), 256, 0, s, pa, gl.list, gl.R, prod,
-           (const uint32_t *)ymx, ba.ew_max, gl.xbase, gl.item_off);
+           (const uint32_t *)ymx, ba.ew_max, gl.ech, gl.xbase, gl.item_off);
         if (scan_i64(gl.item_off, gl.item_off, gl.R, al, s) || scan_i64(gl.xbase, gl.xbase, gl.R, al, s))
             return fail(MP_ERR_NOMEM);
         if (xtot > 0) {

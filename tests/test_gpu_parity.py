@@ -540,3 +540,19 @@ def test_row_lists(c1, c2_small, row_lists, force, monkeypatch):
                 assert_same(g, OC.evaluate(o, q), (row_lists, force, "batch", "".join(q["types"])))
         finally:
             e.close()
+
+
+@pytest.mark.parametrize("ech", [256, 1024, 8192])
+def test_entry_split_item_sizes(c1, c2_small, ech, monkeypatch):
+    """Rows cut by X entries into work items of several sizes (items of 256 entries put
+    many items on every split row): the oracle's results."""
+    mp = _mp()
+    monkeypatch.setenv("MP_TUNING", f"ech={ech}")
+    for (h, o), qs in ((c1, gen.long_queries(5, 6) + [gen.config1_query()]),
+                       (c2_small, gen.config2_queries(c2_small[0], seed=2, n_anchor_a=32, n_anchor_t=4))):
+        e = mp.Engine(h, force_bin_class=mp.MP_BIN_GLOBAL, policy=mp.MP_POLICY_NONE)
+        try:
+            for q in qs:
+                assert_same(e.run(q), OC.evaluate(o, q), (ech, "".join(q["types"])))
+        finally:
+            e.close()
