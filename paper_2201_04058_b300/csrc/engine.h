@@ -38,7 +38,6 @@ struct DevMat {
         if (m.rp) al->free(m.rp, s);
         if (m.ci) al->free(m.ci, s);
         if (m.val) al->free(m.val, s);
-        if (m.arows) al->free(m.arows, s);
     }
 };
 using MatPtr = std::shared_ptr<DevMat>;
@@ -185,7 +184,8 @@ struct mp_ctx {
 
     int parse(const mp_query *q, Query &out);
     int build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vector<int32_t *> *rows = nullptr,
-                    std::vector<int64_t> *nrows = nullptr);
+                    std::vector<int64_t> *nrows = nullptr,
+                    std::vector<std::shared_ptr<const int32_t>> *holds = nullptr);
     void free_masks(std::vector<uint32_t *> &masks);
     void free_row_lists(std::vector<int32_t *> &rows, std::vector<int64_t> &nrows);
 
@@ -202,6 +202,7 @@ struct mp_ctx {
         // device (a factor that starts there runs over these rows only), and their count
         std::vector<int32_t *> rows;
         std::vector<int64_t> nrows;
+        std::vector<std::shared_ptr<const int32_t>> rows_hold;  // owners of rows (shared with results)
         ~QState();
     };
     struct Flight {

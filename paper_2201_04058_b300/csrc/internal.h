@@ -129,8 +129,11 @@ struct Mat {
     int32_t *ci = nullptr;
     uint64_t *val = nullptr;   // nullptr only for base relations
     uint64_t vmax = 1;         // upper bound on the values (1: 0/1 pattern; UINT64_MAX: none known)
-    int32_t *arows = nullptr;  // owned: ascending rows outside which every row is empty (or null)
+    // ascending rows outside which every row is empty (or null), and its owner: a row list is
+    // shared by every result that inherits it and freed when the last one goes
+    const int32_t *arows = nullptr;
     int64_t narows = 0;
+    std::shared_ptr<const int32_t> arows_hold;
     size_t bytes() const { return (size_t)(nrows + 1) * 8 + (size_t)nnz * 12; }
     DCsr view() const { return DCsr{rp, ci, val, nrows, ncols, nnz, arows, narows}; }
 };
@@ -154,12 +157,16 @@ void mask_and_set(uint32_t *m, uint32_t *tmp, const uint32_t *set, int64_t set_l
 
 // nnz of diag(rm) A diag(cm), added into *out (device). long_rows (A.nrows entries) and
 // *n_long (zeroed) are device scratch for rows longer than 8192 entries.
+// The same count when the row mask selects exactly the n listed rows (ascending ids).
+void masked_nnz_list(const DCsr &A, const int32_t *rows, int64_t n, const uint32_t *cm, unsigned long long *out,
+                     cudaStream_t s);
 void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out,
                 uint32_t *long_rows, uint32_t *n_long, cudaStream_t s);
 
 // One product of a wave: C = diag(rm) X diag(km) Y diag(cm) (masks may be nullptr).
 struct WaveIn {
     DCsr X, Y;
+    std::shared_ptr<const int32_t> xrows_hold;  // owner of X.arows, passed on to the result
     const uint32_t *rm = nullptr, *km = nullptr, *cm = nullptr;
     uint64_t ymax = 1;  // upper bound on Y's values (Mat::vmax of Y)
 };

@@ -128,6 +128,33 @@ __global__ void k_masked_nnz_long(DCsr A, const uint32_t *cm, unsigned long long
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// nnz of diag(rm) A diag(cm) when rm selects the listed rows only (ascending ids): one warp
+// per listed row, the lanes over its entries.
+__global__ void k_masked_nnz_list(DCsr A, const int32_t *rows, int64_t n, const uint32_t *cm, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long c = 0;
+    for (int64_t r = w; r < n; r += nwarps) {
+        const int64_t i = rows[r];
+        const int64_t b = A.rp[i], e = A.rp[i + 1];
+        if (!cm) {
+            if (lane == 0) c += (unsigned long long)(e - b);
+            continue;
+        }
+        for (int64_t p = b + lane; p < e; p += 32) c += bit_of(cm, (uint32_t)__ldg(A.ci + p));
+    }
+    for (int d = 16; d; d >>= 1) c += __shfl_down_sync(FULL, c, d);
+    if (lane == 0 && c) atomicAdd(out, c);
+}
+
+void masked_nnz_list(const DCsr &A, const int32_t *rows, int64_t n, const uint32_t *cm, unsigned long long *out,
+                     cudaStream_t s) {
+    if (n <= 0) return;
+    kl(k_masked_nnz_list, (unsigned)std::min<int64_t>(grid_for(n * 32, 256), 148 * 16), 256, 0, s, A, rows, n, cm,
+       out);
+}
+
 void masked_nnz(const DCsr &A, const uint32_t *rm, const uint32_t *cm, unsigned long long *out, uint32_t *long_rows,
                 uint32_t *n_long, cudaStream_t s) {
     if (!A.nrows) return;

@@ -53,7 +53,6 @@ void mp_ctx::free_mat(Mat &m) {
     if (m.rp) alloc->free(m.rp, stream);
     if (m.ci) alloc->free(m.ci, stream);
     if (m.val) alloc->free(m.val, stream);
-    if (m.arows) alloc->free(m.arows, stream);
     m = Mat{};
 }
 
@@ -173,6 +172,7 @@ void mp_ctx::htier_store(const std::string &id, const MatPtr &m, const std::vect
     e.shape.val = nullptr;
     e.shape.arows = nullptr;  // copied back without its row list (any row may be non-empty)
     e.shape.narows = 0;
+    e.shape.arows_hold.reset();
     e.off = off;
     e.bytes = bytes;
     e.c_ms = c_ms;
@@ -228,11 +228,17 @@ MatPtr mp_ctx::htier_load(const std::string &id) {
 }
 
 int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vector<int32_t *> *rows,
-                        std::vector<int64_t> *nrows) {
+                        std::vector<int64_t> *nrows, std::vector<std::shared_ptr<const int32_t>> *holds) {
     const int n = (int)q.types.size();
     masks.assign(n, nullptr);
     if (rows) rows->assign(n, nullptr);
     if (nrows) nrows->assign(n, 0);
+    if (holds) holds->assign(n, nullptr);
+    // a row list's owner: freed (stream ordered) when the query and every result that
+    // inherited the list have let go of it
+    Alloc *al = alloc.get();
+    cudaStream_t s = stream;
+    auto hold = [al, s](int32_t *p) { return std::shared_ptr<const int32_t>(p, [al, s](const int32_t *x) { al->free((void *)x, s); }); };
     for (int i = 0; i < n; i++) {
         if (q.cons[i].empty()) continue;
         // a position of the same type with the same constraints (the canonical key) shares
@@ -242,6 +248,7 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vec
                 masks[i] = masks[j];
                 if (rows) (*rows)[i] = (*rows)[j];
                 if (nrows) (*nrows)[i] = (*nrows)[j];
+                if (holds) (*holds)[i] = (*holds)[j];
             }
         if (masks[i]) continue;
         const int64_t cnt = types[q.types[i]].count;
@@ -251,7 +258,7 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vec
         masks[i] = m;
         // the first constraint stores its words when it is a range; otherwise all ones first
         const bool first_range = q.cons[i][0].op == MP_OP_RANGE || q.cons[i][0].op == MP_OP_EQ;
-        if (rows && first_range && q.cons[i].size() == 1 && q.cons[i][0].prop < 0) {
+        if (rows && holds && first_range && q.cons[i].size() == 1 && q.cons[i][0].prop < 0) {
             // the position's only constraint is a window of node ids: those ids are its row
             // list when they are few (an anchor entity, say)
             const int64_t lo = std::max<int64_t>(q.cons[i][0].lo, 0);
@@ -263,6 +270,7 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vec
                 fill_iota(d, lo, len, stream);
                 (*rows)[i] = d;
                 (*nrows)[i] = len;
+                (*holds)[i] = hold(d);
             }
         }
         if (!first_range) mask_fill(m, cnt, true, stream);
@@ -287,12 +295,13 @@ int mp_ctx::build_masks(const Query &q, std::vector<uint32_t *> &masks, std::vec
                 if (len) cudaMemcpyAsync(dset, c.set.data(), len * 4, cudaMemcpyHostToDevice, stream);
                 mask_and_set(m, tmp, dset, len, cnt, stream);
                 alloc->free(tmp, stream);
-                if (rows && q.cons[i].size() == 1) {
+                if (rows && holds && q.cons[i].size() == 1) {
                     // the position's only constraint: the set (sorted, without repeats since
                     // parsing) is also its row list, without the ids past the type's count
                     (*rows)[i] = (int32_t *)dset;
                     (*nrows)[i] = std::lower_bound(c.set.begin(), c.set.end(), (uint32_t)std::min<int64_t>(cnt, UINT32_MAX)) -
                                   c.set.begin();
+                    (*holds)[i] = hold((int32_t *)dset);
                 } else {
                     alloc->free(dset, stream);
                 }
@@ -340,13 +349,7 @@ mp_ctx::QState::~QState() {
 }
 
 void mp_ctx::free_row_lists(std::vector<int32_t *> &rows, std::vector<int64_t> &nrows) {
-    for (size_t i = 0; i < rows.size(); i++) {
-        if (!rows[i]) continue;
-        bool shared = false;  // positions with equal constraints hold one list
-        for (size_t j = 0; j < i && !shared; j++) shared = rows[j] == rows[i];
-        if (!shared) alloc->free(rows[i], stream);
-    }
-    rows.clear();
+    rows.clear();  // the lists themselves go with their owners (shared with results)
     nrows.clear();
 }
 
@@ -401,7 +404,7 @@ int mp_ctx::admit(std::vector<Query> &qs_in, const std::vector<uint64_t> &ticket
         st[q] = std::make_shared<QState>();
         st[q]->ctx = this;
         st[q]->q = std::move(qs_in[q]);
-        qstatus[q] = build_masks(st[q]->q, st[q]->masks, &st[q]->rows, &st[q]->nrows);
+        qstatus[q] = build_masks(st[q]->q, st[q]->masks, &st[q]->rows, &st[q]->nrows, &st[q]->rows_hold);
     }
     std::vector<Flight *> fl(nq);
     for (size_t q = 0; q < nq; q++) {
@@ -455,6 +458,12 @@ int mp_ctx::admit(std::vector<Query> &qs_in, const std::vector<uint64_t> &ticket
                 }
                 if (first.count(key)) continue;
                 first.emplace(key, off + t);
+                any = true;
+                if ((size_t)t < st[q]->rows.size() && st[q]->rows[t] && st[q]->nrows[t] * 8 <= A.nrows) {
+                    // rows selected by node ids: count over the listed rows only
+                    masked_nnz_list(A.view(), st[q]->rows[t], st[q]->nrows[t], st[q]->masks[t + 1], d + off + t, stream);
+                    continue;
+                }
                 uint32_t *lr = (uint32_t *)alloc->alloc((size_t)(A.nrows + 1) * 4, stream);
                 if (!lr) {
                     free_tmp();
@@ -988,6 +997,7 @@ int mp_ctx::run_wave() {
         const int i = nd.i, j = nd.j, k = nd.k;
         WaveIn in;
         in.X = nd.left >= 0 ? node(nd.left).res->m.view() : rels[Q.rels[i]].dev.view();
+        if (nd.left >= 0) in.xrows_hold = node(nd.left).res->m.arows_hold;
         in.Y = nd.right >= 0 ? node(nd.right).res->m.view() : rels[Q.rels[j]].dev.view();
         in.ymax = nd.right >= 0 ? node(nd.right).res->m.vmax : 1;
         // a base factor enters with the masks of its end positions; a node's result
@@ -1000,6 +1010,7 @@ int mp_ctx::run_wave() {
             // outside the set are masked out, so the set is its row list
             in.X.arows = nd.qs->rows[i];
             in.X.narows = nd.qs->nrows[i];
+            in.xrows_hold = nd.qs->rows_hold[i];
         }
         if (tun.compact) {
             if (nd.left < 0 && !in.rm && in.km && !in.X.val && in.X.nnz >= tun.compact_min && compact(in.X, in.km))

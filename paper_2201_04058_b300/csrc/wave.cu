@@ -148,7 +148,7 @@ struct BinTally {
     unsigned long long gx_pw;  // X entries of the GLOBAL rows split by products (they need offsets)
 };
 
-static constexpr int64_t LONGX = 8192;   // X rows longer than this are summed by several blocks
+static constexpr int64_t LONGX = 2048;   // X rows longer than this are summed by whole blocks
 static constexpr int64_t LONGCH = 16384; // X entries per block of a long row
 // Marks a GLOBAL row with a dense slot between the partition and the numeric binning.
 static constexpr int8_t B_GDENSE = 100;
@@ -594,17 +594,29 @@ __global__ void k_rebase(const Prod *prods, const int32_t *rowprod, const int64_
     }
 }
 
-// Row pointers of a product over a row list: row i's entries start where those of the
-// first listed row at or after i start (the rows off the list are empty).
-__global__ void k_rp_expand(const Prod *P, const int64_t *grp) {
+// Row pointers of the products over a row list (one launch for the wave: blockIdx.y is
+// the product; the others return at once): row i's entries start where those of the first
+// listed row at or after i start (the rows off the list are empty). A list of up to
+// RP_SMEM rows is searched in shared memory.
+static constexpr int RP_SMEM = 4096;
+
+__global__ void __launch_bounds__(256) k_rp_expand(const Prod *prods, const int64_t *grp) {
+    __shared__ int32_t s_rows[RP_SMEM];
+    const Prod *P = prods + blockIdx.y;  // prods: the first product of this launch's range
+    if (!P->arows) return;  // uniform over the block
     const int64_t n = P->X.nrows, na = P->nwr, row0 = P->row0;
     const int32_t *__restrict__ arows = P->arows;
     const int64_t base = grp[row0];
+    const bool shared = na <= RP_SMEM;
+    if (shared)
+        for (int64_t a = threadIdx.x; a < na; a += blockDim.x) s_rows[a] = arows[a];
+    __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = na;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)__ldg(arows + mid) < i) lo = mid + 1; else hi = mid;
+            const int64_t v = shared ? (int64_t)s_rows[mid] : (int64_t)__ldg(arows + mid);
+            if (v < i) lo = mid + 1; else hi = mid;
         }
         P->rp[i] = grp[row0 + lo] - base;
     }
@@ -2652,10 +2664,16 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     if (scan_i64(grp, grp, M, al, s)) return fail(MP_ERR_NOMEM);
     if (M > 0) kl(k_rebase, (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16), 256, 0, s,
                   dprods, rowprod, grp, M, ps);
-    for (int p = 0; p < w; p++)
-        if (hp[p].arows)
-            kl(k_rp_expand, (unsigned)std::min<int64_t>(grid_for(in[p].X.nrows + 1, 256), (int64_t)tun.sm_count * 8), 256,
-               0, s, (const Prod *)(dprods + p), (const int64_t *)grp);
+    {
+        int64_t rows = -1;  // the widest product over a row list
+        for (int p = 0; p < w; p++)
+            if (hp[p].arows) rows = std::max<int64_t>(rows, in[p].X.nrows + 1);
+        for (int p0 = 0; rows > 0 && p0 < w; p0 += 65535)  // grid y is at most 65,535
+            kl(k_rp_expand,
+               dim3((unsigned)std::min<int64_t>(grid_for(rows, 256), (int64_t)tun.sm_count * 8),
+                    (unsigned)std::min(w - p0, 65535)),
+               256, 0, s, (const Prod *)(dprods + p0), (const int64_t *)grp);
+    }
     stage_mark(prof, 3, 1, s);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
@@ -2764,15 +2782,10 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         o.m.rp = hp[p].rp;
         o.m.ci = hp[p].ci;
         o.m.val = hp[p].val;
-        if (hp[p].arows) {  // the result's non-empty rows are on its X's list: it keeps a copy
-            int32_t *ar = (int32_t *)al.alloc((size_t)std::max<int64_t>(hp[p].nwr, 1) * 4, s);
-            if (ar && hp[p].nwr &&
-                !cuda_ok(cudaMemcpyAsync(ar, hp[p].arows, (size_t)hp[p].nwr * 4, cudaMemcpyDeviceToDevice, s), "copy")) {
-                al.free(ar, s);
-                ar = nullptr;
-            }
-            o.m.arows = ar;  // no copy (out of memory): the result simply has no list
-            o.m.narows = ar ? hp[p].nwr : 0;
+        if (hp[p].arows && in[p].xrows_hold) {  // the result's non-empty rows are on its X's list
+            o.m.arows = hp[p].arows;
+            o.m.narows = hp[p].nwr;
+            o.m.arows_hold = in[p].xrows_hold;
         }
     }
     glob_release(gl, al, s);
