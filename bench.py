@@ -728,21 +728,25 @@ def leg_serving(mp, local, peak, peak_kind, scale=1.0, n=2000, loads=(0.5, 0.8, 
         return {"qps": len(qs) / (end - start), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
                 "joined": ct["joined"], "max_inflight": ct["max_inflight"]}
 
-    nocache = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_NONE, max_slots=64,
-                        hbm_budget_bytes=budget)
     rates = {}
     for load in loads:
         rate = load * sat
         arrivals = np.cumsum(gen.stream(4, 950, int(load * 100)).exponential(1.0 / rate, len(qs)))
+        # every arm starts from a fresh context at every rate (the same cold planner memos;
+        # the cache arm's entries never carry over from the previous rate)
+        one = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_NONE, max_slots=1,
+                        hbm_budget_bytes=budget)
+        nocache = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_NONE, max_slots=64,
+                            hbm_budget_bytes=budget)
         cached = mp.Engine(names, device=local, load_path=path, policy=mp.MP_POLICY_ATRAPOS, max_slots=64,
                            hbm_budget_bytes=budget)
         with Clocks(local) as clk:
-            arms = {"plain": serve(plain, arrivals), "served_no_cache": serve(nocache, arrivals),
+            arms = {"plain": serve(one, arrivals), "served_no_cache": serve(nocache, arrivals),
                     "served_cache": serve(cached, arrivals)}
         arms["served_cache"]["cache_hits"] = mp.mp_cache_stats(cached.ctx)["hits"]
-        cached.close()
+        for e in (one, nocache, cached):
+            e.close()
         rates[f"{load:g}x"] = dict(arms, arrival_qps=rate, clocks=clk.summary())
-    nocache.close()
     plain.close()
     try:
         os.remove(path)

@@ -322,7 +322,10 @@ int mp_host_tier_stats(mp_ctx *ctx, uint64_t *stores, uint64_t *loads, uint64_t 
  * "stage_rowwork", "stage_symbin", "stage_globsetup", "stage_rowptr" and "stage_numbin"
  * time the other stages of a wave (row work, symbolic binning, split-row set-up, wave row
  * pointers, numeric binning; several kernels each, host gaps between them included; no
- * bytes).
+ * bytes). By default only the split-row passes, their walks and the pooled bins are timed
+ * (the events cost a few percent of a query); the environment variable MP_TUNING=prof=2,
+ * read when the context is made, times every bin kernel and the stages as well, prof=0
+ * nothing.
  * ms sums the device time between CUDA events recorded on the launch stream around each
  * launch; bytes sums the algorithmic bytes of the launches (X row pointers, X entries with
  * the two Y row pointers each looks up, one Y column id (and value, in the pass that adds

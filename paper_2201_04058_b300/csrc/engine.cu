@@ -175,6 +175,10 @@ extern "C" int mp_create(const mp_config *cfg, mp_ctx **out) {
                 else if (k == "compact") ctx->tun.compact = (int)v;
                 else if (k == "row_lists") ctx->tun.row_lists = (int)v;
                 else if (k == "ech") ctx->tun.ech = (int64_t)v;
+                else if (k == "prof") {
+                    ctx->prof.on = v > 0;
+                    ctx->prof.level = (int)v;
+                }
                 else if (k == "compact_min") ctx->tun.compact_min = (int64_t)v;
                 else if (k == "pool") ctx->tun.pool = (int)v;
 

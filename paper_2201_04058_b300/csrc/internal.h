@@ -93,7 +93,11 @@ struct KStat {
     double ms = 0.0, bytes = 0.0, prods = 0.0;
 };
 struct Prof {
+    // 0: no events; 1: the split-row passes, their walk kernels and the pooled bins; 2: also
+    // every other bin kernel and the stages of each wave (more events on the stream)
     bool on = true;
+    int level = 1;
+    bool full() const { return on && level >= 2; }
     cudaEvent_t ev[2][NBINS][2] = {};
     KStat k[2][NBINS];
     // the pooled launch of the warp-hash and 2048-slot bins (Tuning::pool), per pass
@@ -198,6 +202,12 @@ struct WaveCache {
     std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
     uint64_t captures = 0, replays = 0;
     bool broken = false;  // a capture failed: plain launches from then on
+    // pinned staging of a wave's uploads (product descriptors, row offsets), so they never
+    // wait for the stream (a copy from pageable memory does); reused wave after wave, which
+    // synchronise before it is written again
+    char *pinned = nullptr;
+    size_t pinned_cap = 0;
+    void *stage(const void *src, size_t bytes, size_t at);  // copies to pinned + at; null on failure
     void drop_graphs();
     void clear(Alloc &al, cudaStream_t s);
 };

@@ -2024,12 +2024,12 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
     }
     if (host_counts[B_LANE]) {
         const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[B_LANE];
-        if (prof && prof->on)
+        if (prof && prof->full())
             cudaEventRecordWithFlags(prof->ev[pass][B_LANE][0], s, g_capturing ? cudaEventRecordExternal : 0);
         const unsigned g = blocks_for(rows, LANE_NT, sms * 16);
         if (numeric) launch(k_lane_rows<true>, g, LANE_NT, 0, s, a, (int)B_LANE);
         else launch(k_lane_rows<false>, g, LANE_NT, 0, s, a, (int)B_LANE);
-        if (prof && prof->on)
+        if (prof && prof->full())
             cudaEventRecordWithFlags(prof->ev[pass][B_LANE][1], s, g_capturing ? cudaEventRecordExternal : 0);
     }
     for (int b = 0; b < B_GLOBAL; b++) {
@@ -2037,7 +2037,7 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
         if (pooled && pool_bin(b)) continue;
         const uint32_t rows = fixed_grid ? (1u << 30) : host_counts[b];
         // inside a capture the records become event-record nodes, so replays time the bins
-        if (prof && prof->on) cudaEventRecordWithFlags(prof->ev[pass][b][0], s, g_capturing ? cudaEventRecordExternal : 0);
+        if (prof && prof->full()) cudaEventRecordWithFlags(prof->ev[pass][b][0], s, g_capturing ? cudaEventRecordExternal : 0);
         switch (b) {
 #define WARP_BIN(BIN, T, W)                                                                       \
     case BIN: {                                                                                   \
@@ -2078,7 +2078,7 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
                 break;
             }
         }
-        if (prof && prof->on) cudaEventRecordWithFlags(prof->ev[pass][b][1], s, g_capturing ? cudaEventRecordExternal : 0);
+        if (prof && prof->full()) cudaEventRecordWithFlags(prof->ev[pass][b][1], s, g_capturing ? cudaEventRecordExternal : 0);
     }
 }
 
@@ -2093,6 +2093,38 @@ void WaveCache::clear(Alloc &al, cudaStream_t s) {
     ws = nullptr;
     mcap = 0;
     wcap = 0;
+    if (pinned) {
+        cudaStreamSynchronize(s);  // no upload may still read it
+        cudaFreeHost(pinned);
+    }
+    pinned = nullptr;
+    pinned_cap = 0;
+}
+
+void *WaveCache::stage(const void *src, size_t bytes, size_t at) {
+    if (at + bytes > pinned_cap) return nullptr;  // sized by the caller (reserve below)
+    memcpy(pinned + at, src, bytes);
+    return pinned + at;
+}
+
+// Room for a wave's uploads in the pinned staging buffer (grown by half again; the old one
+// is freed only when the stream is idle, which it is between waves).
+static bool stage_reserve(WaveCache *wc, size_t bytes, cudaStream_t s) {
+    if (!wc) return false;
+    if (bytes <= wc->pinned_cap) return true;
+    const size_t cap = std::max(bytes, wc->pinned_cap + wc->pinned_cap / 2);
+    char *p = nullptr;
+    if (cudaMallocHost(&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (wc->pinned) {
+        cudaStreamSynchronize(s);
+        cudaFreeHost(wc->pinned);
+    }
+    wc->pinned = p;
+    wc->pinned_cap = cap;
+    return true;
 }
 
 // One shared-memory bin pass through a CUDA graph: the wave's shape (pass, non-empty bins,
@@ -2182,6 +2214,7 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
     prof->pool_ran[pass] = false;
     for (int b = 0; b < NBINS; b++) {
         if (!t.counts[b]) continue;
+        if (b != B_GLOBAL && !prof->full() && !(pooled && pool_bin(b))) continue;  // not timed at this level
         if (pooled && pool_bin(b)) {  // timed as one launch below
             prof->pool[pass].bytes += (double)t.bytes[b];
             prof->pool[pass].prods += (double)t.prods[b];
@@ -2212,13 +2245,13 @@ static void prof_collect(Prof *prof, int pass, const BinTally &t) {
 // Events around one stage of a wave (e = 0 start, 1 end); stage_collect adds the stages
 // recorded since the last call once the wave has synchronised.
 static inline void stage_mark(Prof *prof, int st, int e, cudaStream_t s) {
-    if (!prof || !prof->on) return;
+    if (!prof || !prof->full()) return;
     cudaEventRecord(prof->sev[st][e], s);
     if (e) prof->srec[st] = true;
 }
 
 static void stage_collect(Prof *prof) {
-    if (!prof || !prof->on) return;
+    if (!prof || !prof->full()) return;
     for (int st = 0; st < Prof::NSTAGE; st++) {
         if (!prof->srec[st]) continue;
         prof->srec[st] = false;
@@ -2543,8 +2576,14 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         if (!hp[p].rp) return fail(MP_ERR_NOMEM);
         if (in[p].X.nrows == 0 && !cuda_ok(cudaMemsetAsync(hp[p].rp, 0, 8, s), "memset")) return fail(MP_ERR_CUDA);
     }
-    if (!cuda_ok(cudaMemcpyAsync(dprods, hp.data(), sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload") ||
-        !cuda_ok(cudaMemcpyAsync(drow0s, row0s.data(), (size_t)(w + 1) * 8, cudaMemcpyHostToDevice, s), "upload") ||
+    // the uploads from pinned staging when there is one (no wait for the stream), else from
+    // the host vectors
+    const size_t up_prods = align256(sizeof(Prod) * w), up_rows = (size_t)(w + 1) * 8;
+    const bool staged = stage_reserve(wc, up_prods + up_rows, s);
+    const void *src_prods = staged ? wc->stage(hp.data(), sizeof(Prod) * w, 0) : hp.data();
+    const void *src_rows = staged ? wc->stage(row0s.data(), up_rows, up_prods) : row0s.data();
+    if (!cuda_ok(cudaMemcpyAsync(dprods, src_prods, sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload") ||
+        !cuda_ok(cudaMemcpyAsync(drow0s, src_rows, up_rows, cudaMemcpyHostToDevice, s), "upload") ||
         !cuda_ok(cudaMemsetAsync(ps, 0, sizeof(PStat) * w, s), "memset") ||
         !cuda_ok(cudaMemsetAsync(sm_sym, 0, sizeof(Small) * 2, s), "memset"))
         return fail(MP_ERR_CUDA);
@@ -2735,7 +2774,9 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     }
     // 4. numeric pass; products that failed keep null outputs and their rows are skipped
     if (any_out) {
-        if (!cuda_ok(cudaMemcpyAsync(dprods, hp.data(), sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload"))
+        // the stream synchronised since the first upload: the staging buffer is free again
+        const void *src = staged ? wc->stage(hp.data(), sizeof(Prod) * w, 0) : hp.data();
+        if (!cuda_ok(cudaMemcpyAsync(dprods, src, sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload"))
             return fail(MP_ERR_CUDA);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
         stage_mark(prof, 4, 0, s);
