@@ -337,6 +337,18 @@ int filter(const DCsr &A, const uint32_t *rm, const uint32_t *cm, Alloc &al, con
 // [0, nnz] (the last chunk holds position nnz, where the rows that end the matrix start).
 static constexpr int CC_NT = 256, CC_PER = 8, CC_CH = CC_NT * CC_PER;
 
+// A thread's CC_PER consecutive column ids from eb (zeros past nnz): two 16-byte loads when
+// they are all in range and aligned, else one at a time.
+__device__ __forceinline__ void cc_load(const int32_t *__restrict__ ci, int64_t eb, int64_t nnz, int32_t (&j)[CC_PER]) {
+    if (eb + CC_PER <= nnz && (((uintptr_t)(ci + eb)) & 15u) == 0) {
+        const int4 a = __ldg((const int4 *)(ci + eb)), b = __ldg((const int4 *)(ci + eb) + 1);
+        j[0] = a.x, j[1] = a.y, j[2] = a.z, j[3] = a.w, j[4] = b.x, j[5] = b.y, j[6] = b.z, j[7] = b.w;
+        return;
+    }
+#pragma unroll
+    for (int t = 0; t < CC_PER; t++) j[t] = eb + t < nnz ? __ldg(ci + eb + t) : 0;
+}
+
 // Also records, per chunk, the first row that starts inside it (first[c], -1 when none:
 // the caller fills first with -1 bytes), so the fill pass needs no search for its rows.
 __global__ void __launch_bounds__(CC_NT) k_cc_count(const int64_t *__restrict__ rp, int64_t nrows,
@@ -351,10 +363,12 @@ __global__ void __launch_bounds__(CC_NT) k_cc_count(const int64_t *__restrict__ 
     }
     for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const int64_t eb = c * CC_CH + (int64_t)threadIdx.x * CC_PER;
+        int32_t j[CC_PER];
+        cc_load(ci, eb, nnz, j);
         int64_t n = 0;
 #pragma unroll
         for (int t = 0; t < CC_PER; t++)
-            if (eb + t < nnz && bit_of(m, (uint32_t)__ldg(ci + eb + t))) n++;
+            if (eb + t < nnz && bit_of(m, (uint32_t)j[t])) n++;
         block_excl_scan<CC_NT>(n, ws, &tot);
         if (threadIdx.x == 0) cnt[c] = tot;
     }
@@ -373,10 +387,10 @@ __global__ void __launch_bounds__(CC_NT) k_cc_fill(const int64_t *__restrict__ r
         const int64_t eb = e0 + (int64_t)threadIdx.x * CC_PER;
         int32_t j[CC_PER];
         bool f[CC_PER];
+        cc_load(ci, eb, nnz, j);
         int64_t n = 0;
 #pragma unroll
         for (int t = 0; t < CC_PER; t++) {
-            j[t] = eb + t < nnz ? __ldg(ci + eb + t) : 0;
             f[t] = eb + t < nnz && bit_of(m, (uint32_t)j[t]);
             n += f[t];
         }

@@ -249,8 +249,8 @@ __global__ void k_masked_len(const int64_t *__restrict__ yrp, const uint32_t *__
 static constexpr int64_t SHORTX = 16;  // X rows up to this long are summed by one lane
 
 __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, uint64_t *prod, double *xsum,
-                          uint32_t *ymx, uint32_t *long_rows, uint32_t *long_nb, uint32_t *n_long,
-                          uint32_t *mid_rows, uint32_t *n_mid) {
+                          uint32_t *ymx, uint32_t *long_rows, uint32_t *huge_rows, uint32_t *n_long,
+                          uint32_t *n_huge, uint32_t *mid_rows, uint32_t *n_mid) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -270,11 +270,9 @@ __global__ void k_rowwork(const Prod *prods, const int32_t *rowprod, int64_t M, 
         double xs = 0.0;  // the row's sum of X values: x_ik <= xs bounds every product and sum
         uint32_t mx = 0;
         if (e - b <= SHORTX && e > b) row_sums(*P, b, e, 1, s, xs, mx);
-        if (e - b > LONGX) {
-            const uint32_t at = atomicAdd(n_long, 1u);
-            long_rows[at] = (uint32_t)g;
-            long_nb[at] = (uint32_t)((e - b + LONGCH - 1) / LONGCH);  // blocks that share it
-        }
+        if (e - b > LONGX && e - b <= LONGCH) long_rows[atomicAdd(n_long, 1u)] = (uint32_t)g;  // one block
+        if (e - b > LONGCH) huge_rows[atomicAdd(n_huge, 1u)] = (uint32_t)g;                    // several
+
         const bool mid = e - b > SHORTX && e - b <= LONGX;
         const unsigned mm = __ballot_sync(FULL, mid);
         if (mm) {  // warp-aggregated append to the mid-row queue
@@ -324,55 +322,78 @@ __global__ void k_rowwork_mid(const Prod *prods, const int32_t *rowprod, uint64_
     }
 }
 
-// The queued long rows: row r is shared by ceil(len / LONGCH) consecutive blocks (modulo
-// the grid) starting at a block that depends on r, so long rows spread over the grid and a
-// row only as long as a few chunks does not make every block stop at it.
-__global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
-                               uint32_t *ymx, const uint32_t *long_rows, const uint32_t *long_nb,
-                               const uint32_t *n_long) {
-    __shared__ unsigned long long red[32];
-    __shared__ double redx[32];
-    __shared__ uint32_t redm[32];
-    const uint32_t n = *n_long;
+// The queued long rows: a row of up to LONGCH entries is summed by one block (the blocks
+// take such rows in turn); a longer row is shared by ceil(len / LONGCH) consecutive blocks
+// (modulo the grid) starting at a block that depends on the row, so those rows spread over
+// the grid and a row only a few chunks long does not make every block stop at it.
+__device__ __forceinline__ void block_row_sums(const Prod &P, int64_t p0, int64_t e, int64_t st, uint64_t &s,
+                                               double &x, uint32_t &mx, unsigned long long *red, double *redx,
+                                               uint32_t *redm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t G = gridDim.x;
-    for (uint32_t r = 0; r < n; r++) {
-        const int64_t nb = min(G, (int64_t)long_nb[r]);
-        const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
-        if (off >= nb) continue;  // uniform over the block
-        const uint32_t g = long_rows[r];
-        const Prod &P = prods[rowprod[g]];
-        const int64_t i = xrow(P, g);
-        uint64_t s = 0;
-        double x = 0.0;
-        uint32_t mx = 0;
-        row_sums(P, P.X.rp[i] + off * (int64_t)blockDim.x + threadIdx.x, P.X.rp[i + 1], nb * (int64_t)blockDim.x, s,
-                 x, mx);
+    s = 0;
+    x = 0.0;
+    mx = 0;
+    row_sums(P, p0, e, st, s, x, mx);
+    for (int d = 16; d; d >>= 1) {
+        s += __shfl_xor_sync(FULL, s, d);
+        x += __shfl_xor_sync(FULL, x, d);
+    }
+    mx = __reduce_max_sync(FULL, mx);
+    if (lane == 0) {
+        red[wid] = s;
+        redx[wid] = x;
+        redm[wid] = mx;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        s = in ? red[lane] : 0;
+        x = in ? redx[lane] : 0.0;
+        mx = __reduce_max_sync(FULL, in ? redm[lane] : 0u);
         for (int d = 16; d; d >>= 1) {
             s += __shfl_xor_sync(FULL, s, d);
             x += __shfl_xor_sync(FULL, x, d);
         }
-        mx = __reduce_max_sync(FULL, mx);
-        if (lane == 0) {
-            red[wid] = s;
-            redx[wid] = x;
-            redm[wid] = mx;
+    }
+    __syncthreads();  // red* are free again; the sums are valid in warp 0
+}
+
+__global__ void k_rowwork_long(const Prod *prods, const int32_t *rowprod, uint64_t *prod, double *xsum,
+                               uint32_t *ymx, const uint32_t *long_rows, const uint32_t *huge_rows,
+                               const uint32_t *n_long, const uint32_t *n_huge) {
+    __shared__ unsigned long long red[32];
+    __shared__ double redx[32];
+    __shared__ uint32_t redm[32];
+    const int64_t G = gridDim.x;
+    uint64_t s;
+    double x;
+    uint32_t mx;
+    const uint32_t n1 = *n_long;
+    for (int64_t r = blockIdx.x; r < n1; r += G) {  // uniform over the block
+        const uint32_t g = long_rows[r];
+        const Prod &P = prods[rowprod[g]];
+        const int64_t i = xrow(P, g);
+        block_row_sums(P, P.X.rp[i] + threadIdx.x, P.X.rp[i + 1], (int64_t)blockDim.x, s, x, mx, red, redx, redm);
+        if (threadIdx.x == 0) {
+            prod[g] = s;
+            xsum[g] = x;
+            ymx[g] = mx;
         }
-        __syncthreads();
-        if (wid == 0) {
-            const bool in = lane < (int)(blockDim.x >> 5);
-            s = in ? red[lane] : 0;
-            x = in ? redx[lane] : 0.0;
-            mx = __reduce_max_sync(FULL, in ? redm[lane] : 0u);
-            for (int d = 16; d; d >>= 1) {
-                s += __shfl_xor_sync(FULL, s, d);
-                x += __shfl_xor_sync(FULL, x, d);
-            }
-            if (lane == 0 && s) atomicAdd((unsigned long long *)(prod + g), s);
-            if (lane == 0 && x > 0.0) atomicAdd(xsum + g, x);
-            if (lane == 0 && mx) atomicMax(ymx + g, mx);
-        }
-        __syncthreads();
+    }
+    const uint32_t n2 = *n_huge;
+    for (uint32_t r = 0; r < n2; r++) {
+        const uint32_t g = huge_rows[r];
+        const Prod &P = prods[rowprod[g]];
+        const int64_t i = xrow(P, g);
+        const int64_t b = P.X.rp[i], e = P.X.rp[i + 1];
+        const int64_t nb = min(G, (e - b + LONGCH - 1) / LONGCH);
+        const int64_t off = (blockIdx.x - ((int64_t)r * 37) % G + G) % G;  // this block's share
+        if (off >= nb) continue;  // uniform over the block
+        block_row_sums(P, b + off * (int64_t)blockDim.x + threadIdx.x, e, nb * (int64_t)blockDim.x, s, x, mx, red,
+                       redx, redm);
+        if (threadIdx.x == 0 && s) atomicAdd((unsigned long long *)(prod + g), s);
+        if (threadIdx.x == 0 && x > 0.0) atomicAdd(xsum + g, x);
+        if (threadIdx.x == 0 && mx) atomicMax(ymx + g, mx);
     }
 }
 
@@ -2438,7 +2459,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         BinTally tally;
         uint32_t offsets[NBINS + 1];
         uint32_t cursors[NBINS];
-        uint32_t n_long, n_mid;
+        uint32_t n_long, n_mid, n_huge;
         unsigned pool_head;  // the pooled pass's work queue
     };
     std::vector<Prod> hp(w);
@@ -2486,8 +2507,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         Mc = wc->mcap;
         wcp = wc->wcap;
     }
-    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows and their block counts
-    // u32[M] each, rowprod i32[M],
+    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows (one block each) and
+    // longer rows (several blocks each) u32[M] each, rowprod i32[M],
     // wave nnz / row pointers i64[M+1], X row sums f64[M], longest masked Y rows u32[M],
     // product descriptors, row0s, per-product stats, two Smalls (M, w: the capacities when
     // the workspace persists)
@@ -2495,8 +2516,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     const size_t o_bin = align256(o_prod + (size_t)Mc * 8);
     const size_t o_list = align256(o_bin + (size_t)Mc);
     const size_t o_long = align256(o_list + (size_t)Mc * 4);
-    const size_t o_longnb = align256(o_long + (size_t)Mc * 4);
-    const size_t o_mid = align256(o_longnb + (size_t)Mc * 4);
+    const size_t o_huge = align256(o_long + (size_t)Mc * 4);
+    const size_t o_mid = align256(o_huge + (size_t)Mc * 4);
     const size_t o_rowprod = align256(o_mid + (size_t)Mc * 4);
     const size_t o_grp = align256(o_rowprod + (size_t)Mc * 4);
     const size_t o_xsum = align256(o_grp + (size_t)(Mc + 1) * 8);
@@ -2529,7 +2550,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     int8_t *bin = (int8_t *)(ws + o_bin);
     uint32_t *list = (uint32_t *)(ws + o_list);
     uint32_t *long_rows = (uint32_t *)(ws + o_long);
-    uint32_t *long_nb = (uint32_t *)(ws + o_longnb);
+    uint32_t *huge_rows = (uint32_t *)(ws + o_huge);
     uint32_t *mid_rows = (uint32_t *)(ws + o_mid);
     int32_t *rowprod = (int32_t *)(ws + o_rowprod);
     int64_t *grp = (int64_t *)(ws + o_grp);
@@ -2599,12 +2620,13 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         stage_mark(prof, 0, 0, s);
         kl(k_rowprod, gr, 256, 0, s, drow0s, w, M, rowprod);
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
-        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, ymx, long_rows, long_nb, &sm_sym->n_long,
-           mid_rows, &sm_sym->n_mid);
+        kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, ymx, long_rows, huge_rows, &sm_sym->n_long,
+           &sm_sym->n_huge, mid_rows, &sm_sym->n_mid);
         kl(k_rowwork_mid, (unsigned)tun.sm_count * 8, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
            (const uint32_t *)mid_rows, (const uint32_t *)&sm_sym->n_mid);
         kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
-           (const uint32_t *)long_rows, (const uint32_t *)long_nb, (const uint32_t *)&sm_sym->n_long);
+           (const uint32_t *)long_rows, (const uint32_t *)huge_rows, (const uint32_t *)&sm_sym->n_long,
+           (const uint32_t *)&sm_sym->n_huge);
         if (mlbuf) {  // only the row work reads the masked lengths (stream-ordered free)
             al.free(mlbuf, s);
             mlbuf = nullptr;
