@@ -1168,6 +1168,7 @@ struct GlobArgs {
     const uint32_t *ymx;      // per wave row: its longest masked Y row (entry_split)
     int ew_max;
     int64_t ech;              // X entries per work item of a row split by entries
+    int64_t items_ub;         // at least the pass's work items (no more blocks than this)
     int64_t r0, r1;           // rows of this round
     uint2 *bmr;               // (r1 - r0) slots of nw {bitmap word, rank} pairs
     int64_t nw;               // slot size (words)
@@ -2035,9 +2036,16 @@ static void run_pass(int pass, const PassArgs &a, const uint32_t *host_counts, i
                 cudaGetLastError();
                 per_sm = 1;
             }
+            // no more blocks than tiles (a few rows need not start every resident slot);
+            // a captured pass keeps the full grid (its counts are only known on the device)
+            uint64_t tiles = 0;
+            for (int b = 0; b < B_GLOBAL; b++)
+                if (pool_bin(b)) tiles += (host_counts[b] + pool_rows_per_tile(b) - 1) / pool_rows_per_tile(b);
+            const uint64_t slots = (uint64_t)sms * per_sm;
+            const unsigned grid = (unsigned)(fixed_grid ? slots : std::max<uint64_t>(1, std::min(slots, tiles)));
             if (!g_attrs_only) {
                 cudaMemsetAsync(a.pool_head, 0, sizeof(unsigned), s);
-                kl(kern, (unsigned)(sms * per_sm), 256, smem, s, a);
+                kl(kern, grid, 256, smem, s, a);
             }
             if (prof && prof->on)
                 cudaEventRecordWithFlags(prof->pev[pass][1], s, g_capturing ? cudaEventRecordExternal : 0);
@@ -2300,6 +2308,7 @@ struct Glob {
     const uint32_t *ymx = nullptr;  // longest masked Y row per wave row
     int ew_max = -1;                // rows with ymx <= ew_max are split by X entries
     int64_t ech = 4096;             // ... into items of this many entries
+    int64_t items_ub = 0;           // an upper bound on the work items of all its rows
     int kinds = 1;                  // bit 0: rows split by products present, bit 1: by entries
     uint2 *bmr = nullptr, *dbmr = nullptr;
     unsigned long long *dval = nullptr;
@@ -2368,7 +2377,7 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
             if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess &&
                 cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k0, GNT, sm) == cudaSuccess && nb > 0) {
-                both(k0, k1, (unsigned)(tun.sm_count * nb), sm);
+                both(k0, k1, (unsigned)std::min<int64_t>((int64_t)tun.sm_count * nb, ga.items_ub), sm);
                 return;
             }
             cudaGetLastError();  // no room: the global-row walk below
@@ -2378,7 +2387,7 @@ static void glob_set(const Tuning &tun, cudaStream_t s, const PassArgs &a, const
         // the bitmap pass at 6 blocks per SM (40 registers), the count-adding passes at
         // lbs_occ (4: 64 registers; 6 spills a few values of the shuffle walk)
         const int lo = MODE == G_SYM || tun.lbs_occ >= 6 ? 6 : 4;
-        const unsigned g = (unsigned)(tun.sm_count * lo);
+        const unsigned g = (unsigned)std::min<int64_t>((int64_t)tun.sm_count * lo, ga.items_ub);
         if (lo == 6) {
             if (tun.combine) both(k_glob_lbs<MODE, true, 6, false, false>, k_glob_lbs<MODE, true, 6, false, true>, g, 0);
             else both(k_glob_lbs<MODE, false, 6, false, false>, k_glob_lbs<MODE, false, 6, false, true>, g, 0);
@@ -2409,9 +2418,9 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
     const unsigned grid = (unsigned)tun.sm_count * 8;
     if (prof && prof->on) cudaEventRecord(prof->ev[pass][B_GLOBAL][0], s);
     if (g.nd) {
-        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys,           g.prod,       g.ymx,  g.ew_max,
-                          g.ech,  0,          g.nd,    g.dbmr, g.nwd,          tun.short_walk, tun.seg_walk, g.dval,
-                          g.dcols};
+        const GlobArgs ga{g.list, g.item_off,  g.xbase, g.xoff, g.ys,  g.prod,         g.ymx,        g.ew_max,
+                          g.ech,  g.items_ub, 0,       g.nd,   g.dbmr, g.nwd,          tun.short_walk, tun.seg_walk,
+                          g.dval, g.dcols};
         const int64_t words = g.nd * g.nwd;
         if (pass == 0) {
             cudaMemsetAsync(g.dval, 0, (size_t)g.nd * g.dcols * 8, s);
@@ -2425,8 +2434,8 @@ static void glob_pass(int pass, Glob &g, const PassArgs &a, const Tuning &tun, c
         }
     }
     for (int64_t r0 = g.nd; r0 < g.R; r0 += g.per_round) {
-        const GlobArgs ga{g.list,  g.item_off, g.xbase, g.xoff, g.ys, g.prod, g.ymx, g.ew_max, g.ech, r0,
-                          std::min(g.R, r0 + g.per_round), g.bmr, g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
+        const GlobArgs ga{g.list, g.item_off, g.xbase, g.xoff, g.ys, g.prod, g.ymx, g.ew_max, g.ech, g.items_ub,
+                          r0,     std::min(g.R, r0 + g.per_round), g.bmr, g.nw, tun.short_walk, tun.seg_walk, nullptr, 0};
         const int64_t rows = ga.r1 - ga.r0;
         if (pass == 0 || !g.kept) {
             cudaMemsetAsync(g.bmr, 0, (size_t)rows * g.nw * 8, s);
@@ -2622,8 +2631,11 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 32);
         kl(k_rowwork, g, 256, 0, s, dprods, rowprod, M, prod, xsum, ymx, long_rows, huge_rows, &sm_sym->n_long,
            &sm_sym->n_huge, mid_rows, &sm_sym->n_mid);
-        kl(k_rowwork_mid, (unsigned)tun.sm_count * 8, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
+        // the mid queue holds at most M rows: no more warps than that
+        kl(k_rowwork_mid, (unsigned)std::min<int64_t>((int64_t)tun.sm_count * 8, (M + 7) / 8), 256, 0, s, dprods, rowprod,
+           prod, xsum, ymx,
            (const uint32_t *)mid_rows, (const uint32_t *)&sm_sym->n_mid);
+        // (huge rows are shared by the whole grid, so this one stays full size)
         kl(k_rowwork_long, (unsigned)tun.sm_count * 4, 256, 0, s, dprods, rowprod, prod, xsum, ymx,
            (const uint32_t *)long_rows, (const uint32_t *)huge_rows, (const uint32_t *)&sm_sym->n_long,
            (const uint32_t *)&sm_sym->n_huge);
@@ -2670,6 +2682,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         gl.ew_max = ba.ew_max;
         gl.ech = std::max<int64_t>(256, tun.ech / 256 * 256);
         gl.kinds = (xtot > 0 ? 1 : 0) | ((uint64_t)xtot < h_sym.tally.xent[B_GLOBAL] ? 2 : 0);
+        gl.items_ub = (int64_t)(h_sym.tally.prods[B_GLOBAL] / PCH + h_sym.tally.xent[B_GLOBAL] / gl.ech) + 2 * gl.R + 1;
         gl.list = (uint32_t *)al.alloc((size_t)gl.R * 4, s);
         gl.item_off = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
         gl.xbase = (int64_t *)al.alloc((size_t)(gl.R + 1) * 8, s);
