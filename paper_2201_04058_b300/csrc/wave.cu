@@ -101,6 +101,7 @@ struct PStat {
     uint32_t unsafe;           // some row's sum times ymax reaches 2^63: counts are checked
     uint32_t err;
     uint32_t sym_bins[NBINS];
+    uint32_t nerr;  // set by the numeric binning (kept apart from err, which it reads)
     uint32_t num_bins[NBINS];
 };
 
@@ -496,10 +497,12 @@ __global__ void k_binassign(const Prod *prods, const int32_t *rowprod, const uin
     if (t == 0 && hd) atomicAdd(&tally->gdense, hd);
 }
 
-// Numeric bins from the exact row sizes (grp = wave row pointers); rows the symbolic pass
-// put in GLOBAL stay there (their bitmaps give the output positions).
+// Numeric bins (bin) from the exact row sizes (grp = wave row pointers) and the symbolic
+// bins (sbin); rows the symbolic pass put in GLOBAL stay there (their bitmaps give the output
+// positions). With ahead set it runs before the outputs are allocated.
 __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_t *grp, const uint64_t *prod,
-                         const uint32_t *ymx, int64_t M, BinArgs ba, int8_t *bin, BinTally *tally, PStat *ps) {
+                         const uint32_t *ymx, int64_t M, BinArgs ba, const int8_t *sbin, int8_t *bin, int ahead,
+                         BinTally *tally, PStat *ps) {
     __shared__ uint32_t hc[NBINS];
     __shared__ unsigned long long hx[NBINS], hp[NBINS], ho[NBINS], hb[NBINS];
     if (threadIdx.x < NBINS) {
@@ -516,17 +519,21 @@ __global__ void k_numbin(const Prod *prods, const int32_t *rowprod, const int64_
         if (g < M) {
             pi = rowprod[g];
             const Prod &P = prods[pi];
-            const int64_t z = P.ci ? grp[g + 1] - grp[g] : 0;  // no outputs: product failed
-            const bool dense = bin[g] == B_GDENSE;
+            // rows of failed products get no bin: ahead of the output allocation the failures
+            // are the ones the earlier passes flagged, after it the products left without outputs
+            const bool live = ahead ? ps[pi].err == 0 : P.ci != nullptr;
+            const int64_t z = live ? grp[g + 1] - grp[g] : 0;
+            const int sb = sbin[g];
+            const bool dense = sb == B_GDENSE;
             if (z) {
-                if (bin[g] == B_GLOBAL || dense) {
+                if (sb == B_GLOBAL || dense) {
                     b = B_GLOBAL;
-                } else if (bin[g] == B_LANE) {
+                } else if (sb == B_LANE) {
                     b = B_LANE;  // z <= prod_i <= LANE_PROD
                 } else {
                     b = bin_for(prod[g], (uint64_t)z, P.Y.ncols, ba.dense_max_cols, ba.dense_min_u, ~0ull, ba.warp_prod,
                                 ba.force);
-                    if (b == B_GLOBAL) atomicOr(&ps[pi].err, ERR_PROBE);  // cannot happen: nnz <= the bound
+                    if (b == B_GLOBAL) atomicOr(&ps[pi].nerr, ERR_PROBE);  // cannot happen: nnz <= the bound
                 }
                 const int64_t i = xrow(P, g);
                 const unsigned long long xe = (unsigned long long)(P.X.rp[i + 1] - P.X.rp[i]);
@@ -2516,14 +2523,15 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         Mc = wc->mcap;
         wcp = wc->wcap;
     }
-    // workspace: prod u64[M], bins i8[M], row list u32[M], long rows (one block each) and
+    // workspace: prod u64[M], symbolic and numeric bins i8[M] each, row list u32[M], long rows (one block each) and
     // longer rows (several blocks each) u32[M] each, rowprod i32[M],
     // wave nnz / row pointers i64[M+1], X row sums f64[M], longest masked Y rows u32[M],
     // product descriptors, row0s, per-product stats, two Smalls (M, w: the capacities when
     // the workspace persists)
     const size_t o_prod = 0;
     const size_t o_bin = align256(o_prod + (size_t)Mc * 8);
-    const size_t o_list = align256(o_bin + (size_t)Mc);
+    const size_t o_nbin = align256(o_bin + (size_t)Mc);
+    const size_t o_list = align256(o_nbin + (size_t)Mc);
     const size_t o_long = align256(o_list + (size_t)Mc * 4);
     const size_t o_huge = align256(o_long + (size_t)Mc * 4);
     const size_t o_mid = align256(o_huge + (size_t)Mc * 4);
@@ -2557,6 +2565,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     };
     uint64_t *prod = (uint64_t *)(ws + o_prod);
     int8_t *bin = (int8_t *)(ws + o_bin);
+    int8_t *nbin = (int8_t *)(ws + o_nbin);
     uint32_t *list = (uint32_t *)(ws + o_list);
     uint32_t *long_rows = (uint32_t *)(ws + o_long);
     uint32_t *huge_rows = (uint32_t *)(ws + o_huge);
@@ -2749,9 +2758,23 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
                256, 0, s, (const Prod *)(dprods + p0), (const int64_t *)grp);
     }
     stage_mark(prof, 3, 1, s);
+    // 3b. numeric bins ahead of the output allocation, read back with the sizes (a product
+    // the host then refuses sends the binning round again)
+    const bool ahead = !symbolic_only && M > 0;
+    const unsigned gnum = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
+    auto numeric_bins = [&](int pre) {
+        stage_mark(prof, 4, 0, s);
+        kl(k_numbin, gnum, 256, 0, s, dprods, rowprod, grp, prod, (const uint32_t *)ymx, M, ba, (const int8_t *)bin,
+           nbin, pre, &sm_num->tally, ps);
+        kl(k_bin_fill, gnum, 256, 0, s, nbin, M, (const uint32_t *)sm_num->tally.counts, sm_num->offsets,
+           sm_num->cursors, list);
+        stage_mark(prof, 4, 1, s);
+    };
+    if (ahead) numeric_bins(1);
     if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
         !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
                  "copy") ||
+        (ahead && !cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy")) ||
         !cuda_ok(cudaStreamSynchronize(s), "sync"))
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);
@@ -2772,7 +2795,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         return MP_OK;
     }
     // per product: status, size guard, output arrays
-    bool any_out = false;
+    bool any_out = false, rebin = false;
     for (int p = 0; p < w; p++) {
         WaveOut &o = out[p];
         o.products = hps[p].prods;
@@ -2788,11 +2811,13 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         m.nnz = nnz;
         if (max_result_bytes && m.bytes() > max_result_bytes) {
             o.status = MP_ERR_TOO_LARGE;
+            rebin = true;  // its rows were binned
             continue;
         }
         if (bud) {
             if (bud->reserve((int64_t)m.bytes())) {
                 o.status = MP_ERR_BUDGET;
+                rebin = true;
                 continue;
             }
             reserved[p] = (int64_t)m.bytes();
@@ -2813,15 +2838,19 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         const void *src = staged ? wc->stage(hp.data(), sizeof(Prod) * w, 0) : hp.data();
         if (!cuda_ok(cudaMemcpyAsync(dprods, src, sizeof(Prod) * w, cudaMemcpyHostToDevice, s), "upload"))
             return fail(MP_ERR_CUDA);
-        const unsigned g = (unsigned)std::min<int64_t>(grid_for(M, 256), (int64_t)tun.sm_count * 16);
-        stage_mark(prof, 4, 0, s);
-        kl(k_numbin, g, 256, 0, s, dprods, rowprod, grp, prod, (const uint32_t *)ymx, M, ba, bin, &sm_num->tally, ps);
-        kl(k_bin_fill, g, 256, 0, s, bin, M, (const uint32_t *)sm_num->tally.counts, sm_num->offsets, sm_num->cursors,
-           list);
-        stage_mark(prof, 4, 1, s);
-        if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
-            !cuda_ok(cudaStreamSynchronize(s), "sync"))
-            return fail(MP_ERR_CUDA);
+        if (rebin || !ahead) {
+            // bins again without the refused products' rows: tallies, queue head and each
+            // product's numeric bin counts and flag start from zero
+            if (!cuda_ok(cudaMemsetAsync(sm_num, 0, sizeof(Small), s), "memset") ||
+                !cuda_ok(cudaMemset2DAsync(&ps[0].nerr, sizeof(PStat), 0, sizeof(uint32_t) * (NBINS + 1), (size_t)w,
+                                           s),
+                         "memset"))
+                return fail(MP_ERR_CUDA);
+            numeric_bins(0);
+            if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
+                !cuda_ok(cudaStreamSynchronize(s), "sync"))
+                return fail(MP_ERR_CUDA);
+        }
         pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
         pa.pool_head = &sm_num->pool_head;
@@ -2838,7 +2867,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
     for (int p = 0; p < w; p++) {
         WaveOut &o = out[p];
         for (int b = 0; b < NBINS; b++) o.num_bins[b] = hps[p].num_bins[b];
-        if (!o.status && hps[p].err) o.status = (hps[p].err & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
+        const uint32_t e = hps[p].err | hps[p].nerr;
+        if (!o.status && e) o.status = (e & ERR_OVERFLOW) ? MP_ERR_OVERFLOW : MP_ERR_INTERNAL;
         if (o.status) {
             unreserve(p);
             if (hp[p].rp) al.free(hp[p].rp, s);

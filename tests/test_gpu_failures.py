@@ -61,6 +61,38 @@ def test_size_guard(c1, cuda_ok):
         e.close()
 
 
+@pytest.mark.parametrize("guard", ["size", "budget"])
+def test_refused_product_beside_others(c1, cuda_ok, guard):
+    """A one-product query whose result is refused (PAP, 1.5 M entries: beyond a 100 kB size
+    guard and a 1 MB HBM budget) runs in the first wave beside the first products of small
+    anchored queries that share no sub-chain with it. Its rows are binned for the numeric
+    pass before the sizes are known; refusing it must leave the others exact."""
+    from paper_2201_04058_b300 import mp
+    h, o = c1
+    kw = {"max_result_bytes": 100_000} if guard == "size" else {"hbm_budget_bytes": 1 << 20}
+    e = mp.Engine(h, policy=mp.MP_POLICY_NONE, **kw)
+    try:
+        rng = np.random.default_rng(11)
+        qs = []
+        for t, n in (("APTPA", 1), ("APTPA", 3), ("PAP", 0), ("APTPA", 2), ("APVPA", 4)):
+            cons = []
+            if n:
+                anchors = np.sort(rng.choice(1500, size=n, replace=False)).astype(np.uint32)
+                cons = [{"pos": 0, "prop": None, "op": "in", "set": anchors}]
+            qs.append({"types": list(t), "constraints": cons})
+        qs.append({"types": list("APVPA"), "constraints": [{"pos": 0, "prop": None, "op": "eq", "lo": 5}]})
+        refused = mp.MP_ERR_TOO_LARGE if guard == "size" else mp.MP_ERR_BUDGET
+        for rnd in range(2):
+            rc, res = e.run_batch(qs)
+            assert res[2] == refused, (rnd, res[2])
+            for i, (q, r) in enumerate(zip(qs, res)):
+                if i != 2:
+                    assert not isinstance(r, int), (rnd, i, r)
+                    assert_same(r, OC.evaluate(o, q), (guard, rnd, i))
+    finally:
+        e.close()
+
+
 def test_release_while_queued(c1, cuda_ok):
     from paper_2201_04058_b300 import mp
     h, _ = c1
