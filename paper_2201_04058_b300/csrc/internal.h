@@ -208,8 +208,33 @@ struct WaveCache {
     char *pinned = nullptr;
     size_t pinned_cap = 0;
     void *stage(const void *src, size_t bytes, size_t at);  // copies to pinned + at; null on failure
+    // pinned host memory the device writes the host's read-backs into (see Readback)
+    char *rb = nullptr;
+    static constexpr size_t RB_BYTES = 1 << 20;
     void drop_graphs();
     void clear(Alloc &al, cudaStream_t s);
+};
+
+// Device-to-host read-backs of small records (bin tallies, sizes, status flags) that take no
+// copy engine: a kernel writes the bytes into the wave cache's pinned host buffer, which the
+// device addresses directly (unified addressing), and sync() moves them into their host
+// destinations once the stream is idle. A cudaMemcpyAsync to the host would queue on the copy
+// engine behind whatever result copies other streams have in flight. Without a wave cache, or
+// when a record does not fit what is left of the buffer, get() falls back to cudaMemcpyAsync.
+class Readback {
+  public:
+    Readback(WaveCache *wc, cudaStream_t s) : wc_(wc), s_(s) {}
+    bool get(void *dst, const void *src, size_t bytes);  // false: a CUDA call failed
+    bool sync();                                         // false: the stream reported an error
+  private:
+    struct Part {
+        void *dst;
+        size_t at, bytes;
+    };
+    WaveCache *wc_;
+    cudaStream_t s_;
+    std::vector<Part> parts_;
+    size_t used_ = 0;
 };
 
 // The HBM byte budget as the wave executor sees it: each product's exact result bytes are

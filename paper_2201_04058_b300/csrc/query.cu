@@ -478,8 +478,8 @@ int mp_ctx::admit(std::vector<Query> &qs_in, const std::vector<uint64_t> &ticket
         }
         std::vector<unsigned long long> h(std::max<size_t>(total, 1), 0);
         if (any) {
-            cudaMemcpyAsync(h.data(), d, std::max<size_t>(total, 1) * 8, cudaMemcpyDeviceToHost, stream);
-            if (cudaStreamSynchronize(stream) != cudaSuccess) {
+            Readback rb(&wcache, stream);
+            if (!rb.get(h.data(), d, std::max<size_t>(total, 1) * 8) || !rb.sync()) {
                 free_tmp();
                 return fail_all(MP_ERR_CUDA);
             }
@@ -1035,8 +1035,8 @@ int mp_ctx::run_wave() {
             const WaveIn &in = win[ycand[c]];
             raw_products(in.X, in.rm, in.km, in.Y.rp, tun, stream, cnt + c);
         }
-        ok = ok && cudaMemcpyAsync(h.data(), cnt, ycand.size() * 8, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
-             cudaStreamSynchronize(stream) == cudaSuccess;
+        Readback rb(&wcache, stream);
+        ok = ok && rb.get(h.data(), cnt, ycand.size() * 8) && rb.sync();
         if (cnt) alloc->free(cnt, stream);
         if (!ok) cudaGetLastError();  // no copies: the masks apply entry by entry
         for (size_t c = 0; ok && c < ycand.size(); c++) {

@@ -2129,12 +2129,54 @@ void WaveCache::clear(Alloc &al, cudaStream_t s) {
     ws = nullptr;
     mcap = 0;
     wcap = 0;
-    if (pinned) {
-        cudaStreamSynchronize(s);  // no upload may still read it
-        cudaFreeHost(pinned);
-    }
+    if (pinned || rb) cudaStreamSynchronize(s);  // no upload may still read it, no read-back write it
+    if (pinned) cudaFreeHost(pinned);
+    if (rb) cudaFreeHost(rb);
     pinned = nullptr;
     pinned_cap = 0;
+    rb = nullptr;
+}
+
+// Copies a record into pinned host memory: 16-byte words when both ends and the size allow,
+// else bytes.
+__global__ void k_readback(const char *__restrict__ src, char *__restrict__ dst, size_t n) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+    if ((((uintptr_t)src | (uintptr_t)dst | n) & 15) == 0) {
+        for (size_t i = t; i < n / 16; i += st) ((int4 *)dst)[i] = __ldg((const int4 *)src + i);
+    } else {
+        for (size_t i = t; i < n; i += st) dst[i] = src[i];
+    }
+}
+
+bool Readback::get(void *dst, const void *src, size_t bytes) {
+    if (!bytes) return true;
+    if (wc_ && !wc_->rb && cudaMallocHost(&wc_->rb, WaveCache::RB_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        wc_->rb = nullptr;
+    }
+    if (!wc_ || !wc_->rb || used_ + bytes > WaveCache::RB_BYTES)
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s_) == cudaSuccess;
+    const unsigned grid = (unsigned)std::min<size_t>((bytes + 4095) / 4096, 64);
+    kl(k_readback, grid, 256, 0, s_, (const char *)src, wc_->rb + used_, bytes);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mp: read-back: %s\n", cudaGetErrorString(e));
+        return false;
+    }
+    parts_.push_back({dst, used_, bytes});
+    used_ += (bytes + 255) / 256 * 256;
+    return true;
+}
+
+bool Readback::sync() {
+    const cudaError_t e = cudaStreamSynchronize(s_);
+    const bool ok = e == cudaSuccess;
+    if (!ok) fprintf(stderr, "mp: sync: %s\n", cudaGetErrorString(e));
+    if (ok)
+        for (const Part &p : parts_) memcpy(p.dst, wc_->rb + p.at, p.bytes);
+    parts_.clear();
+    used_ = 0;
+    return ok;
 }
 
 void *WaveCache::stage(const void *src, size_t bytes, size_t at) {
@@ -2598,6 +2640,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         fprintf(stderr, "mp: %s: %s\n", what, cudaGetErrorString(e));
         return false;
     };
+    Readback rbk(wc, s);  // the bin tallies, sizes and flags the host reads
     if (ml_total) {
         mlbuf = (uint32_t *)al.alloc((size_t)ml_total * 4, s);
         if (!mlbuf) return fail(MP_ERR_NOMEM);
@@ -2660,9 +2703,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
            list);
         stage_mark(prof, 1, 1, s);
     }
-    if (!cuda_ok(cudaMemcpyAsync(&h_sym, sm_sym, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
-        !cuda_ok(cudaStreamSynchronize(s), "sync"))
-        return fail(MP_ERR_CUDA);
+    if (!rbk.get(&h_sym, sm_sym, sizeof(Small)) || !rbk.sync()) return fail(MP_ERR_CUDA);
     pa.counts = sm_sym->tally.counts;
     pa.offsets = sm_sym->offsets;
     pa.pool_head = &sm_sym->pool_head;
@@ -2771,11 +2812,8 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         stage_mark(prof, 4, 1, s);
     };
     if (ahead) numeric_bins(1);
-    if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
-        !cuda_ok(cudaMemcpyAsync(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally), cudaMemcpyDeviceToHost, s),
-                 "copy") ||
-        (ahead && !cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy")) ||
-        !cuda_ok(cudaStreamSynchronize(s), "sync"))
+    if (!rbk.get(hps.data(), ps, sizeof(PStat) * w) || !rbk.get(&h_sym.tally, &sm_sym->tally, sizeof(h_sym.tally)) ||
+        (ahead && !rbk.get(&h_num, sm_num, sizeof(Small))) || !rbk.sync())
         return fail(MP_ERR_CUDA);
     prof_collect(prof, 0, h_sym.tally);
     if (symbolic_only) {
@@ -2847,9 +2885,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
                          "memset"))
                 return fail(MP_ERR_CUDA);
             numeric_bins(0);
-            if (!cuda_ok(cudaMemcpyAsync(&h_num, sm_num, sizeof(Small), cudaMemcpyDeviceToHost, s), "copy") ||
-                !cuda_ok(cudaStreamSynchronize(s), "sync"))
-                return fail(MP_ERR_CUDA);
+            if (!rbk.get(&h_num, sm_num, sizeof(Small)) || !rbk.sync()) return fail(MP_ERR_CUDA);
         }
         pa.counts = sm_num->tally.counts;
         pa.offsets = sm_num->offsets;
@@ -2857,9 +2893,7 @@ int spgemm_wave(const std::vector<WaveIn> &in, Alloc &al, const Tuning &tun, cud
         if (graphs) run_pass_graph(1, pa, h_num.tally.counts, dense_cols, tun, s, prof, *wc);
         else run_pass(1, pa, h_num.tally.counts, dense_cols, tun, s, prof);
         if (gl.R) glob_pass(1, gl, pa, tun, s, prof);
-        if (!cuda_ok(cudaMemcpyAsync(hps.data(), ps, sizeof(PStat) * w, cudaMemcpyDeviceToHost, s), "copy") ||
-            !cuda_ok(cudaStreamSynchronize(s), "sync"))
-            return fail(MP_ERR_CUDA);
+        if (!rbk.get(hps.data(), ps, sizeof(PStat) * w) || !rbk.sync()) return fail(MP_ERR_CUDA);
         prof_collect(prof, 1, h_num.tally);
     }
     stage_collect(prof);
