@@ -35,6 +35,59 @@ def test_oracle_matches_bruteforce(seed, hin, queries):
         assert csr_to_dict(rp, ci, val) == enumerate_counts(hin, q, adj), q
 
 
+def _compound_queries(hin, seed, n):
+    """Queries whose positions carry one to three constraints at once, mixing every kind
+    the boundary takes: a property range, a property equality, a property value set, an id
+    window, an id equality and an id set."""
+    g = np.random.default_rng(9000 + seed)
+    out = []
+    for _ in range(n):
+        types = gen.schema_walk(g, gen.SCHOLARLY_STAR, int(g.integers(2, 7)))
+        cons = []
+        for i, t in enumerate(types):
+            if g.random() < 0.4:
+                continue
+            nt = hin["types"][t]
+            for _k in range(int(g.integers(1, 4))):
+                kind = int(g.integers(6))
+                if kind == 0:
+                    lo = int(g.integers(1980, 2022))
+                    cons.append({"pos": i, "prop": "year", "op": "range", "lo": lo, "hi": int(g.integers(lo, 2023))})
+                elif kind == 1:
+                    v = int(hin["props"][(t, "year")][int(g.integers(nt))])
+                    cons.append({"pos": i, "prop": "year", "op": "eq", "lo": v})
+                elif kind == 2:
+                    vals = hin["props"][(t, "year")][g.integers(0, nt, size=int(g.integers(1, 4)))]
+                    cons.append({"pos": i, "prop": "year", "op": "in", "set": np.unique(vals).astype(np.uint32)})
+                elif kind == 3:
+                    lo = int(g.integers(nt))
+                    cons.append({"pos": i, "prop": None, "op": "range", "lo": lo, "hi": int(g.integers(lo, nt))})
+                elif kind == 4:
+                    cons.append({"pos": i, "prop": None, "op": "eq", "lo": int(g.integers(nt))})
+                else:
+                    ids = np.unique(g.integers(0, nt, size=int(g.integers(1, nt + 1)))).astype(np.uint32)
+                    cons.append({"pos": i, "prop": None, "op": "in", "set": ids})
+        out.append({"types": types, "constraints": cons})
+    return out
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_oracle_matches_bruteforce_compound_constraints(seed):
+    """Every constraint at a position must hold (Def. 3): the oracle's masks, ANDed over a
+    position's constraints of all kinds, against the brute-force enumeration."""
+    h = gen.tiny_hin(100 + seed, max_nodes=9)
+    o = OracleHIN(h)
+    adj = adjacency(h)
+    nonempty = 0
+    for q in _compound_queries(h, seed, 16):
+        rp, ci, val = OC.evaluate(o, q)
+        check_canonical(rp, ci, val, h["types"][q["types"][0]], h["types"][q["types"][-1]])
+        want = enumerate_counts(h, q, adj)
+        assert csr_to_dict(rp, ci, val) == want, q
+        nonempty += bool(want)
+    assert nonempty > 0  # the constraints leave some instances in some queries
+
+
 def test_total_equals_instance_count():
     h = gen.tiny_hin(77, max_nodes=10)
     o = OracleHIN(h)
