@@ -216,9 +216,10 @@ struct WaveCache {
 };
 
 // Device-to-host read-backs of small records (bin tallies, sizes, status flags) that take no
-// copy engine: a kernel writes the bytes into the wave cache's pinned host buffer, which the
-// device addresses directly (unified addressing), and sync() moves them into their host
-// destinations once the stream is idle. A cudaMemcpyAsync to the host would queue on the copy
+// copy engine: at sync() one kernel writes every queued record into the wave cache's pinned
+// host buffer, which the device addresses directly (unified addressing), and once the stream
+// is idle the bytes move into their host destinations. The sources must not change on the
+// stream between get() and sync(). A cudaMemcpyAsync to the host would queue on the copy
 // engine behind whatever result copies other streams have in flight. Without a wave cache, or
 // when a record does not fit what is left of the buffer, get() falls back to cudaMemcpyAsync.
 class Readback {
@@ -229,6 +230,7 @@ class Readback {
   private:
     struct Part {
         void *dst;
+        const void *src;
         size_t at, bytes;
     };
     WaveCache *wc_;

@@ -2137,9 +2137,17 @@ void WaveCache::clear(Alloc &al, cudaStream_t s) {
     rb = nullptr;
 }
 
-// Copies a record into pinned host memory: 16-byte words when both ends and the size allow,
-// else bytes.
-__global__ void k_readback(const char *__restrict__ src, char *__restrict__ dst, size_t n) {
+// Copies records into pinned host memory, one record per grid row (blockIdx.y): 16-byte
+// words when both ends and the size allow, else bytes.
+struct RbSegs {
+    static constexpr int MAX = 8;
+    const char *src[MAX];
+    size_t at[MAX], n[MAX];
+};
+__global__ void k_readback(RbSegs g, char *__restrict__ dst_base) {
+    const char *__restrict__ src = g.src[blockIdx.y];
+    char *__restrict__ dst = dst_base + g.at[blockIdx.y];
+    const size_t n = g.n[blockIdx.y];
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
     if ((((uintptr_t)src | (uintptr_t)dst | n) & 15) == 0) {
         for (size_t i = t; i < n / 16; i += st) ((int4 *)dst)[i] = __ldg((const int4 *)src + i);
@@ -2156,22 +2164,38 @@ bool Readback::get(void *dst, const void *src, size_t bytes) {
     }
     if (!wc_ || !wc_->rb || used_ + bytes > WaveCache::RB_BYTES)
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s_) == cudaSuccess;
-    const unsigned grid = (unsigned)std::min<size_t>((bytes + 4095) / 4096, 64);
-    kl(k_readback, grid, 256, 0, s_, (const char *)src, wc_->rb + used_, bytes);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        fprintf(stderr, "mp: read-back: %s\n", cudaGetErrorString(e));
-        return false;
-    }
-    parts_.push_back({dst, used_, bytes});
+    // the copy itself is launched by sync(), with the other records, in one kernel
+    parts_.push_back({dst, src, used_, bytes});
     used_ += (bytes + 255) / 256 * 256;
     return true;
 }
 
 bool Readback::sync() {
+    bool ok = true;
+    for (size_t p0 = 0; ok && p0 < parts_.size(); p0 += RbSegs::MAX) {
+        RbSegs g{};
+        size_t most = 0;
+        const int k = (int)std::min<size_t>(RbSegs::MAX, parts_.size() - p0);
+        for (int i = 0; i < k; i++) {
+            const Part &p = parts_[p0 + i];
+            g.src[i] = (const char *)p.src;
+            g.at[i] = p.at;
+            g.n[i] = p.bytes;
+            most = std::max(most, p.bytes);
+        }
+        kl(k_readback, dim3((unsigned)std::min<size_t>((most + 4095) / 4096, 64), (unsigned)k), 256, 0, s_, g,
+           wc_->rb);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            fprintf(stderr, "mp: read-back: %s\n", cudaGetErrorString(e));
+            ok = false;
+        }
+    }
     const cudaError_t e = cudaStreamSynchronize(s_);
-    const bool ok = e == cudaSuccess;
-    if (!ok) fprintf(stderr, "mp: sync: %s\n", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mp: sync: %s\n", cudaGetErrorString(e));
+        ok = false;
+    }
     if (ok)
         for (const Part &p : parts_) memcpy(p.dst, wc_->rb + p.at, p.bytes);
     parts_.clear();
