@@ -180,3 +180,75 @@ def test_pgds_ignores_subtree():
     c.request(icpal, 2, 10, 4)
     c.request(icpa, 3, 6, 4)
     assert c.entries[icpal].c == 10
+
+
+# ---------------------------------------------------------------- reductions and invariants
+
+def _lru_evictions(trace, slots):
+    """Textbook LRU over unit-size items: the evicted keys in order."""
+    from collections import OrderedDict
+    held, out = OrderedDict(), []
+    for k in trace:
+        if k in held:
+            held.move_to_end(k)
+            continue
+        if len(held) == slots:
+            out.append(held.popitem(last=False)[0])
+        held[k] = True
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_dual_with_uniform_items_is_lru(seed):
+    """With every frequency, cost and size equal, h = const + l and l only grows, so the
+    smallest utility is the entry touched longest ago: PGDS and ATRAPOS (keys with no
+    prefix relation) evict exactly as LRU does (the Greedy-Dual reduction to LRU)."""
+    rng = np.random.default_rng(700 + seed)
+    keys = [(tuple(f"K{i:02d}"), "") for i in range(12)]  # keys of one length: none a prefix of another
+    trace = [keys[int(i)] for i in rng.integers(0, len(keys), size=300)]
+    want = _lru_evictions(trace, 5)
+    for policy in ("pgds", "atrapos", "lru"):
+        c = Cache(5, policy, max_fraction=1.0)
+        for k in trace:
+            c.request(k, 1, 1, 1)
+        assert c.evicted == want, policy
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_atrapos_without_subtrees_is_pgds(seed):
+    """Alg. 1's subtree cost updates act only between keys where one is a proper prefix of
+    the other; on keys of one length ATRAPOS and PGDS make the same choices."""
+    rng = np.random.default_rng(800 + seed)
+    keys = [(tuple(rng.choice(list("APVT"), size=3)), "") for _ in range(15)]
+    a, p = Cache(40, "atrapos"), Cache(40, "pgds")
+    for _ in range(400):
+        k = keys[int(rng.integers(len(keys)))]
+        f, cost, size = int(rng.integers(1, 6)), float(rng.integers(1, 50)), float(rng.integers(1, 12))
+        assert a.request(k, f, cost, size) == p.request(k, f, cost, size)
+    assert a.evicted == p.evicted and a.L == p.L
+
+
+@pytest.mark.parametrize("policy", ["atrapos", "pgds", "lru"])
+def test_capacity_and_accounting_invariants(policy):
+    """After every request the bytes held equal the sum of the entries' sizes and never
+    pass the capacity, and costs stay non-negative. Under PGDS the inflation L never
+    decreases (every cached utility is at least the L it was set with); under ATRAPOS it can,
+    since a cached sub-metapath lowers the costs, hence the utilities, of its subtree."""
+    rng = np.random.default_rng(900)
+    alphabet = list("APVT")
+    keys = []
+    for _ in range(40):
+        n = int(rng.integers(2, 6))
+        keys.append((tuple(rng.choice(alphabet, size=n)), ""))
+    keys += [(k[0][:2], "") for k in keys[:10]]  # prefixes, so subtrees exist
+    c = Cache(100, policy)
+    last_L = 0.0
+    for _ in range(1500):
+        k = keys[int(rng.integers(len(keys)))]
+        c.request(k, int(rng.integers(1, 9)), float(rng.integers(1, 100)), float(rng.integers(1, 40)))
+        assert c.used == pytest.approx(sum(e.s for e in c.entries.values()))
+        assert c.used <= c.capacity + 1e-9
+        assert all(e.c >= 0 for e in c.entries.values())
+        if policy == "pgds":
+            assert c.L >= last_L
+        last_L = c.L
